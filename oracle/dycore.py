@@ -1,0 +1,358 @@
+"""Oracle dynamical core (Sec. 3-4), float64, numpy.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Prognostic state (Arakawa-A in the horizontal, Sec. 2.2; vertical momentum at
+the layer interfaces, Sec. 3):
+
+  rho  (N, nv)      density at the centres
+  M    (N, nv, 3)   horizontal momentum rho v_h as a Cartesian vector
+  W    (N, nv+1)    vertical momentum rho v_r at the interfaces, W = 0 at the
+                    bottom and top (rigid lid, Sec. 3)
+  Th   (N, nv)      rho theta
+
+Readings (listed in the design doc):
+
+R1  Time stepping. Sec. 3 calls each of the three Wicker-Skamarock stages a
+    "large time step" when it gives the small-step counts (1 step of dt/3,
+    n/2 steps of dt/n, n steps of dt/n). We read the small-step equations
+    (Eqs. dens2, mom2, momr2, pt2) the same way: Phi^[t] there is the state
+    of the current stage Phi^(s), the slow terms and the linearisation
+    coefficients are evaluated at Phi^(s), and the deviations
+    Phi* = Phi - Phi^(s) start each stage at Phi^t - Phi^(s), so the inner
+    loop always integrates from Phi^t and the stage ends at
+    Phi^(s+1) = Phi^(s) + Phi*. With the acoustic terms frozen this is exactly
+    the RK3 update Phi^(s+1) = Phi^t + dt_s R(Phi^(s)).
+R2  Eq. pt2: (rho v)^[tau+dtau] is the total momentum Phi^(s) + Phi*, and the
+    radial operator is the deep one, r^-2 d(r^2 .)/dr, as in Eq. dens2.
+R3  Eq. vr22 is garbled. The vertical system is instead the exact discrete
+    substitution of the discrete Eqs. dens2 and pt2 into the discrete
+    Eq. momr2, with p* advanced linearly, p*+ = p* + Pi (Th+ - Th),
+    Pi = (cp/cv) p^(s)/Th^(s). Unknown: W* at the interior interfaces.
+    After the solve rho* and Th follow exactly from Eqs. dens2 and pt2 and
+    p* from the nonlinear Eq. theta_to_p.
+R4  Hyperdiffusion (Sec. 4, Eqs. diff_rho ... diff_p): every momentum
+    component is rho-weighted, F_M = -lap(rho K_d lap v_h) component-wise and
+    projected, like Eq. diff_vr; the third line of Eq. diff_vz is F_vhz. F_p
+    enters as a slow tendency of rho theta, F_Th = Th/(gamma p) F_p.
+R5  The divergence damping of Eqs. diff_vx-vz, -K_d lap(grad_h D) with D the
+    3-D divergence of the momentum, is evaluated every small step (Sec. 4)
+    from the current total momentum and then projected.
+R6  Advection and Coriolis (Sec. 3): A_j = div(rho v v_j) for the three
+    Cartesian components of the full velocity v = M/rho + (W/rho) r, then
+    projected by Eqs. proj_h / proj_r; their radial parts are interpolated
+    to the interfaces.
+R7  K_d = D dbar^4 / dt (Eq. kd) with dbar from Eq. grid_qts; the
+    nondimensional D of a planet follows from its Table 1 diffusion time
+    scale through Eq. tau_d at the paper's own time step.
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import operators as op
+from .grid import mean_resolution
+
+
+@dataclass
+class Planet:
+    radius: float
+    omega: float
+    gravity: float
+    Rd: float
+    cp: float
+    p_ref: float = 1.0e5          # Sec. 3: p_ref = 1 bar
+    diff_D: float = 0.0           # nondimensional diffusion parameter of Eq. kd
+
+    @property
+    def cv(self):
+        return self.cp - self.Rd
+
+    @property
+    def gamma(self):
+        return self.cp / self.cv
+
+    @property
+    def kappa(self):
+        return self.Rd / self.cp
+
+
+def diffusion_parameter(dt_paper, tau_d):
+    """Eqs. kd and tau_d: tau_d = dbar^4/(32 K_d) and K_d = D dbar^4/dt give
+    D = dt / (32 tau_d)."""
+    return dt_paper / (32.0 * tau_d)
+
+
+@dataclass
+class State:
+    rho: np.ndarray
+    M: np.ndarray
+    W: np.ndarray
+    Th: np.ndarray
+
+    def copy(self):
+        return State(self.rho.copy(), self.M.copy(), self.W.copy(), self.Th.copy())
+
+
+@dataclass
+class Model:
+    grid: object
+    vg: object
+    planet: Planet
+    forcing: str = "none"          # "none" | "held_suarez" | "hot_jupiter"
+    hj_dT: float = 300.0           # Eq. teq-hj day-night contrast
+    hyperdiffusion: bool = True
+    divergence_damping: bool = True
+    Kd_fixed: float = None         # a fixed K_d instead of Eq. kd (tests)
+    rhat: np.ndarray = field(init=False)
+
+    def __post_init__(self):
+        self.rhat = self.grid.points
+
+    def Kd(self, dt):
+        """Eq. kd."""
+        if self.Kd_fixed is not None:
+            return self.Kd_fixed
+        _, dbar, _ = mean_resolution(self.grid.glevel, self.planet.radius)
+        return self.planet.diff_D * dbar ** 4 / dt
+
+
+# ------------------------------------------------------------ thermodynamics
+
+def pressure(planet, Th):
+    """Eq. pressure: p = p_ref (Rd rho theta / p_ref)^(cp/cv)."""
+    return planet.p_ref * (planet.Rd * Th / planet.p_ref) ** planet.gamma
+
+
+def rhotheta_from_p(planet, p):
+    """Inverse of Eq. pressure."""
+    return planet.p_ref / planet.Rd * (p / planet.p_ref) ** (1.0 / planet.gamma)
+
+
+def temperature(planet, rho, p):
+    """Ideal gas, Sec. 3: p = rho Rd T."""
+    return p / (rho * planet.Rd)
+
+
+# ------------------------------------------------------------- slow terms
+
+def hyperdiffusion(model, X, p, Kd):
+    """Sec. 4, Eqs. diff_rho ... diff_p with readings R4, R7."""
+    g, vg, pl = model.grid, model.vg, model.planet
+    rho_i = op.interp_to_interfaces(vg, X.rho)
+    vh = X.M / X.rho[..., None]
+    vr = np.zeros_like(X.W)
+    vr[:, 1:-1] = X.W[:, 1:-1] / rho_i[:, 1:-1]
+    T = temperature(pl, X.rho, p)
+
+    F_rho = -op.lap_levels(g, vg, Kd * op.lap_levels(g, vg, X.rho))
+    lv = op.vlap_levels(g, vg, vh)
+    F_M = -op.vlap_levels(g, vg, X.rho[..., None] * Kd * lv)
+    F_M = op.project_h(model.rhat, F_M)
+    F_W = np.zeros_like(X.W)
+    inner = op.lap_levels(g, vg, vr, at_interfaces=True)
+    F_W[:, 1:-1] = -op.lap_levels(g, vg, rho_i * Kd * inner, at_interfaces=True)[:, 1:-1]
+    F_p = -pl.Rd * op.lap_levels(g, vg, X.rho * Kd * op.lap_levels(g, vg, T))
+    F_Th = X.Th / (pl.gamma * p) * F_p
+    return F_rho, F_M, F_W, F_Th
+
+
+def slow_terms(model, X, Kd):
+    """Right-hand sides of Eqs. dens2, mom2, momr2 and pt2 at the stage state
+    X = Phi^(s) (reading R1), plus the small-step coefficients."""
+    g, vg, pl = model.grid, model.vg, model.planet
+    rhat = model.rhat
+    N, nv = X.rho.shape
+    p = pressure(pl, X.Th)
+
+    # full 3-D momentum and velocity at the centres (reading R6)
+    Wc = op.interp_to_centres(vg, X.W)
+    mom = X.M + Wc[..., None] * rhat[:, None, :]
+    vel = mom / X.rho[..., None]
+
+    # advection A_j = div_h(M v_j) + r^-2 d(r^2 W v_j)/dr
+    A = np.zeros((N, nv, 3))
+    for j in range(3):
+        A[..., j] = op.div_h_levels(g, vg, X.M * vel[..., j:j + 1]) \
+            + op.div_v(vg, X.W * op.interp_to_interfaces(vg, vel[..., j]))
+    # Coriolis 2 Omega x (rho v), Omega along z
+    Om = np.array([0.0, 0.0, pl.omega])
+    C = 2.0 * np.cross(Om[None, None, :], mom)
+    AC_h = op.project_h(rhat, A + C)
+    AC_r = op.interp_to_interfaces(vg, op.radial(rhat, A + C))
+
+    rho_i = op.interp_to_interfaces(vg, X.rho)
+
+    if model.hyperdiffusion:
+        F_rho, F_M, F_W, F_Th = hyperdiffusion(model, X, p, Kd)
+    else:
+        F_rho, F_M, F_W, F_Th = (np.zeros_like(X.rho), np.zeros_like(X.M),
+                                 np.zeros_like(X.W), np.zeros_like(X.Th))
+
+    S_M = op.project_h(rhat, -op.grad_h_levels(g, vg, p) - AC_h + F_M)
+    S_W = -op.ddz_at_interfaces(vg, p) - pl.gravity * rho_i - AC_r + F_W
+    S_W[:, 0] = 0.0
+    S_W[:, -1] = 0.0
+    S_rho = -op.div_h_levels(g, vg, X.M) - op.div_v(vg, X.W) + F_rho
+    S_Th = F_Th
+
+    theta = X.Th / X.rho
+    return dict(p=p, S_M=S_M, S_W=S_W, S_rho=S_rho, S_Th=S_Th, theta=theta,
+                theta_i=op.interp_to_interfaces(vg, theta),
+                Pi=pl.gamma * p / X.Th)
+
+
+# ----------------------------------------------------------- vertical solve
+
+def vertical_matrices(vg):
+    """Discrete vertical operators of one column as dense matrices acting on
+    the interior interfaces (1..nv-1) or on the centres (0..nv-1):
+    Dv (nv x nv-1) = r^-2 d(r^2 .)/dr restricted to the interior interfaces,
+    Gz (nv-1 x nv) = d/dr from centres to interfaces,
+    Iz (nv-1 x nv) = Lagrange k = 1 interpolation from centres to interfaces."""
+    nv = vg.nv
+    E = np.eye(nv + 1)[:, 1:-1]                       # interior interface basis
+    Dv = op.div_v(vg, E.T).T                          # (nv, nv-1)
+    Ec = np.eye(nv)
+    Gz = op.ddz_at_interfaces(vg, Ec)[:, 1:-1].T      # (nv-1, nv)
+    Iz = op.interp_to_interfaces(vg, Ec)[:, 1:-1].T   # (nv-1, nv)
+    return Dv, Gz, Iz
+
+
+def vertical_solve(model, dtau, Wstar, S_W, a, b, c, theta_i, Pi):
+    """Reading R3. With
+        rho*+ = a - dtau Dv W,   Th+ = b - dtau Dv diag(theta_i) W,
+        p*+   = c - dtau diag(Pi) Dv diag(theta_i) W,
+        W     = W* + dtau (S_W - Gz p*+ - g Iz rho*+)
+    the unknown W (interior interfaces of every column) solves
+        [I - dtau^2 Gz diag(Pi) Dtheta - dtau^2 g Iz Dv] W
+            = W* + dtau S_W - dtau Gz c - dtau g Iz a,
+    solved here with a dense batched LU (numpy.linalg.solve)."""
+    vg, pl = model.vg, model.planet
+    nv = vg.nv
+    Dv, Gz, Iz = vertical_matrices(vg)
+    N = a.shape[0]
+    th = theta_i[:, 1:-1]                              # (N, nv-1)
+    Dth = Dv[None, :, :] * th[:, None, :]              # (N, nv, nv-1)
+    GPi = Gz[None, :, :] * Pi[:, None, :]              # (N, nv-1, nv)
+    A = np.eye(nv - 1)[None] - dtau ** 2 * (GPi @ Dth) - dtau ** 2 * pl.gravity * (Iz @ Dv)[None]
+    rhs = Wstar[:, 1:-1] + dtau * S_W[:, 1:-1] - dtau * (c @ Gz.T) - dtau * pl.gravity * (a @ Iz.T)
+    Wint = np.linalg.solve(A, rhs[..., None])[..., 0]
+    W = np.zeros((N, nv + 1))
+    W[:, 1:-1] = Wint
+    return W
+
+
+# ----------------------------------------------------------- small step
+
+def small_step(model, Xs, co, pert, dtau, Kd):
+    """One forward-backward small step (Sec. 3), order of Sec. 3: horizontal
+    momentum (explicit, Eq. mom2 with the divergence damping of Sec. 4), then
+    vertical momentum (implicit, Eq. momr2), then density (Eq. dens2), then
+    rho theta (Eq. pt2) and p* (Eq. theta_to_p)."""
+    g, vg, pl = model.grid, model.vg, model.planet
+    rhat = model.rhat
+    rho_s, M_s, W_s, Th = pert["rho"], pert["M"], pert["W"], pert["Th"]
+    p_s = pert["p"]
+
+    # divergence damping (reading R5)
+    if model.divergence_damping:
+        D = op.div_h_levels(g, vg, Xs.M + M_s) + op.div_v(vg, Xs.W + W_s)
+        G = op.grad_h_levels(g, vg, D)
+        DD = op.project_h(rhat, -Kd * op.vlap_levels(g, vg, G))
+    else:
+        DD = 0.0
+
+    # Eq. mom2 (explicit)
+    M_new = op.project_h(rhat, M_s + dtau * (-op.grad_h_levels(g, vg, p_s) + DD + co["S_M"]))
+
+    # Eqs. dens2 / pt2 with everything but the implicit vertical fluxes
+    theta = co["theta"]
+    a = rho_s + dtau * (co["S_rho"] - op.div_h_levels(g, vg, M_new))
+    Mtot = Xs.M + M_new
+    b = Th + dtau * (co["S_Th"] - op.div_h_levels(g, vg, theta[..., None] * Mtot)
+                     - op.div_v(vg, co["theta_i"] * Xs.W))
+    c = p_s + co["Pi"] * (b - Th)
+
+    # Eq. momr2 (implicit, reading R3)
+    W_new = vertical_solve(model, dtau, W_s, co["S_W"], a, b, c, co["theta_i"], co["Pi"])
+
+    # Eq. dens2 and Eq. pt2 with the new vertical momentum
+    rho_new = a - dtau * op.div_v(vg, W_new)
+    Th_new = b - dtau * op.div_v(vg, co["theta_i"] * W_new)
+    # Eq. theta_to_p
+    p_new = pressure(pl, Th_new) - co["p"]
+    return dict(rho=rho_new, M=M_new, W=W_new, Th=Th_new, p=p_new)
+
+
+# ----------------------------------------------------------- large step
+
+def stage_schedule(dt, n_small):
+    """Sec. 3 (Wicker-Skamarock RK3 with the Klemp small-step counts):
+    (dtau, number of small steps) for the three stages."""
+    if n_small < 2 or n_small % 2:
+        raise ValueError("n_small must be even and >= 2")
+    return [(dt / 3.0, 1), (dt / n_small, n_small // 2), (dt / n_small, n_small)]
+
+
+def large_step(model, X, dt, n_small):
+    """One large step: three RK3 stages of small steps (reading R1), then the
+    physics of Sec. 5."""
+    from .physics import apply_physics
+    Kd = model.Kd(dt)
+    Xt = X
+    Xs = X
+    for dtau, nsub in stage_schedule(dt, n_small):
+        co = slow_terms(model, Xs, Kd)
+        pert = dict(rho=Xt.rho - Xs.rho, M=Xt.M - Xs.M, W=Xt.W - Xs.W, Th=Xt.Th.copy(),
+                    p=pressure(model.planet, Xt.Th) - co["p"])
+        for _ in range(nsub):
+            pert = small_step(model, Xs, co, pert, dtau, Kd)
+        Xs = State(Xs.rho + pert["rho"], Xs.M + pert["M"], Xs.W + pert["W"], pert["Th"])
+    return apply_physics(model, Xs, dt)
+
+
+def run(model, X, n_large, n_small, dt):
+    for _ in range(n_large):
+        X = large_step(model, X, dt, n_small)
+    return X
+
+
+# ----------------------------------------------------------- initial state
+
+def hydrostatic_profile(model, T, p_surf):
+    """Discretely balanced column for the layer temperatures T (nv,):
+    (p_i - p_i-1)/dz + g rho_iface = 0 at every interior interface, with
+    rho = p/(Rd T) and rho_iface the Lagrange k = 1 interpolation, so that
+    the slow vertical force of Eq. momr2 vanishes at rest. The lowest centre
+    is p_surf exp(-g z_0 / (Rd T_0)) (hydrostatic at constant T)."""
+    vg, pl = model.vg, model.planet
+    nv = vg.nv
+    p = np.zeros(nv)
+    p[0] = p_surf * np.exp(-pl.gravity * vg.zc[0] / (pl.Rd * T[0]))
+    for i in range(1, nv):
+        z0, z1, zh = vg.zc[i - 1], vg.zc[i], vg.zi[i]
+        w0 = (zh - z1) / (z0 - z1)
+        w1 = (zh - z0) / (z1 - z0)
+        dz = z1 - z0
+        p[i] = p[i - 1] * (1.0 - pl.gravity * dz * w0 / (pl.Rd * T[i - 1])) \
+            / (1.0 + pl.gravity * dz * w1 / (pl.Rd * T[i]))
+    return p
+
+
+def initial_state(model, T0, p_surf, noise_amp=0.0, u=None):
+    """Isothermal atmosphere at rest in discrete hydrostatic balance (Sec. 6
+    starts both benchmarks at rest in hydrostatic equilibrium). With
+    ``noise_amp`` > 0 the temperature gets amp (2u - 1) at fixed pressure, so
+    the perturbation is carried by the density; ``u`` (N, nv) in [0, 1) are
+    the random numbers, passed in."""
+    pl = model.planet
+    N, nv = model.grid.ncol, model.vg.nv
+    p1 = hydrostatic_profile(model, np.full(nv, T0), p_surf)
+    p = np.broadcast_to(p1, (N, nv)).copy()
+    T = np.full((N, nv), float(T0))
+    if noise_amp > 0.0:
+        T = T + noise_amp * (2.0 * u - 1.0)
+    rho = p / (pl.Rd * T)
+    return State(rho, np.zeros((N, nv, 3)), np.zeros((N, nv + 1)), rhotheta_from_p(pl, p))
