@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Throughput of the THOR HE-VI dynamical core on GB300.
+
+One step = one large step of the Held-Suarez workload (glevel 6, 40962
+columns x 32 levels, dt = 600 s, 8 small steps: 13 small steps per large
+step), i.e. three RK3 slow-term evaluations with hyperdiffusion, 13 acoustic
+small steps (divergence damping, explicit horizontal momentum, tridiagonal
+vertical solve, density, rho theta, pressure) and the Held-Suarez physics.
+
+Metric: cell-substeps/s = columns x levels x small steps / wall time, plus
+model days per hour. Default precision: mixed (float32 fields and stencils,
+float64 vertical solve); a float64 leg is reported beside it.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank advances its own replica (the path needs no
+exchange between replicas; scaling "weak"); rank 0 prints one JSON line.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wls  # noqa: E402
+
+METRIC = "cell-substeps/s"
+
+# Unique field words each kernel reads or writes per cell (neighbour reads of
+# a field counted once), the counting rule of the algorithmic roofline.
+KERNEL_WORDS = {
+    "derived": 6 + 10, "lap1": 8 + 6, "slow": 17 + 8, "slow_w": 7 + 2, "stage_init": 13 + 7,
+    "ss_div": 5 + 1, "ss_grad": 1 + 3, "ss_mom": 10 + 3, "ss_col": 15 + 4, "stage_end": 12 + 6,
+    "physics": 5 + 4,
+}
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def workload_of(name):
+    return {"hs_g6": wls.HS_G6.with_(spring_max_iter=100000, spring_tol=1e-5),
+            "hs_g4": wls.HS_G4, "hj_g6": wls.HJ_G6}[name]
+
+
+# ------------------------------------------------------------------ oracle
+
+def oracle_sample(wl, n_small_steps=1):
+    """Time the oracle on a bounded sample of the workload: one slow-term
+    evaluation, ``n_small_steps`` small steps and one physics call, then
+    scale to a large step (3 slow evaluations + S_n small steps + physics)."""
+    from oracle import dycore as dc
+    from oracle import operators as op
+    from oracle import physics as ph
+    from oracle.grid import build_grid
+    P = wl.planet
+    G = build_grid(wl.glevel, max_iter=10, tol=0.0)
+    pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+    m = dc.Model(G, op.VerticalGrid(wl.nv, wl.z_top, P.radius), pl, forcing=wl.forcing,
+                 hj_dT=wl.hj_dT)
+    u = wls.temperature_noise(wl, G.ncol)
+    X = dc.initial_state(m, wl.T0, wl.p_surf, wl.noise_amp, u)
+    Kd = m.Kd(wl.dt)
+    t0 = time.perf_counter()
+    co = dc.slow_terms(m, X, Kd)
+    t_slow = time.perf_counter() - t0
+    pert = dict(rho=np.zeros_like(X.rho), M=np.zeros_like(X.M), W=np.zeros_like(X.W),
+                Th=X.Th.copy(), p=np.zeros_like(X.rho))
+    t0 = time.perf_counter()
+    for _ in range(n_small_steps):
+        pert = dc.small_step(m, X, co, pert, wl.dt / wl.n_small, Kd)
+    t_small = (time.perf_counter() - t0) / n_small_steps
+    t0 = time.perf_counter()
+    ph.apply_physics(m, X, wl.dt)
+    t_phys = time.perf_counter() - t0
+    return m, X, co, t_slow, t_small, t_phys
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores (rank 0 only)."""
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    wl = workload_of(args.workload)
+    from oracle import dycore as dc
+    m, X, co, t_slow, t_small, t_phys = oracle_sample(wl)
+    Kd = m.Kd(wl.dt)
+    pert = dict(rho=np.zeros_like(X.rho), M=np.zeros_like(X.M), W=np.zeros_like(X.W),
+                Th=X.Th.copy(), p=np.zeros_like(X.rho))
+    dtau = wl.dt / wl.n_small
+    for _ in range(args.warmup):
+        pert = dc.small_step(m, X, co, pert, dtau, Kd)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pert = dc.small_step(m, X, co, pert, dtau, Kd)
+    t = time.perf_counter() - t0
+    sn = wl.substeps_per_large
+    per_large = sn * t / args.steps + 3 * t_slow + t_phys
+    value = wl.cells * sn / per_large
+    sample = (f"each step = one oracle small step of {wl.name} ({wl.cells} cells); the value "
+              f"scales it to a large step with the measured slow-term ({t_slow:.2f} s) and "
+              f"physics ({t_phys:.2f} s) costs: 3 slow + {sn} small + physics")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(wl, "f64"),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(wl, precision):
+    return {"workload": wl.name, "glevel": wl.glevel, "ncol": wl.ncol, "nv": wl.nv,
+            "dt_s": wl.dt, "n_small": wl.n_small, "substeps_per_large_step": wl.substeps_per_large,
+            "forcing": wl.forcing, "precision": precision,
+            "l2": "inputs larger than L2: state + stage work set at g6x32 exceed 129 MB"}
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_thor(args):
+    import torch
+    import paper_1607_05535_gb300 as thor
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    wl = workload_of(args.workload)
+    P = wl.planet
+    forcing = {"none": 0, "held_suarez": 1, "hot_jupiter": 2}[wl.forcing]
+    sp = thor.thor_spring(1.15, 1.0, 1.0, 0.01, wl.spring_tol, wl.spring_max_iter)
+    grid = thor.thor_grid_create(wl.glevel, wl.nv, P.radius, wl.z_top, sp)
+    planet = thor.thor_planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+
+    def make_state(prec):
+        init = thor.thor_init(wl.T0, wl.p_surf, wl.noise_amp, wl.seed, forcing, wl.hj_dT, prec, 1, 1)
+        return thor.thor_state_init(grid, planet, init, stream.cuda_stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(state, steps):
+        """CUDA-event time (ms) of ``steps`` large steps on the state's stream."""
+        barrier()
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            thor.thor_step(state, 1, wl.n_small, wl.dt)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        return a.elapsed_time(b)
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    sn = wl.substeps_per_large
+    cells = wl.cells
+
+    # ---- mixed precision, the headline
+    st = make_state(thor.THOR_MIXED)
+    for _ in range(args.warmup):
+        thor.thor_step(st, 1, wl.n_small, wl.dt)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    thor.thor_profile(st, 1)
+    l0 = thor.thor_launch_count(st)
+    ms = timed(st, args.steps)
+    launches = thor.thor_launch_count(st) - l0
+    clocks = sampler.stop() if sampler else None
+    prof = {}
+    for kid, name in enumerate(thor.KERNELS):
+        tot, n = thor.thor_profile_read(st, kid)
+        if n:
+            prof[name] = (tot, n)
+    thor.thor_profile(st, 0)
+    ms = max_over_ranks(ms)
+    diag = thor.thor_diag(st)
+    value = world * cells * sn * args.steps / (ms / 1e3)
+    days_per_hour = world * args.steps * wl.dt / 86400.0 / (ms / 1e3 / 3600.0)
+
+    # dominant kernel and its roofline
+    dom = max(prof, key=lambda k: prof[k][0])
+    tot, n = prof[dom]
+    nlev = wl.nv + 1 if dom in ("slow_w",) else wl.nv
+    bytes_per_launch = KERNEL_WORDS[dom] * 4 * wl.ncol * nlev
+    achieved = bytes_per_launch / (tot / n / 1e3) / 1e9
+    peak, peak_kind = _peaks()
+    kernels = {k: {"ms_total": round(v[0], 4), "launches": v[1], "us_avg": round(1e3 * v[0] / v[1], 2),
+                   "share": round(v[0] / sum(x[0] for x in prof.values()), 4)} for k, v in prof.items()}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    shapes = {thor.THOR_FIELD_RHO: (wl.ncol, wl.nv), thor.THOR_FIELD_MOM: (wl.ncol, wl.nv, 3),
+              thor.THOR_FIELD_W: (wl.ncol, wl.nv + 1), thor.THOR_FIELD_RHOTHETA: (wl.ncol, wl.nv)}
+    host = {f: torch.empty(s, dtype=torch.float64, pin_memory=True) for f, s in shapes.items()}
+    for f, h in host.items():
+        thor.thor_state_get(st, f, wl.ncol, wl.nv, out=h.numpy())
+    e2e_steps = max(1, min(args.steps, 10))
+    nbytes = sum(h.numel() * 8 for h in host.values())
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for f, h in host.items():
+            thor.thor_state_set(st, f, h)
+        thor.thor_step(st, 1, wl.n_small, wl.dt)
+        for f, h in host.items():
+            thor.thor_state_get(st, f, wl.ncol, wl.nv, out=h.numpy())
+    torch.cuda.synchronize(dev)
+    barrier()
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    e2e = world * cells * sn * e2e_steps / t_e2e
+    thor.thor_state_destroy(st)
+
+    # ---- float64 leg
+    st64 = make_state(thor.THOR_FP64)
+    for _ in range(min(args.warmup, 2)):
+        thor.thor_step(st64, 1, wl.n_small, wl.dt)
+    k64 = max(1, min(args.steps, 5))
+    ms64 = max_over_ranks(timed(st64, k64))
+    thor.thor_state_destroy(st64)
+    value64 = world * cells * sn * k64 / (ms64 / 1e3)
+    thor.thor_grid_destroy(grid)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config(wl, "mixed: f32 fields and stencils, f64 vertical solve"),
+        "model_days_per_hour": days_per_hour,
+        "fp64": {"value": value64, "unit": METRIC, "steps": k64, "ms_per_step": ms64 / k64,
+                 "model_days_per_hour": world * k64 * wl.dt / 86400.0 / (ms64 / 1e3 / 3600.0)},
+        "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                "steps": e2e_steps},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "us_per_launch": 1e3 * tot / n},
+        "kernels": kernels,
+        "clocks": clocks,
+        "diag_after": {k: diag[k] for k in ("mass", "max_vh", "max_w", "mean_T", "nonfinite")},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        _, _, _, t_slow, t_small, t_phys = oracle_sample(wl)
+        per_large = 3 * t_slow + sn * t_small + t_phys
+        line["cpu_baseline"] = {
+            "value": cells * sn / per_large, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": (f"{wl.name}: one oracle slow-term evaluation ({t_slow:.1f} s), one small step "
+                       f"({t_small:.1f} s) and one physics call, scaled to 3 slow + {sn} small + "
+                       "physics per large step; numpy float64, single thread")}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="thor", choices=["thor", "reference"])
+    ap.add_argument("--workload", default="hs_g6", choices=["hs_g6", "hs_g4", "hj_g6"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)      # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_thor(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * libthor: C ABI of a GB300 (sm_103a) implementation of the THOR dynamical
+ * core's hot path (Mendonca, Grimm, Grosheintz and Heng 2016, "THOR: a new
+ * and flexible global circulation model to explore planetary atmospheres").
+ *
+ * Conventions for every entry point:
+ *  - Return value: THOR_OK (0) or a negative THOR_E* status; nothing throws
+ *    across the ABI. thor_strerror() names a status.
+ *  - Handles (thor_grid, thor_state) and all device memory are owned by the
+ *    library; the caller owns every host buffer it passes and keeps it valid
+ *    for the duration of the call only.
+ *  - Host arrays are float64 in the canonical order: column-major over the
+ *    grid columns, then levels, then vector components, i.e. C arrays
+ *    [ncol][nv] for centre scalars, [ncol][nv][3] for Cartesian vectors and
+ *    [ncol][nv+1] for interface scalars. Column numbering: 10 rhombi of
+ *    n x n points (n = 2^glevel), column r*n*n + j*n + i for rhombus r and
+ *    lattice point (i, j), then the north and the south pole.
+ *  - A handle is not thread-safe; use one state per stream. `stream` is a
+ *    cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Invalid arguments give THOR_EINVAL and leave every handle unchanged.
+ */
+#ifndef THOR_H
+#define THOR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  THOR_OK = 0,
+  THOR_EINVAL = -1,      /* bad argument or size */
+  THOR_ENOMEM = -2,      /* host or device allocation failed */
+  THOR_ECUDA = -3,       /* a CUDA runtime call failed */
+  THOR_ENONFINITE = -4,  /* the state holds NaN or Inf after a step */
+  THOR_ETIMEOUT = -5,    /* a bounded device wait gave up */
+  THOR_ENOTCONV = -6     /* an iteration did not converge where required */
+};
+
+enum { THOR_FP64 = 0, THOR_MIXED = 1 };
+enum { THOR_FORCING_NONE = 0, THOR_FORCING_HELD_SUAREZ = 1, THOR_FORCING_HOT_JUPITER = 2 };
+enum {
+  THOR_FIELD_RHO = 0,       /* density, [ncol][nv]                         */
+  THOR_FIELD_MOM = 1,       /* horizontal momentum rho v_h, [ncol][nv][3]  */
+  THOR_FIELD_W = 2,         /* vertical momentum rho v_r, [ncol][nv+1]     */
+  THOR_FIELD_RHOTHETA = 3,  /* rho theta, [ncol][nv]                       */
+  THOR_FIELD_PRESSURE = 4,  /* p (get only), [ncol][nv]                    */
+  THOR_FIELD_TEMPERATURE = 5 /* T (get only), [ncol][nv]                   */
+};
+
+typedef struct thor_grid thor_grid;
+typedef struct thor_state thor_state;
+
+const char* thor_strerror(int status);
+
+/* ------------------------------------------------------------------ grid */
+
+/* Spring-dynamics parameters (Sec. 2.2, Eqs. spring_force, spr_vel, dbar):
+ * natural-length factor beta (1.15), friction alpha (1), spring constant k
+ * (1), time step dt (0.01), stop when every |dP/dt| < tol (1e-5; tol <= 0
+ * runs exactly max_iter steps). */
+typedef struct {
+  double beta, alpha, k, dt, tol;
+  int max_iter;
+} thor_spring;
+
+/* Build the modified icosahedral grid of Sec. 2 (recursive bisection glevel
+ * times, spring dynamics, centroid relocation, metric terms) on the host in
+ * float64, plus the vertical grid: nv uniform layers from 0 to z_top above a
+ * sphere of `radius` (deep atmosphere, Sec. 3). spring = NULL uses the
+ * defaults above. glevel in [0, 10], nv in [2, 256], radius > 0, z_top > 0,
+ * else THOR_EINVAL. No device memory is touched. */
+int thor_grid_create(int glevel, int nv, double radius, double z_top,
+                     const thor_spring* spring, thor_grid** out);
+
+/* Sizes: ncol = 10*4^glevel + 2, nv, npent = 12, the spring iterations run
+ * and whether the tol criterion was met. Any output pointer may be NULL. */
+int thor_grid_info(const thor_grid* grid, int* ncol, int* nv, int* npent,
+                   int* spring_iters, int* spring_converged);
+
+/* Cell centres on the unit sphere, xyz[ncol][3]; n must be 3*ncol. */
+int thor_grid_points(const thor_grid* grid, double* xyz, size_t n);
+
+/* Counter-clockwise neighbours, nbr[ncol][6], -1 in slot 5 of the 12
+ * pentagons; n must be 6*ncol. */
+int thor_grid_neighbours(const thor_grid* grid, int* nbr, size_t n);
+
+/* Control-volume areas A_c on the unit sphere, area[ncol]; n must be ncol. */
+int thor_grid_areas(const thor_grid* grid, double* area, size_t n);
+
+void thor_grid_destroy(thor_grid* grid);
+
+/* ----------------------------------------------------------------- state */
+
+/* Planet (Table 1): radius (m), rotation rate (1/s), gravity (m/s^2), gas
+ * constant Rd and cp (J/kg/K), reference pressure p_ref of Eq. pressure (Pa)
+ * and the nondimensional diffusion parameter D of Eq. kd
+ * (K_d = D dbar^4/dt; D = dt/(32 tau_d) from Eq. tau_d). radius must equal
+ * the grid's radius. */
+typedef struct {
+  double radius, omega, gravity, Rd, cp, p_ref, diff_D;
+} thor_planet;
+
+/* Initial state and run options. The atmosphere starts at rest, isothermal
+ * at T0, in discrete hydrostatic balance with the lowest layer at
+ * p_surf*exp(-g z_0/(Rd T0)); noise_amp > 0 adds amp*(2u-1) K to T at fixed
+ * p, u = top 53 bits of SplitMix64(seed XOR (col*nv + k)) / 2^53 (Steele, Lea
+ * and Flood 2014). forcing selects Sec. 6.1 (Held-Suarez) or Sec. 6.2
+ * (hot Jupiter, day-night contrast hj_dT) physics after each large step.
+ * precision: THOR_FP64 (all float64) or THOR_MIXED (float32 fields and
+ * stencils, float64 metric terms, vertical solve and reductions).
+ * hyperdiffusion / divergence_damping: 1 = on (Sec. 4), 0 = off. */
+typedef struct {
+  double T0, p_surf, noise_amp;
+  unsigned long long seed;
+  int forcing;
+  double hj_dT;
+  int precision;
+  int hyperdiffusion;
+  int divergence_damping;
+} thor_init;
+
+/* Allocate the device state for `grid` and set the initial condition. The
+ * grid must outlive the state. */
+int thor_state_init(thor_grid* grid, const thor_planet* planet, const thor_init* init,
+                    void* stream, thor_state** out);
+
+/* Advance n_large large steps of dt seconds (Sec. 3): per large step three
+ * Wicker-Skamarock RK3 stages with 1, n_small/2 and n_small forward-backward
+ * small steps (dt/3, dt/n_small, dt/n_small), each small step = divergence
+ * damping, explicit horizontal momentum (Eq. mom2), implicit vertical
+ * momentum (Eq. momr2, tridiagonal per column), density (Eq. dens2),
+ * rho theta (Eq. pt2) and pressure (Eq. theta_to_p); then the physics
+ * (Sec. 5). Asynchronous on the state's stream. n_small even and >= 2,
+ * n_large >= 0, dt > 0, else THOR_EINVAL. */
+int thor_step(thor_state* state, int n_large, int n_small, double dt);
+
+/* Global diagnostics in float64 (deterministic two-pass reductions):
+ * mass = sum rho V, energy = sum (rho cv T + |rho v|^2/(2 rho) + rho g z) V,
+ * axial angular momentum = sum (r x rho v)_z V + sum rho Omega r_perp^2 V,
+ * max |v_h|, max |w|, volume-mean T and the count of non-finite values.
+ * Synchronises the stream. */
+typedef struct {
+  double mass, energy, aam, max_vh, max_w, mean_T;
+  long long nonfinite;
+} thor_diag_t;
+int thor_diag(thor_state* state, thor_diag_t* out);
+
+/* Copy a field to / from a float64 host buffer in the canonical order; n is
+ * the element count of the field. Synchronous. set accepts RHO, MOM, W and
+ * RHOTHETA; W's bottom and top interfaces are forced to 0. */
+int thor_state_get(thor_state* state, int field, double* host, size_t n);
+int thor_state_set(thor_state* state, int field, const double* host, size_t n);
+
+/* Kernel launches issued by this state so far. */
+int thor_launch_count(const thor_state* state, long long* count);
+
+/* Per-kernel timing. While enabled, every launch of the state is bracketed by
+ * two CUDA events recorded on the state's stream; thor_profile_read
+ * synchronises the stream and returns, for one kernel id, the summed
+ * event-measured duration (ms) and the number of launches since the last
+ * thor_profile(state, 1). enable = 0 stops recording. */
+enum {
+  THOR_K_DERIVED = 0, THOR_K_LAP1, THOR_K_SLOW, THOR_K_SLOW_W, THOR_K_STAGE_INIT,
+  THOR_K_SS_DIV, THOR_K_SS_GRAD, THOR_K_SS_MOM, THOR_K_SS_COL, THOR_K_STAGE_END,
+  THOR_K_PHYSICS, THOR_K_COUNT
+};
+int thor_profile(thor_state* state, int enable);
+int thor_profile_read(thor_state* state, int kernel, double* total_ms, long long* launches);
+
+void thor_state_destroy(thor_state* state);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* THOR_H */

@@ -1,0 +1,220 @@
+"""Python binding of libthor (include/thor.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and passes
+plain pointers and sizes through ctypes; all arithmetic of the method runs in
+libthor's CUDA kernels (and its float64 host grid builder). Importing this
+module fails loudly if the library has not been built
+(``python -m paper_1607_05535_gb300.build`` or ``__graft_entry__.build()``).
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBRARY_PATH = os.path.join(_HERE, "libthor.so")
+
+THOR_OK, THOR_EINVAL, THOR_ENOMEM, THOR_ECUDA, THOR_ENONFINITE, THOR_ETIMEOUT, THOR_ENOTCONV = \
+    0, -1, -2, -3, -4, -5, -6
+THOR_FP64, THOR_MIXED = 0, 1
+THOR_FORCING_NONE, THOR_FORCING_HELD_SUAREZ, THOR_FORCING_HOT_JUPITER = 0, 1, 2
+THOR_FIELD_RHO, THOR_FIELD_MOM, THOR_FIELD_W, THOR_FIELD_RHOTHETA, THOR_FIELD_PRESSURE, \
+    THOR_FIELD_TEMPERATURE = range(6)
+
+EXPORTED = [
+    "thor_strerror", "thor_grid_create", "thor_grid_info", "thor_grid_points",
+    "thor_grid_neighbours", "thor_grid_areas", "thor_grid_destroy", "thor_state_init",
+    "thor_step", "thor_diag", "thor_state_get", "thor_state_set", "thor_launch_count",
+    "thor_profile", "thor_profile_read", "thor_state_destroy",
+]
+
+# kernel ids of thor_profile_read
+KERNELS = ["derived", "lap1", "slow", "slow_w", "stage_init", "ss_div", "ss_grad", "ss_mom",
+           "ss_col", "stage_end", "physics"]
+
+
+class thor_spring(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("alpha", ctypes.c_double), ("k", ctypes.c_double),
+                ("dt", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int)]
+
+
+class thor_planet(ctypes.Structure):
+    _fields_ = [("radius", ctypes.c_double), ("omega", ctypes.c_double),
+                ("gravity", ctypes.c_double), ("Rd", ctypes.c_double), ("cp", ctypes.c_double),
+                ("p_ref", ctypes.c_double), ("diff_D", ctypes.c_double)]
+
+
+class thor_init(ctypes.Structure):
+    _fields_ = [("T0", ctypes.c_double), ("p_surf", ctypes.c_double),
+                ("noise_amp", ctypes.c_double), ("seed", ctypes.c_ulonglong),
+                ("forcing", ctypes.c_int), ("hj_dT", ctypes.c_double),
+                ("precision", ctypes.c_int), ("hyperdiffusion", ctypes.c_int),
+                ("divergence_damping", ctypes.c_int)]
+
+
+class thor_diag_t(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("energy", ctypes.c_double), ("aam", ctypes.c_double),
+                ("max_vh", ctypes.c_double), ("max_w", ctypes.c_double),
+                ("mean_T", ctypes.c_double), ("nonfinite", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ThorError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {_lib.thor_strerror(status).decode()} ({status})")
+
+
+def _load():
+    if not os.path.exists(LIBRARY_PATH):
+        raise ImportError(f"libthor is not built ({LIBRARY_PATH} missing); run "
+                          "`python -m paper_1607_05535_gb300.build`")
+    lib = ctypes.CDLL(LIBRARY_PATH)
+    P, I, D, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    IP = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "thor_strerror": (ctypes.c_char_p, [I]),
+        "thor_grid_create": (I, [I, I, D, D, ctypes.POINTER(thor_spring), ctypes.POINTER(P)]),
+        "thor_grid_info": (I, [P, IP, IP, IP, IP, IP]),
+        "thor_grid_points": (I, [P, P, Z]),
+        "thor_grid_neighbours": (I, [P, P, Z]),
+        "thor_grid_areas": (I, [P, P, Z]),
+        "thor_grid_destroy": (None, [P]),
+        "thor_state_init": (I, [P, ctypes.POINTER(thor_planet), ctypes.POINTER(thor_init), P,
+                                ctypes.POINTER(P)]),
+        "thor_step": (I, [P, I, I, D]),
+        "thor_diag": (I, [P, ctypes.POINTER(thor_diag_t)]),
+        "thor_state_get": (I, [P, I, P, Z]),
+        "thor_state_set": (I, [P, I, P, Z]),
+        "thor_launch_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+        "thor_profile": (I, [P, I]),
+        "thor_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_longlong)]),
+        "thor_state_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status, where):
+    if status != THOR_OK:
+        raise ThorError(status, where)
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or a torch tensor (host or device)."""
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def thor_strerror(status):
+    return _lib.thor_strerror(status).decode()
+
+
+def thor_grid_create(glevel, nv, radius, z_top, spring=None):
+    out = ctypes.c_void_p()
+    sp = ctypes.byref(spring) if spring is not None else None
+    _check(_lib.thor_grid_create(glevel, nv, radius, z_top, sp, ctypes.byref(out)), "thor_grid_create")
+    return out
+
+
+def thor_grid_info(grid):
+    v = [ctypes.c_int() for _ in range(5)]
+    _check(_lib.thor_grid_info(grid, *[ctypes.byref(x) for x in v]), "thor_grid_info")
+    return dict(ncol=v[0].value, nv=v[1].value, npent=v[2].value, spring_iters=v[3].value,
+                spring_converged=bool(v[4].value))
+
+
+def thor_grid_points(grid):
+    n = thor_grid_info(grid)["ncol"]
+    out = np.empty((n, 3), dtype=np.float64)
+    _check(_lib.thor_grid_points(grid, _ptr(out), out.size), "thor_grid_points")
+    return out
+
+
+def thor_grid_neighbours(grid):
+    n = thor_grid_info(grid)["ncol"]
+    out = np.empty((n, 6), dtype=np.int32)
+    _check(_lib.thor_grid_neighbours(grid, _ptr(out), out.size), "thor_grid_neighbours")
+    return out
+
+
+def thor_grid_areas(grid):
+    n = thor_grid_info(grid)["ncol"]
+    out = np.empty(n, dtype=np.float64)
+    _check(_lib.thor_grid_areas(grid, _ptr(out), out.size), "thor_grid_areas")
+    return out
+
+
+def thor_grid_destroy(grid):
+    _lib.thor_grid_destroy(grid)
+
+
+def thor_state_init(grid, planet, init, stream=None):
+    out = ctypes.c_void_p()
+    _check(_lib.thor_state_init(grid, ctypes.byref(planet), ctypes.byref(init),
+                                ctypes.c_void_p(stream or 0), ctypes.byref(out)), "thor_state_init")
+    return out
+
+
+def thor_step(state, n_large, n_small, dt):
+    _check(_lib.thor_step(state, n_large, n_small, dt), "thor_step")
+
+
+def thor_diag(state):
+    d = thor_diag_t()
+    _check(_lib.thor_diag(state, ctypes.byref(d)), "thor_diag")
+    return d.as_dict()
+
+
+def _field_shape(field, ncol, nv):
+    if field == THOR_FIELD_MOM:
+        return (ncol, nv, 3)
+    if field == THOR_FIELD_W:
+        return (ncol, nv + 1)
+    return (ncol, nv)
+
+
+def thor_state_get(state, field, ncol, nv, out=None):
+    shape = _field_shape(field, ncol, nv)
+    if out is None:
+        out = np.empty(shape, dtype=np.float64)
+    _check(_lib.thor_state_get(state, field, _ptr(out), int(np.prod(shape))), "thor_state_get")
+    return out
+
+
+def thor_state_set(state, field, host):
+    a = host if hasattr(host, "data_ptr") else np.ascontiguousarray(host, dtype=np.float64)
+    n = a.numel() if hasattr(a, "numel") else a.size
+    _check(_lib.thor_state_set(state, field, _ptr(a), n), "thor_state_set")
+
+
+def thor_launch_count(state):
+    c = ctypes.c_longlong()
+    _check(_lib.thor_launch_count(state, ctypes.byref(c)), "thor_launch_count")
+    return c.value
+
+
+def thor_profile(state, enable):
+    _check(_lib.thor_profile(state, int(bool(enable))), "thor_profile")
+
+
+def thor_profile_read(state, kernel):
+    """(total ms, launches) of kernel id ``kernel`` (an index of KERNELS)."""
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    _check(_lib.thor_profile_read(state, kernel, ctypes.byref(ms), ctypes.byref(n)), "thor_profile_read")
+    return ms.value, n.value
+
+
+def thor_state_destroy(state):
+    _lib.thor_state_destroy(state)

@@ -1,0 +1,625 @@
+// C ABI of libthor (declared in include/thor.h): handles, initial state,
+// field transfer in the canonical order, diagnostics.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "../../include/thor.h"
+#include "grid.h"
+#include "thor_impl.cuh"
+
+struct thor_grid {
+  thor::HostGrid h;
+};
+
+struct thor_state {
+  thor_grid* grid = nullptr;
+  int precision = THOR_FP64;
+  std::unique_ptr<thor::ImplBase> impl;
+};
+
+namespace thor {
+namespace {
+
+inline int colp_of(int ncol) { return (ncol + kBlock - 1) / kBlock * kBlock; }
+
+uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// ------------------------------------------------------------ transfers
+
+// canonical float64 [ncol][nv(+1)][ncomp] -> device planes, reference removed
+template <typename R>
+__global__ void k_from_canonical(const double* src, int ncol, int colp, int nlev, int ncomp,
+                                 const double* ref, R* d0, R* d1, R* d2, int zero_ends) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int k = blockIdx.y;
+  if (c >= ncol) return;
+  R* dst[3] = {d0, d1, d2};
+  for (int j = 0; j < ncomp; ++j) {
+    double v = src[((size_t)c * nlev + k) * ncomp + j];
+    if (ref) v -= ref[k];
+    if (zero_ends && (k == 0 || k == nlev - 1)) v = 0.0;
+    dst[j][(size_t)k * colp + c] = (R)v;
+  }
+}
+
+// device planes -> canonical float64; field selects the reconstruction
+template <typename R>
+__global__ void k_to_canonical(double* dst, Geo<R> G, Vert V, Phys ph, Xf<R> X, int field) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int k = blockIdx.y;
+  if (c >= G.ncol) return;
+  const int S = G.colp, nv = G.nv;
+  size_t i = (size_t)k * S + c;
+  switch (field) {
+    case THOR_FIELD_RHO:
+      dst[(size_t)c * nv + k] = V.rhob[k] + (double)X.rho[i];
+      break;
+    case THOR_FIELD_MOM:
+      dst[((size_t)c * nv + k) * 3 + 0] = (double)X.mx[i];
+      dst[((size_t)c * nv + k) * 3 + 1] = (double)X.my[i];
+      dst[((size_t)c * nv + k) * 3 + 2] = (double)X.mz[i];
+      break;
+    case THOR_FIELD_W:
+      dst[(size_t)c * (nv + 1) + k] = (double)X.w[i];
+      break;
+    case THOR_FIELD_RHOTHETA:
+      dst[(size_t)c * nv + k] = V.thb[k] + (double)X.th[i];
+      break;
+    case THOR_FIELD_PRESSURE:
+    case THOR_FIELD_TEMPERATURE: {
+      double thp = (double)X.th[i];
+      double p = V.pb[k] + V.pb[k] * expm1(ph.gamma * log1p(thp / V.thb[k]));
+      if (field == THOR_FIELD_PRESSURE) {
+        dst[(size_t)c * nv + k] = p;
+      } else {
+        double rho = V.rhob[k] + (double)X.rho[i];
+        dst[(size_t)c * nv + k] = p / (rho * ph.Rd);
+      }
+      break;
+    }
+  }
+}
+
+// ------------------------------------------------------------ diagnostics
+
+constexpr int kDiagBlocks = 512;
+constexpr int kDiagThreads = 256;
+
+struct Kahan {
+  double s = 0, c = 0;
+  __device__ void add(double x) {
+    double y = x - c;
+    double t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+// partial sums per block: mass, energy, aam, sum V T, sum V, max vh, max w, nonfinite
+template <typename R>
+__global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Geo<R> G, Vert V, Phys ph, Xf<R> X,
+                                                               double* part) {
+  const int S = G.colp, nv = G.nv;
+  const long long ncell = (long long)G.ncol * nv;
+  Kahan mass, en, aam, vt, vs;
+  double mvh = 0, mw = 0;
+  double nf = 0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    int k = (int)(q / G.ncol), c = (int)(q % G.ncol);
+    size_t i = (size_t)k * S + c;
+    double rx = G.rhat[c], ry = G.rhat[S + c], rz = G.rhat[2 * S + c];
+    double rho = V.rhob[k] + (double)X.rho[i];
+    double th = V.thb[k] + (double)X.th[i];
+    double p = V.pb[k] + V.pb[k] * expm1(ph.gamma * log1p((double)X.th[i] / V.thb[k]));
+    double Temp = p / (rho * ph.Rd);
+    double wlo = X.w[i], whi = X.w[i + S];
+    double wc = V.clo[k] * wlo + V.chi[k] * whi;
+    double mx = (double)X.mx[i] + wc * rx, my = (double)X.my[i] + wc * ry, mz = (double)X.mz[i] + wc * rz;
+    double vol = G.area[c] * V.rc[k] * V.rc[k] * V.dz[k];
+    mass.add(vol * rho);
+    en.add(vol * (rho * ph.cv * Temp + 0.5 * (mx * mx + my * my + mz * mz) / rho + rho * ph.g * V.zc[k]));
+    double r = V.rc[k];
+    aam.add(vol * (r * (rx * my - ry * mx) + rho * ph.omega * r * r * (rx * rx + ry * ry)));
+    vt.add(vol * Temp);
+    vs.add(vol);
+    double hx = (double)X.mx[i] / rho, hy = (double)X.my[i] / rho, hz = (double)X.mz[i] / rho;
+    mvh = fmax(mvh, sqrt(hx * hx + hy * hy + hz * hz));
+    if (k >= 1) {
+      double rif = V.wlo[k] * (V.rhob[k - 1] + (double)X.rho[i - S]) + V.whi[k] * rho;
+      mw = fmax(mw, fabs(wlo / rif));
+    }
+    double vals[6] = {(double)X.rho[i], (double)X.mx[i], (double)X.my[i], (double)X.mz[i], th, (double)X.w[i]};
+    for (int j = 0; j < 6; ++j)
+      if (!isfinite(vals[j])) nf += 1.0;
+    if (k == nv - 1 && !isfinite((double)X.w[i + S])) nf += 1.0;
+  }
+  __shared__ double sh[8][kDiagThreads];
+  double mine[8] = {mass.s, en.s, aam.s, vt.s, vs.s, mvh, mw, nf};
+  for (int j = 0; j < 8; ++j) sh[j][threadIdx.x] = mine[j];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int j = 0; j < 8; ++j) {
+        double a = sh[j][threadIdx.x], b = sh[j][threadIdx.x + w];
+        sh[j][threadIdx.x] = (j == 5 || j == 6) ? fmax(a, b) : a + b;
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 8; ++j) part[blockIdx.x * 8 + j] = sh[j][0];
+}
+
+__global__ void k_diag_final(double* part, int nblocks) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double out[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double comp[5] = {0, 0, 0, 0, 0};
+  for (int b = 0; b < nblocks; ++b)
+    for (int j = 0; j < 8; ++j) {
+      double x = part[b * 8 + j];
+      if (j == 5 || j == 6) {
+        out[j] = fmax(out[j], x);
+      } else if (j == 7) {
+        out[j] += x;
+      } else {
+        double y = x - comp[j];
+        double t = out[j] + y;
+        comp[j] = (t - out[j]) - y;
+        out[j] = t;
+      }
+    }
+  for (int j = 0; j < 8; ++j) part[nblocks * 8 + j] = out[j];
+}
+
+// ------------------------------------------------------------ allocation
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t n) {
+    size_t bytes = (n * sizeof(T) + 255) / 256 * 256;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+template <typename R>
+void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
+  const size_t S = (size_t)colp_of(ncol);
+  const size_t C = S * nv, F = S * (nv + 1);
+  auto X = [&](Xf<R>& x) {
+    x.rho = cv.take<R>(C); x.mx = cv.take<R>(C); x.my = cv.take<R>(C); x.mz = cv.take<R>(C);
+    x.th = cv.take<R>(C); x.w = cv.take<R>(F);
+  };
+  X(I.Xt);
+  X(I.Xst);
+  Work<R>& T = I.T;
+  R** cen[] = {&T.pp, &T.Tp, &T.theta, &T.vx, &T.vy, &T.vz, &T.vhx, &T.vhy, &T.vhz,
+               &T.qrho, &T.qvx, &T.qvy, &T.qvz, &T.qT, &T.dd, &T.gx, &T.gy, &T.gz};
+  for (R** p : cen) *p = cv.take<R>(C);
+  T.vr = cv.take<R>(F);
+  T.qvr = cv.take<R>(F);
+  Slow<R>& SL = I.SL;
+  R** sc[] = {&SL.smx, &SL.smy, &SL.smz, &SL.srho, &SL.sth, &SL.dsc, &SL.acr, &SL.pi};
+  for (R** p : sc) *p = cv.take<R>(C);
+  SL.sw = cv.take<R>(F);
+  SL.thi = cv.take<R>(F);
+  Pert<R>& P = I.P;
+  R** pc[] = {&P.rho, &P.mx, &P.my, &P.mz, &P.th, &P.p};
+  for (R** p : pc) *p = cv.take<R>(C);
+  P.w = cv.take<R>(F);
+  // tables
+  I.G.nbr = cv.take<int>(6 * S);
+  I.G.wdiv = cv.take<R>(21 * S);
+  I.G.wgrad = cv.take<R>(21 * S);
+  I.G.wlap = cv.take<R>(7 * S);
+  I.G.rhat = cv.take<R>(3 * S);
+  I.G.sinlat = cv.take<R>(S);
+  I.G.coslat = cv.take<R>(S);
+  I.G.coslon = cv.take<R>(S);
+  I.G.area = cv.take<double>(S);
+  const double** vp[] = {&I.V.rc, &I.V.dz, &I.V.clo, &I.V.chi, &I.V.zc, &I.V.rhob, &I.V.thb, &I.V.pb, &I.V.Tb};
+  for (const double** p : vp) *p = cv.take<double>(nv);
+  const double** vi[] = {&I.V.ri, &I.V.dzc, &I.V.wlo, &I.V.whi, &I.V.Rb};
+  for (const double** p : vi) *p = cv.take<double>(nv + 1);
+  I.staging = cv.take<double>((size_t)ncol * (nv + 1) * 3);
+  I.red = cv.take<double>((size_t)(kDiagBlocks + 1) * 8);
+}
+
+template <typename R>
+int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert, cudaStream_t st) {
+  const int ncol = h.ncol, S = colp_of(ncol), nv = h.nv;
+  std::vector<int> nbr(6 * (size_t)S, 0);
+  std::vector<R> wdiv(21 * (size_t)S, 0), wgrad(21 * (size_t)S, 0), wlap(7 * (size_t)S, 0),
+      rhat(3 * (size_t)S, 0), sl(S, 0), cl(S, 0), clon(S, 0);
+  std::vector<double> area(S, 0.0);
+  for (int c = 0; c < ncol; ++c) {
+    for (int j = 0; j < 6; ++j) {
+      int q = h.nbr[6 * c + j];
+      nbr[(size_t)j * S + c] = q < 0 ? c : q;
+    }
+    for (int j = 0; j < 7; ++j) {
+      for (int d = 0; d < 3; ++d) {
+        wdiv[(size_t)(3 * j + d) * S + c] = (R)h.w_div[21 * c + 3 * j + d];
+        wgrad[(size_t)(3 * j + d) * S + c] = (R)h.w_grad[21 * c + 3 * j + d];
+      }
+      wlap[(size_t)j * S + c] = (R)h.w_lap[7 * c + j];
+    }
+    double x = h.P[3 * c], y = h.P[3 * c + 1], z = h.P[3 * c + 2];
+    rhat[c] = (R)x;
+    rhat[S + c] = (R)y;
+    rhat[2 * S + c] = (R)z;
+    double lat = std::asin(std::fmax(-1.0, std::fmin(1.0, z)));
+    double lon = std::atan2(y, x);
+    sl[c] = (R)std::sin(lat);
+    cl[c] = (R)std::cos(lat);
+    clon[c] = (R)std::cos(lon);
+    area[c] = h.area[c];
+  }
+  auto up = [&](const void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  cudaError_t e = cudaSuccess;
+  e = e ? e : up(I.G.nbr, nbr.data(), nbr.size() * sizeof(int));
+  e = e ? e : up(I.G.wdiv, wdiv.data(), wdiv.size() * sizeof(R));
+  e = e ? e : up(I.G.wgrad, wgrad.data(), wgrad.size() * sizeof(R));
+  e = e ? e : up(I.G.wlap, wlap.data(), wlap.size() * sizeof(R));
+  e = e ? e : up(I.G.rhat, rhat.data(), rhat.size() * sizeof(R));
+  e = e ? e : up(I.G.sinlat, sl.data(), sl.size() * sizeof(R));
+  e = e ? e : up(I.G.coslat, cl.data(), cl.size() * sizeof(R));
+  e = e ? e : up(I.G.coslon, clon.data(), clon.size() * sizeof(R));
+  e = e ? e : up(I.G.area, area.data(), area.size() * sizeof(double));
+  const double* vp[] = {I.V.rc, I.V.dz, I.V.clo, I.V.chi, I.V.zc, I.V.rhob, I.V.thb, I.V.pb, I.V.Tb,
+                        I.V.ri, I.V.dzc, I.V.wlo, I.V.whi, I.V.Rb};
+  for (int j = 0; j < 14; ++j) {
+    size_t cnt = j < 9 ? nv : nv + 1;
+    e = e ? e : up(vp[j], vert[j].data(), cnt * sizeof(double));
+  }
+  if (e) return THOR_ECUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? THOR_OK : THOR_ECUDA;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ Impl methods
+
+template <typename R>
+Impl<R>::~Impl() {
+  if (arena) cudaFree(arena);
+}
+
+template <typename R>
+int Impl<R>::get(int field, double* host, size_t n) {
+  const int nv = G.nv;
+  size_t need = field == THOR_FIELD_MOM ? (size_t)G.ncol * nv * 3
+              : field == THOR_FIELD_W  ? (size_t)G.ncol * (nv + 1)
+                                       : (size_t)G.ncol * nv;
+  if (field < 0 || field > THOR_FIELD_TEMPERATURE || n != need || !host) return THOR_EINVAL;
+  int nlev = field == THOR_FIELD_W ? nv + 1 : nv;
+  dim3 grid((G.ncol + 127) / 128, nlev);
+  k_to_canonical<R><<<grid, 128, 0, stream>>>(staging, G, V, ph, Xt, field);
+  ++launches;
+  if (cudaMemcpyAsync(host, staging, need * sizeof(double), cudaMemcpyDeviceToHost, stream)) return THOR_ECUDA;
+  return cudaStreamSynchronize(stream) == cudaSuccess ? THOR_OK : THOR_ECUDA;
+}
+
+template <typename R>
+int Impl<R>::set(int field, const double* host, size_t n) {
+  const int nv = G.nv;
+  if (!host) return THOR_EINVAL;
+  int nlev = nv, ncomp = 1, zero_ends = 0;
+  const double* ref = nullptr;
+  R *d0 = nullptr, *d1 = nullptr, *d2 = nullptr;
+  switch (field) {
+    case THOR_FIELD_RHO: ref = V.rhob; d0 = Xt.rho; break;
+    case THOR_FIELD_MOM: ncomp = 3; d0 = Xt.mx; d1 = Xt.my; d2 = Xt.mz; break;
+    case THOR_FIELD_W: nlev = nv + 1; zero_ends = 1; d0 = Xt.w; break;
+    case THOR_FIELD_RHOTHETA: ref = V.thb; d0 = Xt.th; break;
+    default: return THOR_EINVAL;
+  }
+  if (n != (size_t)G.ncol * nlev * ncomp) return THOR_EINVAL;
+  if (cudaMemcpyAsync(staging, host, n * sizeof(double), cudaMemcpyHostToDevice, stream)) return THOR_ECUDA;
+  dim3 grid((G.ncol + 127) / 128, nlev);
+  k_from_canonical<R><<<grid, 128, 0, stream>>>(staging, G.ncol, G.colp, nlev, ncomp, ref, d0, d1, d2,
+                                                 zero_ends);
+  ++launches;
+  return cudaStreamSynchronize(stream) == cudaSuccess ? THOR_OK : THOR_ECUDA;
+}
+
+template <typename R>
+int Impl<R>::diag(double* out8, long long* nonfinite) {
+  k_diag_partial<R><<<kDiagBlocks, kDiagThreads, 0, stream>>>(G, V, ph, Xt, red);
+  k_diag_final<<<1, 32, 0, stream>>>(red, kDiagBlocks);
+  launches += 2;
+  double h[8];
+  if (cudaMemcpyAsync(h, red + kDiagBlocks * 8, sizeof(h), cudaMemcpyDeviceToHost, stream)) return THOR_ECUDA;
+  if (cudaStreamSynchronize(stream)) return THOR_ECUDA;
+  for (int j = 0; j < 8; ++j) out8[j] = h[j];
+  *nonfinite = (long long)h[7];
+  return THOR_OK;
+}
+
+template Impl<double>::~Impl();
+template Impl<float>::~Impl();
+template int Impl<double>::get(int, double*, size_t);
+template int Impl<float>::get(int, double*, size_t);
+template int Impl<double>::set(int, const double*, size_t);
+template int Impl<float>::set(int, const double*, size_t);
+template int Impl<double>::diag(double*, long long*);
+template int Impl<float>::diag(double*, long long*);
+
+namespace {
+
+// Vertical grid, reference column and initial state in float64 on the host.
+struct HostSetup {
+  std::vector<double> vert[14];   // rc dz clo chi zc rhob thb pb Tb | ri dzc wlo whi Rb
+  std::vector<double> rho, th;    // canonical [ncol][nv]
+};
+
+void host_setup(const HostGrid& h, const thor_planet& pl, const thor_init& in, HostSetup& hs) {
+  const int nv = h.nv, ncol = h.ncol;
+  std::vector<double> zi(nv + 1), zc(nv);
+  const double step = h.z_top / nv;
+  for (int i = 0; i < nv; ++i) zi[i] = i * step;
+  zi[nv] = h.z_top;
+  for (int k = 0; k < nv; ++k) zc[k] = 0.5 * (zi[k] + zi[k + 1]);
+  auto& rc = hs.vert[0]; auto& dz = hs.vert[1]; auto& clo = hs.vert[2]; auto& chi = hs.vert[3];
+  auto& zcv = hs.vert[4]; auto& rhob = hs.vert[5]; auto& thb = hs.vert[6]; auto& pb = hs.vert[7];
+  auto& Tb = hs.vert[8]; auto& ri = hs.vert[9]; auto& dzc = hs.vert[10]; auto& wlo = hs.vert[11];
+  auto& whi = hs.vert[12]; auto& Rb = hs.vert[13];
+  for (int j = 0; j < 9; ++j) hs.vert[j].assign(nv, 0.0);
+  for (int j = 9; j < 14; ++j) hs.vert[j].assign(nv + 1, 0.0);
+  for (int k = 0; k < nv; ++k) {
+    rc[k] = h.radius + zc[k];
+    dz[k] = zi[k + 1] - zi[k];
+    clo[k] = (zc[k] - zi[k + 1]) / (zi[k] - zi[k + 1]);
+    chi[k] = (zc[k] - zi[k]) / (zi[k + 1] - zi[k]);
+    zcv[k] = zc[k];
+  }
+  for (int i = 0; i <= nv; ++i) ri[i] = h.radius + zi[i];
+  for (int i = 1; i < nv; ++i) {
+    dzc[i] = zc[i] - zc[i - 1];
+    wlo[i] = (zi[i] - zc[i]) / (zc[i - 1] - zc[i]);
+    whi[i] = (zi[i] - zc[i - 1]) / (zc[i] - zc[i - 1]);
+  }
+  const double g = pl.gravity, Rd = pl.Rd, T0 = in.T0;
+  const double gamma = pl.cp / (pl.cp - Rd);
+  // discretely balanced isothermal reference column:
+  // (p_i - p_i-1)/dzc + g (wlo rho_i-1 + whi rho_i) = 0 with rho = p/(Rd T0)
+  pb[0] = in.p_surf * std::exp(-g * zc[0] / (Rd * T0));
+  for (int i = 1; i < nv; ++i)
+    pb[i] = pb[i - 1] * (1.0 - g * dzc[i] * wlo[i] / (Rd * T0)) / (1.0 + g * dzc[i] * whi[i] / (Rd * T0));
+  for (int k = 0; k < nv; ++k) {
+    rhob[k] = pb[k] / (Rd * T0);
+    thb[k] = pl.p_ref / Rd * std::pow(pb[k] / pl.p_ref, 1.0 / gamma);
+    Tb[k] = pb[k] / (rhob[k] * Rd);
+  }
+  for (int i = 1; i < nv; ++i)
+    Rb[i] = -(pb[i] - pb[i - 1]) / dzc[i] - g * (wlo[i] * rhob[i - 1] + whi[i] * rhob[i]);
+  hs.rho.assign((size_t)ncol * nv, 0.0);
+  hs.th.assign((size_t)ncol * nv, 0.0);
+  for (int c = 0; c < ncol; ++c)
+    for (int k = 0; k < nv; ++k) {
+      double T = T0;
+      if (in.noise_amp > 0.0) {
+        uint64_t z = splitmix64(in.seed ^ ((uint64_t)c * (uint64_t)nv + (uint64_t)k));
+        double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+        T = T0 + in.noise_amp * (2.0 * u - 1.0);
+      }
+      hs.rho[(size_t)c * nv + k] = pb[k] / (Rd * T);
+      hs.th[(size_t)c * nv + k] = thb[k];
+    }
+}
+
+template <typename R>
+int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaStream_t st,
+              std::unique_ptr<ImplBase>& out) {
+  const HostGrid& h = grid->h;
+  auto I = std::make_unique<Impl<R>>();
+  I->stream = st;
+  I->G.ncol = h.ncol;
+  I->G.colp = colp_of(h.ncol);
+  I->G.nv = h.nv;
+  I->ph.Rd = pl.Rd;
+  I->ph.cp = pl.cp;
+  I->ph.cv = pl.cp - pl.Rd;
+  I->ph.gamma = pl.cp / (pl.cp - pl.Rd);
+  I->ph.kappa = pl.Rd / pl.cp;
+  I->ph.g = pl.gravity;
+  I->ph.omega = pl.omega;
+  I->ph.p_ref = pl.p_ref;
+  I->hyper = in.hyperdiffusion ? 1 : 0;
+  I->divdamp = in.divergence_damping ? 1 : 0;
+  I->forcing = in.forcing;
+  I->hj_dT = in.hj_dT;
+  I->diff_D = pl.diff_D;
+  double dbar = std::sqrt(2.0 * M_PI / 5.0) * pl.radius / std::pow(2.0, h.glevel);
+  I->dbar4 = dbar * dbar * dbar * dbar;
+  Carver dry{nullptr};
+  carve(dry, *I, h.ncol, h.nv);
+  void* arena = nullptr;
+  if (cudaMalloc(&arena, dry.off) != cudaSuccess) return THOR_ENOMEM;
+  if (cudaMemsetAsync(arena, 0, dry.off, st) != cudaSuccess) {
+    cudaFree(arena);
+    return THOR_ECUDA;
+  }
+  I->arena = arena;
+  Carver real{static_cast<char*>(arena)};
+  carve(real, *I, h.ncol, h.nv);
+  HostSetup hs;
+  host_setup(h, pl, in, hs);
+  int rc = upload_tables(*I, h, hs.vert, st);
+  if (rc) return rc;
+  rc = I->set(THOR_FIELD_RHO, hs.rho.data(), hs.rho.size());
+  if (rc) return rc;
+  rc = I->set(THOR_FIELD_RHOTHETA, hs.th.data(), hs.th.size());
+  if (rc) return rc;
+  out = std::move(I);
+  return THOR_OK;
+}
+
+}  // namespace
+}  // namespace thor
+
+// ====================================================================== ABI
+
+extern "C" {
+
+const char* thor_strerror(int s) {
+  switch (s) {
+    case THOR_OK: return "ok";
+    case THOR_EINVAL: return "invalid argument";
+    case THOR_ENOMEM: return "out of memory";
+    case THOR_ECUDA: return "CUDA runtime error";
+    case THOR_ENONFINITE: return "non-finite state";
+    case THOR_ETIMEOUT: return "device wait timed out";
+    case THOR_ENOTCONV: return "not converged";
+    default: return "unknown status";
+  }
+}
+
+int thor_grid_create(int glevel, int nv, double radius, double z_top, const thor_spring* spring,
+                     thor_grid** out) {
+  if (!out || glevel < 0 || glevel > 10 || nv < 2 || nv > 256 || !(radius > 0) || !(z_top > 0))
+    return THOR_EINVAL;
+  thor::SpringParams sp;
+  if (spring) {
+    if (!(spring->dt > 0) || spring->max_iter < 0) return THOR_EINVAL;
+    sp.beta = spring->beta;
+    sp.alpha = spring->alpha;
+    sp.k = spring->k;
+    sp.dt = spring->dt;
+    sp.tol = spring->tol;
+    sp.max_iter = spring->max_iter;
+  }
+  thor_grid* g = new (std::nothrow) thor_grid;
+  if (!g) return THOR_ENOMEM;
+  int rc = thor::build_grid(glevel, nv, radius, z_top, sp, true, g->h);
+  if (rc) {
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return THOR_OK;
+}
+
+int thor_grid_info(const thor_grid* g, int* ncol, int* nv, int* npent, int* iters, int* conv) {
+  if (!g) return THOR_EINVAL;
+  if (ncol) *ncol = g->h.ncol;
+  if (nv) *nv = g->h.nv;
+  if (npent) {
+    int c = 0;
+    for (int x : g->h.nn) c += x == 5;
+    *npent = c;
+  }
+  if (iters) *iters = g->h.spring_iters;
+  if (conv) *conv = g->h.spring_converged;
+  return THOR_OK;
+}
+
+int thor_grid_points(const thor_grid* g, double* xyz, size_t n) {
+  if (!g || !xyz || n != (size_t)3 * g->h.ncol) return THOR_EINVAL;
+  std::memcpy(xyz, g->h.P.data(), n * sizeof(double));
+  return THOR_OK;
+}
+
+int thor_grid_neighbours(const thor_grid* g, int* nbr, size_t n) {
+  if (!g || !nbr || n != (size_t)6 * g->h.ncol) return THOR_EINVAL;
+  std::memcpy(nbr, g->h.nbr.data(), n * sizeof(int));
+  return THOR_OK;
+}
+
+int thor_grid_areas(const thor_grid* g, double* area, size_t n) {
+  if (!g || !area || n != (size_t)g->h.ncol) return THOR_EINVAL;
+  std::memcpy(area, g->h.area.data(), n * sizeof(double));
+  return THOR_OK;
+}
+
+void thor_grid_destroy(thor_grid* g) { delete g; }
+
+int thor_state_init(thor_grid* grid, const thor_planet* pl, const thor_init* in, void* stream,
+                    thor_state** out) {
+  if (!grid || !pl || !in || !out) return THOR_EINVAL;
+  if (!(pl->radius > 0) || std::fabs(pl->radius - grid->h.radius) > 1e-9 * grid->h.radius ||
+      !(pl->Rd > 0) || !(pl->cp > pl->Rd) || !(pl->gravity > 0) || !(pl->p_ref > 0) || !(pl->diff_D >= 0) ||
+      !(in->T0 > 0) || !(in->p_surf > 0) || !(in->noise_amp >= 0) || in->forcing < 0 || in->forcing > 2 ||
+      (in->precision != THOR_FP64 && in->precision != THOR_MIXED) || grid->h.nv > thor::kMaxNv)
+    return THOR_EINVAL;
+  thor_state* s = new (std::nothrow) thor_state;
+  if (!s) return THOR_ENOMEM;
+  s->grid = grid;
+  s->precision = in->precision;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = in->precision == THOR_FP64 ? thor::make_impl<double>(grid, *pl, *in, st, s->impl)
+                                      : thor::make_impl<float>(grid, *pl, *in, st, s->impl);
+  if (rc) {
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return THOR_OK;
+}
+
+int thor_step(thor_state* s, int n_large, int n_small, double dt) {
+  if (!s || n_large < 0 || n_small < 2 || (n_small % 2) || !(dt > 0)) return THOR_EINVAL;
+  return s->impl->step(n_large, n_small, dt);
+}
+
+int thor_diag(thor_state* s, thor_diag_t* out) {
+  if (!s || !out) return THOR_EINVAL;
+  double v[8];
+  long long nf = 0;
+  int rc = s->impl->diag(v, &nf);
+  if (rc) return rc;
+  out->mass = v[0];
+  out->energy = v[1];
+  out->aam = v[2];
+  out->mean_T = v[3] / v[4];
+  out->max_vh = v[5];
+  out->max_w = v[6];
+  out->nonfinite = nf;
+  return THOR_OK;
+}
+
+int thor_state_get(thor_state* s, int field, double* host, size_t n) {
+  if (!s) return THOR_EINVAL;
+  return s->impl->get(field, host, n);
+}
+
+int thor_state_set(thor_state* s, int field, const double* host, size_t n) {
+  if (!s) return THOR_EINVAL;
+  return s->impl->set(field, host, n);
+}
+
+int thor_launch_count(const thor_state* s, long long* count) {
+  if (!s || !count) return THOR_EINVAL;
+  *count = s->impl->launches;
+  return THOR_OK;
+}
+
+int thor_profile(thor_state* s, int enable) {
+  if (!s) return THOR_EINVAL;
+  s->impl->prof_used = 0;
+  s->impl->prof_on = enable != 0;
+  return THOR_OK;
+}
+
+int thor_profile_read(thor_state* s, int kernel, double* total_ms, long long* launches) {
+  if (!s || !total_ms || !launches || kernel < 0 || kernel >= THOR_K_COUNT) return THOR_EINVAL;
+  return s->impl->prof_read(kernel, total_ms, launches) ? THOR_ECUDA : THOR_OK;
+}
+
+void thor_state_destroy(thor_state* s) { delete s; }
+
+}  // extern "C"

@@ -1,0 +1,192 @@
+// Device kernels of the THOR hot path (Mendonca et al. 2016, Sec. 3-5).
+//
+// Data layout in HBM: every field is a set of planes [level][colp] (colp =
+// column count padded to a multiple of 128), so a warp reads 32 consecutive
+// columns of one level in one coalesced transaction; interface fields have
+// nv+1 planes; Cartesian vectors are three separate scalar fields. Columns
+// follow the rhombus numbering of the grid, so the six neighbours of an
+// interior column sit at offsets +-1, +-n, +-(n+1) in the same plane.
+//
+// Thermodynamic fields are stored as deviations from a horizontally uniform
+// float64 reference column (rho_bar, Th_bar, p_bar = EOS(Th_bar), with the
+// reference hydrostatic residual R_bar of the discrete Eq. momr2 kept in
+// float64). This is an exact rewrite: with R = double the kernels compute the
+// same numbers as the plain equations up to rounding; with R = float the
+// large hydrostatic terms never meet in float32.
+//
+// Operators: per-column float64-derived weights over (self, 6 neighbours),
+// divided by the layer radius (horizontal divergence, gradient) or its square
+// (Laplacian), Sec. 3 deep atmosphere.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace thor {
+
+constexpr int kBlock = 128;        // columns per block
+constexpr int kMaxNv = 128;        // largest nv the column kernel supports
+
+// Vertical grid and reference column (float64, device global memory)
+struct Vert {
+  const double* rc;     // [nv]   r at centres
+  const double* ri;     // [nv+1] r at interfaces
+  const double* dz;     // [nv]   layer thickness
+  const double* dzc;    // [nv+1] centre spacing across interface i (1..nv-1)
+  const double* wlo;    // [nv+1] Lagrange weight of centre i-1 at interface i
+  const double* whi;    // [nv+1] Lagrange weight of centre i at interface i
+  const double* clo;    // [nv]   weight of interface k at centre k
+  const double* chi;    // [nv]   weight of interface k+1 at centre k
+  const double* zc;     // [nv]
+  const double* rhob;   // [nv] reference column
+  const double* thb;
+  const double* pb;
+  const double* Tb;
+  const double* Rb;     // [nv+1] reference residual -dp_bar/dr - g rho_bar_iface
+};
+
+template <typename R>
+struct Geo {
+  int ncol, colp, nv;
+  const int* nbr;       // [6][colp]; slot 5 of a pentagon repeats the column
+  const R* wdiv;        // [7][3][colp]
+  const R* wgrad;       // [7][3][colp]
+  const R* wlap;        // [7][colp]
+  const R* rhat;        // [3][colp]
+  const R* sinlat;      // [colp]
+  const R* coslat;
+  const R* coslon;
+  const double* area;   // [colp]
+};
+
+struct Phys {
+  double Rd, cp, cv, gamma, kappa, g, omega, p_ref;
+};
+
+// state in deviation form
+template <typename R>
+struct Xf {
+  R *rho, *mx, *my, *mz, *w, *th;
+};
+
+// ------------------------------------------------------------ small helpers
+
+template <typename R> __device__ __forceinline__ R rlog1p(R x);
+template <> __device__ __forceinline__ double rlog1p<double>(double x) { return log1p(x); }
+template <> __device__ __forceinline__ float rlog1p<float>(float x) { return log1pf(x); }
+template <typename R> __device__ __forceinline__ R rexpm1(R x);
+template <> __device__ __forceinline__ double rexpm1<double>(double x) { return expm1(x); }
+template <> __device__ __forceinline__ float rexpm1<float>(float x) { return expm1f(x); }
+template <typename R> __device__ __forceinline__ R rlog(R x);
+template <> __device__ __forceinline__ double rlog<double>(double x) { return log(x); }
+template <> __device__ __forceinline__ float rlog<float>(float x) { return logf(x); }
+template <typename R> __device__ __forceinline__ R rexp(R x);
+template <> __device__ __forceinline__ double rexp<double>(double x) { return exp(x); }
+template <> __device__ __forceinline__ float rexp<float>(float x) { return expf(x); }
+template <typename R> __device__ __forceinline__ R rpow(R x, R y);
+template <> __device__ __forceinline__ double rpow<double>(double x, double y) { return pow(x, y); }
+template <> __device__ __forceinline__ float rpow<float>(float x, float y) { return powf(x, y); }
+template <typename R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return sqrtf(x); }
+
+// Eq. pressure in deviation form: EOS(Th_bar (1 + x)) - EOS(Th_bar) with
+// x = th'/Th_bar, i.e. p_bar ((1 + x)^gamma - 1)
+template <typename R>
+__device__ __forceinline__ R eos_dev(R pbar, R thbar, R thp, R gamma) {
+  return pbar * rexpm1<R>(gamma * rlog1p<R>(thp / thbar));
+}
+
+struct Nbr7 {
+  int n[7];
+};
+
+template <typename R>
+__device__ __forceinline__ Nbr7 load_nbr(const Geo<R>& G, int c) {
+  Nbr7 s;
+  s.n[0] = c;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) s.n[j + 1] = G.nbr[j * G.colp + c];
+  return s;
+}
+
+template <typename R>
+struct W7 {
+  R v[7];
+};
+template <typename R>
+struct W7x3 {
+  R x[7], y[7], z[7];
+};
+
+template <typename R>
+__device__ __forceinline__ W7<R> load_w7(const R* w, int colp, int c) {
+  W7<R> o;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) o.v[j] = w[j * colp + c];
+  return o;
+}
+template <typename R>
+__device__ __forceinline__ W7x3<R> load_w7x3(const R* w, int colp, int c) {
+  W7x3<R> o;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    o.x[j] = w[(3 * j) * colp + c];
+    o.y[j] = w[(3 * j + 1) * colp + c];
+    o.z[j] = w[(3 * j + 2) * colp + c];
+  }
+  return o;
+}
+
+// sum_j w_j f(n_j) on one plane
+template <typename R>
+__device__ __forceinline__ R apply7(const W7<R>& w, const Nbr7& nb, const R* plane) {
+  R s = 0;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) s += w.v[j] * plane[nb.n[j]];
+  return s;
+}
+// sum_j w_j . F(n_j) with F given by three planes
+template <typename R>
+__device__ __forceinline__ R div7(const W7x3<R>& w, const Nbr7& nb, const R* fx, const R* fy, const R* fz) {
+  R s = 0;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    int q = nb.n[j];
+    s += w.x[j] * fx[q] + w.y[j] * fy[q] + w.z[j] * fz[q];
+  }
+  return s;
+}
+// sum_j w_j . (a(n_j) F(n_j))
+template <typename R>
+__device__ __forceinline__ R div7_scaled(const W7x3<R>& w, const Nbr7& nb, const R* a, const R* fx,
+                                         const R* fy, const R* fz) {
+  R s = 0;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    int q = nb.n[j];
+    R aq = a[q];
+    s += aq * (w.x[j] * fx[q] + w.y[j] * fy[q] + w.z[j] * fz[q]);
+  }
+  return s;
+}
+template <typename R>
+__device__ __forceinline__ void grad7(const W7x3<R>& w, const Nbr7& nb, const R* s, R& gx, R& gy, R& gz) {
+  gx = gy = gz = 0;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    R v = s[nb.n[j]];
+    gx += w.x[j] * v;
+    gy += w.y[j] * v;
+    gz += w.z[j] * v;
+  }
+}
+template <typename R>
+__device__ __forceinline__ void project(R rx, R ry, R rz, R& x, R& y, R& z) {
+  R d = x * rx + y * ry + z * rz;
+  x -= d * rx;
+  y -= d * ry;
+  z -= d * rz;
+}
+
+}  // namespace thor

@@ -1,0 +1,82 @@
+"""Test harness: runs one workload on the CUDA library (through the C ABI)
+and on the oracle, with a column permutation between their numberings found
+by matching grid coordinates. Test infrastructure only."""
+
+import numpy as np
+from scipy.spatial import cKDTree
+
+import paper_1607_05535_gb300 as thor
+from conftest import oracle_grid
+from oracle import dycore as dc
+from oracle import operators as op
+import workloads as wls
+
+FORCING = {"none": thor.THOR_FORCING_NONE, "held_suarez": thor.THOR_FORCING_HELD_SUAREZ,
+           "hot_jupiter": thor.THOR_FORCING_HOT_JUPITER}
+
+
+def planet_struct(P):
+    return thor.thor_planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+
+
+def init_struct(wl, precision=thor.THOR_FP64, hyper=1, divdamp=1):
+    return thor.thor_init(wl.T0, wl.p_surf, wl.noise_amp, wl.seed, FORCING[wl.forcing], wl.hj_dT,
+                          precision, hyper, divdamp)
+
+
+class Pair:
+    """A workload on both sides. ``perm[c]`` is the oracle index of library
+    column c."""
+
+    def __init__(self, wl, precision=thor.THOR_FP64, hyper=True, divdamp=True, stream=None):
+        self.wl = wl
+        sp = thor.thor_spring(1.15, 1.0, 1.0, 0.01, wl.spring_tol, wl.spring_max_iter)
+        self.grid = thor.thor_grid_create(wl.glevel, wl.nv, wl.planet.radius, wl.z_top, sp)
+        self.state = thor.thor_state_init(self.grid, planet_struct(wl.planet),
+                                          init_struct(wl, precision, int(hyper), int(divdamp)), stream)
+        self.ncol, self.nv = wl.ncol, wl.nv
+        P = wl.planet
+        G = oracle_grid(wl.glevel, max_iter=wl.spring_max_iter, tol=wl.spring_tol)
+        pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+        self.model = dc.Model(G, op.VerticalGrid(wl.nv, wl.z_top, P.radius), pl, forcing=wl.forcing,
+                              hj_dT=wl.hj_dT, hyperdiffusion=hyper, divergence_damping=divdamp)
+        d, self.perm = cKDTree(G.points).query(thor.thor_grid_points(self.grid))
+        assert d.max() < 1e-11 and len(np.unique(self.perm)) == self.ncol
+
+    def close(self):
+        thor.thor_state_destroy(self.state)
+        thor.thor_grid_destroy(self.grid)
+
+    def oracle_initial(self):
+        u = None
+        if self.wl.noise_amp > 0:
+            u = np.empty((self.ncol, self.nv))
+            u[self.perm] = wls.temperature_noise(self.wl)
+        return dc.initial_state(self.model, self.wl.T0, self.wl.p_surf, self.wl.noise_amp, u)
+
+    def get(self):
+        """Library state as an oracle State in oracle column order."""
+        g = lambda f: thor.thor_state_get(self.state, f, self.ncol, self.nv)
+        out = dc.State(np.empty((self.ncol, self.nv)), np.empty((self.ncol, self.nv, 3)),
+                       np.empty((self.ncol, self.nv + 1)), np.empty((self.ncol, self.nv)))
+        out.rho[self.perm] = g(thor.THOR_FIELD_RHO)
+        out.M[self.perm] = g(thor.THOR_FIELD_MOM)
+        out.W[self.perm] = g(thor.THOR_FIELD_W)
+        out.Th[self.perm] = g(thor.THOR_FIELD_RHOTHETA)
+        return out
+
+    def set(self, X):
+        thor.thor_state_set(self.state, thor.THOR_FIELD_RHO, X.rho[self.perm])
+        thor.thor_state_set(self.state, thor.THOR_FIELD_MOM, X.M[self.perm])
+        thor.thor_state_set(self.state, thor.THOR_FIELD_W, X.W[self.perm])
+        thor.thor_state_set(self.state, thor.THOR_FIELD_RHOTHETA, X.Th[self.perm])
+
+
+def rel_l2(a, b, floor=0.0):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), floor))
+
+
+def field_errors(A, B):
+    """Relative L2 per field of A against B (oracle) and max-abs on W."""
+    return dict(rho=rel_l2(A.rho, B.rho), M=rel_l2(A.M, B.M, 1e-300), W=rel_l2(A.W, B.W, 1e-300),
+                Th=rel_l2(A.Th, B.Th), W_maxabs=float(np.max(np.abs(A.W - B.W))))

@@ -1,0 +1,78 @@
+"""libthor loads, exports every entry point of include/thor.h, rejects bad
+arguments, and its host grid builder agrees with the oracle. No GPU compute."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+from conftest import ROOT, oracle_grid
+
+thor = pytest.importorskip("paper_1607_05535_gb300")
+
+
+def test_exports_match_header():
+    hdr = open(os.path.join(ROOT, "include", "thor.h")).read()
+    declared = set(re.findall(r"\b(thor_[a-z_]+)\s*\(", hdr))
+    lib = ctypes.CDLL(thor.LIBRARY_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(thor.EXPORTED)
+
+
+def test_invalid_arguments():
+    with pytest.raises(thor.ThorError) as e:
+        thor.thor_grid_create(11, 4, 6.4e6, 3e4)
+    assert e.value.status == thor.THOR_EINVAL
+    for args in ((3, 1, 6.4e6, 3e4), (3, 4, -1.0, 3e4), (3, 4, 6.4e6, 0.0), (-1, 4, 6.4e6, 3e4)):
+        with pytest.raises(thor.ThorError):
+            thor.thor_grid_create(*args)
+    assert thor.thor_strerror(thor.THOR_ETIMEOUT) == "device wait timed out"
+
+
+def _match(P, O):
+    d, idx = cKDTree(O.points).query(P)
+    assert len(np.unique(idx)) == len(idx)
+    return d, idx
+
+
+@pytest.mark.parametrize("g, max_iter, tol", [(0, 10, 0.0), (2, 10, 0.0), (4, 10, 0.0), (3, 100000, 1e-5)])
+def test_grid_parity_with_oracle(g, max_iter, tol):
+    """Independent builders (rhombus lattice vs. triangle list) give the same
+    points, neighbour sets, areas and spring iteration count."""
+    sp = thor.thor_spring(1.15, 1.0, 1.0, 0.01, tol, max_iter)
+    G = thor.thor_grid_create(g, 4, 6.371e6, 3.0e4, sp)
+    try:
+        info = thor.thor_grid_info(G)
+        P = thor.thor_grid_points(G)
+        A = thor.thor_grid_areas(G)
+        nb = thor.thor_grid_neighbours(G)
+    finally:
+        thor.thor_grid_destroy(G)
+    O = oracle_grid(g, max_iter=max_iter, tol=tol)
+    assert info["ncol"] == O.ncol == 10 * 4 ** g + 2 and info["npent"] == 12
+    assert info["spring_iters"] == O.spring_iters
+    assert info["spring_converged"] == O.spring_converged
+    d, idx = _match(P, O)
+    assert d.max() < 1e-12
+    assert np.max(np.abs(A - O.area[idx])) < 1e-13
+    for c in range(len(P)):
+        mine = {idx[x] for x in nb[c] if x >= 0}
+        assert mine == set(O.nbr[idx[c], :O.nn[idx[c]]].tolist())
+
+
+def test_canonical_numbering():
+    """Columns are numbered rhombus by rhombus, then the two poles."""
+    G = thor.thor_grid_create(2, 4, 1.0, 0.1, thor.thor_spring(1.15, 1, 1, 0.01, 0.0, 0))
+    P = thor.thor_grid_points(G)
+    thor.thor_grid_destroy(G)
+    assert np.allclose(P[-2], [0, 0, 1]) and np.allclose(P[-1], [0, 0, -1])
+    n = 4
+    # north rhombus 0 owns U_0 (lat atan(1/2), lon 0) at its lattice origin
+    lat = np.arctan(0.5)
+    assert np.allclose(P[0], [np.cos(lat), 0, np.sin(lat)])
+    # south rhombus 0 owns L_0 (lat -atan(1/2), lon 36 deg)
+    assert np.allclose(P[5 * n * n], [np.cos(lat) * np.cos(np.pi / 5), np.cos(lat) * np.sin(np.pi / 5), -np.sin(lat)])

@@ -1,0 +1,123 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle, float64 mode:
+within 1e-10 relative per field (L2), on the same seeded inputs."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1607_05535_gb300 as thor
+from harness import Pair, field_errors
+from oracle import diagnostics as dg
+from oracle import dycore as dc
+import workloads as wls
+
+TOL = 1e-10
+
+SMALL = wls.HS_G4.with_(name="hs_g3_L12", glevel=3, nv=12, n_large=2)
+
+
+def _assert_close(A, B, tol=TOL):
+    e = field_errors(A, B)
+    assert e["rho"] < tol and e["Th"] < tol, e
+    assert e["M"] < tol and e["W"] < tol, e
+    return e
+
+
+def test_initial_state_matches():
+    p = Pair(SMALL)
+    try:
+        _assert_close(p.get(), p.oracle_initial(), 1e-14)
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("forcing", ["none", "held_suarez", "hot_jupiter"])
+def test_one_large_step(forcing):
+    wl = SMALL.with_(forcing=forcing)
+    if forcing == "hot_jupiter":
+        wl = wls.HJ_G6.with_(glevel=3, nv=12, n_large=1)
+    p = Pair(wl)
+    try:
+        X = p.oracle_initial()
+        ref = dc.large_step(p.model, X, wl.dt, wl.n_small)
+        thor.thor_step(p.state, 1, wl.n_small, wl.dt)
+        _assert_close(p.get(), ref)
+    finally:
+        p.close()
+
+
+def test_injected_state_two_steps_no_diffusion():
+    """A state with motion injected through thor_state_set, diffusion and
+    divergence damping off, two large steps."""
+    wl = SMALL.with_(forcing="none")
+    p = Pair(wl, hyper=False, divdamp=False)
+    try:
+        X = p.oracle_initial()
+        rng = np.random.default_rng(11)
+        from oracle import operators as op
+        X.M[:] = op.project_h(p.model.rhat, rng.standard_normal(X.M.shape)) * X.rho[..., None]
+        X.W[:, 1:-1] = 0.05 * rng.standard_normal((X.W.shape[0], wl.nv - 1))
+        p.set(X)
+        _assert_close(p.get(), X, 1e-15)
+        ref = dc.run(p.model, X, 2, wl.n_small, wl.dt)
+        thor.thor_step(p.state, 2, wl.n_small, wl.dt)
+        _assert_close(p.get(), ref)
+    finally:
+        p.close()
+
+
+def test_held_suarez_g4_ten_steps():
+    """The glevel-4 x 20-level Held-Suarez workload, 10 large steps."""
+    wl = wls.HS_G4
+    p = Pair(wl)
+    try:
+        X = p.oracle_initial()
+        ref = dc.run(p.model, X, wl.n_large, wl.n_small, wl.dt)
+        thor.thor_step(p.state, wl.n_large, wl.n_small, wl.dt)
+        _assert_close(p.get(), ref)
+        d = thor.thor_diag(p.state)
+        o = dg.diagnostics(p.model, ref)
+        for k in ("mass", "energy", "aam"):
+            assert abs(d[k] - o[k]) <= 1e-10 * abs(o[k]), (k, d[k], o[k])
+        assert d["nonfinite"] == 0
+    finally:
+        p.close()
+
+
+def test_mass_conservation_and_rest():
+    wl = wls.HS_G4.with_(glevel=3)
+    p = Pair(wl)
+    try:
+        m0 = thor.thor_diag(p.state)["mass"]
+        thor.thor_step(p.state, 10, wl.n_small, wl.dt)
+        assert abs(thor.thor_diag(p.state)["mass"] - m0) / m0 < 1e-12
+    finally:
+        p.close()
+    rest = wls.HS_G4.with_(glevel=3, forcing="none", noise_amp=0.0)
+    p = Pair(rest)
+    try:
+        thor.thor_step(p.state, 10, rest.n_small, rest.dt)
+        d = thor.thor_diag(p.state)
+        assert d["max_vh"] < 1e-8 and d["max_w"] < 1e-8
+    finally:
+        p.close()
+
+
+def test_odd_substeps_rejected_without_state_change():
+    p = Pair(SMALL)
+    try:
+        before = p.get()
+        with pytest.raises(thor.ThorError) as e:
+            thor.thor_step(p.state, 1, 7, SMALL.dt)
+        assert e.value.status == thor.THOR_EINVAL
+        with pytest.raises(thor.ThorError):
+            thor.thor_step(p.state, 1, 6, -1.0)
+        after = p.get()
+        assert np.array_equal(before.rho, after.rho) and np.array_equal(before.Th, after.Th)
+    finally:
+        p.close()
