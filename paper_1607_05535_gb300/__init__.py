@@ -4,7 +4,7 @@ Every function here has the name of the C entry point it calls and passes
 plain pointers and sizes through ctypes; all arithmetic of the method runs in
 libthor's CUDA kernels (and its float64 host grid builder). Importing this
 module fails loudly if the library has not been built
-(``python -m paper_1607_05535_gb300.build`` or ``__graft_entry__.build()``).
+(``python paper_1607_05535_gb300/build.py`` or ``__graft_entry__.build()``).
 """
 
 import ctypes
@@ -71,7 +71,7 @@ class ThorError(RuntimeError):
 def _load():
     if not os.path.exists(LIBRARY_PATH):
         raise ImportError(f"libthor is not built ({LIBRARY_PATH} missing); run "
-                          "`python -m paper_1607_05535_gb300.build`")
+                          "`python paper_1607_05535_gb300/build.py`")
     lib = ctypes.CDLL(LIBRARY_PATH)
     P, I, D, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
     IP = ctypes.POINTER(ctypes.c_int)
