@@ -22,9 +22,12 @@ struct thor_state {
 };
 
 namespace thor {
+template <typename R>
+int col_kernel_setup(int nv);   // thor_step.cu: opt the column kernel into its shared memory
 namespace {
 
 inline int colp_of(int ncol) { return (ncol + kBlock - 1) / kBlock * kBlock; }
+constexpr int kNumVertCentre = 10, kNumVert = 17;   // float64 vertical arrays (centres, total)
 
 uint64_t splitmix64(uint64_t x) {
   uint64_t z = x + 0x9E3779B97F4A7C15ULL;
@@ -194,6 +197,13 @@ struct Carver {
   }
 };
 
+// the VR arrays in a fixed order (all allocated with nv + 1 entries)
+template <typename R>
+std::vector<const R**> vr_slots(VR<R>& U) {
+  return {&U.inv_rc, &U.inv_rc2, &U.sv, &U.ri2, &U.wlo, &U.whi, &U.clo, &U.chi, &U.inv_dzc,
+          &U.rhob, &U.thb, &U.pb, &U.Tb, &U.Rb, &U.zc};
+}
+
 template <typename R>
 void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   const size_t S = (size_t)colp_of(ncol);
@@ -229,10 +239,12 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   I.G.coslat = cv.take<R>(S);
   I.G.coslon = cv.take<R>(S);
   I.G.area = cv.take<double>(S);
-  const double** vp[] = {&I.V.rc, &I.V.dz, &I.V.clo, &I.V.chi, &I.V.zc, &I.V.rhob, &I.V.thb, &I.V.pb, &I.V.Tb};
+  const double** vp[] = {&I.V.rc, &I.V.dz, &I.V.clo, &I.V.chi, &I.V.zc, &I.V.rhob, &I.V.thb, &I.V.pb,
+                         &I.V.Tb, &I.V.sv};
   for (const double** p : vp) *p = cv.take<double>(nv);
-  const double** vi[] = {&I.V.ri, &I.V.dzc, &I.V.wlo, &I.V.whi, &I.V.Rb};
+  const double** vi[] = {&I.V.ri, &I.V.dzc, &I.V.wlo, &I.V.whi, &I.V.Rb, &I.V.ri2, &I.V.inv_dzc};
   for (const double** p : vi) *p = cv.take<double>(nv + 1);
+  for (const R** p : vr_slots(I.U)) *p = cv.take<R>(nv + 1);
   I.staging = cv.take<double>((size_t)ncol * (nv + 1) * 3);
   I.red = cv.take<double>((size_t)(kDiagBlocks + 1) * 8);
 }
@@ -281,10 +293,38 @@ int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert
   e = e ? e : up(I.G.coslon, clon.data(), clon.size() * sizeof(R));
   e = e ? e : up(I.G.area, area.data(), area.size() * sizeof(double));
   const double* vp[] = {I.V.rc, I.V.dz, I.V.clo, I.V.chi, I.V.zc, I.V.rhob, I.V.thb, I.V.pb, I.V.Tb,
-                        I.V.ri, I.V.dzc, I.V.wlo, I.V.whi, I.V.Rb};
-  for (int j = 0; j < 14; ++j) {
-    size_t cnt = j < 9 ? nv : nv + 1;
+                        I.V.sv, I.V.ri, I.V.dzc, I.V.wlo, I.V.whi, I.V.Rb, I.V.ri2, I.V.inv_dzc};
+  for (int j = 0; j < kNumVert; ++j) {
+    size_t cnt = j < kNumVertCentre ? nv : nv + 1;
     e = e ? e : up(vp[j], vert[j].data(), cnt * sizeof(double));
+  }
+  // storage-type copies with the reciprocals precomputed
+  {
+    const std::vector<double>& rc = vert[0];
+    std::vector<std::vector<R>> vr(15, std::vector<R>(nv + 1, R(0)));
+    for (int k = 0; k < nv; ++k) {
+      vr[0][k] = (R)(1.0 / rc[k]);
+      vr[1][k] = (R)(1.0 / (rc[k] * rc[k]));
+      vr[2][k] = (R)vert[9][k];
+      vr[6][k] = (R)vert[2][k];
+      vr[7][k] = (R)vert[3][k];
+      vr[9][k] = (R)vert[5][k];
+      vr[10][k] = (R)vert[6][k];
+      vr[11][k] = (R)vert[7][k];
+      vr[12][k] = (R)vert[8][k];
+      vr[14][k] = (R)vert[4][k];
+    }
+    for (int i = 0; i <= nv; ++i) {
+      vr[3][i] = (R)vert[15][i];
+      vr[4][i] = (R)vert[12][i];
+      vr[5][i] = (R)vert[13][i];
+      vr[8][i] = (R)vert[16][i];
+      vr[13][i] = (R)vert[14][i];
+    }
+    std::vector<const R**> slots = vr_slots(I.U);
+    for (int j = 0; j < 15; ++j) e = e ? e : up(*slots[j], vr[j].data(), (nv + 1) * sizeof(R));
+    if (e) return THOR_ECUDA;
+    if (cudaStreamSynchronize(st)) return THOR_ECUDA;   // host vectors die here
   }
   if (e) return THOR_ECUDA;
   return cudaStreamSynchronize(st) == cudaSuccess ? THOR_OK : THOR_ECUDA;
@@ -363,7 +403,8 @@ namespace {
 
 // Vertical grid, reference column and initial state in float64 on the host.
 struct HostSetup {
-  std::vector<double> vert[14];   // rc dz clo chi zc rhob thb pb Tb | ri dzc wlo whi Rb
+  // rc dz clo chi zc rhob thb pb Tb sv | ri dzc wlo whi Rb ri2 inv_dzc
+  std::vector<double> vert[kNumVert];
   std::vector<double> rho, th;    // canonical [ncol][nv]
 };
 
@@ -376,10 +417,11 @@ void host_setup(const HostGrid& h, const thor_planet& pl, const thor_init& in, H
   for (int k = 0; k < nv; ++k) zc[k] = 0.5 * (zi[k] + zi[k + 1]);
   auto& rc = hs.vert[0]; auto& dz = hs.vert[1]; auto& clo = hs.vert[2]; auto& chi = hs.vert[3];
   auto& zcv = hs.vert[4]; auto& rhob = hs.vert[5]; auto& thb = hs.vert[6]; auto& pb = hs.vert[7];
-  auto& Tb = hs.vert[8]; auto& ri = hs.vert[9]; auto& dzc = hs.vert[10]; auto& wlo = hs.vert[11];
-  auto& whi = hs.vert[12]; auto& Rb = hs.vert[13];
-  for (int j = 0; j < 9; ++j) hs.vert[j].assign(nv, 0.0);
-  for (int j = 9; j < 14; ++j) hs.vert[j].assign(nv + 1, 0.0);
+  auto& Tb = hs.vert[8]; auto& sv = hs.vert[9]; auto& ri = hs.vert[10]; auto& dzc = hs.vert[11];
+  auto& wlo = hs.vert[12]; auto& whi = hs.vert[13]; auto& Rb = hs.vert[14]; auto& ri2 = hs.vert[15];
+  auto& inv_dzc = hs.vert[16];
+  for (int j = 0; j < kNumVertCentre; ++j) hs.vert[j].assign(nv, 0.0);
+  for (int j = kNumVertCentre; j < kNumVert; ++j) hs.vert[j].assign(nv + 1, 0.0);
   for (int k = 0; k < nv; ++k) {
     rc[k] = h.radius + zc[k];
     dz[k] = zi[k + 1] - zi[k];
@@ -387,9 +429,14 @@ void host_setup(const HostGrid& h, const thor_planet& pl, const thor_init& in, H
     chi[k] = (zc[k] - zi[k]) / (zi[k + 1] - zi[k]);
     zcv[k] = zc[k];
   }
-  for (int i = 0; i <= nv; ++i) ri[i] = h.radius + zi[i];
+  for (int k = 0; k < nv; ++k) sv[k] = 1.0 / (rc[k] * rc[k] * dz[k]);
+  for (int i = 0; i <= nv; ++i) {
+    ri[i] = h.radius + zi[i];
+    ri2[i] = ri[i] * ri[i];
+  }
   for (int i = 1; i < nv; ++i) {
     dzc[i] = zc[i] - zc[i - 1];
+    inv_dzc[i] = 1.0 / dzc[i];
     wlo[i] = (zi[i] - zc[i]) / (zc[i - 1] - zc[i]);
     whi[i] = (zi[i] - zc[i - 1]) / (zc[i] - zc[i - 1]);
   }
@@ -457,6 +504,7 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
   I->arena = arena;
   Carver real{static_cast<char*>(arena)};
   carve(real, *I, h.ncol, h.nv);
+  if (col_kernel_setup<R>(h.nv)) return THOR_ECUDA;
   HostSetup hs;
   host_setup(h, pl, in, hs);
   int rc = upload_tables(*I, h, hs.vert, st);

@@ -94,6 +94,7 @@ template <typename R>
 struct Impl : ImplBase {
   Geo<R> G;
   Vert V;
+  VR<R> U;
   Phys ph;
   Xf<R> Xt, Xst;
   Work<R> T;

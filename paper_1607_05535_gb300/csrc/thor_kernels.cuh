@@ -43,6 +43,17 @@ struct Vert {
   const double* pb;
   const double* Tb;
   const double* Rb;     // [nv+1] reference residual -dp_bar/dr - g rho_bar_iface
+  const double* sv;     // [nv]   1 / (rc^2 dz): radial divergence factor
+  const double* ri2;    // [nv+1] ri^2
+  const double* inv_dzc;// [nv+1] 1 / dzc
+};
+
+// The same vertical quantities in the storage type, with the reciprocals
+// precomputed, so no kernel divides by a level constant per cell.
+template <typename R>
+struct VR {
+  const R *inv_rc, *inv_rc2, *sv, *ri2, *wlo, *whi, *clo, *chi, *inv_dzc;
+  const R *rhob, *thb, *pb, *Tb, *Rb, *zc;
 };
 
 template <typename R>

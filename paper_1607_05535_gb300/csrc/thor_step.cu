@@ -1,38 +1,50 @@
 // Kernels of one large step (Sec. 3-5 of Mendonca et al. 2016) and their
-// launch sequence. Thread mapping for the stencil kernels: one thread per
-// column, looping over a chunk of levels, so that the per-column stencil
-// weights are loaded once and reused across the chunk; blockIdx.y selects the
-// chunk. The vertical solve runs one thread per column over all levels.
+// launch sequence.
+//
+// Stencil kernels: one thread per column, looping over a chunk of levels, so
+// the per-column stencil weights are loaded once per chunk; blockIdx.y picks
+// the chunk. A warp covers 32 consecutive columns of one level, so every
+// field access is a coalesced (or neighbour-shifted) row of one plane.
+//
+// The vertical solve (k_ss_col) runs 32 columns per block with 8 threads per
+// column: the level-parallel phases (horizontal fluxes, the tridiagonal
+// coefficients, the updates) use all 256 threads; the sequential Thomas sweep
+// over the interfaces uses one warp, one lane per column, in float64, on
+// coefficients kept in shared memory.
 #include "../../include/thor.h"
 #include "thor_impl.cuh"
 
 namespace thor {
+
+constexpr int kColTile = 32;   // columns per block of the column kernel
+constexpr int kColRows = 8;    // threads per column in that kernel
 
 // ---------------------------------------------------------------- slow terms
 
 // Pointwise derived quantities at the stage state: p', T', theta, the full
 // 3-D velocity, v_h = M/rho (centres) and v_r = W/rho (interfaces).
 template <typename R>
-__global__ void k_derived(Geo<R> G, Vert V, Phys ph, Xf<R> X, Work<R> T, int kchunk) {
+__global__ void k_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int kchunk) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
+  const R gamma = (R)ph.gamma, inv_Rd = R(1.0 / ph.Rd);
   R rx = G.rhat[c], ry = G.rhat[S + c], rz = G.rhat[2 * S + c];
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
   for (int k = k0; k < k1; ++k) {
     if (k < G.nv) {
       int i = k * S + c;
-      R rho = (R)V.rhob[k] + X.rho[i];
+      R rho = U.rhob[k] + X.rho[i];
       R thp = X.th[i];
-      R pp = eos_dev<R>((R)V.pb[k], (R)V.thb[k], thp, (R)ph.gamma);
-      R p = (R)V.pb[k] + pp;
-      R Temp = p / (rho * (R)ph.Rd);
-      R wc = (R)V.clo[k] * X.w[i] + (R)V.chi[k] * X.w[i + S];
+      R pp = eos_dev<R>(U.pb[k], U.thb[k], thp, gamma);
+      R p = U.pb[k] + pp;
       R inv = R(1) / rho;
+      R Temp = p * inv * inv_Rd;
+      R wc = U.clo[k] * X.w[i] + U.chi[k] * X.w[i + S];
       R mx = X.mx[i], my = X.my[i], mz = X.mz[i];
       T.pp[i] = pp;
-      T.Tp[i] = Temp - (R)V.Tb[k];
-      T.theta[i] = ((R)V.thb[k] + thp) * inv;
+      T.Tp[i] = Temp - U.Tb[k];
+      T.theta[i] = (U.thb[k] + thp) * inv;
       T.vx[i] = (mx + wc * rx) * inv;
       T.vy[i] = (my + wc * ry) * inv;
       T.vz[i] = (mz + wc * rz) * inv;
@@ -42,9 +54,8 @@ __global__ void k_derived(Geo<R> G, Vert V, Phys ph, Xf<R> X, Work<R> T, int kch
     }
     if (k >= 1 && k < G.nv) {
       int i = k * S + c;
-      R rlo = (R)V.rhob[k - 1] + X.rho[i - S], rhi = (R)V.rhob[k] + X.rho[i];
-      R rif = (R)V.wlo[k] * rlo + (R)V.whi[k] * rhi;
-      T.vr[i] = X.w[i] / rif;
+      R rlo = U.rhob[k - 1] + X.rho[i - S], rhi = U.rhob[k] + X.rho[i];
+      T.vr[i] = X.w[i] / (U.wlo[k] * rlo + U.whi[k] * rhi);
     } else if (k == 0 || k == G.nv) {
       T.vr[k * S + c] = 0;
     }
@@ -54,7 +65,7 @@ __global__ void k_derived(Geo<R> G, Vert V, Phys ph, Xf<R> X, Work<R> T, int kch
 // First Laplacians of the hyperdiffusion (Sec. 4), already multiplied by
 // K_d and, for the momentum and temperature terms, by rho.
 template <typename R>
-__global__ void k_lap1(Geo<R> G, Vert V, Xf<R> X, Work<R> T, R Kd, int kchunk) {
+__global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -64,8 +75,8 @@ __global__ void k_lap1(Geo<R> G, Vert V, Xf<R> X, Work<R> T, R Kd, int kchunk) {
   for (int k = k0; k < k1; ++k) {
     if (k < G.nv) {
       int o = k * S;
-      R inv_r2 = R(1.0 / (V.rc[k] * V.rc[k]));
-      R rho = (R)V.rhob[k] + X.rho[o + c];
+      R inv_r2 = U.inv_rc2[k];
+      R rho = U.rhob[k] + X.rho[o + c];
       T.qrho[o + c] = Kd * apply7(wl, nb, X.rho + o) * inv_r2;
       R rk = rho * Kd * inv_r2;
       T.qvx[o + c] = rk * apply7(wl, nb, T.vhx + o);
@@ -75,9 +86,9 @@ __global__ void k_lap1(Geo<R> G, Vert V, Xf<R> X, Work<R> T, R Kd, int kchunk) {
     }
     if (k >= 1 && k < G.nv) {
       int o = k * S;
-      R rlo = (R)V.rhob[k - 1] + X.rho[o - S + c], rhi = (R)V.rhob[k] + X.rho[o + c];
-      R rif = (R)V.wlo[k] * rlo + (R)V.whi[k] * rhi;
-      T.qvr[o + c] = rif * Kd * apply7(wl, nb, T.vr + o) * R(1.0 / (V.ri[k] * V.ri[k]));
+      R rlo = U.rhob[k - 1] + X.rho[o - S + c], rhi = U.rhob[k] + X.rho[o + c];
+      R rif = U.wlo[k] * rlo + U.whi[k] * rhi;
+      T.qvr[o + c] = rif * Kd * apply7(wl, nb, T.vr + o) / U.ri2[k];
     } else if (k == 0 || k == G.nv) {
       T.qvr[k * S + c] = 0;
     }
@@ -90,7 +101,7 @@ __global__ void k_lap1(Geo<R> G, Vert V, Xf<R> X, Work<R> T, R Kd, int kchunk) {
 // stage state (divergence damping), the radial advection+Coriolis and
 // Pi = gamma p / rho theta.
 template <typename R>
-__global__ void k_slow(Geo<R> G, Vert V, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
+__global__ void k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
                        int kchunk) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
@@ -100,17 +111,15 @@ __global__ void k_slow(Geo<R> G, Vert V, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL
   W7x3<R> wg = load_w7x3(G.wgrad, S, c);
   W7<R> wl = load_w7(G.wlap, S, c);
   R rx = G.rhat[c], ry = G.rhat[S + c], rz = G.rhat[2 * S + c];
-  const R two_om = R(2.0 * ph.omega);
+  const R two_om = R(2.0 * ph.omega), gamma = (R)ph.gamma, Rd = (R)ph.Rd;
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
-    const R inv_r = R(1.0 / V.rc[k]);
-    const R inv_r2 = R(1.0 / (V.rc[k] * V.rc[k]));
-    const R qlo = (R)(V.ri[k] * V.ri[k]), qhi = (R)(V.ri[k + 1] * V.ri[k + 1]);
-    const R sv = R(1.0 / (V.rc[k] * V.rc[k] * V.dz[k]));
-    R rho = (R)V.rhob[k] + X.rho[i];
-    R thfull = (R)V.thb[k] + X.th[i];
-    R p = (R)V.pb[k] + T.pp[i];
+    const R inv_r = U.inv_rc[k], inv_r2 = U.inv_rc2[k];
+    const R qlo = U.ri2[k], qhi = U.ri2[k + 1];
+    const R sv = U.sv[k];
+    R thfull = U.thb[k] + X.th[i];
+    R p = U.pb[k] + T.pp[i];
 
     // hyperdiffusion (Sec. 4)
     R Frho = 0, FMx = 0, FMy = 0, FMz = 0, Fth = 0;
@@ -120,8 +129,8 @@ __global__ void k_slow(Geo<R> G, Vert V, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL
       FMy = -apply7(wl, nb, T.qvy + o) * inv_r2;
       FMz = -apply7(wl, nb, T.qvz + o) * inv_r2;
       project(rx, ry, rz, FMx, FMy, FMz);
-      R Fp = -(R)ph.Rd * apply7(wl, nb, T.qT + o) * inv_r2;
-      Fth = thfull / ((R)ph.gamma * p) * Fp;
+      R Fp = -Rd * apply7(wl, nb, T.qT + o) * inv_r2;
+      Fth = thfull / (gamma * p) * Fp;
     }
 
     // advection div(rho v v_j) of the Cartesian components (Sec. 3)
@@ -132,13 +141,13 @@ __global__ void k_slow(Geo<R> G, Vert V, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL
     for (int j = 0; j < 3; ++j) {
       R ah = div7_scaled(wd, nb, vs[j] + o, X.mx + o, X.my + o, X.mz + o) * inv_r;
       R vlo = 0, vhi = 0;
-      if (k >= 1) vlo = (R)V.wlo[k] * vs[j][i - S] + (R)V.whi[k] * vs[j][i];
-      if (k + 1 < G.nv) vhi = (R)V.wlo[k + 1] * vs[j][i] + (R)V.whi[k + 1] * vs[j][i + S];
+      if (k >= 1) vlo = U.wlo[k] * vs[j][i - S] + U.whi[k] * vs[j][i];
+      if (k + 1 < G.nv) vhi = U.wlo[k + 1] * vs[j][i] + U.whi[k + 1] * vs[j][i + S];
       A[j] = ah + (qhi * whi_w * vhi - qlo * wlo_w * vlo) * sv;
     }
     // Coriolis 2 Omega z x (rho v) with the full momentum
-    R wc = (R)V.clo[k] * wlo_w + (R)V.chi[k] * whi_w;
-    R mx = X.mx[i], my = X.my[i], mz = X.mz[i];
+    R wc = U.clo[k] * wlo_w + U.chi[k] * whi_w;
+    R mx = X.mx[i], my = X.my[i];
     R fx = mx + wc * rx, fy = my + wc * ry;
     A[0] += -two_om * fy;
     A[1] += two_om * fx;
@@ -160,25 +169,26 @@ __global__ void k_slow(Geo<R> G, Vert V, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL
 
     R dht = div7_scaled(wd, nb, T.theta + o, X.mx + o, X.my + o, X.mz + o) * inv_r;
     R thlo = 0, thhi = 0;
-    if (k >= 1) thlo = (R)V.wlo[k] * T.theta[i - S] + (R)V.whi[k] * T.theta[i];
-    if (k + 1 < G.nv) thhi = (R)V.wlo[k + 1] * T.theta[i] + (R)V.whi[k + 1] * T.theta[i + S];
+    if (k >= 1) thlo = U.wlo[k] * T.theta[i - S] + U.whi[k] * T.theta[i];
+    if (k + 1 < G.nv) thhi = U.wlo[k + 1] * T.theta[i] + U.whi[k + 1] * T.theta[i + S];
     R dvt = (qhi * thhi * whi_w - qlo * thlo * wlo_w) * sv;
     SL.sth[i] = Fth - dht - dvt;
     SL.acr[i] = acr;
-    SL.pi[i] = (R)ph.gamma * p / thfull;
+    SL.pi[i] = gamma * p / thfull;
   }
 }
 
 // Slow tendency of the vertical momentum at the interior interfaces
 // (right-hand side of Eq. momr2) and theta at the interfaces.
 template <typename R>
-__global__ void k_slow_w(Geo<R> G, Vert V, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
+__global__ void k_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
                          int kchunk) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
   W7<R> wl = load_w7(G.wlap, S, c);
+  const R g = (R)ph.g;
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
   for (int k = k0; k < k1; ++k) {
     const int i = k * S + c;
@@ -187,11 +197,11 @@ __global__ void k_slow_w(Geo<R> G, Vert V, Phys ph, Xf<R> X, Work<R> T, Slow<R> 
       SL.thi[i] = 0;
       continue;
     }
-    R wlo = (R)V.wlo[k], whi = (R)V.whi[k];
+    R wlo = U.wlo[k], whi = U.whi[k];
     R FW = 0;
-    if (hyper) FW = -apply7(wl, nb, T.qvr + k * S) * R(1.0 / (V.ri[k] * V.ri[k]));
-    R sw = (R)V.Rb[k] - (T.pp[i] - T.pp[i - S]) / (R)V.dzc[k]
-         - (R)ph.g * (wlo * X.rho[i - S] + whi * X.rho[i])
+    if (hyper) FW = -apply7(wl, nb, T.qvr + k * S) / U.ri2[k];
+    R sw = U.Rb[k] - (T.pp[i] - T.pp[i - S]) * U.inv_dzc[k]
+         - g * (wlo * X.rho[i - S] + whi * X.rho[i])
          - (wlo * SL.acr[i - S] + whi * SL.acr[i]) + FW;
     SL.sw[i] = sw;
     SL.thi[i] = wlo * T.theta[i - S] + whi * T.theta[i];
@@ -201,7 +211,7 @@ __global__ void k_slow_w(Geo<R> G, Vert V, Phys ph, Xf<R> X, Work<R> T, Slow<R> 
 // Perturbations at the start of a stage: Phi* = Phi^t - Phi^(s); p* from the
 // nonlinear Eq. theta_to_p.
 template <typename R>
-__global__ void k_stage_init(Geo<R> G, Vert V, Phys ph, Xf<R> Xt, Xf<R> Xs, Work<R> T, Pert<R> P,
+__global__ void k_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> Xs, Work<R> T, Pert<R> P,
                              int kchunk) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
@@ -215,7 +225,7 @@ __global__ void k_stage_init(Geo<R> G, Vert V, Phys ph, Xf<R> Xt, Xf<R> Xs, Work
       P.my[i] = Xt.my[i] - Xs.my[i];
       P.mz[i] = Xt.mz[i] - Xs.mz[i];
       P.th[i] = Xt.th[i] - Xs.th[i];
-      R ppt = eos_dev<R>((R)V.pb[k], (R)V.thb[k], Xt.th[i], (R)ph.gamma);
+      R ppt = eos_dev<R>(U.pb[k], U.thb[k], Xt.th[i], (R)ph.gamma);
       P.p[i] = ppt - T.pp[i];
     }
     P.w[i] = Xt.w[i] - Xs.w[i];
@@ -226,7 +236,7 @@ __global__ void k_stage_init(Geo<R> G, Vert V, Phys ph, Xf<R> Xt, Xf<R> Xs, Work
 
 // 3-D divergence of the total momentum (divergence damping, Sec. 4)
 template <typename R>
-__global__ void k_ss_div(Geo<R> G, Vert V, Slow<R> SL, Pert<R> P, Work<R> T, int kchunk) {
+__global__ void k_ss_div(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, int kchunk) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -235,15 +245,14 @@ __global__ void k_ss_div(Geo<R> G, Vert V, Slow<R> SL, Pert<R> P, Work<R> T, int
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
-    R dh = div7(wd, nb, P.mx + o, P.my + o, P.mz + o) * R(1.0 / V.rc[k]);
-    R dv = ((R)(V.ri[k + 1] * V.ri[k + 1]) * P.w[i + S] - (R)(V.ri[k] * V.ri[k]) * P.w[i])
-         * R(1.0 / (V.rc[k] * V.rc[k] * V.dz[k]));
+    R dh = div7(wd, nb, P.mx + o, P.my + o, P.mz + o) * U.inv_rc[k];
+    R dv = (U.ri2[k + 1] * P.w[i + S] - U.ri2[k] * P.w[i]) * U.sv[k];
     T.dd[i] = SL.dsc[i] + dh + dv;
   }
 }
 
 template <typename R>
-__global__ void k_ss_grad(Geo<R> G, Vert V, Work<R> T, int kchunk) {
+__global__ void k_ss_grad(Geo<R> G, VR<R> U, Work<R> T, int kchunk) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -254,7 +263,7 @@ __global__ void k_ss_grad(Geo<R> G, Vert V, Work<R> T, int kchunk) {
     const int o = k * S, i = o + c;
     R gx, gy, gz;
     grad7(wg, nb, T.dd + o, gx, gy, gz);
-    R inv_r = R(1.0 / V.rc[k]);
+    R inv_r = U.inv_rc[k];
     T.gx[i] = gx * inv_r;
     T.gy[i] = gy * inv_r;
     T.gz[i] = gz * inv_r;
@@ -263,7 +272,7 @@ __global__ void k_ss_grad(Geo<R> G, Vert V, Work<R> T, int kchunk) {
 
 // Eq. mom2 with the divergence damping: M* <- proj(M* + dtau(-grad p* + DD + S_M))
 template <typename R>
-__global__ void k_ss_mom(Geo<R> G, Vert V, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, R Kd,
+__global__ void k_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, R Kd,
                          int divdamp, int kchunk) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
@@ -275,10 +284,10 @@ __global__ void k_ss_mom(Geo<R> G, Vert V, Slow<R> SL, Pert<R> P, Work<R> T, R d
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
-    R inv_r = R(1.0 / V.rc[k]);
+    R inv_r = U.inv_rc[k];
     R ddx = 0, ddy = 0, ddz = 0;
     if (divdamp) {
-      R s = -Kd * R(1.0 / (V.rc[k] * V.rc[k]));
+      R s = -Kd * U.inv_rc2[k];
       ddx = s * apply7(wl, nb, T.gx + o);
       ddy = s * apply7(wl, nb, T.gy + o);
       ddz = s * apply7(wl, nb, T.gz + o);
@@ -296,94 +305,132 @@ __global__ void k_ss_mom(Geo<R> G, Vert V, Slow<R> SL, Pert<R> P, Work<R> T, R d
   }
 }
 
-// HE-VI column step: Eqs. dens2 and pt2 substituted into Eq. momr2 give a
-// tridiagonal system in W* at the interior interfaces (rigid lid W* = 0 at
-// the bottom and top), solved by the Thomas algorithm in float64; then
-// Eq. dens2, Eq. pt2 and the nonlinear Eq. theta_to_p with the new W*.
+// HE-VI column step. Eqs. dens2 and pt2 substituted into Eq. momr2 give, at
+// the interior interfaces m = 1..nv-1 (rigid lid: W* = 0 at m = 0 and nv),
+//   lo_m W_m-1 + di_m W_m + up_m W_m+1 = rh_m
+// with, for s_k = 1/(r_k^2 dz_k), q_m = r_m^2, th_m = theta at interface m,
+// w-/w+ the Lagrange weights of centres m-1, m at interface m,
+//   a_k = rho*_k + dtau (S_rho,k - div_h M*_k)
+//   b_k = Th*_k + dtau (S_th,k - div_h(theta M*)_k)
+//   c_k = p*_k + Pi_k (b_k - Th*_k)
+//   lo_m = -dtau^2/dzc_m Pi_m-1 s_m-1 q_m-1 th_m-1 + dtau^2 g w- s_m-1 q_m-1
+//   di_m = 1 + dtau^2/dzc_m q_m th_m (Pi_m s_m + Pi_m-1 s_m-1) - dtau^2 g q_m (w- s_m-1 - w+ s_m)
+//   up_m = -dtau^2/dzc_m Pi_m s_m q_m+1 th_m+1 - dtau^2 g w+ s_m q_m+1
+//   rh_m = W*_m + dtau S_W,m - dtau/dzc_m (c_m - c_m-1) - dtau g (w- a_m-1 + w+ a_m)
+// solved by the Thomas algorithm in float64; then rho* and Th* follow from
+// Eqs. dens2 and pt2 and p* from the nonlinear Eq. theta_to_p.
 template <typename R>
-__global__ void __launch_bounds__(kBlock) k_ss_col(Geo<R> G, Vert V, Phys ph, Xf<R> Xs, Slow<R> SL,
-                                                   Pert<R> P, Work<R> T, double dtau) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= G.ncol) return;
-  const int S = G.colp, nv = G.nv;
-  Nbr7 nb = load_nbr(G, c);
-  W7x3<R> wd = load_w7x3(G.wdiv, S, c);
-  double a[kMaxNv], b[kMaxNv], cc[kMaxNv];
-  double cp_[kMaxNv + 1], dp_[kMaxNv + 1];
+__global__ void __launch_bounds__(kColTile* kColRows) k_ss_col(Geo<R> G, Vert V, VR<R> U, Phys ph,
+                                                               Xf<R> Xs, Slow<R> SL, Pert<R> P,
+                                                               Work<R> T, double dtau) {
+  extern __shared__ double sm[];
+  const int nv = G.nv, S = G.colp;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int c = blockIdx.x * kColTile + tx;
+  const bool valid = c < G.ncol;
+  // shared arrays [level][kColTile]
+  double* sa = sm;                         // a_k
+  double* sb = sa + nv * kColTile;         // b_k
+  double* slo = sb + nv * kColTile;        // c_k, then lo_m
+  double* sdi = slo + nv * kColTile;       // di_m
+  double* sup = sdi + nv * kColTile;       // up_m, then c'_m
+  double* srh = sup + nv * kColTile;       // rh_m, then d'_m, then W_m
   const R rdt = (R)dtau;
-  for (int k = 0; k < nv; ++k) {
-    const int o = k * S, i = o + c;
-    R inv_r = R(1.0 / V.rc[k]);
-    R dh = div7(wd, nb, P.mx + o, P.my + o, P.mz + o) * inv_r;
-    R dht = div7_scaled(wd, nb, T.theta + o, P.mx + o, P.my + o, P.mz + o) * inv_r;
-    R ak = P.rho[i] + rdt * (SL.srho[i] - dh);
-    R thk = P.th[i];
-    R bk = thk + rdt * (SL.sth[i] - dht);
-    a[k] = (double)ak;
-    b[k] = (double)bk;
-    cc[k] = (double)P.p[i] + (double)SL.pi[i] * ((double)bk - (double)thk);
+
+  // phase 1: horizontal fluxes of the new M* and the a, b, c of every cell
+  if (valid) {
+    Nbr7 nb = load_nbr(G, c);
+    W7x3<R> wd = load_w7x3(G.wdiv, S, c);
+    for (int k = ty; k < nv; k += kColRows) {
+      const int o = k * S, i = o + c;
+      R inv_r = U.inv_rc[k];
+      R dh = div7(wd, nb, P.mx + o, P.my + o, P.mz + o) * inv_r;
+      R dht = div7_scaled(wd, nb, T.theta + o, P.mx + o, P.my + o, P.mz + o) * inv_r;
+      R ak = P.rho[i] + rdt * (SL.srho[i] - dh);
+      R thk = P.th[i];
+      R bk = thk + rdt * (SL.sth[i] - dht);
+      sa[k * kColTile + tx] = (double)ak;
+      sb[k * kColTile + tx] = (double)bk;
+      slo[k * kColTile + tx] = (double)P.p[i] + (double)SL.pi[i] * ((double)bk - (double)thk);
+    }
   }
-  // forward elimination over the interior interfaces 1..nv-1
+  __syncthreads();
+  // phase 2: tridiagonal coefficients at the interior interfaces
   const double g = ph.g, dt2 = dtau * dtau;
-  double wprev_c = 0.0, wprev_d = 0.0;
-  for (int m = 1; m < nv; ++m) {
-    const int i = m * S + c;
-    double s_lo = 1.0 / (V.rc[m - 1] * V.rc[m - 1] * V.dz[m - 1]);
-    double s_hi = 1.0 / (V.rc[m] * V.rc[m] * V.dz[m]);
-    double q = V.ri[m] * V.ri[m];
-    double th_m = (double)SL.thi[i];
-    double pi_lo = (double)SL.pi[i - S], pi_hi = (double)SL.pi[i];
-    double wlo = V.wlo[m], whi = V.whi[m], inv_dzc = 1.0 / V.dzc[m];
-    double lower = 0.0, upper = 0.0;
-    if (m > 1) {
-      double qm = V.ri[m - 1] * V.ri[m - 1];
-      double thm = (double)SL.thi[i - S];
-      lower = -dt2 * inv_dzc * pi_lo * s_lo * qm * thm + dt2 * g * wlo * s_lo * qm;
+  double lo_v[(kMaxNv + kColRows - 1) / kColRows];
+  if (valid) {
+    int slot = 0;
+    for (int m = 1 + ty; m < nv; m += kColRows, ++slot) {
+      const int i = m * S + c;
+      const double s_lo = V.sv[m - 1], s_hi = V.sv[m], q = V.ri2[m];
+      const double th_m = (double)SL.thi[i];
+      const double pi_lo = (double)SL.pi[i - S], pi_hi = (double)SL.pi[i];
+      const double wlo = V.wlo[m], whi = V.whi[m], idz = V.inv_dzc[m];
+      double lower = 0.0, upper = 0.0;
+      if (m > 1) {
+        double qm = V.ri2[m - 1];
+        lower = -dt2 * idz * pi_lo * s_lo * qm * (double)SL.thi[i - S] + dt2 * g * wlo * s_lo * qm;
+      }
+      if (m < nv - 1) {
+        double qp = V.ri2[m + 1];
+        upper = -dt2 * idz * pi_hi * s_hi * qp * (double)SL.thi[i + S] - dt2 * g * whi * s_hi * qp;
+      }
+      sdi[m * kColTile + tx] = 1.0 + dt2 * idz * q * th_m * (pi_hi * s_hi + pi_lo * s_lo)
+                             - dt2 * g * q * (wlo * s_lo - whi * s_hi);
+      sup[m * kColTile + tx] = upper;
+      srh[m * kColTile + tx] = (double)P.w[i] + dtau * (double)SL.sw[i]
+                             - dtau * idz * (slo[m * kColTile + tx] - slo[(m - 1) * kColTile + tx])
+                             - dtau * g * (wlo * sa[(m - 1) * kColTile + tx] + whi * sa[m * kColTile + tx]);
+      lo_v[slot] = lower;
     }
-    if (m < nv - 1) {
-      double qp = V.ri[m + 1] * V.ri[m + 1];
-      double thp = (double)SL.thi[i + S];
-      upper = -dt2 * inv_dzc * pi_hi * s_hi * qp * thp - dt2 * g * whi * s_hi * qp;
+  }
+  __syncthreads();
+  if (valid) {   // c_k no longer needed: the same array now holds lo_m
+    int slot = 0;
+    for (int m = 1 + ty; m < nv; m += kColRows, ++slot) slo[m * kColTile + tx] = lo_v[slot];
+  }
+  __syncthreads();
+  // phase 3: Thomas sweep, one lane per column
+  if (ty == 0 && valid) {
+    double cprev = 0.0, dprev = 0.0;
+    for (int m = 1; m < nv; ++m) {
+      const int j = m * kColTile + tx;
+      double lo = slo[j];
+      double inv = 1.0 / (sdi[j] - lo * cprev);
+      cprev = sup[j] * inv;
+      dprev = (srh[j] - lo * dprev) * inv;
+      sup[j] = cprev;
+      srh[j] = dprev;
     }
-    double diag = 1.0 + dt2 * inv_dzc * q * th_m * (pi_hi * s_hi + pi_lo * s_lo)
-                - dt2 * g * q * (wlo * s_lo - whi * s_hi);
-    double rhs = (double)P.w[i] + dtau * (double)SL.sw[i] - dtau * inv_dzc * (cc[m] - cc[m - 1])
-               - dtau * g * (wlo * a[m - 1] + whi * a[m]);
-    double den = diag - lower * wprev_c;
-    double inv = 1.0 / den;
-    double cm = upper * inv;
-    double dm = (rhs - lower * wprev_d) * inv;
-    cp_[m] = cm;
-    dp_[m] = dm;
-    wprev_c = cm;
-    wprev_d = dm;
+    double wnext = 0.0;
+    for (int m = nv - 1; m >= 1; --m) {
+      const int j = m * kColTile + tx;
+      wnext = srh[j] - sup[j] * wnext;
+      srh[j] = wnext;
+    }
+    srh[tx] = 0.0;   // bottom interface (m = 0); the top one (m = nv) is implicit
   }
-  // back substitution; cp_/dp_ now hold W*
-  double wnext = 0.0;
-  for (int m = nv - 1; m >= 1; --m) {
-    double wm = dp_[m] - cp_[m] * wnext;
-    dp_[m] = wm;
-    wnext = wm;
-  }
-  dp_[0] = 0.0;
-  dp_[nv] = 0.0;
-  const double gamma = ph.gamma;
-  for (int k = 0; k < nv; ++k) {
-    const int i = k * S + c;
-    double s = 1.0 / (V.rc[k] * V.rc[k] * V.dz[k]);
-    double qlo = V.ri[k] * V.ri[k], qhi = V.ri[k + 1] * V.ri[k + 1];
-    double wl = dp_[k], wh = dp_[k + 1];
-    double thl = k > 0 ? (double)SL.thi[i] : 0.0;
-    double thh = k + 1 < nv ? (double)SL.thi[i + S] : 0.0;
-    double rho_new = a[k] - dtau * s * (qhi * wh - qlo * wl);
-    double th_new = b[k] - dtau * s * (qhi * thh * wh - qlo * thl * wl);
-    P.rho[i] = (R)rho_new;
-    P.th[i] = (R)th_new;
-    // p* = EOS(Th^(s) + Th*) - p^(s) = p^(s) ((1 + Th*/Th^(s))^gamma - 1)
-    R ps = (R)V.pb[k] + T.pp[i];
-    R ths = (R)V.thb[k] + Xs.th[i];
-    P.p[i] = ps * rexpm1<R>((R)gamma * rlog1p<R>((R)th_new / ths));
-    if (k >= 1) P.w[i] = (R)dp_[k];
+  __syncthreads();
+  // phase 4: Eqs. dens2, pt2, theta_to_p with the new W*
+  if (valid) {
+    const double gamma = ph.gamma;
+    for (int k = ty; k < nv; k += kColRows) {
+      const int i = k * S + c;
+      const double s = V.sv[k], qlo = V.ri2[k], qhi = V.ri2[k + 1];
+      const double wl = srh[k * kColTile + tx];
+      const double wh = k + 1 < nv ? srh[(k + 1) * kColTile + tx] : 0.0;
+      const double thl = k > 0 ? (double)SL.thi[i] : 0.0;
+      const double thh = k + 1 < nv ? (double)SL.thi[i + S] : 0.0;
+      double rho_new = sa[k * kColTile + tx] - dtau * s * (qhi * wh - qlo * wl);
+      double th_new = sb[k * kColTile + tx] - dtau * s * (qhi * thh * wh - qlo * thl * wl);
+      P.rho[i] = (R)rho_new;
+      P.th[i] = (R)th_new;
+      // p* = EOS(Th^(s) + Th*) - p^(s) = p^(s) ((1 + Th*/Th^(s))^gamma - 1)
+      R ps = U.pb[k] + T.pp[i];
+      R ths = U.thb[k] + Xs.th[i];
+      P.p[i] = ps * rexpm1<R>((R)gamma * rlog1p<R>((R)th_new / ths));
+      if (k >= 1) P.w[i] = (R)wl;
+    }
   }
 }
 
@@ -414,25 +461,25 @@ __global__ void k_stage_end(Geo<R> G, Xf<R> Xs, Pert<R> P, Xf<R> Xo, int kchunk)
 // coefficients; sigma = p / p_s with p_s extrapolated hydrostatically at the
 // lowest layer's temperature.
 template <typename R>
-__global__ void k_physics(Geo<R> G, Vert V, Phys ph, Xf<R> X, int forcing, double dt, double hj_dT) {
+__global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, int forcing, double dt, double hj_dT) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
-  const R gamma = (R)ph.gamma;
+  const R gamma = (R)ph.gamma, inv_gamma = R(1.0 / ph.gamma), Rd = (R)ph.Rd;
   R sl = G.sinlat[c], cl = G.coslat[c], clon = G.coslon[c];
-  R p0 = (R)V.pb[0] + eos_dev<R>((R)V.pb[0], (R)V.thb[0], X.th[c], gamma);
-  R T0 = p0 / (((R)V.rhob[0] + X.rho[c]) * (R)ph.Rd);
-  R ps = p0 * rexp<R>((R)(ph.g * V.zc[0]) / ((R)ph.Rd * T0));
+  R p0 = U.pb[0] + eos_dev<R>(U.pb[0], U.thb[0], X.th[c], gamma);
+  R T0 = p0 / ((U.rhob[0] + X.rho[c]) * Rd);
+  R ps = p0 * rexp<R>(R(ph.g) * U.zc[0] / (Rd * T0));
   const R rdt = (R)dt;
   for (int k = 0; k < G.nv; ++k) {
     const int i = k * S + c;
     R rhop = X.rho[i];
-    R rho = (R)V.rhob[k] + rhop;
-    R p = (R)V.pb[k] + eos_dev<R>((R)V.pb[k], (R)V.thb[k], X.th[i], gamma);
-    R Temp = p / (rho * (R)ph.Rd);
+    R rho = U.rhob[k] + rhop;
+    R p = U.pb[k] + eos_dev<R>(U.pb[k], U.thb[k], X.th[i], gamma);
+    R Temp = p / (rho * Rd);
     R sigma = p / ps;
     R Kv, KT, Teq;
-    if (forcing == 1) {
+    if (forcing == THOR_FORCING_HELD_SUAREZ) {
       const R day = R(86400.0);
       const R kf = R(1) / day, ka = R(1) / (R(40) * day), ks = R(1) / (R(4) * day);
       const R sb = R(0.7), p00 = R(1.0e5);
@@ -446,7 +493,7 @@ __global__ void k_physics(Geo<R> G, Vert V, Phys ph, Xf<R> X, int forcing, doubl
       Teq = Teq > R(200) ? Teq : R(200);
     } else {
       const R ss = R(0.12), zs = R(2.0e6), Ts = R(1600), Gt = R(2.0e-4), dTs = R(10);
-      R z = (R)V.zc[k];
+      R z = U.zc[k];
       R Tv, bt;
       if (z <= zs) {
         R h = Gt * (z - zs) / R(2);
@@ -466,8 +513,8 @@ __global__ void k_physics(Geo<R> G, Vert V, Phys ph, Xf<R> X, int forcing, doubl
     X.mz[i] *= fr;
     R Tn = (Temp + KT * rdt * Teq) / (R(1) + KT * rdt);
     // rho theta at fixed rho: Th/Th_bar = ((rho/rho_bar)(T/T_bar))^(1/gamma)
-    R lr = rlog1p<R>(rhop / (R)V.rhob[k]) + rlog<R>(Tn / (R)V.Tb[k]);
-    X.th[i] = (R)V.thb[k] * rexpm1<R>(lr / gamma);
+    R lr = rlog1p<R>(rhop / U.rhob[k]) + rlog<R>(Tn / U.Tb[k]);
+    X.th[i] = U.thb[k] * rexpm1<R>(lr * inv_gamma);
   }
 }
 
@@ -478,6 +525,16 @@ void Impl<R>::launch_2d(int nplanes, int kchunk, dim3& grid) const {
   grid = dim3((G.ncol + kBlock - 1) / kBlock, (nplanes + kchunk - 1) / kchunk);
 }
 
+size_t col_smem_bytes(int nv) { return (size_t)6 * nv * kColTile * sizeof(double); }
+
+template <typename R>
+int col_kernel_setup(int nv) {
+  return cudaFuncSetAttribute(k_ss_col<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)col_smem_bytes(nv)) == cudaSuccess ? 0 : -3;
+}
+template int col_kernel_setup<double>(int);
+template int col_kernel_setup<float>(int);
+
 template <typename R>
 int Impl<R>::large_step(double dt, int n_small) {
   const int kc = kchunk;
@@ -485,46 +542,48 @@ int Impl<R>::large_step(double dt, int n_small) {
   launch_2d(G.nv, kc, g2);
   launch_2d(G.nv + 1, kc, g2i);
   dim3 g1((G.ncol + kBlock - 1) / kBlock);
+  dim3 gcol((G.ncol + kColTile - 1) / kColTile), bcol(kColTile, kColRows);
+  const size_t col_smem = col_smem_bytes(G.nv);
   const R Kd = (R)(diff_D * dbar4 / dt);
   const double dts[3] = {dt / 3.0, dt / n_small, dt / n_small};
   const int nsub[3] = {1, n_small / 2, n_small};
   for (int s = 0; s < 3; ++s) {
     Xf<R> Xs = s == 0 ? Xt : Xst;
     mark(THOR_K_DERIVED, true);
-    k_derived<R><<<g2i, kBlock, 0, stream>>>(G, V, ph, Xs, T, kc);
+    k_derived<R><<<g2i, kBlock, 0, stream>>>(G, U, ph, Xs, T, kc);
     mark(THOR_K_DERIVED, false);
     ++launches;
     if (hyper) {
       mark(THOR_K_LAP1, true);
-      k_lap1<R><<<g2i, kBlock, 0, stream>>>(G, V, Xs, T, Kd, kc);
+      k_lap1<R><<<g2i, kBlock, 0, stream>>>(G, U, Xs, T, Kd, kc);
       mark(THOR_K_LAP1, false);
       ++launches;
     }
     mark(THOR_K_SLOW, true);
-    k_slow<R><<<g2, kBlock, 0, stream>>>(G, V, ph, Xs, T, SL, hyper, kc);
+    k_slow<R><<<g2, kBlock, 0, stream>>>(G, U, ph, Xs, T, SL, hyper, kc);
     mark(THOR_K_SLOW, false);
     mark(THOR_K_SLOW_W, true);
-    k_slow_w<R><<<g2i, kBlock, 0, stream>>>(G, V, ph, Xs, T, SL, hyper, kc);
+    k_slow_w<R><<<g2i, kBlock, 0, stream>>>(G, U, ph, Xs, T, SL, hyper, kc);
     mark(THOR_K_SLOW_W, false);
     mark(THOR_K_STAGE_INIT, true);
-    k_stage_init<R><<<g2i, kBlock, 0, stream>>>(G, V, ph, Xt, Xs, T, P, kc);
+    k_stage_init<R><<<g2i, kBlock, 0, stream>>>(G, U, ph, Xt, Xs, T, P, kc);
     mark(THOR_K_STAGE_INIT, false);
     launches += 3;
     for (int j = 0; j < nsub[s]; ++j) {
       if (divdamp) {
         mark(THOR_K_SS_DIV, true);
-        k_ss_div<R><<<g2, kBlock, 0, stream>>>(G, V, SL, P, T, kc);
+        k_ss_div<R><<<g2, kBlock, 0, stream>>>(G, U, SL, P, T, kc);
         mark(THOR_K_SS_DIV, false);
         mark(THOR_K_SS_GRAD, true);
-        k_ss_grad<R><<<g2, kBlock, 0, stream>>>(G, V, T, kc);
+        k_ss_grad<R><<<g2, kBlock, 0, stream>>>(G, U, T, kc);
         mark(THOR_K_SS_GRAD, false);
         launches += 2;
       }
       mark(THOR_K_SS_MOM, true);
-      k_ss_mom<R><<<g2, kBlock, 0, stream>>>(G, V, SL, P, T, (R)dts[s], Kd, divdamp, kc);
+      k_ss_mom<R><<<g2, kBlock, 0, stream>>>(G, U, SL, P, T, (R)dts[s], Kd, divdamp, kc);
       mark(THOR_K_SS_MOM, false);
       mark(THOR_K_SS_COL, true);
-      k_ss_col<R><<<g1, kBlock, 0, stream>>>(G, V, ph, Xs, SL, P, T, dts[s]);
+      k_ss_col<R><<<gcol, bcol, col_smem, stream>>>(G, V, U, ph, Xs, SL, P, T, dts[s]);
       mark(THOR_K_SS_COL, false);
       launches += 2;
     }
@@ -536,7 +595,7 @@ int Impl<R>::large_step(double dt, int n_small) {
   }
   if (forcing != 0) {
     mark(THOR_K_PHYSICS, true);
-    k_physics<R><<<g1, kBlock, 0, stream>>>(G, V, ph, Xt, forcing, dt, hj_dT);
+    k_physics<R><<<g1, kBlock, 0, stream>>>(G, U, ph, Xt, forcing, dt, hj_dT);
     mark(THOR_K_PHYSICS, false);
     ++launches;
   }
