@@ -156,6 +156,13 @@ int thor_state_set(thor_state* state, int field, const double* host, size_t n);
 /* Kernel launches issued by this state so far. */
 int thor_launch_count(const thor_state* state, long long* count);
 
+/* Launch-shape knobs. THOR_TUNE_KCHUNK: levels each thread of the stencil
+ * kernels walks (1..256, default 8); fewer levels mean more threads in
+ * flight, more levels mean fewer reloads of the per-column weights. The
+ * results do not depend on it. */
+enum { THOR_TUNE_KCHUNK = 0 };
+int thor_tune(thor_state* state, int knob, int value);
+
 /* Per-kernel timing. While enabled, every launch of the state is bracketed by
  * two CUDA events recorded on the state's stream; thor_profile_read
  * synchronises the stream and returns, for one kernel id, the summed

@@ -22,6 +22,9 @@ Readings (listed in DESIGN.md):
   the sine of sigma below z_stra (even where sigma < sigma_stra) and 0
   above; K_v = 0; K_T = 1/tau with tau = 1.5e5 s. The sub-stellar point is at
   longitude 0 (the paper's is shifted by pi, which only moves the pattern).
+  The factor cos(lambda) cos(phi) of Eq. teq-hj is evaluated as the x
+  coordinate of the unit position vector, which it equals exactly; at the
+  poles the longitude is undefined and the factor is 0.
 """
 
 import numpy as np
@@ -73,9 +76,9 @@ def hot_jupiter_beta_trop(sigma, z):
     return np.where(z <= h["z_stra"], s, 0.0)
 
 
-def hot_jupiter_coefficients(sigma, z, lon, lat, dT_ep):
+def hot_jupiter_coefficients(sigma, z, coslon_coslat, dT_ep):
     """Eq. teq-hj with K_v = 0, K_T = 1/tau. Returns (K_v, K_T, T_eq)."""
-    T_eq = hot_jupiter_T_vert(z) + hot_jupiter_beta_trop(sigma, z) * dT_ep * np.cos(lon) * np.cos(lat)
+    T_eq = hot_jupiter_T_vert(z) + hot_jupiter_beta_trop(sigma, z) * dT_ep * coslon_coslat
     return np.zeros_like(sigma), np.full_like(sigma, 1.0 / HJ["tau"]), T_eq
 
 
@@ -92,8 +95,8 @@ def apply_physics(model, X, dt):
     if model.forcing == "held_suarez":
         K_v, K_T, T_eq = held_suarez_coefficients(sigma, p, lat[:, None], pl.kappa)
     elif model.forcing == "hot_jupiter":
-        K_v, K_T, T_eq = hot_jupiter_coefficients(sigma, model.vg.zc[None, :], lon[:, None],
-                                                  lat[:, None], model.hj_dT)
+        K_v, K_T, T_eq = hot_jupiter_coefficients(sigma, model.vg.zc[None, :],
+                                                  model.grid.points[:, 0:1], model.hj_dT)
     else:
         raise ValueError(model.forcing)
     M = X.M / (1.0 + K_v * dt)[..., None]

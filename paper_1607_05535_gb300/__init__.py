@@ -26,7 +26,7 @@ EXPORTED = [
     "thor_strerror", "thor_grid_create", "thor_grid_info", "thor_grid_points",
     "thor_grid_neighbours", "thor_grid_areas", "thor_grid_destroy", "thor_state_init",
     "thor_step", "thor_diag", "thor_state_get", "thor_state_set", "thor_launch_count",
-    "thor_profile", "thor_profile_read", "thor_state_destroy",
+    "thor_tune", "thor_profile", "thor_profile_read", "thor_state_destroy",
 ]
 
 # kernel ids of thor_profile_read
@@ -90,6 +90,7 @@ def _load():
         "thor_state_get": (I, [P, I, P, Z]),
         "thor_state_set": (I, [P, I, P, Z]),
         "thor_launch_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+        "thor_tune": (I, [P, I, I]),
         "thor_profile": (I, [P, I]),
         "thor_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_longlong)]),
@@ -203,6 +204,13 @@ def thor_launch_count(state):
     c = ctypes.c_longlong()
     _check(_lib.thor_launch_count(state, ctypes.byref(c)), "thor_launch_count")
     return c.value
+
+
+THOR_TUNE_KCHUNK = 0
+
+
+def thor_tune(state, knob, value):
+    _check(_lib.thor_tune(state, knob, value), "thor_tune")
 
 
 def thor_profile(state, enable):

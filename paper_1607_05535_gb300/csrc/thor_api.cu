@@ -27,7 +27,7 @@ int col_kernel_setup(int nv);   // thor_step.cu: opt the column kernel into its 
 namespace {
 
 inline int colp_of(int ncol) { return (ncol + kBlock - 1) / kBlock * kBlock; }
-constexpr int kNumVertCentre = 10, kNumVert = 17;   // float64 vertical arrays (centres, total)
+constexpr int kNumVertCentre = 12, kNumVert = 19;   // float64 vertical arrays (centres, total)
 
 uint64_t splitmix64(uint64_t x) {
   uint64_t z = x + 0x9E3779B97F4A7C15ULL;
@@ -201,7 +201,7 @@ struct Carver {
 template <typename R>
 std::vector<const R**> vr_slots(VR<R>& U) {
   return {&U.inv_rc, &U.inv_rc2, &U.sv, &U.ri2, &U.wlo, &U.whi, &U.clo, &U.chi, &U.inv_dzc,
-          &U.rhob, &U.thb, &U.pb, &U.Tb, &U.Rb, &U.zc};
+          &U.rhob, &U.thb, &U.pb, &U.Tb, &U.Rb, &U.zc, &U.sq_lo, &U.sq_hi};
 }
 
 template <typename R>
@@ -237,10 +237,10 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   I.G.rhat = cv.take<R>(3 * S);
   I.G.sinlat = cv.take<R>(S);
   I.G.coslat = cv.take<R>(S);
-  I.G.coslon = cv.take<R>(S);
+  I.G.xdir = cv.take<R>(S);
   I.G.area = cv.take<double>(S);
   const double** vp[] = {&I.V.rc, &I.V.dz, &I.V.clo, &I.V.chi, &I.V.zc, &I.V.rhob, &I.V.thb, &I.V.pb,
-                         &I.V.Tb, &I.V.sv};
+                         &I.V.Tb, &I.V.sv, &I.V.sq_lo, &I.V.sq_hi};
   for (const double** p : vp) *p = cv.take<double>(nv);
   const double** vi[] = {&I.V.ri, &I.V.dzc, &I.V.wlo, &I.V.whi, &I.V.Rb, &I.V.ri2, &I.V.inv_dzc};
   for (const double** p : vi) *p = cv.take<double>(nv + 1);
@@ -273,10 +273,9 @@ int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert
     rhat[S + c] = (R)y;
     rhat[2 * S + c] = (R)z;
     double lat = std::asin(std::fmax(-1.0, std::fmin(1.0, z)));
-    double lon = std::atan2(y, x);
     sl[c] = (R)std::sin(lat);
     cl[c] = (R)std::cos(lat);
-    clon[c] = (R)std::cos(lon);
+    clon[c] = (R)x;   // cos(lon) cos(lat), well defined at the poles
     area[c] = h.area[c];
   }
   auto up = [&](const void* dst, const void* src, size_t bytes) {
@@ -290,10 +289,11 @@ int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert
   e = e ? e : up(I.G.rhat, rhat.data(), rhat.size() * sizeof(R));
   e = e ? e : up(I.G.sinlat, sl.data(), sl.size() * sizeof(R));
   e = e ? e : up(I.G.coslat, cl.data(), cl.size() * sizeof(R));
-  e = e ? e : up(I.G.coslon, clon.data(), clon.size() * sizeof(R));
+  e = e ? e : up(I.G.xdir, clon.data(), clon.size() * sizeof(R));
   e = e ? e : up(I.G.area, area.data(), area.size() * sizeof(double));
   const double* vp[] = {I.V.rc, I.V.dz, I.V.clo, I.V.chi, I.V.zc, I.V.rhob, I.V.thb, I.V.pb, I.V.Tb,
-                        I.V.sv, I.V.ri, I.V.dzc, I.V.wlo, I.V.whi, I.V.Rb, I.V.ri2, I.V.inv_dzc};
+                        I.V.sv, I.V.sq_lo, I.V.sq_hi, I.V.ri, I.V.dzc, I.V.wlo, I.V.whi, I.V.Rb,
+                        I.V.ri2, I.V.inv_dzc};
   for (int j = 0; j < kNumVert; ++j) {
     size_t cnt = j < kNumVertCentre ? nv : nv + 1;
     e = e ? e : up(vp[j], vert[j].data(), cnt * sizeof(double));
@@ -301,7 +301,7 @@ int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert
   // storage-type copies with the reciprocals precomputed
   {
     const std::vector<double>& rc = vert[0];
-    std::vector<std::vector<R>> vr(15, std::vector<R>(nv + 1, R(0)));
+    std::vector<std::vector<R>> vr(17, std::vector<R>(nv + 1, R(0)));
     for (int k = 0; k < nv; ++k) {
       vr[0][k] = (R)(1.0 / rc[k]);
       vr[1][k] = (R)(1.0 / (rc[k] * rc[k]));
@@ -313,16 +313,18 @@ int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert
       vr[11][k] = (R)vert[7][k];
       vr[12][k] = (R)vert[8][k];
       vr[14][k] = (R)vert[4][k];
+      vr[15][k] = (R)vert[10][k];
+      vr[16][k] = (R)vert[11][k];
     }
     for (int i = 0; i <= nv; ++i) {
-      vr[3][i] = (R)vert[15][i];
-      vr[4][i] = (R)vert[12][i];
-      vr[5][i] = (R)vert[13][i];
-      vr[8][i] = (R)vert[16][i];
-      vr[13][i] = (R)vert[14][i];
+      vr[3][i] = (R)vert[17][i];
+      vr[4][i] = (R)vert[14][i];
+      vr[5][i] = (R)vert[15][i];
+      vr[8][i] = (R)vert[18][i];
+      vr[13][i] = (R)vert[16][i];
     }
     std::vector<const R**> slots = vr_slots(I.U);
-    for (int j = 0; j < 15; ++j) e = e ? e : up(*slots[j], vr[j].data(), (nv + 1) * sizeof(R));
+    for (int j = 0; j < 17; ++j) e = e ? e : up(*slots[j], vr[j].data(), (nv + 1) * sizeof(R));
     if (e) return THOR_ECUDA;
     if (cudaStreamSynchronize(st)) return THOR_ECUDA;   // host vectors die here
   }
@@ -403,7 +405,7 @@ namespace {
 
 // Vertical grid, reference column and initial state in float64 on the host.
 struct HostSetup {
-  // rc dz clo chi zc rhob thb pb Tb sv | ri dzc wlo whi Rb ri2 inv_dzc
+  // rc dz clo chi zc rhob thb pb Tb sv sq_lo sq_hi | ri dzc wlo whi Rb ri2 inv_dzc
   std::vector<double> vert[kNumVert];
   std::vector<double> rho, th;    // canonical [ncol][nv]
 };
@@ -417,9 +419,9 @@ void host_setup(const HostGrid& h, const thor_planet& pl, const thor_init& in, H
   for (int k = 0; k < nv; ++k) zc[k] = 0.5 * (zi[k] + zi[k + 1]);
   auto& rc = hs.vert[0]; auto& dz = hs.vert[1]; auto& clo = hs.vert[2]; auto& chi = hs.vert[3];
   auto& zcv = hs.vert[4]; auto& rhob = hs.vert[5]; auto& thb = hs.vert[6]; auto& pb = hs.vert[7];
-  auto& Tb = hs.vert[8]; auto& sv = hs.vert[9]; auto& ri = hs.vert[10]; auto& dzc = hs.vert[11];
-  auto& wlo = hs.vert[12]; auto& whi = hs.vert[13]; auto& Rb = hs.vert[14]; auto& ri2 = hs.vert[15];
-  auto& inv_dzc = hs.vert[16];
+  auto& Tb = hs.vert[8]; auto& sv = hs.vert[9]; auto& sq_lo = hs.vert[10]; auto& sq_hi = hs.vert[11];
+  auto& ri = hs.vert[12]; auto& dzc = hs.vert[13]; auto& wlo = hs.vert[14]; auto& whi = hs.vert[15];
+  auto& Rb = hs.vert[16]; auto& ri2 = hs.vert[17]; auto& inv_dzc = hs.vert[18];
   for (int j = 0; j < kNumVertCentre; ++j) hs.vert[j].assign(nv, 0.0);
   for (int j = kNumVertCentre; j < kNumVert; ++j) hs.vert[j].assign(nv + 1, 0.0);
   for (int k = 0; k < nv; ++k) {
@@ -429,10 +431,14 @@ void host_setup(const HostGrid& h, const thor_planet& pl, const thor_init& in, H
     chi[k] = (zc[k] - zi[k]) / (zi[k + 1] - zi[k]);
     zcv[k] = zc[k];
   }
-  for (int k = 0; k < nv; ++k) sv[k] = 1.0 / (rc[k] * rc[k] * dz[k]);
   for (int i = 0; i <= nv; ++i) {
     ri[i] = h.radius + zi[i];
     ri2[i] = ri[i] * ri[i];
+  }
+  for (int k = 0; k < nv; ++k) {
+    sv[k] = 1.0 / (rc[k] * rc[k] * dz[k]);
+    sq_lo[k] = ri2[k] * sv[k];
+    sq_hi[k] = ri2[k + 1] * sv[k];
   }
   for (int i = 1; i < nv; ++i) {
     dzc[i] = zc[i] - zc[i - 1];
@@ -654,6 +660,16 @@ int thor_launch_count(const thor_state* s, long long* count) {
   if (!s || !count) return THOR_EINVAL;
   *count = s->impl->launches;
   return THOR_OK;
+}
+
+int thor_tune(thor_state* s, int knob, int value) {
+  if (!s) return THOR_EINVAL;
+  if (knob == THOR_TUNE_KCHUNK) {
+    if (value < 1 || value > 256) return THOR_EINVAL;
+    s->impl->kchunk = value;
+    return THOR_OK;
+  }
+  return THOR_EINVAL;
 }
 
 int thor_profile(thor_state* s, int enable) {

@@ -42,6 +42,7 @@ struct ImplBase {
   virtual int get(int field, double* host, size_t n) = 0;
   virtual int set(int field, const double* host, size_t n) = 0;
   long long launches = 0;
+  int kchunk = 8;                      // levels per thread in the stencil kernels
   // per-kernel event timing (off unless enabled)
   cudaStream_t stream = nullptr;
   bool prof_on = false;
@@ -100,7 +101,6 @@ struct Impl : ImplBase {
   Work<R> T;
   Slow<R> SL;
   Pert<R> P;
-  int kchunk = 8;
   int hyper = 1, divdamp = 1, forcing = 0;
   double diff_D = 0, dbar4 = 0, hj_dT = 300.0;
   // device allocations

@@ -46,6 +46,8 @@ struct Vert {
   const double* sv;     // [nv]   1 / (rc^2 dz): radial divergence factor
   const double* ri2;    // [nv+1] ri^2
   const double* inv_dzc;// [nv+1] 1 / dzc
+  const double* sq_lo;  // [nv] ri[k]^2 / (rc^2 dz): weight of the bottom interface in div_v
+  const double* sq_hi;  // [nv] ri[k+1]^2 / (rc^2 dz): weight of the top interface
 };
 
 // The same vertical quantities in the storage type, with the reciprocals
@@ -54,6 +56,7 @@ template <typename R>
 struct VR {
   const R *inv_rc, *inv_rc2, *sv, *ri2, *wlo, *whi, *clo, *chi, *inv_dzc;
   const R *rhob, *thb, *pb, *Tb, *Rb, *zc;
+  const R *sq_lo, *sq_hi;
 };
 
 template <typename R>
@@ -66,7 +69,7 @@ struct Geo {
   const R* rhat;        // [3][colp]
   const R* sinlat;      // [colp]
   const R* coslat;
-  const R* coslon;
+  const R* xdir;        // cos(lon) cos(lat) = x of the unit position
   const double* area;   // [colp]
 };
 
@@ -106,6 +109,17 @@ template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return sqr
 template <typename R>
 __device__ __forceinline__ R eos_dev(R pbar, R thbar, R thp, R gamma) {
   return pbar * rexpm1<R>(gamma * rlog1p<R>(thp / thbar));
+}
+
+// 1/x in float64: a float32 reciprocal refined by two Newton-Raphson steps
+// r <- r + r (1 - x r); each step squares the relative error (2^-23 -> 2^-46
+// -> below 2^-53), at four float64 FMAs instead of a float64 division.
+__device__ __forceinline__ double rcp64(double x) {
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
 }
 
 struct Nbr7 {

@@ -116,8 +116,7 @@ __global__ void k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> S
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
     const R inv_r = U.inv_rc[k], inv_r2 = U.inv_rc2[k];
-    const R qlo = U.ri2[k], qhi = U.ri2[k + 1];
-    const R sv = U.sv[k];
+    const R sql = U.sq_lo[k], sqh = U.sq_hi[k];
     R thfull = U.thb[k] + X.th[i];
     R p = U.pb[k] + T.pp[i];
 
@@ -143,7 +142,7 @@ __global__ void k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> S
       R vlo = 0, vhi = 0;
       if (k >= 1) vlo = U.wlo[k] * vs[j][i - S] + U.whi[k] * vs[j][i];
       if (k + 1 < G.nv) vhi = U.wlo[k + 1] * vs[j][i] + U.whi[k + 1] * vs[j][i + S];
-      A[j] = ah + (qhi * whi_w * vhi - qlo * wlo_w * vlo) * sv;
+      A[j] = ah + sqh * whi_w * vhi - sql * wlo_w * vlo;
     }
     // Coriolis 2 Omega z x (rho v) with the full momentum
     R wc = U.clo[k] * wlo_w + U.chi[k] * whi_w;
@@ -163,7 +162,7 @@ __global__ void k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> S
     SL.smz[i] = smz;
 
     R dh = div7(wd, nb, X.mx + o, X.my + o, X.mz + o) * inv_r;
-    R dv = (qhi * whi_w - qlo * wlo_w) * sv;
+    R dv = sqh * whi_w - sql * wlo_w;
     SL.srho[i] = -dh - dv + Frho;
     SL.dsc[i] = dh + dv;
 
@@ -171,7 +170,7 @@ __global__ void k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> S
     R thlo = 0, thhi = 0;
     if (k >= 1) thlo = U.wlo[k] * T.theta[i - S] + U.whi[k] * T.theta[i];
     if (k + 1 < G.nv) thhi = U.wlo[k + 1] * T.theta[i] + U.whi[k + 1] * T.theta[i + S];
-    R dvt = (qhi * thhi * whi_w - qlo * thlo * wlo_w) * sv;
+    R dvt = sqh * thhi * whi_w - sql * thlo * wlo_w;
     SL.sth[i] = Fth - dht - dvt;
     SL.acr[i] = acr;
     SL.pi[i] = gamma * p / thfull;
@@ -246,7 +245,7 @@ __global__ void k_ss_div(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, in
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
     R dh = div7(wd, nb, P.mx + o, P.my + o, P.mz + o) * U.inv_rc[k];
-    R dv = (U.ri2[k + 1] * P.w[i + S] - U.ri2[k] * P.w[i]) * U.sv[k];
+    R dv = U.sq_hi[k] * P.w[i + S] - U.sq_lo[k] * P.w[i];
     T.dd[i] = SL.dsc[i] + dh + dv;
   }
 }
@@ -308,33 +307,38 @@ __global__ void k_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R 
 // HE-VI column step. Eqs. dens2 and pt2 substituted into Eq. momr2 give, at
 // the interior interfaces m = 1..nv-1 (rigid lid: W* = 0 at m = 0 and nv),
 //   lo_m W_m-1 + di_m W_m + up_m W_m+1 = rh_m
-// with, for s_k = 1/(r_k^2 dz_k), q_m = r_m^2, th_m = theta at interface m,
-// w-/w+ the Lagrange weights of centres m-1, m at interface m,
+// with e_k = r_k^2/(rc_k^2 dz_k) at the bottom (sq_lo) and top (sq_hi)
+// interfaces of cell k, th_m = theta at interface m and w-/w+ the Lagrange
+// weights of centres m-1, m at interface m:
 //   a_k = rho*_k + dtau (S_rho,k - div_h M*_k)
 //   b_k = Th*_k + dtau (S_th,k - div_h(theta M*)_k)
 //   c_k = p*_k + Pi_k (b_k - Th*_k)
-//   lo_m = -dtau^2/dzc_m Pi_m-1 s_m-1 q_m-1 th_m-1 + dtau^2 g w- s_m-1 q_m-1
-//   di_m = 1 + dtau^2/dzc_m q_m th_m (Pi_m s_m + Pi_m-1 s_m-1) - dtau^2 g q_m (w- s_m-1 - w+ s_m)
-//   up_m = -dtau^2/dzc_m Pi_m s_m q_m+1 th_m+1 - dtau^2 g w+ s_m q_m+1
+//   lo_m = -dtau^2/dzc_m Pi_m-1 sq_lo_m-1 th_m-1 + dtau^2 g w- sq_lo_m-1
+//   di_m = 1 + dtau^2/dzc_m th_m (Pi_m sq_lo_m + Pi_m-1 sq_hi_m-1)
+//            - dtau^2 g (w- sq_hi_m-1 - w+ sq_lo_m)
+//   up_m = -dtau^2/dzc_m Pi_m sq_hi_m th_m+1 - dtau^2 g w+ sq_hi_m
 //   rh_m = W*_m + dtau S_W,m - dtau/dzc_m (c_m - c_m-1) - dtau g (w- a_m-1 + w+ a_m)
-// solved by the Thomas algorithm in float64; then rho* and Th* follow from
-// Eqs. dens2 and pt2 and p* from the nonlinear Eq. theta_to_p.
+// The coefficients are assembled in the storage precision; the Thomas
+// elimination runs in float64. Then rho* and Th* follow from Eqs. dens2 and
+// pt2 and p* from the nonlinear Eq. theta_to_p.
 template <typename R>
-__global__ void __launch_bounds__(kColTile* kColRows) k_ss_col(Geo<R> G, Vert V, VR<R> U, Phys ph,
-                                                               Xf<R> Xs, Slow<R> SL, Pert<R> P,
-                                                               Work<R> T, double dtau) {
+__global__ void __launch_bounds__(kColTile* kColRows) k_ss_col(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
+                                                               Slow<R> SL, Pert<R> P, Work<R> T,
+                                                               double dtau) {
   extern __shared__ double sm[];
   const int nv = G.nv, S = G.colp;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int c = blockIdx.x * kColTile + tx;
   const bool valid = c < G.ncol;
-  // shared arrays [level][kColTile]
-  double* sa = sm;                         // a_k
-  double* sb = sa + nv * kColTile;         // b_k
-  double* slo = sb + nv * kColTile;        // c_k, then lo_m
-  double* sdi = slo + nv * kColTile;       // di_m
-  double* sup = sdi + nv * kColTile;       // up_m, then c'_m
-  double* srh = sup + nv * kColTile;       // rh_m, then d'_m, then W_m
+  const int L = nv * kColTile;
+  double* scp = sm;                        // c'_m (float64)
+  double* sdp = scp + L;                   // d'_m, then W_m (float64)
+  R* sa = reinterpret_cast<R*>(sdp + L);   // a_k
+  R* sb = sa + L;                          // b_k
+  R* sc = sb + L;                          // c_k, then lo_m
+  R* sdi = sc + L;                         // di_m
+  R* sup = sdi + L;                        // up_m
+  R* srh = sup + L;                        // rh_m
   const R rdt = (R)dtau;
 
   // phase 1: horizontal fluxes of the new M* and the a, b, c of every cell
@@ -346,90 +350,81 @@ __global__ void __launch_bounds__(kColTile* kColRows) k_ss_col(Geo<R> G, Vert V,
       R inv_r = U.inv_rc[k];
       R dh = div7(wd, nb, P.mx + o, P.my + o, P.mz + o) * inv_r;
       R dht = div7_scaled(wd, nb, T.theta + o, P.mx + o, P.my + o, P.mz + o) * inv_r;
-      R ak = P.rho[i] + rdt * (SL.srho[i] - dh);
       R thk = P.th[i];
       R bk = thk + rdt * (SL.sth[i] - dht);
-      sa[k * kColTile + tx] = (double)ak;
-      sb[k * kColTile + tx] = (double)bk;
-      slo[k * kColTile + tx] = (double)P.p[i] + (double)SL.pi[i] * ((double)bk - (double)thk);
+      sa[k * kColTile + tx] = P.rho[i] + rdt * (SL.srho[i] - dh);
+      sb[k * kColTile + tx] = bk;
+      sc[k * kColTile + tx] = P.p[i] + SL.pi[i] * (bk - thk);
     }
   }
   __syncthreads();
   // phase 2: tridiagonal coefficients at the interior interfaces
-  const double g = ph.g, dt2 = dtau * dtau;
-  double lo_v[(kMaxNv + kColRows - 1) / kColRows];
+  const R g = (R)ph.g, dt2 = (R)(dtau * dtau);
+  R lo_v[(kMaxNv + kColRows - 1) / kColRows];
   if (valid) {
     int slot = 0;
     for (int m = 1 + ty; m < nv; m += kColRows, ++slot) {
-      const int i = m * S + c;
-      const double s_lo = V.sv[m - 1], s_hi = V.sv[m], q = V.ri2[m];
-      const double th_m = (double)SL.thi[i];
-      const double pi_lo = (double)SL.pi[i - S], pi_hi = (double)SL.pi[i];
-      const double wlo = V.wlo[m], whi = V.whi[m], idz = V.inv_dzc[m];
-      double lower = 0.0, upper = 0.0;
-      if (m > 1) {
-        double qm = V.ri2[m - 1];
-        lower = -dt2 * idz * pi_lo * s_lo * qm * (double)SL.thi[i - S] + dt2 * g * wlo * s_lo * qm;
-      }
-      if (m < nv - 1) {
-        double qp = V.ri2[m + 1];
-        upper = -dt2 * idz * pi_hi * s_hi * qp * (double)SL.thi[i + S] - dt2 * g * whi * s_hi * qp;
-      }
-      sdi[m * kColTile + tx] = 1.0 + dt2 * idz * q * th_m * (pi_hi * s_hi + pi_lo * s_lo)
-                             - dt2 * g * q * (wlo * s_lo - whi * s_hi);
-      sup[m * kColTile + tx] = upper;
-      srh[m * kColTile + tx] = (double)P.w[i] + dtau * (double)SL.sw[i]
-                             - dtau * idz * (slo[m * kColTile + tx] - slo[(m - 1) * kColTile + tx])
-                             - dtau * g * (wlo * sa[(m - 1) * kColTile + tx] + whi * sa[m * kColTile + tx]);
+      const int i = m * S + c, j = m * kColTile + tx;
+      const R th_m = SL.thi[i];
+      const R pi_lo = SL.pi[i - S], pi_hi = SL.pi[i];
+      const R wlo = U.wlo[m], whi = U.whi[m], dtz = dt2 * U.inv_dzc[m];
+      const R ql = U.sq_lo[m - 1], qh = U.sq_hi[m - 1];    // cell m-1
+      const R pl = U.sq_lo[m], ph_ = U.sq_hi[m];           // cell m
+      R lower = 0, upper = 0;
+      if (m > 1) lower = (-dtz * pi_lo * SL.thi[i - S] + dt2 * g * wlo) * ql;
+      if (m < nv - 1) upper = (-dtz * pi_hi * SL.thi[i + S] - dt2 * g * whi) * ph_;
+      sdi[j] = R(1) + dtz * th_m * (pi_hi * pl + pi_lo * qh) - dt2 * g * (wlo * qh - whi * pl);
+      sup[j] = upper;
+      srh[j] = P.w[i] + rdt * SL.sw[i] - rdt * U.inv_dzc[m] * (sc[j] - sc[j - kColTile])
+             - rdt * g * (wlo * sa[j - kColTile] + whi * sa[j]);
       lo_v[slot] = lower;
     }
   }
   __syncthreads();
-  if (valid) {   // c_k no longer needed: the same array now holds lo_m
+  if (valid) {   // c_k is no longer needed: the same array now holds lo_m
     int slot = 0;
-    for (int m = 1 + ty; m < nv; m += kColRows, ++slot) slo[m * kColTile + tx] = lo_v[slot];
+    for (int m = 1 + ty; m < nv; m += kColRows, ++slot) sc[m * kColTile + tx] = lo_v[slot];
   }
   __syncthreads();
-  // phase 3: Thomas sweep, one lane per column
+  // phase 3: Thomas sweep in float64, one lane per column
   if (ty == 0 && valid) {
     double cprev = 0.0, dprev = 0.0;
     for (int m = 1; m < nv; ++m) {
       const int j = m * kColTile + tx;
-      double lo = slo[j];
-      double inv = 1.0 / (sdi[j] - lo * cprev);
-      cprev = sup[j] * inv;
-      dprev = (srh[j] - lo * dprev) * inv;
-      sup[j] = cprev;
-      srh[j] = dprev;
+      const double lo = (double)sc[j];
+      const double inv = rcp64((double)sdi[j] - lo * cprev);
+      cprev = (double)sup[j] * inv;
+      dprev = ((double)srh[j] - lo * dprev) * inv;
+      scp[j] = cprev;
+      sdp[j] = dprev;
     }
     double wnext = 0.0;
     for (int m = nv - 1; m >= 1; --m) {
       const int j = m * kColTile + tx;
-      wnext = srh[j] - sup[j] * wnext;
-      srh[j] = wnext;
+      wnext = sdp[j] - scp[j] * wnext;
+      sdp[j] = wnext;
     }
-    srh[tx] = 0.0;   // bottom interface (m = 0); the top one (m = nv) is implicit
+    sdp[tx] = 0.0;   // bottom interface (m = 0); the top one (m = nv) is implicit
   }
   __syncthreads();
   // phase 4: Eqs. dens2, pt2, theta_to_p with the new W*
   if (valid) {
-    const double gamma = ph.gamma;
+    const R gamma = (R)ph.gamma;
     for (int k = ty; k < nv; k += kColRows) {
-      const int i = k * S + c;
-      const double s = V.sv[k], qlo = V.ri2[k], qhi = V.ri2[k + 1];
-      const double wl = srh[k * kColTile + tx];
-      const double wh = k + 1 < nv ? srh[(k + 1) * kColTile + tx] : 0.0;
-      const double thl = k > 0 ? (double)SL.thi[i] : 0.0;
-      const double thh = k + 1 < nv ? (double)SL.thi[i + S] : 0.0;
-      double rho_new = sa[k * kColTile + tx] - dtau * s * (qhi * wh - qlo * wl);
-      double th_new = sb[k * kColTile + tx] - dtau * s * (qhi * thh * wh - qlo * thl * wl);
-      P.rho[i] = (R)rho_new;
-      P.th[i] = (R)th_new;
+      const int i = k * S + c, j = k * kColTile + tx;
+      const R wl = (R)sdp[j];
+      const R wh = k + 1 < nv ? (R)sdp[j + kColTile] : R(0);
+      const R thl = k > 0 ? SL.thi[i] : R(0);
+      const R thh = k + 1 < nv ? SL.thi[i + S] : R(0);
+      const R el = U.sq_lo[k], eh = U.sq_hi[k];
+      R th_new = sb[j] - rdt * (eh * thh * wh - el * thl * wl);
+      P.rho[i] = sa[j] - rdt * (eh * wh - el * wl);
+      P.th[i] = th_new;
       // p* = EOS(Th^(s) + Th*) - p^(s) = p^(s) ((1 + Th*/Th^(s))^gamma - 1)
       R ps = U.pb[k] + T.pp[i];
       R ths = U.thb[k] + Xs.th[i];
-      P.p[i] = ps * rexpm1<R>((R)gamma * rlog1p<R>((R)th_new / ths));
-      if (k >= 1) P.w[i] = (R)wl;
+      P.p[i] = ps * rexpm1<R>(gamma * rlog1p<R>(th_new / ths));
+      if (k >= 1) P.w[i] = wl;
     }
   }
 }
@@ -466,7 +461,7 @@ __global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, int forcing, doub
   if (c >= G.ncol) return;
   const int S = G.colp;
   const R gamma = (R)ph.gamma, inv_gamma = R(1.0 / ph.gamma), Rd = (R)ph.Rd;
-  R sl = G.sinlat[c], cl = G.coslat[c], clon = G.coslon[c];
+  R sl = G.sinlat[c], cl = G.coslat[c], clcl = G.xdir[c];
   R p0 = U.pb[0] + eos_dev<R>(U.pb[0], U.thb[0], X.th[c], gamma);
   R T0 = p0 / ((U.rhob[0] + X.rho[c]) * Rd);
   R ps = p0 * rexp<R>(R(ph.g) * U.zc[0] / (Rd * T0));
@@ -505,7 +500,7 @@ __global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, int forcing, doub
       }
       Kv = 0;
       KT = R(1) / R(1.5e5);
-      Teq = Tv + bt * (R)hj_dT * clon * cl;
+      Teq = Tv + bt * (R)hj_dT * clcl;
     }
     R fr = R(1) / (R(1) + Kv * rdt);
     X.mx[i] *= fr;
@@ -525,12 +520,15 @@ void Impl<R>::launch_2d(int nplanes, int kchunk, dim3& grid) const {
   grid = dim3((G.ncol + kBlock - 1) / kBlock, (nplanes + kchunk - 1) / kchunk);
 }
 
-size_t col_smem_bytes(int nv) { return (size_t)6 * nv * kColTile * sizeof(double); }
+template <typename R>
+size_t col_smem_bytes(int nv) {
+  return (size_t)nv * kColTile * (2 * sizeof(double) + 6 * sizeof(R));
+}
 
 template <typename R>
 int col_kernel_setup(int nv) {
   return cudaFuncSetAttribute(k_ss_col<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)col_smem_bytes(nv)) == cudaSuccess ? 0 : -3;
+                              (int)col_smem_bytes<R>(nv)) == cudaSuccess ? 0 : -3;
 }
 template int col_kernel_setup<double>(int);
 template int col_kernel_setup<float>(int);
@@ -543,7 +541,7 @@ int Impl<R>::large_step(double dt, int n_small) {
   launch_2d(G.nv + 1, kc, g2i);
   dim3 g1((G.ncol + kBlock - 1) / kBlock);
   dim3 gcol((G.ncol + kColTile - 1) / kColTile), bcol(kColTile, kColRows);
-  const size_t col_smem = col_smem_bytes(G.nv);
+  const size_t col_smem = col_smem_bytes<R>(G.nv);
   const R Kd = (R)(diff_D * dbar4 / dt);
   const double dts[3] = {dt / 3.0, dt / n_small, dt / n_small};
   const int nsub[3] = {1, n_small / 2, n_small};
@@ -583,7 +581,7 @@ int Impl<R>::large_step(double dt, int n_small) {
       k_ss_mom<R><<<g2, kBlock, 0, stream>>>(G, U, SL, P, T, (R)dts[s], Kd, divdamp, kc);
       mark(THOR_K_SS_MOM, false);
       mark(THOR_K_SS_COL, true);
-      k_ss_col<R><<<gcol, bcol, col_smem, stream>>>(G, V, U, ph, Xs, SL, P, T, dts[s]);
+      k_ss_col<R><<<gcol, bcol, col_smem, stream>>>(G, U, ph, Xs, SL, P, T, dts[s]);
       mark(THOR_K_SS_COL, false);
       launches += 2;
     }
