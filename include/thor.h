@@ -156,11 +156,14 @@ int thor_state_set(thor_state* state, int field, const double* host, size_t n);
 /* Kernel launches issued by this state so far. */
 int thor_launch_count(const thor_state* state, long long* count);
 
-/* Launch-shape knobs. THOR_TUNE_KCHUNK: levels each thread of the stencil
- * kernels walks (1..256, default 8); fewer levels mean more threads in
- * flight, more levels mean fewer reloads of the per-column weights. The
- * results do not depend on it. */
-enum { THOR_TUNE_KCHUNK = 0 };
+/* Launch-shape knobs; the results do not depend on them.
+ * THOR_TUNE_KCHUNK: levels each thread of the stencil kernels walks (1..256,
+ * default 2); fewer levels mean more threads in flight, more levels fewer
+ * reloads of the per-column weights.
+ * THOR_TUNE_GRAPH: 1 (default) replays a captured CUDA graph of one large
+ * step on a non-default stream (re-captured when dt, n_small or the chunk
+ * change; never while thor_profile records); 0 launches kernel by kernel. */
+enum { THOR_TUNE_KCHUNK = 0, THOR_TUNE_GRAPH = 1 };
 int thor_tune(thor_state* state, int knob, int value);
 
 /* Per-kernel timing. While enabled, every launch of the state is bracketed by

@@ -206,7 +206,7 @@ def thor_launch_count(state):
     return c.value
 
 
-THOR_TUNE_KCHUNK = 0
+THOR_TUNE_KCHUNK, THOR_TUNE_GRAPH = 0, 1
 
 
 def thor_tune(state, knob, value):

@@ -338,6 +338,7 @@ int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert
 
 template <typename R>
 Impl<R>::~Impl() {
+  drop_graph();
   if (arena) cudaFree(arena);
 }
 
@@ -667,6 +668,10 @@ int thor_tune(thor_state* s, int knob, int value) {
   if (knob == THOR_TUNE_KCHUNK) {
     if (value < 1 || value > 256) return THOR_EINVAL;
     s->impl->kchunk = value;
+    return THOR_OK;
+  }
+  if (knob == THOR_TUNE_GRAPH) {
+    s->impl->set_graph(value != 0);
     return THOR_OK;
   }
   return THOR_EINVAL;

@@ -41,8 +41,9 @@ struct ImplBase {
   virtual int diag(double* out8, long long* nonfinite) = 0;
   virtual int get(int field, double* host, size_t n) = 0;
   virtual int set(int field, const double* host, size_t n) = 0;
+  virtual void set_graph(bool on) = 0;
   long long launches = 0;
-  int kchunk = 8;                      // levels per thread in the stencil kernels
+  int kchunk = 2;                      // levels per thread in the stencil kernels
   // per-kernel event timing (off unless enabled)
   cudaStream_t stream = nullptr;
   bool prof_on = false;
@@ -109,10 +110,56 @@ struct Impl : ImplBase {
   double* red = nullptr;           // reduction partials
   int red_blocks = 0;
 
+  int use_graph = 1;
+  void set_graph(bool on) override {
+    use_graph = on;
+    if (!on) drop_graph();
+  }
   ~Impl() override;
   void launch_2d(int nplanes, int kchunk, dim3& grid) const;
   int large_step(double dt, int n_small);
+  // CUDA graph of one large step, replayed while (dt, n_small, kchunk) stay
+  // the same; used on a non-default stream when no profiling is recorded
+  cudaGraphExec_t graph_exec = nullptr;
+  double graph_dt = 0;
+  int graph_n = 0, graph_kc = 0;
+  long long graph_launches = 0;
+  void drop_graph() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    graph_exec = nullptr;
+  }
   int step(int n_large, int n_small, double dt) override {
+    if (use_graph && stream != nullptr && !prof_on && n_large > 0) {
+      if (!graph_exec || graph_dt != dt || graph_n != n_small || graph_kc != kchunk) {
+        drop_graph();
+        cudaGraph_t g = nullptr;
+        long long before = launches;
+        if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal)) return -3;
+        int rc = large_step(dt, n_small);
+        cudaError_t e = cudaStreamEndCapture(stream, &g);
+        if (rc || e) {
+          if (g) cudaGraphDestroy(g);
+          launches = before;
+          return -3;
+        }
+        e = cudaGraphInstantiate(&graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        graph_launches = launches - before;
+        launches = before;
+        if (e) {
+          graph_exec = nullptr;
+          return -3;
+        }
+        graph_dt = dt;
+        graph_n = n_small;
+        graph_kc = kchunk;
+      }
+      for (int i = 0; i < n_large; ++i) {
+        if (cudaGraphLaunch(graph_exec, stream)) return -3;
+        launches += graph_launches;
+      }
+      return 0;
+    }
     for (int i = 0; i < n_large; ++i) {
       int rc = large_step(dt, n_small);
       if (rc) return rc;

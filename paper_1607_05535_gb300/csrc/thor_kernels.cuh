@@ -122,6 +122,14 @@ __device__ __forceinline__ double rcp64(double x) {
   return fma(r, e, r);
 }
 
+// 1/x to about 2^-47: a float32 reciprocal (relative error <= 2^-24) refined
+// by one Newton-Raphson step; used for the pivots of the float64 elimination
+// in the mixed-precision path.
+__device__ __forceinline__ double rcp64_1(double x) {
+  double r = (double)__frcp_rn((float)x);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
 struct Nbr7 {
   int n[7];
 };

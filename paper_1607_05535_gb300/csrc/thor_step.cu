@@ -17,7 +17,7 @@
 namespace thor {
 
 constexpr int kColTile = 32;   // columns per block of the column kernel
-constexpr int kColRows = 8;    // threads per column in that kernel
+constexpr int kColRows = 4;    // threads per column in that kernel
 
 // ---------------------------------------------------------------- slow terms
 
@@ -319,7 +319,8 @@ __global__ void k_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R 
 //   up_m = -dtau^2/dzc_m Pi_m sq_hi_m th_m+1 - dtau^2 g w+ sq_hi_m
 //   rh_m = W*_m + dtau S_W,m - dtau/dzc_m (c_m - c_m-1) - dtau g (w- a_m-1 + w+ a_m)
 // The coefficients are assembled in the storage precision; the Thomas
-// elimination runs in float64. Then rho* and Th* follow from Eqs. dens2 and
+// elimination runs in float64 (the reciprocal of the pivot by an exact
+// division with float64 storage, else by rcp64_1). Then rho* and Th* follow from Eqs. dens2 and
 // pt2 and p* from the nonlinear Eq. theta_to_p.
 template <typename R>
 __global__ void __launch_bounds__(kColTile* kColRows) k_ss_col(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
@@ -331,14 +332,13 @@ __global__ void __launch_bounds__(kColTile* kColRows) k_ss_col(Geo<R> G, VR<R> U
   const int c = blockIdx.x * kColTile + tx;
   const bool valid = c < G.ncol;
   const int L = nv * kColTile;
-  double* scp = sm;                        // c'_m (float64)
-  double* sdp = scp + L;                   // d'_m, then W_m (float64)
-  R* sa = reinterpret_cast<R*>(sdp + L);   // a_k
+  double* slo = sm;                        // lo_m
+  double* sdi = slo + L;                   // di_m
+  double* sup = sdi + L;                   // up_m, then c'_m
+  double* srh = sup + L;                   // rh_m, then d'_m, then W_m
+  R* sa = reinterpret_cast<R*>(srh + L);   // a_k
   R* sb = sa + L;                          // b_k
-  R* sc = sb + L;                          // c_k, then lo_m
-  R* sdi = sc + L;                         // di_m
-  R* sup = sdi + L;                        // up_m
-  R* srh = sup + L;                        // rh_m
+  R* sc = sb + L;                          // c_k
   const R rdt = (R)dtau;
 
   // phase 1: horizontal fluxes of the new M* and the a, b, c of every cell
@@ -347,23 +347,28 @@ __global__ void __launch_bounds__(kColTile* kColRows) k_ss_col(Geo<R> G, VR<R> U
     W7x3<R> wd = load_w7x3(G.wdiv, S, c);
     for (int k = ty; k < nv; k += kColRows) {
       const int o = k * S, i = o + c;
-      R inv_r = U.inv_rc[k];
-      R dh = div7(wd, nb, P.mx + o, P.my + o, P.mz + o) * inv_r;
-      R dht = div7_scaled(wd, nb, T.theta + o, P.mx + o, P.my + o, P.mz + o) * inv_r;
+      R dh = 0, dht = 0;
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        const int q = o + nb.n[j];
+        R f = wd.x[j] * P.mx[q] + wd.y[j] * P.my[q] + wd.z[j] * P.mz[q];
+        dh += f;
+        dht += T.theta[q] * f;
+      }
+      const R inv_r = U.inv_rc[k];
       R thk = P.th[i];
-      R bk = thk + rdt * (SL.sth[i] - dht);
-      sa[k * kColTile + tx] = P.rho[i] + rdt * (SL.srho[i] - dh);
+      R bk = thk + rdt * (SL.sth[i] - dht * inv_r);
+      sa[k * kColTile + tx] = P.rho[i] + rdt * (SL.srho[i] - dh * inv_r);
       sb[k * kColTile + tx] = bk;
       sc[k * kColTile + tx] = P.p[i] + SL.pi[i] * (bk - thk);
     }
   }
   __syncthreads();
-  // phase 2: tridiagonal coefficients at the interior interfaces
-  const R g = (R)ph.g, dt2 = (R)(dtau * dtau);
-  R lo_v[(kMaxNv + kColRows - 1) / kColRows];
+  // phase 2: tridiagonal coefficients at the interior interfaces, assembled
+  // in the storage precision and stored in float64 for the elimination
   if (valid) {
-    int slot = 0;
-    for (int m = 1 + ty; m < nv; m += kColRows, ++slot) {
+    const R g = (R)ph.g, dt2 = (R)(dtau * dtau);
+    for (int m = 1 + ty; m < nv; m += kColRows) {
       const int i = m * S + c, j = m * kColTile + tx;
       const R th_m = SL.thi[i];
       const R pi_lo = SL.pi[i - S], pi_hi = SL.pi[i];
@@ -373,38 +378,34 @@ __global__ void __launch_bounds__(kColTile* kColRows) k_ss_col(Geo<R> G, VR<R> U
       R lower = 0, upper = 0;
       if (m > 1) lower = (-dtz * pi_lo * SL.thi[i - S] + dt2 * g * wlo) * ql;
       if (m < nv - 1) upper = (-dtz * pi_hi * SL.thi[i + S] - dt2 * g * whi) * ph_;
-      sdi[j] = R(1) + dtz * th_m * (pi_hi * pl + pi_lo * qh) - dt2 * g * (wlo * qh - whi * pl);
-      sup[j] = upper;
-      srh[j] = P.w[i] + rdt * SL.sw[i] - rdt * U.inv_dzc[m] * (sc[j] - sc[j - kColTile])
-             - rdt * g * (wlo * sa[j - kColTile] + whi * sa[j]);
-      lo_v[slot] = lower;
+      slo[j] = (double)lower;
+      sdi[j] = (double)(R(1) + dtz * th_m * (pi_hi * pl + pi_lo * qh) - dt2 * g * (wlo * qh - whi * pl));
+      sup[j] = (double)upper;
+      srh[j] = (double)(P.w[i] + rdt * SL.sw[i] - rdt * U.inv_dzc[m] * (sc[j] - sc[j - kColTile])
+                        - rdt * g * (wlo * sa[j - kColTile] + whi * sa[j]));
     }
   }
   __syncthreads();
-  if (valid) {   // c_k is no longer needed: the same array now holds lo_m
-    int slot = 0;
-    for (int m = 1 + ty; m < nv; m += kColRows, ++slot) sc[m * kColTile + tx] = lo_v[slot];
-  }
-  __syncthreads();
-  // phase 3: Thomas sweep in float64, one lane per column
+  // phase 3: Thomas elimination in float64, one lane per column
   if (ty == 0 && valid) {
     double cprev = 0.0, dprev = 0.0;
     for (int m = 1; m < nv; ++m) {
       const int j = m * kColTile + tx;
-      const double lo = (double)sc[j];
-      const double inv = rcp64((double)sdi[j] - lo * cprev);
-      cprev = (double)sup[j] * inv;
-      dprev = ((double)srh[j] - lo * dprev) * inv;
-      scp[j] = cprev;
-      sdp[j] = dprev;
+      const double lo = slo[j];
+      const double den = sdi[j] - lo * cprev;
+      const double inv = sizeof(R) == sizeof(double) ? 1.0 / den : rcp64_1(den);
+      cprev = sup[j] * inv;
+      dprev = (srh[j] - lo * dprev) * inv;
+      sup[j] = cprev;
+      srh[j] = dprev;
     }
     double wnext = 0.0;
     for (int m = nv - 1; m >= 1; --m) {
       const int j = m * kColTile + tx;
-      wnext = sdp[j] - scp[j] * wnext;
-      sdp[j] = wnext;
+      wnext = srh[j] - sup[j] * wnext;
+      srh[j] = wnext;
     }
-    sdp[tx] = 0.0;   // bottom interface (m = 0); the top one (m = nv) is implicit
+    srh[tx] = 0.0;   // bottom interface (m = 0); the top one (m = nv) is implicit
   }
   __syncthreads();
   // phase 4: Eqs. dens2, pt2, theta_to_p with the new W*
@@ -412,8 +413,8 @@ __global__ void __launch_bounds__(kColTile* kColRows) k_ss_col(Geo<R> G, VR<R> U
     const R gamma = (R)ph.gamma;
     for (int k = ty; k < nv; k += kColRows) {
       const int i = k * S + c, j = k * kColTile + tx;
-      const R wl = (R)sdp[j];
-      const R wh = k + 1 < nv ? (R)sdp[j + kColTile] : R(0);
+      const R wl = (R)srh[j];
+      const R wh = k + 1 < nv ? (R)srh[j + kColTile] : R(0);
       const R thl = k > 0 ? SL.thi[i] : R(0);
       const R thh = k + 1 < nv ? SL.thi[i + S] : R(0);
       const R el = U.sq_lo[k], eh = U.sq_hi[k];
@@ -522,7 +523,7 @@ void Impl<R>::launch_2d(int nplanes, int kchunk, dim3& grid) const {
 
 template <typename R>
 size_t col_smem_bytes(int nv) {
-  return (size_t)nv * kColTile * (2 * sizeof(double) + 6 * sizeof(R));
+  return (size_t)nv * kColTile * (4 * sizeof(double) + 3 * sizeof(R));
 }
 
 template <typename R>

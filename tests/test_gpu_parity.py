@@ -125,3 +125,36 @@ def test_odd_substeps_rejected_without_state_change():
         assert np.array_equal(before.rho, after.rho) and np.array_equal(before.Th, after.Th)
     finally:
         p.close()
+
+
+def test_graph_replay_matches_direct_launches():
+    """The captured CUDA graph of a large step gives the same bits as the
+    kernel-by-kernel launches."""
+    wl = SMALL.with_(forcing="held_suarez")
+    s = torch.cuda.Stream()
+    out = []
+    for graph in (1, 0):
+        p = Pair(wl, stream=s.cuda_stream)
+        try:
+            thor.thor_tune(p.state, thor.THOR_TUNE_GRAPH, graph)
+            thor.thor_step(p.state, 2, wl.n_small, wl.dt)
+            thor.thor_step(p.state, 1, wl.n_small, wl.dt)
+            out.append(p.get())
+        finally:
+            p.close()
+    for f in ("rho", "M", "W", "Th"):
+        assert np.array_equal(getattr(out[0], f), getattr(out[1], f)), f
+
+
+@pytest.mark.parametrize("kchunk", [1, 3, 32])
+def test_level_chunk_does_not_change_results(kchunk):
+    wl = SMALL.with_(forcing="held_suarez")
+    p = Pair(wl)
+    try:
+        thor.thor_tune(p.state, thor.THOR_TUNE_KCHUNK, kchunk)
+        X = p.oracle_initial()
+        ref = dc.large_step(p.model, X, wl.dt, wl.n_small)
+        thor.thor_step(p.state, 1, wl.n_small, wl.dt)
+        _assert_close(p.get(), ref)
+    finally:
+        p.close()
