@@ -386,26 +386,74 @@ __global__ void __launch_bounds__(kColTile* kColRows) k_ss_col(Geo<R> G, VR<R> U
     }
   }
   __syncthreads();
-  // phase 3: Thomas elimination in float64, one lane per column
-  if (ty == 0 && valid) {
-    double cprev = 0.0, dprev = 0.0;
-    for (int m = 1; m < nv; ++m) {
-      const int j = m * kColTile + tx;
-      const double lo = slo[j];
-      const double den = sdi[j] - lo * cprev;
-      const double inv = sizeof(R) == sizeof(double) ? 1.0 / den : rcp64_1(den);
-      cprev = sup[j] * inv;
-      dprev = (srh[j] - lo * dprev) * inv;
-      sup[j] = cprev;
-      srh[j] = dprev;
+  // phase 3: two-sided Thomas elimination in float64. Warp 0 eliminates
+  // rows 1..p downwards (c', d'), warp 1 rows nv-1..p+1 upwards (e', f');
+  // both meet at the rows p, p+1 and substitute back outwards. The two
+  // sweeps run on different SM sub-partitions, halving the serial chain.
+  const int N = nv - 1, p = N / 2 > 0 ? N / 2 : 1;
+  if (ty < 2 && valid) {
+    const bool down = ty == 0;
+    double c1 = 0.0, d1 = 0.0;
+    if (down) {
+      for (int m = 1; m <= p; ++m) {
+        const int j = m * kColTile + tx;
+        const double lo = slo[j];
+        const double den = sdi[j] - lo * c1;
+        const double inv = sizeof(R) == sizeof(double) ? 1.0 / den : rcp64_1(den);
+        c1 = sup[j] * inv;
+        d1 = (srh[j] - lo * d1) * inv;
+        sup[j] = c1;
+        srh[j] = d1;
+      }
+    } else {
+      for (int m = N; m > p; --m) {
+        const int j = m * kColTile + tx;
+        const double up = sup[j];
+        const double den = sdi[j] - up * c1;
+        const double inv = sizeof(R) == sizeof(double) ? 1.0 / den : rcp64_1(den);
+        c1 = slo[j] * inv;
+        d1 = (srh[j] - up * d1) * inv;
+        slo[j] = c1;
+        srh[j] = d1;
+      }
     }
-    double wnext = 0.0;
-    for (int m = nv - 1; m >= 1; --m) {
-      const int j = m * kColTile + tx;
-      wnext = srh[j] - sup[j] * wnext;
-      srh[j] = wnext;
+  }
+  __syncthreads();
+  // rows p and p+1: x_p = d'_p - c'_p x_p+1 and x_p+1 = f'_p+1 - e'_p+1 x_p;
+  // every lane of the two sweeping warps reads them before anyone writes
+  double xp = 0.0, xq = 0.0;
+  if (ty < 2 && valid) {
+    const int jp = p * kColTile + tx;
+    if (p < N) {
+      const int jq = jp + kColTile;
+      const double cp_ = sup[jp], dp_ = srh[jp], eq = slo[jq], fq = srh[jq];
+      xp = (dp_ - cp_ * fq) / (1.0 - cp_ * eq);
+      xq = fq - eq * xp;
+    } else {
+      xp = srh[jp];
     }
-    srh[tx] = 0.0;   // bottom interface (m = 0); the top one (m = nv) is implicit
+  }
+  __syncthreads();
+  if (ty < 2 && valid) {
+    const int jp = p * kColTile + tx;
+    if (ty == 0) {
+      double x = xp;
+      srh[jp] = xp;
+      for (int m = p - 1; m >= 1; --m) {
+        const int j = m * kColTile + tx;
+        x = srh[j] - sup[j] * x;
+        srh[j] = x;
+      }
+      srh[tx] = 0.0;   // bottom interface (m = 0); the top one (m = nv) is implicit
+    } else if (p < N) {
+      double x = xq;
+      srh[jp + kColTile] = xq;
+      for (int m = p + 2; m <= N; ++m) {
+        const int j = m * kColTile + tx;
+        x = srh[j] - slo[j] * x;
+        srh[j] = x;
+      }
+    }
   }
   __syncthreads();
   // phase 4: Eqs. dens2, pt2, theta_to_p with the new W*
