@@ -31,7 +31,7 @@ EXPORTED = [
 
 # kernel ids of thor_profile_read
 KERNELS = ["derived", "lap1", "slow", "slow_w", "stage_init", "ss_div", "ss_grad", "ss_mom",
-           "ss_col", "stage_end", "physics"]
+           "ss_solve", "stage_end", "physics", "ss_flux"]
 
 
 class thor_spring(ctypes.Structure):

@@ -19,6 +19,7 @@ struct Work {
   R *qvr;                          // interfaces
   R *dd;                           // 3-D divergence (small step)
   R *gx, *gy, *gz;                 // its horizontal gradient
+  R *ca, *cb, *cc;                 // per-cell parts of the column equations (a, b, c)
 };
 
 // Slow tendencies and small-step coefficients of a stage

@@ -6,18 +6,14 @@
 // the chunk. A warp covers 32 consecutive columns of one level, so every
 // field access is a coalesced (or neighbour-shifted) row of one plane.
 //
-// The vertical solve (k_ss_col) runs 32 columns per block with 8 threads per
-// column: the level-parallel phases (horizontal fluxes, the tridiagonal
-// coefficients, the updates) use all 256 threads; the sequential Thomas sweep
-// over the interfaces uses one warp, one lane per column, in float64, on
-// coefficients kept in shared memory.
+// The vertical solve is split: k_ss_flux (a stencil kernel like the others)
+// forms the per-cell parts of the column equations, and k_ss_solve runs the
+// float64 tridiagonal elimination with two warps per 32 columns.
 #include "../../include/thor.h"
 #include "thor_impl.cuh"
 
 namespace thor {
 
-constexpr int kColTile = 32;   // columns per block of the column kernel
-constexpr int kColRows = 4;    // threads per column in that kernel
 
 // ---------------------------------------------------------------- slow terms
 
@@ -304,170 +300,160 @@ __global__ void k_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R 
   }
 }
 
-// HE-VI column step. Eqs. dens2 and pt2 substituted into Eq. momr2 give, at
-// the interior interfaces m = 1..nv-1 (rigid lid: W* = 0 at m = 0 and nv),
-//   lo_m W_m-1 + di_m W_m + up_m W_m+1 = rh_m
-// with e_k = r_k^2/(rc_k^2 dz_k) at the bottom (sq_lo) and top (sq_hi)
-// interfaces of cell k, th_m = theta at interface m and w-/w+ the Lagrange
-// weights of centres m-1, m at interface m:
+// HE-VI column step, part 1: horizontal fluxes of the new M* and, for every
+// cell, the parts of Eqs. dens2 and pt2 that do not involve W*:
 //   a_k = rho*_k + dtau (S_rho,k - div_h M*_k)
 //   b_k = Th*_k + dtau (S_th,k - div_h(theta M*)_k)
-//   c_k = p*_k + Pi_k (b_k - Th*_k)
+//   c_k = p*_k + Pi_k (b_k - Th*_k)        (p* advanced linearly in Th)
+template <typename R>
+__global__ void k_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, int kchunk) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= G.ncol) return;
+  const int S = G.colp;
+  Nbr7 nb = load_nbr(G, c);
+  W7x3<R> wd = load_w7x3(G.wdiv, S, c);
+  int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
+  for (int k = k0; k < k1; ++k) {
+    const int o = k * S, i = o + c;
+    R dh = 0, dht = 0;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const int q = o + nb.n[j];
+      R f = wd.x[j] * P.mx[q] + wd.y[j] * P.my[q] + wd.z[j] * P.mz[q];
+      dh += f;
+      dht += T.theta[q] * f;
+    }
+    const R inv_r = U.inv_rc[k];
+    R thk = P.th[i];
+    R bk = thk + dtau * (SL.sth[i] - dht * inv_r);
+    T.ca[i] = P.rho[i] + dtau * (SL.srho[i] - dh * inv_r);
+    T.cb[i] = bk;
+    T.cc[i] = P.p[i] + SL.pi[i] * (bk - thk);
+  }
+}
+
+// HE-VI column step, part 2. Substituting Eqs. dens2 and pt2 into Eq. momr2
+// gives at the interior interfaces m = 1..nv-1 (rigid lid: W* = 0 at m = 0
+// and nv)
+//   lo_m W_m-1 + di_m W_m + up_m W_m+1 = rh_m
+// with e_k = r^2/(rc_k^2 dz_k) at the bottom (sq_lo) and top (sq_hi)
+// interfaces of cell k, th_m = theta at interface m, w-/w+ the Lagrange
+// weights of centres m-1, m at interface m:
 //   lo_m = -dtau^2/dzc_m Pi_m-1 sq_lo_m-1 th_m-1 + dtau^2 g w- sq_lo_m-1
 //   di_m = 1 + dtau^2/dzc_m th_m (Pi_m sq_lo_m + Pi_m-1 sq_hi_m-1)
 //            - dtau^2 g (w- sq_hi_m-1 - w+ sq_lo_m)
 //   up_m = -dtau^2/dzc_m Pi_m sq_hi_m th_m+1 - dtau^2 g w+ sq_hi_m
 //   rh_m = W*_m + dtau S_W,m - dtau/dzc_m (c_m - c_m-1) - dtau g (w- a_m-1 + w+ a_m)
-// The coefficients are assembled in the storage precision; the Thomas
-// elimination runs in float64 (the reciprocal of the pivot by an exact
-// division with float64 storage, else by rcp64_1). Then rho* and Th* follow from Eqs. dens2 and
-// pt2 and p* from the nonlinear Eq. theta_to_p.
+// The coefficients are formed in the storage precision; the elimination is
+// a two-sided Thomas algorithm in float64: warp 0 eliminates rows 1..p
+// downwards, warp 1 rows nv-1..p+1 upwards (the two warps run on different
+// SM sub-partitions), they meet at rows p, p+1 and substitute back outwards.
+// Then rho* and Th* follow from Eqs. dens2 and pt2 and p* from the nonlinear
+// Eq. theta_to_p. One block = 32 columns x 2 warps.
 template <typename R>
-__global__ void __launch_bounds__(kColTile* kColRows) k_ss_col(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
-                                                               Slow<R> SL, Pert<R> P, Work<R> T,
-                                                               double dtau) {
+__global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs, Slow<R> SL,
+                                                 Pert<R> P, Work<R> T, double dtau) {
   extern __shared__ double sm[];
-  const int nv = G.nv, S = G.colp;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int c = blockIdx.x * kColTile + tx;
+  const int nv = G.nv, S = G.colp, N = nv - 1;
+  const int tx = threadIdx.x & 31, half = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + tx;
   const bool valid = c < G.ncol;
-  const int L = nv * kColTile;
-  double* slo = sm;                        // lo_m
-  double* sdi = slo + L;                   // di_m
-  double* sup = sdi + L;                   // up_m, then c'_m
-  double* srh = sup + L;                   // rh_m, then d'_m, then W_m
-  R* sa = reinterpret_cast<R*>(srh + L);   // a_k
-  R* sb = sa + L;                          // b_k
-  R* sc = sb + L;                          // c_k
-  const R rdt = (R)dtau;
+  const int cs = valid ? c : 0;          // padding lanes read column 0 and store nothing
+  double* scp = sm;                      // [nv + 1][32] c' (rows <= p) and e' (rows > p)
+  double* sdp = scp + (nv + 1) * 32;     // [nv + 1][32] d' / f', then W
+  double* sx = sdp + (nv + 1) * 32;      // [2][32] junction values
+  const int p = N / 2 > 0 ? N / 2 : 1;
+  const R rdt = (R)dtau, g = (R)ph.g, dt2 = (R)(dtau * dtau);
 
-  // phase 1: horizontal fluxes of the new M* and the a, b, c of every cell
-  if (valid) {
-    Nbr7 nb = load_nbr(G, c);
-    W7x3<R> wd = load_w7x3(G.wdiv, S, c);
-    for (int k = ty; k < nv; k += kColRows) {
-      const int o = k * S, i = o + c;
-      R dh = 0, dht = 0;
-#pragma unroll
-      for (int j = 0; j < 7; ++j) {
-        const int q = o + nb.n[j];
-        R f = wd.x[j] * P.mx[q] + wd.y[j] * P.my[q] + wd.z[j] * P.mz[q];
-        dh += f;
-        dht += T.theta[q] * f;
-      }
-      const R inv_r = U.inv_rc[k];
-      R thk = P.th[i];
-      R bk = thk + rdt * (SL.sth[i] - dht * inv_r);
-      sa[k * kColTile + tx] = P.rho[i] + rdt * (SL.srho[i] - dh * inv_r);
-      sb[k * kColTile + tx] = bk;
-      sc[k * kColTile + tx] = P.p[i] + SL.pi[i] * (bk - thk);
-    }
-  }
-  __syncthreads();
-  // phase 2: tridiagonal coefficients at the interior interfaces, assembled
-  // in the storage precision and stored in float64 for the elimination
-  if (valid) {
-    const R g = (R)ph.g, dt2 = (R)(dtau * dtau);
-    for (int m = 1 + ty; m < nv; m += kColRows) {
-      const int i = m * S + c, j = m * kColTile + tx;
-      const R th_m = SL.thi[i];
-      const R pi_lo = SL.pi[i - S], pi_hi = SL.pi[i];
-      const R wlo = U.wlo[m], whi = U.whi[m], dtz = dt2 * U.inv_dzc[m];
-      const R ql = U.sq_lo[m - 1], qh = U.sq_hi[m - 1];    // cell m-1
-      const R pl = U.sq_lo[m], ph_ = U.sq_hi[m];           // cell m
-      R lower = 0, upper = 0;
-      if (m > 1) lower = (-dtz * pi_lo * SL.thi[i - S] + dt2 * g * wlo) * ql;
-      if (m < nv - 1) upper = (-dtz * pi_hi * SL.thi[i + S] - dt2 * g * whi) * ph_;
-      slo[j] = (double)lower;
-      sdi[j] = (double)(R(1) + dtz * th_m * (pi_hi * pl + pi_lo * qh) - dt2 * g * (wlo * qh - whi * pl));
-      sup[j] = (double)upper;
-      srh[j] = (double)(P.w[i] + rdt * SL.sw[i] - rdt * U.inv_dzc[m] * (sc[j] - sc[j - kColTile])
-                        - rdt * g * (wlo * sa[j - kColTile] + whi * sa[j]));
-    }
-  }
-  __syncthreads();
-  // phase 3: two-sided Thomas elimination in float64. Warp 0 eliminates
-  // rows 1..p downwards (c', d'), warp 1 rows nv-1..p+1 upwards (e', f');
-  // both meet at the rows p, p+1 and substitute back outwards. The two
-  // sweeps run on different SM sub-partitions, halving the serial chain.
-  const int N = nv - 1, p = N / 2 > 0 ? N / 2 : 1;
-  if (ty < 2 && valid) {
-    const bool down = ty == 0;
+  // coefficients of interface m (1 <= m <= N)
+  auto coef = [&](int m, double& lo, double& di, double& up, double& rh) {
+    const int i = m * S + cs;
+    const R pi_lo = SL.pi[i - S], pi_hi = SL.pi[i];
+    const R wlo = U.wlo[m], whi = U.whi[m], dtz = dt2 * U.inv_dzc[m];
+    const R ql = U.sq_lo[m - 1], qh = U.sq_hi[m - 1];    // cell m-1
+    const R pl = U.sq_lo[m], ph_ = U.sq_hi[m];           // cell m
+    const R th_m = SL.thi[i];
+    R lower = 0, upper = 0;
+    if (m > 1) lower = (-dtz * pi_lo * SL.thi[i - S] + dt2 * g * wlo) * ql;
+    if (m < N) upper = (-dtz * pi_hi * SL.thi[i + S] - dt2 * g * whi) * ph_;
+    lo = (double)lower;
+    up = (double)upper;
+    di = (double)(R(1) + dtz * th_m * (pi_hi * pl + pi_lo * qh) - dt2 * g * (wlo * qh - whi * pl));
+    rh = (double)(P.w[i] + rdt * SL.sw[i] - rdt * U.inv_dzc[m] * (T.cc[i] - T.cc[i - S])
+                  - rdt * g * (wlo * T.ca[i - S] + whi * T.ca[i]));
+  };
+  auto inv_of = [](double den) { return sizeof(R) == sizeof(double) ? 1.0 / den : rcp64_1(den); };
+
+  // elimination
+  if (half == 0) {
     double c1 = 0.0, d1 = 0.0;
-    if (down) {
-      for (int m = 1; m <= p; ++m) {
-        const int j = m * kColTile + tx;
-        const double lo = slo[j];
-        const double den = sdi[j] - lo * c1;
-        const double inv = sizeof(R) == sizeof(double) ? 1.0 / den : rcp64_1(den);
-        c1 = sup[j] * inv;
-        d1 = (srh[j] - lo * d1) * inv;
-        sup[j] = c1;
-        srh[j] = d1;
-      }
-    } else {
-      for (int m = N; m > p; --m) {
-        const int j = m * kColTile + tx;
-        const double up = sup[j];
-        const double den = sdi[j] - up * c1;
-        const double inv = sizeof(R) == sizeof(double) ? 1.0 / den : rcp64_1(den);
-        c1 = slo[j] * inv;
-        d1 = (srh[j] - up * d1) * inv;
-        slo[j] = c1;
-        srh[j] = d1;
-      }
+    for (int m = 1; m <= p; ++m) {
+      double lo, di, up, rh;
+      coef(m, lo, di, up, rh);
+      const double inv = inv_of(di - lo * c1);
+      c1 = up * inv;
+      d1 = (rh - lo * d1) * inv;
+      scp[m * 32 + tx] = c1;
+      sdp[m * 32 + tx] = d1;
+    }
+  } else {
+    double e1 = 0.0, f1 = 0.0;
+    for (int m = N; m > p; --m) {
+      double lo, di, up, rh;
+      coef(m, lo, di, up, rh);
+      const double inv = inv_of(di - up * e1);
+      e1 = lo * inv;
+      f1 = (rh - up * f1) * inv;
+      scp[m * 32 + tx] = e1;
+      sdp[m * 32 + tx] = f1;
     }
   }
   __syncthreads();
-  // rows p and p+1: x_p = d'_p - c'_p x_p+1 and x_p+1 = f'_p+1 - e'_p+1 x_p;
-  // every lane of the two sweeping warps reads them before anyone writes
-  double xp = 0.0, xq = 0.0;
-  if (ty < 2 && valid) {
-    const int jp = p * kColTile + tx;
+  // junction rows p and p+1: x_p = d'_p - c'_p x_p+1, x_p+1 = f'_p+1 - e'_p+1 x_p
+  if (half == 0) {
+    double xp, xq = 0.0;
     if (p < N) {
-      const int jq = jp + kColTile;
-      const double cp_ = sup[jp], dp_ = srh[jp], eq = slo[jq], fq = srh[jq];
+      const double cp_ = scp[p * 32 + tx], dp_ = sdp[p * 32 + tx];
+      const double eq = scp[(p + 1) * 32 + tx], fq = sdp[(p + 1) * 32 + tx];
       xp = (dp_ - cp_ * fq) / (1.0 - cp_ * eq);
       xq = fq - eq * xp;
     } else {
-      xp = srh[jp];
+      xp = sdp[p * 32 + tx];
     }
+    sx[tx] = xp;
+    sx[32 + tx] = xq;
   }
   __syncthreads();
-  if (ty < 2 && valid) {
-    const int jp = p * kColTile + tx;
-    if (ty == 0) {
-      double x = xp;
-      srh[jp] = xp;
-      for (int m = p - 1; m >= 1; --m) {
-        const int j = m * kColTile + tx;
-        x = srh[j] - sup[j] * x;
-        srh[j] = x;
-      }
-      srh[tx] = 0.0;   // bottom interface (m = 0); the top one (m = nv) is implicit
-    } else if (p < N) {
-      double x = xq;
-      srh[jp + kColTile] = xq;
-      for (int m = p + 2; m <= N; ++m) {
-        const int j = m * kColTile + tx;
-        x = srh[j] - slo[j] * x;
-        srh[j] = x;
-      }
+  // back substitution, each warp over its own rows
+  if (half == 0) {
+    double x = sx[tx];
+    sdp[p * 32 + tx] = x;
+    for (int m = p - 1; m >= 1; --m) {
+      x = sdp[m * 32 + tx] - scp[m * 32 + tx] * x;
+      sdp[m * 32 + tx] = x;
     }
+    sdp[tx] = 0.0;                 // bottom interface
+  } else {
+    double x = sx[32 + tx];
+    if (p < N) sdp[(p + 1) * 32 + tx] = x;
+    for (int m = p + 2; m <= N; ++m) {
+      x = sdp[m * 32 + tx] - scp[m * 32 + tx] * x;
+      sdp[m * 32 + tx] = x;
+    }
+    sdp[nv * 32 + tx] = 0.0;       // top interface
   }
   __syncthreads();
-  // phase 4: Eqs. dens2, pt2, theta_to_p with the new W*
+  // Eqs. dens2, pt2, theta_to_p with the new W*; the two warps share the levels
   if (valid) {
     const R gamma = (R)ph.gamma;
-    for (int k = ty; k < nv; k += kColRows) {
-      const int i = k * S + c, j = k * kColTile + tx;
-      const R wl = (R)srh[j];
-      const R wh = k + 1 < nv ? (R)srh[j + kColTile] : R(0);
+    for (int k = half; k < nv; k += 2) {
+      const int i = k * S + c;
+      const R wl = (R)sdp[k * 32 + tx], wh = (R)sdp[(k + 1) * 32 + tx];
       const R thl = k > 0 ? SL.thi[i] : R(0);
       const R thh = k + 1 < nv ? SL.thi[i + S] : R(0);
       const R el = U.sq_lo[k], eh = U.sq_hi[k];
-      R th_new = sb[j] - rdt * (eh * thh * wh - el * thl * wl);
-      P.rho[i] = sa[j] - rdt * (eh * wh - el * wl);
+      R th_new = T.cb[i] - rdt * (eh * thh * wh - el * thl * wl);
+      P.rho[i] = T.ca[i] - rdt * (eh * wh - el * wl);
       P.th[i] = th_new;
       // p* = EOS(Th^(s) + Th*) - p^(s) = p^(s) ((1 + Th*/Th^(s))^gamma - 1)
       R ps = U.pb[k] + T.pp[i];
@@ -569,15 +555,12 @@ void Impl<R>::launch_2d(int nplanes, int kchunk, dim3& grid) const {
   grid = dim3((G.ncol + kBlock - 1) / kBlock, (nplanes + kchunk - 1) / kchunk);
 }
 
-template <typename R>
-size_t col_smem_bytes(int nv) {
-  return (size_t)nv * kColTile * (4 * sizeof(double) + 3 * sizeof(R));
-}
+size_t solve_smem_bytes(int nv) { return (size_t)(2 * (nv + 1) + 2) * 32 * sizeof(double); }
 
 template <typename R>
 int col_kernel_setup(int nv) {
-  return cudaFuncSetAttribute(k_ss_col<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)col_smem_bytes<R>(nv)) == cudaSuccess ? 0 : -3;
+  return cudaFuncSetAttribute(k_ss_solve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)solve_smem_bytes(nv)) == cudaSuccess ? 0 : -3;
 }
 template int col_kernel_setup<double>(int);
 template int col_kernel_setup<float>(int);
@@ -589,8 +572,8 @@ int Impl<R>::large_step(double dt, int n_small) {
   launch_2d(G.nv, kc, g2);
   launch_2d(G.nv + 1, kc, g2i);
   dim3 g1((G.ncol + kBlock - 1) / kBlock);
-  dim3 gcol((G.ncol + kColTile - 1) / kColTile), bcol(kColTile, kColRows);
-  const size_t col_smem = col_smem_bytes<R>(G.nv);
+  dim3 gsolve((G.ncol + 31) / 32);
+  const size_t solve_smem = solve_smem_bytes(G.nv);
   const R Kd = (R)(diff_D * dbar4 / dt);
   const double dts[3] = {dt / 3.0, dt / n_small, dt / n_small};
   const int nsub[3] = {1, n_small / 2, n_small};
@@ -629,10 +612,13 @@ int Impl<R>::large_step(double dt, int n_small) {
       mark(THOR_K_SS_MOM, true);
       k_ss_mom<R><<<g2, kBlock, 0, stream>>>(G, U, SL, P, T, (R)dts[s], Kd, divdamp, kc);
       mark(THOR_K_SS_MOM, false);
+      mark(THOR_K_SS_FLUX, true);
+      k_ss_flux<R><<<g2, kBlock, 0, stream>>>(G, U, SL, P, T, (R)dts[s], kc);
+      mark(THOR_K_SS_FLUX, false);
       mark(THOR_K_SS_COL, true);
-      k_ss_col<R><<<gcol, bcol, col_smem, stream>>>(G, U, ph, Xs, SL, P, T, dts[s]);
+      k_ss_solve<R><<<gsolve, 64, solve_smem, stream>>>(G, U, ph, Xs, SL, P, T, dts[s]);
       mark(THOR_K_SS_COL, false);
-      launches += 2;
+      launches += 3;
     }
     Xf<R> Xo = s == 2 ? Xt : Xst;
     mark(THOR_K_STAGE_END, true);
