@@ -130,6 +130,12 @@ __device__ __forceinline__ double rcp64_1(double x) {
   return fma(r, fma(-x, r, 1.0), r);
 }
 
+// read-only load through the non-coherent path: the fields a kernel reads
+// are never written by another thread of the same kernel, so the compiler may
+// issue these loads early and keep many in flight
+template <typename T>
+__device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+
 struct Nbr7 {
   int n[7];
 };
@@ -139,7 +145,7 @@ __device__ __forceinline__ Nbr7 load_nbr(const Geo<R>& G, int c) {
   Nbr7 s;
   s.n[0] = c;
 #pragma unroll
-  for (int j = 0; j < 6; ++j) s.n[j + 1] = G.nbr[j * G.colp + c];
+  for (int j = 0; j < 6; ++j) s.n[j + 1] = ld(G.nbr + j * G.colp + c);
   return s;
 }
 
@@ -156,7 +162,7 @@ template <typename R>
 __device__ __forceinline__ W7<R> load_w7(const R* w, int colp, int c) {
   W7<R> o;
 #pragma unroll
-  for (int j = 0; j < 7; ++j) o.v[j] = w[j * colp + c];
+  for (int j = 0; j < 7; ++j) o.v[j] = ld(w + j * colp + c);
   return o;
 }
 template <typename R>
@@ -164,9 +170,9 @@ __device__ __forceinline__ W7x3<R> load_w7x3(const R* w, int colp, int c) {
   W7x3<R> o;
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
-    o.x[j] = w[(3 * j) * colp + c];
-    o.y[j] = w[(3 * j + 1) * colp + c];
-    o.z[j] = w[(3 * j + 2) * colp + c];
+    o.x[j] = ld(w + (3 * j) * colp + c);
+    o.y[j] = ld(w + (3 * j + 1) * colp + c);
+    o.z[j] = ld(w + (3 * j + 2) * colp + c);
   }
   return o;
 }
@@ -176,7 +182,7 @@ template <typename R>
 __device__ __forceinline__ R apply7(const W7<R>& w, const Nbr7& nb, const R* plane) {
   R s = 0;
 #pragma unroll
-  for (int j = 0; j < 7; ++j) s += w.v[j] * plane[nb.n[j]];
+  for (int j = 0; j < 7; ++j) s += w.v[j] * ld(plane + nb.n[j]);
   return s;
 }
 // sum_j w_j . F(n_j) with F given by three planes
@@ -186,7 +192,7 @@ __device__ __forceinline__ R div7(const W7x3<R>& w, const Nbr7& nb, const R* fx,
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
     int q = nb.n[j];
-    s += w.x[j] * fx[q] + w.y[j] * fy[q] + w.z[j] * fz[q];
+    s += w.x[j] * ld(fx + q) + w.y[j] * ld(fy + q) + w.z[j] * ld(fz + q);
   }
   return s;
 }
@@ -198,8 +204,8 @@ __device__ __forceinline__ R div7_scaled(const W7x3<R>& w, const Nbr7& nb, const
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
     int q = nb.n[j];
-    R aq = a[q];
-    s += aq * (w.x[j] * fx[q] + w.y[j] * fy[q] + w.z[j] * fz[q]);
+    R aq = ld(a + q);
+    s += aq * (w.x[j] * ld(fx + q) + w.y[j] * ld(fy + q) + w.z[j] * ld(fz + q));
   }
   return s;
 }
@@ -208,7 +214,7 @@ __device__ __forceinline__ void grad7(const W7x3<R>& w, const Nbr7& nb, const R*
   gx = gy = gz = 0;
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
-    R v = s[nb.n[j]];
+    R v = ld(s + nb.n[j]);
     gx += w.x[j] * v;
     gy += w.y[j] * v;
     gz += w.z[j] * v;

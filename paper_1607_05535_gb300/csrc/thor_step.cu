@@ -25,22 +25,23 @@ __global__ void k_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int kc
   if (c >= G.ncol) return;
   const int S = G.colp;
   const R gamma = (R)ph.gamma, inv_Rd = R(1.0 / ph.Rd);
-  R rx = G.rhat[c], ry = G.rhat[S + c], rz = G.rhat[2 * S + c];
+  R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
+#pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     if (k < G.nv) {
       int i = k * S + c;
-      R rho = U.rhob[k] + X.rho[i];
-      R thp = X.th[i];
-      R pp = eos_dev<R>(U.pb[k], U.thb[k], thp, gamma);
-      R p = U.pb[k] + pp;
+      R rho = ld(U.rhob + (k)) + ld(X.rho + (i));
+      R thp = ld(X.th + (i));
+      R pp = eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), thp, gamma);
+      R p = ld(U.pb + (k)) + pp;
       R inv = R(1) / rho;
       R Temp = p * inv * inv_Rd;
-      R wc = U.clo[k] * X.w[i] + U.chi[k] * X.w[i + S];
-      R mx = X.mx[i], my = X.my[i], mz = X.mz[i];
+      R wc = ld(U.clo + (k)) * ld(X.w + (i)) + ld(U.chi + (k)) * ld(X.w + (i + S));
+      R mx = ld(X.mx + (i)), my = ld(X.my + (i)), mz = ld(X.mz + (i));
       T.pp[i] = pp;
-      T.Tp[i] = Temp - U.Tb[k];
-      T.theta[i] = (U.thb[k] + thp) * inv;
+      T.Tp[i] = Temp - ld(U.Tb + (k));
+      T.theta[i] = (ld(U.thb + (k)) + thp) * inv;
       T.vx[i] = (mx + wc * rx) * inv;
       T.vy[i] = (my + wc * ry) * inv;
       T.vz[i] = (mz + wc * rz) * inv;
@@ -50,8 +51,8 @@ __global__ void k_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int kc
     }
     if (k >= 1 && k < G.nv) {
       int i = k * S + c;
-      R rlo = U.rhob[k - 1] + X.rho[i - S], rhi = U.rhob[k] + X.rho[i];
-      T.vr[i] = X.w[i] / (U.wlo[k] * rlo + U.whi[k] * rhi);
+      R rlo = ld(U.rhob + (k - 1)) + ld(X.rho + (i - S)), rhi = ld(U.rhob + (k)) + ld(X.rho + (i));
+      T.vr[i] = ld(X.w + (i)) / (ld(U.wlo + (k)) * rlo + ld(U.whi + (k)) * rhi);
     } else if (k == 0 || k == G.nv) {
       T.vr[k * S + c] = 0;
     }
@@ -68,11 +69,12 @@ __global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk) 
   Nbr7 nb = load_nbr(G, c);
   W7<R> wl = load_w7(G.wlap, S, c);
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
+#pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     if (k < G.nv) {
       int o = k * S;
-      R inv_r2 = U.inv_rc2[k];
-      R rho = U.rhob[k] + X.rho[o + c];
+      R inv_r2 = ld(U.inv_rc2 + (k));
+      R rho = ld(U.rhob + (k)) + ld(X.rho + (o + c));
       T.qrho[o + c] = Kd * apply7(wl, nb, X.rho + o) * inv_r2;
       R rk = rho * Kd * inv_r2;
       T.qvx[o + c] = rk * apply7(wl, nb, T.vhx + o);
@@ -82,9 +84,9 @@ __global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk) 
     }
     if (k >= 1 && k < G.nv) {
       int o = k * S;
-      R rlo = U.rhob[k - 1] + X.rho[o - S + c], rhi = U.rhob[k] + X.rho[o + c];
-      R rif = U.wlo[k] * rlo + U.whi[k] * rhi;
-      T.qvr[o + c] = rif * Kd * apply7(wl, nb, T.vr + o) / U.ri2[k];
+      R rlo = ld(U.rhob + (k - 1)) + ld(X.rho + (o - S + c)), rhi = ld(U.rhob + (k)) + ld(X.rho + (o + c));
+      R rif = ld(U.wlo + (k)) * rlo + ld(U.whi + (k)) * rhi;
+      T.qvr[o + c] = rif * Kd * apply7(wl, nb, T.vr + o) / ld(U.ri2 + (k));
     } else if (k == 0 || k == G.nv) {
       T.qvr[k * S + c] = 0;
     }
@@ -106,15 +108,16 @@ __global__ void k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> S
   W7x3<R> wd = load_w7x3(G.wdiv, S, c);
   W7x3<R> wg = load_w7x3(G.wgrad, S, c);
   W7<R> wl = load_w7(G.wlap, S, c);
-  R rx = G.rhat[c], ry = G.rhat[S + c], rz = G.rhat[2 * S + c];
+  R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
   const R two_om = R(2.0 * ph.omega), gamma = (R)ph.gamma, Rd = (R)ph.Rd;
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
+#pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
-    const R inv_r = U.inv_rc[k], inv_r2 = U.inv_rc2[k];
-    const R sql = U.sq_lo[k], sqh = U.sq_hi[k];
-    R thfull = U.thb[k] + X.th[i];
-    R p = U.pb[k] + T.pp[i];
+    const R inv_r = ld(U.inv_rc + (k)), inv_r2 = ld(U.inv_rc2 + (k));
+    const R sql = ld(U.sq_lo + (k)), sqh = ld(U.sq_hi + (k));
+    R thfull = ld(U.thb + (k)) + ld(X.th + (i));
+    R p = ld(U.pb + (k)) + ld(T.pp + (i));
 
     // hyperdiffusion (Sec. 4)
     R Frho = 0, FMx = 0, FMy = 0, FMz = 0, Fth = 0;
@@ -131,18 +134,18 @@ __global__ void k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> S
     // advection div(rho v v_j) of the Cartesian components (Sec. 3)
     const R* vs[3] = {T.vx, T.vy, T.vz};
     R A[3];
-    R wlo_w = X.w[i], whi_w = X.w[i + S];
+    R wlo_w = ld(X.w + (i)), whi_w = ld(X.w + (i + S));
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       R ah = div7_scaled(wd, nb, vs[j] + o, X.mx + o, X.my + o, X.mz + o) * inv_r;
       R vlo = 0, vhi = 0;
-      if (k >= 1) vlo = U.wlo[k] * vs[j][i - S] + U.whi[k] * vs[j][i];
-      if (k + 1 < G.nv) vhi = U.wlo[k + 1] * vs[j][i] + U.whi[k + 1] * vs[j][i + S];
+      if (k >= 1) vlo = ld(U.wlo + (k)) * vs[j][i - S] + ld(U.whi + (k)) * vs[j][i];
+      if (k + 1 < G.nv) vhi = ld(U.wlo + (k + 1)) * vs[j][i] + ld(U.whi + (k + 1)) * vs[j][i + S];
       A[j] = ah + sqh * whi_w * vhi - sql * wlo_w * vlo;
     }
     // Coriolis 2 Omega z x (rho v) with the full momentum
-    R wc = U.clo[k] * wlo_w + U.chi[k] * whi_w;
-    R mx = X.mx[i], my = X.my[i];
+    R wc = ld(U.clo + (k)) * wlo_w + ld(U.chi + (k)) * whi_w;
+    R mx = ld(X.mx + (i)), my = ld(X.my + (i));
     R fx = mx + wc * rx, fy = my + wc * ry;
     A[0] += -two_om * fy;
     A[1] += two_om * fx;
@@ -164,8 +167,8 @@ __global__ void k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> S
 
     R dht = div7_scaled(wd, nb, T.theta + o, X.mx + o, X.my + o, X.mz + o) * inv_r;
     R thlo = 0, thhi = 0;
-    if (k >= 1) thlo = U.wlo[k] * T.theta[i - S] + U.whi[k] * T.theta[i];
-    if (k + 1 < G.nv) thhi = U.wlo[k + 1] * T.theta[i] + U.whi[k + 1] * T.theta[i + S];
+    if (k >= 1) thlo = ld(U.wlo + (k)) * ld(T.theta + (i - S)) + ld(U.whi + (k)) * ld(T.theta + (i));
+    if (k + 1 < G.nv) thhi = ld(U.wlo + (k + 1)) * ld(T.theta + (i)) + ld(U.whi + (k + 1)) * ld(T.theta + (i + S));
     R dvt = sqh * thhi * whi_w - sql * thlo * wlo_w;
     SL.sth[i] = Fth - dht - dvt;
     SL.acr[i] = acr;
@@ -185,6 +188,7 @@ __global__ void k_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R>
   W7<R> wl = load_w7(G.wlap, S, c);
   const R g = (R)ph.g;
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
+#pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int i = k * S + c;
     if (k == 0 || k == G.nv) {
@@ -192,14 +196,14 @@ __global__ void k_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R>
       SL.thi[i] = 0;
       continue;
     }
-    R wlo = U.wlo[k], whi = U.whi[k];
+    R wlo = ld(U.wlo + (k)), whi = ld(U.whi + (k));
     R FW = 0;
-    if (hyper) FW = -apply7(wl, nb, T.qvr + k * S) / U.ri2[k];
-    R sw = U.Rb[k] - (T.pp[i] - T.pp[i - S]) * U.inv_dzc[k]
-         - g * (wlo * X.rho[i - S] + whi * X.rho[i])
-         - (wlo * SL.acr[i - S] + whi * SL.acr[i]) + FW;
+    if (hyper) FW = -apply7(wl, nb, T.qvr + k * S) / ld(U.ri2 + (k));
+    R sw = ld(U.Rb + (k)) - (ld(T.pp + (i)) - ld(T.pp + (i - S))) * ld(U.inv_dzc + (k))
+         - g * (wlo * ld(X.rho + (i - S)) + whi * ld(X.rho + (i)))
+         - (wlo * ld(SL.acr + (i - S)) + whi * ld(SL.acr + (i))) + FW;
     SL.sw[i] = sw;
-    SL.thi[i] = wlo * T.theta[i - S] + whi * T.theta[i];
+    SL.thi[i] = wlo * ld(T.theta + (i - S)) + whi * ld(T.theta + (i));
   }
 }
 
@@ -212,18 +216,19 @@ __global__ void k_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> Xs, Wor
   if (c >= G.ncol) return;
   const int S = G.colp;
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
+#pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     int i = k * S + c;
     if (k < G.nv) {
-      P.rho[i] = Xt.rho[i] - Xs.rho[i];
-      P.mx[i] = Xt.mx[i] - Xs.mx[i];
-      P.my[i] = Xt.my[i] - Xs.my[i];
-      P.mz[i] = Xt.mz[i] - Xs.mz[i];
-      P.th[i] = Xt.th[i] - Xs.th[i];
-      R ppt = eos_dev<R>(U.pb[k], U.thb[k], Xt.th[i], (R)ph.gamma);
-      P.p[i] = ppt - T.pp[i];
+      P.rho[i] = ld(Xt.rho + (i)) - ld(Xs.rho + (i));
+      P.mx[i] = ld(Xt.mx + (i)) - ld(Xs.mx + (i));
+      P.my[i] = ld(Xt.my + (i)) - ld(Xs.my + (i));
+      P.mz[i] = ld(Xt.mz + (i)) - ld(Xs.mz + (i));
+      P.th[i] = ld(Xt.th + (i)) - ld(Xs.th + (i));
+      R ppt = eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), ld(Xt.th + (i)), (R)ph.gamma);
+      P.p[i] = ppt - ld(T.pp + (i));
     }
-    P.w[i] = Xt.w[i] - Xs.w[i];
+    P.w[i] = ld(Xt.w + (i)) - ld(Xs.w + (i));
   }
 }
 
@@ -238,11 +243,12 @@ __global__ void k_ss_div(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, in
   Nbr7 nb = load_nbr(G, c);
   W7x3<R> wd = load_w7x3(G.wdiv, S, c);
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
+#pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
-    R dh = div7(wd, nb, P.mx + o, P.my + o, P.mz + o) * U.inv_rc[k];
-    R dv = U.sq_hi[k] * P.w[i + S] - U.sq_lo[k] * P.w[i];
-    T.dd[i] = SL.dsc[i] + dh + dv;
+    R dh = div7(wd, nb, P.mx + o, P.my + o, P.mz + o) * ld(U.inv_rc + (k));
+    R dv = ld(U.sq_hi + (k)) * ld(P.w + (i + S)) - ld(U.sq_lo + (k)) * ld(P.w + (i));
+    T.dd[i] = ld(SL.dsc + (i)) + dh + dv;
   }
 }
 
@@ -254,11 +260,12 @@ __global__ void k_ss_grad(Geo<R> G, VR<R> U, Work<R> T, int kchunk) {
   Nbr7 nb = load_nbr(G, c);
   W7x3<R> wg = load_w7x3(G.wgrad, S, c);
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
+#pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
     R gx, gy, gz;
     grad7(wg, nb, T.dd + o, gx, gy, gz);
-    R inv_r = U.inv_rc[k];
+    R inv_r = ld(U.inv_rc + (k));
     T.gx[i] = gx * inv_r;
     T.gy[i] = gy * inv_r;
     T.gz[i] = gz * inv_r;
@@ -275,14 +282,15 @@ __global__ void k_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R 
   Nbr7 nb = load_nbr(G, c);
   W7x3<R> wg = load_w7x3(G.wgrad, S, c);
   W7<R> wl = load_w7(G.wlap, S, c);
-  R rx = G.rhat[c], ry = G.rhat[S + c], rz = G.rhat[2 * S + c];
+  R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
+#pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
-    R inv_r = U.inv_rc[k];
+    R inv_r = ld(U.inv_rc + (k));
     R ddx = 0, ddy = 0, ddz = 0;
     if (divdamp) {
-      R s = -Kd * U.inv_rc2[k];
+      R s = -Kd * ld(U.inv_rc2 + (k));
       ddx = s * apply7(wl, nb, T.gx + o);
       ddy = s * apply7(wl, nb, T.gy + o);
       ddz = s * apply7(wl, nb, T.gz + o);
@@ -290,9 +298,9 @@ __global__ void k_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R 
     }
     R gx, gy, gz;
     grad7(wg, nb, P.p + o, gx, gy, gz);
-    R mx = P.mx[i] + dtau * (-gx * inv_r + ddx + SL.smx[i]);
-    R my = P.my[i] + dtau * (-gy * inv_r + ddy + SL.smy[i]);
-    R mz = P.mz[i] + dtau * (-gz * inv_r + ddz + SL.smz[i]);
+    R mx = ld(P.mx + (i)) + dtau * (-gx * inv_r + ddx + ld(SL.smx + (i)));
+    R my = ld(P.my + (i)) + dtau * (-gy * inv_r + ddy + ld(SL.smy + (i)));
+    R mz = ld(P.mz + (i)) + dtau * (-gz * inv_r + ddz + ld(SL.smz + (i)));
     project(rx, ry, rz, mx, my, mz);
     P.mx[i] = mx;
     P.my[i] = my;
@@ -313,22 +321,23 @@ __global__ void k_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R
   Nbr7 nb = load_nbr(G, c);
   W7x3<R> wd = load_w7x3(G.wdiv, S, c);
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
+#pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
     R dh = 0, dht = 0;
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
       const int q = o + nb.n[j];
-      R f = wd.x[j] * P.mx[q] + wd.y[j] * P.my[q] + wd.z[j] * P.mz[q];
+      R f = wd.x[j] * ld(P.mx + (q)) + wd.y[j] * ld(P.my + (q)) + wd.z[j] * ld(P.mz + (q));
       dh += f;
-      dht += T.theta[q] * f;
+      dht += ld(T.theta + (q)) * f;
     }
-    const R inv_r = U.inv_rc[k];
-    R thk = P.th[i];
-    R bk = thk + dtau * (SL.sth[i] - dht * inv_r);
-    T.ca[i] = P.rho[i] + dtau * (SL.srho[i] - dh * inv_r);
+    const R inv_r = ld(U.inv_rc + (k));
+    R thk = ld(P.th + (i));
+    R bk = thk + dtau * (ld(SL.sth + (i)) - dht * inv_r);
+    T.ca[i] = ld(P.rho + (i)) + dtau * (ld(SL.srho + (i)) - dh * inv_r);
     T.cb[i] = bk;
-    T.cc[i] = P.p[i] + SL.pi[i] * (bk - thk);
+    T.cc[i] = ld(P.p + (i)) + ld(SL.pi + (i)) * (bk - thk);
   }
 }
 
@@ -368,25 +377,26 @@ __global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<
   // coefficients of interface m (1 <= m <= N)
   auto coef = [&](int m, double& lo, double& di, double& up, double& rh) {
     const int i = m * S + cs;
-    const R pi_lo = SL.pi[i - S], pi_hi = SL.pi[i];
-    const R wlo = U.wlo[m], whi = U.whi[m], dtz = dt2 * U.inv_dzc[m];
-    const R ql = U.sq_lo[m - 1], qh = U.sq_hi[m - 1];    // cell m-1
-    const R pl = U.sq_lo[m], ph_ = U.sq_hi[m];           // cell m
-    const R th_m = SL.thi[i];
+    const R pi_lo = ld(SL.pi + (i - S)), pi_hi = ld(SL.pi + (i));
+    const R wlo = ld(U.wlo + (m)), whi = ld(U.whi + (m)), dtz = dt2 * ld(U.inv_dzc + (m));
+    const R ql = ld(U.sq_lo + (m - 1)), qh = ld(U.sq_hi + (m - 1));    // cell m-1
+    const R pl = ld(U.sq_lo + (m)), ph_ = ld(U.sq_hi + (m));           // cell m
+    const R th_m = ld(SL.thi + (i));
     R lower = 0, upper = 0;
-    if (m > 1) lower = (-dtz * pi_lo * SL.thi[i - S] + dt2 * g * wlo) * ql;
-    if (m < N) upper = (-dtz * pi_hi * SL.thi[i + S] - dt2 * g * whi) * ph_;
+    if (m > 1) lower = (-dtz * pi_lo * ld(SL.thi + (i - S)) + dt2 * g * wlo) * ql;
+    if (m < N) upper = (-dtz * pi_hi * ld(SL.thi + (i + S)) - dt2 * g * whi) * ph_;
     lo = (double)lower;
     up = (double)upper;
     di = (double)(R(1) + dtz * th_m * (pi_hi * pl + pi_lo * qh) - dt2 * g * (wlo * qh - whi * pl));
-    rh = (double)(P.w[i] + rdt * SL.sw[i] - rdt * U.inv_dzc[m] * (T.cc[i] - T.cc[i - S])
-                  - rdt * g * (wlo * T.ca[i - S] + whi * T.ca[i]));
+    rh = (double)(ld(P.w + (i)) + rdt * ld(SL.sw + (i)) - rdt * ld(U.inv_dzc + (m)) * (ld(T.cc + (i)) - ld(T.cc + (i - S)))
+                  - rdt * g * (wlo * ld(T.ca + (i - S)) + whi * ld(T.ca + (i))));
   };
   auto inv_of = [](double den) { return sizeof(R) == sizeof(double) ? 1.0 / den : rcp64_1(den); };
 
   // elimination
   if (half == 0) {
     double c1 = 0.0, d1 = 0.0;
+#pragma unroll 2
     for (int m = 1; m <= p; ++m) {
       double lo, di, up, rh;
       coef(m, lo, di, up, rh);
@@ -398,6 +408,7 @@ __global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<
     }
   } else {
     double e1 = 0.0, f1 = 0.0;
+#pragma unroll 2
     for (int m = N; m > p; --m) {
       double lo, di, up, rh;
       coef(m, lo, di, up, rh);
@@ -449,15 +460,15 @@ __global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<
     for (int k = half; k < nv; k += 2) {
       const int i = k * S + c;
       const R wl = (R)sdp[k * 32 + tx], wh = (R)sdp[(k + 1) * 32 + tx];
-      const R thl = k > 0 ? SL.thi[i] : R(0);
-      const R thh = k + 1 < nv ? SL.thi[i + S] : R(0);
-      const R el = U.sq_lo[k], eh = U.sq_hi[k];
-      R th_new = T.cb[i] - rdt * (eh * thh * wh - el * thl * wl);
-      P.rho[i] = T.ca[i] - rdt * (eh * wh - el * wl);
+      const R thl = k > 0 ? ld(SL.thi + (i)) : R(0);
+      const R thh = k + 1 < nv ? ld(SL.thi + (i + S)) : R(0);
+      const R el = ld(U.sq_lo + (k)), eh = ld(U.sq_hi + (k));
+      R th_new = ld(T.cb + (i)) - rdt * (eh * thh * wh - el * thl * wl);
+      P.rho[i] = ld(T.ca + (i)) - rdt * (eh * wh - el * wl);
       P.th[i] = th_new;
       // p* = EOS(Th^(s) + Th*) - p^(s) = p^(s) ((1 + Th*/Th^(s))^gamma - 1)
-      R ps = U.pb[k] + T.pp[i];
-      R ths = U.thb[k] + Xs.th[i];
+      R ps = ld(U.pb + (k)) + ld(T.pp + (i));
+      R ths = ld(U.thb + (k)) + ld(Xs.th + (i));
       P.p[i] = ps * rexpm1<R>(gamma * rlog1p<R>(th_new / ths));
       if (k >= 1) P.w[i] = wl;
     }
@@ -471,16 +482,17 @@ __global__ void k_stage_end(Geo<R> G, Xf<R> Xs, Pert<R> P, Xf<R> Xo, int kchunk)
   if (c >= G.ncol) return;
   const int S = G.colp;
   int k0 = blockIdx.y * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
+#pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     int i = k * S + c;
     if (k < G.nv) {
-      Xo.rho[i] = Xs.rho[i] + P.rho[i];
-      Xo.mx[i] = Xs.mx[i] + P.mx[i];
-      Xo.my[i] = Xs.my[i] + P.my[i];
-      Xo.mz[i] = Xs.mz[i] + P.mz[i];
-      Xo.th[i] = Xs.th[i] + P.th[i];
+      Xo.rho[i] = ld(Xs.rho + (i)) + ld(P.rho + (i));
+      Xo.mx[i] = ld(Xs.mx + (i)) + ld(P.mx + (i));
+      Xo.my[i] = ld(Xs.my + (i)) + ld(P.my + (i));
+      Xo.mz[i] = ld(Xs.mz + (i)) + ld(P.mz + (i));
+      Xo.th[i] = ld(Xs.th + (i)) + ld(P.th + (i));
     }
-    Xo.w[i] = Xs.w[i] + P.w[i];
+    Xo.w[i] = ld(Xs.w + (i)) + ld(P.w + (i));
   }
 }
 
@@ -496,16 +508,16 @@ __global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, int forcing, doub
   if (c >= G.ncol) return;
   const int S = G.colp;
   const R gamma = (R)ph.gamma, inv_gamma = R(1.0 / ph.gamma), Rd = (R)ph.Rd;
-  R sl = G.sinlat[c], cl = G.coslat[c], clcl = G.xdir[c];
-  R p0 = U.pb[0] + eos_dev<R>(U.pb[0], U.thb[0], X.th[c], gamma);
-  R T0 = p0 / ((U.rhob[0] + X.rho[c]) * Rd);
-  R ps = p0 * rexp<R>(R(ph.g) * U.zc[0] / (Rd * T0));
+  R sl = ld(G.sinlat + (c)), cl = ld(G.coslat + (c)), clcl = ld(G.xdir + (c));
+  R p0 = ld(U.pb + (0)) + eos_dev<R>(ld(U.pb + (0)), ld(U.thb + (0)), ld(X.th + (c)), gamma);
+  R T0 = p0 / ((ld(U.rhob + (0)) + ld(X.rho + (c))) * Rd);
+  R ps = p0 * rexp<R>(R(ph.g) * ld(U.zc + (0)) / (Rd * T0));
   const R rdt = (R)dt;
   for (int k = 0; k < G.nv; ++k) {
     const int i = k * S + c;
-    R rhop = X.rho[i];
-    R rho = U.rhob[k] + rhop;
-    R p = U.pb[k] + eos_dev<R>(U.pb[k], U.thb[k], X.th[i], gamma);
+    R rhop = ld(X.rho + (i));
+    R rho = ld(U.rhob + (k)) + rhop;
+    R p = ld(U.pb + (k)) + eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), ld(X.th + (i)), gamma);
     R Temp = p / (rho * Rd);
     R sigma = p / ps;
     R Kv, KT, Teq;
@@ -523,7 +535,7 @@ __global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, int forcing, doub
       Teq = Teq > R(200) ? Teq : R(200);
     } else {
       const R ss = R(0.12), zs = R(2.0e6), Ts = R(1600), Gt = R(2.0e-4), dTs = R(10);
-      R z = U.zc[k];
+      R z = ld(U.zc + (k));
       R Tv, bt;
       if (z <= zs) {
         R h = Gt * (z - zs) / R(2);
@@ -543,8 +555,8 @@ __global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, int forcing, doub
     X.mz[i] *= fr;
     R Tn = (Temp + KT * rdt * Teq) / (R(1) + KT * rdt);
     // rho theta at fixed rho: Th/Th_bar = ((rho/rho_bar)(T/T_bar))^(1/gamma)
-    R lr = rlog1p<R>(rhop / U.rhob[k]) + rlog<R>(Tn / U.Tb[k]);
-    X.th[i] = U.thb[k] * rexpm1<R>(lr * inv_gamma);
+    R lr = rlog1p<R>(rhop / ld(U.rhob + (k))) + rlog<R>(Tn / ld(U.Tb + (k)));
+    X.th[i] = ld(U.thb + (k)) * rexpm1<R>(lr * inv_gamma);
   }
 }
 
