@@ -181,6 +181,33 @@ int thor_profile_read(thor_state* state, int kernel, double* total_ms, long long
 
 void thor_state_destroy(thor_state* state);
 
+/* ------------------------------------------------------- allocation-free */
+
+/* Allocation-free float64 mass sum: *mass_out = sum_i rho[i] * volume[i]
+ * over i < n, the same deterministic two-pass compensated reduction that
+ * thor_diag uses for its mass. The paper has no counterpart: this entry
+ * point exists for callers that must not call cudaMalloc, because an outer
+ * framework owns the whole device-memory budget or because cudaMalloc would
+ * synchronise the device in a latency-critical loop.
+ *  - rho, volume: caller-owned device arrays of n float64 values (any
+ *    order, e.g. the canonical [ncol][nv] order of thor_state_get with the
+ *    cell volumes A_c r_k^2 dz_k); mass_out: caller-owned device pointer to
+ *    one float64. Asynchronous on `stream` (NULL = legacy default stream).
+ *  - Allocates nothing. The per-block partial sums live in a file-scope
+ *    static __device__ array of 4097 float64 (about 32 KB) that every GPU
+ *    loading the library holds until the process exits; it bounds n to
+ *    4096 * 16384 = 67,108,864 elements; larger n (or n = 0, or a NULL
+ *    pointer) returns THOR_EINVAL without launching anything.
+ *  - The first call on a device looks up that array's device address with
+ *    cudaGetSymbolAddress (with that device current); make the first call on
+ *    each device before any stream capture.
+ *  - Every call shares the array and leaves its partial sums in it; each
+ *    call overwrites the slots it uses before reading them. Calls that
+ *    overlap on the GPU (on different streams, or from different threads)
+ *    race on the array and must be ordered by the caller. */
+int thor_mass_noalloc(const double* rho, const double* volume, size_t n, double* mass_out,
+                      void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,7 @@ EXPORTED = [
     "thor_grid_neighbours", "thor_grid_areas", "thor_grid_destroy", "thor_state_init",
     "thor_step", "thor_diag", "thor_state_get", "thor_state_set", "thor_launch_count",
     "thor_tune", "thor_profile", "thor_profile_read", "thor_state_destroy",
+    "thor_mass_noalloc",
 ]
 
 # kernel ids of thor_profile_read
@@ -95,6 +96,7 @@ def _load():
         "thor_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_longlong)]),
         "thor_state_destroy": (None, [P]),
+        "thor_mass_noalloc": (I, [P, P, Z, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -226,3 +228,14 @@ def thor_profile_read(state, kernel):
 
 def thor_state_destroy(state):
     _lib.thor_state_destroy(state)
+
+
+def thor_mass_noalloc(rho, volume, mass_out, stream=None):
+    """sum(rho * volume) into the one-element device tensor ``mass_out``;
+    ``rho`` and ``volume`` are float64 device tensors of the same size. For
+    callers that must not allocate: the library allocates nothing here."""
+    n = rho.numel()
+    if volume.numel() != n:
+        raise ValueError("rho and volume differ in size")
+    _check(_lib.thor_mass_noalloc(_ptr(rho), _ptr(volume), n, _ptr(mass_out),
+                                  ctypes.c_void_p(stream or 0)), "thor_mass_noalloc")
