@@ -132,8 +132,9 @@ int thor_state_init(thor_grid* grid, const thor_planet* planet, const thor_init*
  * damping, explicit horizontal momentum (Eq. mom2), implicit vertical
  * momentum (Eq. momr2, tridiagonal per column), density (Eq. dens2),
  * rho theta (Eq. pt2) and pressure (Eq. theta_to_p); then the physics
- * (Sec. 5). Asynchronous on the state's stream. n_small even and >= 2,
- * n_large >= 0, dt > 0, else THOR_EINVAL. */
+ * (Sec. 5). Asynchronous on the state's stream (unless the finite check of
+ * thor_tune is on). n_small even and >= 2, n_large >= 0, dt > 0, else
+ * THOR_EINVAL. */
 int thor_step(thor_state* state, int n_large, int n_small, double dt);
 
 /* Global diagnostics in float64 (deterministic two-pass reductions):
@@ -162,8 +163,12 @@ int thor_launch_count(const thor_state* state, long long* count);
  * reloads of the per-column weights.
  * THOR_TUNE_GRAPH: 1 (default) replays a captured CUDA graph of one large
  * step on a non-default stream (re-captured when dt, n_small or the chunk
- * change; never while thor_profile records); 0 launches kernel by kernel. */
-enum { THOR_TUNE_KCHUNK = 0, THOR_TUNE_GRAPH = 1 };
+ * change; never while thor_profile records); 0 launches kernel by kernel.
+ * THOR_TUNE_CHECK_FINITE: 1 makes thor_step finish with a non-finite count
+ * of the state (one reduction and one stream synchronisation per call) and
+ * return THOR_ENONFINITE if any value is NaN or Inf; the state is the one
+ * after the step (restore a checkpoint with thor_state_set). Default 0. */
+enum { THOR_TUNE_KCHUNK = 0, THOR_TUNE_GRAPH = 1, THOR_TUNE_CHECK_FINITE = 2 };
 int thor_tune(thor_state* state, int knob, int value);
 
 /* Per-kernel timing. While enabled, every launch of the state is bracketed by

@@ -208,7 +208,7 @@ def thor_launch_count(state):
     return c.value
 
 
-THOR_TUNE_KCHUNK, THOR_TUNE_GRAPH = 0, 1
+THOR_TUNE_KCHUNK, THOR_TUNE_GRAPH, THOR_TUNE_CHECK_FINITE = 0, 1, 2
 
 
 def thor_tune(state, knob, value):

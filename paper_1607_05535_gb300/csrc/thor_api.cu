@@ -18,6 +18,7 @@ struct thor_grid {
 struct thor_state {
   thor_grid* grid = nullptr;
   int precision = THOR_FP64;
+  int check_finite = 0;
   std::unique_ptr<thor::ImplBase> impl;
 };
 
@@ -629,7 +630,13 @@ int thor_state_init(thor_grid* grid, const thor_planet* pl, const thor_init* in,
 
 int thor_step(thor_state* s, int n_large, int n_small, double dt) {
   if (!s || n_large < 0 || n_small < 2 || (n_small % 2) || !(dt > 0)) return THOR_EINVAL;
-  return s->impl->step(n_large, n_small, dt);
+  int rc = s->impl->step(n_large, n_small, dt);
+  if (rc || !s->check_finite) return rc;
+  double v[8];
+  long long nf = 0;
+  rc = s->impl->diag(v, &nf);
+  if (rc) return rc;
+  return nf ? THOR_ENONFINITE : THOR_OK;
 }
 
 int thor_diag(thor_state* s, thor_diag_t* out) {
@@ -673,6 +680,10 @@ int thor_tune(thor_state* s, int knob, int value) {
   }
   if (knob == THOR_TUNE_GRAPH) {
     s->impl->set_graph(value != 0);
+    return THOR_OK;
+  }
+  if (knob == THOR_TUNE_CHECK_FINITE) {
+    s->check_finite = value != 0;
     return THOR_OK;
   }
   return THOR_EINVAL;

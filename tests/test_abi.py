@@ -39,7 +39,8 @@ def _match(P, O):
     return d, idx
 
 
-@pytest.mark.parametrize("g, max_iter, tol", [(0, 10, 0.0), (2, 10, 0.0), (4, 10, 0.0), (3, 100000, 1e-5)])
+@pytest.mark.parametrize("g, max_iter, tol", [(0, 10, 0.0), (2, 10, 0.0), (4, 10, 0.0), (3, 100000, 1e-5),
+                                            (6, 10, 0.0)])
 def test_grid_parity_with_oracle(g, max_iter, tol):
     """Independent builders (rhombus lattice vs. triangle list) give the same
     points, neighbour sets, areas and spring iteration count."""

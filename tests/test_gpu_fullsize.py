@@ -1,0 +1,96 @@
+"""Properties that hold at any size, checked at the benchmark size (glevel 6
+x 32 levels, 40962 columns) in the launch configuration bench.py times
+(float32 mixed and float64, graph replay, default level chunk)."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1607_05535_gb300 as thor
+from harness import init_struct, planet_struct
+import workloads as wls
+
+WL = wls.HS_G6
+
+
+def _grid():
+    P = WL.planet
+    return thor.thor_grid_create(WL.glevel, WL.nv, P.radius, WL.z_top,
+                                 thor.thor_spring(1.15, 1.0, 1.0, 0.01, 0.0, WL.spring_max_iter))
+
+
+def _state(grid, wl, precision, stream):
+    return thor.thor_state_init(grid, planet_struct(wl.planet), init_struct(wl, precision), stream)
+
+
+@pytest.fixture(scope="module")
+def grid():
+    g = _grid()
+    yield g
+    thor.thor_grid_destroy(g)
+
+
+@pytest.mark.parametrize("precision, tol", [(thor.THOR_FP64, 1e-12), (thor.THOR_MIXED, 1e-12)])
+def test_mass_conserved_full_size(grid, precision, tol):
+    s = torch.cuda.Stream()
+    st = _state(grid, WL, precision, s.cuda_stream)
+    try:
+        m0 = thor.thor_diag(st)["mass"]
+        thor.thor_step(st, 3, WL.n_small, WL.dt)
+        d = thor.thor_diag(st)
+        assert d["nonfinite"] == 0
+        assert abs(d["mass"] - m0) / m0 < (tol if precision == thor.THOR_FP64 else 1e-7)
+    finally:
+        thor.thor_state_destroy(st)
+
+
+@pytest.mark.parametrize("precision, vmax", [(thor.THOR_FP64, 1e-8), (thor.THOR_MIXED, 1e-3)])
+def test_rest_full_size(grid, precision, vmax):
+    wl = WL.with_(forcing="none", noise_amp=0.0)
+    s = torch.cuda.Stream()
+    st = _state(grid, wl, precision, s.cuda_stream)
+    try:
+        thor.thor_step(st, 3, wl.n_small, wl.dt)
+        d = thor.thor_diag(st)
+        assert d["max_vh"] < vmax and d["max_w"] < vmax, d
+    finally:
+        thor.thor_state_destroy(st)
+
+
+def test_mixed_tracks_fp64_full_size(grid):
+    """Three large steps of the float32 path stay within the mixed-mode
+    tolerances of the float64 path at full size."""
+    s = torch.cuda.Stream()
+    out = []
+    for prec in (thor.THOR_FP64, thor.THOR_MIXED):
+        st = _state(grid, WL, prec, s.cuda_stream)
+        try:
+            thor.thor_step(st, 3, WL.n_small, WL.dt)
+            out.append({f: thor.thor_state_get(st, f, WL.ncol, WL.nv)
+                        for f in (thor.THOR_FIELD_RHO, thor.THOR_FIELD_TEMPERATURE, thor.THOR_FIELD_MOM)})
+        finally:
+            thor.thor_state_destroy(st)
+    a, b = out
+    rel = lambda f: np.linalg.norm(b[f] - a[f]) / np.linalg.norm(a[f])
+    assert rel(thor.THOR_FIELD_RHO) < 1e-6
+    assert rel(thor.THOR_FIELD_TEMPERATURE) < 1e-6
+    assert rel(thor.THOR_FIELD_MOM) < 1e-2
+
+
+def test_graph_matches_direct_full_size(grid):
+    s = torch.cuda.Stream()
+    res = []
+    for graph in (1, 0):
+        st = _state(grid, WL, thor.THOR_MIXED, s.cuda_stream)
+        try:
+            thor.thor_tune(st, thor.THOR_TUNE_GRAPH, graph)
+            thor.thor_step(st, 2, WL.n_small, WL.dt)
+            res.append(thor.thor_state_get(st, thor.THOR_FIELD_MOM, WL.ncol, WL.nv))
+        finally:
+            thor.thor_state_destroy(st)
+    assert np.array_equal(res[0], res[1])

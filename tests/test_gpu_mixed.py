@@ -1,0 +1,63 @@
+"""Mixed precision (float32 fields and stencils, float64 elimination and
+reductions) against the float64 oracle, per field, on the glevel-4 x 20-level
+Held-Suarez workload. The gates are the stated per-field tolerances of the
+mixed mode (also quoted in the design doc)."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1607_05535_gb300 as thor
+from harness import Pair
+from oracle import dycore as dc
+from oracle import operators as op
+import workloads as wls
+
+# stated tolerances after 10 large steps (relative L2 unless noted)
+GATES = {"rho": 1e-6, "T": 1e-6, "vh_abs_max": 2e-3, "vh_rel": 1e-2, "w_abs_max": 5e-5}
+
+
+def field_report(p, X, ref):
+    pl = p.model.planet
+    T = dc.temperature(pl, X.rho, dc.pressure(pl, X.Th))
+    Tr = dc.temperature(pl, ref.rho, dc.pressure(pl, ref.Th))
+    vh = X.M / X.rho[..., None]
+    vhr = ref.M / ref.rho[..., None]
+    ri = op.interp_to_interfaces(p.model.vg, X.rho)[:, 1:-1]
+    rir = op.interp_to_interfaces(p.model.vg, ref.rho)[:, 1:-1]
+    w, wr = X.W[:, 1:-1] / ri, ref.W[:, 1:-1] / rir
+    return {
+        "rho": float(np.linalg.norm(X.rho - ref.rho) / np.linalg.norm(ref.rho)),
+        "T": float(np.linalg.norm(T - Tr) / np.linalg.norm(Tr)),
+        "vh_abs_max": float(np.abs(vh - vhr).max()),
+        "vh_rel": float(np.linalg.norm(vh - vhr) / np.linalg.norm(vhr)),
+        "vh_max": float(np.abs(vhr).max()),
+        "w_abs_max": float(np.abs(w - wr).max()),
+        "w_max": float(np.abs(wr).max()),
+    }
+
+
+def test_mixed_vs_oracle_held_suarez_g4():
+    wl = wls.HS_G4
+    p = Pair(wl, precision=thor.THOR_MIXED)
+    try:
+        X0 = p.oracle_initial()
+        ref = dc.run(p.model, X0, wl.n_large, wl.n_small, wl.dt)
+        thor.thor_step(p.state, wl.n_large, wl.n_small, wl.dt)
+        rep = field_report(p, p.get(), ref)
+    finally:
+        p.close()
+    out = os.path.join(os.path.dirname(os.path.dirname(__file__)), "gpurun_out")
+    if os.path.isdir(out):
+        json.dump(rep, open(os.path.join(out, "mixed_errors_g4.json"), "w"), indent=1)
+    print(rep)
+    for k, g in GATES.items():
+        assert rep[k] < g, (k, rep)

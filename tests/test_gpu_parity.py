@@ -158,3 +158,23 @@ def test_level_chunk_does_not_change_results(kchunk):
         _assert_close(p.get(), ref)
     finally:
         p.close()
+
+
+def test_nonfinite_watchdog():
+    """Fault injection on the host: a NaN written into the state through
+    thor_state_set makes thor_step report THOR_ENONFINITE (NaN arithmetic does
+    not fault the GPU)."""
+    wl = SMALL
+    p = Pair(wl)
+    try:
+        thor.thor_tune(p.state, thor.THOR_TUNE_CHECK_FINITE, 1)
+        thor.thor_step(p.state, 1, wl.n_small, wl.dt)            # clean: no error
+        X = p.get()
+        X.rho[3, 2] = np.nan
+        p.set(X)
+        with pytest.raises(thor.ThorError) as e:
+            thor.thor_step(p.state, 1, wl.n_small, wl.dt)
+        assert e.value.status == thor.THOR_ENONFINITE
+        assert thor.thor_diag(p.state)["nonfinite"] > 0
+    finally:
+        p.close()
