@@ -179,7 +179,7 @@ int thor_tune(thor_state* state, int knob, int value);
 enum {
   THOR_K_DERIVED = 0, THOR_K_LAP1, THOR_K_SLOW, THOR_K_SLOW_W, THOR_K_STAGE_INIT,
   THOR_K_SS_DIV, THOR_K_SS_GRAD, THOR_K_SS_MOM, THOR_K_SS_COL, THOR_K_STAGE_END,
-  THOR_K_PHYSICS, THOR_K_SS_FLUX, THOR_K_COUNT
+  THOR_K_PHYSICS, THOR_K_SS_FLUX, THOR_K_SS_FACTOR, THOR_K_COUNT
 };
 int thor_profile(thor_state* state, int enable);
 int thor_profile_read(thor_state* state, int kernel, double* total_ms, long long* launches);

@@ -231,6 +231,10 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   R** pc[] = {&P.rho, &P.mx, &P.my, &P.mz, &P.th, &P.p};
   for (R** p : pc) *p = cv.take<R>(C);
   P.w = cv.take<R>(F);
+  I.F.inv = cv.take<double>(F);
+  I.F.cf = cv.take<double>(F);
+  I.F.off = cv.take<double>(F);
+  I.F.junction = cv.take<double>(S);
   // tables
   I.G.nbr = cv.take<int>(6 * S);
   I.G.wdiv = cv.take<R>(21 * S);

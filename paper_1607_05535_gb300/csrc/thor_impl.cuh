@@ -103,6 +103,7 @@ struct Impl : ImplBase {
   Work<R> T;
   Slow<R> SL;
   Pert<R> P;
+  Fac F;
   int hyper = 1, divdamp = 1, forcing = 0;
   double diff_D = 0, dbar4 = 0, hj_dT = 300.0;
   // device allocations

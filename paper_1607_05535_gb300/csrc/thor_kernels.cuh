@@ -77,6 +77,12 @@ struct Phys {
   double Rd, cp, cv, gamma, kappa, g, omega, p_ref;
 };
 
+// Float64 factors of the per-stage vertical matrix: planes [nv + 1][colp]
+// (rows 1..nv-1 used) and one plane for the junction of the two sweeps
+struct Fac {
+  double *inv, *cf, *off, *junction;
+};
+
 // state in deviation form
 template <typename R>
 struct Xf {

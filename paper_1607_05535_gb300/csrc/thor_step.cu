@@ -341,9 +341,9 @@ __global__ void k_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R
   }
 }
 
-// HE-VI column step, part 2. Substituting Eqs. dens2 and pt2 into Eq. momr2
-// gives at the interior interfaces m = 1..nv-1 (rigid lid: W* = 0 at m = 0
-// and nv)
+// HE-VI column step, part 2 (matrix). Substituting Eqs. dens2 and pt2 into
+// Eq. momr2 gives at the interior interfaces m = 1..nv-1 (rigid lid: W* = 0
+// at m = 0 and nv)
 //   lo_m W_m-1 + di_m W_m + up_m W_m+1 = rh_m
 // with e_k = r^2/(rc_k^2 dz_k) at the bottom (sq_lo) and top (sq_hi)
 // interfaces of cell k, th_m = theta at interface m, w-/w+ the Lagrange
@@ -352,81 +352,126 @@ __global__ void k_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R
 //   di_m = 1 + dtau^2/dzc_m th_m (Pi_m sq_lo_m + Pi_m-1 sq_hi_m-1)
 //            - dtau^2 g (w- sq_hi_m-1 - w+ sq_lo_m)
 //   up_m = -dtau^2/dzc_m Pi_m sq_hi_m th_m+1 - dtau^2 g w+ sq_hi_m
-//   rh_m = W*_m + dtau S_W,m - dtau/dzc_m (c_m - c_m-1) - dtau g (w- a_m-1 + w+ a_m)
-// The coefficients are formed in the storage precision; the elimination is
-// a two-sided Thomas algorithm in float64: warp 0 eliminates rows 1..p
-// downwards, warp 1 rows nv-1..p+1 upwards (the two warps run on different
-// SM sub-partitions), they meet at rows p, p+1 and substitute back outwards.
-// Then rho* and Th* follow from Eqs. dens2 and pt2 and p* from the nonlinear
-// Eq. theta_to_p. One block = 32 columns x 2 warps.
+// The matrix depends only on the stage state (Pi, theta) and dtau, so it is
+// factorised once per RK stage and the factors serve every small step of
+// the stage. The factorisation is the matrix half of a two-sided Thomas
+// algorithm in float64: warp 0 eliminates rows 1..p downwards
+// (c'_m = up_m / (di_m - lo_m c'_m-1)), warp 1 rows nv-1..p+1 upwards
+// (e'_m = lo_m / (di_m - up_m e'_m+1)); the two warps run on different SM
+// sub-partitions. Stored per row: the pivot reciprocal, c' or e', and lo or
+// up; per column: 1 / (1 - c'_p e'_p+1) for the junction rows p, p+1.
 template <typename R>
-__global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs, Slow<R> SL,
-                                                 Pert<R> P, Work<R> T, double dtau) {
-  extern __shared__ double sm[];
+__global__ void __launch_bounds__(64) k_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> SL, Fac F,
+                                                  double dtau) {
   const int nv = G.nv, S = G.colp, N = nv - 1;
   const int tx = threadIdx.x & 31, half = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + tx;
   const bool valid = c < G.ncol;
-  const int cs = valid ? c : 0;          // padding lanes read column 0 and store nothing
-  double* scp = sm;                      // [nv + 1][32] c' (rows <= p) and e' (rows > p)
-  double* sdp = scp + (nv + 1) * 32;     // [nv + 1][32] d' / f', then W
-  double* sx = sdp + (nv + 1) * 32;      // [2][32] junction values
+  const int cs = valid ? c : 0;          // padding lanes compute on column 0 and store nothing
   const int p = N / 2 > 0 ? N / 2 : 1;
-  const R rdt = (R)dtau, g = (R)ph.g, dt2 = (R)(dtau * dtau);
-
-  // coefficients of interface m (1 <= m <= N)
-  auto coef = [&](int m, double& lo, double& di, double& up, double& rh) {
+  const R g = (R)ph.g, dt2 = (R)(dtau * dtau);
+  __shared__ double sj[2][32];
+  auto coef = [&](int m, double& lo, double& di, double& up) {
     const int i = m * S + cs;
-    const R pi_lo = ld(SL.pi + (i - S)), pi_hi = ld(SL.pi + (i));
-    const R wlo = ld(U.wlo + (m)), whi = ld(U.whi + (m)), dtz = dt2 * ld(U.inv_dzc + (m));
-    const R ql = ld(U.sq_lo + (m - 1)), qh = ld(U.sq_hi + (m - 1));    // cell m-1
-    const R pl = ld(U.sq_lo + (m)), ph_ = ld(U.sq_hi + (m));           // cell m
-    const R th_m = ld(SL.thi + (i));
+    const R pi_lo = ld(SL.pi + (i - S)), pi_hi = ld(SL.pi + i);
+    const R wlo = ld(U.wlo + m), whi = ld(U.whi + m), dtz = dt2 * ld(U.inv_dzc + m);
+    const R ql = ld(U.sq_lo + (m - 1)), qh = ld(U.sq_hi + (m - 1));   // cell m-1
+    const R pl = ld(U.sq_lo + m), ph_ = ld(U.sq_hi + m);              // cell m
+    const R th_m = ld(SL.thi + i);
     R lower = 0, upper = 0;
     if (m > 1) lower = (-dtz * pi_lo * ld(SL.thi + (i - S)) + dt2 * g * wlo) * ql;
     if (m < N) upper = (-dtz * pi_hi * ld(SL.thi + (i + S)) - dt2 * g * whi) * ph_;
     lo = (double)lower;
     up = (double)upper;
     di = (double)(R(1) + dtz * th_m * (pi_hi * pl + pi_lo * qh) - dt2 * g * (wlo * qh - whi * pl));
-    rh = (double)(ld(P.w + (i)) + rdt * ld(SL.sw + (i)) - rdt * ld(U.inv_dzc + (m)) * (ld(T.cc + (i)) - ld(T.cc + (i - S)))
-                  - rdt * g * (wlo * ld(T.ca + (i - S)) + whi * ld(T.ca + (i))));
   };
   auto inv_of = [](double den) { return sizeof(R) == sizeof(double) ? 1.0 / den : rcp64_1(den); };
-
-  // elimination
+  double last = 0.0;
   if (half == 0) {
-    double c1 = 0.0, d1 = 0.0;
-#pragma unroll 2
     for (int m = 1; m <= p; ++m) {
-      double lo, di, up, rh;
-      coef(m, lo, di, up, rh);
-      const double inv = inv_of(di - lo * c1);
-      c1 = up * inv;
-      d1 = (rh - lo * d1) * inv;
-      scp[m * 32 + tx] = c1;
+      double lo, di, up;
+      coef(m, lo, di, up);
+      const double inv = inv_of(di - lo * last);
+      last = up * inv;
+      if (valid) {
+        F.inv[m * S + c] = inv;
+        F.cf[m * S + c] = last;
+        F.off[m * S + c] = lo;
+      }
+    }
+  } else {
+    for (int m = N; m > p; --m) {
+      double lo, di, up;
+      coef(m, lo, di, up);
+      const double inv = inv_of(di - up * last);
+      last = lo * inv;
+      if (valid) {
+        F.inv[m * S + c] = inv;
+        F.cf[m * S + c] = last;
+        F.off[m * S + c] = up;
+      }
+    }
+  }
+  sj[half][tx] = last;     // c'_p (warp 0) and e'_p+1 (warp 1)
+  __syncthreads();
+  if (half == 0 && valid) F.junction[c] = p < N ? 1.0 / (1.0 - sj[0][tx] * sj[1][tx]) : 1.0;
+}
+
+// HE-VI column step, part 3 (every small step). The right-hand side
+//   rh_m = W*_m + dtau S_W,m - dtau/dzc_m (c_m - c_m-1) - dtau g (w- a_m-1 + w+ a_m)
+// goes through the stored factors in float64 (d'_m = (rh_m - lo_m d'_m-1) / piv_m
+// downwards, f'_m = (rh_m - up_m f'_m+1) / piv_m upwards, the junction rows
+// x_p = (d'_p - c'_p f'_p+1) / (1 - c'_p e'_p+1), x_p+1 = f'_p+1 - e'_p+1 x_p,
+// then back substitution outwards); then rho* and Th* follow from Eqs. dens2
+// and pt2 and p* from the nonlinear Eq. theta_to_p. One block = 32 columns
+// x 2 warps.
+template <typename R>
+__global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs, Slow<R> SL,
+                                                 Pert<R> P, Work<R> T, Fac F, double dtau) {
+  extern __shared__ double sm[];
+  const int nv = G.nv, S = G.colp, N = nv - 1;
+  const int tx = threadIdx.x & 31, half = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + tx;
+  const bool valid = c < G.ncol;
+  const int cs = valid ? c : 0;          // padding lanes read column 0 and store nothing
+  double* sdp = sm;                      // [nv + 1][32] d' / f', then W
+  double* sx = sdp + (nv + 1) * 32;      // [2][32] junction values
+  const int p = N / 2 > 0 ? N / 2 : 1;
+  const R rdt = (R)dtau, g = (R)ph.g;
+
+  auto rhs = [&](int m) {
+    const int i = m * S + cs;
+    const R wlo = ld(U.wlo + m), whi = ld(U.whi + m);
+    return (double)(ld(P.w + i) + rdt * ld(SL.sw + i)
+                    - rdt * ld(U.inv_dzc + m) * (ld(T.cc + i) - ld(T.cc + (i - S)))
+                    - rdt * g * (wlo * ld(T.ca + (i - S)) + whi * ld(T.ca + i)));
+  };
+  // forward recurrences through the stored factors
+  if (half == 0) {
+    double d1 = 0.0;
+#pragma unroll 4
+    for (int m = 1; m <= p; ++m) {
+      const int i = m * S + cs;
+      d1 = (rhs(m) - ld(F.off + i) * d1) * ld(F.inv + i);
       sdp[m * 32 + tx] = d1;
     }
   } else {
-    double e1 = 0.0, f1 = 0.0;
-#pragma unroll 2
+    double f1 = 0.0;
+#pragma unroll 4
     for (int m = N; m > p; --m) {
-      double lo, di, up, rh;
-      coef(m, lo, di, up, rh);
-      const double inv = inv_of(di - up * e1);
-      e1 = lo * inv;
-      f1 = (rh - up * f1) * inv;
-      scp[m * 32 + tx] = e1;
+      const int i = m * S + cs;
+      f1 = (rhs(m) - ld(F.off + i) * f1) * ld(F.inv + i);
       sdp[m * 32 + tx] = f1;
     }
   }
   __syncthreads();
-  // junction rows p and p+1: x_p = d'_p - c'_p x_p+1, x_p+1 = f'_p+1 - e'_p+1 x_p
   if (half == 0) {
+    const int ip = p * S + cs;
     double xp, xq = 0.0;
     if (p < N) {
-      const double cp_ = scp[p * 32 + tx], dp_ = sdp[p * 32 + tx];
-      const double eq = scp[(p + 1) * 32 + tx], fq = sdp[(p + 1) * 32 + tx];
-      xp = (dp_ - cp_ * fq) / (1.0 - cp_ * eq);
+      const double cp_ = ld(F.cf + ip), eq = ld(F.cf + (ip + S));
+      const double dp_ = sdp[p * 32 + tx], fq = sdp[(p + 1) * 32 + tx];
+      xp = (dp_ - cp_ * fq) * ld(F.junction + cs);
       xq = fq - eq * xp;
     } else {
       xp = sdp[p * 32 + tx];
@@ -440,7 +485,7 @@ __global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<
     double x = sx[tx];
     sdp[p * 32 + tx] = x;
     for (int m = p - 1; m >= 1; --m) {
-      x = sdp[m * 32 + tx] - scp[m * 32 + tx] * x;
+      x = sdp[m * 32 + tx] - ld(F.cf + (m * S + cs)) * x;
       sdp[m * 32 + tx] = x;
     }
     sdp[tx] = 0.0;                 // bottom interface
@@ -448,7 +493,7 @@ __global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<
     double x = sx[32 + tx];
     if (p < N) sdp[(p + 1) * 32 + tx] = x;
     for (int m = p + 2; m <= N; ++m) {
-      x = sdp[m * 32 + tx] - scp[m * 32 + tx] * x;
+      x = sdp[m * 32 + tx] - ld(F.cf + (m * S + cs)) * x;
       sdp[m * 32 + tx] = x;
     }
     sdp[nv * 32 + tx] = 0.0;       // top interface
@@ -460,15 +505,15 @@ __global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<
     for (int k = half; k < nv; k += 2) {
       const int i = k * S + c;
       const R wl = (R)sdp[k * 32 + tx], wh = (R)sdp[(k + 1) * 32 + tx];
-      const R thl = k > 0 ? ld(SL.thi + (i)) : R(0);
+      const R thl = k > 0 ? ld(SL.thi + i) : R(0);
       const R thh = k + 1 < nv ? ld(SL.thi + (i + S)) : R(0);
-      const R el = ld(U.sq_lo + (k)), eh = ld(U.sq_hi + (k));
-      R th_new = ld(T.cb + (i)) - rdt * (eh * thh * wh - el * thl * wl);
-      P.rho[i] = ld(T.ca + (i)) - rdt * (eh * wh - el * wl);
+      const R el = ld(U.sq_lo + k), eh = ld(U.sq_hi + k);
+      R th_new = ld(T.cb + i) - rdt * (eh * thh * wh - el * thl * wl);
+      P.rho[i] = ld(T.ca + i) - rdt * (eh * wh - el * wl);
       P.th[i] = th_new;
       // p* = EOS(Th^(s) + Th*) - p^(s) = p^(s) ((1 + Th*/Th^(s))^gamma - 1)
-      R ps = ld(U.pb + (k)) + ld(T.pp + (i));
-      R ths = ld(U.thb + (k)) + ld(Xs.th + (i));
+      R ps = ld(U.pb + k) + ld(T.pp + i);
+      R ths = ld(U.thb + k) + ld(Xs.th + i);
       P.p[i] = ps * rexpm1<R>(gamma * rlog1p<R>(th_new / ths));
       if (k >= 1) P.w[i] = wl;
     }
@@ -567,7 +612,7 @@ void Impl<R>::launch_2d(int nplanes, int kchunk, dim3& grid) const {
   grid = dim3((G.ncol + kBlock - 1) / kBlock, (nplanes + kchunk - 1) / kchunk);
 }
 
-size_t solve_smem_bytes(int nv) { return (size_t)(2 * (nv + 1) + 2) * 32 * sizeof(double); }
+size_t solve_smem_bytes(int nv) { return (size_t)((nv + 1) + 2) * 32 * sizeof(double); }
 
 template <typename R>
 int col_kernel_setup(int nv) {
@@ -610,7 +655,10 @@ int Impl<R>::large_step(double dt, int n_small) {
     mark(THOR_K_STAGE_INIT, true);
     k_stage_init<R><<<g2i, kBlock, 0, stream>>>(G, U, ph, Xt, Xs, T, P, kc);
     mark(THOR_K_STAGE_INIT, false);
-    launches += 3;
+    mark(THOR_K_SS_FACTOR, true);
+    k_ss_factor<R><<<gsolve, 64, 0, stream>>>(G, U, ph, SL, F, dts[s]);
+    mark(THOR_K_SS_FACTOR, false);
+    launches += 4;
     for (int j = 0; j < nsub[s]; ++j) {
       if (divdamp) {
         mark(THOR_K_SS_DIV, true);
@@ -628,7 +676,7 @@ int Impl<R>::large_step(double dt, int n_small) {
       k_ss_flux<R><<<g2, kBlock, 0, stream>>>(G, U, SL, P, T, (R)dts[s], kc);
       mark(THOR_K_SS_FLUX, false);
       mark(THOR_K_SS_COL, true);
-      k_ss_solve<R><<<gsolve, 64, solve_smem, stream>>>(G, U, ph, Xs, SL, P, T, dts[s]);
+      k_ss_solve<R><<<gsolve, 64, solve_smem, stream>>>(G, U, ph, Xs, SL, P, T, F, dts[s]);
       mark(THOR_K_SS_COL, false);
       launches += 3;
     }
