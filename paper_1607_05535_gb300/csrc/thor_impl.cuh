@@ -20,6 +20,7 @@ struct Work {
   R *dd;                           // 3-D divergence (small step)
   R *gx, *gy, *gz;                 // its horizontal gradient
   R *ca, *cb, *cc;                 // per-cell parts of the column equations (a, b, c)
+  R *dhm;                          // horizontal divergence of the new M*
 };
 
 // Slow tendencies and small-step coefficients of a stage

@@ -99,7 +99,7 @@ __global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk) 
 // stage state (divergence damping), the radial advection+Coriolis and
 // Pi = gamma p / rho theta.
 template <typename R>
-__global__ void k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
+__global__ void __launch_bounds__(kBlock, 4) k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
                        int kchunk) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
@@ -335,6 +335,7 @@ __global__ void k_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R
     const R inv_r = ld(U.inv_rc + (k));
     R thk = ld(P.th + (i));
     R bk = thk + dtau * (ld(SL.sth + (i)) - dht * inv_r);
+    T.dhm[i] = dh * inv_r;
     T.ca[i] = ld(P.rho + (i)) + dtau * (ld(SL.srho + (i)) - dh * inv_r);
     T.cb[i] = bk;
     T.cc[i] = ld(P.p + (i)) + ld(SL.pi + (i)) * (bk - thk);
@@ -427,7 +428,8 @@ __global__ void __launch_bounds__(64) k_ss_factor(Geo<R> G, VR<R> U, Phys ph, Sl
 // x 2 warps.
 template <typename R>
 __global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs, Slow<R> SL,
-                                                 Pert<R> P, Work<R> T, Fac F, double dtau) {
+                                                 Pert<R> P, Work<R> T, Fac F, double dtau,
+                                                 int want_div) {
   extern __shared__ double sm[];
   const int nv = G.nv, S = G.colp, N = nv - 1;
   const int tx = threadIdx.x & 31, half = threadIdx.x >> 5;
@@ -516,6 +518,9 @@ __global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<
       R ths = ld(U.thb + k) + ld(Xs.th + i);
       P.p[i] = ps * rexpm1<R>(gamma * rlog1p<R>(th_new / ths));
       if (k >= 1) P.w[i] = wl;
+      // 3-D divergence of the new total momentum, for the next small step's
+      // divergence damping: D^(s) + div_h M* (from k_ss_flux) + div_v W*
+      if (want_div) T.dd[i] = ld(SL.dsc + i) + ld(T.dhm + i) + (eh * wh - el * wl);
     }
   }
 }
@@ -661,13 +666,16 @@ int Impl<R>::large_step(double dt, int n_small) {
     launches += 4;
     for (int j = 0; j < nsub[s]; ++j) {
       if (divdamp) {
-        mark(THOR_K_SS_DIV, true);
-        k_ss_div<R><<<g2, kBlock, 0, stream>>>(G, U, SL, P, T, kc);
-        mark(THOR_K_SS_DIV, false);
+        if (j == 0) {   // later small steps get D from the previous k_ss_solve
+          mark(THOR_K_SS_DIV, true);
+          k_ss_div<R><<<g2, kBlock, 0, stream>>>(G, U, SL, P, T, kc);
+          mark(THOR_K_SS_DIV, false);
+          ++launches;
+        }
         mark(THOR_K_SS_GRAD, true);
         k_ss_grad<R><<<g2, kBlock, 0, stream>>>(G, U, T, kc);
         mark(THOR_K_SS_GRAD, false);
-        launches += 2;
+        ++launches;
       }
       mark(THOR_K_SS_MOM, true);
       k_ss_mom<R><<<g2, kBlock, 0, stream>>>(G, U, SL, P, T, (R)dts[s], Kd, divdamp, kc);
@@ -676,7 +684,8 @@ int Impl<R>::large_step(double dt, int n_small) {
       k_ss_flux<R><<<g2, kBlock, 0, stream>>>(G, U, SL, P, T, (R)dts[s], kc);
       mark(THOR_K_SS_FLUX, false);
       mark(THOR_K_SS_COL, true);
-      k_ss_solve<R><<<gsolve, 64, solve_smem, stream>>>(G, U, ph, Xs, SL, P, T, F, dts[s]);
+      const int want_div = divdamp && j + 1 < nsub[s];
+      k_ss_solve<R><<<gsolve, 64, solve_smem, stream>>>(G, U, ph, Xs, SL, P, T, F, dts[s], want_div);
       mark(THOR_K_SS_COL, false);
       launches += 3;
     }
