@@ -131,32 +131,17 @@ __global__ void __launch_bounds__(kBlock, 4) k_slow(Geo<R> G, VR<R> U, Phys ph, 
       Fth = thfull / (gamma * p) * Fp;
     }
 
-    // horizontal fluxes at the 7 points: advection div_h(M v_j) of the
-    // Cartesian components (Sec. 3), div_h(M), div_h(theta M), grad_h(p')
-    R ahx = 0, ahy = 0, ahz = 0, dh = 0, dht = 0, gx = 0, gy = 0, gz = 0;
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-      const int q = o + nb.n[j];
-      const R f = wd.x[j] * ld(X.mx + q) + wd.y[j] * ld(X.my + q) + wd.z[j] * ld(X.mz + q);
-      ahx += f * ld(T.vx + q);
-      ahy += f * ld(T.vy + q);
-      ahz += f * ld(T.vz + q);
-      dh += f;
-      dht += f * ld(T.theta + q);
-      const R pq = ld(T.pp + q);
-      gx += wg.x[j] * pq;
-      gy += wg.y[j] * pq;
-      gz += wg.z[j] * pq;
-    }
-    const R wlo_w = ld(X.w + (i)), whi_w = ld(X.w + (i + S));
+    // advection div(rho v v_j) of the Cartesian components (Sec. 3)
     const R* vs[3] = {T.vx, T.vy, T.vz};
-    R A[3] = {ahx * inv_r, ahy * inv_r, ahz * inv_r};
+    R A[3];
+    R wlo_w = ld(X.w + (i)), whi_w = ld(X.w + (i + S));
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
+      R ah = div7_scaled(wd, nb, vs[j] + o, X.mx + o, X.my + o, X.mz + o) * inv_r;
       R vlo = 0, vhi = 0;
-      if (k >= 1) vlo = ld(U.wlo + (k)) * ld(vs[j] + (i - S)) + ld(U.whi + (k)) * ld(vs[j] + (i));
-      if (k + 1 < G.nv) vhi = ld(U.wlo + (k + 1)) * ld(vs[j] + (i)) + ld(U.whi + (k + 1)) * ld(vs[j] + (i + S));
-      A[j] += sqh * whi_w * vhi - sql * wlo_w * vlo;
+      if (k >= 1) vlo = ld(U.wlo + (k)) * vs[j][i - S] + ld(U.whi + (k)) * vs[j][i];
+      if (k + 1 < G.nv) vhi = ld(U.wlo + (k + 1)) * vs[j][i] + ld(U.whi + (k + 1)) * vs[j][i + S];
+      A[j] = ah + sqh * whi_w * vhi - sql * wlo_w * vlo;
     }
     // Coriolis 2 Omega z x (rho v) with the full momentum
     R wc = ld(U.clo + (k)) * wlo_w + ld(U.chi + (k)) * whi_w;
@@ -165,20 +150,22 @@ __global__ void __launch_bounds__(kBlock, 4) k_slow(Geo<R> G, VR<R> U, Phys ph, 
     A[0] += -two_om * fy;
     A[1] += two_om * fx;
     R acr = A[0] * rx + A[1] * ry + A[2] * rz;
-    R ahx2 = A[0] - acr * rx, ahy2 = A[1] - acr * ry, ahz2 = A[2] - acr * rz;
+    R ahx = A[0] - acr * rx, ahy = A[1] - acr * ry, ahz = A[2] - acr * rz;
 
-    R smx = -gx * inv_r - ahx2 + FMx, smy = -gy * inv_r - ahy2 + FMy, smz = -gz * inv_r - ahz2 + FMz;
+    R gx, gy, gz;
+    grad7(wg, nb, T.pp + o, gx, gy, gz);
+    R smx = -gx * inv_r - ahx + FMx, smy = -gy * inv_r - ahy + FMy, smz = -gz * inv_r - ahz + FMz;
     project(rx, ry, rz, smx, smy, smz);
     SL.smx[i] = smx;
     SL.smy[i] = smy;
     SL.smz[i] = smz;
 
-    dh *= inv_r;
+    R dh = div7(wd, nb, X.mx + o, X.my + o, X.mz + o) * inv_r;
     R dv = sqh * whi_w - sql * wlo_w;
     SL.srho[i] = -dh - dv + Frho;
     SL.dsc[i] = dh + dv;
 
-    dht *= inv_r;
+    R dht = div7_scaled(wd, nb, T.theta + o, X.mx + o, X.my + o, X.mz + o) * inv_r;
     R thlo = 0, thhi = 0;
     if (k >= 1) thlo = ld(U.wlo + (k)) * ld(T.theta + (i - S)) + ld(U.whi + (k)) * ld(T.theta + (i));
     if (k + 1 < G.nv) thhi = ld(U.wlo + (k + 1)) * ld(T.theta + (i)) + ld(U.whi + (k + 1)) * ld(T.theta + (i + S));
