@@ -50,6 +50,22 @@ def _env_int(k, d):
         return d
 
 
+def _traffic(kernel):
+    """ncu DRAM bytes per launch of ``kernel`` from the committed profile, or
+    None if that profile was taken of another version of the kernel source."""
+    import hashlib
+    try:
+        kv = dict(l.split(None, 1) for l in open(os.path.join(ROOT, "profiles", "traffic_hs_g6_L32_mixed.txt"))
+                  if l.strip() and not l.startswith("#"))
+        src = os.path.join(ROOT, "paper_1607_05535_gb300", "csrc", "thor_step.cu")
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        if kv["kernel"].strip() == kernel and kv["thor_step_cu_sha1"].strip() == sha:
+            return float(kv["bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -324,7 +340,7 @@ def run_thor(args):
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "traffic": _traffic(dom), "algorithmic_bytes_per_launch": bytes_per_launch,
                      "us_per_launch": 1e3 * tot / n},
         "kernels": kernels,
         "clocks": clocks,
