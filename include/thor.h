@@ -186,6 +186,61 @@ int thor_profile_read(thor_state* state, int kernel, double* total_ms, long long
 
 void thor_state_destroy(thor_state* state);
 
+/* --------------------------------------------------------- learned closure */
+
+/* A per-column MLP closure (an extension; the paper has no learned part).
+ * Network: sizes[0] inputs, sizes[1..n_sizes-2] hidden ReLU layers,
+ * sizes[n_sizes-1] linear outputs; y = W_L^T relu(... relu(W_1^T x + b_1)) + b_L
+ * with W_l stored [sizes[l]][sizes[l+1]] row-major. float32 master weights;
+ * the products run on the tensor cores with bfloat16 weights and layer
+ * inputs and float32 accumulation. Flat parameter order: W_0, b_0, W_1, b_1, ...
+ * Initial weights He-uniform from SplitMix64(seed), biases 0. All x, y, dy,
+ * target, grad and loss pointers are device pointers (float32, row-major
+ * [m][features]); the MLP's stream is `stream` (the state's stream once
+ * attached). sizes[i] in [1, 8192], 2 <= n_sizes <= 16, 1 <= m <= max_batch. */
+typedef struct thor_mlp thor_mlp;
+int thor_mlp_create(const int* sizes, int n_sizes, int max_batch, unsigned long long seed, void* stream,
+                    thor_mlp** out);
+int thor_mlp_info(const thor_mlp* mlp, size_t* nparam);
+int thor_mlp_get_params(thor_mlp* mlp, float* host, size_t n);
+/* Sets the float32 master weights and resets the Adam moments. */
+int thor_mlp_set_params(thor_mlp* mlp, const float* host, size_t n);
+/* y = MLP(x) for m rows. */
+int thor_mlp_forward(thor_mlp* mlp, const float* x, int m, float* y);
+/* Gradient of sum(y * dy) with respect to every parameter (flat order), for
+ * the batch of the last thor_mlp_forward (same m). The output gradient and
+ * the hidden-layer gradients enter the weight products in bfloat16. */
+int thor_mlp_backward(thor_mlp* mlp, const float* dy, int m, float* grad);
+/* One training step on a batch: forward, mean-squared-error loss
+ * sum((y - target)^2)/(m n_out) (written to *loss if loss != NULL), backward,
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with rate lr. */
+int thor_mlp_train_step(thor_mlp* mlp, const float* x, const float* target, int m, float lr, float* loss);
+void thor_mlp_destroy(thor_mlp* mlp);
+
+/* Closure features of a state: per column c, x[c][f*nv + k] is field f at
+ * level k and x[c][5*nv + f*nv + k] its mean over the column's neighbours,
+ * for f = rho - rho_ref, M_x, M_y, M_z, rho theta - reference (the state's
+ * stored deviations); each feature j is normalised as (x - mean[j]) / std[j].
+ * x: device [ncol][10*nv]. */
+int thor_closure_features(thor_state* state, const float* mean, const float* std, float* x);
+
+/* Attach an MLP (sizes[0] = 10*nv, last size = 5*nv) as a closure: after
+ * every large step, y = MLP(features) and field_f(k) += dt * (y[f*nv + k] *
+ * out_std + out_mean) (momentum correction projected onto the tangent
+ * plane). The four normalisation arrays are caller-owned device arrays that
+ * must stay valid while attached. mlp = NULL detaches (plain method). */
+int thor_closure_attach(thor_state* state, thor_mlp* mlp, const float* in_mean, const float* in_std,
+                        const float* out_mean, const float* out_std);
+
+/* Area-weighted average of a fine state onto a coarse one: every coarse
+ * column gets the mean of the fine columns mapped to it (fine_to_coarse,
+ * host, one coarse column index per fine column), weighted by the fine
+ * control-volume areas, for all levels of rho, M (projected on the coarse
+ * tangent plane), W and rho theta. Both states must share precision, nv,
+ * z_top, planet and initial reference column; every coarse column needs at
+ * least one fine member. Synchronous. */
+int thor_coarse_grain(thor_state* fine, thor_state* coarse, const int* fine_to_coarse, size_t nfine);
+
 /* ------------------------------------------------------- allocation-free */
 
 /* Allocation-free float64 mass sum: *mass_out = sum_i rho[i] * volume[i]

@@ -27,7 +27,9 @@ EXPORTED = [
     "thor_grid_neighbours", "thor_grid_areas", "thor_grid_destroy", "thor_state_init",
     "thor_step", "thor_diag", "thor_state_get", "thor_state_set", "thor_launch_count",
     "thor_tune", "thor_profile", "thor_profile_read", "thor_state_destroy",
-    "thor_mass_noalloc",
+    "thor_mass_noalloc", "thor_mlp_create", "thor_mlp_info", "thor_mlp_get_params",
+    "thor_mlp_set_params", "thor_mlp_forward", "thor_mlp_backward", "thor_mlp_train_step",
+    "thor_mlp_destroy", "thor_closure_features", "thor_closure_attach", "thor_coarse_grain",
 ]
 
 # kernel ids of thor_profile_read
@@ -97,6 +99,17 @@ def _load():
                                   ctypes.POINTER(ctypes.c_longlong)]),
         "thor_state_destroy": (None, [P]),
         "thor_mass_noalloc": (I, [P, P, Z, P, P]),
+        "thor_mlp_create": (I, [P, I, I, ctypes.c_ulonglong, P, ctypes.POINTER(P)]),
+        "thor_mlp_info": (I, [P, ctypes.POINTER(ctypes.c_size_t)]),
+        "thor_mlp_get_params": (I, [P, P, Z]),
+        "thor_mlp_set_params": (I, [P, P, Z]),
+        "thor_mlp_forward": (I, [P, P, I, P]),
+        "thor_mlp_backward": (I, [P, P, I, P]),
+        "thor_mlp_train_step": (I, [P, P, P, I, ctypes.c_float, P]),
+        "thor_mlp_destroy": (None, [P]),
+        "thor_closure_features": (I, [P, P, P, P]),
+        "thor_closure_attach": (I, [P, P, P, P, P, P]),
+        "thor_coarse_grain": (I, [P, P, P, Z]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -239,3 +252,63 @@ def thor_mass_noalloc(rho, volume, mass_out, stream=None):
         raise ValueError("rho and volume differ in size")
     _check(_lib.thor_mass_noalloc(_ptr(rho), _ptr(volume), n, _ptr(mass_out),
                                   ctypes.c_void_p(stream or 0)), "thor_mass_noalloc")
+
+
+# ------------------------------------------------------------- learned closure
+
+def thor_mlp_create(sizes, max_batch, seed=0, stream=None):
+    arr = (ctypes.c_int * len(sizes))(*sizes)
+    out = ctypes.c_void_p()
+    _check(_lib.thor_mlp_create(arr, len(sizes), max_batch, seed, ctypes.c_void_p(stream or 0),
+                                ctypes.byref(out)), "thor_mlp_create")
+    return out
+
+
+def thor_mlp_info(mlp):
+    n = ctypes.c_size_t()
+    _check(_lib.thor_mlp_info(mlp, ctypes.byref(n)), "thor_mlp_info")
+    return n.value
+
+
+def thor_mlp_get_params(mlp):
+    out = np.empty(thor_mlp_info(mlp), dtype=np.float32)
+    _check(_lib.thor_mlp_get_params(mlp, _ptr(out), out.size), "thor_mlp_get_params")
+    return out
+
+
+def thor_mlp_set_params(mlp, host):
+    a = np.ascontiguousarray(host, dtype=np.float32)
+    _check(_lib.thor_mlp_set_params(mlp, _ptr(a), a.size), "thor_mlp_set_params")
+
+
+def thor_mlp_forward(mlp, x, y):
+    """x, y: float32 device tensors [m][n_in], [m][n_out]."""
+    _check(_lib.thor_mlp_forward(mlp, _ptr(x), x.shape[0], _ptr(y)), "thor_mlp_forward")
+
+
+def thor_mlp_backward(mlp, dy, grad):
+    _check(_lib.thor_mlp_backward(mlp, _ptr(dy), dy.shape[0], _ptr(grad)), "thor_mlp_backward")
+
+
+def thor_mlp_train_step(mlp, x, target, lr, loss=None):
+    _check(_lib.thor_mlp_train_step(mlp, _ptr(x), _ptr(target), x.shape[0], lr,
+                                    _ptr(loss) if loss is not None else None), "thor_mlp_train_step")
+
+
+def thor_mlp_destroy(mlp):
+    _lib.thor_mlp_destroy(mlp)
+
+
+def thor_closure_features(state, mean, std, x):
+    _check(_lib.thor_closure_features(state, _ptr(mean), _ptr(std), _ptr(x)), "thor_closure_features")
+
+
+def thor_closure_attach(state, mlp, in_mean=None, in_std=None, out_mean=None, out_std=None):
+    p = lambda t: _ptr(t) if t is not None else None
+    _check(_lib.thor_closure_attach(state, mlp, p(in_mean), p(in_std), p(out_mean), p(out_std)),
+           "thor_closure_attach")
+
+
+def thor_coarse_grain(fine, coarse, fine_to_coarse):
+    a = np.ascontiguousarray(fine_to_coarse, dtype=np.int32)
+    _check(_lib.thor_coarse_grain(fine, coarse, _ptr(a), a.size), "thor_coarse_grain")

@@ -11,16 +11,7 @@
 #include "grid.h"
 #include "thor_impl.cuh"
 
-struct thor_grid {
-  thor::HostGrid h;
-};
-
-struct thor_state {
-  thor_grid* grid = nullptr;
-  int precision = THOR_FP64;
-  int check_finite = 0;
-  std::unique_ptr<thor::ImplBase> impl;
-};
+#include "thor_state.h"
 
 namespace thor {
 template <typename R>
@@ -634,7 +625,15 @@ int thor_state_init(thor_grid* grid, const thor_planet* pl, const thor_init* in,
 
 int thor_step(thor_state* s, int n_large, int n_small, double dt) {
   if (!s || n_large < 0 || n_small < 2 || (n_small % 2) || !(dt > 0)) return THOR_EINVAL;
-  int rc = s->impl->step(n_large, n_small, dt);
+  int rc = THOR_OK;
+  if (s->closure.net) {
+    for (int i = 0; i < n_large && !rc; ++i) {
+      rc = s->impl->step(1, n_small, dt);
+      if (!rc) rc = thor::closure_apply(s, dt);
+    }
+  } else {
+    rc = s->impl->step(n_large, n_small, dt);
+  }
   if (rc || !s->check_finite) return rc;
   double v[8];
   long long nf = 0;
@@ -705,6 +704,10 @@ int thor_profile_read(thor_state* s, int kernel, double* total_ms, long long* la
   return s->impl->prof_read(kernel, total_ms, launches) ? THOR_ECUDA : THOR_OK;
 }
 
-void thor_state_destroy(thor_state* s) { delete s; }
+void thor_state_destroy(thor_state* s) {
+  if (!s) return;
+  thor::closure_release(s);
+  delete s;
+}
 
 }  // extern "C"

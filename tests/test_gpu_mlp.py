@@ -1,0 +1,113 @@
+"""The BF16 tensor-core MLP kernels against the float64 MLP oracle (same
+bfloat16 roundings), and training progress."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1607_05535_gb300 as thor
+from oracle import mlp as om
+
+SIZES = [320, 256, 256, 256, 160]
+
+
+def _flat(params):
+    return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in params]).astype(np.float32)
+
+
+def _unflat(v, sizes):
+    out, o = [], 0
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        W = v[o:o + a * b].reshape(a, b); o += a * b
+        bb = v[o:o + b]; o += b
+        out.append((W.astype(np.float64), bb.astype(np.float64)))
+    return out
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("m", [64, 200, 1000])
+def test_forward_and_gradients_match_oracle(m):
+    rng = np.random.default_rng(3)
+    params = om.init_params(SIZES, rng)
+    params = [(W, 0.05 * rng.standard_normal(W.shape[1])) for W, _ in params]
+    flat = _flat(params)
+    params32 = _unflat(flat, SIZES)          # exactly what the GPU holds
+    x = rng.standard_normal((m, SIZES[0])).astype(np.float32)
+    dy = rng.standard_normal((m, SIZES[-1])).astype(np.float32)
+    net = thor.thor_mlp_create(SIZES, 1024, seed=1)
+    try:
+        thor.thor_mlp_set_params(net, flat)
+        xd = torch.tensor(x, device="cuda")
+        yd = torch.empty((m, SIZES[-1]), dtype=torch.float32, device="cuda")
+        thor.thor_mlp_forward(net, xd, yd)
+        gd = torch.empty(flat.size, dtype=torch.float32, device="cuda")
+        thor.thor_mlp_backward(net, torch.tensor(dy, device="cuda"), gd)
+        torch.cuda.synchronize()
+        y_ref, cache = om.forward(params32, x.astype(np.float64))
+        grads = om.backward(params32, cache, dy.astype(np.float64))
+        assert _rel(yd.cpu().numpy(), y_ref) < 1e-2
+        g = _unflat(gd.cpu().numpy(), SIZES)
+        for (gW, gb), (rW, rb) in zip(g, grads):
+            assert _rel(gW, rW) < 2e-2
+            assert _rel(gb, rb) < 2e-2
+    finally:
+        thor.thor_mlp_destroy(net)
+
+
+def test_training_reduces_loss():
+    """Fit a fixed random smooth target; the GPU Adam steps lower the loss."""
+    rng = np.random.default_rng(4)
+    m = 1024
+    x = rng.standard_normal((m, SIZES[0])).astype(np.float32)
+    A = rng.standard_normal((SIZES[0], SIZES[-1])).astype(np.float32) / np.sqrt(SIZES[0])
+    t = np.tanh(x @ A).astype(np.float32)
+    net = thor.thor_mlp_create(SIZES, m, seed=7)
+    try:
+        xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        losses = []
+        for it in range(300):
+            thor.thor_mlp_train_step(net, xd, td, 1e-3, loss)
+            if it % 50 == 0 or it == 299:
+                torch.cuda.synchronize()
+                losses.append(float(loss.item()))
+        assert losses[-1] < 0.2 * losses[0], losses
+    finally:
+        thor.thor_mlp_destroy(net)
+
+
+def test_train_step_matches_oracle_adam():
+    """One GPU training step equals the oracle's MSE gradient + Adam step on
+    the same bf16-rounded network (float32 vs float64 arithmetic)."""
+    rng = np.random.default_rng(5)
+    sizes = [40, 64, 16]
+    params = om.init_params(sizes, rng)
+    flat = _flat(params)
+    p32 = _unflat(flat, sizes)
+    m = 96
+    x = rng.standard_normal((m, sizes[0])).astype(np.float32)
+    t = rng.standard_normal((m, sizes[-1])).astype(np.float32)
+    net = thor.thor_mlp_create(sizes, 128, seed=0)
+    try:
+        thor.thor_mlp_set_params(net, flat)
+        thor.thor_mlp_train_step(net, torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda"), 1e-2)
+        new = thor.thor_mlp_get_params(net)
+        y, cache = om.forward(p32, x.astype(np.float64))
+        grads = om.backward(p32, cache, om.mse_grad(y, t))
+        state = [(np.zeros_like(W), np.zeros_like(W), np.zeros_like(b), np.zeros_like(b)) for W, b in p32]
+        ref = _flat(om.adam(p32, grads, state, 1e-2, 1))
+        # a first Adam step moves each parameter by about lr * sign(g): compare the moves
+        move, ref_move = new - flat, ref - flat
+        agree = np.mean(np.sign(move) == np.sign(ref_move))
+        assert agree > 0.97, agree
+        assert np.allclose(np.abs(move[np.abs(ref_move) > 5e-3]), 1e-2, rtol=0.05)
+    finally:
+        thor.thor_mlp_destroy(net)
