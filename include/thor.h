@@ -218,7 +218,8 @@ int thor_mlp_train_step(thor_mlp* mlp, const float* x, const float* target, int 
 void thor_mlp_destroy(thor_mlp* mlp);
 
 /* Closure features of a state: per column c, x[c][f*nv + k] is field f at
- * level k and x[c][5*nv + f*nv + k] its mean over the column's neighbours,
+ * level k and x[c][5*nv + f*nv + k] its mean over the column's neighbours
+ * minus its value at c,
  * for f = rho - rho_ref, M_x, M_y, M_z, rho theta - reference (the state's
  * stored deviations); each feature j is normalised as (x - mean[j]) / std[j].
  * x: device [ncol][10*nv]. */

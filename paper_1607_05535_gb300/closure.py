@@ -9,10 +9,12 @@ Targets. For a fine state X_f(t), let C(.) be the area-weighted coarse
 graining and S_c the coarse model's large step. The closure target for the
 coarse column fields (rho, M, rho theta at all levels) is
 
-    tau(t) = [ C(X_f(t + dt)) - S_c(C(X_f(t))) ] / dt,
+    tau(t) = [ C(X_f(t + n dt)) - S_c^n(C(X_f(t))) ] / (n dt),
 
-the tendency the coarse model misses over one large step. The features are
-the coarse state C(X_f(t)) of the column and its neighbour means.
+the mean tendency the coarse model misses over a window of n large steps
+(n = 4 by default; a one-step window is dominated by the fast adjustment of
+the coarse-grained state, which the column cannot predict). The features are
+the coarse state C(X_f(t)) of the column and its neighbour-mean anomalies.
 """
 
 from dataclasses import dataclass
@@ -71,7 +73,7 @@ def make_setup(wl, fine_glevel, coarse_glevel, precision, stream, spring_iters=1
                  thor_grid_info(gc)["ncol"], wl.nv)
 
 
-def generate_samples(su, wl, spinup, snapshots, spacing, torch, device):
+def generate_samples(su, wl, spinup, snapshots, spacing, torch, device, window=4):
     """Features (raw, float32 device tensor [snapshots * ncol_c, 10 nv]) and
     targets (float32 device tensor [.., 5 nv]) from a fine run."""
     nv, ncol = su.nv, su.ncol_c
@@ -84,13 +86,13 @@ def generate_samples(su, wl, spinup, snapshots, spacing, torch, device):
         thor_coarse_grain(su.fine, su.coarse, su.fmap)               # C(X_f(t))
         thor_closure_features(su.coarse, zeros, ones, X[s * ncol:(s + 1) * ncol])
         thor_coarse_grain(su.fine, su.scratch, su.fmap)
-        thor_step(su.scratch, 1, wl.n_small, wl.dt)                  # S_c(C(X_f(t)))
-        thor_step(su.fine, 1, wl.n_small, wl.dt)
-        thor_coarse_grain(su.fine, su.coarse, su.fmap)               # C(X_f(t + dt))
-        tgt = (column_fields(su.coarse, ncol, nv) - column_fields(su.scratch, ncol, nv)) / wl.dt
+        thor_step(su.scratch, window, wl.n_small, wl.dt)             # S_c^n(C(X_f(t)))
+        thor_step(su.fine, window, wl.n_small, wl.dt)
+        thor_coarse_grain(su.fine, su.coarse, su.fmap)               # C(X_f(t + n dt))
+        tgt = (column_fields(su.coarse, ncol, nv) - column_fields(su.scratch, ncol, nv)) / (window * wl.dt)
         Y[s * ncol:(s + 1) * ncol] = torch.tensor(tgt, dtype=torch.float32, device=device)
-        if spacing > 1:
-            thor_step(su.fine, spacing - 1, wl.n_small, wl.dt)
+        if spacing > 0:
+            thor_step(su.fine, spacing, wl.n_small, wl.dt)
     return X, Y
 
 

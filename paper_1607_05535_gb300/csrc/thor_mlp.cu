@@ -7,7 +7,7 @@
 // (mma.sync m16n8k16, float32 accumulate) on shared-memory tiles.
 //
 // Closure: per column, the inputs are 5 fields (rho', M_x, M_y, M_z, Th') at
-// all levels and the means of the same over the column's neighbours; the
+// all levels and the neighbour means of the same (as anomalies); the
 // outputs are correction tendencies of the same 5 fields at all levels,
 // added as field += dt * tendency after every large step. Training data come
 // from high-resolution runs area-averaged onto the coarse grid
@@ -430,8 +430,11 @@ __device__ __forceinline__ R* closure_field_rw(const Xf<R>& X, int f) {
   return f == 0 ? X.rho : f == 1 ? X.mx : f == 2 ? X.my : f == 3 ? X.mz : X.th;
 }
 
-// x[c][f nv + k] = field f at level k; x[c][5 nv + f nv + k] = its mean over
-// the neighbours of c; normalised by (x - mean) / std per feature
+// x[c][f nv + k] = field f at level k; x[c][5 nv + f nv + k] = the mean of
+// that field over the neighbours of c minus its value at c (the neighbour
+// anomaly carries the horizontal-curvature signal without the cancellation
+// that bfloat16 inputs would suffer if centre and mean were given apart);
+// normalised by (x - mean) / std per feature
 template <typename R>
 __global__ void k_features(Geo<R> G, Xf<R> X, const float* mean, const float* std, float* x) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -449,7 +452,7 @@ __global__ void k_features(Geo<R> G, Xf<R> X, const float* mean, const float* st
     double s = 0.0;
     for (int j = 0; j < nn; ++j) s += (double)a[nb[j]];
     x[(size_t)c * F + j0] = ((float)a[c] - mean[j0]) / std[j0];
-    x[(size_t)c * F + j1] = ((float)(s / nn) - mean[j1]) / std[j1];
+    x[(size_t)c * F + j1] = ((float)(s / nn - (double)a[c]) - mean[j1]) / std[j1];
   }
 }
 

@@ -36,8 +36,8 @@ def test_closure_gain_over_plain_coarse_method():
     torch.cuda.set_device(0)
     su = cl.make_setup(wl, 6, 5, thor.THOR_MIXED, None)
     n_train, n_test = 20, 4
-    X, Y = cl.generate_samples(su, wl, spinup=150, snapshots=n_train + n_test, spacing=3, torch=torch,
-                               device=dev)
+    X, Y = cl.generate_samples(su, wl, spinup=600, snapshots=n_train + n_test, spacing=2, torch=torch,
+                               device=dev, window=4)
     ncol, nv = su.ncol_c, su.nv
     ntr = n_train * ncol
     xm, xs, ym, ys = cl.normalisation(X[:ntr], Y[:ntr], torch)
@@ -45,7 +45,7 @@ def test_closure_gain_over_plain_coarse_method():
     Yn = ((Y - ym) / ys).contiguous()
     net = thor.thor_mlp_create([10 * nv, 256, 256, 256, 5 * nv], 1024, seed=11)
     try:
-        hist = cl.train(net, Xn[:ntr], Yn[:ntr], epochs=8, batch=1024, lr=1e-3, torch=torch)
+        hist = cl.train(net, Xn[:ntr], Yn[:ntr], epochs=20, batch=1024, lr=1e-3, torch=torch)
         P = cl.predict(net, Xn[ntr:], 5 * nv, 1024, torch) * ys + ym
         Yt = Y[ntr:]
         err_closure = float(((P - Yt) ** 2).mean())
@@ -55,14 +55,14 @@ def test_closure_gain_over_plain_coarse_method():
                   "tendency_mse_closure": err_closure, "tendency_mse_plain": err_plain,
                   "a_priori_gain": gain}
 
-        # a posteriori: 3 coarse steps from a held-out coarse-grained state
+        # a posteriori: 4 coarse steps from a held-out coarse-grained state
         thor.thor_coarse_grain(su.fine, su.coarse, su.fmap)
         thor.thor_coarse_grain(su.fine, su.scratch, su.fmap)
         thor.thor_closure_attach(su.coarse, net, xm, xs, ym, ys)
-        thor.thor_step(su.coarse, 3, wl.n_small, wl.dt)
+        thor.thor_step(su.coarse, 4, wl.n_small, wl.dt)
         thor.thor_closure_attach(su.coarse, None)
-        thor.thor_step(su.scratch, 3, wl.n_small, wl.dt)
-        thor.thor_step(su.fine, 3, wl.n_small, wl.dt)
+        thor.thor_step(su.scratch, 4, wl.n_small, wl.dt)
+        thor.thor_step(su.fine, 4, wl.n_small, wl.dt)
         truth_state = thor.thor_state_init(su.coarse_grid, cl_planet(wl), cl_init(wl), None)
         thor.thor_coarse_grain(su.fine, truth_state, su.fmap)
         truth = cl.column_fields(truth_state, ncol, nv)
@@ -72,7 +72,7 @@ def test_closure_gain_over_plain_coarse_method():
         scale = np.std(truth, axis=0) + 1e-30
         e_c = float(np.sqrt(np.mean(((with_c - truth) / scale) ** 2)))
         e_p = float(np.sqrt(np.mean(((plain - truth) / scale) ** 2)))
-        report.update({"rollout_steps": 3, "rollout_rmse_closure": e_c, "rollout_rmse_plain": e_p})
+        report.update({"rollout_steps": 4, "rollout_rmse_closure": e_c, "rollout_rmse_plain": e_p})
     finally:
         thor.thor_mlp_destroy(net)
     out = os.path.join(os.path.dirname(os.path.dirname(__file__)), "gpurun_out")
@@ -80,7 +80,7 @@ def test_closure_gain_over_plain_coarse_method():
         json.dump(report, open(os.path.join(out, "closure_report.json"), "w"), indent=1)
     print(report)
     assert hist[-1] < hist[0]
-    assert gain > 0.1, report
+    assert gain > 0.25, report
     assert e_c < e_p, report
 
 
