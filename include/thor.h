@@ -225,13 +225,16 @@ void thor_mlp_destroy(thor_mlp* mlp);
  * x: device [ncol][10*nv]. */
 int thor_closure_features(thor_state* state, const float* mean, const float* std, float* x);
 
-/* Attach an MLP (sizes[0] = 10*nv, last size = 5*nv) as a closure: after
- * every large step, y = MLP(features) and field_f(k) += dt * (y[f*nv + k] *
- * out_std + out_mean) (momentum correction projected onto the tangent
- * plane). The four normalisation arrays are caller-owned device arrays that
- * must stay valid while attached. mlp = NULL detaches (plain method). */
+/* Attach an MLP (sizes[0] = 10*nv, last size = 5*nv) as a closure. Every
+ * `period` large steps (counted from the attach, starting with the first)
+ * the correction tendency tau = MLP(features) * out_std + out_mean is
+ * evaluated on the current state; after every large step
+ * field_f(k) += dt * tau[f*nv + k] (momentum correction projected onto the
+ * tangent plane). A network trained on n-step mean corrections is used with
+ * period n. The four normalisation arrays are caller-owned device arrays
+ * that must stay valid while attached. mlp = NULL detaches (plain method). */
 int thor_closure_attach(thor_state* state, thor_mlp* mlp, const float* in_mean, const float* in_std,
-                        const float* out_mean, const float* out_std);
+                        const float* out_mean, const float* out_std, int period);
 
 /* Area-weighted average of a fine state onto a coarse one: every coarse
  * column gets the mean of the fine columns mapped to it (fine_to_coarse,

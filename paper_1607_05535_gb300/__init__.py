@@ -108,7 +108,7 @@ def _load():
         "thor_mlp_train_step": (I, [P, P, P, I, ctypes.c_float, P]),
         "thor_mlp_destroy": (None, [P]),
         "thor_closure_features": (I, [P, P, P, P]),
-        "thor_closure_attach": (I, [P, P, P, P, P, P]),
+        "thor_closure_attach": (I, [P, P, P, P, P, P, I]),
         "thor_coarse_grain": (I, [P, P, P, Z]),
     }
     for name, (res, args) in sig.items():
@@ -303,9 +303,9 @@ def thor_closure_features(state, mean, std, x):
     _check(_lib.thor_closure_features(state, _ptr(mean), _ptr(std), _ptr(x)), "thor_closure_features")
 
 
-def thor_closure_attach(state, mlp, in_mean=None, in_std=None, out_mean=None, out_std=None):
+def thor_closure_attach(state, mlp, in_mean=None, in_std=None, out_mean=None, out_std=None, period=1):
     p = lambda t: _ptr(t) if t is not None else None
-    _check(_lib.thor_closure_attach(state, mlp, p(in_mean), p(in_std), p(out_mean), p(out_std)),
+    _check(_lib.thor_closure_attach(state, mlp, p(in_mean), p(in_std), p(out_mean), p(out_std), period),
            "thor_closure_attach")
 
 

@@ -489,17 +489,22 @@ int closure_apply_t(thor_state* s, double dt) {
   cudaStream_t st = I->stream;
   const int ncol = I->G.ncol, nv = I->G.nv;
   dim3 grid((ncol + 127) / 128, nv);
-  k_features<R><<<grid, 128, 0, st>>>(I->G, I->Xt, cb.in_mean, cb.in_std, cb.x);
-  const int Fin = 2 * kClosureFields * nv, Fout = kClosureFields * nv;
-  for (int c0 = 0; c0 < ncol; c0 += net->max_batch) {
-    const int m = std::min(net->max_batch, ncol - c0);
-    int rc = mlp_forward(net, cb.x + (size_t)c0 * Fin, m);
-    if (rc) return rc;
-    if (cudaMemcpyAsync(cb.y + (size_t)c0 * Fout, net->y, (size_t)m * Fout * 4, cudaMemcpyDeviceToDevice, st))
-      return THOR_ECUDA;
+  if (cb.counter % cb.period == 0) {       // re-evaluate the network on the current state
+    k_features<R><<<grid, 128, 0, st>>>(I->G, I->Xt, cb.in_mean, cb.in_std, cb.x);
+    const int Fin = 2 * kClosureFields * nv, Fout = kClosureFields * nv;
+    for (int c0 = 0; c0 < ncol; c0 += net->max_batch) {
+      const int m = std::min(net->max_batch, ncol - c0);
+      int rc = mlp_forward(net, cb.x + (size_t)c0 * Fin, m);
+      if (rc) return rc;
+      if (cudaMemcpyAsync(cb.y + (size_t)c0 * Fout, net->y, (size_t)m * Fout * 4, cudaMemcpyDeviceToDevice,
+                          st))
+        return THOR_ECUDA;
+    }
+    I->launches += 1 + 4 * ((ncol + net->max_batch - 1) / net->max_batch);
   }
+  cb.counter += 1;
   k_apply<R><<<grid, 128, 0, st>>>(I->G, I->Xt, cb.y, cb.out_mean, cb.out_std, (float)dt);
-  I->launches += 3 + 4 * ((ncol + net->max_batch - 1) / net->max_batch);
+  I->launches += 1;
   return cudaGetLastError() == cudaSuccess ? THOR_OK : THOR_ECUDA;
 }
 
@@ -606,12 +611,12 @@ int thor_closure_features(thor_state* s, const float* mean, const float* std, fl
 }
 
 int thor_closure_attach(thor_state* s, thor_mlp* net, const float* in_mean, const float* in_std,
-                        const float* out_mean, const float* out_std) {
+                        const float* out_mean, const float* out_std, int period) {
   using namespace thor;
   if (!s) return THOR_EINVAL;
   closure_release(s);
   if (!net) return THOR_OK;                 // detached: plain method
-  if (!in_mean || !in_std || !out_mean || !out_std) return THOR_EINVAL;
+  if (!in_mean || !in_std || !out_mean || !out_std || period < 1) return THOR_EINVAL;
   const int ncol = s->grid->h.ncol, nv = s->grid->h.nv;
   if (net->sizes.front() != 2 * kClosureFields * nv || net->sizes.back() != kClosureFields * nv)
     return THOR_EINVAL;
@@ -621,6 +626,7 @@ int thor_closure_attach(thor_state* s, thor_mlp* net, const float* in_mean, cons
   cb.in_std = in_std;
   cb.out_mean = out_mean;
   cb.out_std = out_std;
+  cb.period = period;
   if (cudaMalloc(&cb.x, (size_t)ncol * 2 * kClosureFields * nv * 4) ||
       cudaMalloc(&cb.y, (size_t)ncol * kClosureFields * nv * 4)) {
     if (cb.x) cudaFree(cb.x);

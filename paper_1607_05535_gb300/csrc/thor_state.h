@@ -17,6 +17,8 @@ struct ClosureBinding {
   thor_mlp* net = nullptr;
   const float *in_mean = nullptr, *in_std = nullptr, *out_mean = nullptr, *out_std = nullptr;
   float *x = nullptr, *y = nullptr;   // per-state feature / output buffers
+  int period = 1;                     // large steps between network evaluations
+  long long counter = 0;              // large steps since attach
 };
 
 struct thor_state {
