@@ -168,8 +168,23 @@ int thor_launch_count(const thor_state* state, long long* count);
  * of the state (one reduction and one stream synchronisation per call) and
  * return THOR_ENONFINITE if any value is NaN or Inf; the state is the one
  * after the step (restore a checkpoint with thor_state_set). Default 0. */
-enum { THOR_TUNE_KCHUNK = 0, THOR_TUNE_GRAPH = 1, THOR_TUNE_CHECK_FINITE = 2 };
+enum { THOR_TUNE_KCHUNK = 0, THOR_TUNE_GRAPH = 1, THOR_TUNE_CHECK_FINITE = 2, THOR_TUNE_BLOCK = 3 };
 int thor_tune(thor_state* state, int knob, int value);
+
+/* THOR_TUNE_BLOCK: threads (one per column) in a block of the stencil
+ * kernels, a multiple of 32 in [32, 256] (default 128). */
+
+/* Launch-shape autotuner (an extension; the paper fixes no launch shapes).
+ * Times `steps` large steps of (n_small, dt) for every levels-per-thread
+ * value in {1, 2, 4, 8} and block size in {64, 128, 256}, each after one
+ * untimed step, with CUDA events on the state's stream; restores the state's
+ * prognostic fields before every candidate and at the end (the state is
+ * unchanged), sets the fastest shape (as thor_tune would) and returns it with
+ * its time per large step in ms (any output pointer may be NULL). Allocates
+ * one state-sized device buffer for the duration of the call and synchronises
+ * the stream. n_small even >= 2, dt > 0, steps >= 1, else THOR_EINVAL. */
+int thor_autotune(thor_state* state, int n_small, double dt, int steps, int* kchunk, int* block,
+                  double* ms_per_step);
 
 /* Per-kernel timing. While enabled, every launch of the state is bracketed by
  * two CUDA events recorded on the state's stream; thor_profile_read
@@ -185,6 +200,47 @@ int thor_profile(thor_state* state, int enable);
 int thor_profile_read(thor_state* state, int kernel, double* total_ms, long long* launches);
 
 void thor_state_destroy(thor_state* state);
+
+/* ---------------------------------------------------------------- ensemble */
+
+/* An ensemble of independent atmospheres stepped together (an extension; the
+ * paper runs one atmosphere at a time). Members are existing states of any
+ * grid level, planet, forcing and time step, with the same level count nv and
+ * precision; every kernel of the large step runs as one launch over all
+ * members, and on a non-default `stream` one large step of the whole ensemble
+ * is captured as a CUDA graph and replayed (re-captured when a member's dt or
+ * n_small, or a launch shape, changes). The results are those of stepping
+ * each member alone with the same (n_small, dt).
+ *
+ * The ensemble keeps the member pointers: members must outlive it and must
+ * not be stepped on their own while an ensemble step may be running (work on
+ * the members' streams is ordered before and after each ensemble step with
+ * events). Closures are not run in an ensemble: a member with a closure
+ * attached makes thor_ensemble_step return THOR_EINVAL. There is no
+ * non-finite watchdog; use thor_diag per member.
+ * create: 1 <= n <= THOR_ENSEMBLE_MAX distinct members, else THOR_EINVAL. */
+#define THOR_ENSEMBLE_MAX 4096
+typedef struct thor_ensemble thor_ensemble;
+int thor_ensemble_create(thor_state* const* members, int n, void* stream, thor_ensemble** out);
+
+/* n_large large steps of every member; n_small[i] (even >= 2) and dt[i] > 0
+ * are member i's, in creation order (host arrays of n). A changed plan
+ * (n_small, dt or launch shape) synchronises the stream once and uploads the
+ * member table and block maps. */
+int thor_ensemble_step(thor_ensemble* ens, int n_large, const int* n_small, const double* dt);
+
+/* Member count and kernel launches issued by the ensemble so far. */
+int thor_ensemble_info(const thor_ensemble* ens, int* n_members, long long* launches);
+
+/* THOR_TUNE_KCHUNK, THOR_TUNE_BLOCK, THOR_TUNE_GRAPH as for one state. */
+int thor_ensemble_tune(thor_ensemble* ens, int knob, int value);
+
+/* thor_autotune over the ensemble: every member's state is restored. */
+int thor_ensemble_autotune(thor_ensemble* ens, const int* n_small, const double* dt, int steps, int* kchunk,
+                           int* block, double* ms_per_step);
+
+/* Waits for the ensemble's stream; the members stay valid. */
+void thor_ensemble_destroy(thor_ensemble* ens);
 
 /* --------------------------------------------------------- learned closure */
 
@@ -225,14 +281,17 @@ void thor_mlp_destroy(thor_mlp* mlp);
  * x: device [ncol][10*nv]. */
 int thor_closure_features(thor_state* state, const float* mean, const float* std, float* x);
 
-/* Attach an MLP (sizes[0] = 10*nv, last size = 5*nv) as a closure. Every
- * `period` large steps (counted from the attach, starting with the first)
- * the correction tendency tau = MLP(features) * out_std + out_mean is
- * evaluated on the current state; after every large step
- * field_f(k) += dt * tau[f*nv + k] (momentum correction projected onto the
- * tangent plane). A network trained on n-step mean corrections is used with
- * period n. The four normalisation arrays are caller-owned device arrays
- * that must stay valid while attached. mlp = NULL detaches (plain method). */
+/* Attach an MLP (sizes[0] = 10*nv, last size = 5*nv) as a closure with a
+ * window of `period` >= 1 large steps, counted from the attach. At the start
+ * of each window the correction tendency tau = MLP(features) * out_std +
+ * out_mean is evaluated on the current state; when the window closes,
+ * field_f(k) += period * dt * tau[f*nv + k] (the momentum correction
+ * projected onto the tangent plane). This is the use that matches a network
+ * trained on the n-step target [C(X_fine(t + n dt)) - S^n(C(X_fine(t)))] /
+ * (n dt) with period = n. thor_step calls that end inside a window carry it
+ * over to the next call. The four normalisation arrays are caller-owned
+ * device arrays that must stay valid while attached. mlp = NULL detaches
+ * (plain method); re-attaching restarts the window count. */
 int thor_closure_attach(thor_state* state, thor_mlp* mlp, const float* in_mean, const float* in_std,
                         const float* out_mean, const float* out_std, int period);
 

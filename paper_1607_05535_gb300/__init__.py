@@ -21,6 +21,8 @@ THOR_FP64, THOR_MIXED = 0, 1
 THOR_FORCING_NONE, THOR_FORCING_HELD_SUAREZ, THOR_FORCING_HOT_JUPITER = 0, 1, 2
 THOR_FIELD_RHO, THOR_FIELD_MOM, THOR_FIELD_W, THOR_FIELD_RHOTHETA, THOR_FIELD_PRESSURE, \
     THOR_FIELD_TEMPERATURE = range(6)
+THOR_TUNE_KCHUNK, THOR_TUNE_GRAPH, THOR_TUNE_CHECK_FINITE, THOR_TUNE_BLOCK = range(4)
+THOR_ENSEMBLE_MAX = 4096
 
 EXPORTED = [
     "thor_strerror", "thor_grid_create", "thor_grid_info", "thor_grid_points",
@@ -30,6 +32,8 @@ EXPORTED = [
     "thor_mass_noalloc", "thor_mlp_create", "thor_mlp_info", "thor_mlp_get_params",
     "thor_mlp_set_params", "thor_mlp_forward", "thor_mlp_backward", "thor_mlp_train_step",
     "thor_mlp_destroy", "thor_closure_features", "thor_closure_attach", "thor_coarse_grain",
+    "thor_autotune", "thor_ensemble_create", "thor_ensemble_step", "thor_ensemble_info",
+    "thor_ensemble_tune", "thor_ensemble_autotune", "thor_ensemble_destroy",
 ]
 
 # kernel ids of thor_profile_read
@@ -110,6 +114,13 @@ def _load():
         "thor_closure_features": (I, [P, P, P, P]),
         "thor_closure_attach": (I, [P, P, P, P, P, P, I]),
         "thor_coarse_grain": (I, [P, P, P, Z]),
+        "thor_autotune": (I, [P, I, D, I, IP, IP, ctypes.POINTER(D)]),
+        "thor_ensemble_create": (I, [ctypes.POINTER(P), I, P, ctypes.POINTER(P)]),
+        "thor_ensemble_step": (I, [P, I, IP, ctypes.POINTER(D)]),
+        "thor_ensemble_info": (I, [P, IP, ctypes.POINTER(ctypes.c_longlong)]),
+        "thor_ensemble_tune": (I, [P, I, I]),
+        "thor_ensemble_autotune": (I, [P, IP, ctypes.POINTER(D), I, IP, IP, ctypes.POINTER(D)]),
+        "thor_ensemble_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -312,3 +323,53 @@ def thor_closure_attach(state, mlp, in_mean=None, in_std=None, out_mean=None, ou
 def thor_coarse_grain(fine, coarse, fine_to_coarse):
     a = np.ascontiguousarray(fine_to_coarse, dtype=np.int32)
     _check(_lib.thor_coarse_grain(fine, coarse, _ptr(a), a.size), "thor_coarse_grain")
+
+
+def thor_autotune(state, n_small, dt, steps=3):
+    """Returns (kchunk, block, ms per large step) of the fastest launch shape,
+    which is left set on the state."""
+    kc, bs, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(_lib.thor_autotune(state, n_small, dt, steps, ctypes.byref(kc), ctypes.byref(bs), ctypes.byref(ms)),
+           "thor_autotune")
+    return kc.value, bs.value, ms.value
+
+
+def _int_array(v):
+    return (ctypes.c_int * len(v))(*[int(x) for x in v])
+
+
+def _double_array(v):
+    return (ctypes.c_double * len(v))(*[float(x) for x in v])
+
+
+def thor_ensemble_create(members, stream=None):
+    arr = (ctypes.c_void_p * len(members))(*[m.value if hasattr(m, "value") else m for m in members])
+    out = ctypes.c_void_p()
+    _check(_lib.thor_ensemble_create(arr, len(members), ctypes.c_void_p(stream or 0), ctypes.byref(out)),
+           "thor_ensemble_create")
+    return out
+
+
+def thor_ensemble_step(ens, n_large, n_small, dt):
+    _check(_lib.thor_ensemble_step(ens, n_large, _int_array(n_small), _double_array(dt)), "thor_ensemble_step")
+
+
+def thor_ensemble_info(ens):
+    n, l = ctypes.c_int(), ctypes.c_longlong()
+    _check(_lib.thor_ensemble_info(ens, ctypes.byref(n), ctypes.byref(l)), "thor_ensemble_info")
+    return {"members": n.value, "launches": l.value}
+
+
+def thor_ensemble_tune(ens, knob, value):
+    _check(_lib.thor_ensemble_tune(ens, knob, value), "thor_ensemble_tune")
+
+
+def thor_ensemble_autotune(ens, n_small, dt, steps=3):
+    kc, bs, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(_lib.thor_ensemble_autotune(ens, _int_array(n_small), _double_array(dt), steps, ctypes.byref(kc),
+                                       ctypes.byref(bs), ctypes.byref(ms)), "thor_ensemble_autotune")
+    return kc.value, bs.value, ms.value
+
+
+def thor_ensemble_destroy(ens):
+    _lib.thor_ensemble_destroy(ens)

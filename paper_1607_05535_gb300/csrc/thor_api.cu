@@ -627,10 +627,7 @@ int thor_step(thor_state* s, int n_large, int n_small, double dt) {
   if (!s || n_large < 0 || n_small < 2 || (n_small % 2) || !(dt > 0)) return THOR_EINVAL;
   int rc = THOR_OK;
   if (s->closure.net) {
-    for (int i = 0; i < n_large && !rc; ++i) {
-      rc = s->impl->step(1, n_small, dt);
-      if (!rc) rc = thor::closure_apply(s, dt);
-    }
+    for (int i = 0; i < n_large && !rc; ++i) rc = thor::closure_large_step(s, n_small, dt);
   } else {
     rc = s->impl->step(n_large, n_small, dt);
   }
@@ -687,6 +684,11 @@ int thor_tune(thor_state* s, int knob, int value) {
   }
   if (knob == THOR_TUNE_CHECK_FINITE) {
     s->check_finite = value != 0;
+    return THOR_OK;
+  }
+  if (knob == THOR_TUNE_BLOCK) {
+    if (value < 32 || value > thor::kMaxBlock || value % 32) return THOR_EINVAL;
+    s->impl->block = value;
     return THOR_OK;
   }
   return THOR_EINVAL;

@@ -37,6 +37,26 @@ struct Pert {
   R *w;                            // interfaces
 };
 
+// Everything the kernels of one state need, as one record: a device array of
+// these lets one launch step an ensemble of states of different sizes,
+// planets and time steps.
+template <typename R>
+struct Member {
+  Geo<R> G;
+  VR<R> U;
+  Phys ph;
+  Xf<R> Xt, Xst;
+  Work<R> T;
+  Slow<R> SL;
+  Pert<R> P;
+  Fac F;
+  double dt, hj_dT;
+  double dts[3];                   // small-step length of each RK stage
+  R Kd;                            // hyperdiffusion coefficient for this dt
+  int nsub[3];                     // small steps of each RK stage
+  int hyper, divdamp, forcing;
+};
+
 struct ImplBase {
   virtual ~ImplBase() { prof_clear(); }
   virtual int step(int n_large, int n_small, double dt) = 0;
@@ -46,6 +66,11 @@ struct ImplBase {
   virtual void set_graph(bool on) = 0;
   long long launches = 0;
   int kchunk = 2;                      // levels per thread in the stencil kernels
+  int block = kBlock;                  // threads (columns) per block of the stencil kernels
+  // copy the prognostic fields to / from a device buffer of state_bytes()
+  virtual size_t state_bytes() const = 0;
+  virtual int save_state(void* dst) = 0;
+  virtual int load_state(const void* src) = 0;
   // per-kernel event timing (off unless enabled)
   cudaStream_t stream = nullptr;
   bool prof_on = false;
@@ -125,7 +150,7 @@ struct Impl : ImplBase {
   // the same; used on a non-default stream when no profiling is recorded
   cudaGraphExec_t graph_exec = nullptr;
   double graph_dt = 0;
-  int graph_n = 0, graph_kc = 0;
+  int graph_n = 0, graph_kc = 0, graph_bs = 0;
   long long graph_launches = 0;
   void drop_graph() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -133,7 +158,7 @@ struct Impl : ImplBase {
   }
   int step(int n_large, int n_small, double dt) override {
     if (use_graph && stream != nullptr && !prof_on && n_large > 0) {
-      if (!graph_exec || graph_dt != dt || graph_n != n_small || graph_kc != kchunk) {
+      if (!graph_exec || graph_dt != dt || graph_n != n_small || graph_kc != kchunk || graph_bs != block) {
         drop_graph();
         cudaGraph_t g = nullptr;
         long long before = launches;
@@ -156,6 +181,7 @@ struct Impl : ImplBase {
         graph_dt = dt;
         graph_n = n_small;
         graph_kc = kchunk;
+        graph_bs = block;
       }
       for (int i = 0; i < n_large; ++i) {
         if (cudaGraphLaunch(graph_exec, stream)) return -3;
@@ -172,6 +198,65 @@ struct Impl : ImplBase {
   int diag(double* out8, long long* nonfinite) override;
   int get(int field, double* host, size_t n) override;
   int set(int field, const double* host, size_t n) override;
+  // rho, M (3), rho theta: nv planes each; W: nv + 1 planes
+  size_t state_bytes() const override { return (size_t)(6 * G.nv + 1) * G.colp * sizeof(R); }
+  int copy_state(char* buf, bool save) {
+    const size_t plane = (size_t)G.colp * sizeof(R), c = G.nv * plane;
+    R* f[6] = {Xt.rho, Xt.mx, Xt.my, Xt.mz, Xt.th, Xt.w};
+    size_t off = 0;
+    for (int i = 0; i < 6; ++i) {
+      const size_t bytes = i == 5 ? c + plane : c;
+      cudaError_t e = save ? cudaMemcpyAsync(buf + off, f[i], bytes, cudaMemcpyDeviceToDevice, stream)
+                           : cudaMemcpyAsync(f[i], buf + off, bytes, cudaMemcpyDeviceToDevice, stream);
+      if (e) return -3;
+      off += bytes;
+    }
+    return 0;
+  }
+  int save_state(void* dst) override { return copy_state(static_cast<char*>(dst), true); }
+  int load_state(const void* src) override { return copy_state(static_cast<char*>(const_cast<void*>(src)), false); }
+  // this state's entry of an ensemble member table
+  Member<R> member(double dt, int n_small) const {
+    Member<R> m;
+    m.G = G;
+    m.U = U;
+    m.ph = ph;
+    m.Xt = Xt;
+    m.Xst = Xst;
+    m.T = T;
+    m.SL = SL;
+    m.P = P;
+    m.F = F;
+    m.dt = dt;
+    m.hj_dT = hj_dT;
+    m.dts[0] = dt / 3.0;
+    m.dts[1] = m.dts[2] = dt / n_small;
+    m.nsub[0] = 1;
+    m.nsub[1] = n_small / 2;
+    m.nsub[2] = n_small;
+    m.Kd = (R)(diff_D * dbar4 / dt);
+    m.hyper = hyper;
+    m.divdamp = divdamp;
+    m.forcing = forcing;
+    return m;
+  }
 };
+
+// Launch plan of an ensemble large step (device member table and block maps
+// built on the host; see ensemble_large_step)
+template <typename R>
+struct EnsPlan {
+  const Member<R>* M = nullptr;
+  const int2* map = nullptr;        // stencil blocks: (member, local block)
+  const int2* mapc = nullptr;       // 32-column blocks of the column kernels
+  int nv = 0, kchunk = 2, block = kBlock;
+  int nblk = 0, nblkc = 0;          // all members
+  int maxsub[3] = {0, 0, 0};
+  std::vector<int> active[3], activec[3];  // blocks of the members still stepping at small step j
+  int any_hyper = 0, any_divdamp = 0, any_forcing = 0;
+};
+
+template <typename R>
+int ensemble_large_step(const EnsPlan<R>& E, cudaStream_t stream, long long* launches);
 
 }  // namespace thor

@@ -24,7 +24,8 @@
 
 namespace thor {
 
-constexpr int kBlock = 128;        // columns per block
+constexpr int kBlock = 128;        // columns per block (default; the padding of colp)
+constexpr int kMaxBlock = 256;     // largest block of the stencil kernels
 constexpr int kMaxNv = 128;        // largest nv the column kernel supports
 
 // Vertical grid and reference column (float64, device global memory)

@@ -456,10 +456,10 @@ __global__ void k_features(Geo<R> G, Xf<R> X, const float* mean, const float* st
   }
 }
 
-// field += dt (y * out_std + out_mean); the momentum correction is projected
+// field += span (y * out_std + out_mean); the momentum correction is projected
 // onto the tangent plane like every horizontal-momentum update
 template <typename R>
-__global__ void k_apply(Geo<R> G, Xf<R> X, const float* y, const float* omean, const float* ostd, float dt) {
+__global__ void k_apply(Geo<R> G, Xf<R> X, const float* y, const float* omean, const float* ostd, float span) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   if (c >= G.ncol) return;
@@ -477,35 +477,56 @@ __global__ void k_apply(Geo<R> G, Xf<R> X, const float* y, const float* omean, c
   t[3] -= d * rz;
   for (int f = 0; f < kClosureFields; ++f) {
     R* a = closure_field_rw(X, f);
-    a[i] = a[i] + (R)(dt * t[f]);
+    a[i] = a[i] + (R)(span * t[f]);
   }
 }
 
+// tau_hat = MLP(features of the current state), kept in the binding's y buffer
 template <typename R>
-int closure_apply_t(thor_state* s, double dt) {
+int closure_evaluate_t(thor_state* s) {
   Impl<R>* I = static_cast<Impl<R>*>(s->impl.get());
   ClosureBinding& cb = s->closure;
   thor_mlp* net = cb.net;
   cudaStream_t st = I->stream;
   const int ncol = I->G.ncol, nv = I->G.nv;
   dim3 grid((ncol + 127) / 128, nv);
-  if (cb.counter % cb.period == 0) {       // re-evaluate the network on the current state
-    k_features<R><<<grid, 128, 0, st>>>(I->G, I->Xt, cb.in_mean, cb.in_std, cb.x);
-    const int Fin = 2 * kClosureFields * nv, Fout = kClosureFields * nv;
-    for (int c0 = 0; c0 < ncol; c0 += net->max_batch) {
-      const int m = std::min(net->max_batch, ncol - c0);
-      int rc = mlp_forward(net, cb.x + (size_t)c0 * Fin, m);
-      if (rc) return rc;
-      if (cudaMemcpyAsync(cb.y + (size_t)c0 * Fout, net->y, (size_t)m * Fout * 4, cudaMemcpyDeviceToDevice,
-                          st))
-        return THOR_ECUDA;
-    }
-    I->launches += 1 + 4 * ((ncol + net->max_batch - 1) / net->max_batch);
+  k_features<R><<<grid, 128, 0, st>>>(I->G, I->Xt, cb.in_mean, cb.in_std, cb.x);
+  const int Fin = 2 * kClosureFields * nv, Fout = kClosureFields * nv;
+  for (int c0 = 0; c0 < ncol; c0 += net->max_batch) {
+    const int m = std::min(net->max_batch, ncol - c0);
+    int rc = mlp_forward(net, cb.x + (size_t)c0 * Fin, m);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(cb.y + (size_t)c0 * Fout, net->y, (size_t)m * Fout * 4, cudaMemcpyDeviceToDevice, st))
+      return THOR_ECUDA;
   }
-  cb.counter += 1;
-  k_apply<R><<<grid, 128, 0, st>>>(I->G, I->Xt, cb.y, cb.out_mean, cb.out_std, (float)dt);
+  I->launches += 1 + 4 * ((ncol + net->max_batch - 1) / net->max_batch);
+  return cudaGetLastError() == cudaSuccess ? THOR_OK : THOR_ECUDA;
+}
+
+template <typename R>
+int closure_correct_t(thor_state* s, double span) {
+  Impl<R>* I = static_cast<Impl<R>*>(s->impl.get());
+  ClosureBinding& cb = s->closure;
+  dim3 grid((I->G.ncol + 127) / 128, I->G.nv);
+  k_apply<R><<<grid, 128, 0, I->stream>>>(I->G, I->Xt, cb.y, cb.out_mean, cb.out_std, (float)span);
   I->launches += 1;
   return cudaGetLastError() == cudaSuccess ? THOR_OK : THOR_ECUDA;
+}
+
+// One large step with the closure. The network sees the state at the start
+// of each window of `period` large steps and its correction, period * dt *
+// tau_hat, is added when the window closes: the coarse solution after n
+// steps plus n dt tau, which is how the training target is defined.
+template <typename R>
+int closure_large_step_t(thor_state* s, int n_small, double dt) {
+  ClosureBinding& cb = s->closure;
+  int rc = THOR_OK;
+  if (cb.counter % cb.period == 0) rc = closure_evaluate_t<R>(s);
+  if (!rc) rc = s->impl->step(1, n_small, dt);
+  if (rc) return rc;
+  cb.counter += 1;
+  if (cb.counter % cb.period == 0) rc = closure_correct_t<R>(s, cb.period * dt);
+  return rc;
 }
 
 // fine -> coarse area-weighted averages (CSR over the fine columns of each
@@ -545,8 +566,9 @@ __global__ void k_coarse_grain(Geo<R> Gc, Xf<R> Xf_, int Sf, Xf<R> Xc, const int
 
 }  // namespace
 
-int closure_apply(thor_state* s, double dt) {
-  return s->precision == THOR_FP64 ? closure_apply_t<double>(s, dt) : closure_apply_t<float>(s, dt);
+int closure_large_step(thor_state* s, int n_small, double dt) {
+  return s->precision == THOR_FP64 ? closure_large_step_t<double>(s, n_small, dt)
+                                   : closure_large_step_t<float>(s, n_small, dt);
 }
 
 void closure_release(thor_state* s) {

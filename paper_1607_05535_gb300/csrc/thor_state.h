@@ -17,7 +17,7 @@ struct ClosureBinding {
   thor_mlp* net = nullptr;
   const float *in_mean = nullptr, *in_std = nullptr, *out_mean = nullptr, *out_std = nullptr;
   float *x = nullptr, *y = nullptr;   // per-state feature / output buffers
-  int period = 1;                     // large steps between network evaluations
+  int period = 1;                     // large steps per closure window
   long long counter = 0;              // large steps since attach
 };
 
@@ -30,6 +30,6 @@ struct thor_state {
 };
 
 namespace thor {
-int closure_apply(thor_state* s, double dt);   // thor_mlp.cu
+int closure_large_step(thor_state* s, int n_small, double dt);   // thor_mlp.cu
 void closure_release(thor_state* s);
 }

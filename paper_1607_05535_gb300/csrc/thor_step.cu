@@ -2,9 +2,10 @@
 // launch sequence.
 //
 // Stencil kernels: one thread per column, looping over a chunk of levels, so
-// the per-column stencil weights are loaded once per chunk; blockIdx.y picks
-// the chunk. A warp covers 32 consecutive columns of one level, so every
-// field access is a coalesced (or neighbour-shifted) row of one plane.
+// the per-column stencil weights are loaded once per chunk; the block's
+// second index picks the chunk. A warp covers 32 consecutive columns of one
+// level, so every field access is a coalesced (or neighbour-shifted) row of
+// one plane.
 //
 // The vertical solve is split: k_ss_flux (a stencil kernel like the others)
 // forms the per-cell parts of the column equations, and k_ss_solve runs the
@@ -14,19 +15,24 @@
 
 namespace thor {
 
+// Each step of the method is a device function over one block of columns
+// (block indices passed in); the kernels below run it either for one state
+// (block indices from the launch grid) or for a whole ensemble of states in
+// one launch (block -> (member, local block) from a block map).
+
 
 // ---------------------------------------------------------------- slow terms
 
 // Pointwise derived quantities at the stage state: p', T', theta, the full
 // 3-D velocity, v_h = M/rho (centres) and v_r = W/rho (interfaces).
 template <typename R>
-__global__ void k_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int kchunk) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void d_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int kchunk, int bx, int by) {
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
   const R gamma = (R)ph.gamma, inv_Rd = R(1.0 / ph.Rd);
   R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
-  int k0 = blockIdx.y * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
+  int k0 = by * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     if (k < G.nv) {
@@ -62,13 +68,13 @@ __global__ void k_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int kc
 // First Laplacians of the hyperdiffusion (Sec. 4), already multiplied by
 // K_d and, for the momentum and temperature terms, by rho.
 template <typename R>
-__global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void d_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk, int bx, int by) {
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
   W7<R> wl = load_w7(G.wlap, S, c);
-  int k0 = blockIdx.y * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
+  int k0 = by * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     if (k < G.nv) {
@@ -99,9 +105,9 @@ __global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk) 
 // stage state (divergence damping), the radial advection+Coriolis and
 // Pi = gamma p / rho theta.
 template <typename R>
-__global__ void __launch_bounds__(kBlock, 4) k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
-                       int kchunk) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
+                                            int kchunk, int bx, int by) {
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
@@ -110,7 +116,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_slow(Geo<R> G, VR<R> U, Phys ph, 
   W7<R> wl = load_w7(G.wlap, S, c);
   R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
   const R two_om = R(2.0 * ph.omega), gamma = (R)ph.gamma, Rd = (R)ph.Rd;
-  int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
+  int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
@@ -179,15 +185,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_slow(Geo<R> G, VR<R> U, Phys ph, 
 // Slow tendency of the vertical momentum at the interior interfaces
 // (right-hand side of Eq. momr2) and theta at the interfaces.
 template <typename R>
-__global__ void k_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
-                         int kchunk) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
+                                            int kchunk, int bx, int by) {
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
   W7<R> wl = load_w7(G.wlap, S, c);
   const R g = (R)ph.g;
-  int k0 = blockIdx.y * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
+  int k0 = by * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int i = k * S + c;
@@ -210,12 +216,12 @@ __global__ void k_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R>
 // Perturbations at the start of a stage: Phi* = Phi^t - Phi^(s); p* from the
 // nonlinear Eq. theta_to_p.
 template <typename R>
-__global__ void k_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> Xs, Work<R> T, Pert<R> P,
-                             int kchunk) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void d_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> Xs, Work<R> T, Pert<R> P,
+                                            int kchunk, int bx, int by) {
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
-  int k0 = blockIdx.y * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
+  int k0 = by * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     int i = k * S + c;
@@ -236,13 +242,13 @@ __global__ void k_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> Xs, Wor
 
 // 3-D divergence of the total momentum (divergence damping, Sec. 4)
 template <typename R>
-__global__ void k_ss_div(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, int kchunk) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void d_ss_div(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, int kchunk, int bx, int by) {
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
   W7x3<R> wd = load_w7x3(G.wdiv, S, c);
-  int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
+  int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
@@ -253,13 +259,13 @@ __global__ void k_ss_div(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, in
 }
 
 template <typename R>
-__global__ void k_ss_grad(Geo<R> G, VR<R> U, Work<R> T, int kchunk) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void d_ss_grad(Geo<R> G, VR<R> U, Work<R> T, int kchunk, int bx, int by) {
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
   W7x3<R> wg = load_w7x3(G.wgrad, S, c);
-  int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
+  int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
@@ -274,16 +280,16 @@ __global__ void k_ss_grad(Geo<R> G, VR<R> U, Work<R> T, int kchunk) {
 
 // Eq. mom2 with the divergence damping: M* <- proj(M* + dtau(-grad p* + DD + S_M))
 template <typename R>
-__global__ void k_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, R Kd,
-                         int divdamp, int kchunk) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void d_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, R Kd,
+                                            int divdamp, int kchunk, int bx, int by) {
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
   W7x3<R> wg = load_w7x3(G.wgrad, S, c);
   W7<R> wl = load_w7(G.wlap, S, c);
   R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
-  int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
+  int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
@@ -314,13 +320,13 @@ __global__ void k_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R 
 //   b_k = Th*_k + dtau (S_th,k - div_h(theta M*)_k)
 //   c_k = p*_k + Pi_k (b_k - Th*_k)        (p* advanced linearly in Th)
 template <typename R>
-__global__ void k_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, int kchunk) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void d_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, int kchunk, int bx, int by) {
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
   W7x3<R> wd = load_w7x3(G.wdiv, S, c);
-  int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
+  int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
@@ -362,11 +368,11 @@ __global__ void k_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R
 // sub-partitions. Stored per row: the pivot reciprocal, c' or e', and lo or
 // up; per column: 1 / (1 - c'_p e'_p+1) for the junction rows p, p+1.
 template <typename R>
-__global__ void __launch_bounds__(64) k_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> SL, Fac F,
-                                                  double dtau) {
+__device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> SL, Fac F,
+                                            double dtau, int bx, int by) {
   const int nv = G.nv, S = G.colp, N = nv - 1;
   const int tx = threadIdx.x & 31, half = threadIdx.x >> 5;
-  const int c = blockIdx.x * 32 + tx;
+  const int c = bx * 32 + tx;
   const bool valid = c < G.ncol;
   const int cs = valid ? c : 0;          // padding lanes compute on column 0 and store nothing
   const int p = N / 2 > 0 ? N / 2 : 1;
@@ -427,13 +433,13 @@ __global__ void __launch_bounds__(64) k_ss_factor(Geo<R> G, VR<R> U, Phys ph, Sl
 // and pt2 and p* from the nonlinear Eq. theta_to_p. One block = 32 columns
 // x 2 warps.
 template <typename R>
-__global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs, Slow<R> SL,
-                                                 Pert<R> P, Work<R> T, Fac F, double dtau,
-                                                 int want_div) {
+__device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs, Slow<R> SL,
+                                            Pert<R> P, Work<R> T, Fac F, double dtau,
+                                            int want_div, int bx, int by) {
   extern __shared__ double sm[];
   const int nv = G.nv, S = G.colp, N = nv - 1;
   const int tx = threadIdx.x & 31, half = threadIdx.x >> 5;
-  const int c = blockIdx.x * 32 + tx;
+  const int c = bx * 32 + tx;
   const bool valid = c < G.ncol;
   const int cs = valid ? c : 0;          // padding lanes read column 0 and store nothing
   double* sdp = sm;                      // [nv + 1][32] d' / f', then W
@@ -527,11 +533,11 @@ __global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<
 
 // Phi^(s+1) = Phi^(s) + Phi*
 template <typename R>
-__global__ void k_stage_end(Geo<R> G, Xf<R> Xs, Pert<R> P, Xf<R> Xo, int kchunk) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void d_stage_end(Geo<R> G, Xf<R> Xs, Pert<R> P, Xf<R> Xo, int kchunk, int bx, int by) {
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
-  int k0 = blockIdx.y * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
+  int k0 = by * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     int i = k * S + c;
@@ -553,8 +559,8 @@ __global__ void k_stage_end(Geo<R> G, Xf<R> Xs, Pert<R> P, Xf<R> Xo, int kchunk)
 // coefficients; sigma = p / p_s with p_s extrapolated hydrostatically at the
 // lowest layer's temperature.
 template <typename R>
-__global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, int forcing, double dt, double hj_dT) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void d_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, int forcing, double dt, double hj_dT, int bx, int by) {
+  int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
   const R gamma = (R)ph.gamma, inv_gamma = R(1.0 / ph.gamma), Rd = (R)ph.Rd;
@@ -610,30 +616,175 @@ __global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, int forcing, doub
   }
 }
 
+// ---------------------------------------------------------------- kernels: one state
+
+template <typename R>
+__global__ void k_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int kchunk) {
+  d_derived<R>(G, U, ph, X, T, kchunk, blockIdx.x, blockIdx.y);
+}
+template <typename R>
+__global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk) {
+  d_lap1<R>(G, U, X, T, Kd, kchunk, blockIdx.x, blockIdx.y);
+}
+template <typename R>
+__global__ void __launch_bounds__(kMaxBlock, 2)
+    k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper, int kchunk) {
+  d_slow<R>(G, U, ph, X, T, SL, hyper, kchunk, blockIdx.x, blockIdx.y);
+}
+template <typename R>
+__global__ void k_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper, int kchunk) {
+  d_slow_w<R>(G, U, ph, X, T, SL, hyper, kchunk, blockIdx.x, blockIdx.y);
+}
+template <typename R>
+__global__ void k_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> Xs, Work<R> T, Pert<R> P, int kchunk) {
+  d_stage_init<R>(G, U, ph, Xt, Xs, T, P, kchunk, blockIdx.x, blockIdx.y);
+}
+template <typename R>
+__global__ void k_ss_div(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, int kchunk) {
+  d_ss_div<R>(G, U, SL, P, T, kchunk, blockIdx.x, blockIdx.y);
+}
+template <typename R>
+__global__ void k_ss_grad(Geo<R> G, VR<R> U, Work<R> T, int kchunk) {
+  d_ss_grad<R>(G, U, T, kchunk, blockIdx.x, blockIdx.y);
+}
+template <typename R>
+__global__ void k_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, R Kd, int divdamp,
+                         int kchunk) {
+  d_ss_mom<R>(G, U, SL, P, T, dtau, Kd, divdamp, kchunk, blockIdx.x, blockIdx.y);
+}
+template <typename R>
+__global__ void k_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, int kchunk) {
+  d_ss_flux<R>(G, U, SL, P, T, dtau, kchunk, blockIdx.x, blockIdx.y);
+}
+template <typename R>
+__global__ void __launch_bounds__(64) k_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> SL, Fac F, double dtau) {
+  d_ss_factor<R>(G, U, ph, SL, F, dtau, blockIdx.x, 0);
+}
+template <typename R>
+__global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs, Slow<R> SL, Pert<R> P,
+                                                 Work<R> T, Fac F, double dtau, int want_div) {
+  d_ss_solve<R>(G, U, ph, Xs, SL, P, T, F, dtau, want_div, blockIdx.x, 0);
+}
+template <typename R>
+__global__ void k_stage_end(Geo<R> G, Xf<R> Xs, Pert<R> P, Xf<R> Xo, int kchunk) {
+  d_stage_end<R>(G, Xs, P, Xo, kchunk, blockIdx.x, blockIdx.y);
+}
+template <typename R>
+__global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, int forcing, double dt, double hj_dT) {
+  d_physics<R>(G, U, ph, X, forcing, dt, hj_dT, blockIdx.x, 0);
+}
+
+// ---------------------------------------------------------------- kernels: ensemble
+//
+// One launch covers every member: block b of the launch works on local block
+// map[b].y of member map[b].x, whose arrays and constants come from the
+// member table. Per-member switches (hyperdiffusion, divergence damping,
+// forcing) are uniform over a block. s is the RK stage, j the small step.
+
+#define THOR_MEMBER()                 \
+  const int2 e = map[blockIdx.x];     \
+  const Member<R>& a = M[e.x];        \
+  const Xf<R> Xs = s == 0 ? a.Xt : a.Xst
+
+template <typename R>
+__global__ void ke_derived(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
+  THOR_MEMBER();
+  d_derived<R>(a.G, a.U, a.ph, Xs, a.T, kchunk, e.y, blockIdx.y);
+}
+template <typename R>
+__global__ void ke_lap1(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
+  THOR_MEMBER();
+  if (a.hyper) d_lap1<R>(a.G, a.U, Xs, a.T, a.Kd, kchunk, e.y, blockIdx.y);
+}
+template <typename R>
+__global__ void __launch_bounds__(kMaxBlock, 2)
+    ke_slow(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
+  THOR_MEMBER();
+  d_slow<R>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, kchunk, e.y, blockIdx.y);
+}
+template <typename R>
+__global__ void ke_slow_w(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
+  THOR_MEMBER();
+  d_slow_w<R>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, kchunk, e.y, blockIdx.y);
+}
+template <typename R>
+__global__ void ke_stage_init(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
+  THOR_MEMBER();
+  d_stage_init<R>(a.G, a.U, a.ph, a.Xt, Xs, a.T, a.P, kchunk, e.y, blockIdx.y);
+}
+template <typename R>
+__global__ void __launch_bounds__(64)
+    ke_ss_factor(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s) {
+  THOR_MEMBER();
+  d_ss_factor<R>(a.G, a.U, a.ph, a.SL, a.F, a.dts[s], e.y, 0);
+}
+template <typename R>
+__global__ void ke_ss_div(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
+  THOR_MEMBER();
+  if (a.divdamp) d_ss_div<R>(a.G, a.U, a.SL, a.P, a.T, kchunk, e.y, blockIdx.y);
+}
+template <typename R>
+__global__ void ke_ss_grad(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
+  THOR_MEMBER();
+  if (a.divdamp) d_ss_grad<R>(a.G, a.U, a.T, kchunk, e.y, blockIdx.y);
+}
+template <typename R>
+__global__ void ke_ss_mom(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
+  THOR_MEMBER();
+  d_ss_mom<R>(a.G, a.U, a.SL, a.P, a.T, (R)a.dts[s], a.Kd, a.divdamp, kchunk, e.y, blockIdx.y);
+}
+template <typename R>
+__global__ void ke_ss_flux(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
+  THOR_MEMBER();
+  d_ss_flux<R>(a.G, a.U, a.SL, a.P, a.T, (R)a.dts[s], kchunk, e.y, blockIdx.y);
+}
+template <typename R>
+__global__ void __launch_bounds__(64)
+    ke_ss_solve(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int j) {
+  THOR_MEMBER();
+  const int want_div = a.divdamp && j + 1 < a.nsub[s];
+  d_ss_solve<R>(a.G, a.U, a.ph, Xs, a.SL, a.P, a.T, a.F, a.dts[s], want_div, e.y, 0);
+}
+template <typename R>
+__global__ void ke_stage_end(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
+  THOR_MEMBER();
+  d_stage_end<R>(a.G, Xs, a.P, s == 2 ? a.Xt : a.Xst, kchunk, e.y, blockIdx.y);
+}
+template <typename R>
+__global__ void ke_physics(const Member<R>* __restrict__ M, const int2* __restrict__ map) {
+  const int2 e = map[blockIdx.x];
+  const Member<R>& a = M[e.x];
+  if (a.forcing) d_physics<R>(a.G, a.U, a.ph, a.Xt, a.forcing, a.dt, a.hj_dT, e.y, 0);
+}
+#undef THOR_MEMBER
+
 // ---------------------------------------------------------------- driver
 
 template <typename R>
 void Impl<R>::launch_2d(int nplanes, int kchunk, dim3& grid) const {
-  grid = dim3((G.ncol + kBlock - 1) / kBlock, (nplanes + kchunk - 1) / kchunk);
+  grid = dim3((G.ncol + block - 1) / block, (nplanes + kchunk - 1) / kchunk);
 }
 
 size_t solve_smem_bytes(int nv) { return (size_t)((nv + 1) + 2) * 32 * sizeof(double); }
 
 template <typename R>
 int col_kernel_setup(int nv) {
-  return cudaFuncSetAttribute(k_ss_solve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)solve_smem_bytes(nv)) == cudaSuccess ? 0 : -3;
+  const int bytes = (int)solve_smem_bytes(nv);
+  if (cudaFuncSetAttribute(k_ss_solve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+    return -3;
+  return cudaFuncSetAttribute(ke_ss_solve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess
+             ? 0 : -3;
 }
 template int col_kernel_setup<double>(int);
 template int col_kernel_setup<float>(int);
 
 template <typename R>
 int Impl<R>::large_step(double dt, int n_small) {
-  const int kc = kchunk;
+  const int kc = kchunk, bs = block;
   dim3 g2, g2i;
   launch_2d(G.nv, kc, g2);
   launch_2d(G.nv + 1, kc, g2i);
-  dim3 g1((G.ncol + kBlock - 1) / kBlock);
+  dim3 g1((G.ncol + bs - 1) / bs);
   dim3 gsolve((G.ncol + 31) / 32);
   const size_t solve_smem = solve_smem_bytes(G.nv);
   const R Kd = (R)(diff_D * dbar4 / dt);
@@ -642,23 +793,23 @@ int Impl<R>::large_step(double dt, int n_small) {
   for (int s = 0; s < 3; ++s) {
     Xf<R> Xs = s == 0 ? Xt : Xst;
     mark(THOR_K_DERIVED, true);
-    k_derived<R><<<g2i, kBlock, 0, stream>>>(G, U, ph, Xs, T, kc);
+    k_derived<R><<<g2i, bs, 0, stream>>>(G, U, ph, Xs, T, kc);
     mark(THOR_K_DERIVED, false);
     ++launches;
     if (hyper) {
       mark(THOR_K_LAP1, true);
-      k_lap1<R><<<g2i, kBlock, 0, stream>>>(G, U, Xs, T, Kd, kc);
+      k_lap1<R><<<g2i, bs, 0, stream>>>(G, U, Xs, T, Kd, kc);
       mark(THOR_K_LAP1, false);
       ++launches;
     }
     mark(THOR_K_SLOW, true);
-    k_slow<R><<<g2, kBlock, 0, stream>>>(G, U, ph, Xs, T, SL, hyper, kc);
+    k_slow<R><<<g2, bs, 0, stream>>>(G, U, ph, Xs, T, SL, hyper, kc);
     mark(THOR_K_SLOW, false);
     mark(THOR_K_SLOW_W, true);
-    k_slow_w<R><<<g2i, kBlock, 0, stream>>>(G, U, ph, Xs, T, SL, hyper, kc);
+    k_slow_w<R><<<g2i, bs, 0, stream>>>(G, U, ph, Xs, T, SL, hyper, kc);
     mark(THOR_K_SLOW_W, false);
     mark(THOR_K_STAGE_INIT, true);
-    k_stage_init<R><<<g2i, kBlock, 0, stream>>>(G, U, ph, Xt, Xs, T, P, kc);
+    k_stage_init<R><<<g2i, bs, 0, stream>>>(G, U, ph, Xt, Xs, T, P, kc);
     mark(THOR_K_STAGE_INIT, false);
     mark(THOR_K_SS_FACTOR, true);
     k_ss_factor<R><<<gsolve, 64, 0, stream>>>(G, U, ph, SL, F, dts[s]);
@@ -668,20 +819,20 @@ int Impl<R>::large_step(double dt, int n_small) {
       if (divdamp) {
         if (j == 0) {   // later small steps get D from the previous k_ss_solve
           mark(THOR_K_SS_DIV, true);
-          k_ss_div<R><<<g2, kBlock, 0, stream>>>(G, U, SL, P, T, kc);
+          k_ss_div<R><<<g2, bs, 0, stream>>>(G, U, SL, P, T, kc);
           mark(THOR_K_SS_DIV, false);
           ++launches;
         }
         mark(THOR_K_SS_GRAD, true);
-        k_ss_grad<R><<<g2, kBlock, 0, stream>>>(G, U, T, kc);
+        k_ss_grad<R><<<g2, bs, 0, stream>>>(G, U, T, kc);
         mark(THOR_K_SS_GRAD, false);
         ++launches;
       }
       mark(THOR_K_SS_MOM, true);
-      k_ss_mom<R><<<g2, kBlock, 0, stream>>>(G, U, SL, P, T, (R)dts[s], Kd, divdamp, kc);
+      k_ss_mom<R><<<g2, bs, 0, stream>>>(G, U, SL, P, T, (R)dts[s], Kd, divdamp, kc);
       mark(THOR_K_SS_MOM, false);
       mark(THOR_K_SS_FLUX, true);
-      k_ss_flux<R><<<g2, kBlock, 0, stream>>>(G, U, SL, P, T, (R)dts[s], kc);
+      k_ss_flux<R><<<g2, bs, 0, stream>>>(G, U, SL, P, T, (R)dts[s], kc);
       mark(THOR_K_SS_FLUX, false);
       mark(THOR_K_SS_COL, true);
       const int want_div = divdamp && j + 1 < nsub[s];
@@ -691,13 +842,13 @@ int Impl<R>::large_step(double dt, int n_small) {
     }
     Xf<R> Xo = s == 2 ? Xt : Xst;
     mark(THOR_K_STAGE_END, true);
-    k_stage_end<R><<<g2i, kBlock, 0, stream>>>(G, Xs, P, Xo, kc);
+    k_stage_end<R><<<g2i, bs, 0, stream>>>(G, Xs, P, Xo, kc);
     mark(THOR_K_STAGE_END, false);
     ++launches;
   }
   if (forcing != 0) {
     mark(THOR_K_PHYSICS, true);
-    k_physics<R><<<g1, kBlock, 0, stream>>>(G, U, ph, Xt, forcing, dt, hj_dT);
+    k_physics<R><<<g1, bs, 0, stream>>>(G, U, ph, Xt, forcing, dt, hj_dT);
     mark(THOR_K_PHYSICS, false);
     ++launches;
   }
@@ -708,5 +859,58 @@ template void Impl<double>::launch_2d(int, int, dim3&) const;
 template void Impl<float>::launch_2d(int, int, dim3&) const;
 template int Impl<double>::large_step(double, int);
 template int Impl<float>::large_step(double, int);
+
+// One large step of every member of an ensemble, one launch per kernel of
+// the sequence above. Members are ordered by decreasing n_small, so the
+// members still in their small-step loop at step j of a stage are a prefix
+// of the block maps.
+template <typename R>
+int ensemble_large_step(const EnsPlan<R>& E, cudaStream_t stream, long long* launches) {
+  const int kc = E.kchunk, bs = E.block;
+  const int yc = (E.nv + kc - 1) / kc, yci = (E.nv + 1 + kc - 1) / kc;
+  const size_t solve_smem = solve_smem_bytes(E.nv);
+  const Member<R>* M = E.M;
+  long long n = 0;
+  for (int s = 0; s < 3; ++s) {
+    const dim3 g2(E.nblk, yc), g2i(E.nblk, yci);
+    ke_derived<R><<<g2i, bs, 0, stream>>>(M, E.map, s, kc);
+    if (E.any_hyper) {
+      ke_lap1<R><<<g2i, bs, 0, stream>>>(M, E.map, s, kc);
+      ++n;
+    }
+    ke_slow<R><<<g2, bs, 0, stream>>>(M, E.map, s, kc);
+    ke_slow_w<R><<<g2i, bs, 0, stream>>>(M, E.map, s, kc);
+    ke_stage_init<R><<<g2i, bs, 0, stream>>>(M, E.map, s, kc);
+    ke_ss_factor<R><<<E.nblkc, 64, 0, stream>>>(M, E.mapc, s);
+    n += 5;
+    for (int j = 0; j < E.maxsub[s]; ++j) {
+      const int nb = E.active[s][j], nbc = E.activec[s][j];
+      const dim3 a2(nb, yc);
+      if (E.any_divdamp) {
+        if (j == 0) {
+          ke_ss_div<R><<<a2, bs, 0, stream>>>(M, E.map, s, kc);
+          ++n;
+        }
+        ke_ss_grad<R><<<a2, bs, 0, stream>>>(M, E.map, s, kc);
+        ++n;
+      }
+      ke_ss_mom<R><<<a2, bs, 0, stream>>>(M, E.map, s, kc);
+      ke_ss_flux<R><<<a2, bs, 0, stream>>>(M, E.map, s, kc);
+      ke_ss_solve<R><<<nbc, 64, solve_smem, stream>>>(M, E.mapc, s, j);
+      n += 3;
+    }
+    ke_stage_end<R><<<g2i, bs, 0, stream>>>(M, E.map, s, kc);
+    ++n;
+  }
+  if (E.any_forcing) {
+    ke_physics<R><<<E.nblk, bs, 0, stream>>>(M, E.map);
+    ++n;
+  }
+  *launches += n;
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+template int ensemble_large_step<double>(const EnsPlan<double>&, cudaStream_t, long long*);
+template int ensemble_large_step<float>(const EnsPlan<float>&, cudaStream_t, long long*);
 
 }  // namespace thor
