@@ -343,7 +343,7 @@ def _double_array(v):
 
 
 def thor_ensemble_create(members, stream=None):
-    arr = (ctypes.c_void_p * len(members))(*[m.value if hasattr(m, "value") else m for m in members])
+    arr = (ctypes.c_void_p * max(len(members), 1))(*[m.value if hasattr(m, "value") else m for m in members])
     out = ctypes.c_void_p()
     _check(_lib.thor_ensemble_create(arr, len(members), ctypes.c_void_p(stream or 0), ctypes.byref(out)),
            "thor_ensemble_create")

@@ -33,6 +33,27 @@ def test_invalid_arguments():
     assert thor.thor_strerror(thor.THOR_ETIMEOUT) == "device wait timed out"
 
 
+def test_ensemble_argument_checks_need_no_device():
+    """Argument errors of the ensemble and autotuner entry points are caught
+    on the host, before any CUDA call."""
+    for members in ([], [None]):
+        with pytest.raises(thor.ThorError) as e:
+            thor.thor_ensemble_create(members)
+        assert e.value.status == thor.THOR_EINVAL
+    with pytest.raises(thor.ThorError) as e:
+        thor.thor_ensemble_create([None] * (thor.THOR_ENSEMBLE_MAX + 1))
+    assert e.value.status == thor.THOR_EINVAL
+    for call in (lambda: thor.thor_ensemble_step(None, 1, [8], [600.0]),
+                 lambda: thor.thor_ensemble_tune(None, thor.THOR_TUNE_BLOCK, 128),
+                 lambda: thor.thor_ensemble_info(None),
+                 lambda: thor.thor_autotune(None, 8, 600.0),
+                 lambda: thor.thor_ensemble_autotune(None, [8], [600.0])):
+        with pytest.raises(thor.ThorError) as e:
+            call()
+        assert e.value.status == thor.THOR_EINVAL
+    thor.thor_ensemble_destroy(None)
+
+
 def _match(P, O):
     d, idx = cKDTree(O.points).query(P)
     assert len(np.unique(idx)) == len(idx)

@@ -128,3 +128,40 @@ def temperature_noise(wl, ncol=None):
     ncol = wl.ncol if ncol is None else ncol
     idx = np.arange(ncol, dtype=np.uint64)[:, None] * np.uint64(wl.nv) + np.arange(wl.nv, dtype=np.uint64)[None, :]
     return uniform01(wl.seed, idx)
+
+
+# Batched ensemble: 64 independent Held-Suarez atmospheres x 32 levels on
+# glevels drawn from {3, 4, 5}, radius and rotation rate each drawn
+# log-uniform over [0.1, 10] x Earth from one seed. The time step keeps the
+# Courant numbers of the glevel-5 Earth case (dt 1200 s, 8 small steps): it
+# scales with the grid spacing, radius * 2^-glevel, and is capped at
+# 1 / (4 Omega) so that the explicit Coriolis term stays well inside the RK3
+# stability region.
+ENSEMBLE_SEED = 0xE45E
+
+
+@dataclass(frozen=True)
+class EnsembleMember:
+    glevel: int
+    planet: PlanetParams
+    dt: float
+    n_small: int = 8
+
+    @property
+    def ncol(self):
+        return 10 * 4 ** self.glevel + 2
+
+
+def ensemble_members(n=64, seed=ENSEMBLE_SEED, glevels=(3, 4, 5), n_small=8):
+    out = []
+    for i in range(n):
+        u = [float(uniform01(seed, 3 * i + j)) for j in range(3)]
+        g = glevels[min(int(u[0] * len(glevels)), len(glevels) - 1)]
+        radius = EARTH.radius * 10.0 ** (2.0 * u[1] - 1.0)
+        omega = EARTH.omega * 10.0 ** (2.0 * u[2] - 1.0)
+        dt = min(1200.0 * (radius / EARTH.radius) * 2.0 ** (5 - g), 0.25 / omega)
+        out.append(EnsembleMember(g, replace(EARTH, radius=radius, omega=omega), dt, n_small))
+    return out
+
+
+ENSEMBLE_NV, ENSEMBLE_Z_TOP = 32, 36.0e3
