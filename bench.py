@@ -323,6 +323,8 @@ def run_thor(args):
     value64 = world * cells * sn * k64 / (ms64 / 1e3)
     thor.thor_grid_destroy(grid)
 
+    ens = run_ensemble(thor, torch, dev, stream, args, max_over_ranks) if not args.no_ensemble else None
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -346,6 +348,8 @@ def run_thor(args):
         "clocks": clocks,
         "diag_after": {k: diag[k] for k in ("mass", "max_vh", "max_w", "mean_T", "nonfinite")},
     }
+    if ens is not None:
+        line["ensemble"] = ens
     if world == 1 and not args.no_cpu_baseline:
         _, _, _, t_slow, t_small, t_phys = oracle_sample(wl)
         per_large = 3 * t_slow + sn * t_small + t_phys
@@ -360,6 +364,71 @@ def run_thor(args):
     return 0
 
 
+def run_ensemble(thor, torch, dev, stream, args, max_over_ranks):
+    """Batched ensemble: 64 Held-Suarez atmospheres (glevels 3-5 x 32 levels,
+    radius and rotation log-uniform over [0.1, 10] x Earth, seeded), mixed
+    precision. Launch shape from the autotuner, then K ensemble large steps
+    timed with CUDA events; the same members stepped one after another (each
+    with its own graph) for comparison."""
+    members = wls.ensemble_members()
+    sp = thor.thor_spring(1.15, 1.0, 1.0, 0.01, 0.0, 10)
+    grids, states = [], []
+    for i, m in enumerate(members):
+        P = m.planet
+        g = thor.thor_grid_create(m.glevel, wls.ENSEMBLE_NV, P.radius, wls.ENSEMBLE_Z_TOP, sp)
+        planet = thor.thor_planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+        init = thor.thor_init(300.0, 1.0e5, 0.1, wls.ENSEMBLE_SEED + i, 1, 300.0, thor.THOR_MIXED, 1, 1)
+        grids.append(g)
+        states.append(thor.thor_state_init(g, planet, init, stream.cuda_stream))
+    n_small = [m.n_small for m in members]
+    dts = [m.dt for m in members]
+    cell_substeps = sum(m.ncol * wls.ENSEMBLE_NV * (1 + n // 2 + n) for m, n in zip(members, n_small))
+    ens = thor.thor_ensemble_create(states, stream.cuda_stream)
+    kc, bs, ms_tuned = thor.thor_ensemble_autotune(ens, n_small, dts, steps=2)
+    for _ in range(args.warmup):
+        thor.thor_ensemble_step(ens, 1, n_small, dts)
+    torch.cuda.synchronize(dev)
+    k = max(1, min(args.steps, 10))
+    l0 = thor.thor_ensemble_info(ens)["launches"]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    thor.thor_ensemble_step(ens, k, n_small, dts)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(a.elapsed_time(b))
+    launches = thor.thor_ensemble_info(ens)["launches"] - l0
+    thor.thor_ensemble_destroy(ens)
+    # the same members one after another, each replaying its own graph
+    for s_, n_, d_ in zip(states, n_small, dts):
+        thor.thor_tune(s_, thor.THOR_TUNE_KCHUNK, kc)
+        thor.thor_tune(s_, thor.THOR_TUNE_BLOCK, bs)
+        thor.thor_step(s_, 1, n_, d_)
+    torch.cuda.synchronize(dev)
+    seq_l0 = sum(thor.thor_launch_count(s_) for s_ in states)
+    a.record(stream)
+    for _ in range(k):
+        for s_, n_, d_ in zip(states, n_small, dts):
+            thor.thor_step(s_, 1, n_, d_)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_seq = max_over_ranks(a.elapsed_time(b))
+    nonfinite = sum(thor.thor_diag(s_)["nonfinite"] for s_ in states)
+    seq_launches = sum(thor.thor_launch_count(s_) for s_ in states) - seq_l0
+    for s_ in states:
+        thor.thor_state_destroy(s_)
+    for g in grids:
+        thor.thor_grid_destroy(g)
+    world = _env_int("WORLD_SIZE", 1)
+    return {"workload": "held_suarez_ensemble_64_g3-5_L32", "members": len(members),
+            "columns": sum(m.ncol for m in members), "levels": wls.ENSEMBLE_NV,
+            "value": world * cell_substeps * k / (ms / 1e3), "unit": METRIC, "steps": k,
+            "ms_per_step": ms / k, "gpu_launches": launches, "launches_per_step": launches / k,
+            "autotuned": {"kchunk": kc, "block": bs, "ms_per_step": ms_tuned},
+            "sequential": {"value": world * cell_substeps * k / (ms_seq / 1e3), "ms_per_step": ms_seq / k,
+                           "launches_per_step": seq_launches / k},
+            "speedup_vs_sequential": ms_seq / ms, "nonfinite": nonfinite, "dtype": "f32"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,6 +437,7 @@ def main():
     ap.add_argument("--impl", default="thor", choices=["thor", "reference"])
     ap.add_argument("--workload", default="hs_g6", choices=["hs_g6", "hs_g4", "hj_g6"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)      # at least 3 untimed warm-up steps
     if args.impl == "reference":
