@@ -168,11 +168,18 @@ int thor_launch_count(const thor_state* state, long long* count);
  * of the state (one reduction and one stream synchronisation per call) and
  * return THOR_ENONFINITE if any value is NaN or Inf; the state is the one
  * after the step (restore a checkpoint with thor_state_set). Default 0. */
-enum { THOR_TUNE_KCHUNK = 0, THOR_TUNE_GRAPH = 1, THOR_TUNE_CHECK_FINITE = 2, THOR_TUNE_BLOCK = 3 };
+enum { THOR_TUNE_KCHUNK = 0, THOR_TUNE_GRAPH = 1, THOR_TUNE_CHECK_FINITE = 2, THOR_TUNE_BLOCK = 3,
+       THOR_TUNE_SOLVE_TMA = 4 };
 int thor_tune(thor_state* state, int knob, int value);
 
 /* THOR_TUNE_BLOCK: threads (one per column) in a block of the stencil
- * kernels, a multiple of 32 in [32, 256] (default 128). */
+ * kernels, a multiple of 32 in [32, 256] (default 128).
+ * THOR_TUNE_SOLVE_TMA: 1 (default) runs the column solve of a THOR_MIXED
+ * state with its planes staged into shared memory by TMA bulk-tensor copies
+ * (where the staging fits, nv <= 80); 0 runs the direct-load solve. Same
+ * arithmetic, same results. A staged copy that has not landed after 2 s ends
+ * the kernel with a device error flag; thor_diag (and thor_step with
+ * THOR_TUNE_CHECK_FINITE) then return THOR_ETIMEOUT. */
 
 /* Launch-shape autotuner (an extension; the paper fixes no launch shapes).
  * Times `steps` large steps of (n_small, dt) for every levels-per-thread

@@ -21,7 +21,7 @@ THOR_FP64, THOR_MIXED = 0, 1
 THOR_FORCING_NONE, THOR_FORCING_HELD_SUAREZ, THOR_FORCING_HOT_JUPITER = 0, 1, 2
 THOR_FIELD_RHO, THOR_FIELD_MOM, THOR_FIELD_W, THOR_FIELD_RHOTHETA, THOR_FIELD_PRESSURE, \
     THOR_FIELD_TEMPERATURE = range(6)
-THOR_TUNE_KCHUNK, THOR_TUNE_GRAPH, THOR_TUNE_CHECK_FINITE, THOR_TUNE_BLOCK = range(4)
+THOR_TUNE_KCHUNK, THOR_TUNE_GRAPH, THOR_TUNE_CHECK_FINITE, THOR_TUNE_BLOCK, THOR_TUNE_SOLVE_TMA = range(5)
 THOR_ENSEMBLE_MAX = 4096
 
 EXPORTED = [

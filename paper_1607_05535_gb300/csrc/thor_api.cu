@@ -154,25 +154,44 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Geo<R> G, Vert V,
     for (int j = 0; j < 8; ++j) part[blockIdx.x * 8 + j] = sh[j][0];
 }
 
-__global__ void k_diag_final(double* part, int nblocks) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double out[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  double comp[5] = {0, 0, 0, 0, 0};
-  for (int b = 0; b < nblocks; ++b)
-    for (int j = 0; j < 8; ++j) {
-      double x = part[b * 8 + j];
-      if (j == 5 || j == 6) {
-        out[j] = fmax(out[j], x);
-      } else if (j == 7) {
-        out[j] += x;
+// One warp per quantity: every lane sums a strided share of the block
+// partials (compensated), then lane 0 adds the 32 lane sums in order
+// (compensated); extrema by max, the non-finite count by plain addition.
+__global__ void __launch_bounds__(256) k_diag_final(double* part, int nblocks) {
+  const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ double lanes[8][32];
+  const bool is_max = j == 5 || j == 6, is_count = j == 7;
+  double s = 0.0, comp = 0.0;
+  for (int b = lane; b < nblocks; b += 32) {
+    const double x = part[b * 8 + j];
+    if (is_max) {
+      s = fmax(s, x);
+    } else if (is_count) {
+      s += x;
+    } else {
+      const double y = x - comp, t = s + y;
+      comp = (t - s) - y;
+      s = t;
+    }
+  }
+  lanes[j][lane] = s;
+  __syncwarp();
+  if (lane == 0) {
+    double o = 0.0, cm = 0.0;
+    for (int l = 0; l < 32; ++l) {
+      const double x = lanes[j][l];
+      if (is_max) {
+        o = fmax(o, x);
+      } else if (is_count) {
+        o += x;
       } else {
-        double y = x - comp[j];
-        double t = out[j] + y;
-        comp[j] = (t - out[j]) - y;
-        out[j] = t;
+        const double y = x - cm, t = o + y;
+        cm = (t - o) - y;
+        o = t;
       }
     }
-  for (int j = 0; j < 8; ++j) part[nblocks * 8 + j] = out[j];
+    part[nblocks * 8 + j] = o;
+  }
 }
 
 // ------------------------------------------------------------ allocation
@@ -224,7 +243,7 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   P.w = cv.take<R>(F);
   I.F.inv = cv.take<double>(F);
   I.F.cf = cv.take<double>(F);
-  I.F.off = cv.take<double>(F);
+  I.F.off = cv.take<R>(F);
   I.F.junction = cv.take<double>(S);
   // tables
   I.G.nbr = cv.take<int>(6 * S);
@@ -244,6 +263,7 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   for (const R** p : vr_slots(I.U)) *p = cv.take<R>(nv + 1);
   I.staging = cv.take<double>((size_t)ncol * (nv + 1) * 3);
   I.red = cv.take<double>((size_t)(kDiagBlocks + 1) * 8);
+  I.dev_err = cv.take<int>(64);
 }
 
 template <typename R>
@@ -380,11 +400,14 @@ int Impl<R>::set(int field, const double* host, size_t n) {
 template <typename R>
 int Impl<R>::diag(double* out8, long long* nonfinite) {
   k_diag_partial<R><<<kDiagBlocks, kDiagThreads, 0, stream>>>(G, V, ph, Xt, red);
-  k_diag_final<<<1, 32, 0, stream>>>(red, kDiagBlocks);
+  k_diag_final<<<1, 256, 0, stream>>>(red, kDiagBlocks);
   launches += 2;
   double h[8];
+  int flag = 0;
   if (cudaMemcpyAsync(h, red + kDiagBlocks * 8, sizeof(h), cudaMemcpyDeviceToHost, stream)) return THOR_ECUDA;
+  if (cudaMemcpyAsync(&flag, dev_err, sizeof(int), cudaMemcpyDeviceToHost, stream)) return THOR_ECUDA;
   if (cudaStreamSynchronize(stream)) return THOR_ECUDA;
+  if (flag) return THOR_ETIMEOUT;
   for (int j = 0; j < 8; ++j) out8[j] = h[j];
   *nonfinite = (long long)h[7];
   return THOR_OK;
@@ -509,6 +532,7 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
   Carver real{static_cast<char*>(arena)};
   carve(real, *I, h.ncol, h.nv);
   if (col_kernel_setup<R>(h.nv)) return THOR_ECUDA;
+  if (I->build_solve_maps()) return THOR_ECUDA;
   HostSetup hs;
   host_setup(h, pl, in, hs);
   int rc = upload_tables(*I, h, hs.vert, st);
@@ -689,6 +713,10 @@ int thor_tune(thor_state* s, int knob, int value) {
   if (knob == THOR_TUNE_BLOCK) {
     if (value < 32 || value > thor::kMaxBlock || value % 32) return THOR_EINVAL;
     s->impl->block = value;
+    return THOR_OK;
+  }
+  if (knob == THOR_TUNE_SOLVE_TMA) {
+    s->impl->solve_tma = value != 0;
     return THOR_OK;
   }
   return THOR_EINVAL;

@@ -2,6 +2,9 @@
 // ABI. R = double (THOR_FP64) or float (THOR_MIXED).
 #pragma once
 
+#include <cuda.h>
+
+#include <memory>
 #include <vector>
 
 #include "thor_kernels.cuh"
@@ -49,12 +52,19 @@ struct Member {
   Work<R> T;
   Slow<R> SL;
   Pert<R> P;
-  Fac F;
+  Fac<R> F;
   double dt, hj_dT;
   double dts[3];                   // small-step length of each RK stage
   R Kd;                            // hyperdiffusion coefficient for this dt
   int nsub[3];                     // small steps of each RK stage
   int hyper, divdamp, forcing;
+};
+
+// TMA descriptors of the planes the staged column solve reads (float storage):
+// each a 2-D map (x = column, y = plane) with a box of 32 columns x all planes
+struct SolveMaps {
+  CUtensorMap w, sw, cc, ca, thi, cb, pp, th_t, th_s, dsc, dhm;   // float
+  CUtensorMap off, inv, cf, junction;                           // float64 factors
 };
 
 struct ImplBase {
@@ -67,6 +77,8 @@ struct ImplBase {
   long long launches = 0;
   int kchunk = 2;                      // levels per thread in the stencil kernels
   int block = kBlock;                  // threads (columns) per block of the stencil kernels
+  int solve_tma = 1;                   // TMA-staged column solve where available
+  int* dev_err = nullptr;              // device flag: 1 = a bounded device wait timed out
   // copy the prognostic fields to / from a device buffer of state_bytes()
   virtual size_t state_bytes() const = 0;
   virtual int save_state(void* dst) = 0;
@@ -129,7 +141,7 @@ struct Impl : ImplBase {
   Work<R> T;
   Slow<R> SL;
   Pert<R> P;
-  Fac F;
+  Fac<R> F;
   int hyper = 1, divdamp = 1, forcing = 0;
   double diff_D = 0, dbar4 = 0, hj_dT = 300.0;
   // device allocations
@@ -150,7 +162,10 @@ struct Impl : ImplBase {
   // the same; used on a non-default stream when no profiling is recorded
   cudaGraphExec_t graph_exec = nullptr;
   double graph_dt = 0;
-  int graph_n = 0, graph_kc = 0, graph_bs = 0;
+  int graph_n = 0, graph_kc = 0, graph_bs = 0, graph_tma = -1;
+  std::unique_ptr<SolveMaps> smaps;   // null where the staged solve does not apply
+  int build_solve_maps();
+  void launch_solve_tma(dim3 grid, int stage0, double dtau, int want_div);
   long long graph_launches = 0;
   void drop_graph() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -158,7 +173,8 @@ struct Impl : ImplBase {
   }
   int step(int n_large, int n_small, double dt) override {
     if (use_graph && stream != nullptr && !prof_on && n_large > 0) {
-      if (!graph_exec || graph_dt != dt || graph_n != n_small || graph_kc != kchunk || graph_bs != block) {
+      if (!graph_exec || graph_dt != dt || graph_n != n_small || graph_kc != kchunk || graph_bs != block ||
+          graph_tma != solve_tma) {
         drop_graph();
         cudaGraph_t g = nullptr;
         long long before = launches;
@@ -182,6 +198,7 @@ struct Impl : ImplBase {
         graph_n = n_small;
         graph_kc = kchunk;
         graph_bs = block;
+        graph_tma = solve_tma;
       }
       for (int i = 0; i < n_large; ++i) {
         if (cudaGraphLaunch(graph_exec, stream)) return -3;

@@ -78,10 +78,14 @@ struct Phys {
   double Rd, cp, cv, gamma, kappa, g, omega, p_ref;
 };
 
-// Float64 factors of the per-stage vertical matrix: planes [nv + 1][colp]
-// (rows 1..nv-1 used) and one plane for the junction of the two sweeps
+// Factors of the per-stage vertical matrix: planes [nv + 1][colp] (rows
+// 1..nv-1 used) and one plane for the junction of the two sweeps. Pivot
+// reciprocals, c' / e' and the junction factor are float64; the off-diagonal
+// entries lo / up are assembled in the storage type, so they are kept in it.
+template <typename R>
 struct Fac {
-  double *inv, *cf, *off, *junction;
+  double *inv, *cf, *junction;
+  R* off;
 };
 
 // state in deviation form
@@ -236,3 +240,70 @@ __device__ __forceinline__ void project(R rx, R ry, R rz, R& x, R& y, R& z) {
 }
 
 }  // namespace thor
+
+// ------------------------------------------------------------ TMA staging
+//
+// Thin wrappers over the PTX mbarrier and bulk-tensor instructions. A block
+// stages a box of planes into shared memory with cp.async.bulk.tensor; the
+// copy engine signals completion on an mbarrier by transaction bytes. Every
+// wait is bounded in time, so a copy that never lands ends the kernel with
+// an error flag instead of a hang.
+
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// makes the initialised barriers visible to the copy engine
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// the one expected arrival, with the byte count the copies will deliver
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// L2 prefetch of a box of a 2-D tensor map (no shared memory, no completion)
+__device__ __forceinline__ void tma_prefetch_2d(const void* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
+}
+// true once the barrier's phase `parity` has completed; false after kWaitNs
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < (1 << 26); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+    __nanosleep(32);
+  }
+  return false;
+}
+// box of a 2-D tensor map (x = column, y = plane) into shared memory
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}

@@ -368,7 +368,7 @@ __device__ __forceinline__ void d_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R>
 // sub-partitions. Stored per row: the pivot reciprocal, c' or e', and lo or
 // up; per column: 1 / (1 - c'_p e'_p+1) for the junction rows p, p+1.
 template <typename R>
-__device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> SL, Fac F,
+__device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> SL, Fac<R> F,
                                             double dtau, int bx, int by) {
   const int nv = G.nv, S = G.colp, N = nv - 1;
   const int tx = threadIdx.x & 31, half = threadIdx.x >> 5;
@@ -403,7 +403,7 @@ __device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> 
       if (valid) {
         F.inv[m * S + c] = inv;
         F.cf[m * S + c] = last;
-        F.off[m * S + c] = lo;
+        F.off[m * S + c] = (R)lo;
       }
     }
   } else {
@@ -415,7 +415,7 @@ __device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> 
       if (valid) {
         F.inv[m * S + c] = inv;
         F.cf[m * S + c] = last;
-        F.off[m * S + c] = up;
+        F.off[m * S + c] = (R)up;
       }
     }
   }
@@ -434,7 +434,7 @@ __device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> 
 // x 2 warps.
 template <typename R>
 __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs, Slow<R> SL,
-                                            Pert<R> P, Work<R> T, Fac F, double dtau,
+                                            Pert<R> P, Work<R> T, Fac<R> F, double dtau,
                                             int want_div, int bx, int by) {
   extern __shared__ double sm[];
   const int nv = G.nv, S = G.colp, N = nv - 1;
@@ -444,6 +444,7 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
   const int cs = valid ? c : 0;          // padding lanes read column 0 and store nothing
   double* sdp = sm;                      // [nv + 1][32] d' / f', then W
   double* sx = sdp + (nv + 1) * 32;      // [2][32] junction values
+  double* scf = sx + 64;                 // [nv + 1][32] c' / e', fetched during the sweeps
   const int p = N / 2 > 0 ? N / 2 : 1;
   const R rdt = (R)dtau, g = (R)ph.g;
 
@@ -460,7 +461,8 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
 #pragma unroll 4
     for (int m = 1; m <= p; ++m) {
       const int i = m * S + cs;
-      d1 = (rhs(m) - ld(F.off + i) * d1) * ld(F.inv + i);
+      scf[m * 32 + tx] = ld(F.cf + i);
+      d1 = (rhs(m) - (double)ld(F.off + i) * d1) * ld(F.inv + i);
       sdp[m * 32 + tx] = d1;
     }
   } else {
@@ -468,16 +470,16 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
 #pragma unroll 4
     for (int m = N; m > p; --m) {
       const int i = m * S + cs;
-      f1 = (rhs(m) - ld(F.off + i) * f1) * ld(F.inv + i);
+      scf[m * 32 + tx] = ld(F.cf + i);
+      f1 = (rhs(m) - (double)ld(F.off + i) * f1) * ld(F.inv + i);
       sdp[m * 32 + tx] = f1;
     }
   }
   __syncthreads();
   if (half == 0) {
-    const int ip = p * S + cs;
     double xp, xq = 0.0;
     if (p < N) {
-      const double cp_ = ld(F.cf + ip), eq = ld(F.cf + (ip + S));
+      const double cp_ = scf[p * 32 + tx], eq = scf[(p + 1) * 32 + tx];
       const double dp_ = sdp[p * 32 + tx], fq = sdp[(p + 1) * 32 + tx];
       xp = (dp_ - cp_ * fq) * ld(F.junction + cs);
       xq = fq - eq * xp;
@@ -493,7 +495,7 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
     double x = sx[tx];
     sdp[p * 32 + tx] = x;
     for (int m = p - 1; m >= 1; --m) {
-      x = sdp[m * 32 + tx] - ld(F.cf + (m * S + cs)) * x;
+      x = sdp[m * 32 + tx] - scf[m * 32 + tx] * x;
       sdp[m * 32 + tx] = x;
     }
     sdp[tx] = 0.0;                 // bottom interface
@@ -501,7 +503,7 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
     double x = sx[32 + tx];
     if (p < N) sdp[(p + 1) * 32 + tx] = x;
     for (int m = p + 2; m <= N; ++m) {
-      x = sdp[m * 32 + tx] - ld(F.cf + (m * S + cs)) * x;
+      x = sdp[m * 32 + tx] - scf[m * 32 + tx] * x;
       sdp[m * 32 + tx] = x;
     }
     sdp[nv * 32 + tx] = 0.0;       // top interface
@@ -510,6 +512,7 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
   // Eqs. dens2, pt2, theta_to_p with the new W*; the two warps share the levels
   if (valid) {
     const R gamma = (R)ph.gamma;
+#pragma unroll 4
     for (int k = half; k < nv; k += 2) {
       const int i = k * S + c;
       const R wl = (R)sdp[k * 32 + tx], wh = (R)sdp[(k + 1) * 32 + tx];
@@ -657,12 +660,12 @@ __global__ void k_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R
   d_ss_flux<R>(G, U, SL, P, T, dtau, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
-__global__ void __launch_bounds__(64) k_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> SL, Fac F, double dtau) {
+__global__ void __launch_bounds__(64) k_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> SL, Fac<R> F, double dtau) {
   d_ss_factor<R>(G, U, ph, SL, F, dtau, blockIdx.x, 0);
 }
 template <typename R>
 __global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs, Slow<R> SL, Pert<R> P,
-                                                 Work<R> T, Fac F, double dtau, int want_div) {
+                                                 Work<R> T, Fac<R> F, double dtau, int want_div) {
   d_ss_solve<R>(G, U, ph, Xs, SL, P, T, F, dtau, want_div, blockIdx.x, 0);
 }
 template <typename R>
@@ -672,6 +675,163 @@ __global__ void k_stage_end(Geo<R> G, Xf<R> Xs, Pert<R> P, Xf<R> Xo, int kchunk)
 template <typename R>
 __global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, int forcing, double dt, double hj_dT) {
   d_physics<R>(G, U, ph, X, forcing, dt, hj_dT, blockIdx.x, 0);
+}
+
+// ---------------------------------------------------------------- staged column solve (float storage)
+//
+// The column step of d_ss_solve for 32 columns with eight warps. Thread 0
+// stages the planes of the elimination (W*, S_W, c, a, lo/up, pivot
+// reciprocals, c'/e', junction factors) into shared memory with one
+// cp.async.bulk.tensor per array, and asks the copy engine to prefetch the
+// planes of the final updates into L2. Warps 0 and 1 then run the two float64
+// sweeps out of shared memory (d' overwrites the pivot reciprocal it has just
+// used); afterwards all eight warps share the levels of Eqs. dens2, pt2 and
+// theta_to_p, whose loads now hit L2. Same operations in the same order as
+// d_ss_solve.
+
+constexpr int kSolveWarps = 8;
+
+size_t solve_tma_smem_bytes(int nv) {
+  const size_t f = 4 * 32, d = 8 * 32;   // one plane row of 32 columns
+  return 128 + (size_t)(2 * (nv + 1) + 2 * nv + (nv + 1) + (nv + 1)) * f + (size_t)(2 * (nv + 1) + 1 + 2) * d +
+         sizeof(uint64_t);
+}
+
+__global__ void __launch_bounds__(32 * kSolveWarps)
+    k_ss_solve_tma(Geo<float> G, VR<float> U, Phys ph, const __grid_constant__ SolveMaps M, int stage0,
+                   Xf<float> Xs, Slow<float> SL, Pert<float> P, Work<float> T, double dtau, int want_div,
+                   int* err) {
+  extern __shared__ unsigned char smraw[];
+  const int nv = G.nv, S = G.colp, N = nv - 1;
+  const int tid = threadIdx.x, tx = tid & 31, warp = tid >> 5;
+  const int c0 = blockIdx.x * 32, c = c0 + tx;
+  const bool valid = c < G.ncol;
+  const int p = N / 2 > 0 ? N / 2 : 1;
+  unsigned char* base = smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u);
+  float* s_w = reinterpret_cast<float*>(base);     // [nv + 1][32]
+  float* s_sw = s_w + (nv + 1) * 32;               // [nv + 1][32]
+  float* s_cc = s_sw + (nv + 1) * 32;              // [nv][32]
+  float* s_ca = s_cc + nv * 32;                    // [nv][32]
+  float* s_off = s_ca + nv * 32;                   // [nv + 1][32]
+  float* s_wf = s_off + (nv + 1) * 32;             // [nv + 1][32] solved W*
+  double* s_inv = reinterpret_cast<double*>(s_wf + (nv + 1) * 32);   // [nv + 1][32], then d' / f' / x
+  double* s_cf = s_inv + (nv + 1) * 32;            // [nv + 1][32]
+  double* s_junc = s_cf + (nv + 1) * 32;           // [32]
+  double* sx = s_junc + 32;                        // [2][32]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sx + 64);
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t fi = (nv + 1) * 128, fc = nv * 128, di = (nv + 1) * 256;
+    mbar_arrive_expect_tx(bar, 3 * fi + 2 * fc + 2 * di + 256);
+    tma_load_2d(s_w, &M.w, c0, 0, bar);
+    tma_load_2d(s_sw, &M.sw, c0, 0, bar);
+    tma_load_2d(s_cc, &M.cc, c0, 0, bar);
+    tma_load_2d(s_ca, &M.ca, c0, 0, bar);
+    tma_load_2d(s_off, &M.off, c0, 0, bar);
+    tma_load_2d(s_inv, &M.inv, c0, 0, bar);
+    tma_load_2d(s_cf, &M.cf, c0, 0, bar);
+    tma_load_2d(s_junc, &M.junction, c0, 0, bar);
+    tma_prefetch_2d(&M.thi, c0, 0);
+    tma_prefetch_2d(&M.cb, c0, 0);
+    tma_prefetch_2d(&M.pp, c0, 0);
+    tma_prefetch_2d(stage0 ? &M.th_t : &M.th_s, c0, 0);
+    if (want_div) {
+      tma_prefetch_2d(&M.dsc, c0, 0);
+      tma_prefetch_2d(&M.dhm, c0, 0);
+    }
+  }
+  if (!__syncthreads_and(mbar_wait(bar, 0))) {
+    if (tid == 0) {                      // flag, give the copies a bounded time to land, leave
+      atomicExch(err, 1);
+      mbar_wait(bar, 0);
+    }
+    return;
+  }
+  const float rdt = (float)dtau, g = (float)ph.g;
+  if (warp < 2) {
+    auto rhs = [&](int m) {
+      const int o = m * 32 + tx;
+      const float wlo = ld(U.wlo + m), whi = ld(U.whi + m);
+      return (double)(s_w[o] + rdt * s_sw[o] - rdt * ld(U.inv_dzc + m) * (s_cc[o] - s_cc[o - 32])
+                      - rdt * g * (wlo * s_ca[o - 32] + whi * s_ca[o]));
+    };
+    double* sdp = s_inv;
+    if (warp == 0) {
+      double d1 = 0.0;
+#pragma unroll 4
+      for (int m = 1; m <= p; ++m) {
+        const int o = m * 32 + tx;
+        d1 = (rhs(m) - (double)s_off[o] * d1) * s_inv[o];
+        sdp[o] = d1;
+      }
+    } else {
+      double f1 = 0.0;
+#pragma unroll 4
+      for (int m = N; m > p; --m) {
+        const int o = m * 32 + tx;
+        f1 = (rhs(m) - (double)s_off[o] * f1) * s_inv[o];
+        sdp[o] = f1;
+      }
+    }
+    asm volatile("bar.sync 1, 64;" ::: "memory");        // the two sweeps only
+    if (warp == 0) {
+      const int op = p * 32 + tx;
+      double xp, xq = 0.0;
+      if (p < N) {
+        const double cp_ = s_cf[op], eq = s_cf[op + 32];
+        const double dp_ = sdp[op], fq = sdp[op + 32];
+        xp = (dp_ - cp_ * fq) * s_junc[tx];
+        xq = fq - eq * xp;
+      } else {
+        xp = sdp[op];
+      }
+      sx[tx] = xp;
+      sx[32 + tx] = xq;
+    }
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    if (warp == 0) {
+      double x = sx[tx];
+      s_wf[p * 32 + tx] = (float)x;
+      for (int m = p - 1; m >= 1; --m) {
+        x = sdp[m * 32 + tx] - s_cf[m * 32 + tx] * x;
+        s_wf[m * 32 + tx] = (float)x;
+      }
+      s_wf[tx] = 0.f;
+    } else {
+      double x = sx[32 + tx];
+      if (p < N) s_wf[(p + 1) * 32 + tx] = (float)x;
+      for (int m = p + 2; m <= N; ++m) {
+        x = sdp[m * 32 + tx] - s_cf[m * 32 + tx] * x;
+        s_wf[m * 32 + tx] = (float)x;
+      }
+      s_wf[nv * 32 + tx] = 0.f;
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    const float gamma = (float)ph.gamma;
+#pragma unroll 4
+    for (int k = warp; k < nv; k += kSolveWarps) {
+      const int o = k * 32 + tx, i = k * S + c;
+      const float wl = s_wf[o], wh = s_wf[o + 32];
+      const float thl = k > 0 ? ld(SL.thi + i) : 0.f;
+      const float thh = k + 1 < nv ? ld(SL.thi + (i + S)) : 0.f;
+      const float el = ld(U.sq_lo + k), eh = ld(U.sq_hi + k);
+      float th_new = ld(T.cb + i) - rdt * (eh * thh * wh - el * thl * wl);
+      P.rho[i] = s_ca[o] - rdt * (eh * wh - el * wl);
+      P.th[i] = th_new;
+      float ps = ld(U.pb + k) + ld(T.pp + i);
+      float ths = ld(U.thb + k) + ld(Xs.th + i);
+      P.p[i] = ps * rexpm1<float>(gamma * rlog1p<float>(th_new / ths));
+      if (k >= 1) P.w[i] = wl;
+      if (want_div) T.dd[i] = ld(SL.dsc + i) + ld(T.dhm + i) + (eh * wh - el * wl);
+    }
+  }
 }
 
 // ---------------------------------------------------------------- kernels: ensemble
@@ -765,7 +925,7 @@ void Impl<R>::launch_2d(int nplanes, int kchunk, dim3& grid) const {
   grid = dim3((G.ncol + block - 1) / block, (nplanes + kchunk - 1) / kchunk);
 }
 
-size_t solve_smem_bytes(int nv) { return (size_t)((nv + 1) + 2) * 32 * sizeof(double); }
+size_t solve_smem_bytes(int nv) { return (size_t)(2 * (nv + 1) + 2) * 32 * sizeof(double); }
 
 template <typename R>
 int col_kernel_setup(int nv) {
@@ -787,6 +947,7 @@ int Impl<R>::large_step(double dt, int n_small) {
   dim3 g1((G.ncol + bs - 1) / bs);
   dim3 gsolve((G.ncol + 31) / 32);
   const size_t solve_smem = solve_smem_bytes(G.nv);
+  const bool staged = solve_tma && smaps != nullptr;
   const R Kd = (R)(diff_D * dbar4 / dt);
   const double dts[3] = {dt / 3.0, dt / n_small, dt / n_small};
   const int nsub[3] = {1, n_small / 2, n_small};
@@ -836,7 +997,10 @@ int Impl<R>::large_step(double dt, int n_small) {
       mark(THOR_K_SS_FLUX, false);
       mark(THOR_K_SS_COL, true);
       const int want_div = divdamp && j + 1 < nsub[s];
-      k_ss_solve<R><<<gsolve, 64, solve_smem, stream>>>(G, U, ph, Xs, SL, P, T, F, dts[s], want_div);
+      if (staged)
+        launch_solve_tma(gsolve, s == 0, dts[s], want_div);
+      else
+        k_ss_solve<R><<<gsolve, 64, solve_smem, stream>>>(G, U, ph, Xs, SL, P, T, F, dts[s], want_div);
       mark(THOR_K_SS_COL, false);
       launches += 3;
     }
@@ -853,6 +1017,73 @@ int Impl<R>::large_step(double dt, int n_small) {
     ++launches;
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+template <>
+void Impl<float>::launch_solve_tma(dim3 grid, int stage0, double dtau, int want_div) {
+  k_ss_solve_tma<<<grid, 32 * kSolveWarps, solve_tma_smem_bytes(G.nv), stream>>>(
+      G, U, ph, *smaps, stage0, stage0 ? Xt : Xst, SL, P, T, dtau, want_div, dev_err);
+}
+template <>
+void Impl<double>::launch_solve_tma(dim3, int, double, int) {}
+
+// TMA descriptors of the staged solve (float storage only; the float64
+// planes would not fit the shared memory of a useful number of blocks)
+template <>
+int Impl<float>::build_solve_maps() {
+  static void* encode_fn = nullptr;
+  const size_t smem = solve_tma_smem_bytes(G.nv);
+  if (smem > 200 * 1024) return 0;                  // stays on the direct solve
+  if (!encode_fn) {
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &encode_fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !encode_fn) {
+      encode_fn = nullptr;
+      return 0;
+    }
+  }
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  Encode encode = reinterpret_cast<Encode>(encode_fn);
+  auto map = std::make_unique<SolveMaps>();
+  bool ok = true;
+  auto make = [&](CUtensorMap* m, const void* ptr, int planes, bool dbl) {
+    const cuuint64_t dims[2] = {(cuuint64_t)G.colp, (cuuint64_t)planes};
+    const cuuint64_t strides[1] = {(cuuint64_t)G.colp * (dbl ? 8 : 4)};
+    const cuuint32_t box[2] = {32, (cuuint32_t)planes};
+    const cuuint32_t es[2] = {1, 1};
+    ok = ok && encode(m, dbl ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                      const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  const int nv = G.nv;
+  make(&map->w, P.w, nv + 1, false);
+  make(&map->sw, SL.sw, nv + 1, false);
+  make(&map->thi, SL.thi, nv + 1, false);
+  make(&map->cc, T.cc, nv, false);
+  make(&map->ca, T.ca, nv, false);
+  make(&map->cb, T.cb, nv, false);
+  make(&map->pp, T.pp, nv, false);
+  make(&map->th_t, Xt.th, nv, false);
+  make(&map->th_s, Xst.th, nv, false);
+  make(&map->dsc, SL.dsc, nv, false);
+  make(&map->dhm, T.dhm, nv, false);
+  make(&map->off, F.off, nv + 1, false);
+  make(&map->inv, F.inv, nv + 1, true);
+  make(&map->cf, F.cf, nv + 1, true);
+  make(&map->junction, F.junction, 1, true);
+  if (!ok) return 0;
+  if (cudaFuncSetAttribute(k_ss_solve_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return -3;
+  smaps = std::move(map);
+  return 0;
+}
+template <>
+int Impl<double>::build_solve_maps() {
+  return 0;
 }
 
 template void Impl<double>::launch_2d(int, int, dim3&) const;

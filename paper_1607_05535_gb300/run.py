@@ -20,7 +20,7 @@ def _workloads():
     return wls, {"hs_g4": wls.HS_G4, "hs_g6": wls.HS_G6, "hj_g6": wls.HJ_G6}
 
 
-def run_workload(thor, wl, precision, steps, spring_iters, kchunk):
+def run_workload(thor, wl, precision, steps, spring_iters, kchunk, solve_tma=1):
     P = wl.planet
     forcing = {"none": 0, "held_suarez": 1, "hot_jupiter": 2}[wl.forcing]
     grid = thor.thor_grid_create(wl.glevel, wl.nv, P.radius, wl.z_top,
@@ -30,6 +30,7 @@ def run_workload(thor, wl, precision, steps, spring_iters, kchunk):
     st = thor.thor_state_init(grid, planet, init, None)
     try:
         thor.thor_tune(st, thor.THOR_TUNE_KCHUNK, kchunk)
+        thor.thor_tune(st, thor.THOR_TUNE_SOLVE_TMA, solve_tma)
         thor.thor_step(st, steps, wl.n_small, wl.dt)
         return {"workload": wl.name, "steps": steps, "diag": thor.thor_diag(st),
                 "launches": thor.thor_launch_count(st)}
@@ -74,6 +75,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--spring-iters", type=int, default=10)
     ap.add_argument("--kchunk", type=int, default=2)
+    ap.add_argument("--solve-tma", type=int, default=1, choices=[0, 1])
     ap.add_argument("--ensemble", action="store_true")
     args = ap.parse_args(argv)
     import torch
@@ -86,7 +88,8 @@ def main(argv=None):
         out = run_ensemble(thor, wls, args.steps, args.spring_iters)
     else:
         prec = thor.THOR_FP64 if args.precision == "fp64" else thor.THOR_MIXED
-        out = run_workload(thor, table[args.workload], prec, args.steps, args.spring_iters, args.kchunk)
+        out = run_workload(thor, table[args.workload], prec, args.steps, args.spring_iters, args.kchunk,
+                           args.solve_tma)
     torch.cuda.synchronize()
     print(json.dumps(out))
     return 0

@@ -61,3 +61,32 @@ def test_mixed_vs_oracle_held_suarez_g4():
     print(rep)
     for k, g in GATES.items():
         assert rep[k] < g, (k, rep)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_staged_solve_matches_direct_solve(graph):
+    """The TMA-staged column solve (default for float storage) computes the
+    same numbers as the direct-load solve: same operations in the same order,
+    only the loads differ."""
+    import torch
+    from harness import init_struct, planet_struct
+    wl = wls.HS_G4.with_(n_large=4)
+    st = torch.cuda.Stream() if graph else None
+    sp = st.cuda_stream if st is not None else None
+    grid = thor.thor_grid_create(wl.glevel, wl.nv, wl.planet.radius, wl.z_top,
+                                 thor.thor_spring(1.15, 1.0, 1.0, 0.01, 0.0, wl.spring_max_iter))
+    a = thor.thor_state_init(grid, planet_struct(wl.planet), init_struct(wl, thor.THOR_MIXED), sp)
+    b = thor.thor_state_init(grid, planet_struct(wl.planet), init_struct(wl, thor.THOR_MIXED), sp)
+    try:
+        thor.thor_tune(b, thor.THOR_TUNE_SOLVE_TMA, 0)
+        for s_ in (a, b):
+            thor.thor_step(s_, wl.n_large, wl.n_small, wl.dt)
+        for f in (thor.THOR_FIELD_RHO, thor.THOR_FIELD_MOM, thor.THOR_FIELD_W, thor.THOR_FIELD_RHOTHETA):
+            x = thor.thor_state_get(a, f, wl.ncol, wl.nv)
+            y = thor.thor_state_get(b, f, wl.ncol, wl.nv)
+            assert np.array_equal(x, y), f
+        assert thor.thor_diag(a)["nonfinite"] == 0
+    finally:
+        thor.thor_state_destroy(a)
+        thor.thor_state_destroy(b)
+        thor.thor_grid_destroy(grid)
