@@ -35,11 +35,15 @@ import workloads as wls  # noqa: E402
 METRIC = "cell-substeps/s"
 
 # Unique field words each kernel reads or writes per cell (neighbour reads of
-# a field counted once), the counting rule of the algorithmic roofline.
+# a field counted once), the counting rule of the algorithmic roofline. The
+# column solve reads 11 float planes (W*, S_W, c, a, lo/up, theta at the
+# interfaces, b, p', Th^(s), D^(s), div_h M*) and 2 float64 factor planes (4
+# words), and writes 5 (rho*, Th*, p*, W*, D); the factorisation reads 2 and
+# writes 2 float64 planes and one float plane.
 KERNEL_WORDS = {
     "derived": 6 + 10, "lap1": 8 + 6, "slow": 17 + 8, "slow_w": 7 + 2, "stage_init": 13 + 7,
-    "ss_div": 5 + 1, "ss_grad": 1 + 3, "ss_mom": 10 + 3, "ss_flux": 10 + 4, "ss_solve": 11 + 5 + 6, "ss_factor": 2 + 6,
-    "stage_end": 12 + 6, "physics": 5 + 4,
+    "ss_div": 5 + 1, "ss_grad": 1 + 3, "ss_mom": 10 + 3, "ss_flux": 10 + 4, "ss_solve": 11 + 4 + 5,
+    "ss_factor": 2 + 5, "stage_end": 12 + 6, "physics": 5 + 4,
 }
 
 
@@ -258,6 +262,8 @@ def run_thor(args):
 
     # ---- mixed precision, the headline
     st = make_state(thor.THOR_MIXED)
+    # launch shape from the autotuner (state restored afterwards)
+    tuned_kc, tuned_bs, tuned_ms = thor.thor_autotune(st, wl.n_small, wl.dt, steps=3)
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     for _ in range(args.warmup):
         thor.thor_step(st, 1, wl.n_small, wl.dt)          # also captures the CUDA graph
@@ -340,6 +346,7 @@ def run_thor(args):
         "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                 "steps": e2e_steps},
         "gpu_launches": launches,
+        "autotuned": {"kchunk": tuned_kc, "block": tuned_bs, "ms_per_step": tuned_ms},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": _traffic(dom), "algorithmic_bytes_per_launch": bytes_per_launch,
