@@ -265,7 +265,17 @@ typedef struct thor_mlp thor_mlp;
 int thor_mlp_create(const int* sizes, int n_sizes, int max_batch, unsigned long long seed, void* stream,
                     thor_mlp** out);
 int thor_mlp_info(const thor_mlp* mlp, size_t* nparam);
+/* Copies the float32 master weights to the host (synchronises the MLP's
+ * stream). Returns THOR_ETIMEOUT if a tensor-core GEMM of this MLP gave up
+ * waiting for its MMAs (bounded at 2 s per wait; its outputs are then
+ * unspecified). */
 int thor_mlp_get_params(thor_mlp* mlp, float* host, size_t n);
+/* GEMM path. THOR_MLP_TUNE_TCGEN05: 1 (default) runs the products as
+ * tcgen05.mma (bfloat16 operands in shared memory, float32 accumulators in
+ * tensor memory, 128-row tiles); 0 runs the warp-level mma.sync kernel.
+ * Both accumulate in float32; results agree to summation order. */
+enum { THOR_MLP_TUNE_TCGEN05 = 0 };
+int thor_mlp_tune(thor_mlp* mlp, int knob, int value);
 /* Sets the float32 master weights and resets the Adam moments. */
 int thor_mlp_set_params(thor_mlp* mlp, const float* host, size_t n);
 /* y = MLP(x) for m rows. */

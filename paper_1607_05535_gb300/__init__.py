@@ -23,6 +23,7 @@ THOR_FIELD_RHO, THOR_FIELD_MOM, THOR_FIELD_W, THOR_FIELD_RHOTHETA, THOR_FIELD_PR
     THOR_FIELD_TEMPERATURE = range(6)
 THOR_TUNE_KCHUNK, THOR_TUNE_GRAPH, THOR_TUNE_CHECK_FINITE, THOR_TUNE_BLOCK, THOR_TUNE_SOLVE_TMA = range(5)
 THOR_ENSEMBLE_MAX = 4096
+THOR_MLP_TUNE_TCGEN05 = 0
 
 EXPORTED = [
     "thor_strerror", "thor_grid_create", "thor_grid_info", "thor_grid_points",
@@ -33,7 +34,7 @@ EXPORTED = [
     "thor_mlp_set_params", "thor_mlp_forward", "thor_mlp_backward", "thor_mlp_train_step",
     "thor_mlp_destroy", "thor_closure_features", "thor_closure_attach", "thor_coarse_grain",
     "thor_autotune", "thor_ensemble_create", "thor_ensemble_step", "thor_ensemble_info",
-    "thor_ensemble_tune", "thor_ensemble_autotune", "thor_ensemble_destroy",
+    "thor_ensemble_tune", "thor_ensemble_autotune", "thor_ensemble_destroy", "thor_mlp_tune",
 ]
 
 # kernel ids of thor_profile_read
@@ -121,6 +122,7 @@ def _load():
         "thor_ensemble_tune": (I, [P, I, I]),
         "thor_ensemble_autotune": (I, [P, IP, ctypes.POINTER(D), I, IP, IP, ctypes.POINTER(D)]),
         "thor_ensemble_destroy": (None, [P]),
+        "thor_mlp_tune": (I, [P, I, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -304,6 +306,10 @@ def thor_mlp_backward(mlp, dy, grad):
 def thor_mlp_train_step(mlp, x, target, lr, loss=None):
     _check(_lib.thor_mlp_train_step(mlp, _ptr(x), _ptr(target), x.shape[0], lr,
                                     _ptr(loss) if loss is not None else None), "thor_mlp_train_step")
+
+
+def thor_mlp_tune(mlp, knob, value):
+    _check(_lib.thor_mlp_tune(mlp, knob, value), "thor_mlp_tune")
 
 
 def thor_mlp_destroy(mlp):

@@ -3,8 +3,11 @@
 // A dense MLP y = W_L^T relu(... relu(W_1^T x + b_1) ...) + b_L with float32
 // master weights, bfloat16 weights and layer inputs on the tensor cores and
 // float32 accumulation; trained with a mean-squared-error loss and Adam
-// (Kingma and Ba 2015). The GEMMs are warp-level BF16 tensor-core MMAs
-// (mma.sync m16n8k16, float32 accumulate) on shared-memory tiles.
+// (Kingma and Ba 2015). The GEMMs run on the fifth-generation tensor cores:
+// tcgen05.mma kind::f16 with bfloat16 operands staged in shared memory and
+// the float32 accumulator in tensor memory (k_gemm_tc); the warp-level
+// mma.sync m16n8k16 kernel (k_gemm_bf16) is kept as a switchable reference
+// path (thor_mlp_tune).
 //
 // Closure: per column, the inputs are 5 fields (rho', M_x, M_y, M_z, Th') at
 // all levels and the neighbour means of the same (as anomalies); the
@@ -184,6 +187,175 @@ uint64_t splitmix(uint64_t x) {
   return z ^ (z >> 31);
 }
 
+
+// ------------------------------------------------------------ tcgen05 GEMM
+//
+// One CTA of 4 warps computes a 128 x NT tile of C (NT <= 256, a multiple of
+// 16): row r of the tile is tensor-memory lane r, column n is tensor-memory
+// column n of a float32 accumulator. Per chunk of 64 k, all threads stage the
+// bfloat16 operand tiles (128 x 64 of op(A), NT x 64 of op(B)^T) into shared
+// memory in the canonical K-major layout without swizzle: 8 x 8 core
+// matrices of 16-byte rows, core matrices adjacent in k 128 B apart (leading
+// byte offset), groups of 8 rows 1024 B apart (stride byte offset). One
+// thread then issues four 128 x NT x 16 MMAs and commits them to an
+// mbarrier, which every thread waits on (bounded) before the tiles are
+// overwritten. The epilogue reads the accumulator with tcgen05.ld (warp w
+// owns lanes 32w..32w+31), adds the bias, applies the ReLU and stores.
+
+constexpr int TC_M = 128, TC_KC = 64;
+
+__device__ __forceinline__ uint32_t tc_core_off(int r, int k) {
+  return (uint32_t)((((r >> 3) * (TC_KC / 8) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+// shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (all >> 4), the fixed version bits 46-48 = 0b001, no swizzle
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: float32 D (bits 4-5 = 1), bfloat16 A
+// and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at 24
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__host__ __device__ constexpr int tc_cols(int nt) { return nt <= 32 ? 32 : nt <= 64 ? 64 : nt <= 128 ? 128 : 256; }
+
+// same contract as k_gemm_bf16; NT = tile width; err: device flag set when
+// an MMA completion is not seen within the wait bound
+__global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const __nv_bfloat16* A, int lda,
+                                                    int transA, const __nv_bfloat16* B, int ldb, int transB,
+                                                    float* C, int ldc, const float* bias, int relu,
+                                                    __nv_bfloat16* Cb, int ldcb, int NT, int* err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * NT;
+  const uint32_t ncols = (uint32_t)tc_cols(NT);
+  unsigned char* As = tsm;                          // [128][64] bf16, core-matrix order
+  unsigned char* Bs = tsm + TC_M * TC_KC * 2;       // [NT][64]
+  if (warp == 0) tc_alloc(&tmem_base, ncols);
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = tc_idesc(TC_M, NT);
+  const uint32_t a_addr = smem_u32(As), b_addr = smem_u32(Bs);
+  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+  bool ok = true;
+  uint32_t phase = 0;
+  for (int k0 = 0; k0 < K && ok; k0 += TC_KC) {
+    // op(A)(m, k): contiguous in k unless transA
+    for (int e = tid; e < TC_M * TC_KC; e += 128) {
+      const int r = transA ? (e & (TC_M - 1)) : (e >> 6), kk = transA ? (e >> 7) : (e & (TC_KC - 1));
+      const int m = m0 + r, k = k0 + kk;
+      __nv_bfloat16 v = zero;
+      if (m < M && k < K) v = transA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
+      *reinterpret_cast<__nv_bfloat16*>(As + tc_core_off(r, kk)) = v;
+    }
+    // op(B)(k, n) stored as the NT x 64 K-major tile of op(B)^T: contiguous in n unless transB
+    for (int e = tid; e < NT * TC_KC; e += 128) {
+      const int c = transB ? (e >> 6) : (e % NT), kk = transB ? (e & (TC_KC - 1)) : (e / NT);
+      const int n = n0 + c, k = k0 + kk;
+      __nv_bfloat16 v = zero;
+      if (n < N && k < K) v = transB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
+      *reinterpret_cast<__nv_bfloat16*>(Bs + tc_core_off(c, kk)) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes -> tensor cores
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < TC_KC / 16; ++kk) {
+        const uint64_t ad = tc_smem_desc(a_addr + kk * 256, 128, 1024);
+        const uint64_t bd = tc_smem_desc(b_addr + kk * 256, 128, 1024);
+        tc_mma(tmem, ad, bd, idesc, (k0 > 0 || kk > 0) ? 1u : 0u);
+      }
+      tc_commit(&bar);
+    }
+    ok = __syncthreads_and(mbar_wait(&bar, phase));
+    phase ^= 1u;
+  }
+  tc_fence_after();
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    for (int c = 0; c < NT; c += 16) {
+      uint32_t v[16];
+      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + c + j;
+          if (n >= N) break;
+          float x = __uint_as_float(v[j]);
+          if (bias) x += bias[n];
+          if (relu) x = x > 0.0f ? x : 0.0f;
+          if (C) C[(size_t)row * ldc + n] = x;
+          if (Cb) Cb[(size_t)row * ldcb + n] = __float2bfloat16(x);
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+    mbar_wait(&bar, phase ^ 1u);         // bounded: let an outstanding MMA finish before freeing
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc_dealloc(tmem, ncols);
+}
+
+// dynamic shared memory of k_gemm_tc: the two tiles, and enough on top that
+// no more CTAs share an SM than its 512 tensor-memory columns can hold
+size_t tc_smem_bytes(int nt) {
+  const size_t tiles = (size_t)(TC_M + nt) * TC_KC * 2;
+  const int ctas = 512 / tc_cols(nt);
+  const size_t cap = (size_t)(228 * 1024) / ctas - 2048;
+  return std::max(tiles, std::min(cap, (size_t)200 * 1024));
+}
 }  // namespace
 }  // namespace thor
 
@@ -191,6 +363,8 @@ uint64_t splitmix(uint64_t x) {
 
 struct thor_mlp {
   std::vector<int> sizes;              // layer widths, n_layers + 1 entries
+  int use_tc = 1;                      // tcgen05 GEMMs (1) or the mma.sync reference path (0)
+  int* err = nullptr;                  // device flag of the tcgen05 kernel
   int max_batch = 0;
   cudaStream_t stream = nullptr;
   size_t nparam = 0;
@@ -212,9 +386,18 @@ struct thor_mlp {
 namespace thor {
 namespace {
 
-void gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A, int lda, int transA,
+void gemm(const thor_mlp* net, int M, int N, int K, const __nv_bfloat16* A, int lda, int transA,
           const __nv_bfloat16* B, int ldb, int transB, float* C, int ldc, const float* bias, int relu,
           __nv_bfloat16* Cb, int ldcb) {
+  cudaStream_t st = net->stream;
+  if (net->use_tc) {
+    const int ntiles = (N + 255) / 256;
+    const int nt = ((N + ntiles - 1) / ntiles + 15) / 16 * 16;
+    dim3 grid(ntiles, (M + TC_M - 1) / TC_M);
+    k_gemm_tc<<<grid, 128, tc_smem_bytes(nt), st>>>(M, N, K, A, lda, transA, B, ldb, transB, C, ldc, bias, relu,
+                                                    Cb, ldcb, nt, net->err);
+    return;
+  }
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
   k_gemm_bf16<<<grid, 128, 0, st>>>(M, N, K, A, lda, transA, B, ldb, transB, C, ldc, bias, relu, Cb, ldcb);
 }
@@ -229,9 +412,9 @@ int mlp_forward(thor_mlp* net, const float* x, int m) {
     const __nv_bfloat16* W = net->pb + net->woff[l];
     const float* b = net->p + net->boff[l];
     if (l + 1 < L)
-      gemm(st, m, N, K, net->h[l], K, 0, W, N, 0, nullptr, 0, b, 1, net->h[l + 1], N);
+      gemm(net, m, N, K, net->h[l], K, 0, W, N, 0, nullptr, 0, b, 1, net->h[l + 1], N);
     else
-      gemm(st, m, N, K, net->h[l], K, 0, W, N, 0, net->y, N, b, 0, nullptr, 0);
+      gemm(net, m, N, K, net->h[l], K, 0, W, N, 0, net->y, N, b, 0, nullptr, 0);
   }
   net->last_m = m;
   return cudaGetLastError() == cudaSuccess ? THOR_OK : THOR_ECUDA;
@@ -253,12 +436,12 @@ int mlp_backward(thor_mlp* net, const float* dy, int m) {
     k_relu_back<<<blocks_for(cnt), 256, 0, st>>>(gl, l + 1 < L ? net->h[l + 1] : nullptr, net->gb, cnt,
                                                  l + 1 < L);
     // dW_l = h_l^T gb  ([K][N]), db_l = column sums of g
-    gemm(st, K, N, m, net->h[l], K, 1, net->gb, N, 0, net->grad + net->woff[l], N, nullptr, 0, nullptr, 0);
+    gemm(net, K, N, m, net->h[l], K, 1, net->gb, N, 0, net->grad + net->woff[l], N, nullptr, 0, nullptr, 0);
     k_colsum<<<(N + 127) / 128, 128, 0, st>>>(gl, m, N, net->grad + net->boff[l]);
     if (l > 0) {
       // g_{l-1} = gb W_l^T ([m][K]) into z[l-1]
       const __nv_bfloat16* W = net->pb + net->woff[l];
-      gemm(st, m, K, N, net->gb, N, 0, W, N, 1, net->z[l - 1], K, nullptr, 0, nullptr, 0);
+      gemm(net, m, K, N, net->gb, N, 0, W, N, 1, net->z[l - 1], K, nullptr, 0, nullptr, 0);
     }
   }
   return cudaGetLastError() == cudaSuccess ? THOR_OK : THOR_ECUDA;
@@ -298,7 +481,7 @@ int thor_mlp_create(const int* sizes, int n_sizes, int max_batch, unsigned long 
   for (int l = 0; l < L; ++l) o_h.push_back(take((size_t)max_batch * sizes[l] * 2));
   for (int l = 0; l < L; ++l) o_z.push_back(take((size_t)max_batch * sizes[l + 1] * 4));
   size_t o_gb = take((size_t)max_batch * wmax * 2), o_y = take((size_t)max_batch * sizes[L] * 4),
-         o_dy = take((size_t)max_batch * sizes[L] * 4), o_part = take(4096 * 4 + 64);
+         o_dy = take((size_t)max_batch * sizes[L] * 4), o_part = take(4096 * 4 + 64), o_err = take(64);
   if (cudaMalloc(&net->arena, bytes) != cudaSuccess) {
     delete net;
     return THOR_ENOMEM;
@@ -315,6 +498,13 @@ int thor_mlp_create(const int* sizes, int n_sizes, int max_batch, unsigned long 
   }
   net->gb = (__nv_bfloat16*)(base + o_gb);
   net->y = (float*)(base + o_y);
+  net->err = (int*)(base + o_err);
+  if (cudaMemsetAsync(net->err, 0, 64, net->stream) ||
+      cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024)) {
+    cudaFree(net->arena);
+    delete net;
+    return THOR_ECUDA;
+  }
   net->dy = (float*)(base + o_dy);
   net->part = (float*)(base + o_part);
   // He-uniform initial weights from SplitMix64, zero biases
@@ -353,8 +543,20 @@ int thor_mlp_info(const thor_mlp* net, size_t* nparam) {
 
 int thor_mlp_get_params(thor_mlp* net, float* host, size_t n) {
   if (!net || !host || n != net->nparam) return THOR_EINVAL;
+  int flag = 0;
   if (cudaMemcpyAsync(host, net->p, n * 4, cudaMemcpyDeviceToHost, net->stream)) return THOR_ECUDA;
-  return cudaStreamSynchronize(net->stream) ? THOR_ECUDA : THOR_OK;
+  if (cudaMemcpyAsync(&flag, net->err, sizeof(int), cudaMemcpyDeviceToHost, net->stream)) return THOR_ECUDA;
+  if (cudaStreamSynchronize(net->stream)) return THOR_ECUDA;
+  return flag ? THOR_ETIMEOUT : THOR_OK;
+}
+
+int thor_mlp_tune(thor_mlp* net, int knob, int value) {
+  if (!net) return THOR_EINVAL;
+  if (knob == THOR_MLP_TUNE_TCGEN05) {
+    net->use_tc = value != 0;
+    return THOR_OK;
+  }
+  return THOR_EINVAL;
 }
 
 int thor_mlp_set_params(thor_mlp* net, const float* host, size_t n) {

@@ -111,3 +111,42 @@ def test_train_step_matches_oracle_adam():
         assert np.allclose(np.abs(move[np.abs(ref_move) > 5e-3]), 1e-2, rtol=0.05)
     finally:
         thor.thor_mlp_destroy(net)
+
+
+@pytest.mark.parametrize("K, N, m", [(320, 160, 1000), (33, 7, 5), (256, 300, 130), (64, 256, 128)])
+def test_tcgen05_gemm_matches_exact_and_mma_sync(K, N, m):
+    """One linear layer (no intermediate rounding): the tcgen05 path equals the
+    float64 product of the same bfloat16 operands to float32 accumulation
+    error, and agrees with the mma.sync path; the backward products
+    (transposed operands) likewise. Shapes cover ragged M and N, N above one
+    256-column tile and K below one 64-deep chunk."""
+    rng = np.random.default_rng(11)
+    sizes = [K, N]
+    W = rng.standard_normal((K, N)) / np.sqrt(K)
+    b = 0.1 * rng.standard_normal(N)
+    flat = _flat([(W, b)])
+    x = rng.standard_normal((m, K)).astype(np.float32)
+    dy = rng.standard_normal((m, N)).astype(np.float32)
+    p32 = _unflat(flat, sizes)
+    y_ref = om.bf16(x) @ om.bf16(p32[0][0]) + p32[0][1]
+    gW_ref = om.bf16(x).T @ om.bf16(dy)
+    out = {}
+    for tc in (1, 0):
+        net = thor.thor_mlp_create(sizes, max(m, 1), seed=0)
+        try:
+            thor.thor_mlp_tune(net, thor.THOR_MLP_TUNE_TCGEN05, tc)
+            thor.thor_mlp_set_params(net, flat)
+            yd = torch.empty((m, N), dtype=torch.float32, device="cuda")
+            thor.thor_mlp_forward(net, torch.tensor(x, device="cuda"), yd)
+            gd = torch.empty(flat.size, dtype=torch.float32, device="cuda")
+            thor.thor_mlp_backward(net, torch.tensor(dy, device="cuda"), gd)
+            thor.thor_mlp_get_params(net)          # synchronises; raises on a timed-out MMA wait
+            out[tc] = (yd.cpu().numpy().astype(np.float64), gd.cpu().numpy().astype(np.float64))
+        finally:
+            thor.thor_mlp_destroy(net)
+    for tc in (1, 0):
+        y, g = out[tc]
+        assert _rel(y, y_ref) < 1e-5, (tc, _rel(y, y_ref))
+        gW = g[:K * N].reshape(K, N)
+        assert _rel(gW, gW_ref) < 1e-5, (tc, _rel(gW, gW_ref))
+    assert _rel(out[1][0], out[0][0]) < 1e-5
