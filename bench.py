@@ -262,8 +262,13 @@ def run_thor(args):
 
     # ---- mixed precision, the headline
     st = make_state(thor.THOR_MIXED)
-    # launch shape from the autotuner (state restored afterwards)
-    tuned_kc, tuned_bs, tuned_ms = thor.thor_autotune(st, wl.n_small, wl.dt, steps=3)
+    # launch shape from the autotuner (state restored afterwards), unless given
+    if args.kchunk:
+        thor.thor_tune(st, thor.THOR_TUNE_KCHUNK, args.kchunk)
+        thor.thor_tune(st, thor.THOR_TUNE_BLOCK, args.block)
+        tuned_kc, tuned_bs, tuned_ms = args.kchunk, args.block, None
+    else:
+        tuned_kc, tuned_bs, tuned_ms = thor.thor_autotune(st, wl.n_small, wl.dt, steps=3)
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     for _ in range(args.warmup):
         thor.thor_step(st, 1, wl.n_small, wl.dt)          # also captures the CUDA graph
@@ -445,6 +450,8 @@ def main():
     ap.add_argument("--workload", default="hs_g6", choices=["hs_g6", "hs_g4", "hj_g6"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--kchunk", type=int, default=0, help="levels per thread (skips the autotuner)")
+    ap.add_argument("--block", type=int, default=128, help="block size with --kchunk")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)      # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -35,6 +35,7 @@ struct EnsImpl : EnsBase {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   EnsPlan<R> plan;
   Member<R>* dM = nullptr;
+  SolveMaps* dmaps = nullptr;          // members' staged-solve descriptors, in plan order
   int2 *dmap = nullptr, *dmapc = nullptr;
   size_t cap_map = 0, cap_mapc = 0;
   // plan key
@@ -48,6 +49,7 @@ struct EnsImpl : EnsBase {
   ~EnsImpl() override {
     drop_graph();
     if (dM) cudaFree(dM);
+    if (dmaps) cudaFree(dmaps);
     if (dmap) cudaFree(dmap);
     if (dmapc) cudaFree(dmapc);
     if (ev_in) cudaEventDestroy(ev_in);
@@ -84,6 +86,17 @@ struct EnsImpl : EnsBase {
     }
     p.nblk = (int)map.size();
     p.nblkc = (int)mapc.size();
+    // staged column solve when every member has its descriptors
+    std::vector<SolveMaps> smaps;
+    p.staged = 1;
+    for (int q = 0; q < n; ++q) {
+      const Impl<R>* I = mem[order[q]];
+      if (!I->solve_tma || !I->smaps) {
+        p.staged = 0;
+        break;
+      }
+      smaps.push_back(*I->smaps);
+    }
     for (int s = 0; s < 3; ++s) {
       p.maxsub[s] = tab[0].nsub[s];
       for (int j = 0; j < p.maxsub[s]; ++j) {
@@ -111,6 +124,11 @@ struct EnsImpl : EnsBase {
       dmapc = nullptr;
       if (cudaMalloc(&dmapc, mapc.size() * sizeof(int2))) return THOR_ENOMEM;
       cap_mapc = mapc.size();
+    }
+    if (p.staged) {
+      if (!dmaps && cudaMalloc(&dmaps, n * sizeof(SolveMaps))) return THOR_ENOMEM;
+      if (cudaMemcpy(dmaps, smaps.data(), n * sizeof(SolveMaps), cudaMemcpyHostToDevice)) return THOR_ECUDA;
+      for (int q = 0; q < n; ++q) tab[q].smap = dmaps + q;
     }
     if (cudaMemcpy(dM, tab.data(), n * sizeof(Member<R>), cudaMemcpyHostToDevice) ||
         cudaMemcpy(dmap, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice) ||

@@ -40,6 +40,13 @@ struct Pert {
   R *w;                            // interfaces
 };
 
+// TMA descriptors of the planes the staged column solve reads (float storage):
+// each a 2-D map (x = column, y = plane) with a box of 32 columns x all planes
+struct SolveMaps {
+  CUtensorMap w, sw, cc, ca, thi, cb, pp, th_t, th_s, dsc, dhm;   // float
+  CUtensorMap off, inv, cf, junction;                           // float64 factors
+};
+
 // Everything the kernels of one state need, as one record: a device array of
 // these lets one launch step an ensemble of states of different sizes,
 // planets and time steps.
@@ -58,13 +65,8 @@ struct Member {
   R Kd;                            // hyperdiffusion coefficient for this dt
   int nsub[3];                     // small steps of each RK stage
   int hyper, divdamp, forcing;
-};
-
-// TMA descriptors of the planes the staged column solve reads (float storage):
-// each a 2-D map (x = column, y = plane) with a box of 32 columns x all planes
-struct SolveMaps {
-  CUtensorMap w, sw, cc, ca, thi, cb, pp, th_t, th_s, dsc, dhm;   // float
-  CUtensorMap off, inv, cf, junction;                           // float64 factors
+  const SolveMaps* smap;           // device copy of the staged-solve descriptors (or null)
+  int* err;                        // the state's device error flag
 };
 
 struct ImplBase {
@@ -255,6 +257,8 @@ struct Impl : ImplBase {
     m.hyper = hyper;
     m.divdamp = divdamp;
     m.forcing = forcing;
+    m.smap = nullptr;
+    m.err = dev_err;
     return m;
   }
 };
@@ -271,6 +275,7 @@ struct EnsPlan {
   int maxsub[3] = {0, 0, 0};
   std::vector<int> active[3], activec[3];  // blocks of the members still stepping at small step j
   int any_hyper = 0, any_divdamp = 0, any_forcing = 0;
+  int staged = 0;                   // every member runs the TMA-staged column solve
 };
 
 template <typename R>

@@ -130,12 +130,24 @@ __global__ void k_relu_back(float* g, const __nv_bfloat16* h, __nv_bfloat16* gb,
 }
 
 // column sums of g [M][N] (deterministic: one thread per column, fixed order)
-__global__ void k_colsum(const float* g, int M, int N, float* out) {
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
+// out[n] = sum over m of g[m][n]: a block sums 32 columns, its 32 x 32
+// threads each take every 32nd row, then the 32 partials of a column are
+// added in a fixed order
+__global__ void __launch_bounds__(1024) k_colsum(const float* g, int M, int N, float* out) {
+  __shared__ float part[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, n = blockIdx.x * 32 + tx;
   float s = 0.0f;
-  for (int m = 0; m < M; ++m) s += g[(size_t)m * N + n];
-  out[n] = s;
+  if (n < N) {
+#pragma unroll 4
+    for (int m = ty; m < M; m += 32) s += g[(size_t)m * N + n];
+  }
+  part[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0 && n < N) {
+    float t = 0.0f;
+    for (int j = 0; j < 32; ++j) t += part[j][tx];
+    out[n] = t;
+  }
 }
 
 // dY = 2 (Y - T) / (M N); per-block partial sums of (Y - T)^2
@@ -260,23 +272,92 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t* v) {
 
 __host__ __device__ constexpr int tc_cols(int nt) { return nt <= 32 ? 32 : nt <= 64 ? 64 : nt <= 128 ? 128 : 256; }
 
+// Stages rows [r0, r0 + R) x k [k0, k0 + 64) of op(X) into core-matrix order
+// at dst; op(X)(r, k) = X[r * ld + k] if kcontig, else X[k * ld + r]; zero
+// outside rows_total x K. vec: ld a multiple of 8 and X 16-byte aligned, so
+// full 8-element groups move as 16-byte vectors (transposed in registers when
+// the source runs along r).
+__device__ __forceinline__ void tc_stage(unsigned char* dst, const __nv_bfloat16* X, int ld, bool kcontig, int r0,
+                                         int R, int rows_total, int k0, int K, bool vec, int tid) {
+  const unsigned short* Xs = reinterpret_cast<const unsigned short*>(X);
+  auto at = [&](int r, int k) -> uint32_t {
+    if (r >= rows_total || k >= K) return 0u;
+    return kcontig ? Xs[(size_t)r * ld + k] : Xs[(size_t)k * ld + r];
+  };
+  if (kcontig) {
+    for (int u = tid; u < R * 8; u += 128) {
+      const int r = u >> 3, kg = u & 7, row = r0 + r, k = k0 + kg * 8;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (row < rows_total) {
+        if (vec && k + 8 <= K) {
+          v = *reinterpret_cast<const uint4*>(Xs + (size_t)row * ld + k);
+        } else {
+          v.x = at(row, k) | (at(row, k + 1) << 16);
+          v.y = at(row, k + 2) | (at(row, k + 3) << 16);
+          v.z = at(row, k + 4) | (at(row, k + 5) << 16);
+          v.w = at(row, k + 6) | (at(row, k + 7) << 16);
+        }
+      }
+      *reinterpret_cast<uint4*>(dst + tc_core_off(r, kg * 8)) = v;
+    }
+  } else {
+    const int G = R >> 3;
+    for (int u = tid; u < G * 8; u += 128) {
+      const int rg = u % G, kg = u / G, row = r0 + rg * 8, kb = k0 + kg * 8;
+      uint32_t w[8][4];               // w[kk][j]: rows 2j, 2j+1 at k = kb + kk
+      if (vec && row + 8 <= rows_total && kb + 8 <= K) {
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const uint4 v = *reinterpret_cast<const uint4*>(Xs + (size_t)(kb + kk) * ld + row);
+          w[kk][0] = v.x;
+          w[kk][1] = v.y;
+          w[kk][2] = v.z;
+          w[kk][3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) w[kk][j] = at(row + 2 * j, kb + kk) | (at(row + 2 * j + 1, kb + kk) << 16);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint4 lo, hi;                 // core rows 2j (low halves) and 2j + 1 (high halves), k = kb..kb+7
+        lo.x = __byte_perm(w[0][j], w[1][j], 0x5410);
+        lo.y = __byte_perm(w[2][j], w[3][j], 0x5410);
+        lo.z = __byte_perm(w[4][j], w[5][j], 0x5410);
+        lo.w = __byte_perm(w[6][j], w[7][j], 0x5410);
+        hi.x = __byte_perm(w[0][j], w[1][j], 0x7632);
+        hi.y = __byte_perm(w[2][j], w[3][j], 0x7632);
+        hi.z = __byte_perm(w[4][j], w[5][j], 0x7632);
+        hi.w = __byte_perm(w[6][j], w[7][j], 0x7632);
+        *reinterpret_cast<uint4*>(dst + tc_core_off(rg * 8 + 2 * j, kg * 8)) = lo;
+        *reinterpret_cast<uint4*>(dst + tc_core_off(rg * 8 + 2 * j + 1, kg * 8)) = hi;
+      }
+    }
+  }
+}
+
 // same contract as k_gemm_bf16; NT = tile width; err: device flag set when
-// an MMA completion is not seen within the wait bound
+// an MMA completion is not seen within the wait bound. Two shared-memory
+// stages: chunk c + 1 is staged while the MMAs of chunk c run.
 __global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const __nv_bfloat16* A, int lda,
                                                     int transA, const __nv_bfloat16* B, int ldb, int transB,
                                                     float* C, int ldc, const float* bias, int relu,
                                                     __nv_bfloat16* Cb, int ldcb, int NT, int* err) {
   extern __shared__ __align__(1024) unsigned char tsm[];
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bar[2];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * NT;
   const uint32_t ncols = (uint32_t)tc_cols(NT);
-  unsigned char* As = tsm;                          // [128][64] bf16, core-matrix order
-  unsigned char* Bs = tsm + TC_M * TC_KC * 2;       // [NT][64]
+  const int stage_bytes = (TC_M + NT) * TC_KC * 2;
+  const bool vecA = (lda % 8 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+  const bool vecB = (ldb % 8 == 0) && ((reinterpret_cast<uintptr_t>(B) & 15) == 0);
   if (warp == 0) tc_alloc(&tmem_base, ncols);
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     mbar_init_fence();
   }
   tc_fence_before();
@@ -284,64 +365,65 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const _
   tc_fence_after();
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = tc_idesc(TC_M, NT);
-  const uint32_t a_addr = smem_u32(As), b_addr = smem_u32(Bs);
-  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+  const int nchunks = (K + TC_KC - 1) / TC_KC;
+  uint32_t uses[2] = {0u, 0u};          // commits issued on each barrier
   bool ok = true;
-  uint32_t phase = 0;
-  for (int k0 = 0; k0 < K && ok; k0 += TC_KC) {
-    // op(A)(m, k): contiguous in k unless transA
-    for (int e = tid; e < TC_M * TC_KC; e += 128) {
-      const int r = transA ? (e & (TC_M - 1)) : (e >> 6), kk = transA ? (e >> 7) : (e & (TC_KC - 1));
-      const int m = m0 + r, k = k0 + kk;
-      __nv_bfloat16 v = zero;
-      if (m < M && k < K) v = transA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
-      *reinterpret_cast<__nv_bfloat16*>(As + tc_core_off(r, kk)) = v;
-    }
-    // op(B)(k, n) stored as the NT x 64 K-major tile of op(B)^T: contiguous in n unless transB
-    for (int e = tid; e < NT * TC_KC; e += 128) {
-      const int c = transB ? (e >> 6) : (e % NT), kk = transB ? (e & (TC_KC - 1)) : (e / NT);
-      const int n = n0 + c, k = k0 + kk;
-      __nv_bfloat16 v = zero;
-      if (n < N && k < K) v = transB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
-      *reinterpret_cast<__nv_bfloat16*>(Bs + tc_core_off(c, kk)) = v;
-    }
+  for (int c = 0; c < nchunks && ok; ++c) {
+    const int b = c & 1;
+    unsigned char* As = tsm + b * stage_bytes;
+    unsigned char* Bs = As + TC_M * TC_KC * 2;
+    if (c >= 2) ok = mbar_wait(&bar[b], (uses[b] - 1) & 1u);   // the MMAs that read this stage are done
+    if (!__syncthreads_and(ok)) break;
+    tc_stage(As, A, lda, !transA, m0, TC_M, M, c * TC_KC, K, vecA, tid);
+    tc_stage(Bs, B, ldb, transB != 0, n0, NT, N, c * TC_KC, K, vecB, tid);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes -> tensor cores
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
+      const uint32_t a_addr = smem_u32(As), b_addr = smem_u32(Bs);
 #pragma unroll
       for (int kk = 0; kk < TC_KC / 16; ++kk) {
         const uint64_t ad = tc_smem_desc(a_addr + kk * 256, 128, 1024);
         const uint64_t bd = tc_smem_desc(b_addr + kk * 256, 128, 1024);
-        tc_mma(tmem, ad, bd, idesc, (k0 > 0 || kk > 0) ? 1u : 0u);
+        tc_mma(tmem, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
       }
-      tc_commit(&bar);
+      tc_commit(&bar[b]);
     }
-    ok = __syncthreads_and(mbar_wait(&bar, phase));
-    phase ^= 1u;
+    uses[b] += 1u;
   }
+  // the last commit covers every MMA issued before it
+  const int last = (nchunks - 1) & 1;
+  if (ok) ok = __syncthreads_and(mbar_wait(&bar[last], (uses[last] - 1) & 1u));
   tc_fence_after();
   if (ok) {
-    const int row = m0 + warp * 32 + lane;
-    for (int c = 0; c < NT; c += 16) {
-      uint32_t v[16];
-      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-      if (row < M) {
+    // 64-column slabs: tensor memory -> shared memory (row r at stride 65
+    // floats), then coalesced rows to global memory
+    float* slab = reinterpret_cast<float*>(tsm);
+    for (int s0 = 0; s0 < NT; s0 += 64) {
+      const int w = NT - s0 < 64 ? NT - s0 : 64;
+      for (int c = 0; c < w; c += 16) {
+        uint32_t v[16];
+        tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s0 + c), v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = n0 + c + j;
-          if (n >= N) break;
-          float x = __uint_as_float(v[j]);
+        for (int j = 0; j < 16; ++j) slab[(warp * 32 + lane) * 65 + c + j] = __uint_as_float(v[j]);
+      }
+      __syncthreads();
+      for (int e = tid; e < TC_M * w; e += 128) {
+        const int r = e / w, cc = e % w, row = m0 + r, n = n0 + s0 + cc;
+        if (row < M && n < N) {
+          float x = slab[r * 65 + cc];
           if (bias) x += bias[n];
           if (relu) x = x > 0.0f ? x : 0.0f;
           if (C) C[(size_t)row * ldc + n] = x;
           if (Cb) Cb[(size_t)row * ldcb + n] = __float2bfloat16(x);
         }
       }
+      __syncthreads();
     }
   } else if (tid == 0) {
     atomicExch(err, 1);
-    mbar_wait(&bar, phase ^ 1u);         // bounded: let an outstanding MMA finish before freeing
+    for (int q = 0; q < 2; ++q)          // bounded: let outstanding MMAs finish before freeing
+      if (uses[q]) mbar_wait(&bar[q], (uses[q] - 1) & 1u);
   }
   tc_fence_before();
   __syncthreads();
@@ -351,7 +433,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const _
 // dynamic shared memory of k_gemm_tc: the two tiles, and enough on top that
 // no more CTAs share an SM than its 512 tensor-memory columns can hold
 size_t tc_smem_bytes(int nt) {
-  const size_t tiles = (size_t)(TC_M + nt) * TC_KC * 2;
+  const size_t tiles = 2 * (size_t)(TC_M + nt) * TC_KC * 2;
   const int ctas = 512 / tc_cols(nt);
   const size_t cap = (size_t)(228 * 1024) / ctas - 2048;
   return std::max(tiles, std::min(cap, (size_t)200 * 1024));
@@ -391,7 +473,16 @@ void gemm(const thor_mlp* net, int M, int N, int K, const __nv_bfloat16* A, int 
           __nv_bfloat16* Cb, int ldcb) {
   cudaStream_t st = net->stream;
   if (net->use_tc) {
-    const int ntiles = (N + 255) / 256;
+    // the widest tile (fewest re-stagings of A) that still gives about one
+    // CTA per SM, else 64 columns
+    const int mtiles = (M + TC_M - 1) / TC_M;
+    int width = 64;
+    for (int w : {256, 128})
+      if (mtiles * ((N + w - 1) / w) >= 148) {
+        width = w;
+        break;
+      }
+    const int ntiles = (N + width - 1) / width;
     const int nt = ((N + ntiles - 1) / ntiles + 15) / 16 * 16;
     dim3 grid(ntiles, (M + TC_M - 1) / TC_M);
     k_gemm_tc<<<grid, 128, tc_smem_bytes(nt), st>>>(M, N, K, A, lda, transA, B, ldb, transB, C, ldc, bias, relu,
@@ -437,7 +528,7 @@ int mlp_backward(thor_mlp* net, const float* dy, int m) {
                                                  l + 1 < L);
     // dW_l = h_l^T gb  ([K][N]), db_l = column sums of g
     gemm(net, K, N, m, net->h[l], K, 1, net->gb, N, 0, net->grad + net->woff[l], N, nullptr, 0, nullptr, 0);
-    k_colsum<<<(N + 127) / 128, 128, 0, st>>>(gl, m, N, net->grad + net->boff[l]);
+    k_colsum<<<(N + 31) / 32, 1024, 0, st>>>(gl, m, N, net->grad + net->boff[l]);
     if (l > 0) {
       // g_{l-1} = gb W_l^T ([m][K]) into z[l-1]
       const __nv_bfloat16* W = net->pb + net->woff[l];

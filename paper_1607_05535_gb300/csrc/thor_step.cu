@@ -697,14 +697,15 @@ size_t solve_tma_smem_bytes(int nv) {
          sizeof(uint64_t);
 }
 
-__global__ void __launch_bounds__(32 * kSolveWarps)
-    k_ss_solve_tma(Geo<float> G, VR<float> U, Phys ph, const __grid_constant__ SolveMaps M, int stage0,
-                   Xf<float> Xs, Slow<float> SL, Pert<float> P, Work<float> T, double dtau, int want_div,
-                   int* err) {
+// M: the state's descriptors, in kernel-parameter or global memory
+__device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<float>& U, const Phys& ph,
+                                               const SolveMaps& M, int stage0, const Xf<float>& Xs,
+                                               const Slow<float>& SL, const Pert<float>& P, const Work<float>& T,
+                                               double dtau, int want_div, int* err, int bx) {
   extern __shared__ unsigned char smraw[];
   const int nv = G.nv, S = G.colp, N = nv - 1;
   const int tid = threadIdx.x, tx = tid & 31, warp = tid >> 5;
-  const int c0 = blockIdx.x * 32, c = c0 + tx;
+  const int c0 = bx * 32, c = c0 + tx;
   const bool valid = c < G.ncol;
   const int p = N / 2 > 0 ? N / 2 : 1;
   unsigned char* base = smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u);
@@ -834,6 +835,13 @@ __global__ void __launch_bounds__(32 * kSolveWarps)
   }
 }
 
+__global__ void __launch_bounds__(32 * kSolveWarps)
+    k_ss_solve_tma(Geo<float> G, VR<float> U, Phys ph, const __grid_constant__ SolveMaps M, int stage0,
+                   Xf<float> Xs, Slow<float> SL, Pert<float> P, Work<float> T, double dtau, int want_div,
+                   int* err) {
+  d_ss_solve_tma(G, U, ph, M, stage0, Xs, SL, P, T, dtau, want_div, err, blockIdx.x);
+}
+
 // ---------------------------------------------------------------- kernels: ensemble
 //
 // One launch covers every member: block b of the launch works on local block
@@ -904,6 +912,14 @@ __global__ void __launch_bounds__(64)
   THOR_MEMBER();
   const int want_div = a.divdamp && j + 1 < a.nsub[s];
   d_ss_solve<R>(a.G, a.U, a.ph, Xs, a.SL, a.P, a.T, a.F, a.dts[s], want_div, e.y, 0);
+}
+__global__ void __launch_bounds__(32 * kSolveWarps)
+    ke_ss_solve_tma(const Member<float>* __restrict__ M, const int2* __restrict__ map, int s, int j) {
+  const int2 e = map[blockIdx.x];
+  const Member<float>& a = M[e.x];
+  const Xf<float> Xs = s == 0 ? a.Xt : a.Xst;
+  const int want_div = a.divdamp && j + 1 < a.nsub[s];
+  d_ss_solve_tma(a.G, a.U, a.ph, *a.smap, s == 0, Xs, a.SL, a.P, a.T, a.dts[s], want_div, a.err, e.y);
 }
 template <typename R>
 __global__ void ke_stage_end(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
@@ -1076,7 +1092,8 @@ int Impl<float>::build_solve_maps() {
   make(&map->cf, F.cf, nv + 1, true);
   make(&map->junction, F.junction, 1, true);
   if (!ok) return 0;
-  if (cudaFuncSetAttribute(k_ss_solve_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_ss_solve_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(ke_ss_solve_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return -3;
   smaps = std::move(map);
   return 0;
@@ -1127,7 +1144,14 @@ int ensemble_large_step(const EnsPlan<R>& E, cudaStream_t stream, long long* lau
       }
       ke_ss_mom<R><<<a2, bs, 0, stream>>>(M, E.map, s, kc);
       ke_ss_flux<R><<<a2, bs, 0, stream>>>(M, E.map, s, kc);
-      ke_ss_solve<R><<<nbc, 64, solve_smem, stream>>>(M, E.mapc, s, j);
+      if constexpr (sizeof(R) == sizeof(float)) {
+        if (E.staged)
+          ke_ss_solve_tma<<<nbc, 32 * kSolveWarps, solve_tma_smem_bytes(E.nv), stream>>>(M, E.mapc, s, j);
+        else
+          ke_ss_solve<R><<<nbc, 64, solve_smem, stream>>>(M, E.mapc, s, j);
+      } else {
+        ke_ss_solve<R><<<nbc, 64, solve_smem, stream>>>(M, E.mapc, s, j);
+      }
       n += 3;
     }
     ke_stage_end<R><<<g2i, bs, 0, stream>>>(M, E.map, s, kc);
