@@ -3,6 +3,10 @@
 
     python -m paper_1607_05535_gb300.run --workload hs_g6 --precision mixed --steps 3
     python -m paper_1607_05535_gb300.run --ensemble --steps 2
+    python -m paper_1607_05535_gb300.run --mlp --steps 3
+
+--mlp runs training steps of the closure-sized MLP (320-256-256-256-160,
+batch 1024) on seeded random data.
 
 Workloads (seeded, synthetic; module ``workloads`` at the repository root):
 hs_g4 (Held-Suarez glevel 4 x 20), hs_g6 (glevel 6 x 32), hj_g6 (hot
@@ -68,6 +72,23 @@ def run_ensemble(thor, wls, steps, spring_iters):
             thor.thor_grid_destroy(g)
 
 
+def run_mlp(thor, torch, steps):
+    sizes = [320, 256, 256, 256, 160]
+    net = thor.thor_mlp_create(sizes, 1024, seed=1)
+    try:
+        g = torch.Generator(device="cuda")
+        g.manual_seed(5)
+        x = torch.randn(1024, sizes[0], device="cuda", generator=g)
+        t = torch.randn(1024, sizes[-1], device="cuda", generator=g)
+        loss = torch.zeros(1, device="cuda")
+        for _ in range(steps):
+            thor.thor_mlp_train_step(net, x, t, 1e-3, loss)
+        thor.thor_mlp_get_params(net)
+        return {"mlp": sizes, "batch": 1024, "steps": steps, "loss": float(loss.item())}
+    finally:
+        thor.thor_mlp_destroy(net)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--workload", default="hs_g6", choices=["hs_g4", "hs_g6", "hj_g6"])
@@ -77,6 +98,7 @@ def main(argv=None):
     ap.add_argument("--kchunk", type=int, default=2)
     ap.add_argument("--solve-tma", type=int, default=1, choices=[0, 1])
     ap.add_argument("--ensemble", action="store_true")
+    ap.add_argument("--mlp", action="store_true")
     args = ap.parse_args(argv)
     import torch
     import paper_1607_05535_gb300 as thor
@@ -84,7 +106,9 @@ def main(argv=None):
         raise SystemExit("a CUDA device is required")
     torch.cuda.set_device(0)
     wls, table = _workloads()
-    if args.ensemble:
+    if args.mlp:
+        out = run_mlp(thor, torch, args.steps)
+    elif args.ensemble:
         out = run_ensemble(thor, wls, args.steps, args.spring_iters)
     else:
         prec = thor.THOR_FP64 if args.precision == "fp64" else thor.THOR_MIXED

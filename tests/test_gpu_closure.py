@@ -30,6 +30,62 @@ def test_coarse_grain_of_rest_is_rest_and_conserves_mass():
     assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
 
 
+def test_coarse_grain_and_features_match_host():
+    """thor_coarse_grain equals the area-weighted mean over each coarse
+    column's fine members (momentum projected onto the coarse tangent plane,
+    W zero at the boundaries), and thor_closure_features equals the column's
+    deviations from the reference column and its neighbour-mean anomalies,
+    both recomputed here on the host from the fine state and the grid tables."""
+    wl = wls.HS_G4
+    su = cl.make_setup(wl, 4, 3, thor.THOR_FP64, None)
+    try:
+        thor.thor_step(su.fine, 3, wl.n_small, wl.dt)
+        nv, ncf, ncc = su.nv, su.ncol_f, su.ncol_c
+        rest_init = thor.thor_init(wl.T0, wl.p_surf, 0.0, wl.seed, 1, wl.hj_dT, thor.THOR_FP64, 1, 1)
+        rest = thor.thor_state_init(su.coarse_grid, cl_planet(wl), rest_init, None)
+        ref = cl.column_fields(rest, ncc, nv)[0]               # the resting state is the reference column
+        thor.thor_state_destroy(rest)
+        thor.thor_coarse_grain(su.fine, su.coarse, su.fmap)
+        F = cl.column_fields(su.fine, ncf, nv)
+        Wf = thor.thor_state_get(su.fine, thor.THOR_FIELD_W, ncf, nv)
+        area = thor.thor_grid_areas(su.fine_grid)
+        w = np.zeros(ncc)
+        np.add.at(w, su.fmap, area)
+        E = np.zeros((ncc, 5 * nv))
+        np.add.at(E, su.fmap, F * area[:, None])
+        E /= w[:, None]
+        EW = np.zeros((ncc, nv + 1))
+        np.add.at(EW, su.fmap, Wf * area[:, None])
+        EW /= w[:, None]
+        EW[:, 0] = EW[:, nv] = 0.0
+        r = thor.thor_grid_points(su.coarse_grid)
+        r /= np.linalg.norm(r, axis=1, keepdims=True)
+        m = np.stack([E[:, nv:2 * nv], E[:, 2 * nv:3 * nv], E[:, 3 * nv:4 * nv]], axis=-1)
+        m -= np.einsum("ckd,cd->ck", m, r)[..., None] * r[:, None, :]
+        E[:, nv:2 * nv], E[:, 2 * nv:3 * nv], E[:, 3 * nv:4 * nv] = m[..., 0], m[..., 1], m[..., 2]
+        got = cl.column_fields(su.coarse, ncc, nv)
+        for f in range(5):
+            sl = slice(f * nv, (f + 1) * nv)
+            d = got[:, sl] - E[:, sl]
+            scale = np.max(np.abs(E[:, sl] - (ref[sl] if f in (0, 4) else 0.0))) + 1e-300
+            assert np.max(np.abs(d)) <= 1e-10 * scale, (f, np.max(np.abs(d)) / scale)
+        gW = thor.thor_state_get(su.coarse, thor.THOR_FIELD_W, ncc, nv)
+        assert np.max(np.abs(gW - EW)) <= 1e-10 * (np.max(np.abs(EW)) + 1e-300)
+
+        x = cl.features(su.coarse, ncc, nv, torch, "cuda").double().cpu().numpy()
+        dev = got - np.where(np.isin(np.arange(5 * nv) // nv, [0, 4]), ref, 0.0)
+        nbr = thor.thor_grid_neighbours(su.coarse_grid)
+        anom = np.empty_like(dev)
+        for c in range(ncc):
+            q = [j for j in nbr[c] if j >= 0 and j != c]
+            anom[c] = dev[q].mean(axis=0) - dev[c]
+        for blk, want in ((slice(0, 5 * nv), dev), (slice(5 * nv, 10 * nv), anom)):
+            scale = np.max(np.abs(want), axis=0) + 1e-300
+            assert np.all(np.abs(x[:, blk] - want) <= 1e-5 * scale + 1e-30)
+    finally:
+        cl.destroy_setup(su)
+
+
 def test_closure_window_semantics():
     """With a window of n large steps, the closure's state after n steps is
     the plain state after n steps plus n dt tau_hat(features of the start
