@@ -154,6 +154,20 @@ int thor_diag(thor_state* state, thor_diag_t* out);
 int thor_state_get(thor_state* state, int field, double* host, size_t n);
 int thor_state_set(thor_state* state, int field, const double* host, size_t n);
 
+/* Raw checkpoint of the prognostic state: the stored arrays (deviation form,
+ * padded layout) bit for bit after a 64-byte header (magic, precision, ncol,
+ * nv). thor_checkpoint_bytes gives the buffer size; save and load copy
+ * to / from `buf` in host or device memory (unified addressing) and
+ * synchronise the state's stream. Loading into a state of another grid
+ * size, level count or precision, or a buffer without the header, returns
+ * THOR_EINVAL and leaves the state unchanged. A restart from a checkpoint
+ * continues bit for bit like an uninterrupted run; thor_state_get/_set,
+ * which exchange full float64 values, round the reference column plus the
+ * deviation (a unit in the last place) in float64 storage. */
+int thor_checkpoint_bytes(const thor_state* state, size_t* bytes);
+int thor_checkpoint_save(thor_state* state, void* buf, size_t bytes);
+int thor_checkpoint_load(thor_state* state, const void* buf, size_t bytes);
+
 /* Kernel launches issued by this state so far. */
 int thor_launch_count(const thor_state* state, long long* count);
 

@@ -35,6 +35,7 @@ EXPORTED = [
     "thor_mlp_destroy", "thor_closure_features", "thor_closure_attach", "thor_coarse_grain",
     "thor_autotune", "thor_ensemble_create", "thor_ensemble_step", "thor_ensemble_info",
     "thor_ensemble_tune", "thor_ensemble_autotune", "thor_ensemble_destroy", "thor_mlp_tune",
+    "thor_checkpoint_bytes", "thor_checkpoint_save", "thor_checkpoint_load",
 ]
 
 # kernel ids of thor_profile_read
@@ -123,6 +124,9 @@ def _load():
         "thor_ensemble_autotune": (I, [P, IP, ctypes.POINTER(D), I, IP, IP, ctypes.POINTER(D)]),
         "thor_ensemble_destroy": (None, [P]),
         "thor_mlp_tune": (I, [P, I, I]),
+        "thor_checkpoint_bytes": (I, [P, ctypes.POINTER(Z)]),
+        "thor_checkpoint_save": (I, [P, P, Z]),
+        "thor_checkpoint_load": (I, [P, P, Z]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -379,3 +383,24 @@ def thor_ensemble_autotune(ens, n_small, dt, steps=3):
 
 def thor_ensemble_destroy(ens):
     _lib.thor_ensemble_destroy(ens)
+
+
+def thor_checkpoint_bytes(state):
+    n = ctypes.c_size_t()
+    _check(_lib.thor_checkpoint_bytes(state, ctypes.byref(n)), "thor_checkpoint_bytes")
+    return n.value
+
+
+def thor_checkpoint_save(state, buf=None):
+    """Raw checkpoint into `buf` (a numpy uint8 array or a torch uint8 tensor,
+    host or device, of thor_checkpoint_bytes bytes); a new host array if None."""
+    n = thor_checkpoint_bytes(state)
+    if buf is None:
+        buf = np.empty(n, dtype=np.uint8)
+    _check(_lib.thor_checkpoint_save(state, _ptr(buf), n), "thor_checkpoint_save")
+    return buf
+
+
+def thor_checkpoint_load(state, buf):
+    n = buf.numel() if hasattr(buf, "numel") else buf.size
+    _check(_lib.thor_checkpoint_load(state, _ptr(buf), n), "thor_checkpoint_load")

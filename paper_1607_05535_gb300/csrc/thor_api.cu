@@ -663,6 +663,54 @@ int thor_step(thor_state* s, int n_large, int n_small, double dt) {
   return nf ? THOR_ENONFINITE : THOR_OK;
 }
 
+namespace {
+// header of a raw checkpoint
+struct CkptHeader {
+  char magic[8];
+  int precision, ncol, nv, colp;
+  unsigned long long payload;
+  char pad[32];
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+const char kCkptMagic[8] = {'T', 'H', 'O', 'R', 'C', 'K', 'P', '1'};
+}  // namespace
+
+int thor_checkpoint_bytes(const thor_state* s, size_t* bytes) {
+  if (!s || !bytes) return THOR_EINVAL;
+  *bytes = sizeof(CkptHeader) + s->impl->state_bytes();
+  return THOR_OK;
+}
+
+int thor_checkpoint_save(thor_state* s, void* buf, size_t bytes) {
+  if (!s || !buf) return THOR_EINVAL;
+  const size_t payload = s->impl->state_bytes();
+  if (bytes != sizeof(CkptHeader) + payload) return THOR_EINVAL;
+  CkptHeader h{};
+  std::memcpy(h.magic, kCkptMagic, 8);
+  h.precision = s->precision;
+  h.ncol = s->grid->h.ncol;
+  h.nv = s->grid->h.nv;
+  h.colp = thor::colp_of(h.ncol);
+  h.payload = payload;
+  char* p = static_cast<char*>(buf);
+  if (cudaMemcpy(p, &h, sizeof(h), cudaMemcpyDefault)) return THOR_ECUDA;
+  if (s->impl->save_state(p + sizeof(h))) return THOR_ECUDA;
+  return cudaStreamSynchronize(s->impl->stream) ? THOR_ECUDA : THOR_OK;
+}
+
+int thor_checkpoint_load(thor_state* s, const void* buf, size_t bytes) {
+  if (!s || !buf) return THOR_EINVAL;
+  const size_t payload = s->impl->state_bytes();
+  if (bytes != sizeof(CkptHeader) + payload) return THOR_EINVAL;
+  CkptHeader h{};
+  if (cudaMemcpy(&h, buf, sizeof(h), cudaMemcpyDefault)) return THOR_ECUDA;
+  if (std::memcmp(h.magic, kCkptMagic, 8) || h.precision != s->precision || h.ncol != s->grid->h.ncol ||
+      h.nv != s->grid->h.nv || h.payload != payload)
+    return THOR_EINVAL;
+  if (s->impl->load_state(static_cast<const char*>(buf) + sizeof(h))) return THOR_ECUDA;
+  return cudaStreamSynchronize(s->impl->stream) ? THOR_ECUDA : THOR_OK;
+}
+
 int thor_diag(thor_state* s, thor_diag_t* out) {
   if (!s || !out) return THOR_EINVAL;
   double v[8];

@@ -217,7 +217,8 @@ struct Impl : ImplBase {
   int diag(double* out8, long long* nonfinite) override;
   int get(int field, double* host, size_t n) override;
   int set(int field, const double* host, size_t n) override;
-  // rho, M (3), rho theta: nv planes each; W: nv + 1 planes
+  // rho, M (3), rho theta: nv planes each; W: nv + 1 planes; buf in device or
+  // host memory (unified addressing)
   size_t state_bytes() const override { return (size_t)(6 * G.nv + 1) * G.colp * sizeof(R); }
   int copy_state(char* buf, bool save) {
     const size_t plane = (size_t)G.colp * sizeof(R), c = G.nv * plane;
@@ -225,8 +226,8 @@ struct Impl : ImplBase {
     size_t off = 0;
     for (int i = 0; i < 6; ++i) {
       const size_t bytes = i == 5 ? c + plane : c;
-      cudaError_t e = save ? cudaMemcpyAsync(buf + off, f[i], bytes, cudaMemcpyDeviceToDevice, stream)
-                           : cudaMemcpyAsync(f[i], buf + off, bytes, cudaMemcpyDeviceToDevice, stream);
+      cudaError_t e = save ? cudaMemcpyAsync(buf + off, f[i], bytes, cudaMemcpyDefault, stream)
+                           : cudaMemcpyAsync(f[i], buf + off, bytes, cudaMemcpyDefault, stream);
       if (e) return -3;
       off += bytes;
     }

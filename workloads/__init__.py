@@ -137,7 +137,7 @@ def temperature_noise(wl, ncol=None):
 # scales with the grid spacing, radius * 2^-glevel, and is capped at
 # 1 / (4 Omega) so that the explicit Coriolis term stays well inside the RK3
 # stability region.
-ENSEMBLE_SEED = 0xE45E
+ENSEMBLE_SEED = 42
 
 
 @dataclass(frozen=True)
