@@ -168,6 +168,14 @@ int thor_checkpoint_bytes(const thor_state* state, size_t* bytes);
 int thor_checkpoint_save(thor_state* state, void* buf, size_t bytes);
 int thor_checkpoint_load(thor_state* state, const void* buf, size_t bytes);
 
+/* Self-test of the bounded device waits (the mbarrier waits of the staged
+ * column solve and of the tensor-core GEMM, normally bounded at 2 s): one
+ * thread waits, with limit limit_us (1 .. 2e6 microseconds), on a barrier of
+ * one expected arrival; arrive = 1 arrives first. *gave_up = 1 if the wait
+ * ran out, 0 if it completed. A wait that runs out leaves nothing in flight,
+ * and the context stays usable. Synchronous (default stream). */
+int thor_wait_selftest(int arrive, unsigned int limit_us, int* gave_up);
+
 /* Kernel launches issued by this state so far. */
 int thor_launch_count(const thor_state* state, long long* count);
 

@@ -35,7 +35,7 @@ EXPORTED = [
     "thor_mlp_destroy", "thor_closure_features", "thor_closure_attach", "thor_coarse_grain",
     "thor_autotune", "thor_ensemble_create", "thor_ensemble_step", "thor_ensemble_info",
     "thor_ensemble_tune", "thor_ensemble_autotune", "thor_ensemble_destroy", "thor_mlp_tune",
-    "thor_checkpoint_bytes", "thor_checkpoint_save", "thor_checkpoint_load",
+    "thor_checkpoint_bytes", "thor_checkpoint_save", "thor_checkpoint_load", "thor_wait_selftest",
 ]
 
 # kernel ids of thor_profile_read
@@ -127,6 +127,7 @@ def _load():
         "thor_checkpoint_bytes": (I, [P, ctypes.POINTER(Z)]),
         "thor_checkpoint_save": (I, [P, P, Z]),
         "thor_checkpoint_load": (I, [P, P, Z]),
+        "thor_wait_selftest": (I, [I, ctypes.c_uint, IP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -404,3 +405,10 @@ def thor_checkpoint_save(state, buf=None):
 def thor_checkpoint_load(state, buf):
     n = buf.numel() if hasattr(buf, "numel") else buf.size
     _check(_lib.thor_checkpoint_load(state, _ptr(buf), n), "thor_checkpoint_load")
+
+
+def thor_wait_selftest(arrive, limit_us):
+    """1 if a bounded device wait ran out, 0 if it completed."""
+    g = ctypes.c_int()
+    _check(_lib.thor_wait_selftest(int(arrive), int(limit_us), ctypes.byref(g)), "thor_wait_selftest")
+    return g.value

@@ -194,6 +194,19 @@ __global__ void __launch_bounds__(256) k_diag_final(double* part, int nblocks) {
   }
 }
 
+// The bounded mbarrier wait of the staged solve and of the tensor-core GEMM,
+// on a barrier of one expected arrival: with arrive = 0 nothing arrives and
+// the wait must give up after limit_ns; with arrive = 1 the thread arrives
+// first and the wait must succeed. out = 1 if the wait gave up, else 0.
+__global__ void k_wait_probe(int arrive, unsigned long long limit_ns, int* out) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  mbar_init_fence();
+  if (arrive) mbar_arrive(&bar);
+  *out = mbar_wait(&bar, 0, limit_ns) ? 0 : 1;
+}
+
 // ------------------------------------------------------------ allocation
 
 struct Carver {
@@ -674,6 +687,19 @@ struct CkptHeader {
 static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
 const char kCkptMagic[8] = {'T', 'H', 'O', 'R', 'C', 'K', 'P', '1'};
 }  // namespace
+
+int thor_wait_selftest(int arrive, unsigned int limit_us, int* gave_up) {
+  if (!gave_up || limit_us < 1 || limit_us > 2000000) return THOR_EINVAL;
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int))) return THOR_ENOMEM;
+  int h = -1;
+  thor::k_wait_probe<<<1, 32>>>(arrive ? 1 : 0, 1000ull * limit_us, d);
+  cudaError_t e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e) return THOR_ECUDA;
+  *gave_up = h;
+  return THOR_OK;
+}
 
 int thor_checkpoint_bytes(const thor_state* s, size_t* bytes) {
   if (!s || !bytes) return THOR_EINVAL;

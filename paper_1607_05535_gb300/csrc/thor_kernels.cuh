@@ -288,16 +288,20 @@ __device__ __forceinline__ void tma_prefetch_2d(const void* map, int x, int y) {
                "r"(x), "r"(y)
                : "memory");
 }
-// true once the barrier's phase `parity` has completed; false after kWaitNs
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// true once the barrier's phase `parity` has completed; false after limit_ns
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (int i = 0; i < (1 << 26); ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
     __nanosleep(32);
   }
   return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 // box of a 2-D tensor map (x = column, y = plane) into shared memory
 __device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y, uint64_t* bar) {

@@ -52,6 +52,10 @@ def test_ensemble_argument_checks_need_no_device():
             call()
         assert e.value.status == thor.THOR_EINVAL
     thor.thor_ensemble_destroy(None)
+    for limit in (0, 2000001):
+        with pytest.raises(thor.ThorError) as e:
+            thor.thor_wait_selftest(0, limit)
+        assert e.value.status == thor.THOR_EINVAL
 
 
 def _match(P, O):

@@ -145,3 +145,23 @@ def test_restart_through_float64_fields(precision):
             if s_ is not None:
                 thor.thor_state_destroy(s_)
         thor.thor_grid_destroy(grid)
+
+
+def test_bounded_device_wait_gives_up_and_the_context_stays_usable():
+    """A device wait on a barrier that nothing completes runs out after its
+    limit and reports it; with the arrival it completes at once; afterwards
+    the same context steps a state normally."""
+    import time
+    t0 = time.perf_counter()
+    assert thor.thor_wait_selftest(0, 20000) == 1
+    assert time.perf_counter() - t0 >= 0.015
+    assert thor.thor_wait_selftest(1, 20000) == 0
+    wl = wls.HS_G4
+    grid = _grid(wl)
+    st = thor.thor_state_init(grid, planet_struct(wl.planet), init_struct(wl, thor.THOR_MIXED), None)
+    try:
+        thor.thor_step(st, 1, wl.n_small, wl.dt)
+        assert thor.thor_diag(st)["nonfinite"] == 0
+    finally:
+        thor.thor_state_destroy(st)
+        thor.thor_grid_destroy(grid)
