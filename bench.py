@@ -36,14 +36,14 @@ METRIC = "cell-substeps/s"
 
 # Unique field words each kernel reads or writes per cell (neighbour reads of
 # a field counted once), the counting rule of the algorithmic roofline. The
-# column solve reads 11 float planes (W*, S_W, c, a, lo/up, theta at the
-# interfaces, b, p', Th^(s), D^(s), div_h M*) and 2 float64 factor planes (4
-# words), and writes 5 (rho*, Th*, p*, W*, D); the factorisation reads 2 and
-# writes 2 float64 planes and one float plane.
+# column solve reads 10 float planes (W*, S_W, c, a, theta at the interfaces,
+# b, p', Th^(s), D^(s), div_h M*) and 3 float64 factor planes (pivot
+# reciprocal, c'/e', q: 6 words), and writes 5 (rho*, Th*, p*, W*, D); the
+# factorisation reads 2 planes and writes the 3 float64 ones.
 KERNEL_WORDS = {
     "derived": 6 + 10, "lap1": 8 + 6, "slow": 17 + 8, "slow_w": 7 + 2, "stage_init": 13 + 7,
-    "ss_div": 5 + 1, "ss_grad": 1 + 3, "ss_mom": 10 + 3, "ss_flux": 10 + 4, "ss_solve": 11 + 4 + 5,
-    "ss_factor": 2 + 5, "stage_end": 12 + 6, "physics": 5 + 4,
+    "ss_div": 5 + 1, "ss_grad": 1 + 3, "ss_mom": 10 + 3, "ss_flux": 10 + 4, "ss_solve": 10 + 6 + 5,
+    "ss_factor": 2 + 6, "stage_end": 12 + 6, "physics": 5 + 4,
 }
 
 

@@ -256,7 +256,7 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   P.w = cv.take<R>(F);
   I.F.inv = cv.take<double>(F);
   I.F.cf = cv.take<double>(F);
-  I.F.off = cv.take<R>(F);
+  I.F.q = cv.take<double>(F);
   I.F.junction = cv.take<double>(S);
   // tables
   I.G.nbr = cv.take<int>(6 * S);

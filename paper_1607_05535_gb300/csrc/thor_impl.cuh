@@ -44,7 +44,7 @@ struct Pert {
 // each a 2-D map (x = column, y = plane) with a box of 32 columns x all planes
 struct SolveMaps {
   CUtensorMap w, sw, cc, ca, thi, cb, pp, th_t, th_s, dsc, dhm;   // float
-  CUtensorMap off, inv, cf, junction;                           // float64 factors
+  CUtensorMap q, inv, cf, junction;                             // float64 factors
 };
 
 // Everything the kernels of one state need, as one record: a device array of

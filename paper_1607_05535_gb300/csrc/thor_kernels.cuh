@@ -78,14 +78,13 @@ struct Phys {
   double Rd, cp, cv, gamma, kappa, g, omega, p_ref;
 };
 
-// Factors of the per-stage vertical matrix: planes [nv + 1][colp] (rows
-// 1..nv-1 used) and one plane for the junction of the two sweeps. Pivot
-// reciprocals, c' / e' and the junction factor are float64; the off-diagonal
-// entries lo / up are assembled in the storage type, so they are kept in it.
+// Float64 factors of the per-stage vertical matrix: planes [nv + 1][colp]
+// (rows 1..nv-1 used) and one plane for the junction of the two sweeps. Per
+// row: the pivot reciprocal, c' (downward sweep) or e' (upward sweep), and q,
+// the off-diagonal entry lo (down) or up (up) times the pivot reciprocal.
 template <typename R>
 struct Fac {
-  double *inv, *cf, *junction;
-  R* off;
+  double *inv, *cf, *junction, *q;
 };
 
 // state in deviation form

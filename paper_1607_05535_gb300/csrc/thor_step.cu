@@ -365,8 +365,9 @@ __device__ __forceinline__ void d_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R>
 // algorithm in float64: warp 0 eliminates rows 1..p downwards
 // (c'_m = up_m / (di_m - lo_m c'_m-1)), warp 1 rows nv-1..p+1 upwards
 // (e'_m = lo_m / (di_m - up_m e'_m+1)); the two warps run on different SM
-// sub-partitions. Stored per row: the pivot reciprocal, c' or e', and lo or
-// up; per column: 1 / (1 - c'_p e'_p+1) for the junction rows p, p+1.
+// sub-partitions. Stored per row: the pivot reciprocal, c' or e', and q = lo
+// or up times the pivot reciprocal; per column: 1 / (1 - c'_p e'_p+1) for the
+// junction rows p, p+1.
 template <typename R>
 __device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> SL, Fac<R> F,
                                             double dtau, int bx, int by) {
@@ -403,7 +404,7 @@ __device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> 
       if (valid) {
         F.inv[m * S + c] = inv;
         F.cf[m * S + c] = last;
-        F.off[m * S + c] = (R)lo;
+        F.q[m * S + c] = lo * inv;
       }
     }
   } else {
@@ -415,7 +416,7 @@ __device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> 
       if (valid) {
         F.inv[m * S + c] = inv;
         F.cf[m * S + c] = last;
-        F.off[m * S + c] = (R)up;
+        F.q[m * S + c] = up * inv;
       }
     }
   }
@@ -426,8 +427,9 @@ __device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> 
 
 // HE-VI column step, part 3 (every small step). The right-hand side
 //   rh_m = W*_m + dtau S_W,m - dtau/dzc_m (c_m - c_m-1) - dtau g (w- a_m-1 + w+ a_m)
-// goes through the stored factors in float64 (d'_m = (rh_m - lo_m d'_m-1) / piv_m
-// downwards, f'_m = (rh_m - up_m f'_m+1) / piv_m upwards, the junction rows
+// goes through the stored factors in float64 (d'_m = rh_m / piv_m - q_m d'_m-1
+// downwards, f'_m = rh_m / piv_m - q_m f'_m+1 upwards: one dependent FMA per
+// row, the product rh_m / piv_m off the chain; then the junction rows
 // x_p = (d'_p - c'_p f'_p+1) / (1 - c'_p e'_p+1), x_p+1 = f'_p+1 - e'_p+1 x_p,
 // then back substitution outwards); then rho* and Th* follow from Eqs. dens2
 // and pt2 and p* from the nonlinear Eq. theta_to_p. One block = 32 columns
@@ -462,7 +464,7 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
     for (int m = 1; m <= p; ++m) {
       const int i = m * S + cs;
       scf[m * 32 + tx] = ld(F.cf + i);
-      d1 = (rhs(m) - (double)ld(F.off + i) * d1) * ld(F.inv + i);
+      d1 = fma(-ld(F.q + i), d1, rhs(m) * ld(F.inv + i));
       sdp[m * 32 + tx] = d1;
     }
   } else {
@@ -471,7 +473,7 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
     for (int m = N; m > p; --m) {
       const int i = m * S + cs;
       scf[m * 32 + tx] = ld(F.cf + i);
-      f1 = (rhs(m) - (double)ld(F.off + i) * f1) * ld(F.inv + i);
+      f1 = fma(-ld(F.q + i), f1, rhs(m) * ld(F.inv + i));
       sdp[m * 32 + tx] = f1;
     }
   }
@@ -680,8 +682,9 @@ __global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, int forcing, doub
 // ---------------------------------------------------------------- staged column solve (float storage)
 //
 // The column step of d_ss_solve for 32 columns with eight warps. Thread 0
-// stages the planes of the elimination (W*, S_W, c, a, lo/up, pivot
-// reciprocals, c'/e', junction factors) into shared memory with one
+// stages the planes of the elimination (W*, S_W, c, a, the scaled
+// off-diagonals q, pivot reciprocals, c'/e', junction factors) into shared
+// memory with one
 // cp.async.bulk.tensor per array, and asks the copy engine to prefetch the
 // planes of the final updates into L2. Warps 0 and 1 then run the two float64
 // sweeps out of shared memory (d' overwrites the pivot reciprocal it has just
@@ -693,8 +696,7 @@ constexpr int kSolveWarps = 8;
 
 size_t solve_tma_smem_bytes(int nv) {
   const size_t f = 4 * 32, d = 8 * 32;   // one plane row of 32 columns
-  return 128 + (size_t)(2 * (nv + 1) + 2 * nv + (nv + 1) + (nv + 1)) * f + (size_t)(2 * (nv + 1) + 1 + 2) * d +
-         sizeof(uint64_t);
+  return 128 + (size_t)(2 * (nv + 1) + 2 * nv) * f + (size_t)(3 * (nv + 1) + 1 + 2) * d + sizeof(uint64_t);
 }
 
 // M: the state's descriptors, in kernel-parameter or global memory
@@ -713,9 +715,9 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
   float* s_sw = s_w + (nv + 1) * 32;               // [nv + 1][32]
   float* s_cc = s_sw + (nv + 1) * 32;              // [nv][32]
   float* s_ca = s_cc + nv * 32;                    // [nv][32]
-  float* s_off = s_ca + nv * 32;                   // [nv + 1][32]
-  float* s_wf = s_off + (nv + 1) * 32;             // [nv + 1][32] solved W*
-  double* s_inv = reinterpret_cast<double*>(s_wf + (nv + 1) * 32);   // [nv + 1][32], then d' / f' / x
+  float* s_wf = s_w;                               // solved W*, over W* once the sweeps are done
+  double* s_q = reinterpret_cast<double*>(s_ca + nv * 32);   // [nv + 1][32]
+  double* s_inv = s_q + (nv + 1) * 32;             // [nv + 1][32], then d' and f'
   double* s_cf = s_inv + (nv + 1) * 32;            // [nv + 1][32]
   double* s_junc = s_cf + (nv + 1) * 32;           // [32]
   double* sx = s_junc + 32;                        // [2][32]
@@ -728,12 +730,12 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
   __syncthreads();
   if (tid == 0) {
     const uint32_t fi = (nv + 1) * 128, fc = nv * 128, di = (nv + 1) * 256;
-    mbar_arrive_expect_tx(bar, 3 * fi + 2 * fc + 2 * di + 256);
+    mbar_arrive_expect_tx(bar, 2 * fi + 2 * fc + 3 * di + 256);
     tma_load_2d(s_w, &M.w, c0, 0, bar);
     tma_load_2d(s_sw, &M.sw, c0, 0, bar);
     tma_load_2d(s_cc, &M.cc, c0, 0, bar);
     tma_load_2d(s_ca, &M.ca, c0, 0, bar);
-    tma_load_2d(s_off, &M.off, c0, 0, bar);
+    tma_load_2d(s_q, &M.q, c0, 0, bar);
     tma_load_2d(s_inv, &M.inv, c0, 0, bar);
     tma_load_2d(s_cf, &M.cf, c0, 0, bar);
     tma_load_2d(s_junc, &M.junction, c0, 0, bar);
@@ -767,7 +769,7 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
 #pragma unroll 4
       for (int m = 1; m <= p; ++m) {
         const int o = m * 32 + tx;
-        d1 = (rhs(m) - (double)s_off[o] * d1) * s_inv[o];
+        d1 = fma(-s_q[o], d1, rhs(m) * s_inv[o]);
         sdp[o] = d1;
       }
     } else {
@@ -775,7 +777,7 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
 #pragma unroll 4
       for (int m = N; m > p; --m) {
         const int o = m * 32 + tx;
-        f1 = (rhs(m) - (double)s_off[o] * f1) * s_inv[o];
+        f1 = fma(-s_q[o], f1, rhs(m) * s_inv[o]);
         sdp[o] = f1;
       }
     }
@@ -1087,7 +1089,7 @@ int Impl<float>::build_solve_maps() {
   make(&map->th_s, Xst.th, nv, false);
   make(&map->dsc, SL.dsc, nv, false);
   make(&map->dhm, T.dhm, nv, false);
-  make(&map->off, F.off, nv + 1, false);
+  make(&map->q, F.q, nv + 1, true);
   make(&map->inv, F.inv, nv + 1, true);
   make(&map->cf, F.cf, nv + 1, true);
   make(&map->junction, F.junction, 1, true);
