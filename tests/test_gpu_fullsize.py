@@ -1,6 +1,8 @@
-"""Properties that hold at any size, checked at the benchmark size (glevel 6
-x 32 levels, 40962 columns) in the launch configuration bench.py times
-(float32 mixed and float64, graph replay, default level chunk)."""
+"""The benchmark size (glevel 6 x 32 levels, 40962 columns): one float64
+large step against the oracle's, and properties that hold at any size,
+checked in the launch configuration bench.py times (float32 mixed with the
+TMA-staged column solve and the autotuned launch shape, float64, graph
+replay)."""
 
 import numpy as np
 import pytest
@@ -12,7 +14,8 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import paper_1607_05535_gb300 as thor
-from harness import init_struct, planet_struct
+from harness import Pair, field_errors, init_struct, planet_struct
+from oracle import dycore as dc
 import workloads as wls
 
 WL = wls.HS_G6
@@ -62,14 +65,34 @@ def test_rest_full_size(grid, precision, vmax):
         thor.thor_state_destroy(st)
 
 
+@pytest.mark.slow
+def test_fp64_large_step_matches_oracle_full_size():
+    """One large step (3 slow-term evaluations, 13 small steps, Held-Suarez
+    physics) of the float64 path at 40962 x 32 against the oracle's, every
+    field to 1e-10 relative; the oracle needs about a minute for it."""
+    wl = WL.with_(n_large=1)
+    p = Pair(wl, precision=thor.THOR_FP64)
+    try:
+        X = p.oracle_initial()
+        ref = dc.large_step(p.model, X, wl.dt, wl.n_small)
+        thor.thor_step(p.state, 1, wl.n_small, wl.dt)
+        e = field_errors(p.get(), ref)
+        assert max(e["rho"], e["Th"], e["M"], e["W"]) < 1e-10, e
+    finally:
+        p.close()
+
+
 def test_mixed_tracks_fp64_full_size(grid):
-    """Three large steps of the float32 path stay within the mixed-mode
+    """Three large steps of the float32 path, with the launch shape the
+    autotuner picks (as bench.py runs it), stay within the mixed-mode
     tolerances of the float64 path at full size."""
     s = torch.cuda.Stream()
     out = []
     for prec in (thor.THOR_FP64, thor.THOR_MIXED):
         st = _state(grid, WL, prec, s.cuda_stream)
         try:
+            if prec == thor.THOR_MIXED:
+                thor.thor_autotune(st, WL.n_small, WL.dt, steps=1)
             thor.thor_step(st, 3, WL.n_small, WL.dt)
             out.append({f: thor.thor_state_get(st, f, WL.ncol, WL.nv)
                         for f in (thor.THOR_FIELD_RHO, thor.THOR_FIELD_TEMPERATURE, thor.THOR_FIELD_MOM)})
