@@ -245,6 +245,7 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   for (R** p : cen) *p = cv.take<R>(C);
   T.vr = cv.take<R>(F);
   T.qvr = cv.take<R>(F);
+  T.psurf = cv.take<R>(S);
   Slow<R>& SL = I.SL;
   R** sc[] = {&SL.smx, &SL.smy, &SL.smz, &SL.srho, &SL.sth, &SL.dsc, &SL.acr, &SL.pi};
   for (R** p : sc) *p = cv.take<R>(C);

@@ -24,6 +24,7 @@ struct Work {
   R *gx, *gy, *gz;                 // its horizontal gradient
   R *ca, *cb, *cc;                 // per-cell parts of the column equations (a, b, c)
   R *dhm;                          // horizontal divergence of the new M*
+  R *psurf;                        // [colp] surface pressure (physics)
 };
 
 // Slow tendencies and small-step coefficients of a stage

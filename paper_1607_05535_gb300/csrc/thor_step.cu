@@ -320,6 +320,34 @@ __device__ __forceinline__ void d_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> 
 //   b_k = Th*_k + dtau (S_th,k - div_h(theta M*)_k)
 //   c_k = p*_k + Pi_k (b_k - Th*_k)        (p* advanced linearly in Th)
 template <typename R>
+struct FluxCell {
+  R dhm, a, b, c;
+};
+// the four values of cell i = o + column (o = level k's plane offset)
+template <typename R>
+__device__ __forceinline__ FluxCell<R> flux_cell(const W7x3<R>& wd, const Nbr7& nb, const VR<R>& U,
+                                                 const Slow<R>& SL, const Pert<R>& P, const Work<R>& T, R dtau,
+                                                 int k, int o, int i) {
+  R dh = 0, dht = 0;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    const int q = o + nb.n[j];
+    R f = wd.x[j] * ld(P.mx + (q)) + wd.y[j] * ld(P.my + (q)) + wd.z[j] * ld(P.mz + (q));
+    dh += f;
+    dht += ld(T.theta + (q)) * f;
+  }
+  const R inv_r = ld(U.inv_rc + (k));
+  const R thk = ld(P.th + (i));
+  const R bk = thk + dtau * (ld(SL.sth + (i)) - dht * inv_r);
+  FluxCell<R> r;
+  r.dhm = dh * inv_r;
+  r.a = ld(P.rho + (i)) + dtau * (ld(SL.srho + (i)) - dh * inv_r);
+  r.b = bk;
+  r.c = ld(P.p + (i)) + ld(SL.pi + (i)) * (bk - thk);
+  return r;
+}
+
+template <typename R>
 __device__ __forceinline__ void d_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
@@ -330,21 +358,11 @@ __device__ __forceinline__ void d_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R>
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
-    R dh = 0, dht = 0;
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-      const int q = o + nb.n[j];
-      R f = wd.x[j] * ld(P.mx + (q)) + wd.y[j] * ld(P.my + (q)) + wd.z[j] * ld(P.mz + (q));
-      dh += f;
-      dht += ld(T.theta + (q)) * f;
-    }
-    const R inv_r = ld(U.inv_rc + (k));
-    R thk = ld(P.th + (i));
-    R bk = thk + dtau * (ld(SL.sth + (i)) - dht * inv_r);
-    T.dhm[i] = dh * inv_r;
-    T.ca[i] = ld(P.rho + (i)) + dtau * (ld(SL.srho + (i)) - dh * inv_r);
-    T.cb[i] = bk;
-    T.cc[i] = ld(P.p + (i)) + ld(SL.pi + (i)) * (bk - thk);
+    const FluxCell<R> f = flux_cell(wd, nb, U, SL, P, T, dtau, k, o, i);
+    T.dhm[i] = f.dhm;
+    T.ca[i] = f.a;
+    T.cb[i] = f.b;
+    T.cc[i] = f.c;
   }
 }
 
@@ -563,18 +581,31 @@ __device__ __forceinline__ void d_stage_end(Geo<R> G, Xf<R> Xs, Pert<R> P, Xf<R>
 // (Eq. im_eq_t) with the Sec. 6.1 Held-Suarez or Sec. 6.2 hot-Jupiter
 // coefficients; sigma = p / p_s with p_s extrapolated hydrostatically at the
 // lowest layer's temperature.
+// p_s of every column before the physics update, from its lowest layer
+// (one thread per column; the update kernel then works on chunks of levels
+// and changes the lowest layer's rho theta)
 template <typename R>
-__device__ __forceinline__ void d_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, int forcing, double dt, double hj_dT, int bx, int by) {
+__device__ __forceinline__ void d_surface_p(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int bx) {
+  int c = bx * blockDim.x + threadIdx.x;
+  if (c >= G.ncol) return;
+  const R gamma = (R)ph.gamma, Rd = (R)ph.Rd;
+  R p0 = ld(U.pb + (0)) + eos_dev<R>(ld(U.pb + (0)), ld(U.thb + (0)), ld(X.th + (c)), gamma);
+  R T0 = p0 / ((ld(U.rhob + (0)) + ld(X.rho + (c))) * Rd);
+  T.psurf[c] = p0 * rexp<R>(R(ph.g) * ld(U.zc + (0)) / (Rd * T0));
+}
+
+template <typename R>
+__device__ __forceinline__ void d_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int forcing, double dt,
+                                          double hj_dT, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
   const R gamma = (R)ph.gamma, inv_gamma = R(1.0 / ph.gamma), Rd = (R)ph.Rd;
   R sl = ld(G.sinlat + (c)), cl = ld(G.coslat + (c)), clcl = ld(G.xdir + (c));
-  R p0 = ld(U.pb + (0)) + eos_dev<R>(ld(U.pb + (0)), ld(U.thb + (0)), ld(X.th + (c)), gamma);
-  R T0 = p0 / ((ld(U.rhob + (0)) + ld(X.rho + (c))) * Rd);
-  R ps = p0 * rexp<R>(R(ph.g) * ld(U.zc + (0)) / (Rd * T0));
+  const R ps = ld(T.psurf + (c));
   const R rdt = (R)dt;
-  for (int k = 0; k < G.nv; ++k) {
+  const int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
+  for (int k = k0; k < k1; ++k) {
     const int i = k * S + c;
     R rhop = ld(X.rho + (i));
     R rho = ld(U.rhob + (k)) + rhop;
@@ -675,8 +706,13 @@ __global__ void k_stage_end(Geo<R> G, Xf<R> Xs, Pert<R> P, Xf<R> Xo, int kchunk)
   d_stage_end<R>(G, Xs, P, Xo, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
-__global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, int forcing, double dt, double hj_dT) {
-  d_physics<R>(G, U, ph, X, forcing, dt, hj_dT, blockIdx.x, 0);
+__global__ void k_surface_p(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T) {
+  d_surface_p<R>(G, U, ph, X, T, blockIdx.x);
+}
+template <typename R>
+__global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int forcing, double dt, double hj_dT,
+                          int kchunk) {
+  d_physics<R>(G, U, ph, X, T, forcing, dt, hj_dT, kchunk, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------- staged column solve (float storage)
@@ -929,10 +965,16 @@ __global__ void ke_stage_end(const Member<R>* __restrict__ M, const int2* __rest
   d_stage_end<R>(a.G, Xs, a.P, s == 2 ? a.Xt : a.Xst, kchunk, e.y, blockIdx.y);
 }
 template <typename R>
-__global__ void ke_physics(const Member<R>* __restrict__ M, const int2* __restrict__ map) {
+__global__ void ke_surface_p(const Member<R>* __restrict__ M, const int2* __restrict__ map) {
   const int2 e = map[blockIdx.x];
   const Member<R>& a = M[e.x];
-  if (a.forcing) d_physics<R>(a.G, a.U, a.ph, a.Xt, a.forcing, a.dt, a.hj_dT, e.y, 0);
+  if (a.forcing) d_surface_p<R>(a.G, a.U, a.ph, a.Xt, a.T, e.y);
+}
+template <typename R>
+__global__ void ke_physics(const Member<R>* __restrict__ M, const int2* __restrict__ map, int kchunk) {
+  const int2 e = map[blockIdx.x];
+  const Member<R>& a = M[e.x];
+  if (a.forcing) d_physics<R>(a.G, a.U, a.ph, a.Xt, a.T, a.forcing, a.dt, a.hj_dT, kchunk, e.y, blockIdx.y);
 }
 #undef THOR_MEMBER
 
@@ -1010,11 +1052,11 @@ int Impl<R>::large_step(double dt, int n_small) {
       mark(THOR_K_SS_MOM, true);
       k_ss_mom<R><<<g2, bs, 0, stream>>>(G, U, SL, P, T, (R)dts[s], Kd, divdamp, kc);
       mark(THOR_K_SS_MOM, false);
+      const int want_div = divdamp && j + 1 < nsub[s];
       mark(THOR_K_SS_FLUX, true);
       k_ss_flux<R><<<g2, bs, 0, stream>>>(G, U, SL, P, T, (R)dts[s], kc);
       mark(THOR_K_SS_FLUX, false);
       mark(THOR_K_SS_COL, true);
-      const int want_div = divdamp && j + 1 < nsub[s];
       if (staged)
         launch_solve_tma(gsolve, s == 0, dts[s], want_div);
       else
@@ -1030,9 +1072,10 @@ int Impl<R>::large_step(double dt, int n_small) {
   }
   if (forcing != 0) {
     mark(THOR_K_PHYSICS, true);
-    k_physics<R><<<g1, bs, 0, stream>>>(G, U, ph, Xt, forcing, dt, hj_dT);
+    k_surface_p<R><<<g1, bs, 0, stream>>>(G, U, ph, Xt, T);
+    k_physics<R><<<g2, bs, 0, stream>>>(G, U, ph, Xt, T, forcing, dt, hj_dT, kc);
     mark(THOR_K_PHYSICS, false);
-    ++launches;
+    launches += 2;
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
@@ -1160,8 +1203,9 @@ int ensemble_large_step(const EnsPlan<R>& E, cudaStream_t stream, long long* lau
     ++n;
   }
   if (E.any_forcing) {
-    ke_physics<R><<<E.nblk, bs, 0, stream>>>(M, E.map);
-    ++n;
+    ke_surface_p<R><<<E.nblk, bs, 0, stream>>>(M, E.map);
+    ke_physics<R><<<dim3(E.nblk, yc), bs, 0, stream>>>(M, E.map, kc);
+    n += 2;
   }
   *launches += n;
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
