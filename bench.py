@@ -40,10 +40,15 @@ METRIC = "cell-substeps/s"
 # b, p', Th^(s), D^(s), div_h M*) and 3 float64 factor planes (pivot
 # reciprocal, c'/e', q: 6 words), and writes 5 (rho*, Th*, p*, W*, D); the
 # factorisation reads 2 planes and writes the 3 float64 ones.
+# The interface kernel also sets the stage's perturbations (reads X^t and
+# X^(s), 12 planes, and p'; writes the 7 perturbation planes), and the last
+# small step of a stage also ends it (momentum and column kernels read the
+# stage state's 3 planes each and write X^(s+1)'s); the counts below are
+# those of the other small steps.
 KERNEL_WORDS = {
-    "derived": 6 + 10, "lap1": 8 + 6, "slow": 17 + 8, "slow_w": 7 + 2, "stage_init": 13 + 7,
-    "ss_div": 5 + 1, "ss_grad": 1 + 3, "ss_mom": 10 + 3, "ss_flux": 10 + 4, "ss_solve": 10 + 6 + 5,
-    "ss_factor": 2 + 6, "stage_end": 12 + 6, "physics": 5 + 4,
+    "derived": 6 + 10, "lap1": 8 + 6, "slow": 17 + 8, "slow_w": 16 + 9,
+    "ss_grad": 1 + 3, "ss_mom": 10 + 3, "ss_flux": 10 + 4, "ss_solve": 10 + 6 + 5,
+    "ss_factor": 2 + 6, "physics": 5 + 4,
 }
 
 

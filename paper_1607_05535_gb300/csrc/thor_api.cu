@@ -240,7 +240,7 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   X(I.Xst);
   Work<R>& T = I.T;
   R** cen[] = {&T.pp, &T.Tp, &T.theta, &T.vx, &T.vy, &T.vz, &T.vhx, &T.vhy, &T.vhz,
-               &T.qrho, &T.qvx, &T.qvy, &T.qvz, &T.qT, &T.dd, &T.gx, &T.gy, &T.gz,
+               &T.qrho, &T.qvx, &T.qvy, &T.qvz, &T.qT, &T.dd, &T.dd0, &T.gx, &T.gy, &T.gz,
                &T.ca, &T.cb, &T.cc, &T.dhm};
   for (R** p : cen) *p = cv.take<R>(C);
   T.vr = cv.take<R>(F);

@@ -21,6 +21,7 @@ struct Work {
   R *qrho, *qvx, *qvy, *qvz, *qT;  // K_d lap(.) (times rho) for the hyperdiffusion
   R *qvr;                          // interfaces
   R *dd;                           // 3-D divergence (small step)
+  R *dd0;                          // 3-D divergence of X^t (first small step of every stage)
   R *gx, *gy, *gz;                 // its horizontal gradient
   R *ca, *cb, *cc;                 // per-cell parts of the column equations (a, b, c)
   R *dhm;                          // horizontal divergence of the new M*
@@ -168,7 +169,7 @@ struct Impl : ImplBase {
   int graph_n = 0, graph_kc = 0, graph_bs = 0, graph_tma = -1;
   std::unique_ptr<SolveMaps> smaps;   // null where the staged solve does not apply
   int build_solve_maps();
-  void launch_solve_tma(dim3 grid, int stage0, double dtau, int want_div);
+  cudaError_t launch_solve_tma(dim3 grid, int stage, double dtau, int want_div, int last);
   long long graph_launches = 0;
   void drop_graph() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);

@@ -13,7 +13,21 @@
 #include "../../include/thor.h"
 #include "thor_impl.cuh"
 
+#include <utility>
+
 namespace thor {
+
+// ---------------------------------------------------------------- launch helper
+
+template <typename... K, typename... A>
+cudaError_t launch_k(void (*kern)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
 
 // Each step of the method is a device function over one block of columns
 // (block indices passed in); the kernels below run it either for one state
@@ -103,10 +117,12 @@ __device__ __forceinline__ void d_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R 
 // S_M = -grad_h p - A_h - C_h + F_M, S_rho = -div(M) - div(W) + F_rho,
 // S_th = F_th - div(theta M) - div(theta W), plus Dsc = div(M) + div(W) of the
 // stage state (divergence damping), the radial advection+Coriolis and
-// Pi = gamma p / rho theta.
+// Pi = gamma p / rho theta. In the first stage (stage state = X^t) Dsc is also
+// kept in d0: it is the divergence D that the first small step of every
+// stage damps, since there M^(s) + M* = M^t and W^(s) + W* = W^t.
 template <typename R>
 __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
-                                            int kchunk, int bx, int by) {
+                                            R* d0, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -170,6 +186,7 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
     R dv = sqh * whi_w - sql * wlo_w;
     SL.srho[i] = -dh - dv + Frho;
     SL.dsc[i] = dh + dv;
+    if (d0) d0[i] = dh + dv;
 
     R dht = div7_scaled(wd, nb, T.theta + o, X.mx + o, X.my + o, X.mz + o) * inv_r;
     R thlo = 0, thhi = 0;
@@ -183,10 +200,12 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
 }
 
 // Slow tendency of the vertical momentum at the interior interfaces
-// (right-hand side of Eq. momr2) and theta at the interfaces.
+// (right-hand side of Eq. momr2) and theta at the interfaces; and, on the same
+// (column, level) grid, the perturbations at the start of the stage:
+// Phi* = Phi^t - Phi^(s), p* from the nonlinear Eq. theta_to_p.
 template <typename R>
-__device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
-                                            int kchunk, int bx, int by) {
+__device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Slow<R> SL,
+                                         Pert<R> P, int hyper, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -197,6 +216,18 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Wo
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int i = k * S + c;
+    // stage start
+    if (k < G.nv) {
+      P.rho[i] = ld(Xt.rho + (i)) - ld(X.rho + (i));
+      P.mx[i] = ld(Xt.mx + (i)) - ld(X.mx + (i));
+      P.my[i] = ld(Xt.my + (i)) - ld(X.my + (i));
+      P.mz[i] = ld(Xt.mz + (i)) - ld(X.mz + (i));
+      P.th[i] = ld(Xt.th + (i)) - ld(X.th + (i));
+      R ppt = eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), ld(Xt.th + (i)), (R)ph.gamma);
+      P.p[i] = ppt - ld(T.pp + (i));
+    }
+    P.w[i] = ld(Xt.w + (i)) - ld(X.w + (i));
+    // slow terms of Eq. momr2
     if (k == 0 || k == G.nv) {
       SL.sw[i] = 0;
       SL.thi[i] = 0;
@@ -213,53 +244,13 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Wo
   }
 }
 
-// Perturbations at the start of a stage: Phi* = Phi^t - Phi^(s); p* from the
-// nonlinear Eq. theta_to_p.
-template <typename R>
-__device__ __forceinline__ void d_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> Xs, Work<R> T, Pert<R> P,
-                                            int kchunk, int bx, int by) {
-  int c = bx * blockDim.x + threadIdx.x;
-  if (c >= G.ncol) return;
-  const int S = G.colp;
-  int k0 = by * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
-#pragma unroll 2
-  for (int k = k0; k < k1; ++k) {
-    int i = k * S + c;
-    if (k < G.nv) {
-      P.rho[i] = ld(Xt.rho + (i)) - ld(Xs.rho + (i));
-      P.mx[i] = ld(Xt.mx + (i)) - ld(Xs.mx + (i));
-      P.my[i] = ld(Xt.my + (i)) - ld(Xs.my + (i));
-      P.mz[i] = ld(Xt.mz + (i)) - ld(Xs.mz + (i));
-      P.th[i] = ld(Xt.th + (i)) - ld(Xs.th + (i));
-      R ppt = eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), ld(Xt.th + (i)), (R)ph.gamma);
-      P.p[i] = ppt - ld(T.pp + (i));
-    }
-    P.w[i] = ld(Xt.w + (i)) - ld(Xs.w + (i));
-  }
-}
-
 // ---------------------------------------------------------------- small step
 
-// 3-D divergence of the total momentum (divergence damping, Sec. 4)
 template <typename R>
-__device__ __forceinline__ void d_ss_div(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, int kchunk, int bx, int by) {
-  int c = bx * blockDim.x + threadIdx.x;
-  if (c >= G.ncol) return;
-  const int S = G.colp;
-  Nbr7 nb = load_nbr(G, c);
-  W7x3<R> wd = load_w7x3(G.wdiv, S, c);
-  int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
-#pragma unroll 2
-  for (int k = k0; k < k1; ++k) {
-    const int o = k * S, i = o + c;
-    R dh = div7(wd, nb, P.mx + o, P.my + o, P.mz + o) * ld(U.inv_rc + (k));
-    R dv = ld(U.sq_hi + (k)) * ld(P.w + (i + S)) - ld(U.sq_lo + (k)) * ld(P.w + (i));
-    T.dd[i] = ld(SL.dsc + (i)) + dh + dv;
-  }
-}
-
-template <typename R>
-__device__ __forceinline__ void d_ss_grad(Geo<R> G, VR<R> U, Work<R> T, int kchunk, int bx, int by) {
+// horizontal gradient G = grad_h D of the 3-D divergence D of the total
+// momentum (divergence damping, Sec. 4): D is d0 in the first small step of a
+// stage and, later, the D the previous column step formed
+__device__ __forceinline__ void d_ss_grad(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -270,7 +261,7 @@ __device__ __forceinline__ void d_ss_grad(Geo<R> G, VR<R> U, Work<R> T, int kchu
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
     R gx, gy, gz;
-    grad7(wg, nb, T.dd + o, gx, gy, gz);
+    grad7(wg, nb, dsrc + o, gx, gy, gz);
     R inv_r = ld(U.inv_rc + (k));
     T.gx[i] = gx * inv_r;
     T.gy[i] = gy * inv_r;
@@ -278,10 +269,13 @@ __device__ __forceinline__ void d_ss_grad(Geo<R> G, VR<R> U, Work<R> T, int kchu
   }
 }
 
-// Eq. mom2 with the divergence damping: M* <- proj(M* + dtau(-grad p* + DD + S_M))
+// Eq. mom2 with the divergence damping: M* <- proj(M* + dtau(-grad p* + DD + S_M));
+// in the last small step of a stage also M^(s+1) = M^(s) + M* into Xo (which
+// may be Xs itself: each cell reads its own Xs value before writing it)
 template <typename R>
 __device__ __forceinline__ void d_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, R Kd,
-                                            int divdamp, int kchunk, int bx, int by) {
+                                            int divdamp, Xf<R> Xs, Xf<R> Xo, int last, int kchunk, int bx,
+                                            int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -311,6 +305,11 @@ __device__ __forceinline__ void d_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> 
     P.mx[i] = mx;
     P.my[i] = my;
     P.mz[i] = mz;
+    if (last) {          // end of the stage: M^(s+1) = M^(s) + M*
+      Xo.mx[i] = ld(Xs.mx + (i)) + mx;
+      Xo.my[i] = ld(Xs.my + (i)) + my;
+      Xo.mz[i] = ld(Xs.mz + (i)) + mz;
+    }
   }
 }
 
@@ -443,6 +442,20 @@ __device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> 
   if (half == 0 && valid) F.junction[c] = p < N ? 1.0 / (1.0 - sj[0][tx] * sj[1][tx]) : 1.0;
 }
 
+// End of an RK stage for one cell of the column step: Phi^(s+1) = Phi^(s) +
+// Phi* for rho, rho theta and W (the momentum in k_ss_mom), into Xo, which may
+// be Xs itself (each cell reads its own Xs values before writing them). The
+// lid and surface interfaces keep W^(s) + W*, as the interior ones.
+template <typename R>
+__device__ __forceinline__ void stage_end_cell(const Xf<R>& Xs, const Xf<R>& Xo, const Pert<R>& P, R rho_new,
+                                               R th_new, R w_new, int k, int i, int S, int nv) {
+  Xo.rho[i] = ld(Xs.rho + i) + rho_new;
+  Xo.th[i] = ld(Xs.th + i) + th_new;
+  if (k >= 1) Xo.w[i] = ld(Xs.w + i) + w_new;
+  if (k == 0) Xo.w[i] = ld(Xs.w + i) + ld(P.w + i);
+  if (k == nv - 1) Xo.w[i + S] = ld(Xs.w + (i + S)) + ld(P.w + (i + S));
+}
+
 // HE-VI column step, part 3 (every small step). The right-hand side
 //   rh_m = W*_m + dtau S_W,m - dtau/dzc_m (c_m - c_m-1) - dtau g (w- a_m-1 + w+ a_m)
 // goes through the stored factors in float64 (d'_m = rh_m / piv_m - q_m d'_m-1
@@ -455,7 +468,7 @@ __device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> 
 template <typename R>
 __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs, Slow<R> SL,
                                             Pert<R> P, Work<R> T, Fac<R> F, double dtau,
-                                            int want_div, int bx, int by) {
+                                            int want_div, Xf<R> Xo, int last, int bx, int by) {
   extern __shared__ double sm[];
   const int nv = G.nv, S = G.colp, N = nv - 1;
   const int tx = threadIdx.x & 31, half = threadIdx.x >> 5;
@@ -540,7 +553,8 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
       const R thh = k + 1 < nv ? ld(SL.thi + (i + S)) : R(0);
       const R el = ld(U.sq_lo + k), eh = ld(U.sq_hi + k);
       R th_new = ld(T.cb + i) - rdt * (eh * thh * wh - el * thl * wl);
-      P.rho[i] = ld(T.ca + i) - rdt * (eh * wh - el * wl);
+      const R rho_new = ld(T.ca + i) - rdt * (eh * wh - el * wl);
+      P.rho[i] = rho_new;
       P.th[i] = th_new;
       // p* = EOS(Th^(s) + Th*) - p^(s) = p^(s) ((1 + Th*/Th^(s))^gamma - 1)
       R ps = ld(U.pb + k) + ld(T.pp + i);
@@ -550,28 +564,8 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
       // 3-D divergence of the new total momentum, for the next small step's
       // divergence damping: D^(s) + div_h M* (from k_ss_flux) + div_v W*
       if (want_div) T.dd[i] = ld(SL.dsc + i) + ld(T.dhm + i) + (eh * wh - el * wl);
+      if (last) stage_end_cell(Xs, Xo, P, rho_new, th_new, wl, k, i, S, nv);
     }
-  }
-}
-
-// Phi^(s+1) = Phi^(s) + Phi*
-template <typename R>
-__device__ __forceinline__ void d_stage_end(Geo<R> G, Xf<R> Xs, Pert<R> P, Xf<R> Xo, int kchunk, int bx, int by) {
-  int c = bx * blockDim.x + threadIdx.x;
-  if (c >= G.ncol) return;
-  const int S = G.colp;
-  int k0 = by * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
-#pragma unroll 2
-  for (int k = k0; k < k1; ++k) {
-    int i = k * S + c;
-    if (k < G.nv) {
-      Xo.rho[i] = ld(Xs.rho + (i)) + ld(P.rho + (i));
-      Xo.mx[i] = ld(Xs.mx + (i)) + ld(P.mx + (i));
-      Xo.my[i] = ld(Xs.my + (i)) + ld(P.my + (i));
-      Xo.mz[i] = ld(Xs.mz + (i)) + ld(P.mz + (i));
-      Xo.th[i] = ld(Xs.th + (i)) + ld(P.th + (i));
-    }
-    Xo.w[i] = ld(Xs.w + (i)) + ld(P.w + (i));
   }
 }
 
@@ -664,29 +658,22 @@ __global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk) 
 }
 template <typename R>
 __global__ void __launch_bounds__(kMaxBlock, 2)
-    k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper, int kchunk) {
-  d_slow<R>(G, U, ph, X, T, SL, hyper, kchunk, blockIdx.x, blockIdx.y);
+    k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper, R* d0, int kchunk) {
+  d_slow<R>(G, U, ph, X, T, SL, hyper, d0, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
-__global__ void k_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper, int kchunk) {
-  d_slow_w<R>(G, U, ph, X, T, SL, hyper, kchunk, blockIdx.x, blockIdx.y);
+__global__ void k_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Slow<R> SL, Pert<R> P, int hyper,
+                         int kchunk) {
+  d_slow_w<R>(G, U, ph, Xt, X, T, SL, P, hyper, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
-__global__ void k_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> Xs, Work<R> T, Pert<R> P, int kchunk) {
-  d_stage_init<R>(G, U, ph, Xt, Xs, T, P, kchunk, blockIdx.x, blockIdx.y);
-}
-template <typename R>
-__global__ void k_ss_div(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, int kchunk) {
-  d_ss_div<R>(G, U, SL, P, T, kchunk, blockIdx.x, blockIdx.y);
-}
-template <typename R>
-__global__ void k_ss_grad(Geo<R> G, VR<R> U, Work<R> T, int kchunk) {
-  d_ss_grad<R>(G, U, T, kchunk, blockIdx.x, blockIdx.y);
+__global__ void k_ss_grad(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, int kchunk) {
+  d_ss_grad<R>(G, U, T, dsrc, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
 __global__ void k_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, R Kd, int divdamp,
-                         int kchunk) {
-  d_ss_mom<R>(G, U, SL, P, T, dtau, Kd, divdamp, kchunk, blockIdx.x, blockIdx.y);
+                         Xf<R> Xs, Xf<R> Xo, int last, int kchunk) {
+  d_ss_mom<R>(G, U, SL, P, T, dtau, Kd, divdamp, Xs, Xo, last, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
 __global__ void k_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, int kchunk) {
@@ -698,12 +685,9 @@ __global__ void __launch_bounds__(64) k_ss_factor(Geo<R> G, VR<R> U, Phys ph, Sl
 }
 template <typename R>
 __global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs, Slow<R> SL, Pert<R> P,
-                                                 Work<R> T, Fac<R> F, double dtau, int want_div) {
-  d_ss_solve<R>(G, U, ph, Xs, SL, P, T, F, dtau, want_div, blockIdx.x, 0);
-}
-template <typename R>
-__global__ void k_stage_end(Geo<R> G, Xf<R> Xs, Pert<R> P, Xf<R> Xo, int kchunk) {
-  d_stage_end<R>(G, Xs, P, Xo, kchunk, blockIdx.x, blockIdx.y);
+                                                 Work<R> T, Fac<R> F, double dtau, int want_div, Xf<R> Xo,
+                                                 int last) {
+  d_ss_solve<R>(G, U, ph, Xs, SL, P, T, F, dtau, want_div, Xo, last, blockIdx.x, 0);
 }
 template <typename R>
 __global__ void k_surface_p(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T) {
@@ -739,7 +723,8 @@ size_t solve_tma_smem_bytes(int nv) {
 __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<float>& U, const Phys& ph,
                                                const SolveMaps& M, int stage0, const Xf<float>& Xs,
                                                const Slow<float>& SL, const Pert<float>& P, const Work<float>& T,
-                                               double dtau, int want_div, int* err, int bx) {
+                                               double dtau, int want_div, const Xf<float>& Xo, int last, int* err,
+                                               int bx) {
   extern __shared__ unsigned char smraw[];
   const int nv = G.nv, S = G.colp, N = nv - 1;
   const int tid = threadIdx.x, tx = tid & 31, warp = tid >> 5;
@@ -862,13 +847,15 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
       const float thh = k + 1 < nv ? ld(SL.thi + (i + S)) : 0.f;
       const float el = ld(U.sq_lo + k), eh = ld(U.sq_hi + k);
       float th_new = ld(T.cb + i) - rdt * (eh * thh * wh - el * thl * wl);
-      P.rho[i] = s_ca[o] - rdt * (eh * wh - el * wl);
+      const float rho_new = s_ca[o] - rdt * (eh * wh - el * wl);
+      P.rho[i] = rho_new;
       P.th[i] = th_new;
       float ps = ld(U.pb + k) + ld(T.pp + i);
       float ths = ld(U.thb + k) + ld(Xs.th + i);
       P.p[i] = ps * rexpm1<float>(gamma * rlog1p<float>(th_new / ths));
       if (k >= 1) P.w[i] = wl;
       if (want_div) T.dd[i] = ld(SL.dsc + i) + ld(T.dhm + i) + (eh * wh - el * wl);
+      if (last) stage_end_cell(Xs, Xo, P, rho_new, th_new, wl, k, i, S, nv);
     }
   }
 }
@@ -876,8 +863,8 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
 __global__ void __launch_bounds__(32 * kSolveWarps)
     k_ss_solve_tma(Geo<float> G, VR<float> U, Phys ph, const __grid_constant__ SolveMaps M, int stage0,
                    Xf<float> Xs, Slow<float> SL, Pert<float> P, Work<float> T, double dtau, int want_div,
-                   int* err) {
-  d_ss_solve_tma(G, U, ph, M, stage0, Xs, SL, P, T, dtau, want_div, err, blockIdx.x);
+                   Xf<float> Xo, int last, int* err) {
+  d_ss_solve_tma(G, U, ph, M, stage0, Xs, SL, P, T, dtau, want_div, Xo, last, err, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- kernels: ensemble
@@ -906,17 +893,13 @@ template <typename R>
 __global__ void __launch_bounds__(kMaxBlock, 2)
     ke_slow(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
   THOR_MEMBER();
-  d_slow<R>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, kchunk, e.y, blockIdx.y);
+  d_slow<R>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, s == 0 && a.divdamp ? a.T.dd0 : nullptr, kchunk, e.y,
+            blockIdx.y);
 }
 template <typename R>
 __global__ void ke_slow_w(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
   THOR_MEMBER();
-  d_slow_w<R>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, kchunk, e.y, blockIdx.y);
-}
-template <typename R>
-__global__ void ke_stage_init(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
-  THOR_MEMBER();
-  d_stage_init<R>(a.G, a.U, a.ph, a.Xt, Xs, a.T, a.P, kchunk, e.y, blockIdx.y);
+  d_slow_w<R>(a.G, a.U, a.ph, a.Xt, Xs, a.T, a.SL, a.P, a.hyper, kchunk, e.y, blockIdx.y);
 }
 template <typename R>
 __global__ void __launch_bounds__(64)
@@ -925,19 +908,17 @@ __global__ void __launch_bounds__(64)
   d_ss_factor<R>(a.G, a.U, a.ph, a.SL, a.F, a.dts[s], e.y, 0);
 }
 template <typename R>
-__global__ void ke_ss_div(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
+__global__ void ke_ss_grad(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int j,
+                           int kchunk) {
   THOR_MEMBER();
-  if (a.divdamp) d_ss_div<R>(a.G, a.U, a.SL, a.P, a.T, kchunk, e.y, blockIdx.y);
+  if (a.divdamp) d_ss_grad<R>(a.G, a.U, a.T, j == 0 ? a.T.dd0 : a.T.dd, kchunk, e.y, blockIdx.y);
 }
 template <typename R>
-__global__ void ke_ss_grad(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
+__global__ void ke_ss_mom(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int j,
+                          int kchunk) {
   THOR_MEMBER();
-  if (a.divdamp) d_ss_grad<R>(a.G, a.U, a.T, kchunk, e.y, blockIdx.y);
-}
-template <typename R>
-__global__ void ke_ss_mom(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
-  THOR_MEMBER();
-  d_ss_mom<R>(a.G, a.U, a.SL, a.P, a.T, (R)a.dts[s], a.Kd, a.divdamp, kchunk, e.y, blockIdx.y);
+  d_ss_mom<R>(a.G, a.U, a.SL, a.P, a.T, (R)a.dts[s], a.Kd, a.divdamp, Xs, s == 2 ? a.Xt : a.Xst,
+              j + 1 == a.nsub[s], kchunk, e.y, blockIdx.y);
 }
 template <typename R>
 __global__ void ke_ss_flux(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
@@ -949,7 +930,8 @@ __global__ void __launch_bounds__(64)
     ke_ss_solve(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int j) {
   THOR_MEMBER();
   const int want_div = a.divdamp && j + 1 < a.nsub[s];
-  d_ss_solve<R>(a.G, a.U, a.ph, Xs, a.SL, a.P, a.T, a.F, a.dts[s], want_div, e.y, 0);
+  d_ss_solve<R>(a.G, a.U, a.ph, Xs, a.SL, a.P, a.T, a.F, a.dts[s], want_div, s == 2 ? a.Xt : a.Xst,
+                j + 1 == a.nsub[s], e.y, 0);
 }
 __global__ void __launch_bounds__(32 * kSolveWarps)
     ke_ss_solve_tma(const Member<float>* __restrict__ M, const int2* __restrict__ map, int s, int j) {
@@ -957,12 +939,8 @@ __global__ void __launch_bounds__(32 * kSolveWarps)
   const Member<float>& a = M[e.x];
   const Xf<float> Xs = s == 0 ? a.Xt : a.Xst;
   const int want_div = a.divdamp && j + 1 < a.nsub[s];
-  d_ss_solve_tma(a.G, a.U, a.ph, *a.smap, s == 0, Xs, a.SL, a.P, a.T, a.dts[s], want_div, a.err, e.y);
-}
-template <typename R>
-__global__ void ke_stage_end(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
-  THOR_MEMBER();
-  d_stage_end<R>(a.G, Xs, a.P, s == 2 ? a.Xt : a.Xst, kchunk, e.y, blockIdx.y);
+  d_ss_solve_tma(a.G, a.U, a.ph, *a.smap, s == 0, Xs, a.SL, a.P, a.T, a.dts[s], want_div, s == 2 ? a.Xt : a.Xst,
+                 j + 1 == a.nsub[s], a.err, e.y);
 }
 template <typename R>
 __global__ void ke_surface_p(const Member<R>* __restrict__ M, const int2* __restrict__ map) {
@@ -1011,82 +989,79 @@ int Impl<R>::large_step(double dt, int n_small) {
   const R Kd = (R)(diff_D * dbar4 / dt);
   const double dts[3] = {dt / 3.0, dt / n_small, dt / n_small};
   const int nsub[3] = {1, n_small / 2, n_small};
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
   for (int s = 0; s < 3; ++s) {
-    Xf<R> Xs = s == 0 ? Xt : Xst;
+    Xf<R> Xs = s == 0 ? Xt : Xst, Xo = s == 2 ? Xt : Xst;
     mark(THOR_K_DERIVED, true);
-    k_derived<R><<<g2i, bs, 0, stream>>>(G, U, ph, Xs, T, kc);
+    chk(launch_k(k_derived<R>, g2i, bs, 0, stream, G, U, ph, Xs, T, kc));
     mark(THOR_K_DERIVED, false);
     ++launches;
     if (hyper) {
       mark(THOR_K_LAP1, true);
-      k_lap1<R><<<g2i, bs, 0, stream>>>(G, U, Xs, T, Kd, kc);
+      chk(launch_k(k_lap1<R>, g2i, bs, 0, stream, G, U, Xs, T, Kd, kc));
       mark(THOR_K_LAP1, false);
       ++launches;
     }
     mark(THOR_K_SLOW, true);
-    k_slow<R><<<g2, bs, 0, stream>>>(G, U, ph, Xs, T, SL, hyper, kc);
+    chk(launch_k(k_slow<R>, g2, bs, 0, stream, G, U, ph, Xs, T, SL, hyper,
+                 s == 0 && divdamp ? T.dd0 : (R*)nullptr, kc));
     mark(THOR_K_SLOW, false);
     mark(THOR_K_SLOW_W, true);
-    k_slow_w<R><<<g2i, bs, 0, stream>>>(G, U, ph, Xs, T, SL, hyper, kc);
+    chk(launch_k(k_slow_w<R>, g2i, bs, 0, stream, G, U, ph, Xt, Xs, T, SL, P, hyper, kc));
     mark(THOR_K_SLOW_W, false);
-    mark(THOR_K_STAGE_INIT, true);
-    k_stage_init<R><<<g2i, bs, 0, stream>>>(G, U, ph, Xt, Xs, T, P, kc);
-    mark(THOR_K_STAGE_INIT, false);
     mark(THOR_K_SS_FACTOR, true);
-    k_ss_factor<R><<<gsolve, 64, 0, stream>>>(G, U, ph, SL, F, dts[s]);
+    chk(launch_k(k_ss_factor<R>, gsolve, 64, 0, stream, G, U, ph, SL, F, dts[s]));
     mark(THOR_K_SS_FACTOR, false);
-    launches += 4;
+    launches += 3;
     for (int j = 0; j < nsub[s]; ++j) {
-      if (divdamp) {
-        if (j == 0) {   // later small steps get D from the previous k_ss_solve
-          mark(THOR_K_SS_DIV, true);
-          k_ss_div<R><<<g2, bs, 0, stream>>>(G, U, SL, P, T, kc);
-          mark(THOR_K_SS_DIV, false);
-          ++launches;
-        }
+      if (divdamp) {   // D: of X^t in the first small step, then from the previous column step
         mark(THOR_K_SS_GRAD, true);
-        k_ss_grad<R><<<g2, bs, 0, stream>>>(G, U, T, kc);
+        chk(launch_k(k_ss_grad<R>, g2, bs, 0, stream, G, U, T, (const R*)(j == 0 ? T.dd0 : T.dd), kc));
         mark(THOR_K_SS_GRAD, false);
         ++launches;
       }
+      // the last small step of a stage also ends the stage: X^(s+1) = X^(s) + X*
+      const int last = j + 1 == nsub[s];
       mark(THOR_K_SS_MOM, true);
-      k_ss_mom<R><<<g2, bs, 0, stream>>>(G, U, SL, P, T, (R)dts[s], Kd, divdamp, kc);
+      chk(launch_k(k_ss_mom<R>, g2, bs, 0, stream, G, U, SL, P, T, (R)dts[s], Kd, divdamp, Xs, Xo, last, kc));
       mark(THOR_K_SS_MOM, false);
-      const int want_div = divdamp && j + 1 < nsub[s];
+      const int want_div = divdamp && !last;
       mark(THOR_K_SS_FLUX, true);
-      k_ss_flux<R><<<g2, bs, 0, stream>>>(G, U, SL, P, T, (R)dts[s], kc);
+      chk(launch_k(k_ss_flux<R>, g2, bs, 0, stream, G, U, SL, P, T, (R)dts[s], kc));
       mark(THOR_K_SS_FLUX, false);
       mark(THOR_K_SS_COL, true);
       if (staged)
-        launch_solve_tma(gsolve, s == 0, dts[s], want_div);
+        chk(launch_solve_tma(gsolve, s, dts[s], want_div, last));
       else
-        k_ss_solve<R><<<gsolve, 64, solve_smem, stream>>>(G, U, ph, Xs, SL, P, T, F, dts[s], want_div);
+        chk(launch_k(k_ss_solve<R>, gsolve, 64, solve_smem, stream, G, U, ph, Xs, SL, P, T, F, dts[s],
+                     want_div, Xo, last));
       mark(THOR_K_SS_COL, false);
       launches += 3;
     }
-    Xf<R> Xo = s == 2 ? Xt : Xst;
-    mark(THOR_K_STAGE_END, true);
-    k_stage_end<R><<<g2i, bs, 0, stream>>>(G, Xs, P, Xo, kc);
-    mark(THOR_K_STAGE_END, false);
-    ++launches;
   }
   if (forcing != 0) {
     mark(THOR_K_PHYSICS, true);
-    k_surface_p<R><<<g1, bs, 0, stream>>>(G, U, ph, Xt, T);
-    k_physics<R><<<g2, bs, 0, stream>>>(G, U, ph, Xt, T, forcing, dt, hj_dT, kc);
+    chk(launch_k(k_surface_p<R>, g1, bs, 0, stream, G, U, ph, Xt, T));
+    chk(launch_k(k_physics<R>, g2, bs, 0, stream, G, U, ph, Xt, T, forcing, dt, hj_dT, kc));
     mark(THOR_K_PHYSICS, false);
     launches += 2;
   }
-  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+  return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 template <>
-void Impl<float>::launch_solve_tma(dim3 grid, int stage0, double dtau, int want_div) {
-  k_ss_solve_tma<<<grid, 32 * kSolveWarps, solve_tma_smem_bytes(G.nv), stream>>>(
-      G, U, ph, *smaps, stage0, stage0 ? Xt : Xst, SL, P, T, dtau, want_div, dev_err);
+cudaError_t Impl<float>::launch_solve_tma(dim3 grid, int stage, double dtau, int want_div, int last) {
+  return launch_k(k_ss_solve_tma, grid, 32 * kSolveWarps, solve_tma_smem_bytes(G.nv), stream, G, U, ph,
+                  *smaps, (int)(stage == 0), stage == 0 ? Xt : Xst, SL, P, T, dtau, want_div,
+                  stage == 2 ? Xt : Xst, last, dev_err);
 }
 template <>
-void Impl<double>::launch_solve_tma(dim3, int, double, int) {}
+cudaError_t Impl<double>::launch_solve_tma(dim3, int, double, int, int) {
+  return cudaErrorInvalidValue;
+}
 
 // TMA descriptors of the staged solve (float storage only; the float64
 // planes would not fit the shared memory of a useful number of blocks)
@@ -1173,21 +1148,16 @@ int ensemble_large_step(const EnsPlan<R>& E, cudaStream_t stream, long long* lau
     }
     ke_slow<R><<<g2, bs, 0, stream>>>(M, E.map, s, kc);
     ke_slow_w<R><<<g2i, bs, 0, stream>>>(M, E.map, s, kc);
-    ke_stage_init<R><<<g2i, bs, 0, stream>>>(M, E.map, s, kc);
     ke_ss_factor<R><<<E.nblkc, 64, 0, stream>>>(M, E.mapc, s);
-    n += 5;
+    n += 4;
     for (int j = 0; j < E.maxsub[s]; ++j) {
       const int nb = E.active[s][j], nbc = E.activec[s][j];
       const dim3 a2(nb, yc);
       if (E.any_divdamp) {
-        if (j == 0) {
-          ke_ss_div<R><<<a2, bs, 0, stream>>>(M, E.map, s, kc);
-          ++n;
-        }
-        ke_ss_grad<R><<<a2, bs, 0, stream>>>(M, E.map, s, kc);
+        ke_ss_grad<R><<<a2, bs, 0, stream>>>(M, E.map, s, j, kc);
         ++n;
       }
-      ke_ss_mom<R><<<a2, bs, 0, stream>>>(M, E.map, s, kc);
+      ke_ss_mom<R><<<a2, bs, 0, stream>>>(M, E.map, s, j, kc);
       ke_ss_flux<R><<<a2, bs, 0, stream>>>(M, E.map, s, kc);
       if constexpr (sizeof(R) == sizeof(float)) {
         if (E.staged)
@@ -1199,8 +1169,6 @@ int ensemble_large_step(const EnsPlan<R>& E, cudaStream_t stream, long long* lau
       }
       n += 3;
     }
-    ke_stage_end<R><<<g2i, bs, 0, stream>>>(M, E.map, s, kc);
-    ++n;
   }
   if (E.any_forcing) {
     ke_surface_p<R><<<E.nblk, bs, 0, stream>>>(M, E.map);

@@ -127,7 +127,7 @@ def test_closure_window_semantics():
 def test_closure_gain_over_plain_coarse_method():
     """A priori: the n-step residual tendency predicted on held-out windows.
     A posteriori: four windows of coarse large steps with the closure (after
-    two rounds of dataset aggregation) against the coarse-grained fine run,
+    three rounds of dataset aggregation) against the coarse-grained fine run,
     compared with the plain coarse method, from two held-out starts."""
     wl = wls.HS_G6
     dev = "cuda"
@@ -154,7 +154,7 @@ def test_closure_gain_over_plain_coarse_method():
               "tendency_mse_closure": err_closure, "tendency_mse_plain": err_plain, "a_priori_gain": gain}
     del Xtr, Ytr, Xte, Yte, P
 
-    net, norm, hists = cl.fit(su, wl, torch, dev, windows=24, window=window, rounds=2)
+    net, norm, hists = cl.fit(su, wl, torch, dev, windows=24, window=window, rounds=3)
     try:
         runs = []
         for _ in range(2):
