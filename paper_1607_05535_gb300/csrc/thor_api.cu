@@ -527,6 +527,16 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
   I->ph.g = pl.gravity;
   I->ph.omega = pl.omega;
   I->ph.p_ref = pl.p_ref;
+  I->ph.inv_Rd = 1.0 / I->ph.Rd;
+  I->ph.inv_gamma = 1.0 / I->ph.gamma;
+  I->ph.two_omega = 2.0 * I->ph.omega;
+  I->ph.Rd_f = (float)I->ph.Rd;
+  I->ph.inv_Rd_f = (float)I->ph.inv_Rd;
+  I->ph.gamma_f = (float)I->ph.gamma;
+  I->ph.inv_gamma_f = (float)I->ph.inv_gamma;
+  I->ph.kappa_f = (float)I->ph.kappa;
+  I->ph.g_f = (float)I->ph.g;
+  I->ph.two_omega_f = (float)I->ph.two_omega;
   I->hyper = in.hyperdiffusion ? 1 : 0;
   I->divdamp = in.divergence_damping ? 1 : 0;
   I->forcing = in.forcing;

@@ -76,7 +76,15 @@ struct Geo {
 
 struct Phys {
   double Rd, cp, cv, gamma, kappa, g, omega, p_ref;
+  double inv_Rd, inv_gamma, two_omega;
+  // float copies for the float kernels (a float64 conversion per thread costs
+  // an issue slot of the GB300's narrow float64 pipe)
+  float Rd_f, inv_Rd_f, gamma_f, inv_gamma_f, kappa_f, g_f, two_omega_f;
 };
+// the constant in the kernel's storage type
+template <typename R> __device__ __forceinline__ R pc(double d, float f);
+template <> __device__ __forceinline__ double pc<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pc<float>(double, float f) { return f; }
 
 // Float64 factors of the per-stage vertical matrix: planes [nv + 1][colp]
 // (rows 1..nv-1 used) and one plane for the junction of the two sweeps. Per

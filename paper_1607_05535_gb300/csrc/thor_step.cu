@@ -44,7 +44,7 @@ __device__ __forceinline__ void d_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, W
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
-  const R gamma = (R)ph.gamma, inv_Rd = R(1.0 / ph.Rd);
+  const R gamma = pc<R>(ph.gamma, ph.gamma_f), inv_Rd = pc<R>(ph.inv_Rd, ph.inv_Rd_f);
   R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
   int k0 = by * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
 #pragma unroll 2
@@ -131,9 +131,11 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
   W7x3<R> wg = load_w7x3(G.wgrad, S, c);
   W7<R> wl = load_w7(G.wlap, S, c);
   R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
-  const R two_om = R(2.0 * ph.omega), gamma = (R)ph.gamma, Rd = (R)ph.Rd;
+  const R two_om = pc<R>(ph.two_omega, ph.two_omega_f), gamma = pc<R>(ph.gamma, ph.gamma_f),
+          Rd = pc<R>(ph.Rd, ph.Rd_f);
   int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
-#pragma unroll 2
+  constexpr int kUnroll = sizeof(R) == sizeof(float) ? 2 : 1;   // float64: registers
+#pragma unroll kUnroll
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
     const R inv_r = ld(U.inv_rc + (k)), inv_r2 = ld(U.inv_rc2 + (k));
@@ -141,25 +143,54 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
     R thfull = ld(U.thb + (k)) + ld(X.th + (i));
     R p = ld(U.pb + (k)) + ld(T.pp + (i));
 
+    // one pass over the 7-point neighbourhood, each neighbour value loaded
+    // once: the edge flux f = w . M of the momentum (shared by the continuity,
+    // advection and rho-theta divergences), the pressure gradient and the
+    // second Laplacians of the hyperdiffusion
+    R sa0 = 0, sa1 = 0, sa2 = 0, sdh = 0, sdt = 0, gx = 0, gy = 0, gz = 0;
+    R hr = 0, hx = 0, hy = 0, hz = 0, hT = 0;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const int q = o + nb.n[j];
+      const R f = wd.x[j] * ld(X.mx + q) + wd.y[j] * ld(X.my + q) + wd.z[j] * ld(X.mz + q);
+      sa0 += ld(T.vx + q) * f;
+      sa1 += ld(T.vy + q) * f;
+      sa2 += ld(T.vz + q) * f;
+      sdh += f;
+      sdt += ld(T.theta + q) * f;
+      const R pq = ld(T.pp + q);
+      gx += wg.x[j] * pq;
+      gy += wg.y[j] * pq;
+      gz += wg.z[j] * pq;
+      if (hyper) {
+        hr += wl.v[j] * ld(T.qrho + q);
+        hx += wl.v[j] * ld(T.qvx + q);
+        hy += wl.v[j] * ld(T.qvy + q);
+        hz += wl.v[j] * ld(T.qvz + q);
+        hT += wl.v[j] * ld(T.qT + q);
+      }
+    }
+
     // hyperdiffusion (Sec. 4)
     R Frho = 0, FMx = 0, FMy = 0, FMz = 0, Fth = 0;
     if (hyper) {
-      Frho = -apply7(wl, nb, T.qrho + o) * inv_r2;
-      FMx = -apply7(wl, nb, T.qvx + o) * inv_r2;
-      FMy = -apply7(wl, nb, T.qvy + o) * inv_r2;
-      FMz = -apply7(wl, nb, T.qvz + o) * inv_r2;
+      Frho = -hr * inv_r2;
+      FMx = -hx * inv_r2;
+      FMy = -hy * inv_r2;
+      FMz = -hz * inv_r2;
       project(rx, ry, rz, FMx, FMy, FMz);
-      R Fp = -Rd * apply7(wl, nb, T.qT + o) * inv_r2;
+      R Fp = -Rd * hT * inv_r2;
       Fth = thfull / (gamma * p) * Fp;
     }
 
     // advection div(rho v v_j) of the Cartesian components (Sec. 3)
     const R* vs[3] = {T.vx, T.vy, T.vz};
+    const R sa[3] = {sa0, sa1, sa2};
     R A[3];
     R wlo_w = ld(X.w + (i)), whi_w = ld(X.w + (i + S));
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      R ah = div7_scaled(wd, nb, vs[j] + o, X.mx + o, X.my + o, X.mz + o) * inv_r;
+      R ah = sa[j] * inv_r;
       R vlo = 0, vhi = 0;
       if (k >= 1) vlo = ld(U.wlo + (k)) * vs[j][i - S] + ld(U.whi + (k)) * vs[j][i];
       if (k + 1 < G.nv) vhi = ld(U.wlo + (k + 1)) * vs[j][i] + ld(U.whi + (k + 1)) * vs[j][i + S];
@@ -174,21 +205,19 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
     R acr = A[0] * rx + A[1] * ry + A[2] * rz;
     R ahx = A[0] - acr * rx, ahy = A[1] - acr * ry, ahz = A[2] - acr * rz;
 
-    R gx, gy, gz;
-    grad7(wg, nb, T.pp + o, gx, gy, gz);
     R smx = -gx * inv_r - ahx + FMx, smy = -gy * inv_r - ahy + FMy, smz = -gz * inv_r - ahz + FMz;
     project(rx, ry, rz, smx, smy, smz);
     SL.smx[i] = smx;
     SL.smy[i] = smy;
     SL.smz[i] = smz;
 
-    R dh = div7(wd, nb, X.mx + o, X.my + o, X.mz + o) * inv_r;
+    R dh = sdh * inv_r;
     R dv = sqh * whi_w - sql * wlo_w;
     SL.srho[i] = -dh - dv + Frho;
     SL.dsc[i] = dh + dv;
     if (d0) d0[i] = dh + dv;
 
-    R dht = div7_scaled(wd, nb, T.theta + o, X.mx + o, X.my + o, X.mz + o) * inv_r;
+    R dht = sdt * inv_r;
     R thlo = 0, thhi = 0;
     if (k >= 1) thlo = ld(U.wlo + (k)) * ld(T.theta + (i - S)) + ld(U.whi + (k)) * ld(T.theta + (i));
     if (k + 1 < G.nv) thhi = ld(U.wlo + (k + 1)) * ld(T.theta + (i)) + ld(U.whi + (k + 1)) * ld(T.theta + (i + S));
@@ -211,7 +240,7 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
   W7<R> wl = load_w7(G.wlap, S, c);
-  const R g = (R)ph.g;
+  const R g = pc<R>(ph.g, ph.g_f), gamma = pc<R>(ph.gamma, ph.gamma_f);
   int k0 = by * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
@@ -223,7 +252,7 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
       P.my[i] = ld(Xt.my + (i)) - ld(X.my + (i));
       P.mz[i] = ld(Xt.mz + (i)) - ld(X.mz + (i));
       P.th[i] = ld(Xt.th + (i)) - ld(X.th + (i));
-      R ppt = eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), ld(Xt.th + (i)), (R)ph.gamma);
+      R ppt = eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), ld(Xt.th + (i)), gamma);
       P.p[i] = ppt - ld(T.pp + (i));
     }
     P.w[i] = ld(Xt.w + (i)) - ld(X.w + (i));
@@ -394,7 +423,7 @@ __device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> 
   const bool valid = c < G.ncol;
   const int cs = valid ? c : 0;          // padding lanes compute on column 0 and store nothing
   const int p = N / 2 > 0 ? N / 2 : 1;
-  const R g = (R)ph.g, dt2 = (R)(dtau * dtau);
+  const R g = pc<R>(ph.g, ph.g_f), dt2 = (R)(dtau * dtau);
   __shared__ double sj[2][32];
   auto coef = [&](int m, double& lo, double& di, double& up) {
     const int i = m * S + cs;
@@ -479,7 +508,7 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
   double* sx = sdp + (nv + 1) * 32;      // [2][32] junction values
   double* scf = sx + 64;                 // [nv + 1][32] c' / e', fetched during the sweeps
   const int p = N / 2 > 0 ? N / 2 : 1;
-  const R rdt = (R)dtau, g = (R)ph.g;
+  const R rdt = (R)dtau, g = pc<R>(ph.g, ph.g_f);
 
   auto rhs = [&](int m) {
     const int i = m * S + cs;
@@ -544,7 +573,7 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
   __syncthreads();
   // Eqs. dens2, pt2, theta_to_p with the new W*; the two warps share the levels
   if (valid) {
-    const R gamma = (R)ph.gamma;
+    const R gamma = pc<R>(ph.gamma, ph.gamma_f);
 #pragma unroll 4
     for (int k = half; k < nv; k += 2) {
       const int i = k * S + c;
@@ -582,10 +611,10 @@ template <typename R>
 __device__ __forceinline__ void d_surface_p(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int bx) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
-  const R gamma = (R)ph.gamma, Rd = (R)ph.Rd;
+  const R gamma = pc<R>(ph.gamma, ph.gamma_f), Rd = pc<R>(ph.Rd, ph.Rd_f);
   R p0 = ld(U.pb + (0)) + eos_dev<R>(ld(U.pb + (0)), ld(U.thb + (0)), ld(X.th + (c)), gamma);
   R T0 = p0 / ((ld(U.rhob + (0)) + ld(X.rho + (c))) * Rd);
-  T.psurf[c] = p0 * rexp<R>(R(ph.g) * ld(U.zc + (0)) / (Rd * T0));
+  T.psurf[c] = p0 * rexp<R>(pc<R>(ph.g, ph.g_f) * ld(U.zc + (0)) / (Rd * T0));
 }
 
 template <typename R>
@@ -594,7 +623,8 @@ __device__ __forceinline__ void d_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, W
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
-  const R gamma = (R)ph.gamma, inv_gamma = R(1.0 / ph.gamma), Rd = (R)ph.Rd;
+  const R gamma = pc<R>(ph.gamma, ph.gamma_f), inv_gamma = pc<R>(ph.inv_gamma, ph.inv_gamma_f),
+          Rd = pc<R>(ph.Rd, ph.Rd_f), kappa = pc<R>(ph.kappa, ph.kappa_f);
   R sl = ld(G.sinlat + (c)), cl = ld(G.coslat + (c)), clcl = ld(G.xdir + (c));
   const R ps = ld(T.psurf + (c));
   const R rdt = (R)dt;
@@ -617,7 +647,7 @@ __device__ __forceinline__ void d_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, W
       R c2 = cl * cl;
       KT = ka + (ks - ka) * ramp * c2 * c2;
       R pr = p / p00;
-      Teq = (R(315) - R(60) * sl * sl - R(10) * rlog<R>(pr) * c2) * rpow<R>(pr, (R)ph.kappa);
+      Teq = (R(315) - R(60) * sl * sl - R(10) * rlog<R>(pr) * c2) * rpow<R>(pr, kappa);
       Teq = Teq > R(200) ? Teq : R(200);
     } else {
       const R ss = R(0.12), zs = R(2.0e6), Ts = R(1600), Gt = R(2.0e-4), dTs = R(10);
@@ -776,7 +806,7 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
     }
     return;
   }
-  const float rdt = (float)dtau, g = (float)ph.g;
+  const float rdt = (float)dtau, g = ph.g_f;
   if (warp < 2) {
     auto rhs = [&](int m) {
       const int o = m * 32 + tx;
@@ -838,7 +868,7 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
   }
   __syncthreads();
   if (valid) {
-    const float gamma = (float)ph.gamma;
+    const float gamma = ph.gamma_f;
 #pragma unroll 4
     for (int k = warp; k < nv; k += kSolveWarps) {
       const int o = k * 32 + tx, i = k * S + c;
