@@ -36,6 +36,7 @@ EXPORTED = [
     "thor_autotune", "thor_ensemble_create", "thor_ensemble_step", "thor_ensemble_info",
     "thor_ensemble_tune", "thor_ensemble_autotune", "thor_ensemble_destroy", "thor_mlp_tune",
     "thor_checkpoint_bytes", "thor_checkpoint_save", "thor_checkpoint_load", "thor_wait_selftest",
+    "thor_convert_selftest",
 ]
 
 # kernel ids of thor_profile_read
@@ -128,6 +129,7 @@ def _load():
         "thor_checkpoint_save": (I, [P, P, Z]),
         "thor_checkpoint_load": (I, [P, P, Z]),
         "thor_wait_selftest": (I, [I, ctypes.c_uint, IP]),
+        "thor_convert_selftest": (I, [ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -412,3 +414,11 @@ def thor_wait_selftest(arrive, limit_us):
     g = ctypes.c_int()
     _check(_lib.thor_wait_selftest(int(arrive), int(limit_us), ctypes.byref(g)), "thor_wait_selftest")
     return g.value
+
+
+def thor_convert_selftest(n, seed=1):
+    """Bit mismatches of the integer-ALU float conversions against the
+    conversion instructions over n seeded patterns per direction."""
+    m = ctypes.c_longlong()
+    _check(_lib.thor_convert_selftest(int(n), int(seed), ctypes.byref(m)), "thor_convert_selftest")
+    return m.value

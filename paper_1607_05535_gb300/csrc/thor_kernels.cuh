@@ -129,6 +129,44 @@ __device__ __forceinline__ R eos_dev(R pbar, R thbar, R thp, R gamma) {
   return pbar * rexpm1<R>(gamma * rlog1p<R>(thp / thbar));
 }
 
+// Conversions between binary32 and binary64 on the integer ALU (IEEE 754-2008
+// formats, Sec. 3.4; round to nearest, ties to even, Sec. 4.3.1). On the
+// GB300 a float64 conversion instruction issues on the narrow float64 pipe at
+// the rate of a float64 FMA; the column solve needs one per cell in and one
+// out, so the common cases are done with integer operations and the rest
+// (zeros, subnormals, infinities, NaN, out of float range) fall back to the
+// conversion instruction. Results are bit-identical to it (checked by
+// thor_convert_selftest).
+__device__ __forceinline__ double f2d_alu(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  // sign to bit 63, exponent and mantissa shifted into place, exponent
+  // rebiased from 127 to 1023
+  const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long em =
+      ((unsigned long long)(u & 0x7fffffffu) << 29) + ((unsigned long long)(1023 - 127) << 52);
+  return __longlong_as_double((long long)(s | em));
+}
+__device__ __forceinline__ float d2f_alu(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned long long a = u & 0x7fffffffffffffffull;
+  // |d| in [2^-126, 2^128): a normal float, or infinity if it rounds up
+  if (a < ((unsigned long long)(1023 - 126) << 52) || a >= ((unsigned long long)(1023 + 128) << 52))
+    return (float)d;
+  const unsigned long long t = a - ((unsigned long long)(1023 - 127) << 52);   // exponent biased by 127
+  unsigned long long r = t >> 29;                        // exponent | top 23 mantissa bits
+  const unsigned long long rem = t & ((1ull << 29) - 1), half = 1ull << 28;
+  r += (rem > half || (rem == half && (r & 1ull))) ? 1ull : 0ull;   // a carry moves into the exponent
+  return __uint_as_float((uint32_t)((u >> 32) & 0x80000000u) | (uint32_t)r);
+}
+template <typename R> __device__ __forceinline__ double to_f64(R x);
+template <> __device__ __forceinline__ double to_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ double to_f64<float>(float x) { return f2d_alu(x); }
+template <typename R> __device__ __forceinline__ R from_f64(double x);
+template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return d2f_alu(x); }
+
 // 1/x in float64: a float32 reciprocal refined by two Newton-Raphson steps
 // r <- r + r (1 - x r); each step squares the relative error (2^-23 -> 2^-46
 // -> below 2^-53), at four float64 FMAs instead of a float64 division.
@@ -144,7 +182,7 @@ __device__ __forceinline__ double rcp64(double x) {
 // by one Newton-Raphson step; used for the pivots of the float64 elimination
 // in the mixed-precision path.
 __device__ __forceinline__ double rcp64_1(double x) {
-  double r = (double)__frcp_rn((float)x);
+  double r = f2d_alu(__frcp_rn(d2f_alu(x)));
   return fma(r, fma(-x, r, 1.0), r);
 }
 

@@ -435,9 +435,9 @@ __device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> 
     R lower = 0, upper = 0;
     if (m > 1) lower = (-dtz * pi_lo * ld(SL.thi + (i - S)) + dt2 * g * wlo) * ql;
     if (m < N) upper = (-dtz * pi_hi * ld(SL.thi + (i + S)) - dt2 * g * whi) * ph_;
-    lo = (double)lower;
-    up = (double)upper;
-    di = (double)(R(1) + dtz * th_m * (pi_hi * pl + pi_lo * qh) - dt2 * g * (wlo * qh - whi * pl));
+    lo = to_f64<R>(lower);
+    up = to_f64<R>(upper);
+    di = to_f64<R>(R(1) + dtz * th_m * (pi_hi * pl + pi_lo * qh) - dt2 * g * (wlo * qh - whi * pl));
   };
   auto inv_of = [](double den) { return sizeof(R) == sizeof(double) ? 1.0 / den : rcp64_1(den); };
   double last = 0.0;
@@ -513,7 +513,7 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
   auto rhs = [&](int m) {
     const int i = m * S + cs;
     const R wlo = ld(U.wlo + m), whi = ld(U.whi + m);
-    return (double)(ld(P.w + i) + rdt * ld(SL.sw + i)
+    return to_f64<R>(ld(P.w + i) + rdt * ld(SL.sw + i)
                     - rdt * ld(U.inv_dzc + m) * (ld(T.cc + i) - ld(T.cc + (i - S)))
                     - rdt * g * (wlo * ld(T.ca + (i - S)) + whi * ld(T.ca + i)));
   };
@@ -577,7 +577,7 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
 #pragma unroll 4
     for (int k = half; k < nv; k += 2) {
       const int i = k * S + c;
-      const R wl = (R)sdp[k * 32 + tx], wh = (R)sdp[(k + 1) * 32 + tx];
+      const R wl = from_f64<R>(sdp[k * 32 + tx]), wh = from_f64<R>(sdp[(k + 1) * 32 + tx]);
       const R thl = k > 0 ? ld(SL.thi + i) : R(0);
       const R thh = k + 1 < nv ? ld(SL.thi + (i + S)) : R(0);
       const R el = ld(U.sq_lo + k), eh = ld(U.sq_hi + k);
@@ -811,7 +811,7 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
     auto rhs = [&](int m) {
       const int o = m * 32 + tx;
       const float wlo = ld(U.wlo + m), whi = ld(U.whi + m);
-      return (double)(s_w[o] + rdt * s_sw[o] - rdt * ld(U.inv_dzc + m) * (s_cc[o] - s_cc[o - 32])
+      return f2d_alu(s_w[o] + rdt * s_sw[o] - rdt * ld(U.inv_dzc + m) * (s_cc[o] - s_cc[o - 32])
                       - rdt * g * (wlo * s_ca[o - 32] + whi * s_ca[o]));
     };
     double* sdp = s_inv;
@@ -850,18 +850,18 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
     asm volatile("bar.sync 1, 64;" ::: "memory");
     if (warp == 0) {
       double x = sx[tx];
-      s_wf[p * 32 + tx] = (float)x;
+      s_wf[p * 32 + tx] = d2f_alu(x);
       for (int m = p - 1; m >= 1; --m) {
         x = sdp[m * 32 + tx] - s_cf[m * 32 + tx] * x;
-        s_wf[m * 32 + tx] = (float)x;
+        s_wf[m * 32 + tx] = d2f_alu(x);
       }
       s_wf[tx] = 0.f;
     } else {
       double x = sx[32 + tx];
-      if (p < N) s_wf[(p + 1) * 32 + tx] = (float)x;
+      if (p < N) s_wf[(p + 1) * 32 + tx] = d2f_alu(x);
       for (int m = p + 2; m <= N; ++m) {
         x = sdp[m * 32 + tx] - s_cf[m * 32 + tx] * x;
-        s_wf[m * 32 + tx] = (float)x;
+        s_wf[m * 32 + tx] = d2f_alu(x);
       }
       s_wf[nv * 32 + tx] = 0.f;
     }
