@@ -410,6 +410,12 @@ int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert
 template <typename R>
 Impl<R>::~Impl() {
   drop_graph();
+  if (side) {
+    cudaStreamSynchronize(side);
+    cudaStreamDestroy(side);
+  }
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
   if (arena) cudaFree(arena);
 }
 
@@ -597,6 +603,15 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
   carve(real, *I, h.ncol, h.nv);
   if (col_kernel_setup<R>(h.nv)) return THOR_ECUDA;
   if (I->build_solve_maps()) return THOR_ECUDA;
+  // side stream of the factorisation (optional: without it everything runs
+  // on the state's stream)
+  if (cudaStreamCreateWithFlags(&I->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&I->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&I->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (I->side) cudaStreamDestroy(I->side);
+    I->side = nullptr;
+  }
   HostSetup hs;
   host_setup(h, pl, in, hs);
   int rc = upload_tables(*I, h, hs.vert, st);

@@ -744,9 +744,148 @@ __global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int fo
 
 constexpr int kSolveWarps = 8;
 
-size_t solve_tma_smem_bytes(int nv) {
-  const size_t f = 4 * 32, d = 8 * 32;   // one plane row of 32 columns
-  return 128 + (size_t)(2 * (nv + 1) + 2 * nv) * f + (size_t)(3 * (nv + 1) + 1 + 2) * d + sizeof(uint64_t);
+// one column group's planes in shared memory (32 columns)
+struct SolveSm {
+  float *w, *sw, *cc, *ca;        // w: W*, then the solved W*
+  double *q, *inv, *cf, *junc;    // inv: the pivot reciprocals, then d' and f'
+};
+__device__ __forceinline__ SolveSm solve_sm(unsigned char* base, int nv) {
+  SolveSm s;
+  s.w = reinterpret_cast<float*>(base);             // [nv + 1][32]
+  s.sw = s.w + (nv + 1) * 32;                       // [nv + 1][32]
+  s.cc = s.sw + (nv + 1) * 32;                      // [nv][32]
+  s.ca = s.cc + nv * 32;                            // [nv][32]
+  s.q = reinterpret_cast<double*>(s.ca + nv * 32);  // [nv + 1][32]
+  s.inv = s.q + (nv + 1) * 32;                      // [nv + 1][32]
+  s.cf = s.inv + (nv + 1) * 32;                     // [nv + 1][32]
+  s.junc = s.cf + (nv + 1) * 32;                    // [32]
+  return s;
+}
+// bytes of one group's planes (a multiple of 128, so every plane and what
+// follows them starts 128-byte aligned)
+__host__ __device__ __forceinline__ size_t solve_stage_bytes(int nv) {
+  return (size_t)(2 * (nv + 1) + 2 * nv) * 128 + (size_t)(3 * (nv + 1) + 1) * 256;
+}
+size_t solve_tma_smem_bytes(int nv) { return 128 + solve_stage_bytes(nv) + 2 * 256 + sizeof(uint64_t); }
+
+// thread 0 of the copies: the group's elimination planes into s (completing
+// on bar) and the planes of its final updates into L2
+__device__ __forceinline__ void solve_issue(const SolveSm& s, const SolveMaps& M, int c0, uint64_t* bar, int nv,
+                                            int stage0, int want_div) {
+  const uint32_t fi = (nv + 1) * 128, fc = nv * 128, di = (nv + 1) * 256;
+  mbar_arrive_expect_tx(bar, 2 * fi + 2 * fc + 3 * di + 256);
+  tma_load_2d(s.w, &M.w, c0, 0, bar);
+  tma_load_2d(s.sw, &M.sw, c0, 0, bar);
+  tma_load_2d(s.cc, &M.cc, c0, 0, bar);
+  tma_load_2d(s.ca, &M.ca, c0, 0, bar);
+  tma_load_2d(s.q, &M.q, c0, 0, bar);
+  tma_load_2d(s.inv, &M.inv, c0, 0, bar);
+  tma_load_2d(s.cf, &M.cf, c0, 0, bar);
+  tma_load_2d(s.junc, &M.junction, c0, 0, bar);
+  tma_prefetch_2d(&M.thi, c0, 0);
+  tma_prefetch_2d(&M.cb, c0, 0);
+  tma_prefetch_2d(&M.pp, c0, 0);
+  tma_prefetch_2d(stage0 ? &M.th_t : &M.th_s, c0, 0);
+  if (want_div) {
+    tma_prefetch_2d(&M.dsc, c0, 0);
+    tma_prefetch_2d(&M.dhm, c0, 0);
+  }
+}
+
+// the two float64 sweeps of one group, sweep 0 (rows 1..p, downwards) or 1
+// (rows nv-1..p+1, upwards) by one warp each, then the junction rows and the
+// back substitution; the solved W* over s.w. The two warps meet at named
+// barrier 1.
+__device__ __forceinline__ void solve_sweeps(const SolveSm& s, double* sx, const VR<float>& U, float rdt, float g,
+                                             int nv, int tx, int sweep) {
+  const int N = nv - 1, p = N / 2 > 0 ? N / 2 : 1;
+  auto rhs = [&](int m) {
+    const int o = m * 32 + tx;
+    const float wlo = ld(U.wlo + m), whi = ld(U.whi + m);
+    return f2d_alu(s.w[o] + rdt * s.sw[o] - rdt * ld(U.inv_dzc + m) * (s.cc[o] - s.cc[o - 32])
+                   - rdt * g * (wlo * s.ca[o - 32] + whi * s.ca[o]));
+  };
+  double* sdp = s.inv;
+  float* s_wf = s.w;
+  if (sweep == 0) {
+    double d1 = 0.0;
+#pragma unroll 4
+    for (int m = 1; m <= p; ++m) {
+      const int o = m * 32 + tx;
+      d1 = fma(-s.q[o], d1, rhs(m) * s.inv[o]);
+      sdp[o] = d1;
+    }
+  } else {
+    double f1 = 0.0;
+#pragma unroll 4
+    for (int m = N; m > p; --m) {
+      const int o = m * 32 + tx;
+      f1 = fma(-s.q[o], f1, rhs(m) * s.inv[o]);
+      sdp[o] = f1;
+    }
+  }
+  asm volatile("bar.sync 1, 64;" ::: "memory");        // the two sweeps only
+  if (sweep == 0) {
+    const int op = p * 32 + tx;
+    double xp, xq = 0.0;
+    if (p < N) {
+      const double cp_ = s.cf[op], eq = s.cf[op + 32];
+      const double dp_ = sdp[op], fq = sdp[op + 32];
+      xp = (dp_ - cp_ * fq) * s.junc[tx];
+      xq = fq - eq * xp;
+    } else {
+      xp = sdp[op];
+    }
+    sx[tx] = xp;
+    sx[32 + tx] = xq;
+  }
+  asm volatile("bar.sync 1, 64;" ::: "memory");
+  if (sweep == 0) {
+    double x = sx[tx];
+    s_wf[p * 32 + tx] = d2f_alu(x);
+    for (int m = p - 1; m >= 1; --m) {
+      x = sdp[m * 32 + tx] - s.cf[m * 32 + tx] * x;
+      s_wf[m * 32 + tx] = d2f_alu(x);
+    }
+    s_wf[tx] = 0.f;
+  } else {
+    double x = sx[32 + tx];
+    if (p < N) s_wf[(p + 1) * 32 + tx] = d2f_alu(x);
+    for (int m = p + 2; m <= N; ++m) {
+      x = sdp[m * 32 + tx] - s.cf[m * 32 + tx] * x;
+      s_wf[m * 32 + tx] = d2f_alu(x);
+    }
+    s_wf[nv * 32 + tx] = 0.f;
+  }
+}
+
+// Eqs. dens2, pt2, theta_to_p with the solved W* of column c, levels k0,
+// k0 + kstep, ...
+__device__ __forceinline__ void solve_updates(const SolveSm& s, const Geo<float>& G, const VR<float>& U,
+                                              const Phys& ph, const Xf<float>& Xs, const Slow<float>& SL,
+                                              const Pert<float>& P, const Work<float>& T, float rdt, int want_div,
+                                              const Xf<float>& Xo, int last, int c, int tx, int k0, int kstep) {
+  const int nv = G.nv, S = G.colp;
+  const float gamma = ph.gamma_f;
+  const float* s_wf = s.w;
+#pragma unroll 4
+  for (int k = k0; k < nv; k += kstep) {
+    const int o = k * 32 + tx, i = k * S + c;
+    const float wl = s_wf[o], wh = s_wf[o + 32];
+    const float thl = k > 0 ? ld(SL.thi + i) : 0.f;
+    const float thh = k + 1 < nv ? ld(SL.thi + (i + S)) : 0.f;
+    const float el = ld(U.sq_lo + k), eh = ld(U.sq_hi + k);
+    float th_new = ld(T.cb + i) - rdt * (eh * thh * wh - el * thl * wl);
+    const float rho_new = s.ca[o] - rdt * (eh * wh - el * wl);
+    P.rho[i] = rho_new;
+    P.th[i] = th_new;
+    float ps = ld(U.pb + k) + ld(T.pp + i);
+    float ths = ld(U.thb + k) + ld(Xs.th + i);
+    P.p[i] = ps * rexpm1<float>(gamma * rlog1p<float>(th_new / ths));
+    if (k >= 1) P.w[i] = wl;
+    if (want_div) T.dd[i] = ld(SL.dsc + i) + ld(T.dhm + i) + (eh * wh - el * wl);
+    if (last) stage_end_cell(Xs, Xo, P, rho_new, th_new, wl, k, i, S, nv);
+  }
 }
 
 // M: the state's descriptors, in kernel-parameter or global memory
@@ -756,22 +895,12 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
                                                double dtau, int want_div, const Xf<float>& Xo, int last, int* err,
                                                int bx) {
   extern __shared__ unsigned char smraw[];
-  const int nv = G.nv, S = G.colp, N = nv - 1;
+  const int nv = G.nv;
   const int tid = threadIdx.x, tx = tid & 31, warp = tid >> 5;
   const int c0 = bx * 32, c = c0 + tx;
-  const bool valid = c < G.ncol;
-  const int p = N / 2 > 0 ? N / 2 : 1;
   unsigned char* base = smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u);
-  float* s_w = reinterpret_cast<float*>(base);     // [nv + 1][32]
-  float* s_sw = s_w + (nv + 1) * 32;               // [nv + 1][32]
-  float* s_cc = s_sw + (nv + 1) * 32;              // [nv][32]
-  float* s_ca = s_cc + nv * 32;                    // [nv][32]
-  float* s_wf = s_w;                               // solved W*, over W* once the sweeps are done
-  double* s_q = reinterpret_cast<double*>(s_ca + nv * 32);   // [nv + 1][32]
-  double* s_inv = s_q + (nv + 1) * 32;             // [nv + 1][32], then d' and f'
-  double* s_cf = s_inv + (nv + 1) * 32;            // [nv + 1][32]
-  double* s_junc = s_cf + (nv + 1) * 32;           // [32]
-  double* sx = s_junc + 32;                        // [2][32]
+  const SolveSm s = solve_sm(base, nv);
+  double* sx = reinterpret_cast<double*>(base + solve_stage_bytes(nv));   // [2][32]
   uint64_t* bar = reinterpret_cast<uint64_t*>(sx + 64);
 
   if (tid == 0) {
@@ -779,26 +908,7 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
     mbar_init_fence();
   }
   __syncthreads();
-  if (tid == 0) {
-    const uint32_t fi = (nv + 1) * 128, fc = nv * 128, di = (nv + 1) * 256;
-    mbar_arrive_expect_tx(bar, 2 * fi + 2 * fc + 3 * di + 256);
-    tma_load_2d(s_w, &M.w, c0, 0, bar);
-    tma_load_2d(s_sw, &M.sw, c0, 0, bar);
-    tma_load_2d(s_cc, &M.cc, c0, 0, bar);
-    tma_load_2d(s_ca, &M.ca, c0, 0, bar);
-    tma_load_2d(s_q, &M.q, c0, 0, bar);
-    tma_load_2d(s_inv, &M.inv, c0, 0, bar);
-    tma_load_2d(s_cf, &M.cf, c0, 0, bar);
-    tma_load_2d(s_junc, &M.junction, c0, 0, bar);
-    tma_prefetch_2d(&M.thi, c0, 0);
-    tma_prefetch_2d(&M.cb, c0, 0);
-    tma_prefetch_2d(&M.pp, c0, 0);
-    tma_prefetch_2d(stage0 ? &M.th_t : &M.th_s, c0, 0);
-    if (want_div) {
-      tma_prefetch_2d(&M.dsc, c0, 0);
-      tma_prefetch_2d(&M.dhm, c0, 0);
-    }
-  }
+  if (tid == 0) solve_issue(s, M, c0, bar, nv, stage0, want_div);
   if (!__syncthreads_and(mbar_wait(bar, 0))) {
     if (tid == 0) {                      // flag, give the copies a bounded time to land, leave
       atomicExch(err, 1);
@@ -807,87 +917,9 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
     return;
   }
   const float rdt = (float)dtau, g = ph.g_f;
-  if (warp < 2) {
-    auto rhs = [&](int m) {
-      const int o = m * 32 + tx;
-      const float wlo = ld(U.wlo + m), whi = ld(U.whi + m);
-      return f2d_alu(s_w[o] + rdt * s_sw[o] - rdt * ld(U.inv_dzc + m) * (s_cc[o] - s_cc[o - 32])
-                      - rdt * g * (wlo * s_ca[o - 32] + whi * s_ca[o]));
-    };
-    double* sdp = s_inv;
-    if (warp == 0) {
-      double d1 = 0.0;
-#pragma unroll 4
-      for (int m = 1; m <= p; ++m) {
-        const int o = m * 32 + tx;
-        d1 = fma(-s_q[o], d1, rhs(m) * s_inv[o]);
-        sdp[o] = d1;
-      }
-    } else {
-      double f1 = 0.0;
-#pragma unroll 4
-      for (int m = N; m > p; --m) {
-        const int o = m * 32 + tx;
-        f1 = fma(-s_q[o], f1, rhs(m) * s_inv[o]);
-        sdp[o] = f1;
-      }
-    }
-    asm volatile("bar.sync 1, 64;" ::: "memory");        // the two sweeps only
-    if (warp == 0) {
-      const int op = p * 32 + tx;
-      double xp, xq = 0.0;
-      if (p < N) {
-        const double cp_ = s_cf[op], eq = s_cf[op + 32];
-        const double dp_ = sdp[op], fq = sdp[op + 32];
-        xp = (dp_ - cp_ * fq) * s_junc[tx];
-        xq = fq - eq * xp;
-      } else {
-        xp = sdp[op];
-      }
-      sx[tx] = xp;
-      sx[32 + tx] = xq;
-    }
-    asm volatile("bar.sync 1, 64;" ::: "memory");
-    if (warp == 0) {
-      double x = sx[tx];
-      s_wf[p * 32 + tx] = d2f_alu(x);
-      for (int m = p - 1; m >= 1; --m) {
-        x = sdp[m * 32 + tx] - s_cf[m * 32 + tx] * x;
-        s_wf[m * 32 + tx] = d2f_alu(x);
-      }
-      s_wf[tx] = 0.f;
-    } else {
-      double x = sx[32 + tx];
-      if (p < N) s_wf[(p + 1) * 32 + tx] = d2f_alu(x);
-      for (int m = p + 2; m <= N; ++m) {
-        x = sdp[m * 32 + tx] - s_cf[m * 32 + tx] * x;
-        s_wf[m * 32 + tx] = d2f_alu(x);
-      }
-      s_wf[nv * 32 + tx] = 0.f;
-    }
-  }
+  if (warp < 2) solve_sweeps(s, sx, U, rdt, g, nv, tx, warp);
   __syncthreads();
-  if (valid) {
-    const float gamma = ph.gamma_f;
-#pragma unroll 4
-    for (int k = warp; k < nv; k += kSolveWarps) {
-      const int o = k * 32 + tx, i = k * S + c;
-      const float wl = s_wf[o], wh = s_wf[o + 32];
-      const float thl = k > 0 ? ld(SL.thi + i) : 0.f;
-      const float thh = k + 1 < nv ? ld(SL.thi + (i + S)) : 0.f;
-      const float el = ld(U.sq_lo + k), eh = ld(U.sq_hi + k);
-      float th_new = ld(T.cb + i) - rdt * (eh * thh * wh - el * thl * wl);
-      const float rho_new = s_ca[o] - rdt * (eh * wh - el * wl);
-      P.rho[i] = rho_new;
-      P.th[i] = th_new;
-      float ps = ld(U.pb + k) + ld(T.pp + i);
-      float ths = ld(U.thb + k) + ld(Xs.th + i);
-      P.p[i] = ps * rexpm1<float>(gamma * rlog1p<float>(th_new / ths));
-      if (k >= 1) P.w[i] = wl;
-      if (want_div) T.dd[i] = ld(SL.dsc + i) + ld(T.dhm + i) + (eh * wh - el * wl);
-      if (last) stage_end_cell(Xs, Xo, P, rho_new, th_new, wl, k, i, S, nv);
-    }
-  }
+  if (c < G.ncol) solve_updates(s, G, U, ph, Xs, SL, P, T, rdt, want_div, Xo, last, c, tx, warp, kSolveWarps);
 }
 
 __global__ void __launch_bounds__(32 * kSolveWarps)
@@ -1042,9 +1074,18 @@ int Impl<R>::large_step(double dt, int n_small) {
     mark(THOR_K_SLOW_W, true);
     chk(launch_k(k_slow_w<R>, g2i, bs, 0, stream, G, U, ph, Xt, Xs, T, SL, P, hyper, kc));
     mark(THOR_K_SLOW_W, false);
+    // the factorisation depends only on the slow terms and is needed first by
+    // the column step: on the side stream it overlaps the first small step's
+    // stencils (graph branch when captured)
+    const bool fork = side != nullptr && !prof_on;
+    if (fork) {
+      chk(cudaEventRecord(ev_fork, stream));
+      chk(cudaStreamWaitEvent(side, ev_fork, 0));
+    }
     mark(THOR_K_SS_FACTOR, true);
-    chk(launch_k(k_ss_factor<R>, gsolve, 64, 0, stream, G, U, ph, SL, F, dts[s]));
+    chk(launch_k(k_ss_factor<R>, gsolve, 64, 0, fork ? side : stream, G, U, ph, SL, F, dts[s]));
     mark(THOR_K_SS_FACTOR, false);
+    if (fork) chk(cudaEventRecord(ev_join, side));
     launches += 3;
     for (int j = 0; j < nsub[s]; ++j) {
       if (divdamp) {   // D: of X^t in the first small step, then from the previous column step
@@ -1062,6 +1103,7 @@ int Impl<R>::large_step(double dt, int n_small) {
       mark(THOR_K_SS_FLUX, true);
       chk(launch_k(k_ss_flux<R>, g2, bs, 0, stream, G, U, SL, P, T, (R)dts[s], kc));
       mark(THOR_K_SS_FLUX, false);
+      if (fork && j == 0) chk(cudaStreamWaitEvent(stream, ev_join, 0));
       mark(THOR_K_SS_COL, true);
       if (staged)
         chk(launch_solve_tma(gsolve, s, dts[s], want_div, last));
