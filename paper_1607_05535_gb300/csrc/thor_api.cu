@@ -416,6 +416,7 @@ Impl<R>::~Impl() {
   }
   if (ev_fork) cudaEventDestroy(ev_fork);
   if (ev_join) cudaEventDestroy(ev_join);
+  if (ev_join0) cudaEventDestroy(ev_join0);
   if (arena) cudaFree(arena);
 }
 
@@ -603,11 +604,12 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
   carve(real, *I, h.ncol, h.nv);
   if (col_kernel_setup<R>(h.nv)) return THOR_ECUDA;
   if (I->build_solve_maps()) return THOR_ECUDA;
-  // side stream of the factorisation (optional: without it everything runs
-  // on the state's stream)
+  // side stream for the stage kernels that run beside others (optional:
+  // without it everything runs on the state's stream)
   if (cudaStreamCreateWithFlags(&I->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&I->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&I->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&I->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&I->ev_join0, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     if (I->side) cudaStreamDestroy(I->side);
     I->side = nullptr;

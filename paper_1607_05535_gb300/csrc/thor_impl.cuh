@@ -168,10 +168,11 @@ struct Impl : ImplBase {
   double graph_dt = 0;
   int graph_n = 0, graph_kc = 0, graph_bs = 0, graph_tma = -1;
   std::unique_ptr<SolveMaps> smaps;   // null where the staged solve does not apply
-  // second stream for the per-stage factorisation, forked from and joined to
-  // the state's stream by events (null: everything on the state's stream)
+  // second stream for the kernels of a stage that run beside others, forked
+  // from and joined to the state's stream by events (null: everything on the
+  // state's stream)
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join0 = nullptr;
   int build_solve_maps();
   cudaError_t launch_solve_tma(dim3 grid, int stage, double dtau, int want_div, int last);
   long long graph_launches = 0;

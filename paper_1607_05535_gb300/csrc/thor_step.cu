@@ -229,12 +229,12 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
 }
 
 // Slow tendency of the vertical momentum at the interior interfaces
-// (right-hand side of Eq. momr2) and theta at the interfaces; and, on the same
-// (column, level) grid, the perturbations at the start of the stage:
-// Phi* = Phi^t - Phi^(s), p* from the nonlinear Eq. theta_to_p.
+// (right-hand side of Eq. momr2) and theta at the interfaces; with init, on
+// the same (column, level) grid, also the perturbations at the start of the
+// stage: Phi* = Phi^t - Phi^(s), p* from the nonlinear Eq. theta_to_p.
 template <typename R>
 __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Slow<R> SL,
-                                         Pert<R> P, int hyper, int kchunk, int bx, int by) {
+                                         Pert<R> P, int hyper, int init, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -245,8 +245,8 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int i = k * S + c;
-    // stage start
-    if (k < G.nv) {
+    // stage start (unless k_stage_init does it)
+    if (init && k < G.nv) {
       P.rho[i] = ld(Xt.rho + (i)) - ld(X.rho + (i));
       P.mx[i] = ld(Xt.mx + (i)) - ld(X.mx + (i));
       P.my[i] = ld(Xt.my + (i)) - ld(X.my + (i));
@@ -255,7 +255,7 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
       R ppt = eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), ld(Xt.th + (i)), gamma);
       P.p[i] = ppt - ld(T.pp + (i));
     }
-    P.w[i] = ld(Xt.w + (i)) - ld(X.w + (i));
+    if (init) P.w[i] = ld(Xt.w + (i)) - ld(X.w + (i));
     // slow terms of Eq. momr2
     if (k == 0 || k == G.nv) {
       SL.sw[i] = 0;
@@ -270,6 +270,38 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
          - (wlo * ld(SL.acr + (i - S)) + whi * ld(SL.acr + (i))) + FW;
     SL.sw[i] = sw;
     SL.thi[i] = wlo * ld(T.theta + (i - S)) + whi * ld(T.theta + (i));
+  }
+}
+
+// The perturbations at the start of a stage on their own (the state's step
+// runs this beside the slow terms): Phi* = Phi^t - Phi^(s), p* from the
+// nonlinear Eq. theta_to_p; all zero in the first stage, where Phi^(s) =
+// Phi^t and p^(s) = EOS(Th^t).
+template <typename R>
+__device__ __forceinline__ void d_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Pert<R> P,
+                                             int zero, int kchunk, int bx, int by) {
+  int c = bx * blockDim.x + threadIdx.x;
+  if (c >= G.ncol) return;
+  const int S = G.colp;
+  const R gamma = pc<R>(ph.gamma, ph.gamma_f);
+  int k0 = by * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
+#pragma unroll 2
+  for (int k = k0; k < k1; ++k) {
+    const int i = k * S + c;
+    if (k < G.nv) {
+      if (zero) {
+        P.rho[i] = P.mx[i] = P.my[i] = P.mz[i] = P.th[i] = P.p[i] = R(0);
+      } else {
+        P.rho[i] = ld(Xt.rho + (i)) - ld(X.rho + (i));
+        P.mx[i] = ld(Xt.mx + (i)) - ld(X.mx + (i));
+        P.my[i] = ld(Xt.my + (i)) - ld(X.my + (i));
+        P.mz[i] = ld(Xt.mz + (i)) - ld(X.mz + (i));
+        P.th[i] = ld(Xt.th + (i)) - ld(X.th + (i));
+        R ppt = eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), ld(Xt.th + (i)), gamma);
+        P.p[i] = ppt - ld(T.pp + (i));
+      }
+    }
+    P.w[i] = zero ? R(0) : ld(Xt.w + (i)) - ld(X.w + (i));
   }
 }
 
@@ -693,8 +725,13 @@ __global__ void __launch_bounds__(kMaxBlock, 2)
 }
 template <typename R>
 __global__ void k_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Slow<R> SL, Pert<R> P, int hyper,
-                         int kchunk) {
-  d_slow_w<R>(G, U, ph, Xt, X, T, SL, P, hyper, kchunk, blockIdx.x, blockIdx.y);
+                         int init, int kchunk) {
+  d_slow_w<R>(G, U, ph, Xt, X, T, SL, P, hyper, init, kchunk, blockIdx.x, blockIdx.y);
+}
+template <typename R>
+__global__ void k_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Pert<R> P, int zero,
+                             int kchunk) {
+  d_stage_init<R>(G, U, ph, Xt, X, T, P, zero, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
 __global__ void k_ss_grad(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, int kchunk) {
@@ -961,7 +998,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2)
 template <typename R>
 __global__ void ke_slow_w(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
   THOR_MEMBER();
-  d_slow_w<R>(a.G, a.U, a.ph, a.Xt, Xs, a.T, a.SL, a.P, a.hyper, kchunk, e.y, blockIdx.y);
+  d_slow_w<R>(a.G, a.U, a.ph, a.Xt, Xs, a.T, a.SL, a.P, a.hyper, 1, kchunk, e.y, blockIdx.y);
 }
 template <typename R>
 __global__ void __launch_bounds__(64)
@@ -1055,12 +1092,37 @@ int Impl<R>::large_step(double dt, int n_small) {
   auto chk = [&](cudaError_t r) {
     if (e == cudaSuccess) e = r;
   };
+  // Kernels of a stage that do not depend on each other run on two streams
+  // (graph branches when captured): after k_derived the stage's perturbations
+  // (k_stage_init) and, from the second stage on, the first small step's
+  // gradient of D (of X^t, kept from the first stage) run on the side stream
+  // beside the slow terms; after k_slow_w the factorisation runs there beside
+  // the first small step's stencils. With per-kernel profiling everything
+  // stays on the state's stream, in the same order.
+  const bool fork = side != nullptr && !prof_on;
   for (int s = 0; s < 3; ++s) {
     Xf<R> Xs = s == 0 ? Xt : Xst, Xo = s == 2 ? Xt : Xst;
+    cudaStream_t aux = fork ? side : stream;
     mark(THOR_K_DERIVED, true);
     chk(launch_k(k_derived<R>, g2i, bs, 0, stream, G, U, ph, Xs, T, kc));
     mark(THOR_K_DERIVED, false);
     ++launches;
+    if (fork) {
+      chk(cudaEventRecord(ev_fork, stream));
+      chk(cudaStreamWaitEvent(side, ev_fork, 0));
+    }
+    mark(THOR_K_STAGE_INIT, true);
+    chk(launch_k(k_stage_init<R>, g2i, bs, 0, aux, G, U, ph, Xt, Xs, T, P, (int)(s == 0), kc));
+    mark(THOR_K_STAGE_INIT, false);
+    ++launches;
+    const bool early_grad = divdamp && s > 0;    // D of X^t is ready before the slow terms
+    if (early_grad) {
+      mark(THOR_K_SS_GRAD, true);
+      chk(launch_k(k_ss_grad<R>, g2, bs, 0, aux, G, U, T, (const R*)T.dd0, kc));
+      mark(THOR_K_SS_GRAD, false);
+      ++launches;
+    }
+    if (fork) chk(cudaEventRecord(ev_join0, side));
     if (hyper) {
       mark(THOR_K_LAP1, true);
       chk(launch_k(k_lap1<R>, g2i, bs, 0, stream, G, U, Xs, T, Kd, kc));
@@ -1072,23 +1134,23 @@ int Impl<R>::large_step(double dt, int n_small) {
                  s == 0 && divdamp ? T.dd0 : (R*)nullptr, kc));
     mark(THOR_K_SLOW, false);
     mark(THOR_K_SLOW_W, true);
-    chk(launch_k(k_slow_w<R>, g2i, bs, 0, stream, G, U, ph, Xt, Xs, T, SL, P, hyper, kc));
+    chk(launch_k(k_slow_w<R>, g2i, bs, 0, stream, G, U, ph, Xt, Xs, T, SL, P, hyper, 0, kc));
     mark(THOR_K_SLOW_W, false);
-    // the factorisation depends only on the slow terms and is needed first by
-    // the column step: on the side stream it overlaps the first small step's
-    // stencils (graph branch when captured)
-    const bool fork = side != nullptr && !prof_on;
     if (fork) {
       chk(cudaEventRecord(ev_fork, stream));
       chk(cudaStreamWaitEvent(side, ev_fork, 0));
     }
     mark(THOR_K_SS_FACTOR, true);
-    chk(launch_k(k_ss_factor<R>, gsolve, 64, 0, fork ? side : stream, G, U, ph, SL, F, dts[s]));
+    chk(launch_k(k_ss_factor<R>, gsolve, 64, 0, aux, G, U, ph, SL, F, dts[s]));
     mark(THOR_K_SS_FACTOR, false);
-    if (fork) chk(cudaEventRecord(ev_join, side));
+    if (fork) {
+      chk(cudaEventRecord(ev_join, side));
+      chk(cudaStreamWaitEvent(stream, ev_join0, 0));
+    }
     launches += 3;
     for (int j = 0; j < nsub[s]; ++j) {
-      if (divdamp) {   // D: of X^t in the first small step, then from the previous column step
+      // D: of X^t in the first small step, then from the previous column step
+      if (divdamp && !(j == 0 && early_grad)) {
         mark(THOR_K_SS_GRAD, true);
         chk(launch_k(k_ss_grad<R>, g2, bs, 0, stream, G, U, T, (const R*)(j == 0 ? T.dd0 : T.dd), kc));
         mark(THOR_K_SS_GRAD, false);
