@@ -296,9 +296,11 @@ def stage_schedule(dt, n_small):
     return [(dt / 3.0, 1), (dt / n_small, n_small // 2), (dt / n_small, n_small)]
 
 
-def large_step(model, X, dt, n_small):
-    """One large step: three RK3 stages of small steps (reading R1), then the
-    physics of Sec. 5."""
+def large_step(model, X, dt, n_small, energy_fixer=False, budget=None):
+    """One large step: three RK3 stages of small steps (reading R1), then, if
+    energy_fixer, the uniform internal-energy adjustment of energy.energy_fix
+    (Sec. 3), then the physics of Sec. 5. If budget is a list, the step's
+    budget row (energy.budget_row) is appended to it."""
     from .physics import apply_physics
     Kd = model.Kd(dt)
     Xt = X
@@ -310,12 +312,19 @@ def large_step(model, X, dt, n_small):
         for _ in range(nsub):
             pert = small_step(model, Xs, co, pert, dtau, Kd)
         Xs = State(Xs.rho + pert["rho"], Xs.M + pert["M"], Xs.W + pert["W"], pert["Th"])
+    if energy_fixer or budget is not None:
+        from .energy import budget_row, energy_fix
+        Xd, dT = Xs, 0.0
+        if energy_fixer:
+            Xs, dT = energy_fix(model, Xt, Xd)
+        if budget is not None:
+            budget.append(budget_row(model, Xt, Xd, dT))
     return apply_physics(model, Xs, dt)
 
 
-def run(model, X, n_large, n_small, dt):
+def run(model, X, n_large, n_small, dt, energy_fixer=False, budget=None):
     for _ in range(n_large):
-        X = large_step(model, X, dt, n_small)
+        X = large_step(model, X, dt, n_small, energy_fixer, budget)
     return X
 
 
