@@ -201,8 +201,20 @@ int thor_launch_count(const thor_state* state, long long* count);
  * return THOR_ENONFINITE if any value is NaN or Inf; the state is the one
  * after the step (restore a checkpoint with thor_state_set). Default 0. */
 enum { THOR_TUNE_KCHUNK = 0, THOR_TUNE_GRAPH = 1, THOR_TUNE_CHECK_FINITE = 2, THOR_TUNE_BLOCK = 3,
-       THOR_TUNE_SOLVE_TMA = 4 };
+       THOR_TUNE_SOLVE_TMA = 4, THOR_TUNE_ENERGY_FIXER = 5, THOR_TUNE_BUDGET = 6 };
 int thor_tune(thor_state* state, int knob, int value);
+
+/* Energy and angular-momentum budget of the large steps recorded since
+ * thor_tune(THOR_TUNE_BUDGET, capacity): row n (8 float64) holds the dry mass,
+ * total energy and axial angular momentum of thor_diag at the start of large
+ * step n and after its dynamics (before the fixer and the physics), then the
+ * fixer's dT (0 when it is off) and 0. The dynamics' numerical sources are
+ * columns 3-5 minus 0-2; the physics' (and the fixer's) are the next row's
+ * 0-2 minus this row's 3-5. Copies min(recorded, max_rows) rows to `out`
+ * (host, max_rows * 8 doubles) and their number to *n_rows (0 when not
+ * recording); synchronises the state's stream. Sec. 3 (energy), Sec. 6.1
+ * (axial angular momentum reaching a statistically steady value). */
+int thor_budget_read(thor_state* state, double* out, int max_rows, int* n_rows);
 
 /* THOR_TUNE_BLOCK: threads (one per column) in a block of the stencil
  * kernels, a multiple of 32 in [32, 256] (default 128).
@@ -211,7 +223,22 @@ int thor_tune(thor_state* state, int knob, int value);
  * (where the staging fits, nv <= 80); 0 runs the direct-load solve. Same
  * arithmetic, same results. A staged copy that has not landed after 2 s ends
  * the kernel with a device error flag; thor_diag (and thor_step with
- * THOR_TUNE_CHECK_FINITE) then return THOR_ETIMEOUT. */
+ * THOR_TUNE_CHECK_FINITE) then return THOR_ETIMEOUT.
+ * THOR_TUNE_ENERGY_FIXER: 1 turns on the energy fixer that Sec. 3 describes
+ * (after Williamson 2009: the internal energy adjusted by the same amount at
+ * every grid point). Once per large step, after the three RK3 stages and
+ * before the physics, every cell's temperature rises by
+ *   dT = (E_start - E_dyn) / (c_v * sum over cells of V rho)
+ * at fixed density and momentum (rho theta from Eq. pressure), E the total
+ * energy of thor_diag at the start of the step and after its dynamics, so
+ * that the dynamics leave the total energy unchanged and the physics is its
+ * only source. 0 (default, as the paper's runs) turns it off. The first use
+ * allocates a small device buffer; synchronises the state's stream.
+ * THOR_TUNE_BUDGET: value > 0 records, for each of the next `value` large
+ * steps (at most 2^24), one budget row that thor_budget_read returns; 0 stops
+ * recording and frees the rows. Allocates value * 64 bytes on the device and
+ * synchronises the state's stream; recording costs two float64 reductions
+ * of the state per large step. Neither knob applies to thor_ensemble_step. */
 
 /* Launch-shape autotuner (an extension; the paper fixes no launch shapes).
  * Times `steps` large steps of (n_small, dt) for every levels-per-thread

@@ -21,7 +21,8 @@ THOR_FP64, THOR_MIXED = 0, 1
 THOR_FORCING_NONE, THOR_FORCING_HELD_SUAREZ, THOR_FORCING_HOT_JUPITER = 0, 1, 2
 THOR_FIELD_RHO, THOR_FIELD_MOM, THOR_FIELD_W, THOR_FIELD_RHOTHETA, THOR_FIELD_PRESSURE, \
     THOR_FIELD_TEMPERATURE = range(6)
-THOR_TUNE_KCHUNK, THOR_TUNE_GRAPH, THOR_TUNE_CHECK_FINITE, THOR_TUNE_BLOCK, THOR_TUNE_SOLVE_TMA = range(5)
+(THOR_TUNE_KCHUNK, THOR_TUNE_GRAPH, THOR_TUNE_CHECK_FINITE, THOR_TUNE_BLOCK, THOR_TUNE_SOLVE_TMA,
+ THOR_TUNE_ENERGY_FIXER, THOR_TUNE_BUDGET) = range(7)
 THOR_ENSEMBLE_MAX = 4096
 THOR_MLP_TUNE_TCGEN05 = 0
 
@@ -36,7 +37,7 @@ EXPORTED = [
     "thor_autotune", "thor_ensemble_create", "thor_ensemble_step", "thor_ensemble_info",
     "thor_ensemble_tune", "thor_ensemble_autotune", "thor_ensemble_destroy", "thor_mlp_tune",
     "thor_checkpoint_bytes", "thor_checkpoint_save", "thor_checkpoint_load", "thor_wait_selftest",
-    "thor_convert_selftest",
+    "thor_convert_selftest", "thor_budget_read",
 ]
 
 # kernel ids of thor_profile_read
@@ -130,6 +131,7 @@ def _load():
         "thor_checkpoint_load": (I, [P, P, Z]),
         "thor_wait_selftest": (I, [I, ctypes.c_uint, IP]),
         "thor_convert_selftest": (I, [ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]),
+        "thor_budget_read": (I, [P, ctypes.POINTER(D), I, IP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -422,3 +424,15 @@ def thor_convert_selftest(n, seed=1):
     m = ctypes.c_longlong()
     _check(_lib.thor_convert_selftest(int(n), int(seed), ctypes.byref(m)), "thor_convert_selftest")
     return m.value
+
+
+def thor_budget_read(state, max_rows=1 << 16):
+    """Budget rows recorded since thor_tune(THOR_TUNE_BUDGET, capacity), as a
+    float64 array (n, 8): mass, energy, axial angular momentum at the start
+    of each large step and after its dynamics, the energy fixer's dT, 0."""
+    import numpy as np
+    out = np.zeros((max_rows, 8))
+    n = ctypes.c_int()
+    _check(_lib.thor_budget_read(state, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(max_rows),
+                                 ctypes.byref(n)), "thor_budget_read")
+    return out[:n.value].copy()

@@ -1,5 +1,6 @@
 // C ABI of libthor (declared in include/thor.h): handles, initial state,
 // field transfer in the canonical order, diagnostics.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -10,6 +11,7 @@
 #include "../../include/thor.h"
 #include "grid.h"
 #include "thor_impl.cuh"
+#include "thor_reduce.cuh"
 
 #include "thor_state.h"
 
@@ -81,116 +83,6 @@ __global__ void k_to_canonical(double* dst, Geo<R> G, Vert V, Phys ph, Xf<R> X, 
       }
       break;
     }
-  }
-}
-
-// ------------------------------------------------------------ diagnostics
-
-constexpr int kDiagBlocks = 512;
-constexpr int kDiagThreads = 256;
-
-struct Kahan {
-  double s = 0, c = 0;
-  __device__ void add(double x) {
-    double y = x - c;
-    double t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-};
-
-// partial sums per block: mass, energy, aam, sum V T, sum V, max vh, max w, nonfinite
-template <typename R>
-__global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Geo<R> G, Vert V, Phys ph, Xf<R> X,
-                                                               double* part) {
-  const int S = G.colp, nv = G.nv;
-  const long long ncell = (long long)G.ncol * nv;
-  Kahan mass, en, aam, vt, vs;
-  double mvh = 0, mw = 0;
-  double nf = 0;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    int k = (int)(q / G.ncol), c = (int)(q % G.ncol);
-    size_t i = (size_t)k * S + c;
-    double rx = G.rhat[c], ry = G.rhat[S + c], rz = G.rhat[2 * S + c];
-    double rho = V.rhob[k] + (double)X.rho[i];
-    double th = V.thb[k] + (double)X.th[i];
-    double p = V.pb[k] + V.pb[k] * expm1(ph.gamma * log1p((double)X.th[i] / V.thb[k]));
-    double Temp = p / (rho * ph.Rd);
-    double wlo = X.w[i], whi = X.w[i + S];
-    double wc = V.clo[k] * wlo + V.chi[k] * whi;
-    double mx = (double)X.mx[i] + wc * rx, my = (double)X.my[i] + wc * ry, mz = (double)X.mz[i] + wc * rz;
-    double vol = G.area[c] * V.rc[k] * V.rc[k] * V.dz[k];
-    mass.add(vol * rho);
-    en.add(vol * (rho * ph.cv * Temp + 0.5 * (mx * mx + my * my + mz * mz) / rho + rho * ph.g * V.zc[k]));
-    double r = V.rc[k];
-    aam.add(vol * (r * (rx * my - ry * mx) + rho * ph.omega * r * r * (rx * rx + ry * ry)));
-    vt.add(vol * Temp);
-    vs.add(vol);
-    double hx = (double)X.mx[i] / rho, hy = (double)X.my[i] / rho, hz = (double)X.mz[i] / rho;
-    mvh = fmax(mvh, sqrt(hx * hx + hy * hy + hz * hz));
-    if (k >= 1) {
-      double rif = V.wlo[k] * (V.rhob[k - 1] + (double)X.rho[i - S]) + V.whi[k] * rho;
-      mw = fmax(mw, fabs(wlo / rif));
-    }
-    double vals[6] = {(double)X.rho[i], (double)X.mx[i], (double)X.my[i], (double)X.mz[i], th, (double)X.w[i]};
-    for (int j = 0; j < 6; ++j)
-      if (!isfinite(vals[j])) nf += 1.0;
-    if (k == nv - 1 && !isfinite((double)X.w[i + S])) nf += 1.0;
-  }
-  __shared__ double sh[8][kDiagThreads];
-  double mine[8] = {mass.s, en.s, aam.s, vt.s, vs.s, mvh, mw, nf};
-  for (int j = 0; j < 8; ++j) sh[j][threadIdx.x] = mine[j];
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int j = 0; j < 8; ++j) {
-        double a = sh[j][threadIdx.x], b = sh[j][threadIdx.x + w];
-        sh[j][threadIdx.x] = (j == 5 || j == 6) ? fmax(a, b) : a + b;
-      }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0)
-    for (int j = 0; j < 8; ++j) part[blockIdx.x * 8 + j] = sh[j][0];
-}
-
-// One warp per quantity: every lane sums a strided share of the block
-// partials (compensated), then lane 0 adds the 32 lane sums in order
-// (compensated); extrema by max, the non-finite count by plain addition.
-__global__ void __launch_bounds__(256) k_diag_final(double* part, int nblocks) {
-  const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __shared__ double lanes[8][32];
-  const bool is_max = j == 5 || j == 6, is_count = j == 7;
-  double s = 0.0, comp = 0.0;
-  for (int b = lane; b < nblocks; b += 32) {
-    const double x = part[b * 8 + j];
-    if (is_max) {
-      s = fmax(s, x);
-    } else if (is_count) {
-      s += x;
-    } else {
-      const double y = x - comp, t = s + y;
-      comp = (t - s) - y;
-      s = t;
-    }
-  }
-  lanes[j][lane] = s;
-  __syncwarp();
-  if (lane == 0) {
-    double o = 0.0, cm = 0.0;
-    for (int l = 0; l < 32; ++l) {
-      const double x = lanes[j][l];
-      if (is_max) {
-        o = fmax(o, x);
-      } else if (is_count) {
-        o += x;
-      } else {
-        const double y = x - cm, t = o + y;
-        cm = (t - o) - y;
-        o = t;
-      }
-    }
-    part[nblocks * 8 + j] = o;
   }
 }
 
@@ -878,7 +770,44 @@ int thor_tune(thor_state* s, int knob, int value) {
     s->impl->solve_tma = value != 0;
     return THOR_OK;
   }
+  if (knob == THOR_TUNE_ENERGY_FIXER || knob == THOR_TUNE_BUDGET) {
+    thor::ImplBase* I = s->impl.get();
+    if (knob == THOR_TUNE_BUDGET && (value < 0 || value > (1 << 24))) return THOR_EINVAL;
+    if (cudaStreamSynchronize(I->stream)) return THOR_ECUDA;   // no step still uses the buffers
+    if (!I->fixbuf && value && cudaMalloc(&I->fixbuf, thor::kFixBufBytes)) return THOR_ENOMEM;
+    if (knob == THOR_TUNE_ENERGY_FIXER) {
+      I->energy_fix = value != 0;
+    } else {
+      if (I->budget) cudaFree(I->budget);
+      I->budget = nullptr;
+      I->budget_cap = 0;
+      if (value) {
+        if (!I->budget_count && cudaMalloc(&I->budget_count, sizeof(int))) return THOR_ENOMEM;
+        if (cudaMalloc(&I->budget, (size_t)value * 8 * sizeof(double))) return THOR_ENOMEM;
+        if (cudaMemset(I->budget_count, 0, sizeof(int))) return THOR_ECUDA;
+        I->budget_cap = value;
+      }
+    }
+    I->reset_graph();
+    return THOR_OK;
+  }
   return THOR_EINVAL;
+}
+
+int thor_budget_read(thor_state* s, double* out, int max_rows, int* n_rows) {
+  if (!s || !n_rows || max_rows < 0 || (max_rows > 0 && !out)) return THOR_EINVAL;
+  thor::ImplBase* I = s->impl.get();
+  *n_rows = 0;
+  if (!I->budget_cap) return THOR_OK;
+  int n = 0;
+  if (cudaMemcpyAsync(&n, I->budget_count, sizeof(int), cudaMemcpyDeviceToHost, I->stream) ||
+      cudaStreamSynchronize(I->stream))
+    return THOR_ECUDA;
+  n = std::min(n, max_rows);
+  if (n > 0 && cudaMemcpy(out, I->budget, (size_t)n * 8 * sizeof(double), cudaMemcpyDeviceToHost))
+    return THOR_ECUDA;
+  *n_rows = n;
+  return THOR_OK;
 }
 
 int thor_profile(thor_state* s, int enable) {

@@ -71,8 +71,18 @@ struct Member {
   int* err;                        // the state's device error flag
 };
 
+// device buffer of the energy fixer and budget: two diagnostics reductions
+// (kDiagBlocks + 1 rows of 8 each), dT in float64, dT in the storage type
+constexpr size_t kFixBufBytes = (size_t)(2 * (512 + 1) * 8 + 2) * sizeof(double);
+
 struct ImplBase {
-  virtual ~ImplBase() { prof_clear(); }
+  virtual ~ImplBase() {
+    prof_clear();
+    if (fixbuf) cudaFree(fixbuf);
+    if (budget) cudaFree(budget);
+    if (budget_count) cudaFree(budget_count);
+  }
+  virtual void reset_graph() = 0;      // drop the captured step (its launches changed)
   virtual int step(int n_large, int n_small, double dt) = 0;
   virtual int diag(double* out8, long long* nonfinite) = 0;
   virtual int get(int field, double* host, size_t n) = 0;
@@ -83,6 +93,12 @@ struct ImplBase {
   int block = kBlock;                  // threads (columns) per block of the stencil kernels
   int solve_tma = 1;                   // TMA-staged column solve where available
   int* dev_err = nullptr;              // device flag: 1 = a bounded device wait timed out
+  // energy fixer and budget (thor_tune THOR_TUNE_ENERGY_FIXER / THOR_TUNE_BUDGET)
+  int energy_fix = 0;
+  int budget_cap = 0;                  // large steps the budget can hold (0: not recording)
+  double* fixbuf = nullptr;            // two diagnostics reductions, dT (float64 and storage type)
+  double* budget = nullptr;            // [budget_cap][8]
+  int* budget_count = nullptr;         // rows recorded
   // copy the prognostic fields to / from a device buffer of state_bytes()
   virtual size_t state_bytes() const = 0;
   virtual int save_state(void* dst) = 0;
@@ -159,6 +175,7 @@ struct Impl : ImplBase {
     use_graph = on;
     if (!on) drop_graph();
   }
+  void reset_graph() override { drop_graph(); }
   ~Impl() override;
   void launch_2d(int nplanes, int kchunk, dim3& grid) const;
   int large_step(double dt, int n_small);
@@ -166,7 +183,7 @@ struct Impl : ImplBase {
   // the same; used on a non-default stream when no profiling is recorded
   cudaGraphExec_t graph_exec = nullptr;
   double graph_dt = 0;
-  int graph_n = 0, graph_kc = 0, graph_bs = 0, graph_tma = -1;
+  int graph_n = 0, graph_kc = 0, graph_bs = 0, graph_tma = -1, graph_energy = -1;
   std::unique_ptr<SolveMaps> smaps;   // null where the staged solve does not apply
   // second stream for the kernels of a stage that run beside others, forked
   // from and joined to the state's stream by events (null: everything on the
@@ -180,10 +197,11 @@ struct Impl : ImplBase {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
     graph_exec = nullptr;
   }
+  int energy_key() const { return energy_fix * 2 + (budget_cap > 0 ? 1 : 0); }
   int step(int n_large, int n_small, double dt) override {
     if (use_graph && stream != nullptr && !prof_on && n_large > 0) {
       if (!graph_exec || graph_dt != dt || graph_n != n_small || graph_kc != kchunk || graph_bs != block ||
-          graph_tma != solve_tma) {
+          graph_tma != solve_tma || graph_energy != energy_key()) {
         drop_graph();
         cudaGraph_t g = nullptr;
         long long before = launches;
@@ -208,6 +226,7 @@ struct Impl : ImplBase {
         graph_kc = kchunk;
         graph_bs = block;
         graph_tma = solve_tma;
+        graph_energy = energy_key();
       }
       for (int i = 0; i < n_large; ++i) {
         if (cudaGraphLaunch(graph_exec, stream)) return -3;

@@ -12,6 +12,7 @@
 // float64 tridiagonal elimination with two warps per 32 columns.
 #include "../../include/thor.h"
 #include "thor_impl.cuh"
+#include "thor_reduce.cuh"
 
 #include <utility>
 
@@ -708,6 +709,64 @@ __device__ __forceinline__ void d_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, W
   }
 }
 
+// ---------------------------------------------------------------- energy budget and fixer
+//
+// Sec. 3 (after Eq. pressure): an energy fixer after Williamson (2009) that
+// adjusts the internal energy by the same amount at every grid point. Once per
+// large step (reading F-1) the global diagnostics are reduced at the start of
+// the step (fin0) and after the three RK3 stages (fin1); the fixer raises the
+// temperature of every cell by dT = (E_start - E_dyn) / (c_v sum V rho) at
+// fixed rho and momentum, before the physics. The budget records, per large
+// step, mass, energy and axial angular momentum at both points and dT.
+
+// one thread: dT (0 without the fixer) into fix[0] (float64) and fixf[0]
+// (storage type), and the step's budget row if recording
+template <typename R>
+__global__ void k_energy_prepare(const double* fin0, const double* fin1, double cv, int do_fix, double* fix,
+                                 R* fixf, double* budget, int* count, int cap) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double dT = do_fix ? (fin0[1] - fin1[1]) / (cv * fin1[0]) : 0.0;
+  fix[0] = dT;
+  fixf[0] = (R)dT;
+  if (budget) {
+    const int n = *count;
+    if (n < cap) {
+      double* row = budget + (size_t)n * 8;
+      row[0] = fin0[0];
+      row[1] = fin0[1];
+      row[2] = fin0[2];
+      row[3] = fin1[0];
+      row[4] = fin1[1];
+      row[5] = fin1[2];
+      row[6] = dT;
+      row[7] = 0.0;
+      *count = n + 1;
+    }
+  }
+}
+
+// every cell: T -> T + dT at fixed rho, i.e. rho theta (Eq. pressure, in
+// deviation form) scaled by (1 + dT / T)^(1 / gamma)
+template <typename R>
+__global__ void k_energy_fix(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, const R* fixf, int kchunk) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= G.ncol) return;
+  const int S = G.colp;
+  const R dT = ld(fixf);
+  const R gamma = pc<R>(ph.gamma, ph.gamma_f), inv_gamma = pc<R>(ph.inv_gamma, ph.inv_gamma_f),
+          inv_Rd = pc<R>(ph.inv_Rd, ph.inv_Rd_f);
+  const int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
+  for (int k = k0; k < k1; ++k) {
+    const int i = k * S + c;
+    const R thp = ld(X.th + i);
+    const R rho = ld(U.rhob + k) + ld(X.rho + i);
+    const R p = ld(U.pb + k) + eos_dev<R>(ld(U.pb + k), ld(U.thb + k), thp, gamma);
+    const R Temp = p / rho * inv_Rd;
+    const R th = ld(U.thb + k) + thp;
+    X.th[i] = thp + th * rexpm1<R>(rlog1p<R>(dT / Temp) * inv_gamma);
+  }
+}
+
 // ---------------------------------------------------------------- kernels: one state
 
 template <typename R>
@@ -737,10 +796,12 @@ template <typename R>
 __global__ void k_ss_grad(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, int kchunk) {
   d_ss_grad<R>(G, U, T, dsrc, kchunk, blockIdx.x, blockIdx.y);
 }
-template <typename R>
+// LAST: the last small step of a stage (a separate instantiation, so the
+// other small steps carry no registers for the stage end)
+template <typename R, bool LAST>
 __global__ void k_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, R Kd, int divdamp,
-                         Xf<R> Xs, Xf<R> Xo, int last, int kchunk) {
-  d_ss_mom<R>(G, U, SL, P, T, dtau, Kd, divdamp, Xs, Xo, last, kchunk, blockIdx.x, blockIdx.y);
+                         Xf<R> Xs, Xf<R> Xo, int kchunk) {
+  d_ss_mom<R>(G, U, SL, P, T, dtau, Kd, divdamp, Xs, Xo, LAST ? 1 : 0, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
 __global__ void k_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, int kchunk) {
@@ -1100,6 +1161,17 @@ int Impl<R>::large_step(double dt, int n_small) {
   // the first small step's stencils. With per-kernel profiling everything
   // stays on the state's stream, in the same order.
   const bool fork = side != nullptr && !prof_on;
+  const bool energy = (energy_fix || budget_cap > 0) && fixbuf != nullptr;
+  double* fin0 = fixbuf + kDiagBlocks * 8;                       // reduction at the step start
+  double* part1 = fixbuf + (kDiagBlocks + 1) * 8;
+  double* fin1 = part1 + kDiagBlocks * 8;                        // after the dynamics
+  double* fixv = fin1 + 8;
+  R* fixf = reinterpret_cast<R*>(fixv + 1);
+  if (energy) {
+    chk(launch_k(k_diag_partial<R>, kDiagBlocks, kDiagThreads, 0, stream, G, V, ph, Xt, fixbuf));
+    chk(launch_k(k_diag_final, 1, 256, 0, stream, fixbuf, kDiagBlocks));
+    launches += 2;
+  }
   for (int s = 0; s < 3; ++s) {
     Xf<R> Xs = s == 0 ? Xt : Xst, Xo = s == 2 ? Xt : Xst;
     cudaStream_t aux = fork ? side : stream;
@@ -1159,7 +1231,8 @@ int Impl<R>::large_step(double dt, int n_small) {
       // the last small step of a stage also ends the stage: X^(s+1) = X^(s) + X*
       const int last = j + 1 == nsub[s];
       mark(THOR_K_SS_MOM, true);
-      chk(launch_k(k_ss_mom<R>, g2, bs, 0, stream, G, U, SL, P, T, (R)dts[s], Kd, divdamp, Xs, Xo, last, kc));
+      chk(launch_k(last ? k_ss_mom<R, true> : k_ss_mom<R, false>, g2, bs, 0, stream, G, U, SL, P, T, (R)dts[s], Kd,
+                   divdamp, Xs, Xo, kc));
       mark(THOR_K_SS_MOM, false);
       const int want_div = divdamp && !last;
       mark(THOR_K_SS_FLUX, true);
@@ -1174,6 +1247,17 @@ int Impl<R>::large_step(double dt, int n_small) {
                      want_div, Xo, last));
       mark(THOR_K_SS_COL, false);
       launches += 3;
+    }
+  }
+  if (energy) {
+    chk(launch_k(k_diag_partial<R>, kDiagBlocks, kDiagThreads, 0, stream, G, V, ph, Xt, part1));
+    chk(launch_k(k_diag_final, 1, 256, 0, stream, part1, kDiagBlocks));
+    chk(launch_k(k_energy_prepare<R>, 1, 32, 0, stream, (const double*)fin0, (const double*)fin1, ph.cv,
+                 energy_fix, fixv, fixf, budget_cap > 0 ? budget : (double*)nullptr, budget_count, budget_cap));
+    launches += 3;
+    if (energy_fix) {
+      chk(launch_k(k_energy_fix<R>, g2, bs, 0, stream, G, U, ph, Xt, (const R*)fixf, kc));
+      ++launches;
     }
   }
   if (forcing != 0) {

@@ -60,6 +60,13 @@ def test_ensemble_argument_checks_need_no_device():
         with pytest.raises(thor.ThorError) as e:
             thor.thor_convert_selftest(n)
         assert e.value.status == thor.THOR_EINVAL
+    with pytest.raises(thor.ThorError) as e:
+        thor.thor_budget_read(None)
+    assert e.value.status == thor.THOR_EINVAL
+    for knob in (thor.THOR_TUNE_ENERGY_FIXER, thor.THOR_TUNE_BUDGET):
+        with pytest.raises(thor.ThorError) as e:
+            thor.thor_tune(None, knob, 1)
+        assert e.value.status == thor.THOR_EINVAL
 
 
 def _match(P, O):
