@@ -172,7 +172,7 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   X(I.Xst);
   Work<R>& T = I.T;
   R** cen[] = {&T.pp, &T.Tp, &T.theta, &T.vx, &T.vy, &T.vz, &T.vhx, &T.vhy, &T.vhz,
-               &T.qrho, &T.qvx, &T.qvy, &T.qvz, &T.qT, &T.dd, &T.dd0, &T.gx, &T.gy, &T.gz,
+               &T.qrho, &T.qvx, &T.qvy, &T.qvz, &T.qT, &T.dd, &T.dd0,
                &T.ca, &T.cb, &T.cc, &T.dhm};
   for (R** p : cen) *p = cv.take<R>(C);
   T.vr = cv.take<R>(F);
@@ -184,8 +184,10 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   SL.sw = cv.take<R>(F);
   SL.thi = cv.take<R>(F);
   Pert<R>& P = I.P;
-  R** pc[] = {&P.rho, &P.mx, &P.my, &P.mz, &P.th, &P.p};
+  R** pc[] = {&P.rho, &P.th, &P.p};
   for (R** p : pc) *p = cv.take<R>(C);
+  P.m4 = cv.take<R>(4 * C);
+  T.g4 = cv.take<R>(4 * C);
   P.w = cv.take<R>(F);
   I.F.inv = cv.take<double>(F);
   I.F.cf = cv.take<double>(F);

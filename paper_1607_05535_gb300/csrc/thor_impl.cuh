@@ -22,7 +22,7 @@ struct Work {
   R *qvr;                          // interfaces
   R *dd;                           // 3-D divergence (small step)
   R *dd0;                          // 3-D divergence of X^t (first small step of every stage)
-  R *gx, *gy, *gz;                 // its horizontal gradient
+  R *g4;                           // [nv][colp][4]: its horizontal gradient (x, y, z) and p*
   R *ca, *cb, *cc;                 // per-cell parts of the column equations (a, b, c)
   R *dhm;                          // horizontal divergence of the new M*
   R *psurf;                        // [colp] surface pressure (physics)
@@ -38,7 +38,8 @@ struct Slow {
 // Small-step perturbations Phi* = Phi - Phi^(s)
 template <typename R>
 struct Pert {
-  R *rho, *mx, *my, *mz, *th, *p;  // centres
+  R *rho, *th, *p;                 // centres
+  R *m4;                           // [nv][colp][4]: M* (x, y, z) and theta of the stage state
   R *w;                            // interfaces
 };
 

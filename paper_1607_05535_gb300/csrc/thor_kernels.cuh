@@ -192,6 +192,30 @@ __device__ __forceinline__ double rcp64_1(double x) {
 template <typename T>
 __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
+// Four values of one cell stored together ([level][colp][4] planes), so that
+// a stencil gathers them with one 16-byte (float) or two 16-byte (double)
+// loads per neighbour instead of four.
+template <typename R>
+struct Q4 {
+  R x, y, z, w;
+};
+__device__ __forceinline__ Q4<float> ld4(const float* base, size_t cell) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(base) + cell);
+  return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Q4<double> ld4(const double* base, size_t cell) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(base) + 2 * cell);
+  const double2 b = __ldg(reinterpret_cast<const double2*>(base) + 2 * cell + 1);
+  return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void st4(float* base, size_t cell, float x, float y, float z, float w) {
+  reinterpret_cast<float4*>(base)[cell] = make_float4(x, y, z, w);
+}
+__device__ __forceinline__ void st4(double* base, size_t cell, double x, double y, double z, double w) {
+  reinterpret_cast<double2*>(base)[2 * cell] = make_double2(x, y);
+  reinterpret_cast<double2*>(base)[2 * cell + 1] = make_double2(z, w);
+}
+
 struct Nbr7 {
   int n[7];
 };

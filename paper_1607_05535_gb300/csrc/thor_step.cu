@@ -249,9 +249,8 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
     // stage start (unless k_stage_init does it)
     if (init && k < G.nv) {
       P.rho[i] = ld(Xt.rho + (i)) - ld(X.rho + (i));
-      P.mx[i] = ld(Xt.mx + (i)) - ld(X.mx + (i));
-      P.my[i] = ld(Xt.my + (i)) - ld(X.my + (i));
-      P.mz[i] = ld(Xt.mz + (i)) - ld(X.mz + (i));
+      st4(P.m4, i, ld(Xt.mx + (i)) - ld(X.mx + (i)), ld(Xt.my + (i)) - ld(X.my + (i)),
+          ld(Xt.mz + (i)) - ld(X.mz + (i)), ld(T.theta + (i)));
       P.th[i] = ld(Xt.th + (i)) - ld(X.th + (i));
       R ppt = eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), ld(Xt.th + (i)), gamma);
       P.p[i] = ppt - ld(T.pp + (i));
@@ -277,7 +276,8 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
 // The perturbations at the start of a stage on their own (the state's step
 // runs this beside the slow terms): Phi* = Phi^t - Phi^(s), p* from the
 // nonlinear Eq. theta_to_p; all zero in the first stage, where Phi^(s) =
-// Phi^t and p^(s) = EOS(Th^t).
+// Phi^t and p^(s) = EOS(Th^t). M* goes into the packed plane with theta of
+// the stage state beside it (the column fluxes gather both).
 template <typename R>
 __device__ __forceinline__ void d_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Pert<R> P,
                                              int zero, int kchunk, int bx, int by) {
@@ -291,12 +291,12 @@ __device__ __forceinline__ void d_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> X
     const int i = k * S + c;
     if (k < G.nv) {
       if (zero) {
-        P.rho[i] = P.mx[i] = P.my[i] = P.mz[i] = P.th[i] = P.p[i] = R(0);
+        P.rho[i] = P.th[i] = P.p[i] = R(0);
+        st4(P.m4, i, R(0), R(0), R(0), ld(T.theta + (i)));
       } else {
         P.rho[i] = ld(Xt.rho + (i)) - ld(X.rho + (i));
-        P.mx[i] = ld(Xt.mx + (i)) - ld(X.mx + (i));
-        P.my[i] = ld(Xt.my + (i)) - ld(X.my + (i));
-        P.mz[i] = ld(Xt.mz + (i)) - ld(X.mz + (i));
+        st4(P.m4, i, ld(Xt.mx + (i)) - ld(X.mx + (i)), ld(Xt.my + (i)) - ld(X.my + (i)),
+            ld(Xt.mz + (i)) - ld(X.mz + (i)), ld(T.theta + (i)));
         P.th[i] = ld(Xt.th + (i)) - ld(X.th + (i));
         R ppt = eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), ld(Xt.th + (i)), gamma);
         P.p[i] = ppt - ld(T.pp + (i));
@@ -311,8 +311,10 @@ __device__ __forceinline__ void d_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> X
 template <typename R>
 // horizontal gradient G = grad_h D of the 3-D divergence D of the total
 // momentum (divergence damping, Sec. 4): D is d0 in the first small step of a
-// stage and, later, the D the previous column step formed
-__device__ __forceinline__ void d_ss_grad(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, int kchunk, int bx, int by) {
+// stage and, later, the D the previous column step formed; stored packed with
+// the cell's p*
+__device__ __forceinline__ void d_ss_grad(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, const R* pstar, int kchunk,
+                                          int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -325,9 +327,8 @@ __device__ __forceinline__ void d_ss_grad(Geo<R> G, VR<R> U, Work<R> T, const R*
     R gx, gy, gz;
     grad7(wg, nb, dsrc + o, gx, gy, gz);
     R inv_r = ld(U.inv_rc + (k));
-    T.gx[i] = gx * inv_r;
-    T.gy[i] = gy * inv_r;
-    T.gz[i] = gz * inv_r;
+    // p* of the cell beside G: the momentum step gathers both
+    st4(T.g4, i, gx * inv_r, gy * inv_r, gz * inv_r, ld(pstar + (i)));
   }
 }
 
@@ -351,22 +352,34 @@ __device__ __forceinline__ void d_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> 
     const int o = k * S, i = o + c;
     R inv_r = ld(U.inv_rc + (k));
     R ddx = 0, ddy = 0, ddz = 0;
+    R gx = 0, gy = 0, gz = 0;
     if (divdamp) {
+      // one packed gather per neighbour: G for the Laplacian, p* for the gradient
+      R ax = 0, ay = 0, az = 0;
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        const Q4<R> q = ld4(T.g4, (size_t)(o + nb.n[j]));
+        ax += wl.v[j] * q.x;
+        ay += wl.v[j] * q.y;
+        az += wl.v[j] * q.z;
+        gx += wg.x[j] * q.w;
+        gy += wg.y[j] * q.w;
+        gz += wg.z[j] * q.w;
+      }
       R s = -Kd * ld(U.inv_rc2 + (k));
-      ddx = s * apply7(wl, nb, T.gx + o);
-      ddy = s * apply7(wl, nb, T.gy + o);
-      ddz = s * apply7(wl, nb, T.gz + o);
+      ddx = s * ax;
+      ddy = s * ay;
+      ddz = s * az;
       project(rx, ry, rz, ddx, ddy, ddz);
+    } else {
+      grad7(wg, nb, P.p + o, gx, gy, gz);
     }
-    R gx, gy, gz;
-    grad7(wg, nb, P.p + o, gx, gy, gz);
-    R mx = ld(P.mx + (i)) + dtau * (-gx * inv_r + ddx + ld(SL.smx + (i)));
-    R my = ld(P.my + (i)) + dtau * (-gy * inv_r + ddy + ld(SL.smy + (i)));
-    R mz = ld(P.mz + (i)) + dtau * (-gz * inv_r + ddz + ld(SL.smz + (i)));
+    const Q4<R> m = ld4(P.m4, (size_t)i);
+    R mx = m.x + dtau * (-gx * inv_r + ddx + ld(SL.smx + (i)));
+    R my = m.y + dtau * (-gy * inv_r + ddy + ld(SL.smy + (i)));
+    R mz = m.z + dtau * (-gz * inv_r + ddz + ld(SL.smz + (i)));
     project(rx, ry, rz, mx, my, mz);
-    P.mx[i] = mx;
-    P.my[i] = my;
-    P.mz[i] = mz;
+    st4(P.m4, i, mx, my, mz, m.w);
     if (last) {          // end of the stage: M^(s+1) = M^(s) + M*
       Xo.mx[i] = ld(Xs.mx + (i)) + mx;
       Xo.my[i] = ld(Xs.my + (i)) + my;
@@ -392,10 +405,10 @@ __device__ __forceinline__ FluxCell<R> flux_cell(const W7x3<R>& wd, const Nbr7& 
   R dh = 0, dht = 0;
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
-    const int q = o + nb.n[j];
-    R f = wd.x[j] * ld(P.mx + (q)) + wd.y[j] * ld(P.my + (q)) + wd.z[j] * ld(P.mz + (q));
+    const Q4<R> m = ld4(P.m4, (size_t)(o + nb.n[j]));    // M* and theta of the neighbour
+    R f = wd.x[j] * m.x + wd.y[j] * m.y + wd.z[j] * m.z;
     dh += f;
-    dht += ld(T.theta + (q)) * f;
+    dht += m.w * f;
   }
   const R inv_r = ld(U.inv_rc + (k));
   const R thk = ld(P.th + (i));
@@ -793,8 +806,8 @@ __global__ void k_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work
   d_stage_init<R>(G, U, ph, Xt, X, T, P, zero, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
-__global__ void k_ss_grad(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, int kchunk) {
-  d_ss_grad<R>(G, U, T, dsrc, kchunk, blockIdx.x, blockIdx.y);
+__global__ void k_ss_grad(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, const R* pstar, int kchunk) {
+  d_ss_grad<R>(G, U, T, dsrc, pstar, kchunk, blockIdx.x, blockIdx.y);
 }
 // LAST: the last small step of a stage (a separate instantiation, so the
 // other small steps carry no registers for the stage end)
@@ -1071,7 +1084,7 @@ template <typename R>
 __global__ void ke_ss_grad(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int j,
                            int kchunk) {
   THOR_MEMBER();
-  if (a.divdamp) d_ss_grad<R>(a.G, a.U, a.T, j == 0 ? a.T.dd0 : a.T.dd, kchunk, e.y, blockIdx.y);
+  if (a.divdamp) d_ss_grad<R>(a.G, a.U, a.T, j == 0 ? a.T.dd0 : a.T.dd, a.P.p, kchunk, e.y, blockIdx.y);
 }
 template <typename R>
 __global__ void ke_ss_mom(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int j,
@@ -1190,7 +1203,7 @@ int Impl<R>::large_step(double dt, int n_small) {
     const bool early_grad = divdamp && s > 0;    // D of X^t is ready before the slow terms
     if (early_grad) {
       mark(THOR_K_SS_GRAD, true);
-      chk(launch_k(k_ss_grad<R>, g2, bs, 0, aux, G, U, T, (const R*)T.dd0, kc));
+      chk(launch_k(k_ss_grad<R>, g2, bs, 0, aux, G, U, T, (const R*)T.dd0, (const R*)P.p, kc));
       mark(THOR_K_SS_GRAD, false);
       ++launches;
     }
@@ -1224,7 +1237,8 @@ int Impl<R>::large_step(double dt, int n_small) {
       // D: of X^t in the first small step, then from the previous column step
       if (divdamp && !(j == 0 && early_grad)) {
         mark(THOR_K_SS_GRAD, true);
-        chk(launch_k(k_ss_grad<R>, g2, bs, 0, stream, G, U, T, (const R*)(j == 0 ? T.dd0 : T.dd), kc));
+        chk(launch_k(k_ss_grad<R>, g2, bs, 0, stream, G, U, T, (const R*)(j == 0 ? T.dd0 : T.dd), (const R*)P.p,
+                     kc));
         mark(THOR_K_SS_GRAD, false);
         ++launches;
       }
