@@ -23,6 +23,8 @@ physics     Sec. 5-6: Eqs. im_eq_v, im_eq_t with the Held-Suarez (Eq.
             im_eq_fv and T_eq, K_T) and hot-Jupiter (Eqs. teq-hj, btrop, tvert)
             forcings.
 diagnostics Global mass, energy, axial angular momentum and extrema (Sec. 3).
+climate     Sec. 6.1: zonal band means of wind, temperature and pressure and
+            the eddy covariances [u'v'], [v'T'] of one state.
 energy      Sec. 3: the globally uniform internal-energy adjustment after
             Williamson (2009) and the per-step mass, energy and angular
             momentum budget.
