@@ -216,6 +216,31 @@ int thor_tune(thor_state* state, int knob, int value);
  * (axial angular momentum reaching a statistically steady value). */
 int thor_budget_read(thor_state* state, double* out, int max_rows, int* n_rows);
 
+/* Zonal band means (Sec. 6.1: the climates are judged by zonal and time
+ * averages of wind and temperature, the mass stream function built from the
+ * averaged northward wind, and the eddy fluxes [u'v'], [v'T'] with
+ * phi' = phi - zonal mean of phi). A zonal mean is the volume-weighted mean
+ * over the cells of one level whose latitude falls in one of nlat equal
+ * bands, band b = floor((lat + pi/2 + 1e-9) / pi * nlat) (the north pole in
+ * the last band; a cell on a band edge, such as the equatorial cells, goes
+ * north). thor_zonal_accumulate adds, for the current state, per level k and
+ * band b the 9 values
+ *   [V, u, v, T, p, u'v', v'T', u'u', v'v']
+ * (V the band's volume, u and v the eastward and northward components of
+ * M / rho, 0 at the two polar cells, then their band means, T and p, then
+ * the band covariances) to the state's accumulator, on the state's stream
+ * without synchronising; nlat in [1, 360], else THOR_EINVAL. The first call
+ * for a given nlat synchronises the stream, allocates the accumulator
+ * (about 150 * nv * nlat bytes plus 28 bytes per column) and clears it.
+ * thor_zonal_read copies the accumulated sums, layout
+ * [nv][nlat][9] float64 (n must be nv * nlat * 9), and the number of states
+ * accumulated; with reset != 0 it then clears them. Divide by the sample
+ * count for time means. A read for an nlat that was never accumulated
+ * returns zeros and 0 samples. thor_zonal_read synchronises the state's
+ * stream. */
+int thor_zonal_accumulate(thor_state* state, int nlat);
+int thor_zonal_read(thor_state* state, int nlat, double* out, size_t n, int reset, long long* samples);
+
 /* THOR_TUNE_BLOCK: threads (one per column) in a block of the stencil
  * kernels, a multiple of 32 in [32, 256] (default 128).
  * THOR_TUNE_SOLVE_TMA: 1 (default) runs the column solve of a THOR_MIXED

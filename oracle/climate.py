@@ -8,11 +8,15 @@ from the averaged northward wind (Eq. for Psi), and the eddy fluxes
 [u'v'] and [v'T'] with phi' = phi - (zonal mean of phi). Reading C-1: on the
 icosahedral grid a zonal mean is the volume-weighted mean over the cells of
 one level whose latitude falls in one of nlat equal latitude bands (band
-b = floor((lat + pi/2) / pi * nlat), the north pole in the last band); the
+b = floor((lat + pi/2 + 1e-9) / pi * nlat), the north pole in the last band;
+the 1e-9 rad puts a cell that sits on a band edge, such as the grid's
+equatorial cells, in the band north of it whatever the last bits of its
+coordinates); the
 eddy terms are the band covariances [ab] - [a][b] of one state, averaged in
 time by the caller. u and v are the eastward and northward components of
-M / rho (the horizontal velocity), T and p follow from Eq. pressure and the
-ideal gas.
+M / rho (the horizontal velocity; both taken as 0 at the two polar cells,
+where east and north are undefined), T and p follow from Eq. pressure and
+the ideal gas.
 """
 
 import numpy as np
@@ -27,7 +31,7 @@ QUANTITIES = ("weight", "u", "v", "T", "p", "uv", "vT", "uu", "vv")
 def band_of(points, nlat):
     """Latitude band of every column (reading C-1)."""
     _, lat = lonlat(points)
-    return np.minimum(np.floor((lat + 0.5 * np.pi) / np.pi * nlat).astype(int), nlat - 1)
+    return np.minimum(np.floor((lat + 0.5 * np.pi + 1e-9) / np.pi * nlat).astype(int), nlat - 1)
 
 
 def zonal_band_means(model, X, nlat):
@@ -38,6 +42,9 @@ def zonal_band_means(model, X, nlat):
     lon, lat = lonlat(pts)
     east = np.stack([-np.sin(lon), np.cos(lon), np.zeros_like(lon)], axis=-1)
     north = np.stack([-np.sin(lat) * np.cos(lon), -np.sin(lat) * np.sin(lon), np.cos(lat)], axis=-1)
+    polar = np.hypot(pts[:, 0], pts[:, 1]) < 1e-9
+    east[polar] = 0.0
+    north[polar] = 0.0
     vel = X.M / X.rho[..., None]
     u = np.einsum("ckj,cj->ck", vel, east)
     v = np.einsum("ckj,cj->ck", vel, north)

@@ -37,7 +37,7 @@ EXPORTED = [
     "thor_autotune", "thor_ensemble_create", "thor_ensemble_step", "thor_ensemble_info",
     "thor_ensemble_tune", "thor_ensemble_autotune", "thor_ensemble_destroy", "thor_mlp_tune",
     "thor_checkpoint_bytes", "thor_checkpoint_save", "thor_checkpoint_load", "thor_wait_selftest",
-    "thor_convert_selftest", "thor_budget_read",
+    "thor_convert_selftest", "thor_budget_read", "thor_zonal_accumulate", "thor_zonal_read",
 ]
 
 # kernel ids of thor_profile_read
@@ -132,6 +132,8 @@ def _load():
         "thor_wait_selftest": (I, [I, ctypes.c_uint, IP]),
         "thor_convert_selftest": (I, [ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]),
         "thor_budget_read": (I, [P, ctypes.POINTER(D), I, IP]),
+        "thor_zonal_accumulate": (I, [P, I]),
+        "thor_zonal_read": (I, [P, I, ctypes.POINTER(D), Z, I, ctypes.POINTER(ctypes.c_longlong)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -436,3 +438,22 @@ def thor_budget_read(state, max_rows=1 << 16):
     _check(_lib.thor_budget_read(state, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(max_rows),
                                  ctypes.byref(n)), "thor_budget_read")
     return out[:n.value].copy()
+
+
+ZONAL_QUANTITIES = ("weight", "u", "v", "T", "p", "uv", "vT", "uu", "vv")
+
+
+def thor_zonal_accumulate(state, nlat):
+    _check(_lib.thor_zonal_accumulate(state, int(nlat)), "thor_zonal_accumulate")
+
+
+def thor_zonal_read(state, nlat, nv, reset=False):
+    """(sums, samples): sums is a float64 array (nv, nlat, 9) of the
+    accumulated band values ZONAL_QUANTITIES; divide by samples for time
+    means."""
+    import numpy as np
+    out = np.zeros((nv, nlat, 9))
+    n = ctypes.c_longlong()
+    _check(_lib.thor_zonal_read(state, int(nlat), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size,
+                                int(bool(reset)), ctypes.byref(n)), "thor_zonal_read")
+    return out, n.value

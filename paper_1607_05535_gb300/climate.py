@@ -1,0 +1,150 @@
+"""Long runs with zonal and time averages (Sec. 6): the Held-Suarez and
+hot-Jupiter climates.
+
+The library steps the state on the GPU and accumulates zonal band means of
+the wind, temperature, pressure and eddy covariances on the device
+(thor_zonal_accumulate). This module only drives those calls and turns the
+accumulated band means (nv x nlat values) into the quantities Sec. 6.1
+discusses: the position and speed of the jets, the mass stream function
+Psi = (2 pi A cos(lat) / g) * integral from the top of the time- and zonal-mean
+northward wind over pressure, and the eddy fluxes [u'v'] and [v'T'].
+
+    python -m paper_1607_05535_gb300.climate --days 1200 --spinup 200 --out run.json
+
+Default: the paper's Held-Suarez run (glevel 5, 37 levels to 32 km, dt
+1000 s, 6 acoustic small steps), from an isothermal 300 K atmosphere at rest
+with 0.1 K of seeded noise (one of the starts Sec. 6.1 lists), mixed
+precision.
+"""
+
+import argparse
+import json
+import math
+import sys
+import time
+
+
+def run(thor, glevel=5, nv=37, z_top=32.0e3, dt=1000.0, n_small=6, days=1200.0, spinup_days=200.0, nlat=36,
+        sample_hours=24.0, forcing="held_suarez", precision="mixed", seed=1234, hj_dT=300.0, stream=None):
+    """Steps the workload, accumulates one zonal sample every sample_hours
+    after the spin-up, and returns (time means (nv, nlat, 9), samples,
+    seconds of stepping)."""
+    import workloads as wls
+    P = wls.EARTH if forcing == "held_suarez" else wls.HOT_JUPITER
+    fid = {"none": 0, "held_suarez": 1, "hot_jupiter": 2}[forcing]
+    prec = thor.THOR_FP64 if precision == "fp64" else thor.THOR_MIXED
+    grid = thor.thor_grid_create(glevel, nv, P.radius, z_top, thor.thor_spring(1.15, 1.0, 1.0, 0.01, 1e-5, 100000))
+    planet = thor.thor_planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+    T0, ps = (300.0, 1.0e5) if forcing != "hot_jupiter" else (1600.0, 2.2e7)
+    init = thor.thor_init(T0, ps, 0.1, seed, fid, hj_dT, prec, 1, 1)
+    st = thor.thor_state_init(grid, planet, init, stream)
+    try:
+        per_sample = max(1, round(sample_hours * 3600.0 / dt))
+        spin = round(spinup_days * 86400.0 / dt)
+        total = round(days * 86400.0 / dt)
+        t0 = time.perf_counter()
+        done = 0
+        while done < spin:
+            n = min(per_sample * 10, spin - done)
+            thor.thor_step(st, n, n_small, dt)
+            done += n
+        while done + per_sample <= total:
+            thor.thor_step(st, per_sample, n_small, dt)
+            done += per_sample
+            thor.thor_zonal_accumulate(st, nlat)
+        sums, samples = thor.thor_zonal_read(st, nlat, nv)
+        seconds = time.perf_counter() - t0
+        diag = thor.thor_diag(st)
+    finally:
+        thor.thor_state_destroy(st)
+        thor.thor_grid_destroy(grid)
+    means = sums / max(samples, 1)
+    return means, samples, seconds, diag
+
+
+def summarize(means, radius, gravity):
+    """The Sec. 6.1 quantities from time-mean band values (nv, nlat, 9)."""
+    import numpy as np
+    nv, nlat, _ = means.shape
+    lat = (np.arange(nlat) + 0.5) * 180.0 / nlat - 90.0
+    u, v, T, p = means[..., 1], means[..., 2], means[..., 3], means[..., 4]
+    uv, vT = means[..., 5], means[..., 6]
+    eke = 0.5 * (means[..., 7] + means[..., 8])
+    out = {"lat": lat.tolist()}
+    jets = {}
+    for name, sel in (("north", lat > 0), ("south", lat < 0)):
+        uu = np.where(sel[None, :], u, -np.inf)
+        k, b = np.unravel_index(np.argmax(uu), uu.shape)
+        jets[name] = {"u_ms": float(u[k, b]), "lat_deg": float(lat[b]), "p_hPa": float(p[k, b] / 100.0),
+                      "level": int(k)}
+    out["jets"] = jets
+    eq = np.argsort(np.abs(lat))[:2]
+    out["surface_u_equator_ms"] = float(u[0, eq].mean())
+    out["surface_u_poleward_60_ms"] = float(u[0, np.abs(lat) > 60].mean())
+    # mass stream function from the top down; the pressure thickness of a
+    # level from the mean pressures of its neighbours (one spacing at the
+    # lowest and highest level)
+    dp = np.zeros_like(p)
+    if nv > 1:
+        dp[1:-1] = 0.5 * (p[:-2] - p[2:])
+        dp[0] = p[0] - p[1]
+        dp[-1] = p[-2] - p[-1]
+    psi = np.cumsum((v * dp)[::-1], axis=0)[::-1] * (2 * math.pi * radius * np.cos(np.radians(lat))[None, :] /
+                                                     gravity)
+    out["psi_max_kg_s"] = float(psi.max())
+    out["psi_min_kg_s"] = float(psi.min())
+    out["psi_max_lat_deg"] = float(lat[np.unravel_index(np.argmax(psi), psi.shape)[1]])
+    out["psi_min_lat_deg"] = float(lat[np.unravel_index(np.argmin(psi), psi.shape)[1]])
+    mid_n, mid_s = (lat > 20) & (lat < 60), (lat < -20) & (lat > -60)
+    out["eddy_uv_north_max"] = float(uv[:, mid_n].max())
+    out["eddy_uv_south_min"] = float(uv[:, mid_s].min())
+    low = p.mean(axis=1) > 6.0e4                      # levels below about 600 hPa
+    out["eddy_vT_north_low_mean"] = float(vT[low][:, mid_n].mean())
+    out["eddy_vT_south_low_mean"] = float(vT[low][:, mid_s].mean())
+    out["eke_max"] = float(eke.max())
+    out["u_zonal_mean"] = u.tolist()
+    out["T_zonal_mean"] = T.tolist()
+    out["p_zonal_mean"] = p.tolist()
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--forcing", default="held_suarez", choices=["held_suarez", "hot_jupiter"])
+    ap.add_argument("--glevel", type=int, default=5)
+    ap.add_argument("--nv", type=int, default=37)
+    ap.add_argument("--z-top", type=float, default=32.0e3)
+    ap.add_argument("--dt", type=float, default=1000.0)
+    ap.add_argument("--n-small", type=int, default=6)
+    ap.add_argument("--days", type=float, default=1200.0)
+    ap.add_argument("--spinup", type=float, default=200.0)
+    ap.add_argument("--nlat", type=int, default=36)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args(argv)
+    import torch
+    import paper_1607_05535_gb300 as thor
+    import workloads as wls
+    if not torch.cuda.is_available():
+        raise SystemExit("a CUDA device is required")
+    torch.cuda.set_device(0)
+    s = torch.cuda.Stream()
+    means, samples, seconds, diag = run(thor, args.glevel, args.nv, args.z_top, args.dt, args.n_small, args.days,
+                                        args.spinup, args.nlat, forcing=args.forcing, precision=args.precision,
+                                        stream=s.cuda_stream)
+    P = wls.EARTH if args.forcing == "held_suarez" else wls.HOT_JUPITER
+    summary = summarize(means, P.radius, P.gravity)
+    summary.update({"config": vars(args), "samples": samples, "seconds": seconds,
+                    "large_steps": round(args.days * 86400.0 / args.dt),
+                    "final_diag": {k: diag[k] for k in ("mass", "energy", "aam", "max_vh", "nonfinite")}})
+    text = json.dumps(summary)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(text)
+    short = {k: v for k, v in summary.items() if k not in ("u_zonal_mean", "T_zonal_mean", "p_zonal_mean", "lat")}
+    print(json.dumps(short))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

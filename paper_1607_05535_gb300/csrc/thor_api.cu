@@ -827,6 +827,8 @@ int thor_profile_read(thor_state* s, int kernel, double* total_ms, long long* la
 void thor_state_destroy(thor_state* s) {
   if (!s) return;
   thor::closure_release(s);
+  if (s->impl) cudaStreamSynchronize(s->impl->stream);
+  thor::zonal_release(s->zonal);
   delete s;
 }
 

@@ -21,15 +21,27 @@ struct ClosureBinding {
   long long counter = 0;              // large steps since attach
 };
 
+// zonal band means accumulated over time (thor_zonal_accumulate)
+struct ZonalAcc {
+  int nlat = 0;                       // bands (0: nothing allocated)
+  int* band = nullptr;                // [colp] band of every column
+  double* basis = nullptr;            // [6][colp] east and north unit vectors
+  double* tmp = nullptr;              // [nv][nlat][9] sums of one state
+  double* acc = nullptr;              // [nv][nlat][9] accumulated band means and covariances
+  long long samples = 0;
+};
+
 struct thor_state {
   thor_grid* grid = nullptr;
   int precision = THOR_FP64;
   int check_finite = 0;
   ClosureBinding closure;
+  ZonalAcc zonal;
   std::unique_ptr<thor::ImplBase> impl;
 };
 
 namespace thor {
 int closure_large_step(thor_state* s, int n_small, double dt);   // thor_mlp.cu
 void closure_release(thor_state* s);
+void zonal_release(ZonalAcc& z);                                  // thor_climate.cu
 }
