@@ -210,19 +210,62 @@ def _config(wl, precision):
             "l2": "inputs larger than L2: state + stage work set at g6x32 exceed 129 MB"}
 
 
+# ------------------------------------------------------------------ ranks
+
+class Ranks:
+    """The replicas of a multi-GPU run (one process per GPU under torchrun,
+    RANK / LOCAL_RANK / WORLD_SIZE / MASTER_* from the environment): every
+    rank steps its own atmosphere (the path needs no exchange between
+    replicas), and only the timing is combined: a barrier on both sides of
+    a timed region and the maximum of the ranks' times. NCCL with CUDA,
+    gloo without."""
+
+    def __init__(self):
+        import torch
+        self.world = _env_int("WORLD_SIZE", 1)
+        self.rank = _env_int("RANK", 0)
+        self.local = _env_int("LOCAL_RANK", 0)
+        self.dist = None
+        self.cuda = torch.cuda.is_available()
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl" if self.cuda else "gloo")
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x):
+        """The largest x over the ranks (a float on every rank)."""
+        if self.dist is None:
+            return float(x)
+        import torch
+        dev = torch.device("cuda", self.local) if self.cuda else torch.device("cpu")
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def whole_job_rate(world, units_per_rank, seconds):
+    """Units of all ranks per second of the slowest rank (weak scaling: every
+    rank processes the same units)."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_thor(args):
     import torch
     import paper_1607_05535_gb300 as thor
 
-    world = _env_int("WORLD_SIZE", 1)
-    rank = _env_int("RANK", 0)
-    local = _env_int("LOCAL_RANK", 0)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    ranks = Ranks()
+    world, rank, local, dist = ranks.world, ranks.rank, ranks.local, ranks.dist
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
@@ -237,9 +280,7 @@ def run_thor(args):
         init = thor.thor_init(wl.T0, wl.p_surf, wl.noise_amp, wl.seed, forcing, wl.hj_dT, prec, 1, 1)
         return thor.thor_state_init(grid, planet, init, stream.cuda_stream)
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    barrier = ranks.barrier
 
     def timed(state, steps):
         """CUDA-event time (ms) of ``steps`` large steps on the state's stream."""
@@ -255,12 +296,7 @@ def run_thor(args):
         barrier()
         return a.elapsed_time(b)
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = ranks.max
 
     sn = wl.substeps_per_large
     cells = wl.cells
@@ -294,7 +330,7 @@ def run_thor(args):
     thor.thor_profile(st, 0)
     ms = max_over_ranks(ms)
     diag = thor.thor_diag(st)
-    value = world * cells * sn * args.steps / (ms / 1e3)
+    value = whole_job_rate(world, cells * sn * args.steps, ms / 1e3)
     days_per_hour = world * args.steps * wl.dt / 86400.0 / (ms / 1e3 / 3600.0)
 
     # dominant kernel and its roofline
@@ -344,8 +380,7 @@ def run_thor(args):
     clocks = sampler.stop() if sampler else None
 
     if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
+        ranks.close()
         return 0
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -378,8 +413,7 @@ def run_thor(args):
                        f"({t_small:.1f} s) and one physics call, scaled to 3 slow + {sn} small + "
                        "physics per large step; numpy float64, single thread")}
     print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 

@@ -12,9 +12,10 @@ northward wind over pressure, and the eddy fluxes [u'v'] and [v'T'].
     python -m paper_1607_05535_gb300.climate --days 1200 --spinup 200 --out run.json
 
 Default: the paper's Held-Suarez run (glevel 5, 37 levels to 32 km, dt
-1000 s, 6 acoustic small steps), from an isothermal 300 K atmosphere at rest
-with 0.1 K of seeded noise (one of the starts Sec. 6.1 lists), mixed
-precision.
+1000 s, 6 acoustic small steps, the planet of Table 1), from an isothermal
+300 K atmosphere at rest with 0.1 K of seeded noise (one of the starts
+Sec. 6.1 lists), mixed precision; --forcing hot_jupiter runs Sec. 6.2's
+(37 levels to 4875 km, dt 600 s, isothermal 1600 K at 220 bar).
 """
 
 import argparse
@@ -24,20 +25,30 @@ import sys
 import time
 
 
+def planet(forcing, table1=True):
+    """The planet of a run: Table 1 of the paper (the Sec. 6 runs) or the
+    benchmark workloads' values (which take c_p, R_d and the hot Jupiter's
+    gravity from the benchmark configurations)."""
+    import workloads as wls
+    if forcing == "hot_jupiter":
+        return wls.HOT_JUPITER_TABLE1 if table1 else wls.HOT_JUPITER
+    return wls.EARTH_TABLE1 if table1 else wls.EARTH
+
+
 def run(thor, glevel=5, nv=37, z_top=32.0e3, dt=1000.0, n_small=6, days=1200.0, spinup_days=200.0, nlat=36,
-        sample_hours=24.0, forcing="held_suarez", precision="mixed", seed=1234, hj_dT=300.0, stream=None):
+        sample_hours=24.0, forcing="held_suarez", precision="mixed", seed=1234, hj_dT=300.0, stream=None,
+        table1=True):
     """Steps the workload, accumulates one zonal sample every sample_hours
     after the spin-up, and returns (time means (nv, nlat, 9), samples,
-    seconds of stepping)."""
-    import workloads as wls
-    P = wls.EARTH if forcing == "held_suarez" else wls.HOT_JUPITER
+    seconds of stepping, final diagnostics)."""
+    P = planet(forcing, table1)
     fid = {"none": 0, "held_suarez": 1, "hot_jupiter": 2}[forcing]
     prec = thor.THOR_FP64 if precision == "fp64" else thor.THOR_MIXED
     grid = thor.thor_grid_create(glevel, nv, P.radius, z_top, thor.thor_spring(1.15, 1.0, 1.0, 0.01, 1e-5, 100000))
-    planet = thor.thor_planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+    pl = thor.thor_planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
     T0, ps = (300.0, 1.0e5) if forcing != "hot_jupiter" else (1600.0, 2.2e7)
     init = thor.thor_init(T0, ps, 0.1, seed, fid, hj_dT, prec, 1, 1)
-    st = thor.thor_state_init(grid, planet, init, stream)
+    st = thor.thor_state_init(grid, pl, init, stream)
     try:
         per_sample = max(1, round(sample_hours * 3600.0 / dt))
         spin = round(spinup_days * 86400.0 / dt)
@@ -113,8 +124,10 @@ def main(argv=None):
     ap.add_argument("--forcing", default="held_suarez", choices=["held_suarez", "hot_jupiter"])
     ap.add_argument("--glevel", type=int, default=5)
     ap.add_argument("--nv", type=int, default=37)
-    ap.add_argument("--z-top", type=float, default=32.0e3)
-    ap.add_argument("--dt", type=float, default=1000.0)
+    ap.add_argument("--z-top", type=float, default=None, help="default 32 km (Earth), 4875 km (hot Jupiter)")
+    ap.add_argument("--dt", type=float, default=None, help="default 1000 s (Earth), 600 s (hot Jupiter)")
+    ap.add_argument("--workload-planet", action="store_true",
+                    help="the benchmark workloads' planet values instead of Table 1")
     ap.add_argument("--n-small", type=int, default=6)
     ap.add_argument("--days", type=float, default=1200.0)
     ap.add_argument("--spinup", type=float, default=200.0)
@@ -122,6 +135,11 @@ def main(argv=None):
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
+    hj = args.forcing == "hot_jupiter"
+    if args.z_top is None:
+        args.z_top = 4.875e6 if hj else 32.0e3
+    if args.dt is None:
+        args.dt = 600.0 if hj else 1000.0
     import torch
     import paper_1607_05535_gb300 as thor
     import workloads as wls
@@ -131,8 +149,8 @@ def main(argv=None):
     s = torch.cuda.Stream()
     means, samples, seconds, diag = run(thor, args.glevel, args.nv, args.z_top, args.dt, args.n_small, args.days,
                                         args.spinup, args.nlat, forcing=args.forcing, precision=args.precision,
-                                        stream=s.cuda_stream)
-    P = wls.EARTH if args.forcing == "held_suarez" else wls.HOT_JUPITER
+                                        stream=s.cuda_stream, table1=not args.workload_planet)
+    P = planet(args.forcing, not args.workload_planet)
     summary = summarize(means, P.radius, P.gravity)
     summary.update({"config": vars(args), "samples": samples, "seconds": seconds,
                     "large_steps": round(args.days * 86400.0 / args.dt),

@@ -56,6 +56,11 @@ EARTH = PlanetParams(radius=6.371e6, omega=7.292e-5, gravity=9.8, Rd=287.0, cp=1
                      dt_paper=1000.0, tau_d=6.46e3)
 HOT_JUPITER = PlanetParams(radius=1.0e8, omega=2.1e-5, gravity=9.42, Rd=3779.0, cp=13226.0,
                            dt_paper=600.0, tau_d=941.2)
+# Table 1 of the paper as printed (the long runs of Sec. 6 use these)
+EARTH_TABLE1 = PlanetParams(radius=6.371e6, omega=7.292e-5, gravity=9.8, Rd=287.04, cp=1004.6,
+                            dt_paper=1000.0, tau_d=6.46e3)
+HOT_JUPITER_TABLE1 = PlanetParams(radius=1.0e8, omega=2.1e-5, gravity=8.0, Rd=3779.0, cp=13226.5,
+                                  dt_paper=600.0, tau_d=941.2)
 
 
 @dataclass(frozen=True)
