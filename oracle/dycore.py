@@ -158,6 +158,30 @@ def hyperdiffusion(model, X, p, Kd):
     return F_rho, F_M, F_W, F_Th
 
 
+def _shallow_advection_coriolis(model, X, Wc):
+    """Advection and Coriolis under the shallow-atmosphere approximation of
+    Sec. 3 with the "traditional approximation" it names: reading S-2, only
+    the local vertical component of Omega acts, on the horizontal momentum,
+    C_h = 2 Omega (z . r) r x M_h, and nothing on the vertical momentum;
+    reading S-3, the metric terms that the traditional approximation drops
+    for angular-momentum conservation (u w / r, v w / r in the horizontal,
+    (u^2 + v^2) / r in the vertical equation) are dropped by advecting the
+    horizontal velocity v_h = M / rho in the horizontal equation and w as a
+    scalar in the vertical one. Returns (AC_h at the centres, AC_r at the
+    interfaces)."""
+    g, vg, pl, rhat = model.grid, model.vg, model.planet, model.rhat
+    vh = X.M / X.rho[..., None]
+    w = Wc / X.rho
+    A_h = np.zeros_like(X.M)
+    for j in range(3):
+        A_h[..., j] = op.div_h_levels(g, vg, X.M * vh[..., j:j + 1]) \
+            + op.div_v(vg, X.W * op.interp_to_interfaces(vg, vh[..., j]))
+    A_r = op.div_h_levels(g, vg, X.M * w[..., None]) + op.div_v(vg, X.W * op.interp_to_interfaces(vg, w))
+    f = 2.0 * pl.omega * rhat[:, 2]
+    C_h = f[:, None, None] * np.cross(np.broadcast_to(rhat[:, None, :], X.M.shape), X.M)
+    return op.project_h(rhat, A_h + C_h), op.interp_to_interfaces(vg, A_r)
+
+
 def slow_terms(model, X, Kd):
     """Right-hand sides of Eqs. dens2, mom2, momr2 and pt2 at the stage state
     X = Phi^(s) (reading R1), plus the small-step coefficients."""
@@ -171,16 +195,19 @@ def slow_terms(model, X, Kd):
     mom = X.M + Wc[..., None] * rhat[:, None, :]
     vel = mom / X.rho[..., None]
 
-    # advection A_j = div_h(M v_j) + r^-2 d(r^2 W v_j)/dr
-    A = np.zeros((N, nv, 3))
-    for j in range(3):
-        A[..., j] = op.div_h_levels(g, vg, X.M * vel[..., j:j + 1]) \
-            + op.div_v(vg, X.W * op.interp_to_interfaces(vg, vel[..., j]))
-    # Coriolis 2 Omega x (rho v), Omega along z
-    Om = np.array([0.0, 0.0, pl.omega])
-    C = 2.0 * np.cross(Om[None, None, :], mom)
-    AC_h = op.project_h(rhat, A + C)
-    AC_r = op.interp_to_interfaces(vg, op.radial(rhat, A + C))
+    if vg.shallow:
+        AC_h, AC_r = _shallow_advection_coriolis(model, X, Wc)
+    else:
+        # advection A_j = div_h(M v_j) + r^-2 d(r^2 W v_j)/dr
+        A = np.zeros((N, nv, 3))
+        for j in range(3):
+            A[..., j] = op.div_h_levels(g, vg, X.M * vel[..., j:j + 1]) \
+                + op.div_v(vg, X.W * op.interp_to_interfaces(vg, vel[..., j]))
+        # Coriolis 2 Omega x (rho v), Omega along z
+        Om = np.array([0.0, 0.0, pl.omega])
+        C = 2.0 * np.cross(Om[None, None, :], mom)
+        AC_h = op.project_h(rhat, A + C)
+        AC_r = op.interp_to_interfaces(vg, op.radial(rhat, A + C))
 
     rho_i = op.interp_to_interfaces(vg, X.rho)
 

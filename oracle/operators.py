@@ -142,16 +142,20 @@ class VerticalGrid:
 
     Reading: the paper does not give the layer spacing; we take uniform
     layers, interfaces z_i = i dz (i = 0..nv) and centres z_k = (k + 1/2) dz.
-    r = radius + z. The cell volume is A_c r_k^2 (z_k+1/2 - z_k-1/2)."""
+    r = radius + z. The cell volume is A_c r_k^2 (z_k+1/2 - z_k-1/2).
+    shallow: the shallow-atmosphere approximation of Sec. 3 (1/r replaced by
+    1/A, A the planet radius): r = A at every centre and interface, the
+    heights z unchanged (reading S-1)."""
 
-    def __init__(self, nv, z_top, radius):
+    def __init__(self, nv, z_top, radius, shallow=False):
         self.nv = nv
         self.radius = radius
+        self.shallow = shallow
         self.zi = np.linspace(0.0, z_top, nv + 1)
         self.zc = 0.5 * (self.zi[:-1] + self.zi[1:])
         self.dz = np.diff(self.zi)
-        self.rc = radius + self.zc
-        self.ri = radius + self.zi
+        self.rc = radius + (0.0 if shallow else 1.0) * self.zc
+        self.ri = radius + (0.0 if shallow else 1.0) * self.zi
 
 
 def interp_to_interfaces(vg, x):
