@@ -265,7 +265,7 @@ def run_thor(args):
     import paper_1607_05535_gb300 as thor
 
     ranks = Ranks()
-    world, rank, local, dist = ranks.world, ranks.rank, ranks.local, ranks.dist
+    world, rank, local = ranks.world, ranks.rank, ranks.local
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)

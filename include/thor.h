@@ -110,7 +110,15 @@ typedef struct {
  * (hot Jupiter, day-night contrast hj_dT) physics after each large step.
  * precision: THOR_FP64 (all float64) or THOR_MIXED (float32 fields and
  * stencils, float64 metric terms, vertical solve and reductions).
- * hyperdiffusion / divergence_damping: 1 = on (Sec. 4), 0 = off. */
+ * hyperdiffusion / divergence_damping: 1 = on (Sec. 4), 0 = off.
+ * shallow: 0 (the paper's runs) = deep atmosphere; 1 = the shallow-atmosphere
+ * approximation that Sec. 3 lists among the switches: 1/r replaced by 1/A
+ * (A the grid's radius) in every metric factor and cell volume, Coriolis
+ * from the local vertical component of Omega acting on the horizontal
+ * momentum only ("traditional approximation"), and the metric terms it
+ * drops (u w / r, v w / r, (u^2 + v^2) / r) left out by advecting the
+ * horizontal velocity and w as a scalar; thor_diag's angular momentum then
+ * uses r = A. */
 typedef struct {
   double T0, p_surf, noise_amp;
   unsigned long long seed;
@@ -119,6 +127,7 @@ typedef struct {
   int precision;
   int hyperdiffusion;
   int divergence_damping;
+  int shallow;
 } thor_init;
 
 /* Allocate the device state for `grid` and set the initial condition. The

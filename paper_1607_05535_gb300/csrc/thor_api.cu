@@ -177,6 +177,7 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   for (R** p : cen) *p = cv.take<R>(C);
   T.vr = cv.take<R>(F);
   T.qvr = cv.take<R>(F);
+  T.wc = cv.take<R>(C);
   T.psurf = cv.take<R>(S);
   Slow<R>& SL = I.SL;
   R** sc[] = {&SL.smx, &SL.smy, &SL.smz, &SL.srho, &SL.sth, &SL.dsc, &SL.acr, &SL.pi};
@@ -400,15 +401,16 @@ void host_setup(const HostGrid& h, const thor_planet& pl, const thor_init& in, H
   auto& Rb = hs.vert[16]; auto& ri2 = hs.vert[17]; auto& inv_dzc = hs.vert[18];
   for (int j = 0; j < kNumVertCentre; ++j) hs.vert[j].assign(nv, 0.0);
   for (int j = kNumVertCentre; j < kNumVert; ++j) hs.vert[j].assign(nv + 1, 0.0);
+  const double deep = in.shallow ? 0.0 : 1.0;   // shallow atmosphere: r = radius everywhere
   for (int k = 0; k < nv; ++k) {
-    rc[k] = h.radius + zc[k];
+    rc[k] = h.radius + deep * zc[k];
     dz[k] = zi[k + 1] - zi[k];
     clo[k] = (zc[k] - zi[k + 1]) / (zi[k] - zi[k + 1]);
     chi[k] = (zc[k] - zi[k]) / (zi[k + 1] - zi[k]);
     zcv[k] = zc[k];
   }
   for (int i = 0; i <= nv; ++i) {
-    ri[i] = h.radius + zi[i];
+    ri[i] = h.radius + deep * zi[i];
     ri2[i] = ri[i] * ri[i];
   }
   for (int k = 0; k < nv; ++k) {
@@ -480,6 +482,7 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
   I->ph.two_omega_f = (float)I->ph.two_omega;
   I->hyper = in.hyperdiffusion ? 1 : 0;
   I->divdamp = in.divergence_damping ? 1 : 0;
+  I->shallow = in.shallow ? 1 : 0;
   I->forcing = in.forcing;
   I->hj_dT = in.hj_dT;
   I->diff_D = pl.diff_D;

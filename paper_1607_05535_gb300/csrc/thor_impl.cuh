@@ -18,6 +18,7 @@ struct Work {
   R *vx, *vy, *vz;                 // full 3-D velocity at the centres
   R *vhx, *vhy, *vhz;              // horizontal velocity M / rho
   R *vr;                           // W / rho at the interfaces
+  R *wc;                           // W / rho at the centres (shallow atmosphere)
   R *qrho, *qvx, *qvy, *qvz, *qT;  // K_d lap(.) (times rho) for the hyperdiffusion
   R *qvr;                          // interfaces
   R *dd;                           // 3-D divergence (small step)
@@ -67,7 +68,7 @@ struct Member {
   double dts[3];                   // small-step length of each RK stage
   R Kd;                            // hyperdiffusion coefficient for this dt
   int nsub[3];                     // small steps of each RK stage
-  int hyper, divdamp, forcing;
+  int hyper, divdamp, forcing, shallow;
   const SolveMaps* smap;           // device copy of the staged-solve descriptors (or null)
   int* err;                        // the state's device error flag
 };
@@ -164,6 +165,7 @@ struct Impl : ImplBase {
   Pert<R> P;
   Fac<R> F;
   int hyper = 1, divdamp = 1, forcing = 0;
+  int shallow = 0;                 // shallow-atmosphere approximation (thor_init.shallow)
   double diff_D = 0, dbar4 = 0, hj_dT = 300.0;
   // device allocations
   void* arena = nullptr;
@@ -285,6 +287,7 @@ struct Impl : ImplBase {
     m.hyper = hyper;
     m.divdamp = divdamp;
     m.forcing = forcing;
+    m.shallow = shallow;
     m.smap = nullptr;
     m.err = dev_err;
     return m;

@@ -41,7 +41,8 @@ cudaError_t launch_k(void (*kern)(K...), dim3 grid, dim3 block, size_t smem, cud
 // Pointwise derived quantities at the stage state: p', T', theta, the full
 // 3-D velocity, v_h = M/rho (centres) and v_r = W/rho (interfaces).
 template <typename R>
-__device__ __forceinline__ void d_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int kchunk, int bx, int by) {
+__device__ __forceinline__ void d_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int shallow, int kchunk,
+                                          int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -69,6 +70,7 @@ __device__ __forceinline__ void d_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, W
       T.vhx[i] = mx * inv;
       T.vhy[i] = my * inv;
       T.vhz[i] = mz * inv;
+      if (shallow) T.wc[i] = wc * inv;
     }
     if (k >= 1 && k < G.nv) {
       int i = k * S + c;
@@ -121,7 +123,11 @@ __device__ __forceinline__ void d_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R 
 // Pi = gamma p / rho theta. In the first stage (stage state = X^t) Dsc is also
 // kept in d0: it is the divergence D that the first small step of every
 // stage damps, since there M^(s) + M* = M^t and W^(s) + W* = W^t.
-template <typename R>
+// SH: the shallow-atmosphere approximation of Sec. 3 (r = A in the tables;
+// here the traditional Coriolis, 2 Omega sin(lat) r x M on the horizontal
+// momentum only, and the horizontal velocity and w advected without the
+// metric terms the approximation drops)
+template <typename R, bool SH = false>
 __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
                                             R* d0, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
@@ -148,15 +154,18 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
     // once: the edge flux f = w . M of the momentum (shared by the continuity,
     // advection and rho-theta divergences), the pressure gradient and the
     // second Laplacians of the hyperdiffusion
-    R sa0 = 0, sa1 = 0, sa2 = 0, sdh = 0, sdt = 0, gx = 0, gy = 0, gz = 0;
+    R sa0 = 0, sa1 = 0, sa2 = 0, sa3 = 0, sdh = 0, sdt = 0, gx = 0, gy = 0, gz = 0;
     R hr = 0, hx = 0, hy = 0, hz = 0, hT = 0;
+    // advected velocity: the full 3-D one, or (SH) the horizontal one and w
+    const R *avx = SH ? T.vhx : T.vx, *avy = SH ? T.vhy : T.vy, *avz = SH ? T.vhz : T.vz;
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
       const int q = o + nb.n[j];
       const R f = wd.x[j] * ld(X.mx + q) + wd.y[j] * ld(X.my + q) + wd.z[j] * ld(X.mz + q);
-      sa0 += ld(T.vx + q) * f;
-      sa1 += ld(T.vy + q) * f;
-      sa2 += ld(T.vz + q) * f;
+      sa0 += ld(avx + q) * f;
+      sa1 += ld(avy + q) * f;
+      sa2 += ld(avz + q) * f;
+      if constexpr (SH) sa3 += ld(T.wc + q) * f;
       sdh += f;
       sdt += ld(T.theta + q) * f;
       const R pq = ld(T.pp + q);
@@ -185,7 +194,7 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
     }
 
     // advection div(rho v v_j) of the Cartesian components (Sec. 3)
-    const R* vs[3] = {T.vx, T.vy, T.vz};
+    const R* vs[3] = {avx, avy, avz};
     const R sa[3] = {sa0, sa1, sa2};
     R A[3];
     R wlo_w = ld(X.w + (i)), whi_w = ld(X.w + (i + S));
@@ -197,14 +206,33 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
       if (k + 1 < G.nv) vhi = ld(U.wlo + (k + 1)) * vs[j][i] + ld(U.whi + (k + 1)) * vs[j][i + S];
       A[j] = ah + sqh * whi_w * vhi - sql * wlo_w * vlo;
     }
-    // Coriolis 2 Omega z x (rho v) with the full momentum
-    R wc = ld(U.clo + (k)) * wlo_w + ld(U.chi + (k)) * whi_w;
-    R mx = ld(X.mx + (i)), my = ld(X.my + (i));
-    R fx = mx + wc * rx, fy = my + wc * ry;
-    A[0] += -two_om * fy;
-    A[1] += two_om * fx;
-    R acr = A[0] * rx + A[1] * ry + A[2] * rz;
-    R ahx = A[0] - acr * rx, ahy = A[1] - acr * ry, ahz = A[2] - acr * rz;
+    R acr, ahx, ahy, ahz;
+    if constexpr (SH) {
+      // traditional Coriolis f r x M_h, f = 2 Omega sin(lat); w advected as a scalar
+      const R mx = ld(X.mx + (i)), my = ld(X.my + (i)), mz = ld(X.mz + (i)), f = two_om * rz;
+      A[0] += f * (ry * mz - rz * my);
+      A[1] += f * (rz * mx - rx * mz);
+      A[2] += f * (rx * my - ry * mx);
+      R wlo_c = 0, whi_c = 0;
+      if (k >= 1) wlo_c = ld(U.wlo + (k)) * ld(T.wc + (i - S)) + ld(U.whi + (k)) * ld(T.wc + (i));
+      if (k + 1 < G.nv) whi_c = ld(U.wlo + (k + 1)) * ld(T.wc + (i)) + ld(U.whi + (k + 1)) * ld(T.wc + (i + S));
+      acr = sa3 * inv_r + sqh * whi_w * whi_c - sql * wlo_w * wlo_c;
+      const R d = A[0] * rx + A[1] * ry + A[2] * rz;
+      ahx = A[0] - d * rx;
+      ahy = A[1] - d * ry;
+      ahz = A[2] - d * rz;
+    } else {
+      // Coriolis 2 Omega z x (rho v) with the full momentum
+      R wc = ld(U.clo + (k)) * wlo_w + ld(U.chi + (k)) * whi_w;
+      R mx = ld(X.mx + (i)), my = ld(X.my + (i));
+      R fx = mx + wc * rx, fy = my + wc * ry;
+      A[0] += -two_om * fy;
+      A[1] += two_om * fx;
+      acr = A[0] * rx + A[1] * ry + A[2] * rz;
+      ahx = A[0] - acr * rx;
+      ahy = A[1] - acr * ry;
+      ahz = A[2] - acr * rz;
+    }
 
     R smx = -gx * inv_r - ahx + FMx, smy = -gy * inv_r - ahy + FMy, smz = -gz * inv_r - ahz + FMz;
     project(rx, ry, rz, smx, smy, smz);
@@ -783,17 +811,17 @@ __global__ void k_energy_fix(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, const R* fixf,
 // ---------------------------------------------------------------- kernels: one state
 
 template <typename R>
-__global__ void k_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int kchunk) {
-  d_derived<R>(G, U, ph, X, T, kchunk, blockIdx.x, blockIdx.y);
+__global__ void k_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int shallow, int kchunk) {
+  d_derived<R>(G, U, ph, X, T, shallow, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
 __global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk) {
   d_lap1<R>(G, U, X, T, Kd, kchunk, blockIdx.x, blockIdx.y);
 }
-template <typename R>
+template <typename R, bool SH>
 __global__ void __launch_bounds__(kMaxBlock, 2)
     k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper, R* d0, int kchunk) {
-  d_slow<R>(G, U, ph, X, T, SL, hyper, d0, kchunk, blockIdx.x, blockIdx.y);
+  d_slow<R, SH>(G, U, ph, X, T, SL, hyper, d0, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
 __global__ void k_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Slow<R> SL, Pert<R> P, int hyper,
@@ -1055,7 +1083,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps)
 template <typename R>
 __global__ void ke_derived(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
   THOR_MEMBER();
-  d_derived<R>(a.G, a.U, a.ph, Xs, a.T, kchunk, e.y, blockIdx.y);
+  d_derived<R>(a.G, a.U, a.ph, Xs, a.T, a.shallow, kchunk, e.y, blockIdx.y);
 }
 template <typename R>
 __global__ void ke_lap1(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
@@ -1066,8 +1094,11 @@ template <typename R>
 __global__ void __launch_bounds__(kMaxBlock, 2)
     ke_slow(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
   THOR_MEMBER();
-  d_slow<R>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, s == 0 && a.divdamp ? a.T.dd0 : nullptr, kchunk, e.y,
-            blockIdx.y);
+  R* d0 = s == 0 && a.divdamp ? a.T.dd0 : nullptr;
+  if (a.shallow)
+    d_slow<R, true>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, d0, kchunk, e.y, blockIdx.y);
+  else
+    d_slow<R, false>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, d0, kchunk, e.y, blockIdx.y);
 }
 template <typename R>
 __global__ void ke_slow_w(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
@@ -1189,7 +1220,7 @@ int Impl<R>::large_step(double dt, int n_small) {
     Xf<R> Xs = s == 0 ? Xt : Xst, Xo = s == 2 ? Xt : Xst;
     cudaStream_t aux = fork ? side : stream;
     mark(THOR_K_DERIVED, true);
-    chk(launch_k(k_derived<R>, g2i, bs, 0, stream, G, U, ph, Xs, T, kc));
+    chk(launch_k(k_derived<R>, g2i, bs, 0, stream, G, U, ph, Xs, T, shallow, kc));
     mark(THOR_K_DERIVED, false);
     ++launches;
     if (fork) {
@@ -1215,7 +1246,7 @@ int Impl<R>::large_step(double dt, int n_small) {
       ++launches;
     }
     mark(THOR_K_SLOW, true);
-    chk(launch_k(k_slow<R>, g2, bs, 0, stream, G, U, ph, Xs, T, SL, hyper,
+    chk(launch_k(shallow ? k_slow<R, true> : k_slow<R, false>, g2, bs, 0, stream, G, U, ph, Xs, T, SL, hyper,
                  s == 0 && divdamp ? T.dd0 : (R*)nullptr, kc));
     mark(THOR_K_SLOW, false);
     mark(THOR_K_SLOW_W, true);

@@ -1,0 +1,91 @@
+"""The shallow-atmosphere approximation of Sec. 3 on the CUDA path
+(thor_init.shallow = 1): float64 parity with the oracle's shallow model
+(r = A in every metric factor, traditional Coriolis on the horizontal
+momentum, v_h and w advected without the dropped metric terms), within the
+1e-10 relative L2 of the deep-atmosphere parity tests, and a check that the
+switch changes the result."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1607_05535_gb300 as thor
+from harness import Pair, field_errors
+from oracle import dycore as dc
+from oracle import operators as op
+import workloads as wls
+
+TOL = 1e-10
+
+SMALL = wls.HS_G4.with_(name="hs_g3_L12", glevel=3, nv=12, n_large=2)
+# a deep model top (z_top / A = 0.08) so that r = A and r = A + z differ well
+# above rounding: the tall hot-Jupiter column
+TALL = wls.HJ_G6.with_(glevel=3, nv=12, n_large=2)
+
+
+def _assert_close(A, B, tol=TOL):
+    e = field_errors(A, B)
+    assert e["rho"] < tol and e["Th"] < tol and e["M"] < tol and e["W"] < tol, e
+    return e
+
+
+def _inject_motion(p, wl, seed):
+    """A horizontal jet-like flow plus random vertical momentum, so that the
+    Coriolis and metric terms act from the first step."""
+    X = p.oracle_initial()
+    rng = np.random.default_rng(seed)
+    rhat = p.model.rhat
+    zonal = np.cross(np.array([0.0, 0.0, 1.0])[None, :], rhat)          # east times cos(lat)
+    M = 30.0 * zonal[:, None, :] + 3.0 * rng.standard_normal(X.M.shape)
+    X.M[:] = op.project_h(rhat, M) * X.rho[..., None]
+    X.W[:, 1:-1] = 0.05 * rng.standard_normal((X.W.shape[0], wl.nv - 1))
+    p.set(X)
+    return X
+
+
+@pytest.mark.parametrize("forcing", ["none", "held_suarez"])
+def test_shallow_parity(forcing):
+    wl = SMALL.with_(forcing=forcing)
+    p = Pair(wl, shallow=True)
+    try:
+        X = _inject_motion(p, wl, 5)
+        ref = dc.run(p.model, X, 2, wl.n_small, wl.dt)
+        thor.thor_step(p.state, 2, wl.n_small, wl.dt)
+        _assert_close(p.get(), ref)
+    finally:
+        p.close()
+
+
+def test_shallow_parity_tall_hot_jupiter():
+    wl = TALL
+    p = Pair(wl, shallow=True)
+    try:
+        X = p.oracle_initial()
+        ref = dc.run(p.model, X, 2, wl.n_small, wl.dt)
+        thor.thor_step(p.state, 2, wl.n_small, wl.dt)
+        assert np.abs(ref.M / ref.rho[..., None]).max() > 1e-6          # the air moves
+        _assert_close(p.get(), ref)
+    finally:
+        p.close()
+
+
+def test_shallow_switch_changes_the_result():
+    """Deep and shallow runs of the same injected state part well above the
+    parity tolerance, and the shallow one is the one that matches its oracle."""
+    wl = SMALL.with_(forcing="none")
+    out = {}
+    for shallow in (False, True):
+        p = Pair(wl, shallow=shallow)
+        try:
+            X = _inject_motion(p, wl, 9)
+            thor.thor_step(p.state, 2, wl.n_small, wl.dt)
+            out[shallow] = p.get()
+        finally:
+            p.close()
+    e = field_errors(out[True], out[False])
+    assert e["M"] > 1e3 * TOL and e["W"] > 1e3 * TOL, e
