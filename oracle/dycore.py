@@ -45,6 +45,15 @@ R6  Advection and Coriolis (Sec. 3): A_j = div(rho v v_j) for the three
 R7  K_d = D dbar^4 / dt (Eq. kd) with dbar from Eq. grid_qts; the
     nondimensional D of a planet follows from its Table 1 diffusion time
     scale through Eq. tau_d at the paper's own time step.
+H1  Hydrostatic switch (Sec. 3 lists the hydrostatic approximation among
+    those the model implements but does not use: the vertical pressure
+    gradient balances gravity). Read as a factor delta on the vertical
+    momentum's inertia: delta = 0 drops dW/dt with the vertical advection,
+    the radial Coriolis part and the diffusion of W, so that Eq. momr2
+    becomes 0 = -dp/dr - g rho at the new small-step state. The vertical
+    system of R3 keeps its form with the identity term and W* on the
+    right-hand side scaled by delta: W is diagnosed every small step so that
+    the new state is in discrete hydrostatic balance (linearised p*, as R3).
 """
 
 from dataclasses import dataclass, field
@@ -104,6 +113,7 @@ class Model:
     hj_dT: float = 300.0           # Eq. teq-hj day-night contrast
     hyperdiffusion: bool = True
     divergence_damping: bool = True
+    hydrostatic: bool = False      # reading H1
     Kd_fixed: float = None         # a fixed K_d instead of Eq. kd (tests)
     rhat: np.ndarray = field(init=False)
 
@@ -218,7 +228,10 @@ def slow_terms(model, X, Kd):
                                  np.zeros_like(X.W), np.zeros_like(X.Th))
 
     S_M = op.project_h(rhat, -op.grad_h_levels(g, vg, p) - AC_h + F_M)
-    S_W = -op.ddz_at_interfaces(vg, p) - pl.gravity * rho_i - AC_r + F_W
+    if model.hydrostatic:
+        S_W = -op.ddz_at_interfaces(vg, p) - pl.gravity * rho_i       # reading H1
+    else:
+        S_W = -op.ddz_at_interfaces(vg, p) - pl.gravity * rho_i - AC_r + F_W
     S_W[:, 0] = 0.0
     S_W[:, -1] = 0.0
     S_rho = -op.div_h_levels(g, vg, X.M) - op.div_v(vg, X.W) + F_rho
@@ -255,16 +268,19 @@ def vertical_solve(model, dtau, Wstar, S_W, a, b, c, theta_i, Pi):
     the unknown W (interior interfaces of every column) solves
         [I - dtau^2 Gz diag(Pi) Dtheta - dtau^2 g Iz Dv] W
             = W* + dtau S_W - dtau Gz c - dtau g Iz a,
-    solved here with a dense batched LU (numpy.linalg.solve)."""
+    solved here with a dense batched LU (numpy.linalg.solve). Under the
+    hydrostatic switch (reading H1) the identity and W* carry the factor
+    delta = 0."""
     vg, pl = model.vg, model.planet
+    delta = 0.0 if model.hydrostatic else 1.0
     nv = vg.nv
     Dv, Gz, Iz = vertical_matrices(vg)
     N = a.shape[0]
     th = theta_i[:, 1:-1]                              # (N, nv-1)
     Dth = Dv[None, :, :] * th[:, None, :]              # (N, nv, nv-1)
     GPi = Gz[None, :, :] * Pi[:, None, :]              # (N, nv-1, nv)
-    A = np.eye(nv - 1)[None] - dtau ** 2 * (GPi @ Dth) - dtau ** 2 * pl.gravity * (Iz @ Dv)[None]
-    rhs = Wstar[:, 1:-1] + dtau * S_W[:, 1:-1] - dtau * (c @ Gz.T) - dtau * pl.gravity * (a @ Iz.T)
+    A = delta * np.eye(nv - 1)[None] - dtau ** 2 * (GPi @ Dth) - dtau ** 2 * pl.gravity * (Iz @ Dv)[None]
+    rhs = delta * Wstar[:, 1:-1] + dtau * S_W[:, 1:-1] - dtau * (c @ Gz.T) - dtau * pl.gravity * (a @ Iz.T)
     Wint = np.linalg.solve(A, rhs[..., None])[..., 0]
     W = np.zeros((N, nv + 1))
     W[:, 1:-1] = Wint
