@@ -118,7 +118,14 @@ typedef struct {
  * momentum only ("traditional approximation"), and the metric terms it
  * drops (u w / r, v w / r, (u^2 + v^2) / r) left out by advecting the
  * horizontal velocity and w as a scalar; thor_diag's angular momentum then
- * uses r = A. */
+ * uses r = A.
+ * hydrostatic: 0 (the paper's runs) = nonhydrostatic; 1 = the hydrostatic
+ * approximation that Sec. 3 lists among the switches: the vertical
+ * momentum's inertia (dW/dt, its advection, radial Coriolis part and
+ * diffusion) is dropped, so that the vertical equation of every small step
+ * (Eq. momr2) reads 0 = -dp/dr - g rho at the new state and the column solve
+ * diagnoses W from it (same tridiagonal system without the identity term).
+ * Both switches may be combined; any nonzero value counts as 1. */
 typedef struct {
   double T0, p_surf, noise_amp;
   unsigned long long seed;
@@ -128,6 +135,7 @@ typedef struct {
   int hyperdiffusion;
   int divergence_damping;
   int shallow;
+  int hydrostatic;
 } thor_init;
 
 /* Allocate the device state for `grid` and set the initial condition. The

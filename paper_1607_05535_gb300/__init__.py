@@ -61,7 +61,8 @@ class thor_init(ctypes.Structure):
                 ("noise_amp", ctypes.c_double), ("seed", ctypes.c_ulonglong),
                 ("forcing", ctypes.c_int), ("hj_dT", ctypes.c_double),
                 ("precision", ctypes.c_int), ("hyperdiffusion", ctypes.c_int),
-                ("divergence_damping", ctypes.c_int), ("shallow", ctypes.c_int)]
+                ("divergence_damping", ctypes.c_int), ("shallow", ctypes.c_int),
+                ("hydrostatic", ctypes.c_int)]
 
 
 class thor_diag_t(ctypes.Structure):

@@ -480,6 +480,9 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
   I->ph.kappa_f = (float)I->ph.kappa;
   I->ph.g_f = (float)I->ph.g;
   I->ph.two_omega_f = (float)I->ph.two_omega;
+  I->ph.hydrostatic = in.hydrostatic ? 1 : 0;
+  I->ph.delta = in.hydrostatic ? 0.0 : 1.0;
+  I->ph.delta_f = (float)I->ph.delta;
   I->hyper = in.hyperdiffusion ? 1 : 0;
   I->divdamp = in.divergence_damping ? 1 : 0;
   I->shallow = in.shallow ? 1 : 0;

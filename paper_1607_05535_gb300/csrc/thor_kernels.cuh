@@ -80,6 +80,11 @@ struct Phys {
   // float copies for the float kernels (a float64 conversion per thread costs
   // an issue slot of the GB300's narrow float64 pipe)
   float Rd_f, inv_Rd_f, gamma_f, inv_gamma_f, kappa_f, g_f, two_omega_f;
+  // hydrostatic switch (Sec. 3): delta on the vertical momentum's inertia,
+  // 1 for the nonhydrostatic equations, 0 under the hydrostatic approximation
+  double delta = 1.0;
+  float delta_f = 1.0f;
+  int hydrostatic = 0;
 };
 // the constant in the kernel's storage type
 template <typename R> __device__ __forceinline__ R pc(double d, float f);

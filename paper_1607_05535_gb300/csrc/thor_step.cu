@@ -291,11 +291,15 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
       continue;
     }
     R wlo = ld(U.wlo + (k)), whi = ld(U.whi + (k));
-    R FW = 0;
-    if (hyper) FW = -apply7(wl, nb, T.qvr + k * S) / ld(U.ri2 + (k));
     R sw = ld(U.Rb + (k)) - (ld(T.pp + (i)) - ld(T.pp + (i - S))) * ld(U.inv_dzc + (k))
-         - g * (wlo * ld(X.rho + (i - S)) + whi * ld(X.rho + (i)))
-         - (wlo * ld(SL.acr + (i - S)) + whi * ld(SL.acr + (i))) + FW;
+         - g * (wlo * ld(X.rho + (i - S)) + whi * ld(X.rho + (i)));
+    // the vertical advection, Coriolis and diffusion of W are part of the
+    // inertia that the hydrostatic switch drops
+    if (!ph.hydrostatic) {
+      R FW = 0;
+      if (hyper) FW = -apply7(wl, nb, T.qvr + k * S) / ld(U.ri2 + (k));
+      sw = sw - (wlo * ld(SL.acr + (i - S)) + whi * ld(SL.acr + (i))) + FW;
+    }
     SL.sw[i] = sw;
     SL.thi[i] = wlo * ld(T.theta + (i - S)) + whi * ld(T.theta + (i));
   }
@@ -497,7 +501,7 @@ __device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> 
   const bool valid = c < G.ncol;
   const int cs = valid ? c : 0;          // padding lanes compute on column 0 and store nothing
   const int p = N / 2 > 0 ? N / 2 : 1;
-  const R g = pc<R>(ph.g, ph.g_f), dt2 = (R)(dtau * dtau);
+  const R g = pc<R>(ph.g, ph.g_f), dt2 = (R)(dtau * dtau), delta = pc<R>(ph.delta, ph.delta_f);
   __shared__ double sj[2][32];
   auto coef = [&](int m, double& lo, double& di, double& up) {
     const int i = m * S + cs;
@@ -511,7 +515,7 @@ __device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> 
     if (m < N) upper = (-dtz * pi_hi * ld(SL.thi + (i + S)) - dt2 * g * whi) * ph_;
     lo = to_f64<R>(lower);
     up = to_f64<R>(upper);
-    di = to_f64<R>(R(1) + dtz * th_m * (pi_hi * pl + pi_lo * qh) - dt2 * g * (wlo * qh - whi * pl));
+    di = to_f64<R>(delta + dtz * th_m * (pi_hi * pl + pi_lo * qh) - dt2 * g * (wlo * qh - whi * pl));
   };
   auto inv_of = [](double den) { return sizeof(R) == sizeof(double) ? 1.0 / den : rcp64_1(den); };
   double last = 0.0;
@@ -582,12 +586,12 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
   double* sx = sdp + (nv + 1) * 32;      // [2][32] junction values
   double* scf = sx + 64;                 // [nv + 1][32] c' / e', fetched during the sweeps
   const int p = N / 2 > 0 ? N / 2 : 1;
-  const R rdt = (R)dtau, g = pc<R>(ph.g, ph.g_f);
+  const R rdt = (R)dtau, g = pc<R>(ph.g, ph.g_f), delta = pc<R>(ph.delta, ph.delta_f);
 
   auto rhs = [&](int m) {
     const int i = m * S + cs;
     const R wlo = ld(U.wlo + m), whi = ld(U.whi + m);
-    return to_f64<R>(ld(P.w + i) + rdt * ld(SL.sw + i)
+    return to_f64<R>(delta * ld(P.w + i) + rdt * ld(SL.sw + i)
                     - rdt * ld(U.inv_dzc + m) * (ld(T.cc + i) - ld(T.cc + (i - S)))
                     - rdt * g * (wlo * ld(T.ca + (i - S)) + whi * ld(T.ca + i)));
   };
@@ -936,12 +940,12 @@ __device__ __forceinline__ void solve_issue(const SolveSm& s, const SolveMaps& M
 // back substitution; the solved W* over s.w. The two warps meet at named
 // barrier 1.
 __device__ __forceinline__ void solve_sweeps(const SolveSm& s, double* sx, const VR<float>& U, float rdt, float g,
-                                             int nv, int tx, int sweep) {
+                                             float delta, int nv, int tx, int sweep) {
   const int N = nv - 1, p = N / 2 > 0 ? N / 2 : 1;
   auto rhs = [&](int m) {
     const int o = m * 32 + tx;
     const float wlo = ld(U.wlo + m), whi = ld(U.whi + m);
-    return f2d_alu(s.w[o] + rdt * s.sw[o] - rdt * ld(U.inv_dzc + m) * (s.cc[o] - s.cc[o - 32])
+    return f2d_alu(delta * s.w[o] + rdt * s.sw[o] - rdt * ld(U.inv_dzc + m) * (s.cc[o] - s.cc[o - 32])
                    - rdt * g * (wlo * s.ca[o - 32] + whi * s.ca[o]));
   };
   double* sdp = s.inv;
@@ -1056,7 +1060,7 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
     return;
   }
   const float rdt = (float)dtau, g = ph.g_f;
-  if (warp < 2) solve_sweeps(s, sx, U, rdt, g, nv, tx, warp);
+  if (warp < 2) solve_sweeps(s, sx, U, rdt, g, ph.delta_f, nv, tx, warp);
   __syncthreads();
   if (c < G.ncol) solve_updates(s, G, U, ph, Xs, SL, P, T, rdt, want_div, Xo, last, c, tx, warp, kSolveWarps);
 }

@@ -1,7 +1,8 @@
 """Ensemble stepping and the launch-shape autotuner: an ensemble of uneven
 members (grid level, radius, rotation, time step, small-step count, forcing)
 stepped in one launch per kernel reproduces every member stepped alone (one
-member under the shallow-atmosphere approximation among deep ones), and
+member under the shallow-atmosphere approximation and one under the
+hydrostatic one among nonhydrostatic deep ones), and
 the autotuner leaves the state unchanged and changes no result.
 
 The ensemble kernels inline the same device code as the single-state ones,
@@ -34,6 +35,7 @@ MEMBERS = [
     (2, 5.0, 0.2, 3600.0, 6, thor.THOR_FORCING_NONE),
 ]
 SHALLOW = {3}                                    # members run with thor_init.shallow = 1
+HYDROSTATIC = {1}                                # members run with thor_init.hydrostatic = 1
 
 
 class Pool:
@@ -47,7 +49,7 @@ class Pool:
             grid = thor.thor_grid_create(g, nv, P.radius * rf, 24.0e3, sp)
             planet = thor.thor_planet(P.radius * rf, P.omega * of, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
             init = thor.thor_init(300.0, 1.0e5, 0.5, 77 + i, forcing, 300.0, precision, 1, 1,
-                                  int(i in SHALLOW))
+                                  int(i in SHALLOW), int(i in HYDROSTATIC))
             self.grids.append(grid)
             self.a.append(thor.thor_state_init(grid, planet, init, stream))
             self.b.append(thor.thor_state_init(grid, planet, init, stream))

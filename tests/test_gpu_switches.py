@@ -1,9 +1,12 @@
-"""The shallow-atmosphere approximation of Sec. 3 on the CUDA path
-(thor_init.shallow = 1): float64 parity with the oracle's shallow model
-(r = A in every metric factor, traditional Coriolis on the horizontal
-momentum, v_h and w advected without the dropped metric terms), within the
-1e-10 relative L2 of the deep-atmosphere parity tests, and a check that the
-switch changes the result."""
+"""The approximation switches of Sec. 3 on the CUDA path: the
+shallow-atmosphere approximation (thor_init.shallow = 1: r = A in every
+metric factor, traditional Coriolis on the horizontal momentum, v_h and w
+advected without the dropped metric terms) and the hydrostatic one
+(thor_init.hydrostatic = 1: W diagnosed by the column solve from
+0 = -dp/dr - g rho), alone and together. Float64 parity with the oracle's
+models within the 1e-10 relative L2 of the default parity tests; the mixed
+mode within the gates of the default mixed tests; a check that each switch
+changes the result."""
 
 import numpy as np
 import pytest
@@ -49,9 +52,10 @@ def _inject_motion(p, wl, seed):
 
 
 @pytest.mark.parametrize("forcing", ["none", "held_suarez"])
-def test_shallow_parity(forcing):
+@pytest.mark.parametrize("shallow,hydrostatic", [(True, False), (False, True), (True, True)])
+def test_switch_parity(forcing, shallow, hydrostatic):
     wl = SMALL.with_(forcing=forcing)
-    p = Pair(wl, shallow=True)
+    p = Pair(wl, shallow=shallow, hydrostatic=hydrostatic)
     try:
         X = _inject_motion(p, wl, 5)
         ref = dc.run(p.model, X, 2, wl.n_small, wl.dt)
@@ -61,9 +65,10 @@ def test_shallow_parity(forcing):
         p.close()
 
 
-def test_shallow_parity_tall_hot_jupiter():
+@pytest.mark.parametrize("shallow,hydrostatic", [(True, False), (False, True)])
+def test_switch_parity_tall_hot_jupiter(shallow, hydrostatic):
     wl = TALL
-    p = Pair(wl, shallow=True)
+    p = Pair(wl, shallow=shallow, hydrostatic=hydrostatic)
     try:
         X = p.oracle_initial()
         ref = dc.run(p.model, X, 2, wl.n_small, wl.dt)
@@ -74,18 +79,37 @@ def test_shallow_parity_tall_hot_jupiter():
         p.close()
 
 
-def test_shallow_switch_changes_the_result():
-    """Deep and shallow runs of the same injected state part well above the
-    parity tolerance, and the shallow one is the one that matches its oracle."""
+@pytest.mark.parametrize("switch", ["shallow", "hydrostatic"])
+def test_switch_changes_the_result(switch):
+    """Runs of the same injected state with and without the switch part well
+    above the parity tolerance."""
     wl = SMALL.with_(forcing="none")
     out = {}
-    for shallow in (False, True):
-        p = Pair(wl, shallow=shallow)
+    for on in (False, True):
+        p = Pair(wl, **{switch: on})
         try:
-            X = _inject_motion(p, wl, 9)
+            _inject_motion(p, wl, 9)
             thor.thor_step(p.state, 2, wl.n_small, wl.dt)
-            out[shallow] = p.get()
+            out[on] = p.get()
         finally:
             p.close()
     e = field_errors(out[True], out[False])
     assert e["M"] > 1e3 * TOL and e["W"] > 1e3 * TOL, e
+
+
+@pytest.mark.parametrize("shallow,hydrostatic", [(True, False), (False, True)])
+def test_switch_mixed_precision(shallow, hydrostatic):
+    """Mixed mode under a switch against the oracle's float64 model under
+    the same switch, 4 Held-Suarez large steps at g4 x 20 L, with the gates
+    of the default mixed-precision test."""
+    from test_gpu_mixed import GATES, field_report
+    wl = wls.HS_G4.with_(n_large=4)
+    p = Pair(wl, precision=thor.THOR_MIXED, shallow=shallow, hydrostatic=hydrostatic)
+    try:
+        ref = dc.run(p.model, p.oracle_initial(), wl.n_large, wl.n_small, wl.dt)
+        thor.thor_step(p.state, wl.n_large, wl.n_small, wl.dt)
+        rep = field_report(p, p.get(), ref)
+    finally:
+        p.close()
+    for k, g in GATES.items():
+        assert rep[k] < g, (k, rep)
