@@ -59,16 +59,28 @@ def _env_int(k, d):
         return d
 
 
+def solve_source_sha1():
+    """SHA-1 of the source the staged column solve compiles from: its section
+    of csrc/thor_step.cu (from its banner to the ensemble kernels' banner),
+    the stage-end helper it calls, and csrc/thor_kernels.cuh."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1607_05535_gb300", "csrc")
+    src = open(os.path.join(d, "thor_step.cu")).read()
+    a = src.index("// " + "-" * 64 + " staged column solve")
+    b = src.index("// " + "-" * 64 + " kernels: ensemble")
+    c0 = src.index("__device__ __forceinline__ void stage_end_cell")
+    c1 = src.index("\n}\n", c0)
+    text = src[a:b] + src[c0:c1] + open(os.path.join(d, "thor_kernels.cuh")).read()
+    return hashlib.sha1(text.encode()).hexdigest()
+
+
 def _traffic(kernel):
     """ncu DRAM bytes per launch of ``kernel`` from the committed profile, or
     None if that profile was taken of another version of the kernel source."""
-    import hashlib
     try:
         kv = dict(l.split(None, 1) for l in open(os.path.join(ROOT, "profiles", "traffic_hs_g6_L32_mixed.txt"))
                   if l.strip() and not l.startswith("#"))
-        src = os.path.join(ROOT, "paper_1607_05535_gb300", "csrc", "thor_step.cu")
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-        if kv["kernel"].strip() == kernel and kv["thor_step_cu_sha1"].strip() == sha:
+        if kv["kernel"].strip() == kernel and kv["solve_source_sha1"].strip() == solve_source_sha1():
             return float(kv["bytes_per_launch"])
     except Exception:
         pass

@@ -31,10 +31,24 @@ SMALL = wls.HS_G4.with_(name="hs_g3_L12", glevel=3, nv=12, n_large=2)
 TALL = wls.HJ_G6.with_(glevel=3, nv=12, n_large=2)
 
 
-def _assert_close(A, B, tol=TOL):
+def _assert_close(A, B, tol=TOL, w_scale=0.0):
+    """Every field within tol relative L2. Under the hydrostatic switch W is
+    diagnosed: the small difference of right-hand-side terms of size
+    w_scale = g rho dtau (the stage's dp/dr and g rho cancel to the
+    departure from balance), solved through a matrix without the identity.
+    Its float64 rounding is then absolute, about 1e-16 w_scale times the
+    conditioning of that matrix (1e1 to 1e3 here), and two float64 solvers
+    of the oracle's own system (dense LU, banded) already differ by 1.6e-8
+    relative in the tall hot-Jupiter column, where W is 1e-5 of w_scale. So
+    W passes at tol relative or 1e-12 w_scale absolute."""
     e = field_errors(A, B)
-    assert e["rho"] < tol and e["Th"] < tol and e["M"] < tol and e["W"] < tol, e
+    assert e["rho"] < tol and e["Th"] < tol and e["M"] < tol, e
+    assert e["W"] < tol or e["W_maxabs"] < 1e-12 * w_scale, e
     return e
+
+
+def _w_scale(p, X, dtau):
+    return p.model.planet.gravity * float(np.abs(X.rho).max()) * dtau
 
 
 def _inject_motion(p, wl, seed):
@@ -60,7 +74,7 @@ def test_switch_parity(forcing, shallow, hydrostatic):
         X = _inject_motion(p, wl, 5)
         ref = dc.run(p.model, X, 2, wl.n_small, wl.dt)
         thor.thor_step(p.state, 2, wl.n_small, wl.dt)
-        _assert_close(p.get(), ref)
+        _assert_close(p.get(), ref, w_scale=_w_scale(p, ref, wl.dt / wl.n_small) if hydrostatic else 0.0)
     finally:
         p.close()
 
@@ -74,7 +88,7 @@ def test_switch_parity_tall_hot_jupiter(shallow, hydrostatic):
         ref = dc.run(p.model, X, 2, wl.n_small, wl.dt)
         thor.thor_step(p.state, 2, wl.n_small, wl.dt)
         assert np.abs(ref.M / ref.rho[..., None]).max() > 1e-6          # the air moves
-        _assert_close(p.get(), ref)
+        _assert_close(p.get(), ref, w_scale=_w_scale(p, ref, wl.dt / wl.n_small) if hydrostatic else 0.0)
     finally:
         p.close()
 
