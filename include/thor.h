@@ -248,15 +248,23 @@ int thor_budget_read(thor_state* state, double* out, int max_rows, int* n_rows);
  * the band covariances) to the state's accumulator, on the state's stream
  * without synchronising; nlat in [1, 360], else THOR_EINVAL. The first call
  * for a given nlat synchronises the stream, allocates the accumulator
- * (about 150 * nv * nlat bytes plus 28 bytes per column) and clears it.
+ * (about 150 * nv * nlat bytes plus 28 + 8 * nv bytes per column) and
+ * clears it. The same call adds every cell's vertical velocity at its
+ * centre, w = (W linearly interpolated to the centre) / rho, to a per-cell
+ * time sum (for the grid-imprinting map [w*] of Sec. 6.1: the time mean of w
+ * minus its zonal band mean).
  * thor_zonal_read copies the accumulated sums, layout
  * [nv][nlat][9] float64 (n must be nv * nlat * 9), and the number of states
- * accumulated; with reset != 0 it then clears them. Divide by the sample
- * count for time means. A read for an nlat that was never accumulated
- * returns zeros and 0 samples. thor_zonal_read synchronises the state's
- * stream. */
+ * accumulated; with reset != 0 it then clears them and the per-cell w sums.
+ * Divide by the sample count for time means. A read for an nlat that was
+ * never accumulated returns zeros and 0 samples. thor_zonal_read_w copies
+ * the time mean [w] (m/s) of every cell, layout [ncol][nv] float64 in the
+ * column order of thor_state_get (n must be ncol * nv), and the sample
+ * count; zeros and 0 samples when nothing was accumulated for nlat. Both
+ * reads synchronise the state's stream. */
 int thor_zonal_accumulate(thor_state* state, int nlat);
 int thor_zonal_read(thor_state* state, int nlat, double* out, size_t n, int reset, long long* samples);
+int thor_zonal_read_w(thor_state* state, int nlat, double* out, size_t n, long long* samples);
 
 /* THOR_TUNE_BLOCK: threads (one per column) in a block of the stencil
  * kernels, a multiple of 32 in [32, 256] (default 128).

@@ -16,7 +16,11 @@ eddy terms are the band covariances [ab] - [a][b] of one state, averaged in
 time by the caller. u and v are the eastward and northward components of
 M / rho (the horizontal velocity; both taken as 0 at the two polar cells,
 where east and north are undefined), T and p follow from Eq. pressure and
-the ideal gas.
+the ideal gas. Reading C-2 (the grid-imprinting map [w*]) is at w_star;
+reading C-3: pressure-level values come from the time- and zonal-mean
+fields on model levels, interpolated in p between the two levels whose
+band-mean pressures bracket the target (the paper interpolates each output
+before averaging).
 """
 
 import numpy as np
@@ -66,4 +70,47 @@ def zonal_band_means(model, X, nlat):
         out[k, :, 6] = mean(v[:, k] * T[:, k]) - mv * mT
         out[k, :, 7] = mean(u[:, k] ** 2) - mu ** 2
         out[k, :, 8] = mean(v[:, k] ** 2) - mv ** 2
+    return out
+
+
+def cell_w(model, X):
+    """Vertical velocity at every cell centre, (N, nv): the vertical momentum
+    interpolated linearly (Lagrange k = 1, Sec. 2.1) from the interfaces to
+    the centre, over the density."""
+    from . import operators as op
+    return op.interp_to_centres(model.vg, X.W) / X.rho
+
+
+def w_star(model, w_mean, nlat):
+    """The grid-imprinting map of Sec. 6.1 (reading C-2): the time mean [w]
+    of every cell minus the volume-weighted mean of [w] over its latitude
+    band at the same level, (N, nv). The paper writes w* = w - [w] with [.]
+    the time average and maps [w*]; taken literally that is zero, so the
+    deviation is read as the one from the zonal mean (the prime of the eddy
+    terms), whose time average keeps what the grid imprints."""
+    V = volumes(model)
+    band = band_of(model.grid.points, nlat)
+    out = np.empty_like(w_mean)
+    for k in range(w_mean.shape[1]):
+        W = np.bincount(band, weights=V[:, k], minlength=nlat)
+        m = np.bincount(band, weights=V[:, k] * w_mean[:, k], minlength=nlat)
+        out[:, k] = w_mean[:, k] - np.divide(m, W, out=np.zeros(nlat), where=W > 0)[band]
+    return out
+
+
+def to_pressure_levels(values, p_mean, p_levels):
+    """Sec. 6: results shown against pressure are interpolated linearly to a
+    pressure grid after the run. values and p_mean (nv, nlat) on model
+    levels (p_mean the band's mean pressure, reading C-3) ->
+    (len(p_levels), nlat); a target outside a band's pressure range is NaN."""
+    nv, nlat = values.shape
+    out = np.full((len(p_levels), nlat), np.nan)
+    for b in range(nlat):
+        p, f = p_mean[:, b], values[:, b]
+        for i, pt in enumerate(p_levels):
+            for k in range(nv - 1):
+                lo, hi = min(p[k], p[k + 1]), max(p[k], p[k + 1])
+                if lo <= pt <= hi:
+                    out[i, b] = f[k] if hi == lo else f[k] + (f[k + 1] - f[k]) * (pt - p[k]) / (p[k + 1] - p[k])
+                    break
     return out

@@ -38,6 +38,7 @@ EXPORTED = [
     "thor_ensemble_tune", "thor_ensemble_autotune", "thor_ensemble_destroy", "thor_mlp_tune",
     "thor_checkpoint_bytes", "thor_checkpoint_save", "thor_checkpoint_load", "thor_wait_selftest",
     "thor_convert_selftest", "thor_budget_read", "thor_zonal_accumulate", "thor_zonal_read",
+    "thor_zonal_read_w",
 ]
 
 # kernel ids of thor_profile_read
@@ -135,6 +136,7 @@ def _load():
         "thor_budget_read": (I, [P, ctypes.POINTER(D), I, IP]),
         "thor_zonal_accumulate": (I, [P, I]),
         "thor_zonal_read": (I, [P, I, ctypes.POINTER(D), Z, I, ctypes.POINTER(ctypes.c_longlong)]),
+        "thor_zonal_read_w": (I, [P, I, ctypes.POINTER(D), Z, ctypes.POINTER(ctypes.c_longlong)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -457,4 +459,15 @@ def thor_zonal_read(state, nlat, nv, reset=False):
     n = ctypes.c_longlong()
     _check(_lib.thor_zonal_read(state, int(nlat), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size,
                                 int(bool(reset)), ctypes.byref(n)), "thor_zonal_read")
+    return out, n.value
+
+
+def thor_zonal_read_w(state, nlat, ncol, nv):
+    """(w_mean, samples): the time mean of w at every cell centre, float64
+    (ncol, nv) in the column order of thor_state_get."""
+    import numpy as np
+    out = np.zeros((ncol, nv))
+    n = ctypes.c_longlong()
+    _check(_lib.thor_zonal_read_w(state, int(nlat), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size,
+                                  ctypes.byref(n)), "thor_zonal_read_w")
     return out, n.value

@@ -11,7 +11,10 @@
 // band histograms per block, then global atomics), turns them into the
 // band means and covariances of that state and adds them to the state's
 // time accumulator; thor_zonal_read returns the accumulated sums. At the two
-// polar cells east and north are undefined and u = v = 0.
+// polar cells east and north are undefined and u = v = 0. The same pass adds
+// every cell's vertical velocity at its centre, w = (W interpolated to the
+// centre) / rho, to a per-cell time sum: the time mean [w] behind the
+// grid-imprinting map [w*] of Sec. 6.1 (thor_zonal_read_w).
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -28,7 +31,8 @@ constexpr int kZonalQ = 9;    // weight, u, v, T, p, uv, vT, uu, vv
 template <typename R>
 __global__ void __launch_bounds__(kZonalThreads)
     k_zonal_partial(Geo<R> G, Vert V, Phys ph, Xf<R> X, const int* __restrict__ band,
-                    const double* __restrict__ basis, int nlat, double* __restrict__ tmp) {
+                    const double* __restrict__ basis, int nlat, double* __restrict__ tmp,
+                    double* __restrict__ wsum) {
   extern __shared__ double hist[];                 // [nlat][kZonalQ]
   const int k = blockIdx.y, S = G.colp;
   for (int t = threadIdx.x; t < nlat * kZonalQ; t += blockDim.x) hist[t] = 0.0;
@@ -42,6 +46,7 @@ __global__ void __launch_bounds__(kZonalThreads)
     const double vx = (double)X.mx[i] / rho, vy = (double)X.my[i] / rho, vz = (double)X.mz[i] / rho;
     const double u = vx * basis[c] + vy * basis[S + c] + vz * basis[2 * S + c];
     const double v = vx * basis[3 * S + c] + vy * basis[4 * S + c] + vz * basis[5 * S + c];
+    wsum[i] += (V.clo[k] * (double)X.w[i] + V.chi[k] * (double)X.w[i + S]) / rho;
     const double w = G.area[c] * V.rc[k] * V.rc[k] * V.dz[k];
     const double q[kZonalQ] = {w, w * u, w * v, w * T, w * p, w * u * v, w * v * T, w * u * u, w * v * v};
     double* h = hist + band[c] * kZonalQ;
@@ -84,7 +89,7 @@ int zonal_launch(thor_state* s) {
   dim3 grid((I->G.ncol + kZonalThreads - 1) / kZonalThreads, nv);
   const size_t smem = (size_t)z.nlat * kZonalQ * sizeof(double);
   k_zonal_partial<R><<<grid, kZonalThreads, smem, I->stream>>>(I->G, I->V, I->ph, I->Xt, z.band, z.basis, z.nlat,
-                                                                z.tmp);
+                                                                z.tmp, z.wsum);
   const int n = nv * z.nlat;
   k_zonal_finish<<<(n + 255) / 256, 256, 0, I->stream>>>(n, z.tmp, z.acc);
   I->launches += 2;
@@ -117,14 +122,17 @@ int zonal_setup(thor_state* s, int nlat) {
     basis[5 * S + c] = std::cos(lat);
   }
   const size_t nq = (size_t)nv * nlat * kZonalQ;
+  const size_t nw = (size_t)nv * S;
   if (cudaMalloc(&z.band, S * sizeof(int)) || cudaMalloc(&z.basis, basis.size() * sizeof(double)) ||
-      cudaMalloc(&z.tmp, nq * sizeof(double)) || cudaMalloc(&z.acc, nq * sizeof(double))) {
+      cudaMalloc(&z.tmp, nq * sizeof(double)) || cudaMalloc(&z.acc, nq * sizeof(double)) ||
+      cudaMalloc(&z.wsum, nw * sizeof(double))) {
     zonal_release(z);
     return THOR_ENOMEM;
   }
   if (cudaMemcpy(z.band, band.data(), S * sizeof(int), cudaMemcpyHostToDevice) ||
       cudaMemcpy(z.basis, basis.data(), basis.size() * sizeof(double), cudaMemcpyHostToDevice) ||
-      cudaMemset(z.tmp, 0, nq * sizeof(double)) || cudaMemset(z.acc, 0, nq * sizeof(double))) {
+      cudaMemset(z.tmp, 0, nq * sizeof(double)) || cudaMemset(z.acc, 0, nq * sizeof(double)) ||
+      cudaMemset(z.wsum, 0, nw * sizeof(double))) {
     zonal_release(z);
     return THOR_ECUDA;
   }
@@ -140,6 +148,7 @@ void zonal_release(ZonalAcc& z) {
   if (z.basis) cudaFree(z.basis);
   if (z.tmp) cudaFree(z.tmp);
   if (z.acc) cudaFree(z.acc);
+  if (z.wsum) cudaFree(z.wsum);
   z = ZonalAcc{};
 }
 
@@ -173,9 +182,33 @@ int thor_zonal_read(thor_state* s, int nlat, double* out, size_t n, int reset, l
     return THOR_ECUDA;
   *samples = s->zonal.samples;
   if (reset) {
-    if (cudaMemset(s->zonal.acc, 0, need * sizeof(double))) return THOR_ECUDA;
+    const size_t colp = (size_t)(s->grid->h.ncol + thor::kBlock - 1) / thor::kBlock * thor::kBlock;
+    if (cudaMemset(s->zonal.acc, 0, need * sizeof(double)) ||
+        cudaMemset(s->zonal.wsum, 0, (size_t)s->grid->h.nv * colp * sizeof(double)))
+      return THOR_ECUDA;
     s->zonal.samples = 0;
   }
+  return THOR_OK;
+}
+
+int thor_zonal_read_w(thor_state* s, int nlat, double* out, size_t n, long long* samples) {
+  if (!s || !samples || !out) return THOR_EINVAL;
+  const int ncol = s->grid->h.ncol, nv = s->grid->h.nv;
+  if (nlat < 1 || n != (size_t)ncol * nv) return THOR_EINVAL;
+  if (s->zonal.nlat != nlat || s->zonal.samples == 0) {
+    std::memset(out, 0, n * sizeof(double));
+    *samples = 0;
+    return THOR_OK;
+  }
+  const size_t S = (size_t)(ncol + thor::kBlock - 1) / thor::kBlock * thor::kBlock;
+  std::vector<double> buf((size_t)nv * S);
+  if (cudaStreamSynchronize(s->impl->stream) ||
+      cudaMemcpy(buf.data(), s->zonal.wsum, buf.size() * sizeof(double), cudaMemcpyDeviceToHost))
+    return THOR_ECUDA;
+  const double inv = 1.0 / (double)s->zonal.samples;
+  for (int c = 0; c < ncol; ++c)
+    for (int k = 0; k < nv; ++k) out[(size_t)c * nv + k] = buf[k * S + c] * inv;
+  *samples = s->zonal.samples;
   return THOR_OK;
 }
 

@@ -28,6 +28,7 @@ struct ZonalAcc {
   double* basis = nullptr;            // [6][colp] east and north unit vectors
   double* tmp = nullptr;              // [nv][nlat][9] sums of one state
   double* acc = nullptr;              // [nv][nlat][9] accumulated band means and covariances
+  double* wsum = nullptr;             // [nv][colp] time sum of w at the centres of every cell
   long long samples = 0;
 };
 

@@ -1,6 +1,7 @@
-"""Zonal band means on the GPU (thor_zonal_accumulate / thor_zonal_read)
-against the oracle's (oracle/climate.py) on the same state, and the climate
-runner on a short run."""
+"""Zonal band means and the per-cell time mean of w on the GPU
+(thor_zonal_accumulate / thor_zonal_read / thor_zonal_read_w) against the
+oracle's (oracle/climate.py) on the same states, and the climate runner on
+short runs."""
 
 import numpy as np
 import pytest
@@ -75,3 +76,58 @@ def test_climate_runner_short_held_suarez():
     s = climate.summarize(means, wls.EARTH.radius, wls.EARTH.gravity)
     assert np.all(np.isfinite(means))
     assert s["jets"]["north"]["u_ms"] > 0 and s["jets"]["south"]["u_ms"] > 0
+
+
+@pytest.mark.parametrize("precision", [thor.THOR_FP64, thor.THOR_MIXED])
+def test_time_mean_w_and_imprint_map_match_the_oracle(precision):
+    """The per-cell time mean [w] that thor_zonal_accumulate keeps, over four
+    states, against the oracle's w of the library's own states averaged on
+    the host, and the [w*] map built from it; thor_zonal_read's reset clears
+    it."""
+    from paper_1607_05535_gb300 import climate
+    nlat = 12
+    p = Pair(SMALL, precision=precision)
+    try:
+        ws = []
+        for _ in range(4):
+            thor.thor_step(p.state, 1, SMALL.n_small, SMALL.dt)
+            thor.thor_zonal_accumulate(p.state, nlat)
+            ws.append(ocl.cell_w(p.model, p.get()))
+        got_lib, n = thor.thor_zonal_read_w(p.state, nlat, p.ncol, p.nv)
+        assert n == 4
+        got = np.empty_like(got_lib)
+        got[p.perm] = got_lib
+        ref = np.mean(ws, axis=0)
+        assert np.abs(ref).max() > 1e-6                                # the air moves vertically
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+        pts = np.empty((p.ncol, 3))
+        pts[p.perm] = thor.thor_grid_points(p.grid)
+        area = np.empty(p.ncol)
+        area[p.perm] = thor.thor_grid_areas(p.grid)
+        np.testing.assert_allclose(climate.w_star(got, pts, area, nlat), ocl.w_star(p.model, ref, nlat),
+                                   atol=1e-11 * np.abs(ref).max())
+        thor.thor_zonal_read(p.state, nlat, p.nv, reset=True)
+        zero, n0 = thor.thor_zonal_read_w(p.state, nlat, p.ncol, p.nv)
+        assert n0 == 0 and not zero.any()
+        thor.thor_zonal_accumulate(p.state, nlat)
+        one, n1 = thor.thor_zonal_read_w(p.state, nlat, p.ncol, p.nv)
+        assert n1 == 1 and np.abs(one).max() > 0
+    finally:
+        p.close()
+
+
+def test_climate_runner_switches_and_post_processing():
+    """Ten days of Held-Suarez at glevel 3 with both approximation switches:
+    the runner's extras, [w*] summary and pressure-level fields are finite."""
+    from paper_1607_05535_gb300 import climate
+    extras = {}
+    means, samples, seconds, diag = climate.run(thor, glevel=3, nv=12, z_top=32.0e3, dt=1800.0, n_small=6,
+                                                days=10.0, spinup_days=5.0, nlat=12, shallow=True,
+                                                hydrostatic=True, extras=extras)
+    assert samples == 5 and diag["nonfinite"] == 0
+    ws = climate.w_star(extras["w_mean"], extras["points"], extras["areas"], 12)
+    imp = climate.imprint_summary(ws, extras["w_mean"], extras["points"], extras["areas"], 12)
+    assert np.isfinite(list(imp.values())).all() and 0 <= imp["w_star_wave5_share"] <= 1
+    pm = means[..., 4]
+    s = climate.summarize(means, wls.EARTH.radius, wls.EARTH.gravity, np.geomspace(pm.max(), pm.min(), 8))
+    assert s["u_p_levels"][0][0] is not None or s["u_p_levels"][1][0] is not None

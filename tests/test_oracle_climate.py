@@ -70,3 +70,76 @@ def test_zonal_wave_has_zero_mean_and_its_variance():
     assert np.abs(z[:, mid, 1]).max() < 0.05 * U
     np.testing.assert_allclose(z[:, mid, 7], U * U / 2, rtol=0.1)
     assert np.abs(z[:, :, 8]).max() < 1e-20
+
+
+def test_w_star_vanishes_for_band_constant_fields_and_is_linear():
+    """[w*] is zero where [w] is constant over every band and level, it has a
+    zero volume-weighted mean in every band, and w* of a sum is the sum."""
+    m = _model()
+    band = cl.band_of(m.grid.points, NLAT)
+    rng = np.random.default_rng(2)
+    per_band = rng.standard_normal((NLAT, m.vg.nv))
+    ws = cl.w_star(m, per_band[band], NLAT)
+    assert np.abs(ws).max() <= 1e-14 * np.abs(per_band).max()      # rounding of the weighted sums
+    a, b = rng.standard_normal((2, m.grid.ncol, m.vg.nv))
+    wa, wb = cl.w_star(m, a, NLAT), cl.w_star(m, b, NLAT)
+    np.testing.assert_allclose(cl.w_star(m, a + b, NLAT), wa + wb, atol=1e-14)
+    V = volumes(m)
+    for k in range(m.vg.nv):
+        s = np.bincount(band, weights=V[:, k] * wa[:, k], minlength=NLAT)
+        assert np.abs(s).max() <= 1e-13 * np.abs(V[:, k] * wa[:, k]).sum()
+    # a band-constant part added to a field leaves its map unchanged
+    np.testing.assert_allclose(cl.w_star(m, a + per_band[band], NLAT), wa, atol=1e-14)
+
+
+def test_cell_w_of_a_linear_profile():
+    """W linear in height with a uniform density: the centre value is exact
+    (Lagrange k = 1 reproduces a linear function), w = (a + b z_c) / rho."""
+    m = _model()
+    X = dc.initial_state(m, 280.0, 1.0e5)
+    X.rho[:] = 1.2
+    X.W[:] = 0.3 + 2e-5 * m.vg.zi[None, :]
+    np.testing.assert_allclose(cl.cell_w(m, X), (0.3 + 2e-5 * m.vg.zc[None, :]) / 1.2 * np.ones_like(X.rho),
+                               rtol=1e-14)
+
+
+def test_pressure_levels_linear_and_bounds():
+    """A field linear in p comes back exactly at any target inside a band's
+    pressure range (whichever way the levels are ordered), the model levels'
+    own pressures return the level values, and targets outside are NaN."""
+    rng = np.random.default_rng(5)
+    nv, nlat = 8, 5
+    p = np.sort(rng.uniform(1e3, 1e5, (nv, nlat)), axis=0)[::-1]      # decreasing with height
+    f = 3.0 - 2e-4 * p
+    targets = np.array([2e5, 9e4, 5e4, 2e4, 5e3, 10.0])
+    out = cl.to_pressure_levels(f, p, targets)
+    for b in range(nlat):
+        for i, pt in enumerate(targets):
+            if p[:, b].min() <= pt <= p[:, b].max():
+                assert abs(out[i, b] - (3.0 - 2e-4 * pt)) <= 1e-12
+            else:
+                assert np.isnan(out[i, b])
+    g = rng.standard_normal((nv, nlat))
+    for b in range(nlat):
+        np.testing.assert_allclose(cl.to_pressure_levels(g[:, b:b + 1], p[:, b:b + 1], p[:, b])[:, 0], g[:, b],
+                                   rtol=1e-13)
+
+
+def test_runner_post_processing_matches_the_oracle():
+    """The climate runner's [w*] and pressure-level interpolation (numpy on
+    the host, written apart from the oracle) against the oracle's on the same
+    inputs; the runner weights a level by area, the oracle by volume."""
+    climate = __import__("paper_1607_05535_gb300.climate", fromlist=["w_star"])
+    m = _model()
+    rng = np.random.default_rng(8)
+    wm = rng.standard_normal((m.grid.ncol, m.vg.nv))
+    np.testing.assert_allclose(climate.w_star(wm, m.grid.points, m.grid.area, NLAT), cl.w_star(m, wm, NLAT),
+                               atol=1e-13)
+    np.testing.assert_array_equal(climate.bands(m.grid.points, NLAT), cl.band_of(m.grid.points, NLAT))
+    nv, nlat = 10, 7
+    p = np.sort(rng.uniform(1e2, 1e5, (nv, nlat)), axis=0)[::-1]
+    f = rng.standard_normal((nv, nlat))
+    targets = np.geomspace(2e5, 10.0, 25)
+    a, b = climate.to_pressure_levels(f, p, targets), cl.to_pressure_levels(f, p, targets)
+    np.testing.assert_array_equal(np.isnan(a), np.isnan(b))
+    np.testing.assert_allclose(a[~np.isnan(a)], b[~np.isnan(b)], rtol=1e-12, atol=1e-14)
