@@ -19,7 +19,8 @@ Default: the paper's Held-Suarez run (glevel 5, 37 levels to 32 km, dt
 1000 s, 6 acoustic small steps, the planet of Table 1), from an isothermal
 300 K atmosphere at rest with 0.1 K of seeded noise (one of the starts
 Sec. 6.1 lists), mixed precision; --forcing hot_jupiter runs Sec. 6.2's
-(37 levels to 4875 km, dt 600 s, isothermal 1600 K at 220 bar).
+(37 levels to 4875 km, dt 600 s, isothermal 1600 K at rest, 1 bar at the
+surface unless --p-surf says otherwise).
 """
 
 import argparse
@@ -41,11 +42,14 @@ def planet(forcing, table1=True):
 
 def run(thor, glevel=5, nv=37, z_top=32.0e3, dt=1000.0, n_small=6, days=1200.0, spinup_days=200.0, nlat=36,
         sample_hours=24.0, forcing="held_suarez", precision="mixed", seed=1234, hj_dT=300.0, stream=None,
-        table1=True, shallow=False, hydrostatic=False, extras=None):
+        table1=True, shallow=False, hydrostatic=False, extras=None, p_surf=1.0e5):
     """Steps the workload, accumulates one zonal sample every sample_hours
     after the spin-up, and returns (time means (nv, nlat, 9), samples,
     seconds of stepping, final diagnostics). shallow / hydrostatic: the
-    approximation switches of Sec. 3. If extras is a dict it receives the
+    approximation switches of Sec. 3. p_surf: the surface pressure of the
+    resting start (1 bar for both planets: Sec. 6 gives none; p_ref is
+    1 bar, and the hot Jupiter's jet is reported at 800 mbar). If extras is
+    a dict it receives the
     time mean of w at every cell ("w_mean", (ncol, nv)), the unit position
     ("points") and the control-volume area ("areas") of every column."""
     P = planet(forcing, table1)
@@ -53,7 +57,7 @@ def run(thor, glevel=5, nv=37, z_top=32.0e3, dt=1000.0, n_small=6, days=1200.0, 
     prec = thor.THOR_FP64 if precision == "fp64" else thor.THOR_MIXED
     grid = thor.thor_grid_create(glevel, nv, P.radius, z_top, thor.thor_spring(1.15, 1.0, 1.0, 0.01, 1e-5, 100000))
     pl = thor.thor_planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
-    T0, ps = (300.0, 1.0e5) if forcing != "hot_jupiter" else (1600.0, 2.2e7)
+    T0, ps = (300.0 if forcing != "hot_jupiter" else 1600.0), p_surf
     init = thor.thor_init(T0, ps, 0.1, seed, fid, hj_dT, prec, 1, 1, int(shallow), int(hydrostatic))
     st = thor.thor_state_init(grid, pl, init, stream)
     try:
@@ -222,6 +226,7 @@ def main(argv=None):
     ap.add_argument("--spinup", type=float, default=200.0)
     ap.add_argument("--nlat", type=int, default=36)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--p-surf", type=float, default=1.0e5, help="surface pressure of the resting start (Pa)")
     ap.add_argument("--shallow", action="store_true", help="shallow-atmosphere approximation (Sec. 3)")
     ap.add_argument("--hydrostatic", action="store_true", help="hydrostatic approximation (Sec. 3)")
     ap.add_argument("--p-levels", type=int, default=20,
@@ -244,7 +249,8 @@ def main(argv=None):
     means, samples, seconds, diag = run(thor, args.glevel, args.nv, args.z_top, args.dt, args.n_small, args.days,
                                         args.spinup, args.nlat, forcing=args.forcing, precision=args.precision,
                                         stream=s.cuda_stream, table1=not args.workload_planet,
-                                        shallow=args.shallow, hydrostatic=args.hydrostatic, extras=extras)
+                                        shallow=args.shallow, hydrostatic=args.hydrostatic, extras=extras,
+                                        p_surf=args.p_surf)
     P = planet(args.forcing, not args.workload_planet)
     import numpy as np
     pm = means[..., 4]
