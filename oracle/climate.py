@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 Sec. 6.1 judges the Held-Suarez climate by zonal and time averages: the
 eastward and northward wind, temperature, the mass stream function built
 from the averaged northward wind (Eq. for Psi), and the eddy fluxes
-[u'v'] and [v'T'] with phi' = phi - (zonal mean of phi). Reading C-1: on the
+[u'v'] and [v'T'] with phi' = phi - (zonal mean of phi). Reading Z-1: on the
 icosahedral grid a zonal mean is the volume-weighted mean over the cells of
 one level whose latitude falls in one of nlat equal latitude bands (band
 b = floor((lat + pi/2 + 1e-9) / pi * nlat), the north pole in the last band;
@@ -16,8 +16,8 @@ eddy terms are the band covariances [ab] - [a][b] of one state, averaged in
 time by the caller. u and v are the eastward and northward components of
 M / rho (the horizontal velocity; both taken as 0 at the two polar cells,
 where east and north are undefined), T and p follow from Eq. pressure and
-the ideal gas. Reading C-2 (the grid-imprinting map [w*]) is at w_star;
-reading C-3: pressure-level values come from the time- and zonal-mean
+the ideal gas. Reading Z-5 (the grid-imprinting map [w*]) is at w_star;
+reading Z-6: pressure-level values come from the time- and zonal-mean
 fields on model levels, interpolated in p between the two levels whose
 band-mean pressures bracket the target (the paper interpolates each output
 before averaging).
@@ -33,7 +33,7 @@ QUANTITIES = ("weight", "u", "v", "T", "p", "uv", "vT", "uu", "vv")
 
 
 def band_of(points, nlat):
-    """Latitude band of every column (reading C-1)."""
+    """Latitude band of every column (reading Z-1)."""
     _, lat = lonlat(points)
     return np.minimum(np.floor((lat + 0.5 * np.pi + 1e-9) / np.pi * nlat).astype(int), nlat - 1)
 
@@ -82,7 +82,7 @@ def cell_w(model, X):
 
 
 def w_star(model, w_mean, nlat):
-    """The grid-imprinting map of Sec. 6.1 (reading C-2): the time mean [w]
+    """The grid-imprinting map of Sec. 6.1 (reading Z-5): the time mean [w]
     of every cell minus the volume-weighted mean of [w] over its latitude
     band at the same level, (N, nv). The paper writes w* = w - [w] with [.]
     the time average and maps [w*]; taken literally that is zero, so the
@@ -101,7 +101,7 @@ def w_star(model, w_mean, nlat):
 def to_pressure_levels(values, p_mean, p_levels):
     """Sec. 6: results shown against pressure are interpolated linearly to a
     pressure grid after the run. values and p_mean (nv, nlat) on model
-    levels (p_mean the band's mean pressure, reading C-3) ->
+    levels (p_mean the band's mean pressure, reading Z-6) ->
     (len(p_levels), nlat); a target outside a band's pressure range is NaN."""
     nv, nlat = values.shape
     out = np.full((len(p_levels), nlat), np.nan)
