@@ -359,19 +359,17 @@ def run_thor(args):
     shapes = {thor.THOR_FIELD_RHO: (wl.ncol, wl.nv), thor.THOR_FIELD_MOM: (wl.ncol, wl.nv, 3),
               thor.THOR_FIELD_W: (wl.ncol, wl.nv + 1), thor.THOR_FIELD_RHOTHETA: (wl.ncol, wl.nv)}
     host = {f: torch.empty(s, dtype=torch.float64, pin_memory=True) for f, s in shapes.items()}
-    for f, h in host.items():
-        thor.thor_state_get(st, f, wl.ncol, wl.nv, out=h.numpy())
+    bufs = [host[f] for f in thor.PROGNOSTIC]
+    thor.thor_state_get_all(st, wl.ncol, wl.nv, out=bufs)
     e2e_steps = max(1, min(args.steps, 10))
     nbytes = sum(h.numel() * 8 for h in host.values())
     barrier()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for f, h in host.items():
-            thor.thor_state_set(st, f, h)
+        thor.thor_state_set_all(st, *bufs)
         thor.thor_step(st, 1, wl.n_small, wl.dt)
-        for f, h in host.items():
-            thor.thor_state_get(st, f, wl.ncol, wl.nv, out=h.numpy())
+        thor.thor_state_get_all(st, wl.ncol, wl.nv, out=bufs)
     torch.cuda.synchronize(dev)
     barrier()
     t_e2e = max_over_ranks(time.perf_counter() - t0)

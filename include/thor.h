@@ -171,6 +171,17 @@ int thor_diag(thor_state* state, thor_diag_t* out);
 int thor_state_get(thor_state* state, int field, double* host, size_t n);
 int thor_state_set(thor_state* state, int field, const double* host, size_t n);
 
+/* The four prognostic fields at once, each in the layout of thor_state_get
+ * (rho and rho theta [ncol][nv], rho v_h [ncol][nv][3], W [ncol][nv+1]);
+ * ncol and nv must be the grid's, else THOR_EINVAL. The copies and
+ * conversions of all four are queued on the state's stream and the call
+ * synchronises once (page-locked host buffers let the copies run at the
+ * link's rate). Results equal four thor_state_get / thor_state_set calls
+ * bit for bit. */
+int thor_state_get_all(thor_state* state, double* rho, double* mom, double* w, double* rhotheta, int ncol, int nv);
+int thor_state_set_all(thor_state* state, const double* rho, const double* mom, const double* w,
+                       const double* rhotheta, int ncol, int nv);
+
 /* Raw checkpoint of the prognostic state: the stored arrays (deviation form,
  * padded layout) bit for bit after a 64-byte header (magic, precision, ncol,
  * nv). thor_checkpoint_bytes gives the buffer size; save and load copy

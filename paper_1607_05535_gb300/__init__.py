@@ -29,7 +29,8 @@ THOR_MLP_TUNE_TCGEN05 = 0
 EXPORTED = [
     "thor_strerror", "thor_grid_create", "thor_grid_info", "thor_grid_points",
     "thor_grid_neighbours", "thor_grid_areas", "thor_grid_destroy", "thor_state_init",
-    "thor_step", "thor_diag", "thor_state_get", "thor_state_set", "thor_launch_count",
+    "thor_step", "thor_diag", "thor_state_get", "thor_state_set", "thor_state_get_all", "thor_state_set_all",
+    "thor_launch_count",
     "thor_tune", "thor_profile", "thor_profile_read", "thor_state_destroy",
     "thor_mass_noalloc", "thor_mlp_create", "thor_mlp_info", "thor_mlp_get_params",
     "thor_mlp_set_params", "thor_mlp_forward", "thor_mlp_backward", "thor_mlp_train_step",
@@ -102,6 +103,8 @@ def _load():
         "thor_diag": (I, [P, ctypes.POINTER(thor_diag_t)]),
         "thor_state_get": (I, [P, I, P, Z]),
         "thor_state_set": (I, [P, I, P, Z]),
+        "thor_state_get_all": (I, [P, P, P, P, P, I, I]),
+        "thor_state_set_all": (I, [P, P, P, P, P, I, I]),
         "thor_launch_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
         "thor_tune": (I, [P, I, I]),
         "thor_profile": (I, [P, I]),
@@ -240,6 +243,39 @@ def thor_state_set(state, field, host):
     a = host if hasattr(host, "data_ptr") else np.ascontiguousarray(host, dtype=np.float64)
     n = a.numel() if hasattr(a, "numel") else a.size
     _check(_lib.thor_state_set(state, field, _ptr(a), n), "thor_state_set")
+
+
+PROGNOSTIC = (THOR_FIELD_RHO, THOR_FIELD_MOM, THOR_FIELD_W, THOR_FIELD_RHOTHETA)
+
+
+def _checked(a, shape):
+    """A float64 host buffer of the given shape (numpy array or CPU tensor),
+    C-contiguous, without a copy."""
+    if hasattr(a, "data_ptr"):
+        if a.dtype != __import__("torch").float64 or not a.is_contiguous() or tuple(a.shape) != tuple(shape):
+            raise ValueError("expected a contiguous float64 tensor of shape %s" % (shape,))
+    elif a.dtype != np.float64 or not a.flags.c_contiguous or a.shape != tuple(shape):
+        raise ValueError("expected a C-contiguous float64 array of shape %s" % (shape,))
+    return a
+
+
+def thor_state_get_all(state, ncol, nv, out=None):
+    """(rho, mom, w, rhotheta) in the layouts of thor_state_get, one
+    synchronisation; out: four buffers to fill (e.g. page-locked tensors)."""
+    shapes = [_field_shape(f, ncol, nv) for f in PROGNOSTIC]
+    if out is None:
+        out = [np.empty(s, dtype=np.float64) for s in shapes]
+    bufs = [_checked(a, s) for a, s in zip(out, shapes)]
+    _check(_lib.thor_state_get_all(state, *[_ptr(a) for a in bufs], int(ncol), int(nv)), "thor_state_get_all")
+    return tuple(out)
+
+
+def thor_state_set_all(state, rho, mom, w, rhotheta):
+    """All four prognostic fields from host buffers (layouts of
+    thor_state_get), one synchronisation."""
+    ncol, nv = rho.shape
+    bufs = [_checked(a, _field_shape(f, ncol, nv)) for a, f in zip((rho, mom, w, rhotheta), PROGNOSTIC)]
+    _check(_lib.thor_state_set_all(state, *[_ptr(a) for a in bufs], int(ncol), int(nv)), "thor_state_set_all")
 
 
 def thor_launch_count(state):

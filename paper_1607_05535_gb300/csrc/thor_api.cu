@@ -210,7 +210,7 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   const double** vi[] = {&I.V.ri, &I.V.dzc, &I.V.wlo, &I.V.whi, &I.V.Rb, &I.V.ri2, &I.V.inv_dzc};
   for (const double** p : vi) *p = cv.take<double>(nv + 1);
   for (const R** p : vr_slots(I.U)) *p = cv.take<R>(nv + 1);
-  I.staging = cv.take<double>((size_t)ncol * (nv + 1) * 3);
+  I.staging = cv.take<double>((size_t)ncol * (6 * nv + 1));    // rho, 3 x rho v_h, W, rho theta
   I.red = cv.take<double>((size_t)(kDiagBlocks + 1) * 8);
   I.dev_err = cv.take<int>(64);
 }
@@ -332,8 +332,52 @@ int Impl<R>::get(int field, double* host, size_t n) {
 
 template <typename R>
 int Impl<R>::set(int field, const double* host, size_t n) {
+  const size_t need = field == THOR_FIELD_MOM ? (size_t)G.ncol * G.nv * 3
+                    : field == THOR_FIELD_W   ? (size_t)G.ncol * (G.nv + 1)
+                                              : (size_t)G.ncol * G.nv;
+  if (!host || n != need) return THOR_EINVAL;
+  const int rc = set_async(field, host, staging);
+  if (rc) return rc;
+  return cudaStreamSynchronize(stream) == cudaSuccess ? THOR_OK : THOR_ECUDA;
+}
+
+// the element count of a prognostic field, in THOR_FIELD order
+static size_t field_count(int field, int ncol, int nv) {
+  return field == THOR_FIELD_MOM ? (size_t)ncol * nv * 3 : field == THOR_FIELD_W ? (size_t)ncol * (nv + 1)
+                                                                                 : (size_t)ncol * nv;
+}
+
+template <typename R>
+int Impl<R>::set_all(const double* const host[4]) {
+  size_t off = 0;
+  for (int f = 0; f < 4; ++f) {
+    if (!host[f]) return THOR_EINVAL;
+    const int rc = set_async(f, host[f], staging + off);
+    if (rc) return rc;
+    off += field_count(f, G.ncol, G.nv);
+  }
+  return cudaStreamSynchronize(stream) == cudaSuccess ? THOR_OK : THOR_ECUDA;
+}
+
+template <typename R>
+int Impl<R>::get_all(double* const host[4]) {
+  size_t off = 0;
+  for (int f = 0; f < 4; ++f) {
+    if (!host[f]) return THOR_EINVAL;
+    const size_t n = field_count(f, G.ncol, G.nv);
+    dim3 grid((G.ncol + 127) / 128, f == THOR_FIELD_W ? G.nv + 1 : G.nv);
+    k_to_canonical<R><<<grid, 128, 0, stream>>>(staging + off, G, V, ph, Xt, f);
+    ++launches;
+    if (cudaMemcpyAsync(host[f], staging + off, n * sizeof(double), cudaMemcpyDeviceToHost, stream))
+      return THOR_ECUDA;
+    off += n;
+  }
+  return cudaStreamSynchronize(stream) == cudaSuccess ? THOR_OK : THOR_ECUDA;
+}
+
+template <typename R>
+int Impl<R>::set_async(int field, const double* host, double* buf) {
   const int nv = G.nv;
-  if (!host) return THOR_EINVAL;
   int nlev = nv, ncomp = 1, zero_ends = 0;
   const double* ref = nullptr;
   R *d0 = nullptr, *d1 = nullptr, *d2 = nullptr;
@@ -344,13 +388,12 @@ int Impl<R>::set(int field, const double* host, size_t n) {
     case THOR_FIELD_RHOTHETA: ref = V.thb; d0 = Xt.th; break;
     default: return THOR_EINVAL;
   }
-  if (n != (size_t)G.ncol * nlev * ncomp) return THOR_EINVAL;
-  if (cudaMemcpyAsync(staging, host, n * sizeof(double), cudaMemcpyHostToDevice, stream)) return THOR_ECUDA;
+  const size_t n = (size_t)G.ncol * nlev * ncomp;
+  if (cudaMemcpyAsync(buf, host, n * sizeof(double), cudaMemcpyHostToDevice, stream)) return THOR_ECUDA;
   dim3 grid((G.ncol + 127) / 128, nlev);
-  k_from_canonical<R><<<grid, 128, 0, stream>>>(staging, G.ncol, G.colp, nlev, ncomp, ref, d0, d1, d2,
-                                                 zero_ends);
+  k_from_canonical<R><<<grid, 128, 0, stream>>>(buf, G.ncol, G.colp, nlev, ncomp, ref, d0, d1, d2, zero_ends);
   ++launches;
-  return cudaStreamSynchronize(stream) == cudaSuccess ? THOR_OK : THOR_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? THOR_OK : THOR_ECUDA;
 }
 
 template <typename R>
@@ -746,6 +789,19 @@ int thor_state_get(thor_state* s, int field, double* host, size_t n) {
 int thor_state_set(thor_state* s, int field, const double* host, size_t n) {
   if (!s) return THOR_EINVAL;
   return s->impl->set(field, host, n);
+}
+
+int thor_state_get_all(thor_state* s, double* rho, double* mom, double* w, double* rhotheta, int ncol, int nv) {
+  if (!s || ncol != s->grid->h.ncol || nv != s->grid->h.nv) return THOR_EINVAL;
+  double* const host[4] = {rho, mom, w, rhotheta};
+  return s->impl->get_all(host);
+}
+
+int thor_state_set_all(thor_state* s, const double* rho, const double* mom, const double* w, const double* rhotheta,
+                       int ncol, int nv) {
+  if (!s || ncol != s->grid->h.ncol || nv != s->grid->h.nv) return THOR_EINVAL;
+  const double* const host[4] = {rho, mom, w, rhotheta};
+  return s->impl->set_all(host);
 }
 
 int thor_launch_count(const thor_state* s, long long* count) {

@@ -89,6 +89,9 @@ struct ImplBase {
   virtual int diag(double* out8, long long* nonfinite) = 0;
   virtual int get(int field, double* host, size_t n) = 0;
   virtual int set(int field, const double* host, size_t n) = 0;
+  // the four prognostic fields (RHO, MOM, W, RHOTHETA) with one synchronisation
+  virtual int get_all(double* const host[4]) = 0;
+  virtual int set_all(const double* const host[4]) = 0;
   virtual void set_graph(bool on) = 0;
   long long launches = 0;
   int kchunk = 2;                      // levels per thread in the stencil kernels
@@ -169,7 +172,7 @@ struct Impl : ImplBase {
   double diff_D = 0, dbar4 = 0, hj_dT = 300.0;
   // device allocations
   void* arena = nullptr;
-  double* staging = nullptr;       // canonical-order float64 transfer buffer
+  double* staging = nullptr;       // canonical-order float64 transfer buffer (room for all four fields)
   double* red = nullptr;           // reduction partials
   int red_blocks = 0;
 
@@ -246,6 +249,9 @@ struct Impl : ImplBase {
   int diag(double* out8, long long* nonfinite) override;
   int get(int field, double* host, size_t n) override;
   int set(int field, const double* host, size_t n) override;
+  int get_all(double* const host[4]) override;
+  int set_all(const double* const host[4]) override;
+  int set_async(int field, const double* host, double* buf);   // queue one field, no synchronisation
   // rho, M (3), rho theta: nv planes each; W: nv + 1 planes; buf in device or
   // host memory (unified addressing)
   size_t state_bytes() const override { return (size_t)(6 * G.nv + 1) * G.colp * sizeof(R); }

@@ -178,3 +178,35 @@ def test_nonfinite_watchdog():
         assert thor.thor_diag(p.state)["nonfinite"] > 0
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("precision", [thor.THOR_FP64, thor.THOR_MIXED])
+def test_whole_state_transfers_equal_per_field_ones(precision):
+    """thor_state_get_all / thor_state_set_all give the same bytes as four
+    thor_state_get / thor_state_set calls, into page-locked tensors as the
+    benchmark uses them; shape and size mismatches are refused."""
+    p = Pair(SMALL, precision=precision)
+    q = Pair(SMALL, precision=precision)
+    try:
+        thor.thor_step(p.state, 1, SMALL.n_small, SMALL.dt)
+        per_field = [thor.thor_state_get(p.state, f, p.ncol, p.nv) for f in thor.PROGNOSTIC]
+        bufs = [torch.empty(a.shape, dtype=torch.float64, pin_memory=True) for a in per_field]
+        thor.thor_state_get_all(p.state, p.ncol, p.nv, out=bufs)
+        for a, b in zip(per_field, bufs):
+            assert np.array_equal(a, b.numpy())
+        rng = np.random.default_rng(3)
+        new = [a * (1.0 + 1e-3 * rng.standard_normal(a.shape)) for a in per_field]
+        thor.thor_state_set_all(q.state, *new)
+        for f, a in zip(thor.PROGNOSTIC, new):
+            thor.thor_state_set(p.state, f, a)
+        for f in thor.PROGNOSTIC:
+            assert np.array_equal(thor.thor_state_get(p.state, f, p.ncol, p.nv),
+                                  thor.thor_state_get(q.state, f, q.ncol, q.nv))
+        with pytest.raises(ValueError):
+            thor.thor_state_set_all(q.state, new[0], new[1], new[2][:, :-1].copy(), new[3])
+        with pytest.raises(thor.ThorError):
+            thor.thor_state_get_all(q.state, p.ncol + 1, p.nv,
+                                    out=[np.empty(thor._field_shape(f, p.ncol + 1, p.nv)) for f in thor.PROGNOSTIC])
+    finally:
+        p.close()
+        q.close()
