@@ -23,3 +23,12 @@ def oracle_grid(glevel, modified=True, max_iter=100000, tol=1e-5):
     if key not in _GRIDS:
         _GRIDS[key] = build_grid(glevel, modified=modified, max_iter=max_iter, tol=tol)
     return _GRIDS[key]
+
+
+def report_dir():
+    """Folder for the measured reports some GPU tests write (JSON, text), from
+    the THOR_REPORT_DIR environment variable; None (no report) when unset or
+    not a folder."""
+    import os
+    d = os.environ.get("THOR_REPORT_DIR")
+    return d if d and os.path.isdir(d) else None

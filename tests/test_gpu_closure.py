@@ -15,6 +15,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import paper_1607_05535_gb300 as thor
+from conftest import report_dir
 from paper_1607_05535_gb300 import closure as cl
 import workloads as wls
 
@@ -168,8 +169,8 @@ def test_closure_gain_over_plain_coarse_method():
     report.update({"aggregation_loss_history": hists, "rollout_window": window,
                    "rollout_rmse_closure": e_c.tolist(), "rollout_rmse_plain": e_p.tolist(),
                    "rollouts": runs, "a_posteriori_gain": float(1.0 - e_c.mean() / e_p.mean())})
-    out = os.path.join(os.path.dirname(os.path.dirname(__file__)), "gpurun_out")
-    if os.path.isdir(out):
+    out = report_dir()
+    if out:
         json.dump(report, open(os.path.join(out, "closure_report.json"), "w"), indent=1)
     print({k: v for k, v in report.items() if "history" not in k})
     assert hist[-1] < hist[0]

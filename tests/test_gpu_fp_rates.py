@@ -12,6 +12,8 @@ import tempfile
 
 import pytest
 
+from conftest import report_dir
+
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -25,9 +27,8 @@ def test_float64_issue_rates():
                         os.path.join(HERE, "probes", "fp_rates.cu")], check=True)
         out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
     rates = {k: float(v) for k, v in (line.split() for line in out.strip().splitlines())}
-    root = os.path.dirname(HERE)
-    if os.path.isdir(os.path.join(root, "gpurun_out")):
-        with open(os.path.join(root, "gpurun_out", "fp_rates.txt"), "w") as f:
+    if report_dir():
+        with open(os.path.join(report_dir(), "fp_rates.txt"), "w") as f:
             f.write(out)
     print(rates)
     assert all(v > 0 for v in rates.values()), rates

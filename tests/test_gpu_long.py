@@ -15,6 +15,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import paper_1607_05535_gb300 as thor
+from conftest import report_dir
 from harness import init_struct, planet_struct
 import workloads as wls
 
@@ -69,8 +70,8 @@ def test_mixed_against_float64_at_10_100_1000_large_steps():
         thor.thor_state_destroy(a)
         thor.thor_state_destroy(b)
         thor.thor_grid_destroy(grid)
-    out = os.path.join(os.path.dirname(os.path.dirname(__file__)), "gpurun_out")
-    if os.path.isdir(out):
+    out = report_dir()
+    if out:
         json.dump(report, open(os.path.join(out, "mixed_long.json"), "w"), indent=1)
     print(report)
     r10, r100, r1000 = report[10], report[100], report[1000]

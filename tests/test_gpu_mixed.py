@@ -16,6 +16,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import paper_1607_05535_gb300 as thor
+from conftest import report_dir
 from harness import Pair
 from oracle import dycore as dc
 from oracle import operators as op
@@ -55,8 +56,8 @@ def test_mixed_vs_oracle_held_suarez_g4():
         rep = field_report(p, p.get(), ref)
     finally:
         p.close()
-    out = os.path.join(os.path.dirname(os.path.dirname(__file__)), "gpurun_out")
-    if os.path.isdir(out):
+    out = report_dir()
+    if out:
         json.dump(rep, open(os.path.join(out, "mixed_errors_g4.json"), "w"), indent=1)
     print(rep)
     for k, g in GATES.items():
