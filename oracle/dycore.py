@@ -393,17 +393,41 @@ def hydrostatic_profile(model, T, p_surf):
     return p
 
 
-def initial_state(model, T0, p_surf, noise_amp=0.0, u=None):
+def held_suarez_start_profile(model, p_surf, tol=1e-12, max_iter=1000):
+    """The layer temperatures of the Held-Suarez start of Sec. 6.1: every
+    column at rest with the T_eq of Sec. 6.1 at the equator, in hydrostatic
+    equilibrium. T_eq depends on p and the balanced p on T, so the column is
+    the fixed point T = T_eq(p(T)) with p(T) = hydrostatic_profile, iterated
+    from 315 K until no layer moves by more than tol K. Returns (T, p)."""
+    from .physics import held_suarez_coefficients
+    nv = model.vg.nv
+    T = np.full(nv, 315.0)
+    for _ in range(max_iter):
+        p = hydrostatic_profile(model, T, p_surf)
+        T_new = held_suarez_coefficients(np.ones(nv), p, np.zeros(nv), model.planet.kappa)[2]
+        done = np.abs(T_new - T).max() <= tol
+        T = T_new
+        if done:
+            return T, hydrostatic_profile(model, T, p_surf)
+    raise RuntimeError("the Held-Suarez start profile did not converge")
+
+
+def initial_state(model, T0, p_surf, noise_amp=0.0, u=None, profile=None):
     """Isothermal atmosphere at rest in discrete hydrostatic balance (Sec. 6
     starts both benchmarks at rest in hydrostatic equilibrium). With
     ``noise_amp`` > 0 the temperature gets amp (2u - 1) at fixed pressure, so
     the perturbation is carried by the density; ``u`` (N, nv) in [0, 1) are
-    the random numbers, passed in."""
+    the random numbers, passed in. profile="held_suarez": the layer
+    temperatures of held_suarez_start_profile instead of T0."""
     pl = model.planet
     N, nv = model.grid.ncol, model.vg.nv
-    p1 = hydrostatic_profile(model, np.full(nv, T0), p_surf)
+    if profile == "held_suarez":
+        T1, p1 = held_suarez_start_profile(model, p_surf)
+    else:
+        T1 = np.full(nv, float(T0))
+        p1 = hydrostatic_profile(model, T1, p_surf)
     p = np.broadcast_to(p1, (N, nv)).copy()
-    T = np.full((N, nv), float(T0))
+    T = np.broadcast_to(T1, (N, nv)).copy()
     if noise_amp > 0.0:
         T = T + noise_amp * (2.0 * u - 1.0)
     rho = p / (pl.Rd * T)

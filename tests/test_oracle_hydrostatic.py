@@ -134,3 +134,25 @@ def test_switch_off_is_the_nonhydrostatic_model():
     dM = np.abs(h.M - a.M).max() / np.abs(a.M).max()
     dW = np.abs(h.W - a.W).max() / np.abs(a.W).max()
     assert 0 < dM < 1e-2 and dW > 10 * dM, (dM, dW)
+
+
+def test_held_suarez_start_profile():
+    """Sec. 6.1's start: every layer at the equatorial T_eq of its own
+    pressure (written out here: max(200 K, (315 K - 10 K ln(p / 1e5 Pa))
+    (p / 1e5 Pa)^kappa)), the column in discrete hydrostatic balance, the
+    same profile in every column, at rest; near the ground T_eq is about
+    315 K and the top of a 30 km column is on the 200 K floor."""
+    m = _model(False, nv=30)
+    X = dc.initial_state(m, 0.0, 1.0e5, profile="held_suarez")
+    pl = m.planet
+    p = dc.pressure(pl, X.Th)
+    T = p / (pl.Rd * X.rho)
+    kappa = pl.Rd / pl.cp
+    T_eq = np.maximum(200.0, (315.0 - 10.0 * np.log(p / 1e5)) * (p / 1e5) ** kappa)
+    assert np.abs(T - T_eq).max() < 1e-9
+    assert _imbalance(m, X) < 1e-12
+    assert np.abs(T - T[:1]).max() == 0.0 and not X.M.any() and not X.W.any()
+    assert 300.0 < T[0, 0] < 316.0 and abs(T[0, -1] - 200.0) < 1e-9
+    # and it stays at rest without forcing
+    Y = dc.run(_model(False, nv=30), X, 2, 6, 600.0)
+    assert np.abs(Y.M).max() < 1e-8 * np.abs(Y.rho).max() and np.abs(Y.W).max() < 1e-8
