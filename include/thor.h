@@ -125,7 +125,16 @@ typedef struct {
  * diffusion) is dropped, so that the vertical equation of every small step
  * (Eq. momr2) reads 0 = -dp/dr - g rho at the new state and the column solve
  * diagnoses W from it (same tridiagonal system without the identity term).
- * Both switches may be combined; any nonzero value counts as 1. */
+ * Both switches may be combined; any nonzero value counts as 1.
+ * profile: THOR_PROFILE_ISOTHERMAL (0) = the layers at T0 as above;
+ * THOR_PROFILE_HELD_SUAREZ (1) = the start of Sec. 6.1's run: every layer
+ * at the equatorial Held-Suarez T_eq of its own pressure,
+ * max(200 K, (315 K - 10 K ln(p / 1e5 Pa)) (p / 1e5 Pa)^(Rd/cp)), the column
+ * in the same discrete hydrostatic balance (found as the fixed point
+ * T = T_eq(p(T)) to 1e-12 K, else THOR_ENOTCONV), T0 ignored; noise_amp
+ * still adds its perturbation. The balanced start column is also the
+ * reference column of the deviation form. */
+enum { THOR_PROFILE_ISOTHERMAL = 0, THOR_PROFILE_HELD_SUAREZ = 1 };
 typedef struct {
   double T0, p_surf, noise_amp;
   unsigned long long seed;
@@ -136,6 +145,7 @@ typedef struct {
   int divergence_damping;
   int shallow;
   int hydrostatic;
+  int profile;
 } thor_init;
 
 /* Allocate the device state for `grid` and set the initial condition. The

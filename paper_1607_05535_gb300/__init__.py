@@ -58,13 +58,16 @@ class thor_planet(ctypes.Structure):
                 ("p_ref", ctypes.c_double), ("diff_D", ctypes.c_double)]
 
 
+THOR_PROFILE_ISOTHERMAL, THOR_PROFILE_HELD_SUAREZ = 0, 1
+
+
 class thor_init(ctypes.Structure):
     _fields_ = [("T0", ctypes.c_double), ("p_surf", ctypes.c_double),
                 ("noise_amp", ctypes.c_double), ("seed", ctypes.c_ulonglong),
                 ("forcing", ctypes.c_int), ("hj_dT", ctypes.c_double),
                 ("precision", ctypes.c_int), ("hyperdiffusion", ctypes.c_int),
                 ("divergence_damping", ctypes.c_int), ("shallow", ctypes.c_int),
-                ("hydrostatic", ctypes.c_int)]
+                ("hydrostatic", ctypes.c_int), ("profile", ctypes.c_int)]
 
 
 class thor_diag_t(ctypes.Structure):

@@ -16,11 +16,12 @@ follows; zonal means go to pressure levels by linear interpolation in p
     python -m paper_1607_05535_gb300.climate --days 1200 --spinup 200 --out run.json
 
 Default: the paper's Held-Suarez run (glevel 5, 37 levels to 32 km, dt
-1000 s, 6 acoustic small steps, the planet of Table 1), from an isothermal
-300 K atmosphere at rest with 0.1 K of seeded noise (one of the starts
-Sec. 6.1 lists), mixed precision; --forcing hot_jupiter runs Sec. 6.2's
-(37 levels to 4875 km, dt 600 s, isothermal 1600 K at rest, 1 bar at the
-surface unless --p-surf says otherwise).
+1000 s, 6 acoustic small steps, the planet of Table 1), from rest with the
+equatorial T_eq in every column in hydrostatic balance (the start of Sec.
+6.1; --isothermal starts from 300 K with 0.1 K of seeded noise instead),
+mixed precision; --forcing hot_jupiter runs Sec. 6.2's
+(37 levels to 4875 km, dt 600 s, isothermal 1600 K at rest without noise,
+1 bar at the surface unless --p-surf says otherwise).
 """
 
 import argparse
@@ -42,14 +43,17 @@ def planet(forcing, table1=True):
 
 def run(thor, glevel=5, nv=37, z_top=32.0e3, dt=1000.0, n_small=6, days=1200.0, spinup_days=200.0, nlat=36,
         sample_hours=24.0, forcing="held_suarez", precision="mixed", seed=1234, hj_dT=300.0, stream=None,
-        table1=True, shallow=False, hydrostatic=False, extras=None, p_surf=1.0e5):
+        table1=True, shallow=False, hydrostatic=False, extras=None, p_surf=1.0e5, profile=None, noise=0.1):
     """Steps the workload, accumulates one zonal sample every sample_hours
     after the spin-up, and returns (time means (nv, nlat, 9), samples,
     seconds of stepping, final diagnostics). shallow / hydrostatic: the
     approximation switches of Sec. 3. p_surf: the surface pressure of the
     resting start (1 bar for both planets: Sec. 6 gives none; p_ref is
-    1 bar, and the hot Jupiter's jet is reported at 800 mbar). If extras is
-    a dict it receives the
+    1 bar, and the hot Jupiter's jet is reported at 800 mbar). profile:
+    "held_suarez" starts every column at the equatorial T_eq of Sec. 6.1 in
+    hydrostatic balance (the paper's start), None isothermal; noise: the
+    amplitude (K) of the seeded temperature noise. If extras is a dict it
+    receives the
     time mean of w at every cell ("w_mean", (ncol, nv)), the unit position
     ("points") and the control-volume area ("areas") of every column."""
     P = planet(forcing, table1)
@@ -58,7 +62,8 @@ def run(thor, glevel=5, nv=37, z_top=32.0e3, dt=1000.0, n_small=6, days=1200.0, 
     grid = thor.thor_grid_create(glevel, nv, P.radius, z_top, thor.thor_spring(1.15, 1.0, 1.0, 0.01, 1e-5, 100000))
     pl = thor.thor_planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
     T0, ps = (300.0 if forcing != "hot_jupiter" else 1600.0), p_surf
-    init = thor.thor_init(T0, ps, 0.1, seed, fid, hj_dT, prec, 1, 1, int(shallow), int(hydrostatic))
+    init = thor.thor_init(T0, ps, noise, seed, fid, hj_dT, prec, 1, 1, int(shallow), int(hydrostatic),
+                          thor.THOR_PROFILE_HELD_SUAREZ if profile == "held_suarez" else thor.THOR_PROFILE_ISOTHERMAL)
     st = thor.thor_state_init(grid, pl, init, stream)
     try:
         per_sample = max(1, round(sample_hours * 3600.0 / dt))
@@ -227,6 +232,8 @@ def main(argv=None):
     ap.add_argument("--nlat", type=int, default=36)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--p-surf", type=float, default=1.0e5, help="surface pressure of the resting start (Pa)")
+    ap.add_argument("--isothermal", action="store_true",
+                    help="Held-Suarez from an isothermal 300 K start with 0.1 K of noise instead of the T_eq profile")
     ap.add_argument("--shallow", action="store_true", help="shallow-atmosphere approximation (Sec. 3)")
     ap.add_argument("--hydrostatic", action="store_true", help="hydrostatic approximation (Sec. 3)")
     ap.add_argument("--p-levels", type=int, default=20,
@@ -250,7 +257,9 @@ def main(argv=None):
                                         args.spinup, args.nlat, forcing=args.forcing, precision=args.precision,
                                         stream=s.cuda_stream, table1=not args.workload_planet,
                                         shallow=args.shallow, hydrostatic=args.hydrostatic, extras=extras,
-                                        p_surf=args.p_surf)
+                                        p_surf=args.p_surf,
+                                        profile=None if (hj or args.isothermal) else "held_suarez",
+                                        noise=0.1 if (args.isothermal and not hj) else 0.0)
     P = planet(args.forcing, not args.workload_planet)
     import numpy as np
     pm = means[..., 4]

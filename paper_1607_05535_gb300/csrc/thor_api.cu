@@ -430,7 +430,40 @@ struct HostSetup {
   std::vector<double> rho, th;    // canonical [ncol][nv]
 };
 
-void host_setup(const HostGrid& h, const thor_planet& pl, const thor_init& in, HostSetup& hs) {
+// The start column of Sec. 6.1's Held-Suarez run: every layer at the
+// equatorial T_eq of its own pressure, max(200, (315 - 10 ln(p/p0)) (p/p0)^kappa)
+// with p0 = 1e5 Pa, in the discrete hydrostatic balance of the reference
+// column below. Layer by layer from the ground, T_k is the fixed point of
+// T -> T_eq(p_k(T)), p_k(T) the balanced pressure over layer k-1; returns
+// false when a layer does not settle to 1e-12 K.
+static bool held_suarez_column(const std::vector<double>& zc, const std::vector<double>& dzc,
+                               const std::vector<double>& wlo, const std::vector<double>& whi, double p_surf,
+                               double g, double Rd, double kappa, std::vector<double>& T, std::vector<double>& p) {
+  const int nv = (int)zc.size();
+  auto teq = [&](double pp) {
+    const double s = pp / 1.0e5;
+    return std::fmax(200.0, (315.0 - 10.0 * std::log(s)) * std::pow(s, kappa));
+  };
+  auto balanced = [&](int k, double Tk) {
+    if (k == 0) return p_surf * std::exp(-g * zc[0] / (Rd * Tk));
+    return p[k - 1] * (1.0 - g * dzc[k] * wlo[k] / (Rd * T[k - 1])) / (1.0 + g * dzc[k] * whi[k] / (Rd * Tk));
+  };
+  for (int k = 0; k < nv; ++k) {
+    double t = k == 0 ? 315.0 : T[k - 1];
+    bool settled = false;
+    for (int it = 0; it < 1000 && !settled; ++it) {
+      const double tn = teq(balanced(k, t));
+      settled = std::fabs(tn - t) <= 1e-12;
+      t = tn;
+    }
+    if (!settled) return false;
+    T[k] = t;
+    p[k] = balanced(k, t);
+  }
+  return true;
+}
+
+int host_setup(const HostGrid& h, const thor_planet& pl, const thor_init& in, HostSetup& hs) {
   const int nv = h.nv, ncol = h.ncol;
   std::vector<double> zi(nv + 1), zc(nv);
   const double step = h.z_top / nv;
@@ -467,15 +500,21 @@ void host_setup(const HostGrid& h, const thor_planet& pl, const thor_init& in, H
     wlo[i] = (zi[i] - zc[i]) / (zc[i - 1] - zc[i]);
     whi[i] = (zi[i] - zc[i - 1]) / (zc[i] - zc[i - 1]);
   }
-  const double g = pl.gravity, Rd = pl.Rd, T0 = in.T0;
+  const double g = pl.gravity, Rd = pl.Rd;
   const double gamma = pl.cp / (pl.cp - Rd);
-  // discretely balanced isothermal reference column:
-  // (p_i - p_i-1)/dzc + g (wlo rho_i-1 + whi rho_i) = 0 with rho = p/(Rd T0)
-  pb[0] = in.p_surf * std::exp(-g * zc[0] / (Rd * T0));
-  for (int i = 1; i < nv; ++i)
-    pb[i] = pb[i - 1] * (1.0 - g * dzc[i] * wlo[i] / (Rd * T0)) / (1.0 + g * dzc[i] * whi[i] / (Rd * T0));
+  // discretely balanced reference column, isothermal at T0 or the
+  // Held-Suarez start: (p_i - p_i-1)/dzc + g (wlo rho_i-1 + whi rho_i) = 0
+  // with rho = p/(Rd T)
+  std::vector<double> Tcol(nv, in.T0);
+  if (in.profile == THOR_PROFILE_HELD_SUAREZ) {
+    if (!held_suarez_column(zc, dzc, wlo, whi, in.p_surf, g, Rd, Rd / pl.cp, Tcol, pb)) return THOR_ENOTCONV;
+  } else {
+    pb[0] = in.p_surf * std::exp(-g * zc[0] / (Rd * in.T0));
+    for (int i = 1; i < nv; ++i)
+      pb[i] = pb[i - 1] * (1.0 - g * dzc[i] * wlo[i] / (Rd * in.T0)) / (1.0 + g * dzc[i] * whi[i] / (Rd * in.T0));
+  }
   for (int k = 0; k < nv; ++k) {
-    rhob[k] = pb[k] / (Rd * T0);
+    rhob[k] = pb[k] / (Rd * Tcol[k]);
     thb[k] = pl.p_ref / Rd * std::pow(pb[k] / pl.p_ref, 1.0 / gamma);
     Tb[k] = pb[k] / (rhob[k] * Rd);
   }
@@ -485,15 +524,16 @@ void host_setup(const HostGrid& h, const thor_planet& pl, const thor_init& in, H
   hs.th.assign((size_t)ncol * nv, 0.0);
   for (int c = 0; c < ncol; ++c)
     for (int k = 0; k < nv; ++k) {
-      double T = T0;
+      double T = Tcol[k];
       if (in.noise_amp > 0.0) {
         uint64_t z = splitmix64(in.seed ^ ((uint64_t)c * (uint64_t)nv + (uint64_t)k));
         double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
-        T = T0 + in.noise_amp * (2.0 * u - 1.0);
+        T = Tcol[k] + in.noise_amp * (2.0 * u - 1.0);
       }
       hs.rho[(size_t)c * nv + k] = pb[k] / (Rd * T);
       hs.th[(size_t)c * nv + k] = thb[k];
     }
+  return THOR_OK;
 }
 
 template <typename R>
@@ -558,8 +598,9 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
     I->side = nullptr;
   }
   HostSetup hs;
-  host_setup(h, pl, in, hs);
-  int rc = upload_tables(*I, h, hs.vert, st);
+  int rc = host_setup(h, pl, in, hs);
+  if (rc) return rc;
+  rc = upload_tables(*I, h, hs.vert, st);
   if (rc) return rc;
   rc = I->set(THOR_FIELD_RHO, hs.rho.data(), hs.rho.size());
   if (rc) return rc;
@@ -653,7 +694,9 @@ int thor_state_init(thor_grid* grid, const thor_planet* pl, const thor_init* in,
   if (!grid || !pl || !in || !out) return THOR_EINVAL;
   if (!(pl->radius > 0) || std::fabs(pl->radius - grid->h.radius) > 1e-9 * grid->h.radius ||
       !(pl->Rd > 0) || !(pl->cp > pl->Rd) || !(pl->gravity > 0) || !(pl->p_ref > 0) || !(pl->diff_D >= 0) ||
-      !(in->T0 > 0) || !(in->p_surf > 0) || !(in->noise_amp >= 0) || in->forcing < 0 || in->forcing > 2 ||
+      !(in->T0 > 0 || in->profile == THOR_PROFILE_HELD_SUAREZ) || !(in->p_surf > 0) || !(in->noise_amp >= 0) ||
+      in->profile < THOR_PROFILE_ISOTHERMAL || in->profile > THOR_PROFILE_HELD_SUAREZ || in->forcing < 0 ||
+      in->forcing > 2 ||
       (in->precision != THOR_FP64 && in->precision != THOR_MIXED) || grid->h.nv > thor::kMaxNv)
     return THOR_EINVAL;
   thor_state* s = new (std::nothrow) thor_state;

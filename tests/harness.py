@@ -19,9 +19,9 @@ def planet_struct(P):
     return thor.thor_planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
 
 
-def init_struct(wl, precision=thor.THOR_FP64, hyper=1, divdamp=1, shallow=0, hydrostatic=0):
+def init_struct(wl, precision=thor.THOR_FP64, hyper=1, divdamp=1, shallow=0, hydrostatic=0, profile=0):
     return thor.thor_init(wl.T0, wl.p_surf, wl.noise_amp, wl.seed, FORCING[wl.forcing], wl.hj_dT,
-                          precision, hyper, divdamp, shallow, hydrostatic)
+                          precision, hyper, divdamp, shallow, hydrostatic, profile)
 
 
 class Pair:
@@ -29,15 +29,17 @@ class Pair:
     column c."""
 
     def __init__(self, wl, precision=thor.THOR_FP64, hyper=True, divdamp=True, stream=None, shallow=False,
-                 hydrostatic=False):
+                 hydrostatic=False, profile=False):
         self.wl = wl
         sp = thor.thor_spring(1.15, 1.0, 1.0, 0.01, wl.spring_tol, wl.spring_max_iter)
         self.grid = thor.thor_grid_create(wl.glevel, wl.nv, wl.planet.radius, wl.z_top, sp)
         self.state = thor.thor_state_init(self.grid, planet_struct(wl.planet),
                                           init_struct(wl, precision, int(hyper), int(divdamp), int(shallow),
-                                                      int(hydrostatic)),
+                                                      int(hydrostatic),
+                                                      thor.THOR_PROFILE_HELD_SUAREZ if profile else 0),
                                           stream)
         self.ncol, self.nv = wl.ncol, wl.nv
+        self.profile = "held_suarez" if profile else None
         P = wl.planet
         G = oracle_grid(wl.glevel, max_iter=wl.spring_max_iter, tol=wl.spring_tol)
         pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
@@ -56,7 +58,7 @@ class Pair:
         if self.wl.noise_amp > 0:
             u = np.empty((self.ncol, self.nv))
             u[self.perm] = wls.temperature_noise(self.wl)
-        return dc.initial_state(self.model, self.wl.T0, self.wl.p_surf, self.wl.noise_amp, u)
+        return dc.initial_state(self.model, self.wl.T0, self.wl.p_surf, self.wl.noise_amp, u, profile=self.profile)
 
     def get(self):
         """Library state as an oracle State in oracle column order."""

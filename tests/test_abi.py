@@ -33,6 +33,29 @@ def test_invalid_arguments():
     assert thor.thor_strerror(thor.THOR_ETIMEOUT) == "device wait timed out"
 
 
+def test_state_init_argument_checks_need_no_device():
+    """thor_state_init refuses a bad start (unknown profile, T0 <= 0 for the
+    isothermal profile, a planet radius other than the grid's) on the host,
+    before any CUDA call."""
+    grid = thor.thor_grid_create(2, 4, 6.4e6, 3e4, thor.thor_spring(1.15, 1.0, 1.0, 0.01, 0.0, 5))
+    try:
+        planet = thor.thor_planet(6.4e6, 7.292e-5, 9.8, 287.0, 1005.0, 1.0e5, 0.0)
+        for kw in (dict(profile=2), dict(profile=-1), dict(T0=0.0), dict(T0=-5.0, profile=0)):
+            a = dict(T0=300.0, profile=0)
+            a.update(kw)
+            init = thor.thor_init(a["T0"], 1.0e5, 0.0, 1, 0, 300.0, thor.THOR_FP64, 1, 1, 0, 0, a["profile"])
+            with pytest.raises(thor.ThorError) as e:
+                thor.thor_state_init(grid, planet, init)
+            assert e.value.status == thor.THOR_EINVAL, kw
+        bad = thor.thor_planet(6.5e6, 7.292e-5, 9.8, 287.0, 1005.0, 1.0e5, 0.0)
+        init = thor.thor_init(300.0, 1.0e5, 0.0, 1, 0, 300.0, thor.THOR_FP64, 1, 1, 0, 0, 0)
+        with pytest.raises(thor.ThorError) as e:
+            thor.thor_state_init(grid, bad, init)
+        assert e.value.status == thor.THOR_EINVAL
+    finally:
+        thor.thor_grid_destroy(grid)
+
+
 def test_ensemble_argument_checks_need_no_device():
     """Argument errors of the ensemble and autotuner entry points are caught
     on the host, before any CUDA call."""

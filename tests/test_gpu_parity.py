@@ -210,3 +210,28 @@ def test_whole_state_transfers_equal_per_field_ones(precision):
     finally:
         p.close()
         q.close()
+
+
+@pytest.mark.parametrize("precision", [thor.THOR_FP64, thor.THOR_MIXED])
+def test_held_suarez_start_profile(precision):
+    """THOR_PROFILE_HELD_SUAREZ: the start of Sec. 6.1 (equatorial T_eq in
+    discrete hydrostatic balance, found by the library's own layer-by-layer
+    fixed point) equals the oracle's column fixed point, and two forced large
+    steps from it match the oracle (float64) or stay within the mixed gates."""
+    wl = SMALL.with_(forcing="held_suarez", noise_amp=0.0)
+    p = Pair(wl, precision=precision, profile=True)
+    try:
+        X = p.oracle_initial()
+        _assert_close(p.get(), X, 1e-13 if precision == thor.THOR_FP64 else 1e-7)
+        ref = dc.run(p.model, X, 2, wl.n_small, wl.dt)
+        thor.thor_step(p.state, 2, wl.n_small, wl.dt)
+        assert np.abs(ref.M / ref.rho[..., None]).max() > 1e-4            # the forcing moves air
+        if precision == thor.THOR_FP64:
+            _assert_close(p.get(), ref)
+        else:
+            from test_gpu_mixed import GATES, field_report
+            rep = field_report(p, p.get(), ref)
+            for k, g in GATES.items():
+                assert rep[k] < g, (k, rep)
+    finally:
+        p.close()
