@@ -21,10 +21,16 @@ TOL = 1e-10
 SMALL = wls.HS_G4.with_(name="hs_g3_L12", glevel=3, nv=12, n_large=2)
 
 
-def _assert_close(A, B, tol=TOL):
+def _assert_close(A, B, tol=TOL, w_scale=0.0):
+    """Every field within tol relative L2; with w_scale > 0, W may instead
+    pass at 1e-12 w_scale absolute: from a column in discrete balance W
+    answers the difference -dp/dr - g rho of nearly equal terms of size
+    w_scale = g rho dtau per small step, which float64 rounds at about
+    1e-16 w_scale in either implementation, however small W itself is."""
     e = field_errors(A, B)
     assert e["rho"] < tol and e["Th"] < tol, e
-    assert e["M"] < tol and e["W"] < tol, e
+    assert e["M"] < tol, e
+    assert e["W"] < tol or e["W_maxabs"] < 1e-12 * w_scale, e
     return e
 
 
@@ -218,11 +224,10 @@ def test_held_suarez_start_profile(precision):
     discrete hydrostatic balance, found by the library's own layer-by-layer
     fixed point) equals the oracle's column fixed point; two forced large
     steps from the library's start match the oracle run from the same values
-    (float64) or stay within the mixed gates. The oracle starts from the
-    library's values because both fixed points stop within 1e-12 K, and
-    from a balanced column at rest the vertical momentum answers that
-    difference: its relative error would measure the stopping rule, not the
-    step."""
+    (float64; W, small and driven by nearly cancelling terms from a balanced
+    column, to 1e-12 g rho dtau absolute) or stay within the mixed gates.
+    The oracle starts from the library's values because both fixed points
+    stop within 1e-12 K."""
     wl = SMALL.with_(forcing="held_suarez", noise_amp=0.0)
     p = Pair(wl, precision=precision, profile=True)
     try:
@@ -231,7 +236,8 @@ def test_held_suarez_start_profile(precision):
         thor.thor_step(p.state, 2, wl.n_small, wl.dt)
         assert np.abs(ref.M / ref.rho[..., None]).max() > 1e-4            # the forcing moves air
         if precision == thor.THOR_FP64:
-            _assert_close(p.get(), ref)
+            w_scale = p.model.planet.gravity * float(np.abs(ref.rho).max()) * wl.dt / wl.n_small
+            _assert_close(p.get(), ref, w_scale=w_scale)
         else:
             from test_gpu_mixed import GATES, field_report
             rep = field_report(p, p.get(), ref)
