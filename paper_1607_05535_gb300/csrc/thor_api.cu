@@ -315,12 +315,16 @@ Impl<R>::~Impl() {
   if (arena) cudaFree(arena);
 }
 
+// the element count of a field in the canonical layout of thor_state_get
+static size_t field_count(int field, int ncol, int nv) {
+  return field == THOR_FIELD_MOM ? (size_t)ncol * nv * 3 : field == THOR_FIELD_W ? (size_t)ncol * (nv + 1)
+                                                                                 : (size_t)ncol * nv;
+}
+
 template <typename R>
 int Impl<R>::get(int field, double* host, size_t n) {
   const int nv = G.nv;
-  size_t need = field == THOR_FIELD_MOM ? (size_t)G.ncol * nv * 3
-              : field == THOR_FIELD_W  ? (size_t)G.ncol * (nv + 1)
-                                       : (size_t)G.ncol * nv;
+  const size_t need = field_count(field, G.ncol, nv);
   if (field < 0 || field > THOR_FIELD_TEMPERATURE || n != need || !host) return THOR_EINVAL;
   int nlev = field == THOR_FIELD_W ? nv + 1 : nv;
   dim3 grid((G.ncol + 127) / 128, nlev);
@@ -332,19 +336,10 @@ int Impl<R>::get(int field, double* host, size_t n) {
 
 template <typename R>
 int Impl<R>::set(int field, const double* host, size_t n) {
-  const size_t need = field == THOR_FIELD_MOM ? (size_t)G.ncol * G.nv * 3
-                    : field == THOR_FIELD_W   ? (size_t)G.ncol * (G.nv + 1)
-                                              : (size_t)G.ncol * G.nv;
-  if (!host || n != need) return THOR_EINVAL;
+  if (!host || n != field_count(field, G.ncol, G.nv)) return THOR_EINVAL;
   const int rc = set_async(field, host, staging);
   if (rc) return rc;
   return cudaStreamSynchronize(stream) == cudaSuccess ? THOR_OK : THOR_ECUDA;
-}
-
-// the element count of a prognostic field, in THOR_FIELD order
-static size_t field_count(int field, int ncol, int nv) {
-  return field == THOR_FIELD_MOM ? (size_t)ncol * nv * 3 : field == THOR_FIELD_W ? (size_t)ncol * (nv + 1)
-                                                                                 : (size_t)ncol * nv;
 }
 
 template <typename R>
