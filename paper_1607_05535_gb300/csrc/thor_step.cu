@@ -1173,13 +1173,21 @@ void Impl<R>::launch_2d(int nplanes, int kchunk, dim3& grid) const {
 
 size_t solve_smem_bytes(int nv) { return (size_t)(2 * (nv + 1) + 2) * 32 * sizeof(double); }
 
+// Raise a kernel's dynamic shared-memory limit to at least bytes, never
+// lower it: states with different level counts share the kernels, and a
+// later state with fewer levels must not take room from an earlier one.
+template <typename K>
+static bool raise_smem_limit(K* kernel, int bytes) {
+  cudaFuncAttributes a{};
+  if (cudaFuncGetAttributes(&a, kernel) != cudaSuccess) return false;
+  if (a.maxDynamicSharedSizeBytes >= bytes) return true;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+}
+
 template <typename R>
 int col_kernel_setup(int nv) {
   const int bytes = (int)solve_smem_bytes(nv);
-  if (cudaFuncSetAttribute(k_ss_solve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
-    return -3;
-  return cudaFuncSetAttribute(ke_ss_solve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess
-             ? 0 : -3;
+  return raise_smem_limit(k_ss_solve<R>, bytes) && raise_smem_limit(ke_ss_solve<R>, bytes) ? 0 : -3;
 }
 template int col_kernel_setup<double>(int);
 template int col_kernel_setup<float>(int);
@@ -1379,9 +1387,7 @@ int Impl<float>::build_solve_maps() {
   make(&map->cf, F.cf, nv + 1, true);
   make(&map->junction, F.junction, 1, true);
   if (!ok) return 0;
-  if (cudaFuncSetAttribute(k_ss_solve_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-      cudaFuncSetAttribute(ke_ss_solve_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return -3;
+  if (!raise_smem_limit(k_ss_solve_tma, (int)smem) || !raise_smem_limit(ke_ss_solve_tma, (int)smem)) return -3;
   smaps = std::move(map);
   return 0;
 }
