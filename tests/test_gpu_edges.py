@@ -44,7 +44,11 @@ def test_edge_parity_fp64(glevel, nv):
         ref = dc.run(p.model, X, 1, wl.n_small, wl.dt)
         thor.thor_step(p.state, 1, wl.n_small, wl.dt)
         e = field_errors(p.get(), ref)
-        assert e["rho"] < 1e-10 and e["Th"] < 1e-10 and e["M"] < 1e-10 and e["W"] < 1e-10, e
+        assert e["rho"] < 1e-10 and e["Th"] < 1e-10 and e["M"] < 1e-10, e
+        # W, small after one step, is the difference of the nearly equal vertical
+        # terms of size g rho dtau, which float64 rounds at about 1e-16 of that
+        w_scale = wl.planet.gravity * float(np.abs(ref.rho).max()) * wl.dt / wl.n_small
+        assert e["W"] < 1e-10 or e["W_maxabs"] < 1e-12 * w_scale, e
     finally:
         p.close()
 
