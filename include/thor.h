@@ -74,19 +74,26 @@ typedef struct {
 int thor_grid_create(int glevel, int nv, double radius, double z_top,
                      const thor_spring* spring, thor_grid** out);
 
-/* Sizes: ncol = 10*4^glevel + 2, nv, npent = 12, the spring iterations run
- * and whether the tol criterion was met. Any output pointer may be NULL. */
+/* Sizes (Sec. 2.1, Eq. grid_qts: ncol = 10*4^glevel + 2 points, 12 of them
+ * pentagons), nv, the spring iterations run and whether the tol criterion
+ * was met (Sec. 2.2). Any output pointer may be NULL; THOR_EINVAL for a NULL
+ * grid. */
 int thor_grid_info(const thor_grid* grid, int* ncol, int* nv, int* npent,
                    int* spring_iters, int* spring_converged);
 
-/* Cell centres on the unit sphere, xyz[ncol][3]; n must be 3*ncol. */
+/* Cell centres on the unit sphere after the spring dynamics and the
+ * centroid relocation of Sec. 2.2, xyz[ncol][3] in the library's column
+ * order (caller's buffer); n must be 3*ncol, else THOR_EINVAL. */
 int thor_grid_points(const thor_grid* grid, double* xyz, size_t n);
 
-/* Counter-clockwise neighbours, nbr[ncol][6], -1 in slot 5 of the 12
- * pentagons; n must be 6*ncol. */
+/* Counter-clockwise neighbours of every cell (the hexagons and pentagons of
+ * Sec. 2.1), nbr[ncol][6] column indices, -1 in slot 5 of the 12 pentagons
+ * (caller's buffer); n must be 6*ncol, else THOR_EINVAL. */
 int thor_grid_neighbours(const thor_grid* grid, int* nbr, size_t n);
 
-/* Control-volume areas A_c on the unit sphere, area[ncol]; n must be ncol. */
+/* Control-volume areas A_c on the unit sphere (Sec. 2.2: the polygons of
+ * the triangle centroids around each point, the areas of Eq. int_grid),
+ * area[ncol] (caller's buffer); n must be ncol, else THOR_EINVAL. */
 int thor_grid_areas(const thor_grid* grid, double* area, size_t n);
 
 void thor_grid_destroy(thor_grid* grid);
@@ -175,9 +182,12 @@ typedef struct {
 } thor_diag_t;
 int thor_diag(thor_state* state, thor_diag_t* out);
 
-/* Copy a field to / from a float64 host buffer in the canonical order; n is
- * the element count of the field. Synchronous. set accepts RHO, MOM, W and
- * RHOTHETA; W's bottom and top interfaces are forced to 0. */
+/* Copy a field to / from a float64 host buffer (caller's) in the canonical
+ * order [ncol][level(s)][components] (the output of the prognostic variables
+ * that Sec. 5 describes; pressure and temperature follow from Eq. pressure
+ * and the ideal gas); n is the element count of the field, else THOR_EINVAL.
+ * Synchronous. set accepts RHO, MOM, W and RHOTHETA (the rigid lid of Sec. 3:
+ * W's bottom and top interfaces are forced to 0). */
 int thor_state_get(thor_state* state, int field, double* host, size_t n);
 int thor_state_set(thor_state* state, int field, const double* host, size_t n);
 
@@ -192,7 +202,8 @@ int thor_state_get_all(thor_state* state, double* rho, double* mom, double* w, d
 int thor_state_set_all(thor_state* state, const double* rho, const double* mom, const double* w,
                        const double* rhotheta, int ncol, int nv);
 
-/* Raw checkpoint of the prognostic state: the stored arrays (deviation form,
+/* Raw checkpoint of the prognostic state (Sec. 5: the long runs write the
+ * state out and restart from it): the stored arrays (deviation form,
  * padded layout) bit for bit after a 64-byte header (magic, precision, ncol,
  * nv). thor_checkpoint_bytes gives the buffer size; save and load copy
  * to / from `buf` in host or device memory (unified addressing) and
@@ -224,10 +235,12 @@ int thor_wait_selftest(int arrive, unsigned int limit_us, int* gave_up);
  * one counter. No counterpart in the paper. */
 int thor_convert_selftest(long long n, unsigned long long seed, long long* mismatches);
 
-/* Kernel launches issued by this state so far. */
+/* Kernel launches issued by this state so far (instrumentation; no passage
+ * of the paper). THOR_EINVAL for NULL arguments. */
 int thor_launch_count(const thor_state* state, long long* count);
 
-/* Launch-shape knobs; the results do not depend on them.
+/* Launch-shape knobs (no passage of the paper: the paper's K20 kernels use
+ * fixed 2-D blocks of 256 threads, Sec. 5); the results do not depend on them.
  * THOR_TUNE_KCHUNK: levels each thread of the stencil kernels walks (1..256,
  * default 2); fewer levels mean more threads in flight, more levels fewer
  * reloads of the per-column weights.
@@ -323,7 +336,8 @@ int thor_zonal_read_w(thor_state* state, int nlat, double* out, size_t n, long l
 int thor_autotune(thor_state* state, int n_small, double dt, int steps, int* kchunk, int* block,
                   double* ms_per_step);
 
-/* Per-kernel timing. While enabled, every launch of the state is bracketed by
+/* Per-kernel timing (instrumentation; no passage of the paper). While
+ * enabled, every launch of the state is bracketed by
  * two CUDA events recorded on the state's stream; thor_profile_read
  * synchronises the stream and returns, for one kernel id, the summed
  * event-measured duration (ms) and the number of launches since the last
@@ -366,7 +380,8 @@ int thor_ensemble_create(thor_state* const* members, int n, void* stream, thor_e
  * member table and block maps. */
 int thor_ensemble_step(thor_ensemble* ens, int n_large, const int* n_small, const double* dt);
 
-/* Member count and kernel launches issued by the ensemble so far. */
+/* Member count and kernel launches issued by the ensemble so far
+ * (instrumentation). */
 int thor_ensemble_info(const thor_ensemble* ens, int* n_members, long long* launches);
 
 /* THOR_TUNE_KCHUNK, THOR_TUNE_BLOCK, THOR_TUNE_GRAPH as for one state. */
