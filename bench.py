@@ -159,7 +159,8 @@ def oracle_sample(wl, n_small_steps=1):
     from oracle.grid import build_grid
     P = wl.planet
     G = build_grid(wl.glevel, max_iter=10, tol=0.0)
-    pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+    pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref,
+                   dc.diffusion_parameter(P.dt_paper, P.tau_d))
     m = dc.Model(G, op.VerticalGrid(wl.nv, wl.z_top, P.radius), pl, forcing=wl.forcing,
                  hj_dT=wl.hj_dT)
     u = wls.temperature_noise(wl, G.ncol)

@@ -205,11 +205,16 @@ int thor_state_set_all(thor_state* state, const double* rho, const double* mom, 
 /* Raw checkpoint of the prognostic state (Sec. 5: the long runs write the
  * state out and restart from it): the stored arrays (deviation form,
  * padded layout) bit for bit after a 64-byte header (magic, precision, ncol,
- * nv). thor_checkpoint_bytes gives the buffer size; save and load copy
- * to / from `buf` in host or device memory (unified addressing) and
- * synchronise the state's stream. Loading into a state of another grid
- * size, level count or precision, or a buffer without the header, returns
- * THOR_EINVAL and leaves the state unchanged. A restart from a checkpoint
+ * nv, a 64-bit hash of the reference column, vertical tables, planet and
+ * switches that the stored deviations are relative to, and the large steps
+ * since a closure was attached). thor_checkpoint_bytes gives the buffer
+ * size; save and load copy to / from `buf` in host or device memory
+ * (unified addressing) and synchronise the state's stream. Loading into a
+ * state of another grid size, level count or precision, into a state whose
+ * reference differs (another planet, top, start temperature or surface
+ * pressure, or switch), or from a buffer without the header, returns
+ * THOR_EINVAL and leaves the state unchanged; a load restores the position
+ * inside the closure window. A restart from a checkpoint
  * continues bit for bit like an uninterrupted run; thor_state_get/_set,
  * which exchange full float64 values, round the reference column plus the
  * deviation (a unit in the last place) in float64 storage. */
@@ -344,8 +349,8 @@ int thor_autotune(thor_state* state, int n_small, double dt, int steps, int* kch
  * thor_profile(state, 1). enable = 0 stops recording. */
 enum {
   THOR_K_DERIVED = 0, THOR_K_LAP1, THOR_K_SLOW, THOR_K_SLOW_W, THOR_K_STAGE_INIT,
-  THOR_K_SS_DIV, THOR_K_SS_GRAD, THOR_K_SS_MOM, THOR_K_SS_COL, THOR_K_STAGE_END,
-  THOR_K_PHYSICS, THOR_K_SS_FLUX, THOR_K_SS_FACTOR, THOR_K_COUNT
+  THOR_K_SS_GRAD, THOR_K_SS_MOM, THOR_K_SS_SOLVE, THOR_K_PHYSICS, THOR_K_SS_FLUX,
+  THOR_K_SS_FACTOR, THOR_K_COUNT
 };
 int thor_profile(thor_state* state, int enable);
 int thor_profile_read(thor_state* state, int kernel, double* total_ms, long long* launches);
@@ -469,8 +474,11 @@ int thor_coarse_grain(thor_state* fine, thor_state* coarse, const int* fine_to_c
 /* ------------------------------------------------------- allocation-free */
 
 /* Allocation-free float64 mass sum: *mass_out = sum_i rho[i] * volume[i]
- * over i < n, the same deterministic two-pass compensated reduction that
- * thor_diag uses for its mass. The paper has no counterpart: this entry
+ * over i < n. It is deterministic and uses the scheme of thor_diag's mass
+ * (compensated per-block partial sums, then one ordered compensated sum of
+ * the partials) with a different blocking (contiguous chunks of 16384
+ * elements per block), so the two agree to rounding, not bit for bit. The
+ * paper has no counterpart: this entry
  * point exists for callers that must not call cudaMalloc, because an outer
  * framework owns the whole device-memory budget or because cudaMalloc would
  * synchronise the device in a latency-critical loop.

@@ -11,7 +11,7 @@ the layer interfaces, Sec. 3):
                     bottom and top (rigid lid, Sec. 3)
   Th   (N, nv)      rho theta
 
-Readings (listed in DESIGN.md):
+Readings:
 
 R1  Time stepping. Sec. 3 calls each of the three Wicker-Skamarock stages a
     "large time step" when it gives the small-step counts (1 step of dt/3,
@@ -289,6 +289,18 @@ def vertical_solve(model, dtau, Wstar, S_W, a, b, c, theta_i, Pi):
 
 # ----------------------------------------------------------- small step
 
+def divergence_damping(model, M, W, Kd):
+    """Sec. 4, the divergence-damping terms of Eqs. diff_vx-vz (reading R5):
+    D = div_h M + r^-2 d(r^2 W)/dr, the 3-D divergence of the momentum (M at
+    the centres, W at the interfaces), G = grad_h D, and the damping
+    -K_d lap(G) taken component-wise in Cartesian coordinates and projected
+    on the horizontal (Eq. proj_h)."""
+    g, vg = model.grid, model.vg
+    D = op.div_h_levels(g, vg, M) + op.div_v(vg, W)
+    G = op.grad_h_levels(g, vg, D)
+    return op.project_h(model.rhat, -Kd * op.vlap_levels(g, vg, G))
+
+
 def small_step(model, Xs, co, pert, dtau, Kd):
     """One forward-backward small step (Sec. 3), order of Sec. 3: horizontal
     momentum (explicit, Eq. mom2 with the divergence damping of Sec. 4), then
@@ -299,13 +311,8 @@ def small_step(model, Xs, co, pert, dtau, Kd):
     rho_s, M_s, W_s, Th = pert["rho"], pert["M"], pert["W"], pert["Th"]
     p_s = pert["p"]
 
-    # divergence damping (reading R5)
-    if model.divergence_damping:
-        D = op.div_h_levels(g, vg, Xs.M + M_s) + op.div_v(vg, Xs.W + W_s)
-        G = op.grad_h_levels(g, vg, D)
-        DD = op.project_h(rhat, -Kd * op.vlap_levels(g, vg, G))
-    else:
-        DD = 0.0
+    # divergence damping (reading R5) of the total momentum
+    DD = divergence_damping(model, Xs.M + M_s, Xs.W + W_s, Kd) if model.divergence_damping else 0.0
 
     # Eq. mom2 (explicit)
     M_new = op.project_h(rhat, M_s + dtau * (-op.grad_h_levels(g, vg, p_s) + DD + co["S_M"]))

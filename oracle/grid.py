@@ -20,7 +20,7 @@ This module uses a generic triangle list (faces) with creation-order
 numbering; it shares nothing with the CUDA path's grid builder, which uses its
 own numbering. Tests relate the two by matching point coordinates.
 
-Readings of silent or garbled passages (each one is listed in the design doc):
+Readings of silent or garbled passages:
 
 * Icosahedron orientation: north pole, five vertices at latitude +atan(1/2)
   and longitudes 0, 72, ... deg, five at latitude -atan(1/2) and longitudes

@@ -8,7 +8,7 @@ unit sphere; at radius r a horizontal divergence or gradient is divided by r
 and the Laplacian by r^2 (deep atmosphere, Sec. 3: the control volume at
 radius r has area A_c r^2 and edges l_k r).
 
-Readings (listed in DESIGN.md):
+Readings:
 
 * Corner values are defined once per triangle (Eq. int_grid is symmetric in
   the triangle's three vertices), so both cells that share an edge see the

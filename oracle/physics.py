@@ -8,7 +8,7 @@ relaxation of T), with the same dt as the large step. rho is not touched;
 rho theta is recomputed from the new T at fixed rho (ideal gas + Eq.
 pressure). W is not touched.
 
-Readings (listed in DESIGN.md):
+Readings:
 
 * sigma = p / p_s with p_s extrapolated from the lowest layer centre to z = 0
   with the hydrostatic equation at that layer's constant temperature:

@@ -43,8 +43,8 @@ EXPORTED = [
 ]
 
 # kernel ids of thor_profile_read
-KERNELS = ["derived", "lap1", "slow", "slow_w", "stage_init", "ss_div", "ss_grad", "ss_mom",
-           "ss_solve", "stage_end", "physics", "ss_flux", "ss_factor"]
+KERNELS = ["derived", "lap1", "slow", "slow_w", "stage_init", "ss_grad", "ss_mom", "ss_solve",
+           "physics", "ss_flux", "ss_factor"]
 
 
 class thor_spring(ctypes.Structure):

@@ -595,6 +595,19 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
   HostSetup hs;
   int rc = host_setup(h, pl, in, hs);
   if (rc) return rc;
+  {
+    unsigned long long x = 1469598103934665603ull;           // FNV-1a, 64 bit
+    auto mix = [&x](const void* p, size_t n) {
+      const unsigned char* b = static_cast<const unsigned char*>(p);
+      for (size_t i = 0; i < n; ++i) x = (x ^ b[i]) * 1099511628211ull;
+    };
+    for (int v = 0; v < kNumVert; ++v) mix(hs.vert[v].data(), hs.vert[v].size() * sizeof(double));
+    const double pv[7] = {pl.radius, pl.omega, pl.gravity, pl.Rd, pl.cp, pl.p_ref, pl.diff_D};
+    mix(pv, sizeof(pv));
+    const int sw[3] = {in.shallow, in.hydrostatic, in.forcing};
+    mix(sw, sizeof(sw));
+    I->ref_hash = x;
+  }
   rc = upload_tables(*I, h, hs.vert, st);
   if (rc) return rc;
   rc = I->set(THOR_FIELD_RHO, hs.rho.data(), hs.rho.size());
@@ -731,10 +744,12 @@ struct CkptHeader {
   char magic[8];
   int precision, ncol, nv, colp;
   unsigned long long payload;
-  char pad[32];
+  unsigned long long ref_hash;    // the saving state's reference (ImplBase::ref_hash)
+  long long closure_steps;        // large steps since its closure was attached
+  char pad[16];
 };
 static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
-const char kCkptMagic[8] = {'T', 'H', 'O', 'R', 'C', 'K', 'P', '1'};
+const char kCkptMagic[8] = {'T', 'H', 'O', 'R', 'C', 'K', 'P', '2'};
 }  // namespace
 
 int thor_convert_selftest(long long n, unsigned long long seed, long long* mismatches) {
@@ -784,6 +799,8 @@ int thor_checkpoint_save(thor_state* s, void* buf, size_t bytes) {
   h.nv = s->grid->h.nv;
   h.colp = thor::colp_of(h.ncol);
   h.payload = payload;
+  h.ref_hash = s->impl->ref_hash;
+  h.closure_steps = s->closure.counter;
   char* p = static_cast<char*>(buf);
   if (cudaMemcpy(p, &h, sizeof(h), cudaMemcpyDefault)) return THOR_ECUDA;
   if (s->impl->save_state(p + sizeof(h))) return THOR_ECUDA;
@@ -797,9 +814,10 @@ int thor_checkpoint_load(thor_state* s, const void* buf, size_t bytes) {
   CkptHeader h{};
   if (cudaMemcpy(&h, buf, sizeof(h), cudaMemcpyDefault)) return THOR_ECUDA;
   if (std::memcmp(h.magic, kCkptMagic, 8) || h.precision != s->precision || h.ncol != s->grid->h.ncol ||
-      h.nv != s->grid->h.nv || h.payload != payload)
+      h.nv != s->grid->h.nv || h.payload != payload || h.ref_hash != s->impl->ref_hash || h.closure_steps < 0)
     return THOR_EINVAL;
   if (s->impl->load_state(static_cast<const char*>(buf) + sizeof(h))) return THOR_ECUDA;
+  s->closure.counter = h.closure_steps;        // resume inside the same closure window
   return cudaStreamSynchronize(s->impl->stream) ? THOR_ECUDA : THOR_OK;
 }
 

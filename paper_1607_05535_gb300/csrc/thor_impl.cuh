@@ -104,6 +104,10 @@ struct ImplBase {
   double* fixbuf = nullptr;            // two diagnostics reductions, dT (float64 and storage type)
   double* budget = nullptr;            // [budget_cap][8]
   int* budget_count = nullptr;         // rows recorded
+  // FNV-1a hash of what the stored deviations are relative to: the
+  // reference column and vertical tables, the planet and the switches
+  // (checkpoints record it and refuse to load into another)
+  unsigned long long ref_hash = 0;
   // copy the prognostic fields to / from a device buffer of state_bytes()
   virtual size_t state_bytes() const = 0;
   virtual int save_state(void* dst) = 0;

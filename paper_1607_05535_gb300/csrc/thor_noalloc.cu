@@ -8,9 +8,10 @@
 // which allocates nothing.
 //
 // The two-pass reduction (per-block compensated partial sums, then one
-// ordered compensated sum of the partials) is the one thor_diag runs; here
-// the partials live in a file-scope device array of fixed size instead of
-// the state's own scratch. Device code names that array directly; host code
+// ordered compensated sum of the partials) follows thor_diag's scheme with
+// its own blocking (contiguous chunks per block), so the two agree to
+// rounding; here the partials live in a file-scope device array of fixed
+// size instead of the state's own scratch. Device code names that array directly; host code
 // only ever passes its device address, obtained once per device with
 // cudaGetSymbolAddress (the host-side symbol is a stand-in, not a device
 // address).

@@ -1296,13 +1296,13 @@ int Impl<R>::large_step(double dt, int n_small) {
       chk(launch_k(k_ss_flux<R>, g2, bs, 0, stream, G, U, SL, P, T, (R)dts[s], kc));
       mark(THOR_K_SS_FLUX, false);
       if (fork && j == 0) chk(cudaStreamWaitEvent(stream, ev_join, 0));
-      mark(THOR_K_SS_COL, true);
+      mark(THOR_K_SS_SOLVE, true);
       if (staged)
         chk(launch_solve_tma(gsolve, s, dts[s], want_div, last));
       else
         chk(launch_k(k_ss_solve<R>, gsolve, 64, solve_smem, stream, G, U, ph, Xs, SL, P, T, F, dts[s],
                      want_div, Xo, last));
-      mark(THOR_K_SS_COL, false);
+      mark(THOR_K_SS_SOLVE, false);
       launches += 3;
     }
   }

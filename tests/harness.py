@@ -42,7 +42,8 @@ class Pair:
         self.profile = "held_suarez" if profile else None
         P = wl.planet
         G = oracle_grid(wl.glevel, max_iter=wl.spring_max_iter, tol=wl.spring_tol)
-        pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+        pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref,
+                   dc.diffusion_parameter(P.dt_paper, P.tau_d))
         self.model = dc.Model(G, op.VerticalGrid(wl.nv, wl.z_top, P.radius, shallow=shallow), pl, forcing=wl.forcing,
                               hj_dT=wl.hj_dT, hyperdiffusion=hyper, divergence_damping=divdamp,
                               hydrostatic=hydrostatic)

@@ -106,6 +106,19 @@ def test_restart_from_checkpoint_is_bit_exact(precision, device_buffer):
                                   thor.thor_state_get(c, f, wl.ncol, wl.nv)), f
         with pytest.raises(thor.ThorError):
             thor.thor_checkpoint_load(c, buf[:-1])
+        # the stored deviations are relative to the saving state's reference
+        # column: a state of the same size with another start temperature or
+        # planet refuses the checkpoint and keeps its fields
+        for other in (wl.with_(T0=wl.T0 + 10.0), wl.with_(planet=wls.EARTH_TABLE1)):
+            d = thor.thor_state_init(grid, planet_struct(other.planet), init_struct(other, precision), None)
+            try:
+                before = thor.thor_state_get(d, thor.THOR_FIELD_RHO, wl.ncol, wl.nv)
+                with pytest.raises(thor.ThorError) as e:
+                    thor.thor_checkpoint_load(d, buf)
+                assert e.value.status == thor.THOR_EINVAL
+                assert np.array_equal(before, thor.thor_state_get(d, thor.THOR_FIELD_RHO, wl.ncol, wl.nv))
+            finally:
+                thor.thor_state_destroy(d)
     finally:
         for s_ in (a, b, c):
             if s_ is not None:

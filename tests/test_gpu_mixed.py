@@ -1,7 +1,7 @@
 """Mixed precision (float32 fields and stencils, float64 elimination and
 reductions) against the float64 oracle, per field, on the glevel-4 x 20-level
 Held-Suarez workload. The gates are the stated per-field tolerances of the
-mixed mode (also quoted in the design doc)."""
+mixed mode."""
 
 import json
 import os

@@ -17,7 +17,8 @@ NLAT = 18
 
 def _model():
     P = wls.EARTH
-    pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+    pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref,
+                   dc.diffusion_parameter(P.dt_paper, P.tau_d))
     return dc.Model(oracle_grid(4, max_iter=10, tol=0.0), op.VerticalGrid(6, 30.0e3, P.radius), pl)
 
 

@@ -14,7 +14,8 @@ import workloads as wls
 
 def _model(glevel=3, nv=10, z_top=30.0e3, forcing="none", **kw):
     P = wls.EARTH
-    pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+    pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref,
+                   dc.diffusion_parameter(P.dt_paper, P.tau_d))
     G = oracle_grid(glevel, max_iter=10, tol=0.0)
     return dc.Model(G, op.VerticalGrid(nv, z_top, P.radius), pl, forcing=forcing, **kw)
 
@@ -144,7 +145,8 @@ def test_hyperdiffusion_of_a_harmonic():
     modified grid. (Applied twice, the Sec. 4 Laplacian amplifies its own
     grid-scale error, so the agreement is a few percent, not second order.)"""
     P_ = wls.EARTH
-    pl = dc.Planet(P_.radius, P_.omega, P_.gravity, P_.Rd, P_.cp, P_.p_ref, P_.diff_D)
+    pl = dc.Planet(P_.radius, P_.omega, P_.gravity, P_.Rd, P_.cp, P_.p_ref,
+                   dc.diffusion_parameter(P_.dt_paper, P_.tau_d))
     m = dc.Model(oracle_grid(3), op.VerticalGrid(3, 30.0e3, P_.radius), pl)
     P = m.grid.points
     Y = P[:, 0] * P[:, 1]
@@ -189,7 +191,8 @@ def test_diffusion_parameter_reproduces_tau_d():
 
 def _rest_model(omega, hyper=False, glevel=3, nv=4):
     P_ = wls.EARTH
-    pl = dc.Planet(P_.radius, omega, P_.gravity, P_.Rd, P_.cp, P_.p_ref, P_.diff_D)
+    pl = dc.Planet(P_.radius, omega, P_.gravity, P_.Rd, P_.cp, P_.p_ref,
+                   dc.diffusion_parameter(P_.dt_paper, P_.tau_d))
     return dc.Model(oracle_grid(glevel), op.VerticalGrid(nv, 8.0e3, P_.radius), pl,
                     hyperdiffusion=hyper)
 

@@ -16,7 +16,8 @@ import workloads as wls
 
 def _model(forcing="none"):
     P = wls.EARTH
-    pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+    pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref,
+                   dc.diffusion_parameter(P.dt_paper, P.tau_d))
     return dc.Model(oracle_grid(3, max_iter=10, tol=0.0), op.VerticalGrid(10, 30.0e3, P.radius), pl,
                     forcing=forcing)
 

@@ -17,7 +17,8 @@ import workloads as wls
 
 def _model(hydrostatic, forcing="none", hyper=False, nv=10, glevel=2, omega=None):
     P = wls.EARTH
-    pl = dc.Planet(P.radius, P.omega if omega is None else omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+    pl = dc.Planet(P.radius, P.omega if omega is None else omega, P.gravity, P.Rd, P.cp, P.p_ref,
+                   dc.diffusion_parameter(P.dt_paper, P.tau_d))
     return dc.Model(oracle_grid(glevel, max_iter=10, tol=0.0), op.VerticalGrid(nv, 30.0e3, P.radius), pl,
                     forcing=forcing, hyperdiffusion=hyper, divergence_damping=hyper, hydrostatic=hydrostatic)
 

@@ -66,7 +66,8 @@ def test_backward_euler_updates():
     toward T_eq; rho unchanged; surface pressure recovers p_surf for the
     discretely balanced isothermal column."""
     P = wls.EARTH
-    pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+    pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref,
+                   dc.diffusion_parameter(P.dt_paper, P.tau_d))
     G = oracle_grid(2, max_iter=10, tol=0.0)
     m = dc.Model(G, op.VerticalGrid(12, 30.0e3, P.radius), pl, forcing="held_suarez")
     X = dc.initial_state(m, 300.0, 1.0e5)

@@ -14,7 +14,8 @@ import workloads as wls
 
 def _model(shallow, omega=None, forcing="none", hyper=False, nv=6, glevel=3):
     P = wls.EARTH
-    pl = dc.Planet(P.radius, P.omega if omega is None else omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+    pl = dc.Planet(P.radius, P.omega if omega is None else omega, P.gravity, P.Rd, P.cp, P.p_ref,
+                   dc.diffusion_parameter(P.dt_paper, P.tau_d))
     return dc.Model(oracle_grid(glevel, max_iter=10, tol=0.0), op.VerticalGrid(nv, 30.0e3, P.radius, shallow=shallow),
                     pl, forcing=forcing, hyperdiffusion=hyper, divergence_damping=hyper)
 

@@ -28,7 +28,8 @@ import workloads as wls
 
 def _rigid_rotation_change(glevel, w=1e-5, nv=8, steps=2):
     P = wls.EARTH
-    pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+    pl = dc.Planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref,
+                   dc.diffusion_parameter(P.dt_paper, P.tau_d))
     vg = op.VerticalGrid(nv, 12.0e3, P.radius)
     m = dc.Model(oracle_grid(glevel, max_iter=200, tol=1e-6), vg, pl, hyperdiffusion=False,
                  divergence_damping=False)

@@ -44,8 +44,15 @@ def test_mass_noalloc_matches_diag_twice():
             ref = thor.thor_diag(state)["mass"]
             rho = thor.thor_state_get(state, thor.THOR_FIELD_RHO, wl.ncol, wl.nv)
             rho_d = torch.tensor(rho, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            torch_before, free_before = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
             thor.thor_mass_noalloc(rho_d, vol_d, out)
             torch.cuda.synchronize()
+            if call == 1:
+                # the first call may load the kernels' module (lazy loading);
+                # from then on a call allocates nothing, from torch or the device
+                assert torch.cuda.memory_allocated() == torch_before
+                assert torch.cuda.mem_get_info()[0] == free_before
             got = float(out.item())
             assert abs(got - ref) <= TOL * abs(ref), (call, got, ref)
     finally:
