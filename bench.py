@@ -25,6 +25,11 @@ import subprocess
 import sys
 import time
 
+# the oracle legs time plain single-threaded numpy per process (their "cores"
+# is the number of processes); set before numpy loads its BLAS
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -34,21 +39,37 @@ import workloads as wls  # noqa: E402
 
 METRIC = "cell-substeps/s"
 
-# Unique field words each kernel reads or writes per cell (neighbour reads of
-# a field counted once), the counting rule of the algorithmic roofline. The
-# column solve reads 10 float planes (W*, S_W, c, a, theta at the interfaces,
-# b, p', Th^(s), D^(s), div_h M*) and 3 float64 factor planes (pivot
-# reciprocal, c'/e', q: 6 words), and writes 5 (rho*, Th*, p*, W*, D); the
-# factorisation reads 2 planes and writes the 3 float64 ones.
-# The interface kernel also sets the stage's perturbations (reads X^t and
-# X^(s), 12 planes, and p'; writes the 7 perturbation planes), and the last
-# small step of a stage also ends it (momentum and column kernels read the
-# stage state's 3 planes each and write X^(s+1)'s); the counts below are
-# those of the other small steps.
-KERNEL_WORDS = {
-    "derived": 6 + 10, "lap1": 8 + 6, "slow": 17 + 8, "slow_w": 16 + 9,
-    "ss_grad": 1 + 3, "ss_mom": 10 + 3, "ss_flux": 10 + 4, "ss_solve": 10 + 6 + 5,
-    "ss_factor": 2 + 6, "physics": 5 + 4,
+# The counting rule of the algorithmic roofline: unique field words a cell
+# must read or write per pass that the method requires, times the word size
+# (4 B in mixed precision); on-chip intermediates are not counted. Per large
+# step at n small steps that is 3 x 13 (slow terms) + S_n x 27 (small steps)
+# + 9 (physics) words, 399 at n = 8. The 27 words of a small step: the
+# perturbations M* (3), W*, rho*, Theta, p* read and written (14), the slow
+# tendencies S_M (3), S_W, S_rho, S_Theta (6) and the stage coefficients
+# theta, Pi, M^(s) (3), W^(s), p (7).
+SLOW_WORDS, SMALL_WORDS, PHYSICS_WORDS = 13, 27, 9
+
+
+def step_method_words(n_small):
+    return 3 * SLOW_WORDS + (1 + n_small // 2 + n_small) * SMALL_WORDS + PHYSICS_WORDS
+
+
+# Per kernel: the method's words it reads or writes (those of the counting
+# rule above that the kernel's part of the step consumes or produces,
+# directly or through the kernel split's intermediates), and the words it
+# actually moves, the split's intermediates included. The column solve's 15
+# method words: W*, rho*, Theta and p* read and written (8; rho*, Theta, p*
+# read through the flux kernel's a, b, c), S_W, S_rho, S_Theta (3; the
+# latter two through a and b), theta at the interfaces, Pi, W^(s) and p (4).
+# It moves 21: W*, S_W, a, b, c, theta_iface, p', Th^(s), D^(s), div_h M*
+# read (10), the three float64 factor planes (6 words) and rho*, Theta, p*,
+# W*, D written (5). The interface kernel also sets the stage's
+# perturbations, and the last small step of a stage also ends it; the
+# counts below are those of the other small steps.
+KERNEL_WORDS = {        # name: (method words, moved words)
+    "derived": (7, 16), "lap1": (6, 14), "slow": (13, 25), "slow_w": (4, 9),
+    "ss_grad": (1, 4), "ss_mom": (10, 13), "ss_flux": (10, 14), "ss_solve": (15, 21),
+    "ss_factor": (2, 8), "physics": (9, 9), "stage_init": (7, 20),
 }
 
 
@@ -181,6 +202,63 @@ def oracle_sample(wl, n_small_steps=1):
     return m, X, co, t_slow, t_small, t_phys
 
 
+def _oracle_sample_times(name):
+    """Worker of the oracle legs (a spawned process): the timed sample of
+    oracle_sample for workload ``name``, as (slow, small, physics) seconds."""
+    _, _, _, t_slow, t_small, t_phys = oracle_sample(workload_of(name))
+    return t_slow, t_small, t_phys
+
+
+def _mem_available_gb():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) / 1048576.0
+    except Exception:
+        pass
+    return 0.0
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def oracle_rates(wl, processes):
+    """The oracle as it stands, timed on ``processes`` host processes at
+    once (spawned, one thread each), every process running the bounded
+    sample of oracle_sample on its own copy of the workload. Returns the
+    whole host's cell-substeps/s (the sum over the processes) and the
+    samples' times."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")          # never fork a process that holds a CUDA context
+    with ctx.Pool(processes) as pool:
+        times = pool.map(_oracle_sample_times, [args_name(wl)] * processes)
+    sn = wl.substeps_per_large
+    rate = sum(wl.cells * sn / (3 * a + sn * b + c) for a, b, c in times)
+    return rate, times
+
+
+def args_name(wl):
+    for k in ("hs_g6", "hs_g4", "hj_g6"):
+        if workload_of(k).name == wl.name:
+            return k
+    raise KeyError(wl.name)
+
+
 def run_reference(args):
     """The oracle as it stands on the host cores (rank 0 only)."""
     rank = _env_int("RANK", 0)
@@ -208,18 +286,21 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": _config(wl, "f64"),
+            "data": "synthetic", "config": _config(wl),
+            "precision": "float64 (numpy), one thread",
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "host_cpus": os.cpu_count(), "cpu_model": cpu_model(), "sample": sample},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def _config(wl, precision):
+def _config(wl):
+    """The workload (the same for both arms; the precision is in dtype and
+    precision)."""
     return {"workload": wl.name, "glevel": wl.glevel, "ncol": wl.ncol, "nv": wl.nv,
             "dt_s": wl.dt, "n_small": wl.n_small, "substeps_per_large_step": wl.substeps_per_large,
-            "forcing": wl.forcing, "precision": precision,
+            "forcing": wl.forcing,
             "l2": "inputs larger than L2: state + stage work set at g6x32 exceed 129 MB"}
 
 
@@ -273,6 +354,85 @@ def whole_job_rate(world, units_per_rank, seconds):
 
 # ------------------------------------------------------------------ GPU arm
 
+def _lonlat_basis(points):
+    """East and north unit vectors at unit positions (N, 3); zero at the
+    poles, where they are undefined."""
+    x, y, z = points[:, 0], points[:, 1], points[:, 2]
+    rxy = np.hypot(x, y)
+    ok = rxy > 1e-12
+    east = np.zeros_like(points)
+    north = np.zeros_like(points)
+    east[ok] = np.stack([-y[ok] / rxy[ok], x[ok] / rxy[ok], np.zeros(ok.sum())], 1)
+    north[ok] = np.stack([-z[ok] * x[ok] / rxy[ok], -z[ok] * y[ok] / rxy[ok], rxy[ok]], 1)
+    return east, north
+
+
+def physical_fields(thor, state, ncol, nv, east, north):
+    """u, v (eastward, northward wind), w (vertical wind at the centres, the
+    mean of the two interfaces), T and rho of a state, each (ncol, nv)."""
+    rho = thor.thor_state_get(state, thor.THOR_FIELD_RHO, ncol, nv)
+    M = thor.thor_state_get(state, thor.THOR_FIELD_MOM, ncol, nv)
+    W = thor.thor_state_get(state, thor.THOR_FIELD_W, ncol, nv)
+    T = thor.thor_state_get(state, thor.THOR_FIELD_TEMPERATURE, ncol, nv)
+    v3 = M / rho[..., None]
+    return {"u": np.einsum("ckj,cj->ck", v3, east), "v": np.einsum("ckj,cj->ck", v3, north),
+            "w": 0.5 * (W[:, :-1] + W[:, 1:]) / rho, "T": T, "rho": rho}
+
+
+def field_error_row(a, b):
+    """Per field of the mixed run a against the float64 run b: relative L2
+    and the largest absolute difference (m/s for the winds, K, kg/m^3)."""
+    out = {}
+    for k in ("u", "v", "w", "T", "rho"):
+        d = a[k] - b[k]
+        out[k] = {"rel_l2": float(np.linalg.norm(d) / max(np.linalg.norm(b[k]), 1e-300)),
+                  "max_abs": float(np.max(np.abs(d)))}
+    return out
+
+
+def precision_error(thor, make_state, grid, wl, checkpoints, kc, bs):
+    """The mixed path (launch shape kc, bs, graph replay) against the float64
+    path from the same start, per field after each large-step count in
+    ``checkpoints``."""
+    east, north = _lonlat_basis(thor.thor_grid_points(grid))
+    a = make_state(thor.THOR_MIXED)
+    b = make_state(thor.THOR_FP64)
+    rows = {}
+    try:
+        thor.thor_tune(a, thor.THOR_TUNE_KCHUNK, kc)
+        thor.thor_tune(a, thor.THOR_TUNE_BLOCK, bs)
+        done = 0
+        for n in checkpoints:
+            thor.thor_step(a, n - done, wl.n_small, wl.dt)
+            thor.thor_step(b, n - done, wl.n_small, wl.dt)
+            done = n
+            fa = physical_fields(thor, a, wl.ncol, wl.nv, east, north)
+            fb = physical_fields(thor, b, wl.ncol, wl.nv, east, north)
+            rows[str(n)] = field_error_row(fa, fb)
+        m_a, m_b = thor.thor_diag(a)["mass"], thor.thor_diag(b)["mass"]
+    finally:
+        thor.thor_state_destroy(a)
+        thor.thor_state_destroy(b)
+    return {"against": "the float64 path from the same start (which matches the float64 oracle to 1e-10)",
+            "large_steps": rows, "mass_rel_diff_at_end": abs(m_a - m_b) / m_b}
+
+
+def fp64_flops(kind):
+    """Float64 operations per large step of the float64 path, from the
+    committed ncu instruction counts, if they were taken of this source
+    (thor_step.cu's SHA-1), else None."""
+    import hashlib
+    try:
+        src = open(os.path.join(ROOT, "paper_1607_05535_gb300", "csrc", "thor_step.cu")).read()
+        kv = dict(l.split(None, 1) for l in open(os.path.join(ROOT, "profiles", "fp64_ops_hs_g6_L32.txt"))
+                  if l.strip() and not l.startswith("#"))
+        if kv["step_source_sha1"].strip() == hashlib.sha1(src.encode()).hexdigest():
+            return float(kv[kind])
+    except Exception:
+        pass
+    return None
+
+
 def run_thor(args):
     import torch
     import paper_1607_05535_gb300 as thor
@@ -282,20 +442,22 @@ def run_thor(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    wl = workload_of(args.workload)
-    P = wl.planet
-    forcing = {"none": 0, "held_suarez": 1, "hot_jupiter": 2}[wl.forcing]
-    sp = thor.thor_spring(1.15, 1.0, 1.0, 0.01, wl.spring_tol, wl.spring_max_iter)
-    grid = thor.thor_grid_create(wl.glevel, wl.nv, P.radius, wl.z_top, sp)
-    planet = thor.thor_planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
-
-    def make_state(prec):
-        init = thor.thor_init(wl.T0, wl.p_surf, wl.noise_amp, wl.seed, forcing, wl.hj_dT, prec, 1, 1)
-        return thor.thor_state_init(grid, planet, init, stream.cuda_stream)
-
     barrier = ranks.barrier
+    max_over_ranks = ranks.max
 
-    def timed(state, steps):
+    def setup(wl):
+        P = wl.planet
+        forcing = {"none": 0, "held_suarez": 1, "hot_jupiter": 2}[wl.forcing]
+        sp = thor.thor_spring(1.15, 1.0, 1.0, 0.01, wl.spring_tol, wl.spring_max_iter)
+        grid = thor.thor_grid_create(wl.glevel, wl.nv, P.radius, wl.z_top, sp)
+        planet = thor.thor_planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
+
+        def make_state(prec):
+            init = thor.thor_init(wl.T0, wl.p_surf, wl.noise_amp, wl.seed, forcing, wl.hj_dT, prec, 1, 1)
+            return thor.thor_state_init(grid, planet, init, stream.cuda_stream)
+        return grid, make_state
+
+    def timed(state, wl, steps):
         """CUDA-event time (ms) of ``steps`` large steps on the state's stream."""
         barrier()
         torch.cuda.synchronize(dev)
@@ -309,15 +471,16 @@ def run_thor(args):
         barrier()
         return a.elapsed_time(b)
 
-    max_over_ranks = ranks.max
-
+    wl = workload_of(args.workload)
+    grid, make_state = setup(wl)
     sn = wl.substeps_per_large
     cells = wl.cells
+    peak, peak_kind = _peaks()
 
     # ---- mixed precision, the headline
     st = make_state(thor.THOR_MIXED)
     # clocks sampled over the whole GPU leg (autotuning, warm-up, timed steps,
-    # profiled pass, end to end, float64 leg, ensemble)
+    # profiled pass, end to end, float64 leg, ensemble, hot Jupiter, errors)
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     # launch shape from the autotuner (state restored afterwards), unless given
     if args.kchunk:
@@ -330,11 +493,11 @@ def run_thor(args):
         thor.thor_step(st, 1, wl.n_small, wl.dt)          # also captures the CUDA graph
     torch.cuda.synchronize(dev)
     l0 = thor.thor_launch_count(st)
-    ms = timed(st, args.steps)                             # graph replays, no per-kernel events
+    ms = timed(st, wl, args.steps)                          # graph replays, no per-kernel events
     launches = thor.thor_launch_count(st) - l0
     # per-kernel CUDA-event durations: the same steps launched kernel by kernel
     thor.thor_profile(st, 1)
-    timed(st, args.steps)
+    timed(st, wl, args.steps)
     prof = {}
     for kid, name in enumerate(thor.KERNELS):
         tot, n = thor.thor_profile_read(st, kid)
@@ -346,15 +509,31 @@ def run_thor(args):
     value = whole_job_rate(world, cells * sn * args.steps, ms / 1e3)
     days_per_hour = world * args.steps * wl.dt / 86400.0 / (ms / 1e3 / 3600.0)
 
-    # dominant kernel and its roofline
+    # dominant kernel and its roofline (method words of the counting rule)
     dom = max(prof, key=lambda k: prof[k][0])
     tot, n = prof[dom]
     nlev = wl.nv + 1 if dom in ("slow_w",) else wl.nv
-    bytes_per_launch = KERNEL_WORDS[dom] * 4 * wl.ncol * nlev
-    achieved = bytes_per_launch / (tot / n / 1e3) / 1e9
-    peak, peak_kind = _peaks()
-    kernels = {k: {"ms_total": round(v[0], 4), "launches": v[1], "us_avg": round(1e3 * v[0] / v[1], 2),
-                   "share": round(v[0] / sum(x[0] for x in prof.values()), 4)} for k, v in prof.items()}
+    mw, moved = KERNEL_WORDS[dom]
+    bytes_per_launch = mw * 4 * wl.ncol * nlev
+    us = 1e3 * tot / n
+    achieved = bytes_per_launch / (us / 1e6) / 1e9
+    moved_bytes = moved * 4 * wl.ncol * nlev
+    kernels = {}
+    for k, v in prof.items():
+        lev = wl.nv + 1 if k in ("slow_w",) else wl.nv
+        kw = KERNEL_WORDS.get(k, (None, None))
+        avg = 1e3 * v[0] / v[1]
+        kernels[k] = {"ms_total": round(v[0], 4), "launches": v[1], "us_avg": round(avg, 2),
+                      "share": round(v[0] / sum(x[0] for x in prof.values()), 4)}
+        if kw[0] is not None:
+            kernels[k]["method_words"] = kw[0]
+            kernels[k]["moved_words"] = kw[1]
+            kernels[k]["frac_method"] = round(kw[0] * 4 * wl.ncol * lev / (avg / 1e6) / 1e9 / peak, 4)
+    step_bytes = step_method_words(wl.n_small) * 4 * cells
+    whole = {"method_words_per_cell": step_method_words(wl.n_small), "bytes": step_bytes,
+             "ms": ms / args.steps, "achieved": step_bytes / (ms / args.steps / 1e3) / 1e9,
+             "unit": "GB/s", "peak": peak}
+    whole["frac"] = whole["achieved"] / peak
 
     # ---- end to end through the C ABI with pinned host buffers
     shapes = {thor.THOR_FIELD_RHO: (wl.ncol, wl.nv), thor.THOR_FIELD_MOM: (wl.ncol, wl.nv, 3),
@@ -377,17 +556,58 @@ def run_thor(args):
     e2e = world * cells * sn * e2e_steps / t_e2e
     thor.thor_state_destroy(st)
 
-    # ---- float64 leg
+    # ---- float64 leg and its bound: min of HBM (8-byte words) and the
+    # float64 pipe (the float64 operations of a large step, counted by ncu,
+    # at the GB300's nominal 1.25 TFLOP/s; 1.0 TFLOP/s measured)
     st64 = make_state(thor.THOR_FP64)
     for _ in range(min(args.warmup, 2)):
         thor.thor_step(st64, 1, wl.n_small, wl.dt)
     k64 = max(1, min(args.steps, 5))
-    ms64 = max_over_ranks(timed(st64, k64))
+    ms64 = max_over_ranks(timed(st64, wl, k64))
     thor.thor_state_destroy(st64)
     value64 = world * cells * sn * k64 / (ms64 / 1e3)
-    thor.thor_grid_destroy(grid)
+    t_hbm64 = 2 * step_bytes / (peak * 1e9)
+    flops64 = fp64_flops("fp64_ops_per_large_step") if wl.name == wls.HS_G6.name else None
+    fp64 = {"value": value64, "unit": METRIC, "steps": k64, "ms_per_step": ms64 / k64,
+            "model_days_per_hour": world * k64 * wl.dt / 86400.0 / (ms64 / 1e3 / 3600.0),
+            "bound": {"hbm_ms": 1e3 * t_hbm64, "hbm_frac": t_hbm64 / (ms64 / k64 / 1e3)}}
+    if flops64:
+        t_alu = flops64 / 1.25e12
+        fp64["bound"].update({"fp64_ops_per_step": flops64, "fp64_peak_tflops": 1.25, "fp64_peak_kind": "nominal",
+                              "fp64_ms": 1e3 * t_alu, "fp64_frac": t_alu / (ms64 / k64 / 1e3),
+                              "bound": "fp64" if t_alu > t_hbm64 else "hbm"})
 
     ens = run_ensemble(thor, torch, dev, stream, args, max_over_ranks) if not args.no_ensemble else None
+
+    # ---- hot Jupiter (config 3), mixed precision in the same launch shape
+    hj = None
+    if not args.no_hot_jupiter and args.workload != "hj_g6":
+        whj = workload_of("hj_g6")
+        ghj, mk_hj = setup(whj)
+        sh = mk_hj(thor.THOR_MIXED)
+        thor.thor_tune(sh, thor.THOR_TUNE_KCHUNK, tuned_kc)
+        thor.thor_tune(sh, thor.THOR_TUNE_BLOCK, tuned_bs)
+        for _ in range(args.warmup):
+            thor.thor_step(sh, 1, whj.n_small, whj.dt)
+        khj = max(1, min(args.steps, 20))
+        ms_hj = max_over_ranks(timed(sh, whj, khj))
+        nf = thor.thor_diag(sh)["nonfinite"]
+        thor.thor_state_destroy(sh)
+        snj = whj.substeps_per_large
+        hj = {"workload": whj.name, "value": world * whj.cells * snj * khj / (ms_hj / 1e3), "unit": METRIC,
+              "steps": khj, "ms_per_step": ms_hj / khj, "substeps_per_large_step": snj, "dt_s": whj.dt,
+              "model_days_per_hour": world * khj * whj.dt / 86400.0 / (ms_hj / 1e3 / 3600.0),
+              "nonfinite": nf, "dtype": "f32"}
+        hj_bytes = step_method_words(whj.n_small) * 4 * whj.cells
+        hj["whole_step_frac"] = hj_bytes / (ms_hj / khj / 1e3) / 1e9 / peak
+        if args.error_steps:
+            hj["error"] = precision_error(thor, mk_hj, ghj, whj, args.error_steps, tuned_kc, tuned_bs)
+        thor.thor_grid_destroy(ghj)
+
+    # ---- per-field error of the headline number (mixed against float64)
+    err = precision_error(thor, make_state, grid, wl, args.error_steps, tuned_kc, tuned_bs) \
+        if args.error_steps else None
+    thor.thor_grid_destroy(grid)
     clocks = sampler.stop() if sampler else None
 
     if rank != 0:
@@ -397,10 +617,11 @@ def run_thor(args):
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": _config(wl, "mixed: f32 fields and stencils, f64 vertical solve"),
+        "config": _config(wl),
+        "precision": "mixed: f32 fields and stencils, f64 vertical solve and reductions",
         "model_days_per_hour": days_per_hour,
-        "fp64": {"value": value64, "unit": METRIC, "steps": k64, "ms_per_step": ms64 / k64,
-                 "model_days_per_hour": world * k64 * wl.dt / 86400.0 / (ms64 / 1e3 / 3600.0)},
+        "error": err,
+        "fp64": fp64,
         "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                 "steps": e2e_steps},
         "gpu_launches": launches,
@@ -408,21 +629,33 @@ def run_thor(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": _traffic(dom), "algorithmic_bytes_per_launch": bytes_per_launch,
-                     "us_per_launch": 1e3 * tot / n},
+                     "method_words_per_cell": mw, "moved_words_per_cell": moved,
+                     "moved_bytes_per_launch": moved_bytes,
+                     "frac_moved": moved_bytes / (us / 1e6) / 1e9 / peak, "us_per_launch": us,
+                     "whole_step": whole},
         "kernels": kernels,
         "clocks": clocks,
         "diag_after": {k: diag[k] for k in ("mass", "max_vh", "max_w", "mean_T", "nonfinite")},
     }
     if ens is not None:
         line["ensemble"] = ens
+    if hj is not None:
+        line["hot_jupiter"] = hj
     if world == 1 and not args.no_cpu_baseline:
-        _, _, _, t_slow, t_small, t_phys = oracle_sample(wl)
-        per_large = 3 * t_slow + sn * t_small + t_phys
+        ncpu = os.cpu_count() or 1
+        one, t1 = oracle_rates(wl, 1)
+        # one process of the sample holds about 1.8 GB at glevel 6: keep
+        # the leg well inside the memory the host has free
+        procs = max(1, min(ncpu, args.cpu_processes, int(_mem_available_gb() // 4.0)))
+        allc, tall = oracle_rates(wl, procs) if procs > 1 else (one, t1)
+        a, b, c = t1[0]
         line["cpu_baseline"] = {
-            "value": cells * sn / per_large, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": (f"{wl.name}: one oracle slow-term evaluation ({t_slow:.1f} s), one small step "
-                       f"({t_small:.1f} s) and one physics call, scaled to 3 slow + {sn} small + "
-                       "physics per large step; numpy float64, single thread")}
+            "value": allc, "unit": METRIC, "cores": procs, "kind": "oracle",
+            "single_core": one, "host_cpus": ncpu, "cpu_model": cpu_model(),
+            "sample": (f"{wl.name}: one oracle slow-term evaluation ({a:.1f} s), one small step ({b:.1f} s) and "
+                       f"one physics call ({c:.1f} s) per process, scaled to 3 slow + {sn} small + physics per "
+                       f"large step; numpy float64, one thread per process; value = {procs} processes at once "
+                       "(each its own copy of the workload), single_core = one process alone")}
     print(json.dumps(line), flush=True)
     ranks.close()
     return 0
@@ -504,8 +737,13 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--kchunk", type=int, default=0, help="levels per thread (skips the autotuner)")
     ap.add_argument("--block", type=int, default=128, help="block size with --kchunk")
+    ap.add_argument("--no-hot-jupiter", action="store_true")
+    ap.add_argument("--error-steps", default="10,100,1000",
+                    help="large-step counts at which the mixed path is compared with float64 ('' skips)")
+    ap.add_argument("--cpu-processes", type=int, default=16, help="processes of the all-cores oracle leg")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)      # at least 3 untimed warm-up steps
+    args.error_steps = [int(x) for x in args.error_steps.split(",") if x.strip()]
     if args.impl == "reference":
         return run_reference(args)
     return run_thor(args)

@@ -257,7 +257,8 @@ int thor_launch_count(const thor_state* state, long long* count);
  * return THOR_ENONFINITE if any value is NaN or Inf; the state is the one
  * after the step (restore a checkpoint with thor_state_set). Default 0. */
 enum { THOR_TUNE_KCHUNK = 0, THOR_TUNE_GRAPH = 1, THOR_TUNE_CHECK_FINITE = 2, THOR_TUNE_BLOCK = 3,
-       THOR_TUNE_SOLVE_TMA = 4, THOR_TUNE_ENERGY_FIXER = 5, THOR_TUNE_BUDGET = 6 };
+       THOR_TUNE_SOLVE_TMA = 4, THOR_TUNE_ENERGY_FIXER = 5, THOR_TUNE_BUDGET = 6,
+       THOR_TUNE_RK_STAGES = 7 };
 int thor_tune(thor_state* state, int knob, int value);
 
 /* Energy and angular-momentum budget of the large steps recorded since
@@ -327,7 +328,13 @@ int thor_zonal_read_w(thor_state* state, int nlat, double* out, size_t n, long l
  * steps (at most 2^24), one budget row that thor_budget_read returns; 0 stops
  * recording and frees the rows. Allocates value * 64 bytes on the device and
  * synchronises the state's stream; recording costs two float64 reductions
- * of the state per large step. Neither knob applies to thor_ensemble_step. */
+ * of the state per large step. Neither knob applies to thor_ensemble_step.
+ * THOR_TUNE_RK_STAGES: 1, 2 or 3 (default) RK3 stages per large step (Sec.
+ * 3). With fewer than 3 a large step ends after that stage with the stage's
+ * result X^(s+1) = X^t + X* in the state and runs neither the energy fixer
+ * nor the physics; with 1 a large step is one slow-term evaluation and one
+ * small step of dt/3 from X^t. For tests that check the first small step on
+ * its own; THOR_EINVAL outside 1..3. */
 
 /* Launch-shape autotuner (an extension; the paper fixes no launch shapes).
  * Times `steps` large steps of (n_small, dt) for every levels-per-thread

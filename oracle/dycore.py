@@ -346,6 +346,18 @@ def stage_schedule(dt, n_small):
     return [(dt / 3.0, 1), (dt / n_small, n_small // 2), (dt / n_small, n_small)]
 
 
+def rk_stage(model, Xt, Xs, dtau, nsub, Kd):
+    """One RK3 stage (reading R1): the slow terms at the stage state Xs, the
+    perturbations started at Xt - Xs (p* from Eq. theta_to_p), nsub small
+    steps of dtau, and the stage's result X^(s+1) = Xs + X*."""
+    co = slow_terms(model, Xs, Kd)
+    pert = dict(rho=Xt.rho - Xs.rho, M=Xt.M - Xs.M, W=Xt.W - Xs.W, Th=Xt.Th.copy(),
+                p=pressure(model.planet, Xt.Th) - co["p"])
+    for _ in range(nsub):
+        pert = small_step(model, Xs, co, pert, dtau, Kd)
+    return State(Xs.rho + pert["rho"], Xs.M + pert["M"], Xs.W + pert["W"], pert["Th"])
+
+
 def large_step(model, X, dt, n_small, energy_fixer=False, budget=None):
     """One large step: three RK3 stages of small steps (reading R1), then, if
     energy_fixer, the uniform internal-energy adjustment of energy.energy_fix
@@ -356,12 +368,7 @@ def large_step(model, X, dt, n_small, energy_fixer=False, budget=None):
     Xt = X
     Xs = X
     for dtau, nsub in stage_schedule(dt, n_small):
-        co = slow_terms(model, Xs, Kd)
-        pert = dict(rho=Xt.rho - Xs.rho, M=Xt.M - Xs.M, W=Xt.W - Xs.W, Th=Xt.Th.copy(),
-                    p=pressure(model.planet, Xt.Th) - co["p"])
-        for _ in range(nsub):
-            pert = small_step(model, Xs, co, pert, dtau, Kd)
-        Xs = State(Xs.rho + pert["rho"], Xs.M + pert["M"], Xs.W + pert["W"], pert["Th"])
+        Xs = rk_stage(model, Xt, Xs, dtau, nsub, Kd)
     if energy_fixer or budget is not None:
         from .energy import budget_row, energy_fix
         Xd, dT = Xs, 0.0

@@ -890,6 +890,12 @@ int thor_tune(thor_state* s, int knob, int value) {
     s->impl->solve_tma = value != 0;
     return THOR_OK;
   }
+  if (knob == THOR_TUNE_RK_STAGES) {
+    if (value < 1 || value > 3) return THOR_EINVAL;
+    s->impl->rk_stages = value;
+    s->impl->reset_graph();
+    return THOR_OK;
+  }
   if (knob == THOR_TUNE_ENERGY_FIXER || knob == THOR_TUNE_BUDGET) {
     thor::ImplBase* I = s->impl.get();
     if (knob == THOR_TUNE_BUDGET && (value < 0 || value > (1 << 24))) return THOR_EINVAL;

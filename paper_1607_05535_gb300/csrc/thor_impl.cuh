@@ -97,6 +97,7 @@ struct ImplBase {
   int kchunk = 2;                      // levels per thread in the stencil kernels
   int block = kBlock;                  // threads (columns) per block of the stencil kernels
   int solve_tma = 1;                   // TMA-staged column solve where available
+  int rk_stages = 3;                   // RK3 stages a large step runs (THOR_TUNE_RK_STAGES; tests)
   int* dev_err = nullptr;              // device flag: 1 = a bounded device wait timed out
   // energy fixer and budget (thor_tune THOR_TUNE_ENERGY_FIXER / THOR_TUNE_BUDGET)
   int energy_fix = 0;
@@ -193,7 +194,7 @@ struct Impl : ImplBase {
   // the same; used on a non-default stream when no profiling is recorded
   cudaGraphExec_t graph_exec = nullptr;
   double graph_dt = 0;
-  int graph_n = 0, graph_kc = 0, graph_bs = 0, graph_tma = -1, graph_energy = -1;
+  int graph_n = 0, graph_kc = 0, graph_bs = 0, graph_tma = -1, graph_energy = -1, graph_stages = -1;
   std::unique_ptr<SolveMaps> smaps;   // null where the staged solve does not apply
   // second stream for the kernels of a stage that run beside others, forked
   // from and joined to the state's stream by events (null: everything on the
@@ -201,7 +202,7 @@ struct Impl : ImplBase {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join0 = nullptr;
   int build_solve_maps();
-  cudaError_t launch_solve_tma(dim3 grid, int stage, double dtau, int want_div, int last);
+  cudaError_t launch_solve_tma(dim3 grid, int stage, const Xf<R>& Xo, double dtau, int want_div, int last);
   long long graph_launches = 0;
   void drop_graph() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -211,7 +212,7 @@ struct Impl : ImplBase {
   int step(int n_large, int n_small, double dt) override {
     if (use_graph && stream != nullptr && !prof_on && n_large > 0) {
       if (!graph_exec || graph_dt != dt || graph_n != n_small || graph_kc != kchunk || graph_bs != block ||
-          graph_tma != solve_tma || graph_energy != energy_key()) {
+          graph_tma != solve_tma || graph_energy != energy_key() || graph_stages != rk_stages) {
         drop_graph();
         cudaGraph_t g = nullptr;
         long long before = launches;
@@ -237,6 +238,7 @@ struct Impl : ImplBase {
         graph_bs = block;
         graph_tma = solve_tma;
         graph_energy = energy_key();
+        graph_stages = rk_stages;
       }
       for (int i = 0; i < n_large; ++i) {
         if (cudaGraphLaunch(graph_exec, stream)) return -3;

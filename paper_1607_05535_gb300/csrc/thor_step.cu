@@ -1217,7 +1217,8 @@ int Impl<R>::large_step(double dt, int n_small) {
   // the first small step's stencils. With per-kernel profiling everything
   // stays on the state's stream, in the same order.
   const bool fork = side != nullptr && !prof_on;
-  const bool energy = (energy_fix || budget_cap > 0) && fixbuf != nullptr;
+  const int nstages = rk_stages;      // 3, or fewer when a test stops the step early
+  const bool energy = (energy_fix || budget_cap > 0) && fixbuf != nullptr && nstages == 3;
   double* fin0 = fixbuf + kDiagBlocks * 8;                       // reduction at the step start
   double* part1 = fixbuf + (kDiagBlocks + 1) * 8;
   double* fin1 = part1 + kDiagBlocks * 8;                        // after the dynamics
@@ -1228,8 +1229,9 @@ int Impl<R>::large_step(double dt, int n_small) {
     chk(launch_k(k_diag_final, 1, 256, 0, stream, fixbuf, kDiagBlocks));
     launches += 2;
   }
-  for (int s = 0; s < 3; ++s) {
-    Xf<R> Xs = s == 0 ? Xt : Xst, Xo = s == 2 ? Xt : Xst;
+  for (int s = 0; s < nstages; ++s) {
+    // the last stage run writes X^(s+1) into the state
+    Xf<R> Xs = s == 0 ? Xt : Xst, Xo = s == nstages - 1 ? Xt : Xst;
     cudaStream_t aux = fork ? side : stream;
     mark(THOR_K_DERIVED, true);
     chk(launch_k(k_derived<R>, g2i, bs, 0, stream, G, U, ph, Xs, T, shallow, kc));
@@ -1298,7 +1300,7 @@ int Impl<R>::large_step(double dt, int n_small) {
       if (fork && j == 0) chk(cudaStreamWaitEvent(stream, ev_join, 0));
       mark(THOR_K_SS_SOLVE, true);
       if (staged)
-        chk(launch_solve_tma(gsolve, s, dts[s], want_div, last));
+        chk(launch_solve_tma(gsolve, s, Xo, dts[s], want_div, last));
       else
         chk(launch_k(k_ss_solve<R>, gsolve, 64, solve_smem, stream, G, U, ph, Xs, SL, P, T, F, dts[s],
                      want_div, Xo, last));
@@ -1317,7 +1319,7 @@ int Impl<R>::large_step(double dt, int n_small) {
       ++launches;
     }
   }
-  if (forcing != 0) {
+  if (forcing != 0 && nstages == 3) {
     mark(THOR_K_PHYSICS, true);
     chk(launch_k(k_surface_p<R>, g1, bs, 0, stream, G, U, ph, Xt, T));
     chk(launch_k(k_physics<R>, g2, bs, 0, stream, G, U, ph, Xt, T, forcing, dt, hj_dT, kc));
@@ -1328,13 +1330,13 @@ int Impl<R>::large_step(double dt, int n_small) {
 }
 
 template <>
-cudaError_t Impl<float>::launch_solve_tma(dim3 grid, int stage, double dtau, int want_div, int last) {
+cudaError_t Impl<float>::launch_solve_tma(dim3 grid, int stage, const Xf<float>& Xo, double dtau, int want_div,
+                                          int last) {
   return launch_k(k_ss_solve_tma, grid, 32 * kSolveWarps, solve_tma_smem_bytes(G.nv), stream, G, U, ph,
-                  *smaps, (int)(stage == 0), stage == 0 ? Xt : Xst, SL, P, T, dtau, want_div,
-                  stage == 2 ? Xt : Xst, last, dev_err);
+                  *smaps, (int)(stage == 0), stage == 0 ? Xt : Xst, SL, P, T, dtau, want_div, Xo, last, dev_err);
 }
 template <>
-cudaError_t Impl<double>::launch_solve_tma(dim3, int, double, int, int) {
+cudaError_t Impl<double>::launch_solve_tma(dim3, int, const Xf<double>&, double, int, int) {
   return cudaErrorInvalidValue;
 }
 

@@ -87,3 +87,18 @@ def field_errors(A, B):
     """Relative L2 per field of A against B (oracle) and max-abs on W."""
     return dict(rho=rel_l2(A.rho, B.rho), M=rel_l2(A.M, B.M, 1e-300), W=rel_l2(A.W, B.W, 1e-300),
                 Th=rel_l2(A.Th, B.Th), W_maxabs=float(np.max(np.abs(A.W - B.W))))
+
+
+def change_errors(A, B, X0):
+    """Per element, per field: max |A - B| over the largest change of the
+    oracle's field from its start, max |B - X0|. A localised error (a
+    pentagon, a rhombus edge) cannot hide in this the way it can in a
+    relative L2 dominated by the hydrostatic background of rho and rho theta."""
+    out = {}
+    for f in ("rho", "M", "W", "Th"):
+        a, b, x0 = getattr(A, f), getattr(B, f), getattr(X0, f)
+        change = float(np.max(np.abs(b - x0)))
+        err = float(np.max(np.abs(a - b)))
+        out[f] = err / change if change > 0 else err
+    return out
+

@@ -105,6 +105,58 @@ def test_ensemble_matches_members_stepped_alone(precision, graph):
         pool.close()
 
 
+# (glevel, radius factor, omega factor, dt, n_small, forcing, shallow, hydrostatic)
+ORACLE_MEMBERS = [
+    (3, 1.0, 1.0, 1800.0, 6, "held_suarez", 0, 0),
+    (2, 0.3, 4.0, 900.0, 8, "held_suarez", 0, 1),
+    (3, 0.5, 2.0, 600.0, 4, "none", 1, 0),
+    (2, 2.0, 0.5, 2400.0, 6, "held_suarez", 0, 0),
+]
+
+
+def test_ensemble_members_match_the_oracle():
+    """Four uneven members (grid level, radius, rotation, time step, small-step
+    count, forcing; one under the hydrostatic and one under the shallow
+    approximation) stepped together in float64, two large steps, against the
+    oracle run of each member: every field within 1e-10 relative L2 and every
+    element within 1e-8 of its field's largest change (W of the hydrostatic
+    member, diagnosed from nearly cancelling terms, to 1e-12 g rho dtau)."""
+    from dataclasses import replace
+    from harness import Pair, change_errors, field_errors
+    from oracle import dycore as dc
+    torch.cuda.set_device(0)
+    pairs, n_small, dts = [], [], []
+    try:
+        for i, (g, rf, of, dt, ns, forcing, sh, hy) in enumerate(ORACLE_MEMBERS):
+            planet = replace(wls.EARTH, radius=wls.EARTH.radius * rf, omega=wls.EARTH.omega * of)
+            wl = wls.Workload(f"member_{i}", glevel=g, nv=12, z_top=24.0e3, planet=planet, T0=300.0,
+                              p_surf=1.0e5, noise_amp=0.5, seed=77 + i, forcing=forcing, dt=dt, n_small=ns,
+                              n_large=2)
+            pairs.append(Pair(wl, shallow=bool(sh), hydrostatic=bool(hy)))
+            n_small.append(ns)
+            dts.append(dt)
+        X0 = [p.oracle_initial() for p in pairs]
+        ens = thor.thor_ensemble_create([p.state for p in pairs], None)
+        try:
+            thor.thor_ensemble_step(ens, 2, n_small, dts)
+        finally:
+            thor.thor_ensemble_destroy(ens)
+        for p, X, ns, dt in zip(pairs, X0, n_small, dts):
+            ref = dc.run(p.model, X, 2, ns, dt)
+            got = p.get()
+            e = field_errors(got, ref)
+            c = change_errors(got, ref, X)
+            w_scale = p.wl.planet.gravity * float(np.max(ref.rho)) * dt / ns
+            assert e["rho"] < 1e-10 and e["Th"] < 1e-10 and e["M"] < 1e-10, (p.wl.name, e)
+            assert e["W"] < 1e-10 or e["W_maxabs"] < 1e-12 * w_scale, (p.wl.name, e)
+            for k in ("rho", "Th", "M"):
+                assert c[k] < 1e-8, (p.wl.name, k, c)
+            assert c["W"] < 1e-8 or e["W_maxabs"] < 1e-12 * w_scale, (p.wl.name, c)
+    finally:
+        for p in pairs:
+            p.close()
+
+
 def test_ensemble_launch_count_is_independent_of_members():
     """One launch per kernel for the whole ensemble: the launch count of a
     large step does not grow with the member count."""

@@ -14,7 +14,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import paper_1607_05535_gb300 as thor
-from harness import Pair, field_errors, init_struct, planet_struct
+from harness import Pair, change_errors, field_errors, init_struct, planet_struct
 from oracle import dycore as dc
 import workloads as wls
 
@@ -76,8 +76,54 @@ def test_fp64_large_step_matches_oracle_full_size():
         X = p.oracle_initial()
         ref = dc.large_step(p.model, X, wl.dt, wl.n_small)
         thor.thor_step(p.state, 1, wl.n_small, wl.dt)
-        e = field_errors(p.get(), ref)
+        got = p.get()
+        e = field_errors(got, ref)
         assert max(e["rho"], e["Th"], e["M"], e["W"]) < 1e-10, e
+        c = change_errors(got, ref, X)
+        assert max(c.values()) < 1e-8, c
+    finally:
+        p.close()
+
+
+def test_fp64_first_small_step_matches_oracle_full_size():
+    """The first RK stage alone (one slow-term evaluation and one small step
+    of dt/3, THOR_TUNE_RK_STAGES = 1) at 40962 x 32 in float64 against the
+    oracle's rk_stage: every field to 1e-10 relative L2 and every element
+    to 1e-8 of its field's largest change."""
+    wl = WL.with_(n_large=1)
+    p = Pair(wl, precision=thor.THOR_FP64)
+    try:
+        X = p.oracle_initial()
+        ref = dc.rk_stage(p.model, X, X, wl.dt / 3.0, 1, p.model.Kd(wl.dt))
+        thor.thor_tune(p.state, thor.THOR_TUNE_RK_STAGES, 1)
+        thor.thor_step(p.state, 1, wl.n_small, wl.dt)
+        got = p.get()
+        e = field_errors(got, ref)
+        assert max(e["rho"], e["Th"], e["M"], e["W"]) < 1e-10, e
+        c = change_errors(got, ref, X)
+        assert max(c.values()) < 1e-8, c
+    finally:
+        p.close()
+
+
+@pytest.mark.slow
+def test_fp64_hot_jupiter_large_step_matches_oracle_full_size():
+    """The hot-Jupiter workload at full size (40962 x 32, R = 1e8 m, 220 bar
+    to 1 mbar, dt 300 s, 6 small steps, Newtonian relaxation to the day-night
+    T_eq of Sec. 6.2 with the seeded contrast): one float64 large step
+    against the oracle's, every field to 1e-10 relative L2. From rest the
+    first step moves air only through the heating of the day side."""
+    wl = wls.HJ_G6.with_(n_large=1)
+    p = Pair(wl, precision=thor.THOR_FP64)
+    try:
+        X = p.oracle_initial()
+        ref = dc.large_step(p.model, X, wl.dt, wl.n_small)
+        thor.thor_step(p.state, 1, wl.n_small, wl.dt)
+        got = p.get()
+        e = field_errors(got, ref)
+        w_scale = wl.planet.gravity * float(np.max(ref.rho)) * wl.dt / wl.n_small
+        assert max(e["rho"], e["Th"], e["M"]) < 1e-10, e
+        assert e["W"] < 1e-10 or e["W_maxabs"] < 1e-12 * w_scale, e
     finally:
         p.close()
 

@@ -11,26 +11,49 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import paper_1607_05535_gb300 as thor
-from harness import Pair, field_errors
+from conftest import report_dir
+from harness import Pair, change_errors, field_errors
 from oracle import diagnostics as dg
 from oracle import dycore as dc
 import workloads as wls
 
 TOL = 1e-10
+# per element: the largest difference over the largest change of the field
+# from its start (float64 rounding of the fields' full values, carried by a
+# few large steps, stays near 1e-12 of the change)
+CHANGE_TOL = 1e-8
+
+REPORT = {}
 
 SMALL = wls.HS_G4.with_(name="hs_g3_L12", glevel=3, nv=12, n_large=2)
 
 
-def _assert_close(A, B, tol=TOL, w_scale=0.0):
+def _assert_close(A, B, tol=TOL, w_scale=0.0, X0=None, name=None):
     """Every field within tol relative L2; with w_scale > 0, W may instead
     pass at 1e-12 w_scale absolute: from a column in discrete balance W
     answers the difference -dp/dr - g rho of nearly equal terms of size
     w_scale = g rho dtau per small step, which float64 rounds at about
-    1e-16 w_scale in either implementation, however small W itself is."""
+    1e-16 w_scale in either implementation, however small W itself is.
+    With the start state X0 every element is also held to CHANGE_TOL of its
+    field's largest change (change_errors)."""
     e = field_errors(A, B)
     assert e["rho"] < tol and e["Th"] < tol, e
     assert e["M"] < tol, e
     assert e["W"] < tol or e["W_maxabs"] < 1e-12 * w_scale, e
+    if X0 is not None:
+        c = change_errors(A, B, X0)
+        e.update({"change_" + k: v for k, v in c.items()})
+        for k in ("rho", "Th", "M"):
+            assert c[k] < CHANGE_TOL, (k, c)
+        assert c["W"] < CHANGE_TOL or e["W_maxabs"] < 1e-12 * w_scale, c
+    if name:
+        REPORT[name] = e
+        d = report_dir()
+        if d:
+            import json
+            import os
+            with open(os.path.join(d, "parity_float64.json"), "w") as f:
+                json.dump(REPORT, f, indent=1)
     return e
 
 
@@ -56,7 +79,7 @@ def test_large_steps(forcing):
         ref = dc.run(p.model, X, steps, wl.n_small, wl.dt)
         thor.thor_step(p.state, steps, wl.n_small, wl.dt)
         assert np.abs(ref.M / ref.rho[..., None]).max() > 1e-6     # the air moves
-        _assert_close(p.get(), ref)
+        _assert_close(p.get(), ref, X0=X, name=f"large_steps_{forcing}")
     finally:
         p.close()
 
@@ -76,7 +99,7 @@ def test_injected_state_two_steps_no_diffusion():
         _assert_close(p.get(), X, 1e-15)
         ref = dc.run(p.model, X, 2, wl.n_small, wl.dt)
         thor.thor_step(p.state, 2, wl.n_small, wl.dt)
-        _assert_close(p.get(), ref)
+        _assert_close(p.get(), ref, X0=X, name="injected_no_diffusion")
     finally:
         p.close()
 
@@ -89,12 +112,57 @@ def test_held_suarez_g4_ten_steps():
         X = p.oracle_initial()
         ref = dc.run(p.model, X, wl.n_large, wl.n_small, wl.dt)
         thor.thor_step(p.state, wl.n_large, wl.n_small, wl.dt)
-        _assert_close(p.get(), ref)
+        _assert_close(p.get(), ref, X0=X, name="held_suarez_g4_L20_10_steps")
         d = thor.thor_diag(p.state)
         o = dg.diagnostics(p.model, ref)
         for k in ("mass", "energy", "aam"):
             assert abs(d[k] - o[k]) <= 1e-10 * abs(o[k]), (k, d[k], o[k])
         assert d["nonfinite"] == 0
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("stages", [1, 2])
+def test_held_suarez_g4_first_stages(stages):
+    """The glevel-4 x 20-level Held-Suarez workload stopped after its first RK
+    stage (one slow-term evaluation and one small step of dt/3 from X^t: the
+    small step on its own) or its second (n/2 more small steps of dt/n), with
+    THOR_TUNE_RK_STAGES, against the oracle's rk_stage."""
+    wl = wls.HS_G4
+    p = Pair(wl)
+    try:
+        X = p.oracle_initial()
+        Kd = p.model.Kd(wl.dt)
+        ref = X
+        for dtau, nsub in dc.stage_schedule(wl.dt, wl.n_small)[:stages]:
+            ref = dc.rk_stage(p.model, X, ref, dtau, nsub, Kd)
+        thor.thor_tune(p.state, thor.THOR_TUNE_RK_STAGES, stages)
+        thor.thor_step(p.state, 1, wl.n_small, wl.dt)
+        assert np.abs(ref.M).max() > 0.0
+        _assert_close(p.get(), ref, X0=X, name=f"held_suarez_g4_L20_stages_{stages}")
+    finally:
+        p.close()
+
+
+def test_held_suarez_g4_one_large_step():
+    """The glevel-4 x 20-level Held-Suarez workload, one large step."""
+    wl = wls.HS_G4
+    p = Pair(wl)
+    try:
+        X = p.oracle_initial()
+        ref = dc.large_step(p.model, X, wl.dt, wl.n_small)
+        thor.thor_step(p.state, 1, wl.n_small, wl.dt)
+        _assert_close(p.get(), ref, X0=X, name="held_suarez_g4_L20_1_step")
+    finally:
+        p.close()
+
+
+def test_rk_stages_knob_is_checked():
+    p = Pair(SMALL)
+    try:
+        for bad in (0, 4):
+            with pytest.raises(thor.ThorError):
+                thor.thor_tune(p.state, thor.THOR_TUNE_RK_STAGES, bad)
     finally:
         p.close()
 
