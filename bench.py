@@ -390,31 +390,54 @@ def field_error_row(a, b):
     return out
 
 
-def precision_error(thor, make_state, grid, wl, checkpoints, kc, bs):
-    """The mixed path (launch shape kc, bs, graph replay) against the float64
-    path from the same start, per field after each large-step count in
-    ``checkpoints``."""
+def precision_error(thor, make_state, grid, wl, checkpoints, kc, bs, compensated=(False, True)):
+    """The mixed path (launch shape kc, bs, graph replay), plain and with the
+    compensated state, against the float64 path from the same start, per
+    field after each large-step count in ``checkpoints``."""
     east, north = _lonlat_basis(thor.thor_grid_points(grid))
-    a = make_state(thor.THOR_MIXED)
-    b = make_state(thor.THOR_FP64)
-    rows = {}
-    try:
+    ref = make_state(thor.THOR_FP64)
+    runs = {}
+    # the spread of the flow itself: a float64 run whose start differs from
+    # the reference's only by the float32 rounding of the mixed start
+    tmp = make_state(thor.THOR_MIXED)
+    start = thor.thor_state_get_all(tmp, wl.ncol, wl.nv)
+    thor.thor_state_destroy(tmp)
+    floor = make_state(thor.THOR_FP64)
+    thor.thor_state_set_all(floor, *start)
+    runs["fp64_rounded_start"] = floor
+    for cmp in compensated:
+        a = make_state(thor.THOR_MIXED)
         thor.thor_tune(a, thor.THOR_TUNE_KCHUNK, kc)
         thor.thor_tune(a, thor.THOR_TUNE_BLOCK, bs)
+        if cmp:
+            thor.thor_tune(a, thor.THOR_TUNE_COMPENSATED, 1)
+        runs["compensated" if cmp else "plain"] = a
+    rows = {k: {} for k in runs}
+    mass = {}
+    try:
         done = 0
+        m0 = thor.thor_diag(ref)["mass"]
         for n in checkpoints:
-            thor.thor_step(a, n - done, wl.n_small, wl.dt)
-            thor.thor_step(b, n - done, wl.n_small, wl.dt)
+            thor.thor_step(ref, n - done, wl.n_small, wl.dt)
+            for a in runs.values():
+                thor.thor_step(a, n - done, wl.n_small, wl.dt)
             done = n
-            fa = physical_fields(thor, a, wl.ncol, wl.nv, east, north)
-            fb = physical_fields(thor, b, wl.ncol, wl.nv, east, north)
-            rows[str(n)] = field_error_row(fa, fb)
-        m_a, m_b = thor.thor_diag(a)["mass"], thor.thor_diag(b)["mass"]
+            fb = physical_fields(thor, ref, wl.ncol, wl.nv, east, north)
+            for k, a in runs.items():
+                rows[k][str(n)] = field_error_row(physical_fields(thor, a, wl.ncol, wl.nv, east, north), fb)
+        mass["fp64"] = abs(thor.thor_diag(ref)["mass"] - m0) / m0
+        for k, a in runs.items():
+            mass[k] = abs(thor.thor_diag(a)["mass"] - m0) / m0
     finally:
-        thor.thor_state_destroy(a)
-        thor.thor_state_destroy(b)
-    return {"against": "the float64 path from the same start (which matches the float64 oracle to 1e-10)",
-            "large_steps": rows, "mass_rel_diff_at_end": abs(m_a - m_b) / m_b}
+        thor.thor_state_destroy(ref)
+        for a in runs.values():
+            thor.thor_state_destroy(a)
+    out = {"against": "the float64 path from the same start (which matches the float64 oracle to 1e-10)",
+           "large_steps": rows.get("plain", {}), "mass_drift_at_end": mass,
+           "fp64_rounded_start_large_steps": rows["fp64_rounded_start"]}
+    if "compensated" in rows:
+        out["compensated_large_steps"] = rows["compensated"]
+    return out
 
 
 def fp64_flops(kind):
@@ -535,6 +558,15 @@ def run_thor(args):
              "unit": "GB/s", "peak": peak}
     whole["frac"] = whole["achieved"] / peak
 
+    # ---- the same steps with the compensated state (THOR_TUNE_COMPENSATED)
+    thor.thor_tune(st, thor.THOR_TUNE_COMPENSATED, 1)
+    for _ in range(2):
+        thor.thor_step(st, 1, wl.n_small, wl.dt)
+    ms_cmp = max_over_ranks(timed(st, wl, args.steps))
+    thor.thor_tune(st, thor.THOR_TUNE_COMPENSATED, 0)
+    compensated = {"value": whole_job_rate(world, cells * sn * args.steps, ms_cmp / 1e3), "unit": METRIC,
+                   "ms_per_step": ms_cmp / args.steps, "steps": args.steps}
+
     # ---- end to end through the C ABI with pinned host buffers
     shapes = {thor.THOR_FIELD_RHO: (wl.ncol, wl.nv), thor.THOR_FIELD_MOM: (wl.ncol, wl.nv, 3),
               thor.THOR_FIELD_W: (wl.ncol, wl.nv + 1), thor.THOR_FIELD_RHOTHETA: (wl.ncol, wl.nv)}
@@ -571,9 +603,14 @@ def run_thor(args):
     fp64 = {"value": value64, "unit": METRIC, "steps": k64, "ms_per_step": ms64 / k64,
             "model_days_per_hour": world * k64 * wl.dt / 86400.0 / (ms64 / 1e3 / 3600.0),
             "bound": {"hbm_ms": 1e3 * t_hbm64, "hbm_frac": t_hbm64 / (ms64 / k64 / 1e3)}}
-    if flops64:
-        t_alu = flops64 / 1.25e12
-        fp64["bound"].update({"fp64_ops_per_step": flops64, "fp64_peak_tflops": 1.25, "fp64_peak_kind": "nominal",
+    inst64 = fp64_flops("fp64_instructions_per_large_step") if flops64 else None
+    if flops64 and inst64:
+        # each float64 add, multiply or FMA is one issue of the float64 pipe:
+        # 0.625 T/s at the nominal 1.25 TFLOP/s
+        t_alu = inst64 / 0.625e12
+        fp64["bound"].update({"fp64_ops_per_step": flops64, "fp64_instructions_per_step": inst64,
+                              "fp64_peak_tflops": 1.25, "fp64_peak_kind": "nominal",
+                              "achieved_tflops": flops64 / (ms64 / k64 / 1e3) / 1e12,
                               "fp64_ms": 1e3 * t_alu, "fp64_frac": t_alu / (ms64 / k64 / 1e3),
                               "bound": "fp64" if t_alu > t_hbm64 else "hbm"})
 
@@ -621,6 +658,7 @@ def run_thor(args):
         "precision": "mixed: f32 fields and stencils, f64 vertical solve and reductions",
         "model_days_per_hour": days_per_hour,
         "error": err,
+        "compensated": compensated,
         "fp64": fp64,
         "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                 "steps": e2e_steps},

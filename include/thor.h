@@ -258,7 +258,7 @@ int thor_launch_count(const thor_state* state, long long* count);
  * after the step (restore a checkpoint with thor_state_set). Default 0. */
 enum { THOR_TUNE_KCHUNK = 0, THOR_TUNE_GRAPH = 1, THOR_TUNE_CHECK_FINITE = 2, THOR_TUNE_BLOCK = 3,
        THOR_TUNE_SOLVE_TMA = 4, THOR_TUNE_ENERGY_FIXER = 5, THOR_TUNE_BUDGET = 6,
-       THOR_TUNE_RK_STAGES = 7 };
+       THOR_TUNE_RK_STAGES = 7, THOR_TUNE_COMPENSATED = 8 };
 int thor_tune(thor_state* state, int knob, int value);
 
 /* Energy and angular-momentum budget of the large steps recorded since
@@ -334,7 +334,20 @@ int thor_zonal_read_w(thor_state* state, int nlat, double* out, size_t n, long l
  * result X^(s+1) = X^t + X* in the state and runs neither the energy fixer
  * nor the physics; with 1 a large step is one slow-term evaluation and one
  * small step of dt/3 from X^t. For tests that check the first small step on
- * its own; THOR_EINVAL outside 1..3. */
+ * its own; THOR_EINVAL outside 1..3.
+ * THOR_TUNE_COMPENSATED (THOR_MIXED states): 1 keeps every prognostic field
+ * of the state (and of the RK stage state) as a float pair hi + lo, |lo| at
+ * most half a unit in the last place of hi, and adds each stage's
+ * accumulated small-step perturbations (Eqs. dens2, mom2, momr2, pt2), the
+ * physics increments (Eqs. im_eq_v, im_eq_t) and the energy fixer's to the
+ * pair with an error-free sum (TwoSum), so that the float32 storage does
+ * not round the state at every stage end; thor_state_get / _set, thor_diag
+ * and checkpoints (then twice the size) use the full pairs. The tendencies
+ * are still evaluated from the float parts. The first use allocates the
+ * low parts (12 planes), zeroed; 0 frees them and rounds the state to its
+ * float parts. Synchronises the state's stream. Compensated states cannot
+ * join an ensemble (thor_ensemble_step returns THOR_EINVAL); THOR_EINVAL
+ * for THOR_FP64 states. Default 0. */
 
 /* Launch-shape autotuner (an extension; the paper fixes no launch shapes).
  * Times `steps` large steps of (n_small, dt) for every levels-per-thread

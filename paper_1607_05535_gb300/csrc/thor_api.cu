@@ -32,53 +32,60 @@ uint64_t splitmix64(uint64_t x) {
 
 // ------------------------------------------------------------ transfers
 
-// canonical float64 [ncol][nv(+1)][ncomp] -> device planes, reference removed
+// canonical float64 [ncol][nv(+1)][ncomp] -> device planes, reference removed;
+// with low planes l0.. (a compensated state) the value is split into its
+// storage-type part and the remainder
 template <typename R>
 __global__ void k_from_canonical(const double* src, int ncol, int colp, int nlev, int ncomp,
-                                 const double* ref, R* d0, R* d1, R* d2, int zero_ends) {
+                                 const double* ref, R* d0, R* d1, R* d2, R* l0, R* l1, R* l2, int zero_ends) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   int k = blockIdx.y;
   if (c >= ncol) return;
   R* dst[3] = {d0, d1, d2};
+  R* low[3] = {l0, l1, l2};
   for (int j = 0; j < ncomp; ++j) {
     double v = src[((size_t)c * nlev + k) * ncomp + j];
     if (ref) v -= ref[k];
     if (zero_ends && (k == 0 || k == nlev - 1)) v = 0.0;
-    dst[j][(size_t)k * colp + c] = (R)v;
+    const R hi = (R)v;
+    dst[j][(size_t)k * colp + c] = hi;
+    if (low[j]) low[j][(size_t)k * colp + c] = (R)(v - (double)hi);
   }
 }
 
-// device planes -> canonical float64; field selects the reconstruction
+// device planes -> canonical float64; field selects the reconstruction; XL:
+// the low parts of a compensated state (null: none)
 template <typename R>
-__global__ void k_to_canonical(double* dst, Geo<R> G, Vert V, Phys ph, Xf<R> X, int field) {
+__global__ void k_to_canonical(double* dst, Geo<R> G, Vert V, Phys ph, Xf<R> X, Xf<R> XL, int field) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   int k = blockIdx.y;
   if (c >= G.ncol) return;
   const int S = G.colp, nv = G.nv;
   size_t i = (size_t)k * S + c;
+  auto val = [&](const R* hi, const R* lo) { return lo ? (double)hi[i] + (double)lo[i] : (double)hi[i]; };
   switch (field) {
     case THOR_FIELD_RHO:
-      dst[(size_t)c * nv + k] = V.rhob[k] + (double)X.rho[i];
+      dst[(size_t)c * nv + k] = V.rhob[k] + val(X.rho, XL.rho);
       break;
     case THOR_FIELD_MOM:
-      dst[((size_t)c * nv + k) * 3 + 0] = (double)X.mx[i];
-      dst[((size_t)c * nv + k) * 3 + 1] = (double)X.my[i];
-      dst[((size_t)c * nv + k) * 3 + 2] = (double)X.mz[i];
+      dst[((size_t)c * nv + k) * 3 + 0] = val(X.mx, XL.mx);
+      dst[((size_t)c * nv + k) * 3 + 1] = val(X.my, XL.my);
+      dst[((size_t)c * nv + k) * 3 + 2] = val(X.mz, XL.mz);
       break;
     case THOR_FIELD_W:
-      dst[(size_t)c * (nv + 1) + k] = (double)X.w[i];
+      dst[(size_t)c * (nv + 1) + k] = val(X.w, XL.w);
       break;
     case THOR_FIELD_RHOTHETA:
-      dst[(size_t)c * nv + k] = V.thb[k] + (double)X.th[i];
+      dst[(size_t)c * nv + k] = V.thb[k] + val(X.th, XL.th);
       break;
     case THOR_FIELD_PRESSURE:
     case THOR_FIELD_TEMPERATURE: {
-      double thp = (double)X.th[i];
+      double thp = val(X.th, XL.th);
       double p = V.pb[k] + V.pb[k] * expm1(ph.gamma * log1p(thp / V.thb[k]));
       if (field == THOR_FIELD_PRESSURE) {
         dst[(size_t)c * nv + k] = p;
       } else {
-        double rho = V.rhob[k] + (double)X.rho[i];
+        double rho = V.rhob[k] + val(X.rho, XL.rho);
         dst[(size_t)c * nv + k] = p / (rho * ph.Rd);
       }
       break;
@@ -313,6 +320,7 @@ Impl<R>::~Impl() {
   if (ev_join) cudaEventDestroy(ev_join);
   if (ev_join0) cudaEventDestroy(ev_join0);
   if (arena) cudaFree(arena);
+  if (lo_buf) cudaFree(lo_buf);
 }
 
 // the element count of a field in the canonical layout of thor_state_get
@@ -328,7 +336,7 @@ int Impl<R>::get(int field, double* host, size_t n) {
   if (field < 0 || field > THOR_FIELD_TEMPERATURE || n != need || !host) return THOR_EINVAL;
   int nlev = field == THOR_FIELD_W ? nv + 1 : nv;
   dim3 grid((G.ncol + 127) / 128, nlev);
-  k_to_canonical<R><<<grid, 128, 0, stream>>>(staging, G, V, ph, Xt, field);
+  k_to_canonical<R><<<grid, 128, 0, stream>>>(staging, G, V, ph, Xt, XtL, field);
   ++launches;
   if (cudaMemcpyAsync(host, staging, need * sizeof(double), cudaMemcpyDeviceToHost, stream)) return THOR_ECUDA;
   return cudaStreamSynchronize(stream) == cudaSuccess ? THOR_OK : THOR_ECUDA;
@@ -361,7 +369,7 @@ int Impl<R>::get_all(double* const host[4]) {
     if (!host[f]) return THOR_EINVAL;
     const size_t n = field_count(f, G.ncol, G.nv);
     dim3 grid((G.ncol + 127) / 128, f == THOR_FIELD_W ? G.nv + 1 : G.nv);
-    k_to_canonical<R><<<grid, 128, 0, stream>>>(staging + off, G, V, ph, Xt, f);
+    k_to_canonical<R><<<grid, 128, 0, stream>>>(staging + off, G, V, ph, Xt, XtL, f);
     ++launches;
     if (cudaMemcpyAsync(host[f], staging + off, n * sizeof(double), cudaMemcpyDeviceToHost, stream))
       return THOR_ECUDA;
@@ -375,25 +383,28 @@ int Impl<R>::set_async(int field, const double* host, double* buf) {
   const int nv = G.nv;
   int nlev = nv, ncomp = 1, zero_ends = 0;
   const double* ref = nullptr;
-  R *d0 = nullptr, *d1 = nullptr, *d2 = nullptr;
+  R *d0 = nullptr, *d1 = nullptr, *d2 = nullptr, *l0 = nullptr, *l1 = nullptr, *l2 = nullptr;
   switch (field) {
-    case THOR_FIELD_RHO: ref = V.rhob; d0 = Xt.rho; break;
-    case THOR_FIELD_MOM: ncomp = 3; d0 = Xt.mx; d1 = Xt.my; d2 = Xt.mz; break;
-    case THOR_FIELD_W: nlev = nv + 1; zero_ends = 1; d0 = Xt.w; break;
-    case THOR_FIELD_RHOTHETA: ref = V.thb; d0 = Xt.th; break;
+    case THOR_FIELD_RHO: ref = V.rhob; d0 = Xt.rho; l0 = XtL.rho; break;
+    case THOR_FIELD_MOM:
+      ncomp = 3; d0 = Xt.mx; d1 = Xt.my; d2 = Xt.mz; l0 = XtL.mx; l1 = XtL.my; l2 = XtL.mz;
+      break;
+    case THOR_FIELD_W: nlev = nv + 1; zero_ends = 1; d0 = Xt.w; l0 = XtL.w; break;
+    case THOR_FIELD_RHOTHETA: ref = V.thb; d0 = Xt.th; l0 = XtL.th; break;
     default: return THOR_EINVAL;
   }
   const size_t n = (size_t)G.ncol * nlev * ncomp;
   if (cudaMemcpyAsync(buf, host, n * sizeof(double), cudaMemcpyHostToDevice, stream)) return THOR_ECUDA;
   dim3 grid((G.ncol + 127) / 128, nlev);
-  k_from_canonical<R><<<grid, 128, 0, stream>>>(buf, G.ncol, G.colp, nlev, ncomp, ref, d0, d1, d2, zero_ends);
+  k_from_canonical<R><<<grid, 128, 0, stream>>>(buf, G.ncol, G.colp, nlev, ncomp, ref, d0, d1, d2, l0, l1, l2,
+                                                zero_ends);
   ++launches;
   return cudaGetLastError() == cudaSuccess ? THOR_OK : THOR_ECUDA;
 }
 
 template <typename R>
 int Impl<R>::diag(double* out8, long long* nonfinite) {
-  k_diag_partial<R><<<kDiagBlocks, kDiagThreads, 0, stream>>>(G, V, ph, Xt, red);
+  k_diag_partial<R><<<kDiagBlocks, kDiagThreads, 0, stream>>>(G, V, ph, Xt, XtL, red);
   k_diag_final<<<1, 256, 0, stream>>>(red, kDiagBlocks);
   launches += 2;
   double h[8];
@@ -407,6 +418,44 @@ int Impl<R>::diag(double* out8, long long* nonfinite) {
   return THOR_OK;
 }
 
+// the low parts of a compensated float state: on allocates them zeroed (the
+// state's value is unchanged), off frees them (the value rounds to the float
+// parts); float64 states need none
+template <typename R>
+int Impl<R>::set_compensated(int on) {
+  if (sizeof(R) == sizeof(double)) return on ? THOR_EINVAL : THOR_OK;
+  if ((on != 0) == (compensated != 0)) return THOR_OK;
+  if (cudaStreamSynchronize(stream)) return THOR_ECUDA;
+  drop_graph();
+  if (!on) {
+    cudaFree(lo_buf);
+    lo_buf = nullptr;
+    XtL = Xf<R>{};
+    XstL = Xf<R>{};
+    compensated = 0;
+    return THOR_OK;
+  }
+  const size_t S = G.colp, C = S * G.nv, F = S * (G.nv + 1);
+  const size_t per = 5 * C + F;                 // rho, M (3), rho theta, W
+  if (cudaMalloc(&lo_buf, 2 * per * sizeof(R))) {
+    lo_buf = nullptr;
+    return THOR_ENOMEM;
+  }
+  if (cudaMemsetAsync(lo_buf, 0, 2 * per * sizeof(R), stream) || cudaStreamSynchronize(stream)) {
+    cudaFree(lo_buf);
+    lo_buf = nullptr;
+    return THOR_ECUDA;
+  }
+  R* b = static_cast<R*>(lo_buf);
+  auto lay = [&](Xf<R>& x, R* p) {
+    x.rho = p; x.mx = p + C; x.my = p + 2 * C; x.mz = p + 3 * C; x.th = p + 4 * C; x.w = p + 5 * C;
+  };
+  lay(XtL, b);
+  lay(XstL, b + per);
+  compensated = 1;
+  return THOR_OK;
+}
+
 template Impl<double>::~Impl();
 template Impl<float>::~Impl();
 template int Impl<double>::get(int, double*, size_t);
@@ -414,6 +463,8 @@ template int Impl<float>::get(int, double*, size_t);
 template int Impl<double>::set(int, const double*, size_t);
 template int Impl<float>::set(int, const double*, size_t);
 template int Impl<double>::diag(double*, long long*);
+template int Impl<double>::set_compensated(int);
+template int Impl<float>::set_compensated(int);
 template int Impl<float>::diag(double*, long long*);
 
 namespace {
@@ -890,6 +941,7 @@ int thor_tune(thor_state* s, int knob, int value) {
     s->impl->solve_tma = value != 0;
     return THOR_OK;
   }
+  if (knob == THOR_TUNE_COMPENSATED) return s->impl->set_compensated(value != 0);
   if (knob == THOR_TUNE_RK_STAGES) {
     if (value < 1 || value > 3) return THOR_EINVAL;
     s->impl->rk_stages = value;

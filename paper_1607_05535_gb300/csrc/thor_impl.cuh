@@ -93,6 +93,11 @@ struct ImplBase {
   virtual int get_all(double* const host[4]) = 0;
   virtual int set_all(const double* const host[4]) = 0;
   virtual void set_graph(bool on) = 0;
+  // compensated state (THOR_TUNE_COMPENSATED): on = 1 adds zeroed low parts
+  // to the prognostic fields of a float state, on = 0 drops them (the state
+  // rounds to its float parts); -1 for a float64 state
+  virtual int set_compensated(int on) = 0;
+  int compensated = 0;
   long long launches = 0;
   int kchunk = 2;                      // levels per thread in the stencil kernels
   int block = kBlock;                  // threads (columns) per block of the stencil kernels
@@ -172,6 +177,11 @@ struct Impl : ImplBase {
   Slow<R> SL;
   Pert<R> P;
   Fac<R> F;
+  // low parts of X^t and of the stage state when compensated (null pointers
+  // otherwise): the value of a field is hi + lo, with |lo| at most half a
+  // unit in the last place of hi
+  Xf<R> XtL{}, XstL{};
+  void* lo_buf = nullptr;
   int hyper = 1, divdamp = 1, forcing = 0;
   int shallow = 0;                 // shallow-atmosphere approximation (thor_init.shallow)
   double diff_D = 0, dbar4 = 0, hj_dT = 300.0;
@@ -194,7 +204,8 @@ struct Impl : ImplBase {
   // the same; used on a non-default stream when no profiling is recorded
   cudaGraphExec_t graph_exec = nullptr;
   double graph_dt = 0;
-  int graph_n = 0, graph_kc = 0, graph_bs = 0, graph_tma = -1, graph_energy = -1, graph_stages = -1;
+  int graph_n = 0, graph_kc = 0, graph_bs = 0, graph_tma = -1, graph_energy = -1, graph_stages = -1,
+      graph_cmp = -1;
   std::unique_ptr<SolveMaps> smaps;   // null where the staged solve does not apply
   // second stream for the kernels of a stage that run beside others, forked
   // from and joined to the state's stream by events (null: everything on the
@@ -202,7 +213,8 @@ struct Impl : ImplBase {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join0 = nullptr;
   int build_solve_maps();
-  cudaError_t launch_solve_tma(dim3 grid, int stage, const Xf<R>& Xo, double dtau, int want_div, int last);
+  cudaError_t launch_solve_tma(dim3 grid, int stage, const Xf<R>& Xo, const Xf<R>& XsL, const Xf<R>& XoL,
+                               double dtau, int want_div, int last);
   long long graph_launches = 0;
   void drop_graph() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -212,7 +224,8 @@ struct Impl : ImplBase {
   int step(int n_large, int n_small, double dt) override {
     if (use_graph && stream != nullptr && !prof_on && n_large > 0) {
       if (!graph_exec || graph_dt != dt || graph_n != n_small || graph_kc != kchunk || graph_bs != block ||
-          graph_tma != solve_tma || graph_energy != energy_key() || graph_stages != rk_stages) {
+          graph_tma != solve_tma || graph_energy != energy_key() || graph_stages != rk_stages ||
+          graph_cmp != compensated) {
         drop_graph();
         cudaGraph_t g = nullptr;
         long long before = launches;
@@ -239,6 +252,7 @@ struct Impl : ImplBase {
         graph_tma = solve_tma;
         graph_energy = energy_key();
         graph_stages = rk_stages;
+        graph_cmp = compensated;
       }
       for (int i = 0; i < n_large; ++i) {
         if (cudaGraphLaunch(graph_exec, stream)) return -3;
@@ -258,15 +272,19 @@ struct Impl : ImplBase {
   int get_all(double* const host[4]) override;
   int set_all(const double* const host[4]) override;
   int set_async(int field, const double* host, double* buf);   // queue one field, no synchronisation
-  // rho, M (3), rho theta: nv planes each; W: nv + 1 planes; buf in device or
-  // host memory (unified addressing)
-  size_t state_bytes() const override { return (size_t)(6 * G.nv + 1) * G.colp * sizeof(R); }
+  int set_compensated(int on) override;
+  // rho, M (3), rho theta: nv planes each; W: nv + 1 planes (and the same
+  // again for the low parts of a compensated state); buf in device or host
+  // memory (unified addressing)
+  size_t state_bytes() const override {
+    return (size_t)(6 * G.nv + 1) * G.colp * sizeof(R) * (compensated ? 2 : 1);
+  }
   int copy_state(char* buf, bool save) {
     const size_t plane = (size_t)G.colp * sizeof(R), c = G.nv * plane;
-    R* f[6] = {Xt.rho, Xt.mx, Xt.my, Xt.mz, Xt.th, Xt.w};
+    R* f[12] = {Xt.rho, Xt.mx, Xt.my, Xt.mz, Xt.th, Xt.w, XtL.rho, XtL.mx, XtL.my, XtL.mz, XtL.th, XtL.w};
     size_t off = 0;
-    for (int i = 0; i < 6; ++i) {
-      const size_t bytes = i == 5 ? c + plane : c;
+    for (int i = 0; i < (compensated ? 12 : 6); ++i) {
+      const size_t bytes = i % 6 == 5 ? c + plane : c;
       cudaError_t e = save ? cudaMemcpyAsync(buf + off, f[i], bytes, cudaMemcpyDefault, stream)
                            : cudaMemcpyAsync(f[i], buf + off, bytes, cudaMemcpyDefault, stream);
       if (e) return -3;

@@ -127,6 +127,28 @@ template <typename R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return sqrtf(x); }
 
+// Knuth's TwoSum: s = fl(a + b) and the rounding error e, so that s + e equals
+// a + b exactly (no multiplication, so no contraction into an FMA can touch
+// it). The compensated state keeps every prognostic field as such a pair.
+template <typename R>
+__device__ __forceinline__ void two_sum(R a, R b, R& s, R& e) {
+  s = a + b;
+  const R bv = s - a;
+  e = (a - (s - bv)) + (b - bv);
+}
+
+// Compensated state update hi/lo += d at element i: the new value
+// hi + (lo + d) is split into its float and the float remainder, so the
+// state's own rounding is not repeated at every update (only d + lo rounds).
+// out_hi / out_lo may be hi / lo themselves (each element is read first).
+template <typename R>
+__device__ __forceinline__ void comp_add(const R* hi, const R* lo, R* out_hi, R* out_lo, size_t i, R d) {
+  R s, e;
+  two_sum(hi[i], lo[i] + d, s, e);
+  out_hi[i] = s;
+  out_lo[i] = e;
+}
+
 // Eq. pressure in deviation form: EOS(Th_bar (1 + x)) - EOS(Th_bar) with
 // x = th'/Th_bar, i.e. p_bar ((1 + x)^gamma - 1)
 template <typename R>

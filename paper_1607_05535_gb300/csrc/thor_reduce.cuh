@@ -26,8 +26,9 @@ struct Kahan {
 };
 
 // partial sums per block: mass, energy, aam, sum V T, sum V, max vh, max w, nonfinite
+// XL: the low parts of a compensated state (null pointers: none)
 template <typename R>
-__global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Geo<R> G, Vert V, Phys ph, Xf<R> X,
+__global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Geo<R> G, Vert V, Phys ph, Xf<R> X, Xf<R> XL,
                                                                double* part) {
   const int S = G.colp, nv = G.nv;
   const long long ncell = (long long)G.ncol * nv;
@@ -38,14 +39,20 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Geo<R> G, Vert V,
        q += (long long)gridDim.x * blockDim.x) {
     int k = (int)(q / G.ncol), c = (int)(q % G.ncol);
     size_t i = (size_t)k * S + c;
+    const bool cmp = XL.rho != nullptr;
+    auto val = [&](const R* hi, const R* lo, size_t j) {
+      return cmp ? (double)hi[j] + (double)lo[j] : (double)hi[j];
+    };
     double rx = G.rhat[c], ry = G.rhat[S + c], rz = G.rhat[2 * S + c];
-    double rho = V.rhob[k] + (double)X.rho[i];
-    double th = V.thb[k] + (double)X.th[i];
-    double p = V.pb[k] + V.pb[k] * expm1(ph.gamma * log1p((double)X.th[i] / V.thb[k]));
+    const double rhop = val(X.rho, XL.rho, i), thp = val(X.th, XL.th, i);
+    double rho = V.rhob[k] + rhop;
+    double th = V.thb[k] + thp;
+    double p = V.pb[k] + V.pb[k] * expm1(ph.gamma * log1p(thp / V.thb[k]));
     double Temp = p / (rho * ph.Rd);
-    double wlo = X.w[i], whi = X.w[i + S];
+    double wlo = val(X.w, XL.w, i), whi = val(X.w, XL.w, i + S);
     double wc = V.clo[k] * wlo + V.chi[k] * whi;
-    double mx = (double)X.mx[i] + wc * rx, my = (double)X.my[i] + wc * ry, mz = (double)X.mz[i] + wc * rz;
+    const double mhx = val(X.mx, XL.mx, i), mhy = val(X.my, XL.my, i), mhz = val(X.mz, XL.mz, i);
+    double mx = mhx + wc * rx, my = mhy + wc * ry, mz = mhz + wc * rz;
     double vol = G.area[c] * V.rc[k] * V.rc[k] * V.dz[k];
     mass.add(vol * rho);
     en.add(vol * (rho * ph.cv * Temp + 0.5 * (mx * mx + my * my + mz * mz) / rho + rho * ph.g * V.zc[k]));
@@ -53,10 +60,10 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Geo<R> G, Vert V,
     aam.add(vol * (r * (rx * my - ry * mx) + rho * ph.omega * r * r * (rx * rx + ry * ry)));
     vt.add(vol * Temp);
     vs.add(vol);
-    double hx = (double)X.mx[i] / rho, hy = (double)X.my[i] / rho, hz = (double)X.mz[i] / rho;
+    double hx = mhx / rho, hy = mhy / rho, hz = mhz / rho;
     mvh = fmax(mvh, sqrt(hx * hx + hy * hy + hz * hz));
     if (k >= 1) {
-      double rif = V.wlo[k] * (V.rhob[k - 1] + (double)X.rho[i - S]) + V.whi[k] * rho;
+      double rif = V.wlo[k] * (V.rhob[k - 1] + val(X.rho, XL.rho, i - S)) + V.whi[k] * rho;
       mw = fmax(mw, fabs(wlo / rif));
     }
     double vals[6] = {(double)X.rho[i], (double)X.mx[i], (double)X.my[i], (double)X.mz[i], th, (double)X.w[i]};

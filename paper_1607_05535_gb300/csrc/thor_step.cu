@@ -309,32 +309,42 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
 // runs this beside the slow terms): Phi* = Phi^t - Phi^(s), p* from the
 // nonlinear Eq. theta_to_p; all zero in the first stage, where Phi^(s) =
 // Phi^t and p^(s) = EOS(Th^t). M* goes into the packed plane with theta of
-// the stage state beside it (the column fluxes gather both).
+// the stage state beside it (the column fluxes gather both). XtL, XL: the low
+// parts of a compensated state (null pointers: none), so that
+// Phi^t - Phi^(s) is taken from the full pairs.
 template <typename R>
 __device__ __forceinline__ void d_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Pert<R> P,
-                                             int zero, int kchunk, int bx, int by) {
+                                             Xf<R> XtL, Xf<R> XL, int zero, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
   const R gamma = pc<R>(ph.gamma, ph.gamma_f);
+  const bool cmp = XtL.rho != nullptr;
   int k0 = by * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int i = k * S + c;
+    // Phi^t - Phi^(s) of one field
+    auto dif = [&](const R* a, const R* b, const R* al, const R* bl) {
+      R d = ld(a + i) - ld(b + i);
+      if (cmp) d += ld(al + i) - ld(bl + i);
+      return d;
+    };
     if (k < G.nv) {
       if (zero) {
         P.rho[i] = P.th[i] = P.p[i] = R(0);
         st4(P.m4, i, R(0), R(0), R(0), ld(T.theta + (i)));
       } else {
-        P.rho[i] = ld(Xt.rho + (i)) - ld(X.rho + (i));
-        st4(P.m4, i, ld(Xt.mx + (i)) - ld(X.mx + (i)), ld(Xt.my + (i)) - ld(X.my + (i)),
-            ld(Xt.mz + (i)) - ld(X.mz + (i)), ld(T.theta + (i)));
-        P.th[i] = ld(Xt.th + (i)) - ld(X.th + (i));
-        R ppt = eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), ld(Xt.th + (i)), gamma);
+        P.rho[i] = dif(Xt.rho, X.rho, XtL.rho, XL.rho);
+        st4(P.m4, i, dif(Xt.mx, X.mx, XtL.mx, XL.mx), dif(Xt.my, X.my, XtL.my, XL.my),
+            dif(Xt.mz, X.mz, XtL.mz, XL.mz), ld(T.theta + (i)));
+        P.th[i] = dif(Xt.th, X.th, XtL.th, XL.th);
+        const R tht = cmp ? ld(Xt.th + (i)) + ld(XtL.th + (i)) : ld(Xt.th + (i));
+        R ppt = eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), tht, gamma);
         P.p[i] = ppt - ld(T.pp + (i));
       }
     }
-    P.w[i] = zero ? R(0) : ld(Xt.w + (i)) - ld(X.w + (i));
+    P.w[i] = zero ? R(0) : dif(Xt.w, X.w, XtL.w, XL.w);
   }
 }
 
@@ -366,11 +376,12 @@ __device__ __forceinline__ void d_ss_grad(Geo<R> G, VR<R> U, Work<R> T, const R*
 
 // Eq. mom2 with the divergence damping: M* <- proj(M* + dtau(-grad p* + DD + S_M));
 // in the last small step of a stage also M^(s+1) = M^(s) + M* into Xo (which
-// may be Xs itself: each cell reads its own Xs value before writing it)
+// may be Xs itself: each cell reads its own Xs value before writing it), with
+// the low parts XsL -> XoL of a compensated state (null: none)
 template <typename R>
 __device__ __forceinline__ void d_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, R Kd,
-                                            int divdamp, Xf<R> Xs, Xf<R> Xo, int last, int kchunk, int bx,
-                                            int by) {
+                                            int divdamp, Xf<R> Xs, Xf<R> Xo, Xf<R> XsL, Xf<R> XoL, int last,
+                                            int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -413,9 +424,15 @@ __device__ __forceinline__ void d_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> 
     project(rx, ry, rz, mx, my, mz);
     st4(P.m4, i, mx, my, mz, m.w);
     if (last) {          // end of the stage: M^(s+1) = M^(s) + M*
-      Xo.mx[i] = ld(Xs.mx + (i)) + mx;
-      Xo.my[i] = ld(Xs.my + (i)) + my;
-      Xo.mz[i] = ld(Xs.mz + (i)) + mz;
+      if (XoL.mx) {
+        comp_add<R>(Xs.mx, XsL.mx, Xo.mx, XoL.mx, i, mx);
+        comp_add<R>(Xs.my, XsL.my, Xo.my, XoL.my, i, my);
+        comp_add<R>(Xs.mz, XsL.mz, Xo.mz, XoL.mz, i, mz);
+      } else {
+        Xo.mx[i] = ld(Xs.mx + (i)) + mx;
+        Xo.my[i] = ld(Xs.my + (i)) + my;
+        Xo.mz[i] = ld(Xs.mz + (i)) + mz;
+      }
     }
   }
 }
@@ -553,9 +570,20 @@ __device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> 
 // Phi* for rho, rho theta and W (the momentum in k_ss_mom), into Xo, which may
 // be Xs itself (each cell reads its own Xs values before writing them). The
 // lid and surface interfaces keep W^(s) + W*, as the interior ones.
+// XsL, XoL: the low parts of a compensated state (null: none), updated
+// with comp_add so that the stage end does not round the state.
 template <typename R>
-__device__ __forceinline__ void stage_end_cell(const Xf<R>& Xs, const Xf<R>& Xo, const Pert<R>& P, R rho_new,
-                                               R th_new, R w_new, int k, int i, int S, int nv) {
+__device__ __forceinline__ void stage_end_cell(const Xf<R>& Xs, const Xf<R>& Xo, const Xf<R>& XsL, const Xf<R>& XoL,
+                                               const Pert<R>& P, R rho_new, R th_new, R w_new, int k, int i, int S,
+                                               int nv) {
+  if (XoL.rho) {
+    comp_add<R>(Xs.rho, XsL.rho, Xo.rho, XoL.rho, i, rho_new);
+    comp_add<R>(Xs.th, XsL.th, Xo.th, XoL.th, i, th_new);
+    if (k >= 1) comp_add<R>(Xs.w, XsL.w, Xo.w, XoL.w, i, w_new);
+    if (k == 0) comp_add<R>(Xs.w, XsL.w, Xo.w, XoL.w, i, ld(P.w + i));
+    if (k == nv - 1) comp_add<R>(Xs.w, XsL.w, Xo.w, XoL.w, i + S, ld(P.w + (i + S)));
+    return;
+  }
   Xo.rho[i] = ld(Xs.rho + i) + rho_new;
   Xo.th[i] = ld(Xs.th + i) + th_new;
   if (k >= 1) Xo.w[i] = ld(Xs.w + i) + w_new;
@@ -575,7 +603,8 @@ __device__ __forceinline__ void stage_end_cell(const Xf<R>& Xs, const Xf<R>& Xo,
 template <typename R>
 __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs, Slow<R> SL,
                                             Pert<R> P, Work<R> T, Fac<R> F, double dtau,
-                                            int want_div, Xf<R> Xo, int last, int bx, int by) {
+                                            int want_div, Xf<R> Xo, Xf<R> XsL, Xf<R> XoL, int last, int bx,
+                                            int by) {
   extern __shared__ double sm[];
   const int nv = G.nv, S = G.colp, N = nv - 1;
   const int tx = threadIdx.x & 31, half = threadIdx.x >> 5;
@@ -671,7 +700,7 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
       // 3-D divergence of the new total momentum, for the next small step's
       // divergence damping: D^(s) + div_h M* (from k_ss_flux) + div_v W*
       if (want_div) T.dd[i] = ld(SL.dsc + i) + ld(T.dhm + i) + (eh * wh - el * wl);
-      if (last) stage_end_cell(Xs, Xo, P, rho_new, th_new, wl, k, i, S, nv);
+      if (last) stage_end_cell(Xs, Xo, XsL, XoL, P, rho_new, th_new, wl, k, i, S, nv);
     }
   }
 }
@@ -695,9 +724,13 @@ __device__ __forceinline__ void d_surface_p(Geo<R> G, VR<R> U, Phys ph, Xf<R> X,
   T.psurf[c] = p0 * rexp<R>(pc<R>(ph.g, ph.g_f) * ld(U.zc + (0)) / (Rd * T0));
 }
 
+// XL: the low parts of a compensated state (null: none); there the friction
+// and the relaxation enter as increments of the state's pairs, the same
+// update written as M (1/(1 + K_v dt) - 1) and rho theta at fixed rho
+// scaled by (T_new / T)^(1/gamma).
 template <typename R>
-__device__ __forceinline__ void d_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int forcing, double dt,
-                                          double hj_dT, int kchunk, int bx, int by) {
+__device__ __forceinline__ void d_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Xf<R> XL, Work<R> T, int forcing,
+                                          double dt, double hj_dT, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -707,11 +740,13 @@ __device__ __forceinline__ void d_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, W
   const R ps = ld(T.psurf + (c));
   const R rdt = (R)dt;
   const int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
+  const bool cmp = XL.rho != nullptr;
   for (int k = k0; k < k1; ++k) {
     const int i = k * S + c;
-    R rhop = ld(X.rho + (i));
+    R rhop = cmp ? ld(X.rho + (i)) + ld(XL.rho + (i)) : ld(X.rho + (i));
+    const R thp = cmp ? ld(X.th + (i)) + ld(XL.th + (i)) : ld(X.th + (i));
     R rho = ld(U.rhob + (k)) + rhop;
-    R p = ld(U.pb + (k)) + eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), ld(X.th + (i)), gamma);
+    R p = ld(U.pb + (k)) + eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), thp, gamma);
     R Temp = p / (rho * Rd);
     R sigma = p / ps;
     R Kv, KT, Teq;
@@ -742,6 +777,16 @@ __device__ __forceinline__ void d_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, W
       Kv = 0;
       KT = R(1) / R(1.5e5);
       Teq = Tv + bt * (R)hj_dT * clcl;
+    }
+    if (cmp) {
+      const R dfr = -Kv * rdt / (R(1) + Kv * rdt);      // 1 / (1 + K_v dt) - 1
+      comp_add<R>(X.mx, XL.mx, X.mx, XL.mx, i, (ld(X.mx + i) + ld(XL.mx + i)) * dfr);
+      comp_add<R>(X.my, XL.my, X.my, XL.my, i, (ld(X.my + i) + ld(XL.my + i)) * dfr);
+      comp_add<R>(X.mz, XL.mz, X.mz, XL.mz, i, (ld(X.mz + i) + ld(XL.mz + i)) * dfr);
+      const R dT = KT * rdt * (Teq - Temp) / (R(1) + KT * rdt);
+      const R th = ld(U.thb + (k)) + thp;
+      comp_add<R>(X.th, XL.th, X.th, XL.th, i, th * rexpm1<R>(rlog1p<R>(dT / Temp) * inv_gamma));
+      continue;
     }
     R fr = R(1) / (R(1) + Kv * rdt);
     X.mx[i] *= fr;
@@ -793,7 +838,7 @@ __global__ void k_energy_prepare(const double* fin0, const double* fin1, double 
 // every cell: T -> T + dT at fixed rho, i.e. rho theta (Eq. pressure, in
 // deviation form) scaled by (1 + dT / T)^(1 / gamma)
 template <typename R>
-__global__ void k_energy_fix(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, const R* fixf, int kchunk) {
+__global__ void k_energy_fix(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Xf<R> XL, const R* fixf, int kchunk) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -803,12 +848,17 @@ __global__ void k_energy_fix(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, const R* fixf,
   const int k0 = blockIdx.y * kchunk, k1 = min(G.nv, k0 + kchunk);
   for (int k = k0; k < k1; ++k) {
     const int i = k * S + c;
-    const R thp = ld(X.th + i);
-    const R rho = ld(U.rhob + k) + ld(X.rho + i);
+    const bool cmp = XL.rho != nullptr;
+    const R thp = cmp ? ld(X.th + i) + ld(XL.th + i) : ld(X.th + i);
+    const R rho = ld(U.rhob + k) + (cmp ? ld(X.rho + i) + ld(XL.rho + i) : ld(X.rho + i));
     const R p = ld(U.pb + k) + eos_dev<R>(ld(U.pb + k), ld(U.thb + k), thp, gamma);
     const R Temp = p / rho * inv_Rd;
     const R th = ld(U.thb + k) + thp;
-    X.th[i] = thp + th * rexpm1<R>(rlog1p<R>(dT / Temp) * inv_gamma);
+    const R d = th * rexpm1<R>(rlog1p<R>(dT / Temp) * inv_gamma);
+    if (cmp)
+      comp_add<R>(X.th, XL.th, X.th, XL.th, i, d);
+    else
+      X.th[i] = thp + d;
   }
 }
 
@@ -833,9 +883,9 @@ __global__ void k_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> 
   d_slow_w<R>(G, U, ph, Xt, X, T, SL, P, hyper, init, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
-__global__ void k_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Pert<R> P, int zero,
-                             int kchunk) {
-  d_stage_init<R>(G, U, ph, Xt, X, T, P, zero, kchunk, blockIdx.x, blockIdx.y);
+__global__ void k_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Pert<R> P, Xf<R> XtL,
+                             Xf<R> XL, int zero, int kchunk) {
+  d_stage_init<R>(G, U, ph, Xt, X, T, P, XtL, XL, zero, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
 __global__ void k_ss_grad(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, const R* pstar, int kchunk) {
@@ -845,8 +895,8 @@ __global__ void k_ss_grad(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, const R* 
 // other small steps carry no registers for the stage end)
 template <typename R, bool LAST>
 __global__ void k_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, R Kd, int divdamp,
-                         Xf<R> Xs, Xf<R> Xo, int kchunk) {
-  d_ss_mom<R>(G, U, SL, P, T, dtau, Kd, divdamp, Xs, Xo, LAST ? 1 : 0, kchunk, blockIdx.x, blockIdx.y);
+                         Xf<R> Xs, Xf<R> Xo, Xf<R> XsL, Xf<R> XoL, int kchunk) {
+  d_ss_mom<R>(G, U, SL, P, T, dtau, Kd, divdamp, Xs, Xo, XsL, XoL, LAST ? 1 : 0, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
 __global__ void k_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, int kchunk) {
@@ -859,17 +909,17 @@ __global__ void __launch_bounds__(64) k_ss_factor(Geo<R> G, VR<R> U, Phys ph, Sl
 template <typename R>
 __global__ void __launch_bounds__(64) k_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs, Slow<R> SL, Pert<R> P,
                                                  Work<R> T, Fac<R> F, double dtau, int want_div, Xf<R> Xo,
-                                                 int last) {
-  d_ss_solve<R>(G, U, ph, Xs, SL, P, T, F, dtau, want_div, Xo, last, blockIdx.x, 0);
+                                                 Xf<R> XsL, Xf<R> XoL, int last) {
+  d_ss_solve<R>(G, U, ph, Xs, SL, P, T, F, dtau, want_div, Xo, XsL, XoL, last, blockIdx.x, 0);
 }
 template <typename R>
 __global__ void k_surface_p(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T) {
   d_surface_p<R>(G, U, ph, X, T, blockIdx.x);
 }
 template <typename R>
-__global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int forcing, double dt, double hj_dT,
-                          int kchunk) {
-  d_physics<R>(G, U, ph, X, T, forcing, dt, hj_dT, kchunk, blockIdx.x, blockIdx.y);
+__global__ void k_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Xf<R> XL, Work<R> T, int forcing, double dt,
+                          double hj_dT, int kchunk) {
+  d_physics<R>(G, U, ph, X, XL, T, forcing, dt, hj_dT, kchunk, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------- staged column solve (float storage)
@@ -1007,7 +1057,8 @@ __device__ __forceinline__ void solve_sweeps(const SolveSm& s, double* sx, const
 __device__ __forceinline__ void solve_updates(const SolveSm& s, const Geo<float>& G, const VR<float>& U,
                                               const Phys& ph, const Xf<float>& Xs, const Slow<float>& SL,
                                               const Pert<float>& P, const Work<float>& T, float rdt, int want_div,
-                                              const Xf<float>& Xo, int last, int c, int tx, int k0, int kstep) {
+                                              const Xf<float>& Xo, const Xf<float>& XsL, const Xf<float>& XoL,
+                                              int last, int c, int tx, int k0, int kstep) {
   const int nv = G.nv, S = G.colp;
   const float gamma = ph.gamma_f;
   const float* s_wf = s.w;
@@ -1027,7 +1078,7 @@ __device__ __forceinline__ void solve_updates(const SolveSm& s, const Geo<float>
     P.p[i] = ps * rexpm1<float>(gamma * rlog1p<float>(th_new / ths));
     if (k >= 1) P.w[i] = wl;
     if (want_div) T.dd[i] = ld(SL.dsc + i) + ld(T.dhm + i) + (eh * wh - el * wl);
-    if (last) stage_end_cell(Xs, Xo, P, rho_new, th_new, wl, k, i, S, nv);
+    if (last) stage_end_cell(Xs, Xo, XsL, XoL, P, rho_new, th_new, wl, k, i, S, nv);
   }
 }
 
@@ -1035,8 +1086,8 @@ __device__ __forceinline__ void solve_updates(const SolveSm& s, const Geo<float>
 __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<float>& U, const Phys& ph,
                                                const SolveMaps& M, int stage0, const Xf<float>& Xs,
                                                const Slow<float>& SL, const Pert<float>& P, const Work<float>& T,
-                                               double dtau, int want_div, const Xf<float>& Xo, int last, int* err,
-                                               int bx) {
+                                               double dtau, int want_div, const Xf<float>& Xo, const Xf<float>& XsL,
+                                               const Xf<float>& XoL, int last, int* err, int bx) {
   extern __shared__ unsigned char smraw[];
   const int nv = G.nv;
   const int tid = threadIdx.x, tx = tid & 31, warp = tid >> 5;
@@ -1062,14 +1113,15 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
   const float rdt = (float)dtau, g = ph.g_f;
   if (warp < 2) solve_sweeps(s, sx, U, rdt, g, ph.delta_f, nv, tx, warp);
   __syncthreads();
-  if (c < G.ncol) solve_updates(s, G, U, ph, Xs, SL, P, T, rdt, want_div, Xo, last, c, tx, warp, kSolveWarps);
+  if (c < G.ncol)
+    solve_updates(s, G, U, ph, Xs, SL, P, T, rdt, want_div, Xo, XsL, XoL, last, c, tx, warp, kSolveWarps);
 }
 
 __global__ void __launch_bounds__(32 * kSolveWarps)
     k_ss_solve_tma(Geo<float> G, VR<float> U, Phys ph, const __grid_constant__ SolveMaps M, int stage0,
                    Xf<float> Xs, Slow<float> SL, Pert<float> P, Work<float> T, double dtau, int want_div,
-                   Xf<float> Xo, int last, int* err) {
-  d_ss_solve_tma(G, U, ph, M, stage0, Xs, SL, P, T, dtau, want_div, Xo, last, err, blockIdx.x);
+                   Xf<float> Xo, Xf<float> XsL, Xf<float> XoL, int last, int* err) {
+  d_ss_solve_tma(G, U, ph, M, stage0, Xs, SL, P, T, dtau, want_div, Xo, XsL, XoL, last, err, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- kernels: ensemble
@@ -1125,8 +1177,8 @@ template <typename R>
 __global__ void ke_ss_mom(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int j,
                           int kchunk) {
   THOR_MEMBER();
-  d_ss_mom<R>(a.G, a.U, a.SL, a.P, a.T, (R)a.dts[s], a.Kd, a.divdamp, Xs, s == 2 ? a.Xt : a.Xst,
-              j + 1 == a.nsub[s], kchunk, e.y, blockIdx.y);
+  d_ss_mom<R>(a.G, a.U, a.SL, a.P, a.T, (R)a.dts[s], a.Kd, a.divdamp, Xs, s == 2 ? a.Xt : a.Xst, Xf<R>{},
+              Xf<R>{}, j + 1 == a.nsub[s], kchunk, e.y, blockIdx.y);
 }
 template <typename R>
 __global__ void ke_ss_flux(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
@@ -1138,8 +1190,8 @@ __global__ void __launch_bounds__(64)
     ke_ss_solve(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int j) {
   THOR_MEMBER();
   const int want_div = a.divdamp && j + 1 < a.nsub[s];
-  d_ss_solve<R>(a.G, a.U, a.ph, Xs, a.SL, a.P, a.T, a.F, a.dts[s], want_div, s == 2 ? a.Xt : a.Xst,
-                j + 1 == a.nsub[s], e.y, 0);
+  d_ss_solve<R>(a.G, a.U, a.ph, Xs, a.SL, a.P, a.T, a.F, a.dts[s], want_div, s == 2 ? a.Xt : a.Xst, Xf<R>{},
+                Xf<R>{}, j + 1 == a.nsub[s], e.y, 0);
 }
 __global__ void __launch_bounds__(32 * kSolveWarps)
     ke_ss_solve_tma(const Member<float>* __restrict__ M, const int2* __restrict__ map, int s, int j) {
@@ -1148,7 +1200,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps)
   const Xf<float> Xs = s == 0 ? a.Xt : a.Xst;
   const int want_div = a.divdamp && j + 1 < a.nsub[s];
   d_ss_solve_tma(a.G, a.U, a.ph, *a.smap, s == 0, Xs, a.SL, a.P, a.T, a.dts[s], want_div, s == 2 ? a.Xt : a.Xst,
-                 j + 1 == a.nsub[s], a.err, e.y);
+                 Xf<float>{}, Xf<float>{}, j + 1 == a.nsub[s], a.err, e.y);
 }
 template <typename R>
 __global__ void ke_surface_p(const Member<R>* __restrict__ M, const int2* __restrict__ map) {
@@ -1160,7 +1212,7 @@ template <typename R>
 __global__ void ke_physics(const Member<R>* __restrict__ M, const int2* __restrict__ map, int kchunk) {
   const int2 e = map[blockIdx.x];
   const Member<R>& a = M[e.x];
-  if (a.forcing) d_physics<R>(a.G, a.U, a.ph, a.Xt, a.T, a.forcing, a.dt, a.hj_dT, kchunk, e.y, blockIdx.y);
+  if (a.forcing) d_physics<R>(a.G, a.U, a.ph, a.Xt, Xf<R>{}, a.T, a.forcing, a.dt, a.hj_dT, kchunk, e.y, blockIdx.y);
 }
 #undef THOR_MEMBER
 
@@ -1225,13 +1277,14 @@ int Impl<R>::large_step(double dt, int n_small) {
   double* fixv = fin1 + 8;
   R* fixf = reinterpret_cast<R*>(fixv + 1);
   if (energy) {
-    chk(launch_k(k_diag_partial<R>, kDiagBlocks, kDiagThreads, 0, stream, G, V, ph, Xt, fixbuf));
+    chk(launch_k(k_diag_partial<R>, kDiagBlocks, kDiagThreads, 0, stream, G, V, ph, Xt, XtL, fixbuf));
     chk(launch_k(k_diag_final, 1, 256, 0, stream, fixbuf, kDiagBlocks));
     launches += 2;
   }
   for (int s = 0; s < nstages; ++s) {
     // the last stage run writes X^(s+1) into the state
     Xf<R> Xs = s == 0 ? Xt : Xst, Xo = s == nstages - 1 ? Xt : Xst;
+    Xf<R> XsL = s == 0 ? XtL : XstL, XoL = s == nstages - 1 ? XtL : XstL;    // null unless compensated
     cudaStream_t aux = fork ? side : stream;
     mark(THOR_K_DERIVED, true);
     chk(launch_k(k_derived<R>, g2i, bs, 0, stream, G, U, ph, Xs, T, shallow, kc));
@@ -1242,7 +1295,7 @@ int Impl<R>::large_step(double dt, int n_small) {
       chk(cudaStreamWaitEvent(side, ev_fork, 0));
     }
     mark(THOR_K_STAGE_INIT, true);
-    chk(launch_k(k_stage_init<R>, g2i, bs, 0, aux, G, U, ph, Xt, Xs, T, P, (int)(s == 0), kc));
+    chk(launch_k(k_stage_init<R>, g2i, bs, 0, aux, G, U, ph, Xt, Xs, T, P, XtL, XsL, (int)(s == 0), kc));
     mark(THOR_K_STAGE_INIT, false);
     ++launches;
     const bool early_grad = divdamp && s > 0;    // D of X^t is ready before the slow terms
@@ -1291,7 +1344,7 @@ int Impl<R>::large_step(double dt, int n_small) {
       const int last = j + 1 == nsub[s];
       mark(THOR_K_SS_MOM, true);
       chk(launch_k(last ? k_ss_mom<R, true> : k_ss_mom<R, false>, g2, bs, 0, stream, G, U, SL, P, T, (R)dts[s], Kd,
-                   divdamp, Xs, Xo, kc));
+                   divdamp, Xs, Xo, XsL, XoL, kc));
       mark(THOR_K_SS_MOM, false);
       const int want_div = divdamp && !last;
       mark(THOR_K_SS_FLUX, true);
@@ -1300,29 +1353,29 @@ int Impl<R>::large_step(double dt, int n_small) {
       if (fork && j == 0) chk(cudaStreamWaitEvent(stream, ev_join, 0));
       mark(THOR_K_SS_SOLVE, true);
       if (staged)
-        chk(launch_solve_tma(gsolve, s, Xo, dts[s], want_div, last));
+        chk(launch_solve_tma(gsolve, s, Xo, XsL, XoL, dts[s], want_div, last));
       else
         chk(launch_k(k_ss_solve<R>, gsolve, 64, solve_smem, stream, G, U, ph, Xs, SL, P, T, F, dts[s],
-                     want_div, Xo, last));
+                     want_div, Xo, XsL, XoL, last));
       mark(THOR_K_SS_SOLVE, false);
       launches += 3;
     }
   }
   if (energy) {
-    chk(launch_k(k_diag_partial<R>, kDiagBlocks, kDiagThreads, 0, stream, G, V, ph, Xt, part1));
+    chk(launch_k(k_diag_partial<R>, kDiagBlocks, kDiagThreads, 0, stream, G, V, ph, Xt, XtL, part1));
     chk(launch_k(k_diag_final, 1, 256, 0, stream, part1, kDiagBlocks));
     chk(launch_k(k_energy_prepare<R>, 1, 32, 0, stream, (const double*)fin0, (const double*)fin1, ph.cv,
                  energy_fix, fixv, fixf, budget_cap > 0 ? budget : (double*)nullptr, budget_count, budget_cap));
     launches += 3;
     if (energy_fix) {
-      chk(launch_k(k_energy_fix<R>, g2, bs, 0, stream, G, U, ph, Xt, (const R*)fixf, kc));
+      chk(launch_k(k_energy_fix<R>, g2, bs, 0, stream, G, U, ph, Xt, XtL, (const R*)fixf, kc));
       ++launches;
     }
   }
   if (forcing != 0 && nstages == 3) {
     mark(THOR_K_PHYSICS, true);
     chk(launch_k(k_surface_p<R>, g1, bs, 0, stream, G, U, ph, Xt, T));
-    chk(launch_k(k_physics<R>, g2, bs, 0, stream, G, U, ph, Xt, T, forcing, dt, hj_dT, kc));
+    chk(launch_k(k_physics<R>, g2, bs, 0, stream, G, U, ph, Xt, XtL, T, forcing, dt, hj_dT, kc));
     mark(THOR_K_PHYSICS, false);
     launches += 2;
   }
@@ -1330,13 +1383,15 @@ int Impl<R>::large_step(double dt, int n_small) {
 }
 
 template <>
-cudaError_t Impl<float>::launch_solve_tma(dim3 grid, int stage, const Xf<float>& Xo, double dtau, int want_div,
-                                          int last) {
+cudaError_t Impl<float>::launch_solve_tma(dim3 grid, int stage, const Xf<float>& Xo, const Xf<float>& XsL,
+                                          const Xf<float>& XoL, double dtau, int want_div, int last) {
   return launch_k(k_ss_solve_tma, grid, 32 * kSolveWarps, solve_tma_smem_bytes(G.nv), stream, G, U, ph,
-                  *smaps, (int)(stage == 0), stage == 0 ? Xt : Xst, SL, P, T, dtau, want_div, Xo, last, dev_err);
+                  *smaps, (int)(stage == 0), stage == 0 ? Xt : Xst, SL, P, T, dtau, want_div, Xo, XsL, XoL, last,
+                  dev_err);
 }
 template <>
-cudaError_t Impl<double>::launch_solve_tma(dim3, int, const Xf<double>&, double, int, int) {
+cudaError_t Impl<double>::launch_solve_tma(dim3, int, const Xf<double>&, const Xf<double>&, const Xf<double>&,
+                                           double, int, int) {
   return cudaErrorInvalidValue;
 }
 

@@ -102,3 +102,21 @@ def change_errors(A, B, X0):
         out[f] = err / change if change > 0 else err
     return out
 
+
+def moving_start(pair, X, seed=11, amp=5.0):
+    """X (an oracle state at rest) with a smooth motion added and injected into
+    both sides: horizontal momentum rho (u0 z x r + a random projected
+    field of 1% of it) with u0 = amp m/s at the equator, vertical momentum of
+    1e-3 kg m^-2 s^-1 on the interior interfaces. From rest with density-only
+    noise the pressure is horizontally uniform and the first small step
+    leaves M at zero, where the oracle keeps float64 rounding noise."""
+    from oracle import operators as op
+    rng = np.random.default_rng(seed)
+    r = pair.model.rhat
+    rot = np.cross(np.array([0.0, 0.0, 1.0])[None, :], r)
+    v = amp * rot[:, None, :] + 0.01 * amp * op.project_h(r, rng.standard_normal(X.M.shape))
+    X.M[:] = X.rho[..., None] * v
+    X.W[:, 1:-1] = 1e-3 * rng.standard_normal((X.W.shape[0], X.W.shape[1] - 2))
+    pair.set(X)
+    return X
+
