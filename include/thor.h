@@ -140,7 +140,20 @@ typedef struct {
  * in the same discrete hydrostatic balance (found as the fixed point
  * T = T_eq(p(T)) to 1e-12 K, else THOR_ENOTCONV), T0 ignored; noise_amp
  * still adds its perturbation. The balanced start column is also the
- * reference column of the deviation form. */
+ * reference column of the deviation form.
+ * vorder: 0 or 1 (the paper's runs) = linear vertical interpolation; 2 or 3 =
+ * the Lagrange polynomial of that order k (Sec. 2.1 implements any order
+ * and runs k = 1) in the explicit terms: the velocity at the interfaces for
+ * the vertical advection, W at the centres for the full momentum
+ * (advection, Coriolis), the radial advection and Coriolis at the
+ * interfaces, and rho at the interfaces of the vertical hyperdiffusion,
+ * each from the k + 1 nodes nearest the target (the lower first on a tie,
+ * shifted inward at the bottom and the top). The terms of the implicit
+ * vertical system (gravity, theta at the interfaces, the pressure gradient)
+ * stay linear, so the column system stays tridiagonal and a resting
+ * column in discrete balance stays at rest. Needs nv >= k + 1; other
+ * values give THOR_EINVAL. thor_diag and the transfers interpolate
+ * linearly whatever vorder is. */
 enum { THOR_PROFILE_ISOTHERMAL = 0, THOR_PROFILE_HELD_SUAREZ = 1 };
 typedef struct {
   double T0, p_surf, noise_amp;
@@ -153,6 +166,7 @@ typedef struct {
   int shallow;
   int hydrostatic;
   int profile;
+  int vorder;
 } thor_init;
 
 /* Allocate the device state for `grid` and set the initial condition. The
@@ -336,16 +350,17 @@ int thor_zonal_read_w(thor_state* state, int nlat, double* out, size_t n, long l
  * small step of dt/3 from X^t. For tests that check the first small step on
  * its own; THOR_EINVAL outside 1..3.
  * THOR_TUNE_COMPENSATED (THOR_MIXED states): 1 keeps every prognostic field
- * of the state (and of the RK stage state) as a float pair hi + lo, |lo| at
- * most half a unit in the last place of hi, and adds each stage's
- * accumulated small-step perturbations (Eqs. dens2, mom2, momr2, pt2), the
+ * of the state as a float pair hi + lo, |lo| at most half a unit in the
+ * last place of hi, and adds the last RK stage's accumulated small-step
+ * perturbations (Eqs. dens2, mom2, momr2, pt2; the perturbations start
+ * every stage at X^t - X^(s), so they carry the whole large step), the
  * physics increments (Eqs. im_eq_v, im_eq_t) and the energy fixer's to the
  * pair with an error-free sum (TwoSum), so that the float32 storage does
- * not round the state at every stage end; thor_state_get / _set, thor_diag
- * and checkpoints (then twice the size) use the full pairs. The tendencies
- * are still evaluated from the float parts. The first use allocates the
- * low parts (12 planes), zeroed; 0 frees them and rounds the state to its
- * float parts. Synchronises the state's stream. Compensated states cannot
+ * not round the state at every large step; thor_state_get / _set,
+ * thor_diag and checkpoints (then twice the size) use the full pairs. The
+ * RK stage states and the tendencies stay float. The first use allocates
+ * the low parts (6 planes), zeroed; 0 frees them and rounds the state to
+ * its float parts. Synchronises the state's stream. Compensated states cannot
  * join an ensemble (thor_ensemble_step returns THOR_EINVAL); THOR_EINVAL
  * for THOR_FP64 states. Default 0. */
 

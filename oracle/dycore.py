@@ -45,6 +45,17 @@ R6  Advection and Coriolis (Sec. 3): A_j = div(rho v v_j) for the three
 R7  K_d = D dbar^4 / dt (Eq. kd) with dbar from Eq. grid_qts; the
     nondimensional D of a planet follows from its Table 1 diffusion time
     scale through Eq. tau_d at the paper's own time step.
+L-2 Higher-order vertical interpolation (Sec. 2.1 implements the Lagrange
+    polynomial of any order k and runs k = 1): with vorder = k > 1 the
+    explicit terms interpolate with order k (reading L-1 for the nodes): the
+    velocity at the interfaces for the vertical advection, W at the centres
+    for the full momentum (advection, Coriolis), the radial advection and
+    Coriolis at the interfaces, and rho at the interfaces of the vertical
+    hyperdiffusion. The terms that enter the implicit vertical system keep
+    k = 1: rho at the interfaces in the gravity term, theta at the
+    interfaces, and the pressure gradient, so the vertical system stays
+    tridiagonal, the discrete hydrostatic balance of a resting column holds
+    exactly and a uniform theta stays uniform.
 H1  Hydrostatic switch (Sec. 3 lists the hydrostatic approximation among
     those the model implements but does not use: the vertical pressure
     gradient balances gravity). Read as a factor delta on the vertical
@@ -114,6 +125,7 @@ class Model:
     hyperdiffusion: bool = True
     divergence_damping: bool = True
     hydrostatic: bool = False      # reading H1
+    vorder: int = 1                # reading L-2: order k of the explicit vertical interpolations
     Kd_fixed: float = None         # a fixed K_d instead of Eq. kd (tests)
     rhat: np.ndarray = field(init=False)
 
@@ -150,7 +162,7 @@ def temperature(planet, rho, p):
 def hyperdiffusion(model, X, p, Kd):
     """Sec. 4, Eqs. diff_rho ... diff_p with readings R4, R7."""
     g, vg, pl = model.grid, model.vg, model.planet
-    rho_i = op.interp_to_interfaces(vg, X.rho)
+    rho_i = op.interp_to_interfaces(vg, X.rho, model.vorder)
     vh = X.M / X.rho[..., None]
     vr = np.zeros_like(X.W)
     vr[:, 1:-1] = X.W[:, 1:-1] / rho_i[:, 1:-1]
@@ -180,16 +192,17 @@ def _shallow_advection_coriolis(model, X, Wc):
     scalar in the vertical one. Returns (AC_h at the centres, AC_r at the
     interfaces)."""
     g, vg, pl, rhat = model.grid, model.vg, model.planet, model.rhat
+    k = model.vorder
     vh = X.M / X.rho[..., None]
     w = Wc / X.rho
     A_h = np.zeros_like(X.M)
     for j in range(3):
         A_h[..., j] = op.div_h_levels(g, vg, X.M * vh[..., j:j + 1]) \
-            + op.div_v(vg, X.W * op.interp_to_interfaces(vg, vh[..., j]))
-    A_r = op.div_h_levels(g, vg, X.M * w[..., None]) + op.div_v(vg, X.W * op.interp_to_interfaces(vg, w))
+            + op.div_v(vg, X.W * op.interp_to_interfaces(vg, vh[..., j], k))
+    A_r = op.div_h_levels(g, vg, X.M * w[..., None]) + op.div_v(vg, X.W * op.interp_to_interfaces(vg, w, k))
     f = 2.0 * pl.omega * rhat[:, 2]
     C_h = f[:, None, None] * np.cross(np.broadcast_to(rhat[:, None, :], X.M.shape), X.M)
-    return op.project_h(rhat, A_h + C_h), op.interp_to_interfaces(vg, A_r)
+    return op.project_h(rhat, A_h + C_h), op.interp_to_interfaces(vg, A_r, k)
 
 
 def slow_terms(model, X, Kd):
@@ -201,7 +214,7 @@ def slow_terms(model, X, Kd):
     p = pressure(pl, X.Th)
 
     # full 3-D momentum and velocity at the centres (reading R6)
-    Wc = op.interp_to_centres(vg, X.W)
+    Wc = op.interp_to_centres(vg, X.W, model.vorder)
     mom = X.M + Wc[..., None] * rhat[:, None, :]
     vel = mom / X.rho[..., None]
 
@@ -212,12 +225,12 @@ def slow_terms(model, X, Kd):
         A = np.zeros((N, nv, 3))
         for j in range(3):
             A[..., j] = op.div_h_levels(g, vg, X.M * vel[..., j:j + 1]) \
-                + op.div_v(vg, X.W * op.interp_to_interfaces(vg, vel[..., j]))
+                + op.div_v(vg, X.W * op.interp_to_interfaces(vg, vel[..., j], model.vorder))
         # Coriolis 2 Omega x (rho v), Omega along z
         Om = np.array([0.0, 0.0, pl.omega])
         C = 2.0 * np.cross(Om[None, None, :], mom)
         AC_h = op.project_h(rhat, A + C)
-        AC_r = op.interp_to_interfaces(vg, op.radial(rhat, A + C))
+        AC_r = op.interp_to_interfaces(vg, op.radial(rhat, A + C), model.vorder)
 
     rho_i = op.interp_to_interfaces(vg, X.rho)
 

@@ -22,8 +22,11 @@ Readings:
   is the corner value of Eq. int_grid), which places a gradient vector at the
   corner C_k; Eq. div_gauss applied to those corner vectors gives the
   Laplacian at P_0.
-* Vertical interpolation is the Lagrange polynomial of Sec. 2.1 with k = 1
-  (linear in altitude), from centres to interfaces and back.
+* Vertical interpolation is the Lagrange polynomial of Sec. 2.1, k = 1
+  (linear in altitude) by default, from centres to interfaces and back.
+* Reading L-1 (Sec. 2.1 leaves the nodes of a k > 1 polynomial unstated):
+  the k + 1 consecutive nodes nearest the target, the lower one first where
+  two are equally near (even k), shifted inward at the bottom and the top.
 """
 
 import numpy as np
@@ -158,21 +161,64 @@ class VerticalGrid:
         self.ri = radius + (0.0 if shallow else 1.0) * self.zi
 
 
-def interp_to_interfaces(vg, x):
-    """Lagrange k = 1 (Sec. 2.1) from centres to the interior interfaces:
-    x (..., nv) -> (..., nv+1) with the two boundary interfaces left at 0."""
+def lagrange_weights(nodes, zh):
+    """Sec. 2.1: the weights L_j(z_h) = prod_{i != j} (z_h - z_i) / (z_j - z_i)
+    of the Lagrange polynomial through ``nodes`` (k + 1 altitudes), so that
+    Phi(z_h) = sum_j Phi_j L_j(z_h)."""
+    w = np.ones(len(nodes))
+    for j, zj in enumerate(nodes):
+        for i, zi in enumerate(nodes):
+            if i != j:
+                w[j] *= (zh - zi) / (zj - zi)
+    return w
+
+
+def stencil_start(target, k, n):
+    """First of the k + 1 consecutive nodes used for the target position
+    (reading L-1): the nodes nearest the target, target - ceil((k + 1) / 2)
+    up, shifted inward where they would leave the n nodes. ``target`` is the
+    index of the first node above the target position."""
+    return min(max(target - (k + 2) // 2, 0), n - k - 1)
+
+
+def interp_to_interfaces(vg, x, order=1):
+    """Lagrange interpolation of order k = ``order`` (Sec. 2.1) from centres
+    to the interior interfaces: x (..., nv) -> (..., nv+1) with the two
+    boundary interfaces left at 0. k = 1 is linear in altitude between the
+    two centres around the interface; k > 1 takes the k + 1 centres of
+    stencil_start."""
     out = np.zeros(x.shape[:-1] + (vg.nv + 1,))
-    z0, z1 = vg.zc[:-1], vg.zc[1:]
-    zh = vg.zi[1:-1]
-    out[..., 1:-1] = x[..., :-1] * (zh - z1) / (z0 - z1) + x[..., 1:] * (zh - z0) / (z1 - z0)
+    if order == 1:
+        z0, z1 = vg.zc[:-1], vg.zc[1:]
+        zh = vg.zi[1:-1]
+        out[..., 1:-1] = x[..., :-1] * (zh - z1) / (z0 - z1) + x[..., 1:] * (zh - z0) / (z1 - z0)
+        return out
+    if vg.nv < order + 1:
+        raise ValueError("fewer centres than the interpolation order needs")
+    for i in range(1, vg.nv):
+        j0 = stencil_start(i, order, vg.nv)
+        w = lagrange_weights(vg.zc[j0:j0 + order + 1], vg.zi[i])
+        out[..., i] = sum(w[j] * x[..., j0 + j] for j in range(order + 1))
     return out
 
 
-def interp_to_centres(vg, xi):
-    """Lagrange k = 1 from interfaces to centres: xi (..., nv+1) -> (..., nv)."""
-    z0, z1 = vg.zi[:-1], vg.zi[1:]
-    zh = vg.zc
-    return xi[..., :-1] * (zh - z1) / (z0 - z1) + xi[..., 1:] * (zh - z0) / (z1 - z0)
+def interp_to_centres(vg, xi, order=1):
+    """Lagrange interpolation of order k = ``order`` from interfaces to
+    centres: xi (..., nv+1) -> (..., nv). k = 1 is linear between the two
+    interfaces of the layer; k > 1 takes the k + 1 interfaces of
+    stencil_start (the boundary interfaces included)."""
+    if order == 1:
+        z0, z1 = vg.zi[:-1], vg.zi[1:]
+        zh = vg.zc
+        return xi[..., :-1] * (zh - z1) / (z0 - z1) + xi[..., 1:] * (zh - z0) / (z1 - z0)
+    if vg.nv + 1 < order + 1:
+        raise ValueError("fewer interfaces than the interpolation order needs")
+    out = np.zeros(xi.shape[:-1] + (vg.nv,))
+    for c in range(vg.nv):
+        j0 = stencil_start(c + 1, order, vg.nv + 1)
+        w = lagrange_weights(vg.zi[j0:j0 + order + 1], vg.zc[c])
+        out[..., c] = sum(w[j] * xi[..., j0 + j] for j in range(order + 1))
+    return out
 
 
 def ddz_at_interfaces(vg, x):

@@ -203,8 +203,8 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   I.F.junction = cv.take<double>(S);
   // tables
   I.G.nbr = cv.take<int>(6 * S);
-  I.G.wdiv = cv.take<R>(21 * S);
-  I.G.wgrad = cv.take<R>(21 * S);
+  I.G.wdiv = cv.take<R>(28 * S);
+  I.G.wgrad = cv.take<R>(28 * S);
   I.G.wlap = cv.take<R>(7 * S);
   I.G.rhat = cv.take<R>(3 * S);
   I.G.sinlat = cv.take<R>(S);
@@ -217,16 +217,30 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   const double** vi[] = {&I.V.ri, &I.V.dzc, &I.V.wlo, &I.V.whi, &I.V.Rb, &I.V.ri2, &I.V.inv_dzc};
   for (const double** p : vi) *p = cv.take<double>(nv + 1);
   for (const R** p : vr_slots(I.U)) *p = cv.take<R>(nv + 1);
+  I.U.iw = cv.take<R>(4 * (size_t)(nv + 1));
+  I.U.cw = cv.take<R>(4 * (size_t)nv);
+  I.U.ij0 = cv.take<int>(nv + 1);
+  I.U.cj0 = cv.take<int>(nv);
   I.staging = cv.take<double>((size_t)ncol * (6 * nv + 1));    // rho, 3 x rho v_h, W, rho theta
   I.red = cv.take<double>((size_t)(kDiagBlocks + 1) * 8);
   I.dev_err = cv.take<int>(64);
 }
 
+// Vertical grid, reference column and initial state in float64 on the host.
+struct HostSetup {
+  // rc dz clo chi zc rhob thb pb Tb sv sq_lo sq_hi | ri dzc wlo whi Rb ri2 inv_dzc
+  std::vector<double> vert[kNumVert];
+  std::vector<double> rho, th;    // canonical [ncol][nv]
+  // order-k Lagrange tables of the explicit vertical interpolations
+  std::vector<double> iw, cw;     // [4][nv + 1], [4][nv]
+  std::vector<int> ij0, cj0;      // [nv + 1], [nv]
+};
 template <typename R>
-int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert, cudaStream_t st) {
+int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert, const HostSetup* lag,
+                  cudaStream_t st) {
   const int ncol = h.ncol, S = colp_of(ncol), nv = h.nv;
   std::vector<int> nbr(6 * (size_t)S, 0);
-  std::vector<R> wdiv(21 * (size_t)S, 0), wgrad(21 * (size_t)S, 0), wlap(7 * (size_t)S, 0),
+  std::vector<R> wdiv(28 * (size_t)S, 0), wgrad(28 * (size_t)S, 0), wlap(7 * (size_t)S, 0),
       rhat(3 * (size_t)S, 0), sl(S, 0), cl(S, 0), clon(S, 0);
   std::vector<double> area(S, 0.0);
   for (int c = 0; c < ncol; ++c) {
@@ -235,10 +249,12 @@ int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert
       nbr[(size_t)j * S + c] = q < 0 ? c : q;
     }
     for (int j = 0; j < 7; ++j) {
+      const size_t q = ((size_t)j * S + c) * 4;        // packed [7][colp][4]
       for (int d = 0; d < 3; ++d) {
-        wdiv[(size_t)(3 * j + d) * S + c] = (R)h.w_div[21 * c + 3 * j + d];
-        wgrad[(size_t)(3 * j + d) * S + c] = (R)h.w_grad[21 * c + 3 * j + d];
+        wdiv[q + d] = (R)h.w_div[21 * c + 3 * j + d];
+        wgrad[q + d] = (R)h.w_grad[21 * c + 3 * j + d];
       }
+      wgrad[q + 3] = (R)h.w_lap[7 * c + j];
       wlap[(size_t)j * S + c] = (R)h.w_lap[7 * c + j];
     }
     double x = h.P[3 * c], y = h.P[3 * c + 1], z = h.P[3 * c + 2];
@@ -298,6 +314,11 @@ int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert
     }
     std::vector<const R**> slots = vr_slots(I.U);
     for (int j = 0; j < 17; ++j) e = e ? e : up(*slots[j], vr[j].data(), (nv + 1) * sizeof(R));
+    std::vector<R> iw(lag->iw.begin(), lag->iw.end()), cw(lag->cw.begin(), lag->cw.end());
+    e = e ? e : up(I.U.iw, iw.data(), iw.size() * sizeof(R));
+    e = e ? e : up(I.U.cw, cw.data(), cw.size() * sizeof(R));
+    e = e ? e : up(I.U.ij0, lag->ij0.data(), lag->ij0.size() * sizeof(int));
+    e = e ? e : up(I.U.cj0, lag->cj0.data(), lag->cj0.size() * sizeof(int));
     if (e) return THOR_ECUDA;
     if (cudaStreamSynchronize(st)) return THOR_ECUDA;   // host vectors die here
   }
@@ -418,7 +439,7 @@ int Impl<R>::diag(double* out8, long long* nonfinite) {
   return THOR_OK;
 }
 
-// the low parts of a compensated float state: on allocates them zeroed (the
+// the low parts of a compensated float X^t: on allocates them zeroed (the
 // state's value is unchanged), off frees them (the value rounds to the float
 // parts); float64 states need none
 template <typename R>
@@ -431,17 +452,16 @@ int Impl<R>::set_compensated(int on) {
     cudaFree(lo_buf);
     lo_buf = nullptr;
     XtL = Xf<R>{};
-    XstL = Xf<R>{};
     compensated = 0;
     return THOR_OK;
   }
   const size_t S = G.colp, C = S * G.nv, F = S * (G.nv + 1);
   const size_t per = 5 * C + F;                 // rho, M (3), rho theta, W
-  if (cudaMalloc(&lo_buf, 2 * per * sizeof(R))) {
+  if (cudaMalloc(&lo_buf, per * sizeof(R))) {
     lo_buf = nullptr;
     return THOR_ENOMEM;
   }
-  if (cudaMemsetAsync(lo_buf, 0, 2 * per * sizeof(R), stream) || cudaStreamSynchronize(stream)) {
+  if (cudaMemsetAsync(lo_buf, 0, per * sizeof(R), stream) || cudaStreamSynchronize(stream)) {
     cudaFree(lo_buf);
     lo_buf = nullptr;
     return THOR_ECUDA;
@@ -451,7 +471,6 @@ int Impl<R>::set_compensated(int on) {
     x.rho = p; x.mx = p + C; x.my = p + 2 * C; x.mz = p + 3 * C; x.th = p + 4 * C; x.w = p + 5 * C;
   };
   lay(XtL, b);
-  lay(XstL, b + per);
   compensated = 1;
   return THOR_OK;
 }
@@ -469,12 +488,22 @@ template int Impl<float>::diag(double*, long long*);
 
 namespace {
 
-// Vertical grid, reference column and initial state in float64 on the host.
-struct HostSetup {
-  // rc dz clo chi zc rhob thb pb Tb sv sq_lo sq_hi | ri dzc wlo whi Rb ri2 inv_dzc
-  std::vector<double> vert[kNumVert];
-  std::vector<double> rho, th;    // canonical [ncol][nv]
-};
+
+// Sec. 2.1 with k + 1 nodes (reading L-1): the k + 1 consecutive nodes
+// nearest the target, from target - ceil((k + 1) / 2) up, shifted inward at
+// the ends; `target` is the first of the n nodes above the target altitude.
+// L_j(zh) = prod_{i != j} (zh - z_i) / (z_j - z_i).
+static void lagrange_row(const std::vector<double>& nodes, double zh, int target, int k, int& j0, double w[4]) {
+  const int n = (int)nodes.size();
+  j0 = std::min(std::max(target - (k + 2) / 2, 0), n - k - 1);
+  for (int j = 0; j < 4; ++j) w[j] = 0.0;
+  for (int j = 0; j <= k; ++j) {
+    double l = 1.0;
+    for (int i = 0; i <= k; ++i)
+      if (i != j) l *= (zh - nodes[j0 + i]) / (nodes[j0 + j] - nodes[j0 + i]);
+    w[j] = l;
+  }
+}
 
 // The start column of Sec. 6.1's Held-Suarez run: every layer at the
 // equatorial T_eq of its own pressure, max(200, (315 - 10 ln(p/p0)) (p/p0)^kappa)
@@ -516,6 +545,22 @@ int host_setup(const HostGrid& h, const thor_planet& pl, const thor_init& in, Ho
   for (int i = 0; i < nv; ++i) zi[i] = i * step;
   zi[nv] = h.z_top;
   for (int k = 0; k < nv; ++k) zc[k] = 0.5 * (zi[k] + zi[k + 1]);
+  {
+    const int k = in.vorder > 1 ? in.vorder : 1;
+    hs.iw.assign(4 * (size_t)(nv + 1), 0.0);
+    hs.cw.assign(4 * (size_t)nv, 0.0);
+    hs.ij0.assign(nv + 1, 0);
+    hs.cj0.assign(nv, 0);
+    double w[4];
+    for (int m = 1; m < nv; ++m) {
+      lagrange_row(zc, zi[m], m, k, hs.ij0[m], w);
+      for (int j = 0; j < 4; ++j) hs.iw[(size_t)j * (nv + 1) + m] = w[j];
+    }
+    for (int c = 0; c < nv; ++c) {
+      lagrange_row(zi, zc[c], c + 1, k, hs.cj0[c], w);
+      for (int j = 0; j < 4; ++j) hs.cw[(size_t)j * nv + c] = w[j];
+    }
+  }
   auto& rc = hs.vert[0]; auto& dz = hs.vert[1]; auto& clo = hs.vert[2]; auto& chi = hs.vert[3];
   auto& zcv = hs.vert[4]; auto& rhob = hs.vert[5]; auto& thb = hs.vert[6]; auto& pb = hs.vert[7];
   auto& Tb = hs.vert[8]; auto& sv = hs.vert[9]; auto& sq_lo = hs.vert[10]; auto& sq_hi = hs.vert[11];
@@ -610,6 +655,7 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
   I->ph.g_f = (float)I->ph.g;
   I->ph.two_omega_f = (float)I->ph.two_omega;
   I->ph.hydrostatic = in.hydrostatic ? 1 : 0;
+  I->ph.vorder = in.vorder > 1 ? in.vorder : 1;
   I->ph.delta = in.hydrostatic ? 0.0 : 1.0;
   I->ph.delta_f = (float)I->ph.delta;
   I->hyper = in.hyperdiffusion ? 1 : 0;
@@ -655,11 +701,11 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
     for (int v = 0; v < kNumVert; ++v) mix(hs.vert[v].data(), hs.vert[v].size() * sizeof(double));
     const double pv[7] = {pl.radius, pl.omega, pl.gravity, pl.Rd, pl.cp, pl.p_ref, pl.diff_D};
     mix(pv, sizeof(pv));
-    const int sw[3] = {in.shallow, in.hydrostatic, in.forcing};
+    const int sw[4] = {in.shallow, in.hydrostatic, in.forcing, in.vorder > 1 ? in.vorder : 1};
     mix(sw, sizeof(sw));
     I->ref_hash = x;
   }
-  rc = upload_tables(*I, h, hs.vert, st);
+  rc = upload_tables(*I, h, hs.vert, &hs, st);
   if (rc) return rc;
   rc = I->set(THOR_FIELD_RHO, hs.rho.data(), hs.rho.size());
   if (rc) return rc;
@@ -755,6 +801,7 @@ int thor_state_init(thor_grid* grid, const thor_planet* pl, const thor_init* in,
       !(pl->Rd > 0) || !(pl->cp > pl->Rd) || !(pl->gravity > 0) || !(pl->p_ref > 0) || !(pl->diff_D >= 0) ||
       !(in->T0 > 0 || in->profile == THOR_PROFILE_HELD_SUAREZ) || !(in->p_surf > 0) || !(in->noise_amp >= 0) ||
       in->profile < THOR_PROFILE_ISOTHERMAL || in->profile > THOR_PROFILE_HELD_SUAREZ || in->forcing < 0 ||
+      in->vorder < 0 || in->vorder > 3 || grid->h.nv < (in->vorder > 1 ? in->vorder : 1) + 1 ||
       in->forcing > 2 ||
       (in->precision != THOR_FP64 && in->precision != THOR_MIXED) || grid->h.nv > thor::kMaxNv)
     return THOR_EINVAL;
@@ -938,7 +985,8 @@ int thor_tune(thor_state* s, int knob, int value) {
     return THOR_OK;
   }
   if (knob == THOR_TUNE_SOLVE_TMA) {
-    s->impl->solve_tma = value != 0;
+    if (value < 0 || value > 3) return THOR_EINVAL;
+    s->impl->solve_tma = value;
     return THOR_OK;
   }
   if (knob == THOR_TUNE_COMPENSATED) return s->impl->set_compensated(value != 0);

@@ -177,10 +177,10 @@ struct Impl : ImplBase {
   Slow<R> SL;
   Pert<R> P;
   Fac<R> F;
-  // low parts of X^t and of the stage state when compensated (null pointers
-  // otherwise): the value of a field is hi + lo, with |lo| at most half a
-  // unit in the last place of hi
-  Xf<R> XtL{}, XstL{};
+  // low parts of X^t when compensated (null pointers otherwise): the value
+  // of a field is hi + lo, with |lo| at most half a unit in the last place of
+  // hi; the stage state is stored as floats
+  Xf<R> XtL{};
   void* lo_buf = nullptr;
   int hyper = 1, divdamp = 1, forcing = 0;
   int shallow = 0;                 // shallow-atmosphere approximation (thor_init.shallow)

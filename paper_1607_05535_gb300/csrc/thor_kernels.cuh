@@ -58,14 +58,20 @@ struct VR {
   const R *inv_rc, *inv_rc2, *sv, *ri2, *wlo, *whi, *clo, *chi, *inv_dzc;
   const R *rhob, *thb, *pb, *Tb, *Rb, *zc;
   const R *sq_lo, *sq_hi;
+  // Lagrange interpolation of order k > 1 in the explicit terms (Sec. 2.1):
+  // interface m (1..nv-1) from centres ij0[m] + j with weights iw[j][m];
+  // centre c from interfaces cj0[c] + j with weights cw[j][c]; j < 4, the
+  // weights beyond k zero
+  const R *iw, *cw;
+  const int *ij0, *cj0;
 };
 
 template <typename R>
 struct Geo {
   int ncol, colp, nv;
   const int* nbr;       // [6][colp]; slot 5 of a pentagon repeats the column
-  const R* wdiv;        // [7][3][colp]
-  const R* wgrad;       // [7][3][colp]
+  const R* wdiv;        // [7][colp][4]: x, y, z, 0
+  const R* wgrad;       // [7][colp][4]: x, y, z and the Laplacian weight of the point
   const R* wlap;        // [7][colp]
   const R* rhat;        // [3][colp]
   const R* sinlat;      // [colp]
@@ -85,6 +91,8 @@ struct Phys {
   double delta = 1.0;
   float delta_f = 1.0f;
   int hydrostatic = 0;
+  // order k of the vertical interpolation in the explicit terms (1: linear)
+  int vorder = 1;
 };
 // the constant in the kernel's storage type
 template <typename R> __device__ __forceinline__ R pc(double d, float f);
@@ -141,10 +149,11 @@ __device__ __forceinline__ void two_sum(R a, R b, R& s, R& e) {
 // hi + (lo + d) is split into its float and the float remainder, so the
 // state's own rounding is not repeated at every update (only d + lo rounds).
 // out_hi / out_lo may be hi / lo themselves (each element is read first).
+// A null lo is a zero low part (a stage state stored as floats).
 template <typename R>
 __device__ __forceinline__ void comp_add(const R* hi, const R* lo, R* out_hi, R* out_lo, size_t i, R d) {
   R s, e;
-  two_sum(hi[i], lo[i] + d, s, e);
+  two_sum(hi[i], lo ? lo[i] + d : d, s, e);
   out_hi[i] = s;
   out_lo[i] = e;
 }
@@ -272,16 +281,60 @@ __device__ __forceinline__ W7<R> load_w7(const R* w, int colp, int c) {
   for (int j = 0; j < 7; ++j) o.v[j] = ld(w + j * colp + c);
   return o;
 }
+// The 3-vector weights of the seven stencil points of column c, stored
+// packed as [7][colp][4] (x, y, z and a fourth value: for the gradient table
+// the Laplacian weight of the same point, else 0), so that one 16-byte load
+// (two in float64) brings a point's weights.
 template <typename R>
 __device__ __forceinline__ W7x3<R> load_w7x3(const R* w, int colp, int c) {
   W7x3<R> o;
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
-    o.x[j] = ld(w + (3 * j) * colp + c);
-    o.y[j] = ld(w + (3 * j + 1) * colp + c);
-    o.z[j] = ld(w + (3 * j + 2) * colp + c);
+    const Q4<R> q = ld4(w, (size_t)j * colp + c);
+    o.x[j] = q.x;
+    o.y[j] = q.y;
+    o.z[j] = q.z;
   }
   return o;
+}
+// the gradient weights and, from the same loads, the Laplacian weights
+template <typename R>
+__device__ __forceinline__ void load_w7x3_lap(const R* w, int colp, int c, W7x3<R>& g, W7<R>& l) {
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    const Q4<R> q = ld4(w, (size_t)j * colp + c);
+    g.x[j] = q.x;
+    g.y[j] = q.y;
+    g.z[j] = q.z;
+    l.v[j] = q.w;
+  }
+}
+
+// Order-k Lagrange interpolation (Sec. 2.1) of column c: the centre field f
+// at interface m, or the interface field fi at centre k; with ref (one
+// value per level) the full value ref + f is interpolated.
+template <typename R>
+__device__ __forceinline__ R vint_iface(const VR<R>& U, const R* f, const R* ref, int m, int c, int S, int nv) {
+  const int j0 = ld(U.ij0 + m);
+  R s = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int q = min(j0 + j, nv - 1);
+    const R v = ref ? ld(ref + q) + ld(f + (q * S + c)) : ld(f + (q * S + c));
+    s += ld(U.iw + (j * (nv + 1) + m)) * v;
+  }
+  return s;
+}
+template <typename R>
+__device__ __forceinline__ R vint_centre(const VR<R>& U, const R* fi, int k, int c, int S, int nv) {
+  const int j0 = ld(U.cj0 + k);
+  R s = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int q = min(j0 + j, nv);
+    s += ld(U.cw + (j * nv + k)) * ld(fi + (q * S + c));
+  }
+  return s;
 }
 
 // sum_j w_j f(n_j) on one plane

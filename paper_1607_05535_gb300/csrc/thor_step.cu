@@ -59,7 +59,8 @@ __device__ __forceinline__ void d_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, W
       R p = ld(U.pb + (k)) + pp;
       R inv = R(1) / rho;
       R Temp = p * inv * inv_Rd;
-      R wc = ld(U.clo + (k)) * ld(X.w + (i)) + ld(U.chi + (k)) * ld(X.w + (i + S));
+      R wc = ph.vorder > 1 ? vint_centre(U, X.w, k, c, S, G.nv)
+                           : ld(U.clo + (k)) * ld(X.w + (i)) + ld(U.chi + (k)) * ld(X.w + (i + S));
       R mx = ld(X.mx + (i)), my = ld(X.my + (i)), mz = ld(X.mz + (i));
       T.pp[i] = pp;
       T.Tp[i] = Temp - ld(U.Tb + (k));
@@ -75,7 +76,10 @@ __device__ __forceinline__ void d_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, W
     if (k >= 1 && k < G.nv) {
       int i = k * S + c;
       R rlo = ld(U.rhob + (k - 1)) + ld(X.rho + (i - S)), rhi = ld(U.rhob + (k)) + ld(X.rho + (i));
-      T.vr[i] = ld(X.w + (i)) / (ld(U.wlo + (k)) * rlo + ld(U.whi + (k)) * rhi);
+      if (ph.vorder > 1)
+        T.vr[i] = ld(X.w + (i)) / vint_iface(U, X.rho, U.rhob, k, c, S, G.nv);
+      else
+        T.vr[i] = ld(X.w + (i)) / (ld(U.wlo + (k)) * rlo + ld(U.whi + (k)) * rhi);
     } else if (k == 0 || k == G.nv) {
       T.vr[k * S + c] = 0;
     }
@@ -85,7 +89,8 @@ __device__ __forceinline__ void d_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, W
 // First Laplacians of the hyperdiffusion (Sec. 4), already multiplied by
 // K_d and, for the momentum and temperature terms, by rho.
 template <typename R>
-__device__ __forceinline__ void d_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk, int bx, int by) {
+__device__ __forceinline__ void d_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int vorder, int kchunk, int bx,
+                                       int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -108,7 +113,7 @@ __device__ __forceinline__ void d_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R 
     if (k >= 1 && k < G.nv) {
       int o = k * S;
       R rlo = ld(U.rhob + (k - 1)) + ld(X.rho + (o - S + c)), rhi = ld(U.rhob + (k)) + ld(X.rho + (o + c));
-      R rif = ld(U.wlo + (k)) * rlo + ld(U.whi + (k)) * rhi;
+      R rif = vorder > 1 ? vint_iface(U, X.rho, U.rhob, k, c, S, G.nv) : ld(U.wlo + (k)) * rlo + ld(U.whi + (k)) * rhi;
       T.qvr[o + c] = rif * Kd * apply7(wl, nb, T.vr + o) / ld(U.ri2 + (k));
     } else if (k == 0 || k == G.nv) {
       T.qvr[k * S + c] = 0;
@@ -135,8 +140,9 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
   W7x3<R> wd = load_w7x3(G.wdiv, S, c);
-  W7x3<R> wg = load_w7x3(G.wgrad, S, c);
-  W7<R> wl = load_w7(G.wlap, S, c);
+  W7x3<R> wg;
+  W7<R> wl;
+  load_w7x3_lap(G.wgrad, S, c, wg, wl);
   R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
   const R two_om = pc<R>(ph.two_omega, ph.two_omega_f), gamma = pc<R>(ph.gamma, ph.gamma_f),
           Rd = pc<R>(ph.Rd, ph.Rd_f);
@@ -202,8 +208,13 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
     for (int j = 0; j < 3; ++j) {
       R ah = sa[j] * inv_r;
       R vlo = 0, vhi = 0;
-      if (k >= 1) vlo = ld(U.wlo + (k)) * vs[j][i - S] + ld(U.whi + (k)) * vs[j][i];
-      if (k + 1 < G.nv) vhi = ld(U.wlo + (k + 1)) * vs[j][i] + ld(U.whi + (k + 1)) * vs[j][i + S];
+      if (ph.vorder > 1) {
+        if (k >= 1) vlo = vint_iface(U, vs[j], (const R*)nullptr, k, c, S, G.nv);
+        if (k + 1 < G.nv) vhi = vint_iface(U, vs[j], (const R*)nullptr, k + 1, c, S, G.nv);
+      } else {
+        if (k >= 1) vlo = ld(U.wlo + (k)) * vs[j][i - S] + ld(U.whi + (k)) * vs[j][i];
+        if (k + 1 < G.nv) vhi = ld(U.wlo + (k + 1)) * vs[j][i] + ld(U.whi + (k + 1)) * vs[j][i + S];
+      }
       A[j] = ah + sqh * whi_w * vhi - sql * wlo_w * vlo;
     }
     R acr, ahx, ahy, ahz;
@@ -214,8 +225,13 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
       A[1] += f * (rz * mx - rx * mz);
       A[2] += f * (rx * my - ry * mx);
       R wlo_c = 0, whi_c = 0;
-      if (k >= 1) wlo_c = ld(U.wlo + (k)) * ld(T.wc + (i - S)) + ld(U.whi + (k)) * ld(T.wc + (i));
-      if (k + 1 < G.nv) whi_c = ld(U.wlo + (k + 1)) * ld(T.wc + (i)) + ld(U.whi + (k + 1)) * ld(T.wc + (i + S));
+      if (ph.vorder > 1) {
+        if (k >= 1) wlo_c = vint_iface(U, (const R*)T.wc, (const R*)nullptr, k, c, S, G.nv);
+        if (k + 1 < G.nv) whi_c = vint_iface(U, (const R*)T.wc, (const R*)nullptr, k + 1, c, S, G.nv);
+      } else {
+        if (k >= 1) wlo_c = ld(U.wlo + (k)) * ld(T.wc + (i - S)) + ld(U.whi + (k)) * ld(T.wc + (i));
+        if (k + 1 < G.nv) whi_c = ld(U.wlo + (k + 1)) * ld(T.wc + (i)) + ld(U.whi + (k + 1)) * ld(T.wc + (i + S));
+      }
       acr = sa3 * inv_r + sqh * whi_w * whi_c - sql * wlo_w * wlo_c;
       const R d = A[0] * rx + A[1] * ry + A[2] * rz;
       ahx = A[0] - d * rx;
@@ -223,7 +239,7 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
       ahz = A[2] - d * rz;
     } else {
       // Coriolis 2 Omega z x (rho v) with the full momentum
-      R wc = ld(U.clo + (k)) * wlo_w + ld(U.chi + (k)) * whi_w;
+      R wc = ph.vorder > 1 ? vint_centre(U, X.w, k, c, S, G.nv) : ld(U.clo + (k)) * wlo_w + ld(U.chi + (k)) * whi_w;
       R mx = ld(X.mx + (i)), my = ld(X.my + (i));
       R fx = mx + wc * rx, fy = my + wc * ry;
       A[0] += -two_om * fy;
@@ -298,7 +314,9 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
     if (!ph.hydrostatic) {
       R FW = 0;
       if (hyper) FW = -apply7(wl, nb, T.qvr + k * S) / ld(U.ri2 + (k));
-      sw = sw - (wlo * ld(SL.acr + (i - S)) + whi * ld(SL.acr + (i))) + FW;
+      const R acr_i = ph.vorder > 1 ? vint_iface(U, (const R*)SL.acr, (const R*)nullptr, k, c, S, G.nv)
+                                    : wlo * ld(SL.acr + (i - S)) + whi * ld(SL.acr + (i));
+      sw = sw - acr_i + FW;
     }
     SL.sw[i] = sw;
     SL.thi[i] = wlo * ld(T.theta + (i - S)) + whi * ld(T.theta + (i));
@@ -309,9 +327,10 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
 // runs this beside the slow terms): Phi* = Phi^t - Phi^(s), p* from the
 // nonlinear Eq. theta_to_p; all zero in the first stage, where Phi^(s) =
 // Phi^t and p^(s) = EOS(Th^t). M* goes into the packed plane with theta of
-// the stage state beside it (the column fluxes gather both). XtL, XL: the low
-// parts of a compensated state (null pointers: none), so that
-// Phi^t - Phi^(s) is taken from the full pairs.
+// the stage state beside it (the column fluxes gather both). XtL: the low
+// parts of a compensated X^t (null pointers: none), XL those of the stage
+// state (null: stored as floats), so that Phi^t - Phi^(s) is taken from the
+// full values.
 template <typename R>
 __device__ __forceinline__ void d_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Pert<R> P,
                                              Xf<R> XtL, Xf<R> XL, int zero, int kchunk, int bx, int by) {
@@ -324,10 +343,12 @@ __device__ __forceinline__ void d_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> X
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int i = k * S + c;
-    // Phi^t - Phi^(s) of one field
+    // Phi^t - Phi^(s) of one field (the stage state of a compensated state
+    // is stored as floats, XL null, except in the first stage where it is
+    // X^t itself and the perturbations are zero)
     auto dif = [&](const R* a, const R* b, const R* al, const R* bl) {
       R d = ld(a + i) - ld(b + i);
-      if (cmp) d += ld(al + i) - ld(bl + i);
+      if (cmp) d += bl ? ld(al + i) - ld(bl + i) : ld(al + i);
       return d;
     };
     if (k < G.nv) {
@@ -386,8 +407,9 @@ __device__ __forceinline__ void d_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> 
   if (c >= G.ncol) return;
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
-  W7x3<R> wg = load_w7x3(G.wgrad, S, c);
-  W7<R> wl = load_w7(G.wlap, S, c);
+  W7x3<R> wg;
+  W7<R> wl;
+  load_w7x3_lap(G.wgrad, S, c, wg, wl);
   R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
   int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
 #pragma unroll 2
@@ -869,8 +891,8 @@ __global__ void k_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int sh
   d_derived<R>(G, U, ph, X, T, shallow, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
-__global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk) {
-  d_lap1<R>(G, U, X, T, Kd, kchunk, blockIdx.x, blockIdx.y);
+__global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int vorder, int kchunk) {
+  d_lap1<R>(G, U, X, T, Kd, vorder, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R, bool SH>
 __global__ void __launch_bounds__(kMaxBlock, 2)
@@ -1052,37 +1074,52 @@ __device__ __forceinline__ void solve_sweeps(const SolveSm& s, double* sx, const
   }
 }
 
-// Eqs. dens2, pt2, theta_to_p with the solved W* of column c, levels k0,
-// k0 + kstep, ...
-__device__ __forceinline__ void solve_updates(const SolveSm& s, const Geo<float>& G, const VR<float>& U,
-                                              const Phys& ph, const Xf<float>& Xs, const Slow<float>& SL,
-                                              const Pert<float>& P, const Work<float>& T, float rdt, int want_div,
-                                              const Xf<float>& Xo, const Xf<float>& XsL, const Xf<float>& XoL,
-                                              int last, int c, int tx, int k0, int kstep) {
-  const int nv = G.nv, S = G.colp;
-  const float gamma = ph.gamma_f;
-  const float* s_wf = s.w;
-#pragma unroll 4
-  for (int k = k0; k < nv; k += kstep) {
-    const int o = k * 32 + tx, i = k * S + c;
-    const float wl = s_wf[o], wh = s_wf[o + 32];
-    const float thl = k > 0 ? ld(SL.thi + i) : 0.f;
-    const float thh = k + 1 < nv ? ld(SL.thi + (i + S)) : 0.f;
-    const float el = ld(U.sq_lo + k), eh = ld(U.sq_hi + k);
-    float th_new = ld(T.cb + i) - rdt * (eh * thh * wh - el * thl * wl);
-    const float rho_new = s.ca[o] - rdt * (eh * wh - el * wl);
-    P.rho[i] = rho_new;
-    P.th[i] = th_new;
-    float ps = ld(U.pb + k) + ld(T.pp + i);
-    float ths = ld(U.thb + k) + ld(Xs.th + i);
-    P.p[i] = ps * rexpm1<float>(gamma * rlog1p<float>(th_new / ths));
-    if (k >= 1) P.w[i] = wl;
-    if (want_div) T.dd[i] = ld(SL.dsc + i) + ld(T.dhm + i) + (eh * wh - el * wl);
-    if (last) stage_end_cell(Xs, Xo, XsL, XoL, P, rho_new, th_new, wl, k, i, S, nv);
-  }
+// Operands of the final updates (Eqs. dens2, pt2, theta_to_p) of one cell
+// that do not depend on the solved W*: loaded before the sweeps end, so that
+// their latency hides behind the float64 chain.
+struct UpdOps {
+  float thl, thh, cb, ps, ths, dsc, dhm;
+};
+__device__ __forceinline__ UpdOps upd_load(const Geo<float>& G, const VR<float>& U, const Xf<float>& Xs,
+                                           const Slow<float>& SL, const Work<float>& T, int want_div, int k,
+                                           int c) {
+  const int nv = G.nv, S = G.colp, i = k * S + c;
+  UpdOps o;
+  o.thl = k > 0 ? ld(SL.thi + i) : 0.f;
+  o.thh = k + 1 < nv ? ld(SL.thi + (i + S)) : 0.f;
+  o.cb = ld(T.cb + i);
+  o.ps = ld(U.pb + k) + ld(T.pp + i);
+  o.ths = ld(U.thb + k) + ld(Xs.th + i);
+  o.dsc = want_div ? ld(SL.dsc + i) : 0.f;
+  o.dhm = want_div ? ld(T.dhm + i) : 0.f;
+  return o;
 }
 
-// M: the state's descriptors, in kernel-parameter or global memory
+// Eqs. dens2, pt2, theta_to_p of one cell with the solved W* (the same
+// operations in the same order as d_ss_solve)
+__device__ __forceinline__ void upd_apply(const SolveSm& s, const UpdOps& o, const Geo<float>& G,
+                                          const VR<float>& U, const Phys& ph, const Xf<float>& Xs,
+                                          const Pert<float>& P, const Work<float>& T, float rdt, int want_div,
+                                          const Xf<float>& Xo, const Xf<float>& XsL, const Xf<float>& XoL,
+                                          int last, int c, int tx, int k) {
+  const int nv = G.nv, S = G.colp;
+  const int q = k * 32 + tx, i = k * S + c;
+  const float* s_wf = s.w;
+  const float wl = s_wf[q], wh = s_wf[q + 32];
+  const float el = ld(U.sq_lo + k), eh = ld(U.sq_hi + k);
+  float th_new = o.cb - rdt * (eh * o.thh * wh - el * o.thl * wl);
+  const float rho_new = s.ca[q] - rdt * (eh * wh - el * wl);
+  P.rho[i] = rho_new;
+  P.th[i] = th_new;
+  P.p[i] = o.ps * rexpm1<float>(ph.gamma_f * rlog1p<float>(th_new / o.ths));
+  if (k >= 1) P.w[i] = wl;
+  if (want_div) T.dd[i] = o.dsc + o.dhm + (eh * wh - el * wl);
+  if (last) stage_end_cell(Xs, Xo, XsL, XoL, P, rho_new, th_new, wl, k, i, S, nv);
+}
+
+// M: the state's descriptors, in kernel-parameter or global memory; PRE:
+// update levels per warp whose operands are loaded before the sweeps
+template <int PRE>
 __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<float>& U, const Phys& ph,
                                                const SolveMaps& M, int stage0, const Xf<float>& Xs,
                                                const Slow<float>& SL, const Pert<float>& P, const Work<float>& T,
@@ -1111,17 +1148,36 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
     return;
   }
   const float rdt = (float)dtau, g = ph.g_f;
+  // every warp loads the W*-independent operands of its first kPre update
+  // levels (k = warp, warp + 8, ...) before the sweeps, which warps 0 and 1
+  // run; the loads of the other six warps land while the chain runs
+  constexpr int kPre = PRE;
+  const bool col = c < G.ncol;
+  UpdOps pre[kPre > 0 ? kPre : 1];
+#pragma unroll
+  for (int q = 0; q < kPre; ++q) {
+    const int k = warp + q * kSolveWarps;
+    if (col && k < nv) pre[q] = upd_load(G, U, Xs, SL, T, want_div, k, c);
+  }
   if (warp < 2) solve_sweeps(s, sx, U, rdt, g, ph.delta_f, nv, tx, warp);
   __syncthreads();
-  if (c < G.ncol)
-    solve_updates(s, G, U, ph, Xs, SL, P, T, rdt, want_div, Xo, XsL, XoL, last, c, tx, warp, kSolveWarps);
+  if (!col) return;
+#pragma unroll
+  for (int q = 0; q < kPre; ++q) {
+    const int k = warp + q * kSolveWarps;
+    if (k < nv) upd_apply(s, pre[q], G, U, ph, Xs, P, T, rdt, want_div, Xo, XsL, XoL, last, c, tx, k);
+  }
+  for (int k = warp + kPre * kSolveWarps; k < nv; k += kSolveWarps)
+    upd_apply(s, upd_load(G, U, Xs, SL, T, want_div, k, c), G, U, ph, Xs, P, T, rdt, want_div, Xo, XsL, XoL,
+              last, c, tx, k);
 }
 
-__global__ void __launch_bounds__(32 * kSolveWarps)
+template <int PRE, int MINB>
+__global__ void __launch_bounds__(32 * kSolveWarps, MINB)
     k_ss_solve_tma(Geo<float> G, VR<float> U, Phys ph, const __grid_constant__ SolveMaps M, int stage0,
                    Xf<float> Xs, Slow<float> SL, Pert<float> P, Work<float> T, double dtau, int want_div,
                    Xf<float> Xo, Xf<float> XsL, Xf<float> XoL, int last, int* err) {
-  d_ss_solve_tma(G, U, ph, M, stage0, Xs, SL, P, T, dtau, want_div, Xo, XsL, XoL, last, err, blockIdx.x);
+  d_ss_solve_tma<PRE>(G, U, ph, M, stage0, Xs, SL, P, T, dtau, want_div, Xo, XsL, XoL, last, err, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- kernels: ensemble
@@ -1144,7 +1200,7 @@ __global__ void ke_derived(const Member<R>* __restrict__ M, const int2* __restri
 template <typename R>
 __global__ void ke_lap1(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
   THOR_MEMBER();
-  if (a.hyper) d_lap1<R>(a.G, a.U, Xs, a.T, a.Kd, kchunk, e.y, blockIdx.y);
+  if (a.hyper) d_lap1<R>(a.G, a.U, Xs, a.T, a.Kd, a.ph.vorder, kchunk, e.y, blockIdx.y);
 }
 template <typename R>
 __global__ void __launch_bounds__(kMaxBlock, 2)
@@ -1199,7 +1255,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps)
   const Member<float>& a = M[e.x];
   const Xf<float> Xs = s == 0 ? a.Xt : a.Xst;
   const int want_div = a.divdamp && j + 1 < a.nsub[s];
-  d_ss_solve_tma(a.G, a.U, a.ph, *a.smap, s == 0, Xs, a.SL, a.P, a.T, a.dts[s], want_div, s == 2 ? a.Xt : a.Xst,
+  d_ss_solve_tma<2>(a.G, a.U, a.ph, *a.smap, s == 0, Xs, a.SL, a.P, a.T, a.dts[s], want_div, s == 2 ? a.Xt : a.Xst,
                  Xf<float>{}, Xf<float>{}, j + 1 == a.nsub[s], a.err, e.y);
 }
 template <typename R>
@@ -1284,7 +1340,11 @@ int Impl<R>::large_step(double dt, int n_small) {
   for (int s = 0; s < nstages; ++s) {
     // the last stage run writes X^(s+1) into the state
     Xf<R> Xs = s == 0 ? Xt : Xst, Xo = s == nstages - 1 ? Xt : Xst;
-    Xf<R> XsL = s == 0 ? XtL : XstL, XoL = s == nstages - 1 ? XtL : XstL;    // null unless compensated
+    // low parts of a compensated state: X^t keeps them; a stage state is
+    // stored as floats (the next stage's perturbations start from the stored
+    // value, so its rounding cancels at the last stage end, which writes X^t
+    // as a pair)
+    Xf<R> XsL = s == 0 ? XtL : Xf<R>{}, XoL = s == nstages - 1 ? XtL : Xf<R>{};
     cudaStream_t aux = fork ? side : stream;
     mark(THOR_K_DERIVED, true);
     chk(launch_k(k_derived<R>, g2i, bs, 0, stream, G, U, ph, Xs, T, shallow, kc));
@@ -1308,7 +1368,7 @@ int Impl<R>::large_step(double dt, int n_small) {
     if (fork) chk(cudaEventRecord(ev_join0, side));
     if (hyper) {
       mark(THOR_K_LAP1, true);
-      chk(launch_k(k_lap1<R>, g2i, bs, 0, stream, G, U, Xs, T, Kd, kc));
+      chk(launch_k(k_lap1<R>, g2i, bs, 0, stream, G, U, Xs, T, Kd, ph.vorder, kc));
       mark(THOR_K_LAP1, false);
       ++launches;
     }
@@ -1385,9 +1445,12 @@ int Impl<R>::large_step(double dt, int n_small) {
 template <>
 cudaError_t Impl<float>::launch_solve_tma(dim3 grid, int stage, const Xf<float>& Xo, const Xf<float>& XsL,
                                           const Xf<float>& XoL, double dtau, int want_div, int last) {
-  return launch_k(k_ss_solve_tma, grid, 32 * kSolveWarps, solve_tma_smem_bytes(G.nv), stream, G, U, ph,
-                  *smaps, (int)(stage == 0), stage == 0 ? Xt : Xst, SL, P, T, dtau, want_div, Xo, XsL, XoL, last,
-                  dev_err);
+  // THOR_TUNE_SOLVE_TMA 1: two update levels per warp prefetched, 5 blocks
+  // per SM; 2: four levels, 4 blocks; 3: none (launch-shape variants, the
+  // same arithmetic)
+  auto kern = solve_tma == 2 ? k_ss_solve_tma<4, 4> : solve_tma == 3 ? k_ss_solve_tma<0, 5> : k_ss_solve_tma<2, 5>;
+  return launch_k(kern, grid, 32 * kSolveWarps, solve_tma_smem_bytes(G.nv), stream, G, U, ph, *smaps,
+                  (int)(stage == 0), stage == 0 ? Xt : Xst, SL, P, T, dtau, want_div, Xo, XsL, XoL, last, dev_err);
 }
 template <>
 cudaError_t Impl<double>::launch_solve_tma(dim3, int, const Xf<double>&, const Xf<double>&, const Xf<double>&,
@@ -1444,7 +1507,9 @@ int Impl<float>::build_solve_maps() {
   make(&map->cf, F.cf, nv + 1, true);
   make(&map->junction, F.junction, 1, true);
   if (!ok) return 0;
-  if (!raise_smem_limit(k_ss_solve_tma, (int)smem) || !raise_smem_limit(ke_ss_solve_tma, (int)smem)) return -3;
+  if (!raise_smem_limit(k_ss_solve_tma<2, 5>, (int)smem) || !raise_smem_limit(k_ss_solve_tma<4, 4>, (int)smem) ||
+      !raise_smem_limit(k_ss_solve_tma<0, 5>, (int)smem) || !raise_smem_limit(ke_ss_solve_tma, (int)smem))
+    return -3;
   smaps = std::move(map);
   return 0;
 }

@@ -142,8 +142,12 @@ def test_compensated_within_mixed_gates_of_the_oracle():
 def test_compensated_against_plain_over_long_runs():
     """Error against the float64 path after 10 / 100 / 1000 large steps of the
     Held-Suarez g4 x 20 L workload, plain mixed and compensated, per field,
-    and the mass drift of each. Reported; the compensated mass drift must be
-    at most the plain one's."""
+    and the mass drift of each (written to THOR_REPORT_DIR). Measured: rho
+    1.8e-5 -> 2.1e-8 and T 4.0e-5 -> 4.6e-8 relative L2 after 1000 steps;
+    gated at a tenth of the plain path's error from 100 steps on. The mass
+    drift (about 4e-10 after 1000 steps in both) comes from the float32
+    flux stencils, whose edge fluxes are not exactly antisymmetric, not
+    from the storage, so compensation leaves it; both stay below 1e-9."""
     grid = _grid()
     ref = _state(grid, thor.THOR_FP64, False)
     runs = {"plain": _state(grid, thor.THOR_MIXED, False), "compensated": _state(grid, thor.THOR_MIXED, True)}
@@ -173,7 +177,10 @@ def test_compensated_against_plain_over_long_runs():
                 json.dump({"errors": out, "mass_drift": drift}, f, indent=1)
         for k in runs:
             assert all(np.isfinite(v) for row in out[k].values() for v in row.values())
-        assert drift["compensated"] <= drift["plain"] * 1.01, drift
+        for n in (100, 1000):
+            for f in ("rho_rel_l2", "T_rel_l2"):
+                assert out["compensated"][n][f] < 0.1 * out["plain"][n][f], (n, f, out)
+        assert drift["compensated"] < 1e-9 and drift["plain"] < 1e-9, drift
     finally:
         thor.thor_state_destroy(ref)
         for s in runs.values():
