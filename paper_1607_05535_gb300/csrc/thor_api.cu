@@ -985,8 +985,7 @@ int thor_tune(thor_state* s, int knob, int value) {
     return THOR_OK;
   }
   if (knob == THOR_TUNE_SOLVE_TMA) {
-    if (value < 0 || value > 3) return THOR_EINVAL;
-    s->impl->solve_tma = value;
+    s->impl->solve_tma = value != 0;
     return THOR_OK;
   }
   if (knob == THOR_TUNE_COMPENSATED) return s->impl->set_compensated(value != 0);

@@ -40,7 +40,8 @@ cudaError_t launch_k(void (*kern)(K...), dim3 grid, dim3 block, size_t smem, cud
 
 // Pointwise derived quantities at the stage state: p', T', theta, the full
 // 3-D velocity, v_h = M/rho (centres) and v_r = W/rho (interfaces).
-template <typename R>
+// HO: the order-k interpolation of the explicit terms (thor_init.vorder > 1)
+template <typename R, bool HO = false>
 __device__ __forceinline__ void d_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int shallow, int kchunk,
                                           int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
@@ -59,7 +60,7 @@ __device__ __forceinline__ void d_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, W
       R p = ld(U.pb + (k)) + pp;
       R inv = R(1) / rho;
       R Temp = p * inv * inv_Rd;
-      R wc = ph.vorder > 1 ? vint_centre(U, X.w, k, c, S, G.nv)
+      R wc = HO ? vint_centre(U, X.w, k, c, S, G.nv)
                            : ld(U.clo + (k)) * ld(X.w + (i)) + ld(U.chi + (k)) * ld(X.w + (i + S));
       R mx = ld(X.mx + (i)), my = ld(X.my + (i)), mz = ld(X.mz + (i));
       T.pp[i] = pp;
@@ -76,7 +77,7 @@ __device__ __forceinline__ void d_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, W
     if (k >= 1 && k < G.nv) {
       int i = k * S + c;
       R rlo = ld(U.rhob + (k - 1)) + ld(X.rho + (i - S)), rhi = ld(U.rhob + (k)) + ld(X.rho + (i));
-      if (ph.vorder > 1)
+      if constexpr (HO)
         T.vr[i] = ld(X.w + (i)) / vint_iface(U, X.rho, U.rhob, k, c, S, G.nv);
       else
         T.vr[i] = ld(X.w + (i)) / (ld(U.wlo + (k)) * rlo + ld(U.whi + (k)) * rhi);
@@ -88,9 +89,8 @@ __device__ __forceinline__ void d_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, W
 
 // First Laplacians of the hyperdiffusion (Sec. 4), already multiplied by
 // K_d and, for the momentum and temperature terms, by rho.
-template <typename R>
-__device__ __forceinline__ void d_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int vorder, int kchunk, int bx,
-                                       int by) {
+template <typename R, bool HO = false>
+__device__ __forceinline__ void d_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -113,7 +113,7 @@ __device__ __forceinline__ void d_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R 
     if (k >= 1 && k < G.nv) {
       int o = k * S;
       R rlo = ld(U.rhob + (k - 1)) + ld(X.rho + (o - S + c)), rhi = ld(U.rhob + (k)) + ld(X.rho + (o + c));
-      R rif = vorder > 1 ? vint_iface(U, X.rho, U.rhob, k, c, S, G.nv) : ld(U.wlo + (k)) * rlo + ld(U.whi + (k)) * rhi;
+      R rif = HO ? vint_iface(U, X.rho, U.rhob, k, c, S, G.nv) : ld(U.wlo + (k)) * rlo + ld(U.whi + (k)) * rhi;
       T.qvr[o + c] = rif * Kd * apply7(wl, nb, T.vr + o) / ld(U.ri2 + (k));
     } else if (k == 0 || k == G.nv) {
       T.qvr[k * S + c] = 0;
@@ -132,7 +132,7 @@ __device__ __forceinline__ void d_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R 
 // here the traditional Coriolis, 2 Omega sin(lat) r x M on the horizontal
 // momentum only, and the horizontal velocity and w advected without the
 // metric terms the approximation drops)
-template <typename R, bool SH = false>
+template <typename R, bool SH = false, bool HO = false>
 __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
                                             R* d0, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
@@ -208,7 +208,7 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
     for (int j = 0; j < 3; ++j) {
       R ah = sa[j] * inv_r;
       R vlo = 0, vhi = 0;
-      if (ph.vorder > 1) {
+      if constexpr (HO) {
         if (k >= 1) vlo = vint_iface(U, vs[j], (const R*)nullptr, k, c, S, G.nv);
         if (k + 1 < G.nv) vhi = vint_iface(U, vs[j], (const R*)nullptr, k + 1, c, S, G.nv);
       } else {
@@ -225,7 +225,7 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
       A[1] += f * (rz * mx - rx * mz);
       A[2] += f * (rx * my - ry * mx);
       R wlo_c = 0, whi_c = 0;
-      if (ph.vorder > 1) {
+      if constexpr (HO) {
         if (k >= 1) wlo_c = vint_iface(U, (const R*)T.wc, (const R*)nullptr, k, c, S, G.nv);
         if (k + 1 < G.nv) whi_c = vint_iface(U, (const R*)T.wc, (const R*)nullptr, k + 1, c, S, G.nv);
       } else {
@@ -239,7 +239,7 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
       ahz = A[2] - d * rz;
     } else {
       // Coriolis 2 Omega z x (rho v) with the full momentum
-      R wc = ph.vorder > 1 ? vint_centre(U, X.w, k, c, S, G.nv) : ld(U.clo + (k)) * wlo_w + ld(U.chi + (k)) * whi_w;
+      R wc = HO ? vint_centre(U, X.w, k, c, S, G.nv) : ld(U.clo + (k)) * wlo_w + ld(U.chi + (k)) * whi_w;
       R mx = ld(X.mx + (i)), my = ld(X.my + (i));
       R fx = mx + wc * rx, fy = my + wc * ry;
       A[0] += -two_om * fy;
@@ -277,7 +277,7 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
 // (right-hand side of Eq. momr2) and theta at the interfaces; with init, on
 // the same (column, level) grid, also the perturbations at the start of the
 // stage: Phi* = Phi^t - Phi^(s), p* from the nonlinear Eq. theta_to_p.
-template <typename R>
+template <typename R, bool HO = false>
 __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Slow<R> SL,
                                          Pert<R> P, int hyper, int init, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
@@ -314,7 +314,7 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
     if (!ph.hydrostatic) {
       R FW = 0;
       if (hyper) FW = -apply7(wl, nb, T.qvr + k * S) / ld(U.ri2 + (k));
-      const R acr_i = ph.vorder > 1 ? vint_iface(U, (const R*)SL.acr, (const R*)nullptr, k, c, S, G.nv)
+      const R acr_i = HO ? vint_iface(U, (const R*)SL.acr, (const R*)nullptr, k, c, S, G.nv)
                                     : wlo * ld(SL.acr + (i - S)) + whi * ld(SL.acr + (i));
       sw = sw - acr_i + FW;
     }
@@ -407,9 +407,8 @@ __device__ __forceinline__ void d_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> 
   if (c >= G.ncol) return;
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
-  W7x3<R> wg;
-  W7<R> wl;
-  load_w7x3_lap(G.wgrad, S, c, wg, wl);
+  W7x3<R> wg = load_w7x3(G.wgrad, S, c);
+  W7<R> wl = load_w7(G.wlap, S, c);
   R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
   int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
 #pragma unroll 2
@@ -886,23 +885,23 @@ __global__ void k_energy_fix(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Xf<R> XL, cons
 
 // ---------------------------------------------------------------- kernels: one state
 
-template <typename R>
+template <typename R, bool HO>
 __global__ void k_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int shallow, int kchunk) {
-  d_derived<R>(G, U, ph, X, T, shallow, kchunk, blockIdx.x, blockIdx.y);
+  d_derived<R, HO>(G, U, ph, X, T, shallow, kchunk, blockIdx.x, blockIdx.y);
 }
-template <typename R>
-__global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int vorder, int kchunk) {
-  d_lap1<R>(G, U, X, T, Kd, vorder, kchunk, blockIdx.x, blockIdx.y);
+template <typename R, bool HO>
+__global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk) {
+  d_lap1<R, HO>(G, U, X, T, Kd, kchunk, blockIdx.x, blockIdx.y);
 }
-template <typename R, bool SH>
+template <typename R, bool SH, bool HO>
 __global__ void __launch_bounds__(kMaxBlock, 2)
     k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper, R* d0, int kchunk) {
-  d_slow<R, SH>(G, U, ph, X, T, SL, hyper, d0, kchunk, blockIdx.x, blockIdx.y);
+  d_slow<R, SH, HO>(G, U, ph, X, T, SL, hyper, d0, kchunk, blockIdx.x, blockIdx.y);
 }
-template <typename R>
+template <typename R, bool HO>
 __global__ void k_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Slow<R> SL, Pert<R> P, int hyper,
                          int init, int kchunk) {
-  d_slow_w<R>(G, U, ph, Xt, X, T, SL, P, hyper, init, kchunk, blockIdx.x, blockIdx.y);
+  d_slow_w<R, HO>(G, U, ph, Xt, X, T, SL, P, hyper, init, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
 __global__ void k_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Pert<R> P, Xf<R> XtL,
@@ -1075,8 +1074,7 @@ __device__ __forceinline__ void solve_sweeps(const SolveSm& s, double* sx, const
 }
 
 // Operands of the final updates (Eqs. dens2, pt2, theta_to_p) of one cell
-// that do not depend on the solved W*: loaded before the sweeps end, so that
-// their latency hides behind the float64 chain.
+// that do not depend on the solved W*.
 struct UpdOps {
   float thl, thh, cb, ps, ths, dsc, dhm;
 };
@@ -1117,9 +1115,7 @@ __device__ __forceinline__ void upd_apply(const SolveSm& s, const UpdOps& o, con
   if (last) stage_end_cell(Xs, Xo, XsL, XoL, P, rho_new, th_new, wl, k, i, S, nv);
 }
 
-// M: the state's descriptors, in kernel-parameter or global memory; PRE:
-// update levels per warp whose operands are loaded before the sweeps
-template <int PRE>
+// M: the state's descriptors, in kernel-parameter or global memory
 __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<float>& U, const Phys& ph,
                                                const SolveMaps& M, int stage0, const Xf<float>& Xs,
                                                const Slow<float>& SL, const Pert<float>& P, const Work<float>& T,
@@ -1148,36 +1144,21 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
     return;
   }
   const float rdt = (float)dtau, g = ph.g_f;
-  // every warp loads the W*-independent operands of its first kPre update
-  // levels (k = warp, warp + 8, ...) before the sweeps, which warps 0 and 1
-  // run; the loads of the other six warps land while the chain runs
-  constexpr int kPre = PRE;
-  const bool col = c < G.ncol;
-  UpdOps pre[kPre > 0 ? kPre : 1];
-#pragma unroll
-  for (int q = 0; q < kPre; ++q) {
-    const int k = warp + q * kSolveWarps;
-    if (col && k < nv) pre[q] = upd_load(G, U, Xs, SL, T, want_div, k, c);
-  }
   if (warp < 2) solve_sweeps(s, sx, U, rdt, g, ph.delta_f, nv, tx, warp);
   __syncthreads();
-  if (!col) return;
-#pragma unroll
-  for (int q = 0; q < kPre; ++q) {
-    const int k = warp + q * kSolveWarps;
-    if (k < nv) upd_apply(s, pre[q], G, U, ph, Xs, P, T, rdt, want_div, Xo, XsL, XoL, last, c, tx, k);
-  }
-  for (int k = warp + kPre * kSolveWarps; k < nv; k += kSolveWarps)
+  if (c >= G.ncol) return;
+  // the eight warps share the levels of the final updates
+#pragma unroll 4
+  for (int k = warp; k < nv; k += kSolveWarps)
     upd_apply(s, upd_load(G, U, Xs, SL, T, want_div, k, c), G, U, ph, Xs, P, T, rdt, want_div, Xo, XsL, XoL,
               last, c, tx, k);
 }
 
-template <int PRE, int MINB>
-__global__ void __launch_bounds__(32 * kSolveWarps, MINB)
+__global__ void __launch_bounds__(32 * kSolveWarps)
     k_ss_solve_tma(Geo<float> G, VR<float> U, Phys ph, const __grid_constant__ SolveMaps M, int stage0,
                    Xf<float> Xs, Slow<float> SL, Pert<float> P, Work<float> T, double dtau, int want_div,
                    Xf<float> Xo, Xf<float> XsL, Xf<float> XoL, int last, int* err) {
-  d_ss_solve_tma<PRE>(G, U, ph, M, stage0, Xs, SL, P, T, dtau, want_div, Xo, XsL, XoL, last, err, blockIdx.x);
+  d_ss_solve_tma(G, U, ph, M, stage0, Xs, SL, P, T, dtau, want_div, Xo, XsL, XoL, last, err, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- kernels: ensemble
@@ -1195,27 +1176,41 @@ __global__ void __launch_bounds__(32 * kSolveWarps, MINB)
 template <typename R>
 __global__ void ke_derived(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
   THOR_MEMBER();
-  d_derived<R>(a.G, a.U, a.ph, Xs, a.T, a.shallow, kchunk, e.y, blockIdx.y);
+  if (a.ph.vorder > 1)
+    d_derived<R, true>(a.G, a.U, a.ph, Xs, a.T, a.shallow, kchunk, e.y, blockIdx.y);
+  else
+    d_derived<R>(a.G, a.U, a.ph, Xs, a.T, a.shallow, kchunk, e.y, blockIdx.y);
 }
 template <typename R>
 __global__ void ke_lap1(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
   THOR_MEMBER();
-  if (a.hyper) d_lap1<R>(a.G, a.U, Xs, a.T, a.Kd, a.ph.vorder, kchunk, e.y, blockIdx.y);
+  if (a.hyper && a.ph.vorder > 1)
+    d_lap1<R, true>(a.G, a.U, Xs, a.T, a.Kd, kchunk, e.y, blockIdx.y);
+  else if (a.hyper)
+    d_lap1<R>(a.G, a.U, Xs, a.T, a.Kd, kchunk, e.y, blockIdx.y);
 }
 template <typename R>
 __global__ void __launch_bounds__(kMaxBlock, 2)
     ke_slow(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
   THOR_MEMBER();
   R* d0 = s == 0 && a.divdamp ? a.T.dd0 : nullptr;
-  if (a.shallow)
+  const bool ho = a.ph.vorder > 1;
+  if (a.shallow && ho)
+    d_slow<R, true, true>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, d0, kchunk, e.y, blockIdx.y);
+  else if (a.shallow)
     d_slow<R, true>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, d0, kchunk, e.y, blockIdx.y);
+  else if (ho)
+    d_slow<R, false, true>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, d0, kchunk, e.y, blockIdx.y);
   else
     d_slow<R, false>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, d0, kchunk, e.y, blockIdx.y);
 }
 template <typename R>
 __global__ void ke_slow_w(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
   THOR_MEMBER();
-  d_slow_w<R>(a.G, a.U, a.ph, a.Xt, Xs, a.T, a.SL, a.P, a.hyper, 1, kchunk, e.y, blockIdx.y);
+  if (a.ph.vorder > 1)
+    d_slow_w<R, true>(a.G, a.U, a.ph, a.Xt, Xs, a.T, a.SL, a.P, a.hyper, 1, kchunk, e.y, blockIdx.y);
+  else
+    d_slow_w<R>(a.G, a.U, a.ph, a.Xt, Xs, a.T, a.SL, a.P, a.hyper, 1, kchunk, e.y, blockIdx.y);
 }
 template <typename R>
 __global__ void __launch_bounds__(64)
@@ -1255,7 +1250,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps)
   const Member<float>& a = M[e.x];
   const Xf<float> Xs = s == 0 ? a.Xt : a.Xst;
   const int want_div = a.divdamp && j + 1 < a.nsub[s];
-  d_ss_solve_tma<2>(a.G, a.U, a.ph, *a.smap, s == 0, Xs, a.SL, a.P, a.T, a.dts[s], want_div, s == 2 ? a.Xt : a.Xst,
+  d_ss_solve_tma(a.G, a.U, a.ph, *a.smap, s == 0, Xs, a.SL, a.P, a.T, a.dts[s], want_div, s == 2 ? a.Xt : a.Xst,
                  Xf<float>{}, Xf<float>{}, j + 1 == a.nsub[s], a.err, e.y);
 }
 template <typename R>
@@ -1347,7 +1342,8 @@ int Impl<R>::large_step(double dt, int n_small) {
     Xf<R> XsL = s == 0 ? XtL : Xf<R>{}, XoL = s == nstages - 1 ? XtL : Xf<R>{};
     cudaStream_t aux = fork ? side : stream;
     mark(THOR_K_DERIVED, true);
-    chk(launch_k(k_derived<R>, g2i, bs, 0, stream, G, U, ph, Xs, T, shallow, kc));
+    const bool ho = ph.vorder > 1;
+    chk(launch_k(ho ? k_derived<R, true> : k_derived<R, false>, g2i, bs, 0, stream, G, U, ph, Xs, T, shallow, kc));
     mark(THOR_K_DERIVED, false);
     ++launches;
     if (fork) {
@@ -1368,16 +1364,19 @@ int Impl<R>::large_step(double dt, int n_small) {
     if (fork) chk(cudaEventRecord(ev_join0, side));
     if (hyper) {
       mark(THOR_K_LAP1, true);
-      chk(launch_k(k_lap1<R>, g2i, bs, 0, stream, G, U, Xs, T, Kd, ph.vorder, kc));
+      chk(launch_k(ho ? k_lap1<R, true> : k_lap1<R, false>, g2i, bs, 0, stream, G, U, Xs, T, Kd, kc));
       mark(THOR_K_LAP1, false);
       ++launches;
     }
     mark(THOR_K_SLOW, true);
-    chk(launch_k(shallow ? k_slow<R, true> : k_slow<R, false>, g2, bs, 0, stream, G, U, ph, Xs, T, SL, hyper,
+    auto slow = shallow ? (ho ? k_slow<R, true, true> : k_slow<R, true, false>)
+                        : (ho ? k_slow<R, false, true> : k_slow<R, false, false>);
+    chk(launch_k(slow, g2, bs, 0, stream, G, U, ph, Xs, T, SL, hyper,
                  s == 0 && divdamp ? T.dd0 : (R*)nullptr, kc));
     mark(THOR_K_SLOW, false);
     mark(THOR_K_SLOW_W, true);
-    chk(launch_k(k_slow_w<R>, g2i, bs, 0, stream, G, U, ph, Xt, Xs, T, SL, P, hyper, 0, kc));
+    chk(launch_k(ho ? k_slow_w<R, true> : k_slow_w<R, false>, g2i, bs, 0, stream, G, U, ph, Xt, Xs, T, SL, P, hyper,
+                 0, kc));
     mark(THOR_K_SLOW_W, false);
     if (fork) {
       chk(cudaEventRecord(ev_fork, stream));
@@ -1445,11 +1444,7 @@ int Impl<R>::large_step(double dt, int n_small) {
 template <>
 cudaError_t Impl<float>::launch_solve_tma(dim3 grid, int stage, const Xf<float>& Xo, const Xf<float>& XsL,
                                           const Xf<float>& XoL, double dtau, int want_div, int last) {
-  // THOR_TUNE_SOLVE_TMA 1: two update levels per warp prefetched, 5 blocks
-  // per SM; 2: four levels, 4 blocks; 3: none (launch-shape variants, the
-  // same arithmetic)
-  auto kern = solve_tma == 2 ? k_ss_solve_tma<4, 4> : solve_tma == 3 ? k_ss_solve_tma<0, 5> : k_ss_solve_tma<2, 5>;
-  return launch_k(kern, grid, 32 * kSolveWarps, solve_tma_smem_bytes(G.nv), stream, G, U, ph, *smaps,
+  return launch_k(k_ss_solve_tma, grid, 32 * kSolveWarps, solve_tma_smem_bytes(G.nv), stream, G, U, ph, *smaps,
                   (int)(stage == 0), stage == 0 ? Xt : Xst, SL, P, T, dtau, want_div, Xo, XsL, XoL, last, dev_err);
 }
 template <>
@@ -1507,9 +1502,7 @@ int Impl<float>::build_solve_maps() {
   make(&map->cf, F.cf, nv + 1, true);
   make(&map->junction, F.junction, 1, true);
   if (!ok) return 0;
-  if (!raise_smem_limit(k_ss_solve_tma<2, 5>, (int)smem) || !raise_smem_limit(k_ss_solve_tma<4, 4>, (int)smem) ||
-      !raise_smem_limit(k_ss_solve_tma<0, 5>, (int)smem) || !raise_smem_limit(ke_ss_solve_tma, (int)smem))
-    return -3;
+  if (!raise_smem_limit(k_ss_solve_tma, (int)smem) || !raise_smem_limit(ke_ss_solve_tma, (int)smem)) return -3;
   smaps = std::move(map);
   return 0;
 }
