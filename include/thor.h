@@ -360,9 +360,9 @@ int thor_zonal_read_w(thor_state* state, int nlat, double* out, size_t n, long l
  * thor_diag and checkpoints (then twice the size) use the full pairs. The
  * RK stage states and the tendencies stay float. The first use allocates
  * the low parts (6 planes), zeroed; 0 frees them and rounds the state to
- * its float parts. Synchronises the state's stream. Compensated states cannot
- * join an ensemble (thor_ensemble_step returns THOR_EINVAL); THOR_EINVAL
- * for THOR_FP64 states. Default 0. */
+ * its float parts. Synchronises the state's stream. Ensembles step
+ * compensated members the same way. THOR_EINVAL for THOR_FP64 states.
+ * Default 1 for THOR_MIXED states (thor_state_init allocates the low parts). */
 
 /* Launch-shape autotuner (an extension; the paper fixes no launch shapes).
  * Times `steps` large steps of (n_small, dt) for every levels-per-thread
@@ -384,7 +384,7 @@ int thor_autotune(thor_state* state, int n_small, double dt, int steps, int* kch
  * thor_profile(state, 1). enable = 0 stops recording. */
 enum {
   THOR_K_DERIVED = 0, THOR_K_LAP1, THOR_K_SLOW, THOR_K_SLOW_W, THOR_K_STAGE_INIT,
-  THOR_K_SS_GRAD, THOR_K_SS_MOM, THOR_K_SS_SOLVE, THOR_K_PHYSICS, THOR_K_SS_FLUX,
+  THOR_K_SS_LAPD, THOR_K_SS_MOM, THOR_K_SS_SOLVE, THOR_K_PHYSICS, THOR_K_SS_FLUX,
   THOR_K_SS_FACTOR, THOR_K_COUNT
 };
 int thor_profile(thor_state* state, int enable);

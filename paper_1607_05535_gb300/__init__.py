@@ -43,7 +43,7 @@ EXPORTED = [
 ]
 
 # kernel ids of thor_profile_read
-KERNELS = ["derived", "lap1", "slow", "slow_w", "stage_init", "ss_grad", "ss_mom", "ss_solve",
+KERNELS = ["derived", "lap1", "slow", "slow_w", "stage_init", "ss_lapd", "ss_mom", "ss_solve",
            "physics", "ss_flux", "ss_factor"]
 
 

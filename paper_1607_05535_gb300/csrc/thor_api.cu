@@ -195,7 +195,7 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   R** pc[] = {&P.rho, &P.th, &P.p};
   for (R** p : pc) *p = cv.take<R>(C);
   P.m4 = cv.take<R>(4 * C);
-  T.g4 = cv.take<R>(4 * C);
+  T.lp = cv.take<R>(2 * C);
   P.w = cv.take<R>(F);
   I.F.inv = cv.take<double>(F);
   I.F.cf = cv.take<double>(F);
@@ -812,6 +812,8 @@ int thor_state_init(thor_grid* grid, const thor_planet* pl, const thor_init* in,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = in->precision == THOR_FP64 ? thor::make_impl<double>(grid, *pl, *in, st, s->impl)
                                       : thor::make_impl<float>(grid, *pl, *in, st, s->impl);
+  // mixed states keep X^t as compensated float pairs unless switched off
+  if (!rc && in->precision == THOR_MIXED) rc = s->impl->set_compensated(1);
   if (rc) {
     delete s;
     return rc;

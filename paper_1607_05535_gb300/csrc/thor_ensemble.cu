@@ -42,6 +42,7 @@ struct EnsImpl : EnsBase {
   bool planned = false;
   std::vector<int> key_n;
   std::vector<double> key_dt;
+  std::vector<const void*> key_lo;    // members' low-part planes (compensated state) at planning
   int key_kc = 0, key_bs = 0;
   cudaGraphExec_t gexec = nullptr;
   long long graph_launches = 0;
@@ -142,14 +143,18 @@ struct EnsImpl : EnsBase {
     key_dt.assign(dt, dt + n);
     key_kc = kchunk;
     key_bs = block;
+    key_lo.clear();
+    for (const Impl<R>* I : mem) key_lo.push_back(I->XtL.rho);
     planned = true;
     return THOR_OK;
   }
 
   int step(int n_large, const int* n_small, const double* dt) override {
     const int n = (int)mem.size();
+    bool lo_same = key_lo.size() == mem.size();
+    for (size_t i = 0; lo_same && i < mem.size(); ++i) lo_same = key_lo[i] == mem[i]->XtL.rho;
     if (!planned || key_kc != kchunk || key_bs != block || !std::equal(key_n.begin(), key_n.end(), n_small) ||
-        !std::equal(key_dt.begin(), key_dt.end(), dt)) {
+        !std::equal(key_dt.begin(), key_dt.end(), dt) || !lo_same) {
       int rc = build_plan(n_small, dt);
       if (rc) return rc;
     }
@@ -269,7 +274,7 @@ int check_steps(const thor_ensemble* E, int n_large, const int* n_small, const d
   if (!E || n_large < 0 || !n_small || !dt) return THOR_EINVAL;
   for (size_t i = 0; i < E->members.size(); ++i) {
     if (n_small[i] < 2 || (n_small[i] % 2) || !(dt[i] > 0)) return THOR_EINVAL;
-    if (E->members[i]->closure.net || E->members[i]->impl->compensated) return THOR_EINVAL;
+    if (E->members[i]->closure.net) return THOR_EINVAL;
   }
   return THOR_OK;
 }

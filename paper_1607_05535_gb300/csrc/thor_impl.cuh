@@ -23,7 +23,7 @@ struct Work {
   R *qvr;                          // interfaces
   R *dd;                           // 3-D divergence (small step)
   R *dd0;                          // 3-D divergence of X^t (first small step of every stage)
-  R *g4;                           // [nv][colp][4]: its horizontal gradient (x, y, z) and p*
+  R *lp;                           // [nv][colp][2]: the Laplacian of that D and the cell's p*
   R *ca, *cb, *cc;                 // per-cell parts of the column equations (a, b, c)
   R *dhm;                          // horizontal divergence of the new M*
   R *psurf;                        // [colp] surface pressure (physics)
@@ -60,6 +60,7 @@ struct Member {
   VR<R> U;
   Phys ph;
   Xf<R> Xt, Xst;
+  Xf<R> XtL;                       // low parts of a compensated X^t (null pointers: none)
   Work<R> T;
   Slow<R> SL;
   Pert<R> P;
@@ -302,6 +303,7 @@ struct Impl : ImplBase {
     m.ph = ph;
     m.Xt = Xt;
     m.Xst = Xst;
+    m.XtL = XtL;
     m.T = T;
     m.SL = SL;
     m.P = P;

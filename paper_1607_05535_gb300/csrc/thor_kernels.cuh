@@ -252,6 +252,26 @@ __device__ __forceinline__ void st4(double* base, size_t cell, double x, double 
   reinterpret_cast<double2*>(base)[2 * cell + 1] = make_double2(z, w);
 }
 
+// two values of one cell stored together ([level][colp][2] planes)
+template <typename R>
+struct Q2 {
+  R x, y;
+};
+__device__ __forceinline__ Q2<float> ld2(const float* base, size_t cell) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(base) + cell);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ Q2<double> ld2(const double* base, size_t cell) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(base) + cell);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void st2(float* base, size_t cell, float x, float y) {
+  reinterpret_cast<float2*>(base)[cell] = make_float2(x, y);
+}
+__device__ __forceinline__ void st2(double* base, size_t cell, double x, double y) {
+  reinterpret_cast<double2*>(base)[cell] = make_double2(x, y);
+}
+
 struct Nbr7 {
   int n[7];
 };

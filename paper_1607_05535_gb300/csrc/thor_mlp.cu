@@ -907,6 +907,9 @@ int coarse_t(thor_state* fine, thor_state* coarse, const std::vector<int>& start
     rc = THOR_ECUDA;
   } else {
     dim3 grid((C->G.ncol + 127) / 128, C->G.nv + 1);
+    // the coarse state's fields are replaced: a compensated one's low parts restart at zero
+    if (C->lo_buf)
+      cudaMemsetAsync(C->lo_buf, 0, (size_t)(6 * C->G.nv + 1) * C->G.colp * sizeof(R), st);
     k_coarse_grain<R><<<grid, 128, 0, st>>>(C->G, F->Xt, F->G.colp, C->Xt, d_start, d_member, d_weight);
     C->launches += 1;
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st)) rc = THOR_ECUDA;

@@ -277,9 +277,13 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
 // (right-hand side of Eq. momr2) and theta at the interfaces; with init, on
 // the same (column, level) grid, also the perturbations at the start of the
 // stage: Phi* = Phi^t - Phi^(s), p* from the nonlinear Eq. theta_to_p.
+// XtL (init only): the low parts of a compensated X^t (null pointers when X
+// is X^t itself or the state is not compensated); the stage state is stored
+// as floats
 template <typename R, bool HO = false>
 __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Slow<R> SL,
-                                         Pert<R> P, int hyper, int init, int kchunk, int bx, int by) {
+                                         Pert<R> P, int hyper, int init, int kchunk, int bx, int by,
+                                         Xf<R> XtL = Xf<R>{}) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -291,15 +295,21 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
   for (int k = k0; k < k1; ++k) {
     const int i = k * S + c;
     // stage start (unless k_stage_init does it)
+    auto dif = [&](const R* a, const R* b, const R* al) {
+      R d = ld(a + (i)) - ld(b + (i));
+      if (al) d += ld(al + (i));
+      return d;
+    };
     if (init && k < G.nv) {
-      P.rho[i] = ld(Xt.rho + (i)) - ld(X.rho + (i));
-      st4(P.m4, i, ld(Xt.mx + (i)) - ld(X.mx + (i)), ld(Xt.my + (i)) - ld(X.my + (i)),
-          ld(Xt.mz + (i)) - ld(X.mz + (i)), ld(T.theta + (i)));
-      P.th[i] = ld(Xt.th + (i)) - ld(X.th + (i));
-      R ppt = eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), ld(Xt.th + (i)), gamma);
+      P.rho[i] = dif(Xt.rho, X.rho, XtL.rho);
+      st4(P.m4, i, dif(Xt.mx, X.mx, XtL.mx), dif(Xt.my, X.my, XtL.my), dif(Xt.mz, X.mz, XtL.mz),
+          ld(T.theta + (i)));
+      P.th[i] = dif(Xt.th, X.th, XtL.th);
+      const R tht = XtL.th ? ld(Xt.th + (i)) + ld(XtL.th + (i)) : ld(Xt.th + (i));
+      R ppt = eos_dev<R>(ld(U.pb + (k)), ld(U.thb + (k)), tht, gamma);
       P.p[i] = ppt - ld(T.pp + (i));
     }
-    if (init) P.w[i] = ld(Xt.w + (i)) - ld(X.w + (i));
+    if (init) P.w[i] = dif(Xt.w, X.w, XtL.w);
     // slow terms of Eq. momr2
     if (k == 0 || k == G.nv) {
       SL.sw[i] = 0;
@@ -372,26 +382,23 @@ __device__ __forceinline__ void d_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> X
 // ---------------------------------------------------------------- small step
 
 template <typename R>
-// horizontal gradient G = grad_h D of the 3-D divergence D of the total
-// momentum (divergence damping, Sec. 4): D is d0 in the first small step of a
-// stage and, later, the D the previous column step formed; stored packed with
-// the cell's p*
-__device__ __forceinline__ void d_ss_grad(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, const R* pstar, int kchunk,
+// Divergence damping, first stencil (Sec. 4, reading R5: the damping is
+// -K_d grad_h(lap D)): the Laplacian of the 3-D divergence D of the total
+// momentum, D = d0 in the first small step of a stage and later the D the
+// previous column step formed; stored packed with the cell's p* (the
+// momentum step gathers both)
+__device__ __forceinline__ void d_ss_lapd(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, const R* pstar, int kchunk,
                                           int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
-  W7x3<R> wg = load_w7x3(G.wgrad, S, c);
+  W7<R> wl = load_w7(G.wlap, S, c);
   int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     const int o = k * S, i = o + c;
-    R gx, gy, gz;
-    grad7(wg, nb, dsrc + o, gx, gy, gz);
-    R inv_r = ld(U.inv_rc + (k));
-    // p* of the cell beside G: the momentum step gathers both
-    st4(T.g4, i, gx * inv_r, gy * inv_r, gz * inv_r, ld(pstar + (i)));
+    st2(T.lp, i, apply7(wl, nb, dsrc + o) * ld(U.inv_rc2 + (k)), ld(pstar + (i)));
   }
 }
 
@@ -408,7 +415,6 @@ __device__ __forceinline__ void d_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> 
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
   W7x3<R> wg = load_w7x3(G.wgrad, S, c);
-  W7<R> wl = load_w7(G.wlap, S, c);
   R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
   int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
 #pragma unroll 2
@@ -418,23 +424,23 @@ __device__ __forceinline__ void d_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> 
     R ddx = 0, ddy = 0, ddz = 0;
     R gx = 0, gy = 0, gz = 0;
     if (divdamp) {
-      // one packed gather per neighbour: G for the Laplacian, p* for the gradient
+      // one packed gather per neighbour: the Laplacian of D and p*, both
+      // through the (projected) gradient weights
       R ax = 0, ay = 0, az = 0;
 #pragma unroll
       for (int j = 0; j < 7; ++j) {
-        const Q4<R> q = ld4(T.g4, (size_t)(o + nb.n[j]));
-        ax += wl.v[j] * q.x;
-        ay += wl.v[j] * q.y;
-        az += wl.v[j] * q.z;
-        gx += wg.x[j] * q.w;
-        gy += wg.y[j] * q.w;
-        gz += wg.z[j] * q.w;
+        const Q2<R> q = ld2(T.lp, (size_t)(o + nb.n[j]));
+        ax += wg.x[j] * q.x;
+        ay += wg.y[j] * q.x;
+        az += wg.z[j] * q.x;
+        gx += wg.x[j] * q.y;
+        gy += wg.y[j] * q.y;
+        gz += wg.z[j] * q.y;
       }
-      R s = -Kd * ld(U.inv_rc2 + (k));
+      R s = -Kd * inv_r;
       ddx = s * ax;
       ddy = s * ay;
       ddz = s * az;
-      project(rx, ry, rz, ddx, ddy, ddz);
     } else {
       grad7(wg, nb, P.p + o, gx, gy, gz);
     }
@@ -909,8 +915,8 @@ __global__ void k_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work
   d_stage_init<R>(G, U, ph, Xt, X, T, P, XtL, XL, zero, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R>
-__global__ void k_ss_grad(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, const R* pstar, int kchunk) {
-  d_ss_grad<R>(G, U, T, dsrc, pstar, kchunk, blockIdx.x, blockIdx.y);
+__global__ void k_ss_lapd(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, const R* pstar, int kchunk) {
+  d_ss_lapd<R>(G, U, T, dsrc, pstar, kchunk, blockIdx.x, blockIdx.y);
 }
 // LAST: the last small step of a stage (a separate instantiation, so the
 // other small steps carry no registers for the stage end)
@@ -1207,10 +1213,11 @@ __global__ void __launch_bounds__(kMaxBlock, 2)
 template <typename R>
 __global__ void ke_slow_w(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
   THOR_MEMBER();
+  const Xf<R> XtL = s == 0 ? Xf<R>{} : a.XtL;      // stage 0: X^(s) is X^t, pair and all
   if (a.ph.vorder > 1)
-    d_slow_w<R, true>(a.G, a.U, a.ph, a.Xt, Xs, a.T, a.SL, a.P, a.hyper, 1, kchunk, e.y, blockIdx.y);
+    d_slow_w<R, true>(a.G, a.U, a.ph, a.Xt, Xs, a.T, a.SL, a.P, a.hyper, 1, kchunk, e.y, blockIdx.y, XtL);
   else
-    d_slow_w<R>(a.G, a.U, a.ph, a.Xt, Xs, a.T, a.SL, a.P, a.hyper, 1, kchunk, e.y, blockIdx.y);
+    d_slow_w<R>(a.G, a.U, a.ph, a.Xt, Xs, a.T, a.SL, a.P, a.hyper, 1, kchunk, e.y, blockIdx.y, XtL);
 }
 template <typename R>
 __global__ void __launch_bounds__(64)
@@ -1219,17 +1226,17 @@ __global__ void __launch_bounds__(64)
   d_ss_factor<R>(a.G, a.U, a.ph, a.SL, a.F, a.dts[s], e.y, 0);
 }
 template <typename R>
-__global__ void ke_ss_grad(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int j,
+__global__ void ke_ss_lapd(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int j,
                            int kchunk) {
   THOR_MEMBER();
-  if (a.divdamp) d_ss_grad<R>(a.G, a.U, a.T, j == 0 ? a.T.dd0 : a.T.dd, a.P.p, kchunk, e.y, blockIdx.y);
+  if (a.divdamp) d_ss_lapd<R>(a.G, a.U, a.T, j == 0 ? a.T.dd0 : a.T.dd, a.P.p, kchunk, e.y, blockIdx.y);
 }
 template <typename R>
 __global__ void ke_ss_mom(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int j,
                           int kchunk) {
   THOR_MEMBER();
-  d_ss_mom<R>(a.G, a.U, a.SL, a.P, a.T, (R)a.dts[s], a.Kd, a.divdamp, Xs, s == 2 ? a.Xt : a.Xst, Xf<R>{},
-              Xf<R>{}, j + 1 == a.nsub[s], kchunk, e.y, blockIdx.y);
+  d_ss_mom<R>(a.G, a.U, a.SL, a.P, a.T, (R)a.dts[s], a.Kd, a.divdamp, Xs, s == 2 ? a.Xt : a.Xst,
+              s == 0 ? a.XtL : Xf<R>{}, s == 2 ? a.XtL : Xf<R>{}, j + 1 == a.nsub[s], kchunk, e.y, blockIdx.y);
 }
 template <typename R>
 __global__ void ke_ss_flux(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
@@ -1241,8 +1248,8 @@ __global__ void __launch_bounds__(64)
     ke_ss_solve(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int j) {
   THOR_MEMBER();
   const int want_div = a.divdamp && j + 1 < a.nsub[s];
-  d_ss_solve<R>(a.G, a.U, a.ph, Xs, a.SL, a.P, a.T, a.F, a.dts[s], want_div, s == 2 ? a.Xt : a.Xst, Xf<R>{},
-                Xf<R>{}, j + 1 == a.nsub[s], e.y, 0);
+  d_ss_solve<R>(a.G, a.U, a.ph, Xs, a.SL, a.P, a.T, a.F, a.dts[s], want_div, s == 2 ? a.Xt : a.Xst,
+                s == 0 ? a.XtL : Xf<R>{}, s == 2 ? a.XtL : Xf<R>{}, j + 1 == a.nsub[s], e.y, 0);
 }
 __global__ void __launch_bounds__(32 * kSolveWarps)
     ke_ss_solve_tma(const Member<float>* __restrict__ M, const int2* __restrict__ map, int s, int j) {
@@ -1251,7 +1258,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps)
   const Xf<float> Xs = s == 0 ? a.Xt : a.Xst;
   const int want_div = a.divdamp && j + 1 < a.nsub[s];
   d_ss_solve_tma(a.G, a.U, a.ph, *a.smap, s == 0, Xs, a.SL, a.P, a.T, a.dts[s], want_div, s == 2 ? a.Xt : a.Xst,
-                 Xf<float>{}, Xf<float>{}, j + 1 == a.nsub[s], a.err, e.y);
+                 s == 0 ? a.XtL : Xf<float>{}, s == 2 ? a.XtL : Xf<float>{}, j + 1 == a.nsub[s], a.err, e.y);
 }
 template <typename R>
 __global__ void ke_surface_p(const Member<R>* __restrict__ M, const int2* __restrict__ map) {
@@ -1263,7 +1270,7 @@ template <typename R>
 __global__ void ke_physics(const Member<R>* __restrict__ M, const int2* __restrict__ map, int kchunk) {
   const int2 e = map[blockIdx.x];
   const Member<R>& a = M[e.x];
-  if (a.forcing) d_physics<R>(a.G, a.U, a.ph, a.Xt, Xf<R>{}, a.T, a.forcing, a.dt, a.hj_dT, kchunk, e.y, blockIdx.y);
+  if (a.forcing) d_physics<R>(a.G, a.U, a.ph, a.Xt, a.XtL, a.T, a.forcing, a.dt, a.hj_dT, kchunk, e.y, blockIdx.y);
 }
 #undef THOR_MEMBER
 
@@ -1356,9 +1363,9 @@ int Impl<R>::large_step(double dt, int n_small) {
     ++launches;
     const bool early_grad = divdamp && s > 0;    // D of X^t is ready before the slow terms
     if (early_grad) {
-      mark(THOR_K_SS_GRAD, true);
-      chk(launch_k(k_ss_grad<R>, g2, bs, 0, aux, G, U, T, (const R*)T.dd0, (const R*)P.p, kc));
-      mark(THOR_K_SS_GRAD, false);
+      mark(THOR_K_SS_LAPD, true);
+      chk(launch_k(k_ss_lapd<R>, g2, bs, 0, aux, G, U, T, (const R*)T.dd0, (const R*)P.p, kc));
+      mark(THOR_K_SS_LAPD, false);
       ++launches;
     }
     if (fork) chk(cudaEventRecord(ev_join0, side));
@@ -1393,10 +1400,10 @@ int Impl<R>::large_step(double dt, int n_small) {
     for (int j = 0; j < nsub[s]; ++j) {
       // D: of X^t in the first small step, then from the previous column step
       if (divdamp && !(j == 0 && early_grad)) {
-        mark(THOR_K_SS_GRAD, true);
-        chk(launch_k(k_ss_grad<R>, g2, bs, 0, stream, G, U, T, (const R*)(j == 0 ? T.dd0 : T.dd), (const R*)P.p,
+        mark(THOR_K_SS_LAPD, true);
+        chk(launch_k(k_ss_lapd<R>, g2, bs, 0, stream, G, U, T, (const R*)(j == 0 ? T.dd0 : T.dd), (const R*)P.p,
                      kc));
-        mark(THOR_K_SS_GRAD, false);
+        mark(THOR_K_SS_LAPD, false);
         ++launches;
       }
       // the last small step of a stage also ends the stage: X^(s+1) = X^(s) + X*
@@ -1542,7 +1549,7 @@ int ensemble_large_step(const EnsPlan<R>& E, cudaStream_t stream, long long* lau
       const int nb = E.active[s][j], nbc = E.activec[s][j];
       const dim3 a2(nb, yc);
       if (E.any_divdamp) {
-        ke_ss_grad<R><<<a2, bs, 0, stream>>>(M, E.map, s, j, kc);
+        ke_ss_lapd<R><<<a2, bs, 0, stream>>>(M, E.map, s, j, kc);
         ++n;
       }
       ke_ss_mom<R><<<a2, bs, 0, stream>>>(M, E.map, s, j, kc);

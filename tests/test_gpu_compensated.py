@@ -1,6 +1,7 @@
-"""The compensated state of the mixed path (THOR_TUNE_COMPENSATED): every
-prognostic field kept as a float pair hi + lo, the stage ends, physics and
-fixer adding their increments with an error-free sum.
+"""The compensated state of the mixed path (THOR_TUNE_COMPENSATED, on by
+default for mixed states): every prognostic field of X^t kept as a float
+pair hi + lo, the last stage end, physics and fixer adding their increments
+with an error-free sum.
 
 Checked here: the pair carries a float64 value through thor_state_set /
 thor_state_get to about 2^-48 of it; compensated steps in float64 parity
@@ -40,8 +41,8 @@ def _grid(wl=WL):
 
 def _state(grid, precision, compensated, wl=WL):
     s = thor.thor_state_init(grid, planet_struct(wl.planet), init_struct(wl, precision), None)
-    if compensated:
-        thor.thor_tune(s, thor.THOR_TUNE_COMPENSATED, 1)
+    if precision == thor.THOR_MIXED:
+        thor.thor_tune(s, thor.THOR_TUNE_COMPENSATED, 1 if compensated else 0)
     return s
 
 
@@ -68,22 +69,40 @@ def test_pair_carries_float64_values():
         thor.thor_grid_destroy(grid)
 
 
-def test_float64_state_refuses_and_ensemble_refuses():
+def test_float64_state_refuses():
     grid = _grid()
     s64 = _state(grid, thor.THOR_FP64, False)
-    sc = _state(grid, thor.THOR_MIXED, True)
     try:
         with pytest.raises(thor.ThorError):
             thor.thor_tune(s64, thor.THOR_TUNE_COMPENSATED, 1)
-        ens = thor.thor_ensemble_create([sc], None)
-        try:
-            with pytest.raises(thor.ThorError):
-                thor.thor_ensemble_step(ens, 1, [WL.n_small], [WL.dt])
-        finally:
-            thor.thor_ensemble_destroy(ens)
+        thor.thor_tune(s64, thor.THOR_TUNE_COMPENSATED, 0)         # nothing to drop
     finally:
         thor.thor_state_destroy(s64)
-        thor.thor_state_destroy(sc)
+        thor.thor_grid_destroy(grid)
+
+
+def test_ensemble_follows_a_member_switching_compensation():
+    """An ensemble member switched between plain and compensated between
+    ensemble steps is replanned: the ensemble matches the member stepped
+    alone either way (mixed tolerances of the ensemble tests)."""
+    grid = _grid()
+    a, b = _state(grid, thor.THOR_MIXED, True), _state(grid, thor.THOR_MIXED, True)
+    ens = thor.thor_ensemble_create([a], None)
+    try:
+        for cmp in (1, 0, 1):
+            thor.thor_tune(a, thor.THOR_TUNE_COMPENSATED, cmp)
+            thor.thor_tune(b, thor.THOR_TUNE_COMPENSATED, cmp)
+            thor.thor_ensemble_step(ens, 1, [WL.n_small], [WL.dt])
+            thor.thor_step(b, 1, WL.n_small, WL.dt)
+            for f in FIELDS:
+                x = thor.thor_state_get(a, f, WL.ncol, WL.nv)
+                y = thor.thor_state_get(b, f, WL.ncol, WL.nv)
+                tol = 1e-4 if f == thor.THOR_FIELD_W else 1e-5
+                assert np.max(np.abs(x - y)) <= tol * np.max(np.abs(y)), (cmp, f)
+    finally:
+        thor.thor_ensemble_destroy(ens)
+        thor.thor_state_destroy(a)
+        thor.thor_state_destroy(b)
         thor.thor_grid_destroy(grid)
 
 
@@ -101,6 +120,7 @@ def test_compensated_checkpoint_restart_is_bit_exact():
         thor.thor_step(b, 2, WL.n_small, WL.dt)
         buf = thor.thor_checkpoint_save(b)
         c = mk()
+        thor.thor_tune(c, thor.THOR_TUNE_COMPENSATED, 0)
         with pytest.raises(thor.ThorError):          # twice the size: a plain state refuses it
             thor.thor_checkpoint_load(c, buf)
         thor.thor_tune(c, thor.THOR_TUNE_COMPENSATED, 1)

@@ -126,17 +126,24 @@ def test_restart_from_checkpoint_is_bit_exact(precision, device_buffer):
         thor.thor_grid_destroy(grid)
 
 
-@pytest.mark.parametrize("precision", [thor.THOR_FP64, thor.THOR_MIXED])
-def test_restart_through_float64_fields(precision):
-    """The same restart through thor_state_get / thor_state_set: bit for bit in
-    mixed precision (a float32 deviation plus the float64 reference is exact
-    in float64). In float64 storage reference + deviation rounds to the last
-    place of the full value (rho theta near 300, p near 1e5); three large
-    steps carry that into the small momentum field at about 4e-13 of its
-    largest value, so the bound there is 1e-11."""
+@pytest.mark.parametrize("precision, compensated", [(thor.THOR_FP64, 0), (thor.THOR_MIXED, 1),
+                                                     (thor.THOR_MIXED, 0)])
+def test_restart_through_float64_fields(precision, compensated):
+    """The same restart through thor_state_get / thor_state_set: bit for bit
+    for a plain float state (a float32 deviation plus the float64 reference
+    is exact in float64). In float64 storage, and in a compensated float
+    state (a pair of about 48 bits), reference + deviation rounds to the
+    last place of the full value (rho theta near 300, p near 1e5); three
+    large steps carry that into the small momentum field at about 4e-13 of
+    its largest value, so the bound there is 1e-11."""
     wl = wls.HS_G4
     grid = _grid(wl)
-    mk = lambda: thor.thor_state_init(grid, planet_struct(wl.planet), init_struct(wl, precision), None)
+
+    def mk():
+        st = thor.thor_state_init(grid, planet_struct(wl.planet), init_struct(wl, precision), None)
+        if precision == thor.THOR_MIXED:
+            thor.thor_tune(st, thor.THOR_TUNE_COMPENSATED, compensated)
+        return st
     a, b = mk(), mk()
     c = None
     try:
@@ -150,7 +157,7 @@ def test_restart_through_float64_fields(precision):
         for f in FIELDS:
             x = thor.thor_state_get(a, f, wl.ncol, wl.nv)
             y = thor.thor_state_get(c, f, wl.ncol, wl.nv)
-            if precision == thor.THOR_MIXED:
+            if precision == thor.THOR_MIXED and not compensated:
                 assert np.array_equal(x, y), f
             else:
                 assert np.max(np.abs(x - y)) <= 1e-11 * np.max(np.abs(x)), f
