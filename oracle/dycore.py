@@ -132,6 +132,8 @@ class Model:
     divergence_damping: bool = True
     hydrostatic: bool = False      # reading H1
     vorder: int = 1                # reading L-2: order k of the explicit vertical interpolations
+    anelastic: bool = False        # readings A-1..A-6 (oracle.anelastic)
+    reference: tuple = None        # (rho0, theta0) of the anelastic reference column, (nv,) each
     Kd_fixed: float = None         # a fixed K_d instead of Eq. kd (tests)
     rhat: np.ndarray = field(init=False)
 
@@ -259,7 +261,9 @@ def slow_terms(model, X, Kd):
     theta = X.Th / X.rho
     return dict(p=p, S_M=S_M, S_W=S_W, S_rho=S_rho, S_Th=S_Th, theta=theta,
                 theta_i=op.interp_to_interfaces(vg, theta),
-                Pi=pl.gamma * p / X.Th)
+                Pi=pl.gamma * p / X.Th,
+                # the parts, for the anelastic switch (oracle.anelastic)
+                AC_h=AC_h, AC_r=AC_r, F_M=F_M, F_W=F_W)
 
 
 # ----------------------------------------------------------- vertical solve
@@ -385,6 +389,9 @@ def large_step(model, X, dt, n_small, energy_fixer=False, budget=None):
     (Sec. 3), then the physics of Sec. 5. If budget is a list, the step's
     budget row (energy.budget_row) is appended to it."""
     from .physics import apply_physics
+    if model.anelastic:
+        from .anelastic import large_step as anelastic_large_step
+        return anelastic_large_step(model, X, dt)
     Kd = model.Kd(dt)
     Xt = X
     Xs = X
