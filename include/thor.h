@@ -153,7 +153,23 @@ typedef struct {
  * stay linear, so the column system stays tridiagonal and a resting
  * column in discrete balance stays at rest. Needs nv >= k + 1; other
  * values give THOR_EINVAL. thor_diag and the transfers interpolate
- * linearly whatever vorder is. */
+ * linearly whatever vorder is.
+ * anelastic: 0 (the paper's runs) = compressible; 1 = the anelastic
+ * approximation that Sec. 3 lists among the switches (the density of the
+ * continuity equation's divergence term replaced by the reference column
+ * rho0(z), after Ogura and Phillips 1962, which filters the sound waves):
+ * the state keeps rho = rho0 (the start's temperature noise becomes a
+ * theta' = theta0 dT / T at rho0), the momentum obeys the constraint
+ * div_h M + r^-2 d(r^2 W)/dr = 0 of the discrete 3-D divergence, the
+ * pressure gradient and gravity give way to the buoyancy g rho0 theta' /
+ * theta0 at the interfaces, and each RK3 stage (dt/3, dt/2, dt) is one
+ * projection from X^t with the pressure p' of L p' = D(M^, W^) / dt_s,
+ * L = div o grad, solved in float64 (BiCGStab with a column preconditioner,
+ * relative residual 1e-12, at most 500 iterations, else THOR_ENOTCONV from
+ * thor_step); no acoustic small steps, so n_small is ignored, and no CUDA
+ * graph (the solver checks convergence on the host every iteration). Not
+ * with hydrostatic (THOR_EINVAL), not in ensembles (THOR_EINVAL from
+ * thor_ensemble_step), no compensated state, no energy fixer. */
 enum { THOR_PROFILE_ISOTHERMAL = 0, THOR_PROFILE_HELD_SUAREZ = 1 };
 typedef struct {
   double T0, p_surf, noise_amp;
@@ -167,6 +183,7 @@ typedef struct {
   int hydrostatic;
   int profile;
   int vorder;
+  int anelastic;
 } thor_init;
 
 /* Allocate the device state for `grid` and set the initial condition. The

@@ -67,7 +67,8 @@ class thor_init(ctypes.Structure):
                 ("forcing", ctypes.c_int), ("hj_dT", ctypes.c_double),
                 ("precision", ctypes.c_int), ("hyperdiffusion", ctypes.c_int),
                 ("divergence_damping", ctypes.c_int), ("shallow", ctypes.c_int),
-                ("hydrostatic", ctypes.c_int), ("profile", ctypes.c_int), ("vorder", ctypes.c_int)]
+                ("hydrostatic", ctypes.c_int), ("profile", ctypes.c_int), ("vorder", ctypes.c_int),
+                ("anelastic", ctypes.c_int)]
 
 
 class thor_diag_t(ctypes.Structure):

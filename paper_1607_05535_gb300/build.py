@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libthor.so")
 SOURCES = ["grid.cpp", "thor_step.cu", "thor_api.cu", "thor_noalloc.cu", "thor_mlp.cu", "thor_ensemble.cu",
-           "thor_climate.cu"]
+           "thor_climate.cu", "thor_anelastic.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp,-O3", "--expt-relaxed-constexpr"]
 

@@ -1,0 +1,420 @@
+// The anelastic switch of Sec. 3 on the device: the projection step that
+// replaces the acoustic small steps (thor_init.anelastic).
+//
+// Sec. 3 lists the anelastic approximation among the model's switches: the
+// density in the divergence term of the continuity equation is replaced by
+// a reference density rho0(z) (after Ogura and Phillips 1962), which neglects
+// the elasticity of the fluid and filters the sound waves. Read as the
+// constraint D(M, W) = div_h M + r^-2 d(r^2 W)/dr = 0 on the discrete 3-D
+// divergence, with rho = rho0 (the state's density deviation stays zero),
+// M = rho0 v_h and W = rho0_i v_r. Every RK3 stage s (lengths dt/3, dt/2,
+// dt) is one projection step from X^t:
+//   M^ = M^t + dt_s S_M(X^(s)),  W^ = W^t + dt_s S_W(X^(s)),
+//   L p' = D(M^, W^) / dt_s,     L = D o G,
+//   M = M^ - dt_s G_h p',        W = W^ - dt_s G_v p',
+// with G_h the projected gradient of Eq. grad and G_v the difference across
+// the interfaces (zero normal flow at the ground and the lid). The slow
+// terms (advection, Coriolis, hyperdiffusion, the Ogura-Phillips buoyancy
+// g rho0 theta' / theta0 in place of the pressure gradient and gravity) come
+// from the stage kernels of thor_step.cu with ph.anelastic set.
+//
+// The pressure equation is solved in float64 by BiCGStab (van der Vorst
+// 1992) with a column preconditioner: per column the vertical part of L plus
+// the diagonal of its horizontal part, a tridiagonal matrix factorised once
+// per state (the vertical coupling dominates L by (dx / dz)^2). L is singular
+// (constants are its null space and the cell volumes its left null vector);
+// the right-hand side is in its range by the exact discrete Gauss theorem, so
+// the iteration converges; the momentum is unique, p' only up to a constant.
+#include <cmath>
+#include <vector>
+
+#include "../../include/thor.h"
+#include "grid.h"
+#include "thor_impl.cuh"
+
+namespace thor {
+namespace {
+
+constexpr int kAnThreads = 256;
+constexpr int kAnBlocks = 608;          // 4 per SM of the GB300's 152: reduction partials
+
+// one cell (c, k) of the padded layout per thread, grid-stride
+#define AN_LOOP(n) for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < (n); \
+                        q += (long long)gridDim.x * blockDim.x)
+
+template <typename R>
+__device__ __forceinline__ double d_of(R x) { return (double)x; }
+
+// M^ = M^t + dt_s S_M, W^ = W^t + dt_s S_W (float64 work planes), and the
+// stage's rho theta Th = Th^t + dt_s S_Th and rho deviation 0 into Xo (which
+// may be X^t itself: every cell reads its own values first)
+template <typename R>
+__global__ void k_an_predict(Geo<R> G, Xf<R> Xt, Slow<R> SL, Xf<R> Xo, double dts, double* mx, double* my,
+                             double* mz, double* wi) {
+  const int S = G.colp, nv = G.nv;
+  AN_LOOP((long long)(nv + 1) * S) {
+    const int k = (int)(q / S), c = (int)(q % S);
+    const size_t i = (size_t)k * S + c;
+    if (c >= G.ncol) {
+      if (k < nv) mx[i] = my[i] = mz[i] = 0.0;
+      wi[i] = 0.0;
+      continue;
+    }
+    if (k < nv) {
+      mx[i] = d_of(Xt.mx[i]) + dts * d_of(SL.smx[i]);
+      my[i] = d_of(Xt.my[i]) + dts * d_of(SL.smy[i]);
+      mz[i] = d_of(Xt.mz[i]) + dts * d_of(SL.smz[i]);
+      Xo.th[i] = (R)(d_of(Xt.th[i]) + dts * d_of(SL.sth[i]));
+      Xo.rho[i] = R(0);
+    }
+    wi[i] = (k == 0 || k == nv) ? 0.0 : d_of(Xt.w[i]) + dts * d_of(SL.sw[i]);
+  }
+}
+
+// b = D(M^, W^) / dt_s at every cell
+template <typename R>
+__global__ void k_an_rhs(Geo<R> G, Vert V, const double* mx, const double* my, const double* mz,
+                         const double* wi, double inv_dts, double* b) {
+  const int S = G.colp, nv = G.nv;
+  AN_LOOP((long long)nv * S) {
+    const int k = (int)(q / S), c = (int)(q % S);
+    const size_t i = (size_t)k * S + c;
+    if (c >= G.ncol) {
+      b[i] = 0.0;
+      continue;
+    }
+    const size_t o = (size_t)k * S;
+    double dh = 0.0;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const int n = j == 0 ? c : G.nbr[(j - 1) * S + c];
+      const R* w = G.wdiv + ((size_t)j * S + c) * 4;
+      dh += d_of(w[0]) * mx[o + n] + d_of(w[1]) * my[o + n] + d_of(w[2]) * mz[o + n];
+    }
+    const double dv = V.sq_hi[k] * wi[i + S] - V.sq_lo[k] * wi[i];
+    b[i] = (dh / V.rc[k] + dv) * inv_dts;
+  }
+}
+
+// G_h phi at every cell (the projected gradient, divided by r)
+template <typename R>
+__global__ void k_an_grad(Geo<R> G, Vert V, const double* phi, double* gx, double* gy, double* gz) {
+  const int S = G.colp, nv = G.nv;
+  AN_LOOP((long long)nv * S) {
+    const int k = (int)(q / S), c = (int)(q % S);
+    const size_t i = (size_t)k * S + c;
+    if (c >= G.ncol) {
+      gx[i] = gy[i] = gz[i] = 0.0;
+      continue;
+    }
+    const size_t o = (size_t)k * S;
+    double ax = 0.0, ay = 0.0, az = 0.0;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const int n = j == 0 ? c : G.nbr[(j - 1) * S + c];
+      const R* w = G.wgrad + ((size_t)j * S + c) * 4;
+      const double v = phi[o + n];
+      ax += d_of(w[0]) * v;
+      ay += d_of(w[1]) * v;
+      az += d_of(w[2]) * v;
+    }
+    const double inv_r = 1.0 / V.rc[k];
+    gx[i] = ax * inv_r;
+    gy[i] = ay * inv_r;
+    gz[i] = az * inv_r;
+  }
+}
+
+// y = L phi = D_h(G_h phi) + div_v(G_v phi)
+template <typename R>
+__global__ void k_an_apply(Geo<R> G, Vert V, const double* phi, const double* gx, const double* gy,
+                           const double* gz, double* y) {
+  const int S = G.colp, nv = G.nv;
+  AN_LOOP((long long)nv * S) {
+    const int k = (int)(q / S), c = (int)(q % S);
+    const size_t i = (size_t)k * S + c;
+    if (c >= G.ncol) {
+      y[i] = 0.0;
+      continue;
+    }
+    const size_t o = (size_t)k * S;
+    double dh = 0.0;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const int n = j == 0 ? c : G.nbr[(j - 1) * S + c];
+      const R* w = G.wdiv + ((size_t)j * S + c) * 4;
+      dh += d_of(w[0]) * gx[o + n] + d_of(w[1]) * gy[o + n] + d_of(w[2]) * gz[o + n];
+    }
+    double dv = 0.0;
+    if (k + 1 < nv) dv += V.sq_hi[k] * (phi[i + S] - phi[i]) / V.dzc[k + 1];
+    if (k >= 1) dv -= V.sq_lo[k] * (phi[i] - phi[i - S]) / V.dzc[k];
+    y[i] = dh / V.rc[k] + dv;
+  }
+}
+
+// z = P^-1 r: per column the tridiagonal of the vertical part of L plus the
+// horizontal diagonal, with the factors of an_setup (pivot reciprocals piv,
+// super-diagonal ratios cp; forward elimination then back substitution)
+template <typename R>
+__global__ void k_an_precond(Geo<R> G, Vert V, const double* piv, const double* cp, const double* r, double* z) {
+  const int S = G.colp, nv = G.nv;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < S; c += gridDim.x * blockDim.x) {
+    if (c >= G.ncol) {
+      for (int k = 0; k < nv; ++k) z[(size_t)k * S + c] = 0.0;
+      continue;
+    }
+    double d = 0.0;
+    for (int k = 0; k < nv; ++k) {
+      const size_t i = (size_t)k * S + c;
+      const double lo = k >= 1 ? V.sq_lo[k] / V.dzc[k] : 0.0;
+      d = (r[i] - lo * d) * piv[i];
+      z[i] = d;
+    }
+    for (int k = nv - 2; k >= 0; --k) {
+      const size_t i = (size_t)k * S + c;
+      z[i] -= cp[i] * z[i + S];
+    }
+  }
+}
+
+// the preconditioner's factors per column (once per state): diagonal
+// dh[c] / rc^2 - (sq_hi / dzc_k+1 + sq_lo / dzc_k), off-diagonals
+// sq_lo_k / dzc_k below and sq_hi_k / dzc_k+1 above
+template <typename R>
+__global__ void k_an_factor(Geo<R> G, Vert V, const double* dh, double* piv, double* cp) {
+  const int S = G.colp, nv = G.nv;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G.ncol; c += gridDim.x * blockDim.x) {
+    double cprev = 0.0;
+    for (int k = 0; k < nv; ++k) {
+      const size_t i = (size_t)k * S + c;
+      const double lo = k >= 1 ? V.sq_lo[k] / V.dzc[k] : 0.0;
+      const double up = k + 1 < nv ? V.sq_hi[k] / V.dzc[k + 1] : 0.0;
+      const double di = dh[c] / (V.rc[k] * V.rc[k]) - lo - up;
+      const double p = 1.0 / (di - lo * cprev);
+      piv[i] = p;
+      cprev = up * p;
+      cp[i] = cprev;
+    }
+  }
+}
+
+// BiCGStab scalars in device memory: [0] rho, [1] rho_old, [2] alpha,
+// [3] omega, [4] (r0, v), [5] (t, s), [6] (t, t), [7] (r, r), [8] (b, b)
+enum { SC_RHO = 0, SC_RHO_OLD, SC_ALPHA, SC_OMEGA, SC_R0V, SC_TS, SC_TT, SC_RR, SC_BB, SC_N };
+
+// block partial sums of up to two dot products over n entries
+__global__ void __launch_bounds__(kAnThreads) k_an_dot(const double* a, const double* b, const double* c,
+                                                       const double* d, long long n, double* part) {
+  double s0 = 0.0, s1 = 0.0;
+  AN_LOOP(n) {
+    s0 += a[q] * b[q];
+    if (c) s1 += c[q] * d[q];
+  }
+  __shared__ double sh[2][kAnThreads];
+  sh[0][threadIdx.x] = s0;
+  sh[1][threadIdx.x] = s1;
+  __syncthreads();
+  for (int w = kAnThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sh[0][0];
+    part[2 * blockIdx.x + 1] = sh[1][0];
+  }
+}
+
+// the partials summed in order into sc[i0] (and sc[i1] if i1 >= 0); then the
+// scalar update `op`: 1 = beta for the direction update after rho,
+// 2 = alpha = rho / (r0, v), 3 = omega = (t, s) / (t, t)
+__global__ void k_an_finish(const double* part, int nb, double* sc, int i0, int i1, int op) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int j = 0; j < nb; ++j) {
+    a += part[2 * j];
+    b += part[2 * j + 1];
+  }
+  sc[i0] = a;
+  if (i1 >= 0) sc[i1] = b;
+  if (op == 2) sc[SC_ALPHA] = sc[SC_R0V] != 0.0 ? sc[SC_RHO] / sc[SC_R0V] : 0.0;
+  if (op == 3) sc[SC_OMEGA] = sc[SC_TT] != 0.0 ? sc[SC_TS] / sc[SC_TT] : 0.0;
+}
+
+// p = r + beta (p - omega v), beta = (rho / rho_old) (alpha / omega); first
+// iteration (first = 1): p = r
+__global__ void k_an_dir(const double* r, const double* v, double* p, const double* sc, long long n, int first) {
+  const double beta = first ? 0.0 : (sc[SC_RHO] / sc[SC_RHO_OLD]) * (sc[SC_ALPHA] / sc[SC_OMEGA]);
+  const double om = sc[SC_OMEGA];
+  AN_LOOP(n) p[q] = first ? r[q] : r[q] + beta * (p[q] - om * v[q]);
+}
+
+// s = r - alpha v (into r), x += alpha y
+__global__ void k_an_half(double* x, double* r, const double* y, const double* v, const double* sc, long long n) {
+  const double al = sc[SC_ALPHA];
+  AN_LOOP(n) {
+    x[q] += al * y[q];
+    r[q] -= al * v[q];
+  }
+}
+
+// x += omega z, r = s - omega t; rho_old = rho
+__global__ void k_an_full(double* x, double* r, const double* z, const double* t, double* sc, long long n) {
+  const double om = sc[SC_OMEGA];
+  AN_LOOP(n) {
+    x[q] += om * z[q];
+    r[q] -= om * t[q];
+  }
+}
+__global__ void k_an_keep_rho(double* sc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) sc[SC_RHO_OLD] = sc[SC_RHO];
+}
+
+// M = M^ - dt_s G_h p', W = W^ - dt_s G_v p' into Xo (storage type)
+template <typename R>
+__global__ void k_an_correct(Geo<R> G, Vert V, const double* mx, const double* my, const double* mz,
+                             const double* wi, const double* gx, const double* gy, const double* gz,
+                             const double* phi, double dts, Xf<R> Xo) {
+  const int S = G.colp, nv = G.nv;
+  AN_LOOP((long long)(nv + 1) * S) {
+    const int k = (int)(q / S), c = (int)(q % S);
+    if (c >= G.ncol) continue;
+    const size_t i = (size_t)k * S + c;
+    if (k < nv) {
+      Xo.mx[i] = (R)(mx[i] - dts * gx[i]);
+      Xo.my[i] = (R)(my[i] - dts * gy[i]);
+      Xo.mz[i] = (R)(mz[i] - dts * gz[i]);
+    }
+    double w = 0.0;
+    if (k >= 1 && k < nv) w = wi[i] - dts * (phi[i] - phi[i - S]) / V.dzc[k];
+    Xo.w[i] = (R)w;
+  }
+}
+
+}  // namespace
+
+// The diagonal of D_h o G_h on the unit sphere at every column, from the
+// stencil weights: sum over the stencil points n_j of c of
+// w_div[c][j] . w_grad[n_j][slot of c in n_j's stencil].
+std::vector<double> anelastic_hdiag(const HostGrid& h) {
+  std::vector<double> d(h.ncol, 0.0);
+  for (int c = 0; c < h.ncol; ++c) {
+    double s = 0.0;
+    for (int j = 0; j < 7; ++j) {
+      const int m = j == 0 ? c : h.nbr[6 * c + j - 1];
+      if (m < 0 || (j > 0 && m == c)) continue;
+      int slot = -1;
+      if (m == c) {
+        slot = 0;
+      } else {
+        for (int k = 0; k < 6; ++k)
+          if (h.nbr[6 * m + k] == c) slot = k + 1;
+      }
+      if (slot < 0) continue;
+      for (int a = 0; a < 3; ++a) s += h.w_div[21 * c + 3 * j + a] * h.w_grad[21 * m + 3 * slot + a];
+    }
+    d[c] = s;
+  }
+  return d;
+}
+
+template <typename R>
+int anelastic_setup(Impl<R>& I, const std::vector<double>& hdiag) {
+  const size_t S = I.G.colp, C = S * I.G.nv, F = S * (I.G.nv + 1);
+  // mx my mz gx gy gz x r r0 p v y s z t b: 16 cell planes; wi: interfaces;
+  // piv, cp: the preconditioner; dh: [colp]; partials; scalars
+  const size_t doubles = 16 * C + F + 2 * C + S + 2 * kAnBlocks + 16;
+  if (cudaMalloc(&I.an_buf, doubles * sizeof(double))) {
+    I.an_buf = nullptr;
+    return THOR_ENOMEM;
+  }
+  double* b = static_cast<double*>(I.an_buf);
+  I.an_dh = b + 16 * C + F + 2 * C;
+  if (cudaMemsetAsync(I.an_buf, 0, doubles * sizeof(double), I.stream) ||
+      cudaMemcpyAsync(I.an_dh, hdiag.data(), hdiag.size() * sizeof(double), cudaMemcpyHostToDevice, I.stream))
+    return THOR_ECUDA;
+  double* piv = b + 16 * C + F;
+  k_an_factor<R><<<(I.G.ncol + 127) / 128, 128, 0, I.stream>>>(I.G, I.V, I.an_dh, piv, piv + C);
+  return cudaStreamSynchronize(I.stream) == cudaSuccess ? THOR_OK : THOR_ECUDA;
+}
+
+// One projection step into Xo (the stage's M, W, Th and zero rho deviation)
+// from X^t and the stage's slow terms; iterations into *iters.
+template <typename R>
+int anelastic_project(Impl<R>& I, double dts, const Xf<R>& Xo, int* iters) {
+  const size_t S = I.G.colp, C = S * I.G.nv;
+  const long long n = (long long)C;
+  double* b0 = static_cast<double*>(I.an_buf);
+  double *mx = b0, *my = b0 + C, *mz = b0 + 2 * C, *gx = b0 + 3 * C, *gy = b0 + 4 * C, *gz = b0 + 5 * C;
+  double *x = b0 + 6 * C, *r = b0 + 7 * C, *r0 = b0 + 8 * C, *p = b0 + 9 * C, *v = b0 + 10 * C;
+  double *y = b0 + 11 * C, *s = b0 + 12 * C, *z = b0 + 13 * C, *t = b0 + 14 * C, *rhs = b0 + 15 * C;
+  double* wi = b0 + 16 * C;
+  double* piv = wi + (S * (I.G.nv + 1));
+  double* cp = piv + C;
+  double* part = I.an_dh + S;
+  double* sc = part + 2 * kAnBlocks;
+  cudaStream_t st = I.stream;
+  const int nb = kAnBlocks, nt = kAnThreads;
+  const int pb = (int)((S + 127) / 128);
+  auto apply = [&](const double* in, double* out) {
+    k_an_grad<R><<<nb, nt, 0, st>>>(I.G, I.V, in, gx, gy, gz);
+    k_an_apply<R><<<nb, nt, 0, st>>>(I.G, I.V, in, gx, gy, gz, out);
+  };
+  auto dot = [&](const double* a, const double* bb, const double* c, const double* d, int i0, int i1, int op) {
+    k_an_dot<<<nb, nt, 0, st>>>(a, bb, c, d, n, part);
+    k_an_finish<<<1, 32, 0, st>>>(part, nb, sc, i0, i1, op);
+  };
+  k_an_predict<R><<<nb, nt, 0, st>>>(I.G, I.Xt, I.SL, Xo, dts, mx, my, mz, wi);
+  k_an_rhs<R><<<nb, nt, 0, st>>>(I.G, I.V, mx, my, mz, wi, 1.0 / dts, rhs);
+  // x = 0, r = r0 = b
+  cudaMemsetAsync(x, 0, C * sizeof(double), st);
+  cudaMemcpyAsync(r, rhs, C * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(r0, rhs, C * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  dot(rhs, rhs, nullptr, nullptr, SC_BB, -1, 0);
+  double hb[SC_N];
+  if (cudaMemcpyAsync(hb, sc, sizeof(hb), cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
+    return THOR_ECUDA;
+  const double bb = hb[SC_BB];
+  int it = 0;
+  int rc = THOR_OK;
+  if (bb > 0.0) {
+    rc = THOR_ENOTCONV;
+    for (it = 1; it <= I.an_max_iter; ++it) {
+      dot(r0, r, nullptr, nullptr, SC_RHO, -1, 0);
+      k_an_dir<<<nb, nt, 0, st>>>(r, v, p, sc, n, it == 1);
+      k_an_precond<R><<<pb, 128, 0, st>>>(I.G, I.V, piv, cp, p, y);
+      apply(y, v);
+      dot(r0, v, nullptr, nullptr, SC_R0V, -1, 2);
+      k_an_half<<<nb, nt, 0, st>>>(x, r, y, v, sc, n);           // r now holds s
+      k_an_precond<R><<<pb, 128, 0, st>>>(I.G, I.V, piv, cp, r, z);
+      apply(z, t);
+      dot(t, r, t, t, SC_TS, SC_TT, 3);
+      k_an_full<<<nb, nt, 0, st>>>(x, r, z, t, sc, n);
+      k_an_keep_rho<<<1, 32, 0, st>>>(sc);
+      dot(r, r, nullptr, nullptr, SC_RR, -1, 0);
+      I.launches += 18;
+      if (cudaMemcpyAsync(hb, sc, sizeof(hb), cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
+        return THOR_ECUDA;
+      if (!(hb[SC_RR] == hb[SC_RR])) break;                     // NaN: leave as not converged
+      if (hb[SC_RR] <= I.an_tol * I.an_tol * bb) {
+        rc = THOR_OK;
+        break;
+      }
+    }
+  }
+  *iters = it;
+  apply(x, y);                                                 // G_h p' into gx, gy, gz
+  k_an_correct<R><<<nb, nt, 0, st>>>(I.G, I.V, mx, my, mz, wi, gx, gy, gz, x, dts, Xo);
+  I.launches += 8;
+  if (cudaGetLastError() != cudaSuccess) return THOR_ECUDA;
+  return rc;
+}
+
+template int anelastic_setup<double>(Impl<double>&, const std::vector<double>&);
+template int anelastic_setup<float>(Impl<float>&, const std::vector<double>&);
+template int anelastic_project<double>(Impl<double>&, double, const Xf<double>&, int*);
+template int anelastic_project<float>(Impl<float>&, double, const Xf<float>&, int*);
+
+}  // namespace thor

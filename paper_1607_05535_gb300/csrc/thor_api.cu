@@ -18,6 +18,10 @@
 namespace thor {
 template <typename R>
 int col_kernel_setup(int nv);   // thor_step.cu: opt the column kernel into its shared memory
+// thor_anelastic.cu: the pressure solve of the anelastic switch
+std::vector<double> anelastic_hdiag(const HostGrid& h);
+template <typename R>
+int anelastic_setup(Impl<R>& I, const std::vector<double>& hdiag);
 namespace {
 
 inline int colp_of(int ncol) { return (ncol + kBlock - 1) / kBlock * kBlock; }
@@ -342,6 +346,7 @@ Impl<R>::~Impl() {
   if (ev_join0) cudaEventDestroy(ev_join0);
   if (arena) cudaFree(arena);
   if (lo_buf) cudaFree(lo_buf);
+  if (an_buf) cudaFree(an_buf);
 }
 
 // the element count of a field in the canonical layout of thor_state_get
@@ -444,7 +449,7 @@ int Impl<R>::diag(double* out8, long long* nonfinite) {
 // parts); float64 states need none
 template <typename R>
 int Impl<R>::set_compensated(int on) {
-  if (sizeof(R) == sizeof(double)) return on ? THOR_EINVAL : THOR_OK;
+  if (sizeof(R) == sizeof(double) || ph.anelastic) return on ? THOR_EINVAL : THOR_OK;
   if ((on != 0) == (compensated != 0)) return THOR_OK;
   if (cudaStreamSynchronize(stream)) return THOR_ECUDA;
   drop_graph();
@@ -621,8 +626,15 @@ int host_setup(const HostGrid& h, const thor_planet& pl, const thor_init& in, Ho
         double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
         T = Tcol[k] + in.noise_amp * (2.0 * u - 1.0);
       }
-      hs.rho[(size_t)c * nv + k] = pb[k] / (Rd * T);
-      hs.th[(size_t)c * nv + k] = thb[k];
+      if (in.anelastic) {
+        // anelastic start: rho stays the reference column; the temperature
+        // perturbation at fixed pressure is a theta' = theta0 dT / T
+        hs.rho[(size_t)c * nv + k] = rhob[k];
+        hs.th[(size_t)c * nv + k] = thb[k] * (1.0 + (T - Tcol[k]) / Tcol[k]);
+      } else {
+        hs.rho[(size_t)c * nv + k] = pb[k] / (Rd * T);
+        hs.th[(size_t)c * nv + k] = thb[k];
+      }
     }
   return THOR_OK;
 }
@@ -656,6 +668,7 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
   I->ph.two_omega_f = (float)I->ph.two_omega;
   I->ph.hydrostatic = in.hydrostatic ? 1 : 0;
   I->ph.vorder = in.vorder > 1 ? in.vorder : 1;
+  I->ph.anelastic = in.anelastic ? 1 : 0;
   I->ph.delta = in.hydrostatic ? 0.0 : 1.0;
   I->ph.delta_f = (float)I->ph.delta;
   I->hyper = in.hyperdiffusion ? 1 : 0;
@@ -701,12 +714,16 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
     for (int v = 0; v < kNumVert; ++v) mix(hs.vert[v].data(), hs.vert[v].size() * sizeof(double));
     const double pv[7] = {pl.radius, pl.omega, pl.gravity, pl.Rd, pl.cp, pl.p_ref, pl.diff_D};
     mix(pv, sizeof(pv));
-    const int sw[4] = {in.shallow, in.hydrostatic, in.forcing, in.vorder > 1 ? in.vorder : 1};
+    const int sw[5] = {in.shallow, in.hydrostatic, in.forcing, in.vorder > 1 ? in.vorder : 1, in.anelastic ? 1 : 0};
     mix(sw, sizeof(sw));
     I->ref_hash = x;
   }
   rc = upload_tables(*I, h, hs.vert, &hs, st);
   if (rc) return rc;
+  if (in.anelastic) {
+    rc = anelastic_setup(*I, anelastic_hdiag(h));
+    if (rc) return rc;
+  }
   rc = I->set(THOR_FIELD_RHO, hs.rho.data(), hs.rho.size());
   if (rc) return rc;
   rc = I->set(THOR_FIELD_RHOTHETA, hs.th.data(), hs.th.size());
@@ -802,6 +819,7 @@ int thor_state_init(thor_grid* grid, const thor_planet* pl, const thor_init* in,
       !(in->T0 > 0 || in->profile == THOR_PROFILE_HELD_SUAREZ) || !(in->p_surf > 0) || !(in->noise_amp >= 0) ||
       in->profile < THOR_PROFILE_ISOTHERMAL || in->profile > THOR_PROFILE_HELD_SUAREZ || in->forcing < 0 ||
       in->vorder < 0 || in->vorder > 3 || grid->h.nv < (in->vorder > 1 ? in->vorder : 1) + 1 ||
+      (in->anelastic && in->hydrostatic) ||
       in->forcing > 2 ||
       (in->precision != THOR_FP64 && in->precision != THOR_MIXED) || grid->h.nv > thor::kMaxNv)
     return THOR_EINVAL;
@@ -813,7 +831,7 @@ int thor_state_init(thor_grid* grid, const thor_planet* pl, const thor_init* in,
   int rc = in->precision == THOR_FP64 ? thor::make_impl<double>(grid, *pl, *in, st, s->impl)
                                       : thor::make_impl<float>(grid, *pl, *in, st, s->impl);
   // mixed states keep X^t as compensated float pairs unless switched off
-  if (!rc && in->precision == THOR_MIXED) rc = s->impl->set_compensated(1);
+  if (!rc && in->precision == THOR_MIXED && !in->anelastic) rc = s->impl->set_compensated(1);
   if (rc) {
     delete s;
     return rc;

@@ -30,7 +30,7 @@ constexpr int kZonalQ = 9;    // weight, u, v, T, p, uv, vT, uu, vv
 
 template <typename R>
 __global__ void __launch_bounds__(kZonalThreads)
-    k_zonal_partial(Geo<R> G, Vert V, Phys ph, Xf<R> X, const int* __restrict__ band,
+    k_zonal_partial(Geo<R> G, Vert V, Phys ph, Xf<R> X, Xf<R> XL, const int* __restrict__ band,
                     const double* __restrict__ basis, int nlat, double* __restrict__ tmp,
                     double* __restrict__ wsum) {
   extern __shared__ double hist[];                 // [nlat][kZonalQ]
@@ -40,13 +40,15 @@ __global__ void __launch_bounds__(kZonalThreads)
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < G.ncol) {
     const size_t i = (size_t)k * S + c;
-    const double rho = V.rhob[k] + (double)X.rho[i];
-    const double p = V.pb[k] + V.pb[k] * expm1(ph.gamma * log1p((double)X.th[i] / V.thb[k]));
+    // the full value of a field: a compensated state adds its low part XL
+    auto val = [&](const R* hi, const R* lo, size_t j) { return lo ? (double)hi[j] + (double)lo[j] : (double)hi[j]; };
+    const double rho = V.rhob[k] + val(X.rho, XL.rho, i);
+    const double p = V.pb[k] + V.pb[k] * expm1(ph.gamma * log1p(val(X.th, XL.th, i) / V.thb[k]));
     const double T = p / (rho * ph.Rd);
-    const double vx = (double)X.mx[i] / rho, vy = (double)X.my[i] / rho, vz = (double)X.mz[i] / rho;
+    const double vx = val(X.mx, XL.mx, i) / rho, vy = val(X.my, XL.my, i) / rho, vz = val(X.mz, XL.mz, i) / rho;
     const double u = vx * basis[c] + vy * basis[S + c] + vz * basis[2 * S + c];
     const double v = vx * basis[3 * S + c] + vy * basis[4 * S + c] + vz * basis[5 * S + c];
-    wsum[i] += (V.clo[k] * (double)X.w[i] + V.chi[k] * (double)X.w[i + S]) / rho;
+    wsum[i] += (V.clo[k] * val(X.w, XL.w, i) + V.chi[k] * val(X.w, XL.w, i + S)) / rho;
     const double w = G.area[c] * V.rc[k] * V.rc[k] * V.dz[k];
     const double q[kZonalQ] = {w, w * u, w * v, w * T, w * p, w * u * v, w * v * T, w * u * u, w * v * v};
     double* h = hist + band[c] * kZonalQ;
@@ -88,7 +90,7 @@ int zonal_launch(thor_state* s) {
   const int nv = I->G.nv;
   dim3 grid((I->G.ncol + kZonalThreads - 1) / kZonalThreads, nv);
   const size_t smem = (size_t)z.nlat * kZonalQ * sizeof(double);
-  k_zonal_partial<R><<<grid, kZonalThreads, smem, I->stream>>>(I->G, I->V, I->ph, I->Xt, z.band, z.basis, z.nlat,
+  k_zonal_partial<R><<<grid, kZonalThreads, smem, I->stream>>>(I->G, I->V, I->ph, I->Xt, I->XtL, z.band, z.basis, z.nlat,
                                                                 z.tmp, z.wsum);
   const int n = nv * z.nlat;
   k_zonal_finish<<<(n + 255) / 256, 256, 0, I->stream>>>(n, z.tmp, z.acc);

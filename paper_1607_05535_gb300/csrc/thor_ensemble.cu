@@ -274,7 +274,7 @@ int check_steps(const thor_ensemble* E, int n_large, const int* n_small, const d
   if (!E || n_large < 0 || !n_small || !dt) return THOR_EINVAL;
   for (size_t i = 0; i < E->members.size(); ++i) {
     if (n_small[i] < 2 || (n_small[i] % 2) || !(dt[i] > 0)) return THOR_EINVAL;
-    if (E->members[i]->closure.net) return THOR_EINVAL;
+    if (E->members[i]->closure.net || E->members[i]->impl->anelastic()) return THOR_EINVAL;
   }
   return THOR_OK;
 }

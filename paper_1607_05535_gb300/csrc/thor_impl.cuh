@@ -98,6 +98,7 @@ struct ImplBase {
   // to the prognostic fields of a float state, on = 0 drops them (the state
   // rounds to its float parts); -1 for a float64 state
   virtual int set_compensated(int on) = 0;
+  virtual bool anelastic() const = 0;
   int compensated = 0;
   long long launches = 0;
   int kchunk = 2;                      // levels per thread in the stencil kernels
@@ -183,6 +184,14 @@ struct Impl : ImplBase {
   // hi; the stage state is stored as floats
   Xf<R> XtL{};
   void* lo_buf = nullptr;
+  // anelastic switch: float64 work planes of the pressure solve, the
+  // horizontal diagonal of its operator per column, solver limits
+  void* an_buf = nullptr;
+  double* an_dh = nullptr;
+  int an_max_iter = 500;
+  double an_tol = 1e-12;
+  int an_last_iters = 0;
+  int anelastic_step(double dt);
   int hyper = 1, divdamp = 1, forcing = 0;
   int shallow = 0;                 // shallow-atmosphere approximation (thor_init.shallow)
   double diff_D = 0, dbar4 = 0, hj_dT = 300.0;
@@ -223,6 +232,13 @@ struct Impl : ImplBase {
   }
   int energy_key() const { return energy_fix * 2 + (budget_cap > 0 ? 1 : 0); }
   int step(int n_large, int n_small, double dt) override {
+    if (ph.anelastic) {                  // host-driven solver iterations: no graph
+      for (int i = 0; i < n_large; ++i) {
+        int rc = anelastic_step(dt);
+        if (rc) return rc;
+      }
+      return 0;
+    }
     if (use_graph && stream != nullptr && !prof_on && n_large > 0) {
       if (!graph_exec || graph_dt != dt || graph_n != n_small || graph_kc != kchunk || graph_bs != block ||
           graph_tma != solve_tma || graph_energy != energy_key() || graph_stages != rk_stages ||
@@ -274,6 +290,7 @@ struct Impl : ImplBase {
   int set_all(const double* const host[4]) override;
   int set_async(int field, const double* host, double* buf);   // queue one field, no synchronisation
   int set_compensated(int on) override;
+  bool anelastic() const override { return ph.anelastic != 0; }
   // rho, M (3), rho theta: nv planes each; W: nv + 1 planes (and the same
   // again for the low parts of a compensated state); buf in device or host
   // memory (unified addressing)

@@ -93,6 +93,10 @@ struct Phys {
   int hydrostatic = 0;
   // order k of the vertical interpolation in the explicit terms (1: linear)
   int vorder = 1;
+  // anelastic switch (Sec. 3): the slow terms drop the pressure gradient
+  // and gravity for the Ogura-Phillips buoyancy; a projection replaces the
+  // acoustic small steps
+  int anelastic = 0;
 };
 // the constant in the kernel's storage type
 template <typename R> __device__ __forceinline__ R pc(double d, float f);

@@ -250,7 +250,9 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
       ahz = A[2] - acr * rz;
     }
 
-    R smx = -gx * inv_r - ahx + FMx, smy = -gy * inv_r - ahy + FMy, smz = -gz * inv_r - ahz + FMz;
+    // the anelastic switch leaves the pressure force to the projection
+    const R pgr = ph.anelastic ? R(0) : inv_r;
+    R smx = -gx * pgr - ahx + FMx, smy = -gy * pgr - ahy + FMy, smz = -gz * pgr - ahz + FMz;
     project(rx, ry, rz, smx, smy, smz);
     SL.smx[i] = smx;
     SL.smy[i] = smy;
@@ -317,8 +319,16 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
       continue;
     }
     R wlo = ld(U.wlo + (k)), whi = ld(U.whi + (k));
-    R sw = ld(U.Rb + (k)) - (ld(T.pp + (i)) - ld(T.pp + (i - S))) * ld(U.inv_dzc + (k))
-         - g * (wlo * ld(X.rho + (i - S)) + whi * ld(X.rho + (i)));
+    R sw;
+    if (ph.anelastic) {
+      // Ogura-Phillips buoyancy g rho0_i (theta' / theta0)_i, theta' / theta0 =
+      // Th' / Th_bar at rho = rho_bar, both interpolated linearly
+      sw = g * (wlo * ld(U.rhob + (k - 1)) + whi * ld(U.rhob + (k)))
+           * (wlo * ld(X.th + (i - S)) / ld(U.thb + (k - 1)) + whi * ld(X.th + (i)) / ld(U.thb + (k)));
+    } else {
+      sw = ld(U.Rb + (k)) - (ld(T.pp + (i)) - ld(T.pp + (i - S))) * ld(U.inv_dzc + (k))
+           - g * (wlo * ld(X.rho + (i - S)) + whi * ld(X.rho + (i)));
+    }
     // the vertical advection, Coriolis and diffusion of W are part of the
     // inertia that the hydrostatic switch drops
     if (!ph.hydrostatic) {
@@ -1447,6 +1457,52 @@ int Impl<R>::large_step(double dt, int n_small) {
   }
   return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
+
+template <typename R>
+int anelastic_project(Impl<R>& I, double dts, const Xf<R>& Xo, int* iters);   // thor_anelastic.cu
+
+// One large step under the anelastic switch (Sec. 3): the three RK3 stages
+// of lengths dt/3, dt/2, dt, each the slow terms at the stage state
+// (pressure gradient and gravity replaced by the buoyancy) and one
+// projection from X^t (thor_anelastic.cu), then the physics.
+template <typename R>
+int Impl<R>::anelastic_step(double dt) {
+  const int kc = kchunk, bs = block;
+  dim3 g2, g2i;
+  launch_2d(G.nv, kc, g2);
+  launch_2d(G.nv + 1, kc, g2i);
+  dim3 g1((G.ncol + bs - 1) / bs);
+  const R Kd = (R)(diff_D * dbar4 / dt);
+  const double dts[3] = {dt / 3.0, dt / 2.0, dt};
+  const bool ho = ph.vorder > 1;
+  for (int s = 0; s < 3; ++s) {
+    Xf<R> Xs = s == 0 ? Xt : Xst, Xo = s == 2 ? Xt : Xst;
+    if (launch_k(ho ? k_derived<R, true> : k_derived<R, false>, g2i, bs, 0, stream, G, U, ph, Xs, T, shallow, kc))
+      return -3;
+    if (hyper && launch_k(ho ? k_lap1<R, true> : k_lap1<R, false>, g2i, bs, 0, stream, G, U, Xs, T, Kd, kc))
+      return -3;
+    auto slow = shallow ? (ho ? k_slow<R, true, true> : k_slow<R, true, false>)
+                        : (ho ? k_slow<R, false, true> : k_slow<R, false, false>);
+    if (launch_k(slow, g2, bs, 0, stream, G, U, ph, Xs, T, SL, hyper, (R*)nullptr, kc) ||
+        launch_k(ho ? k_slow_w<R, true> : k_slow_w<R, false>, g2i, bs, 0, stream, G, U, ph, Xt, Xs, T, SL, P,
+                 hyper, 0, kc))
+      return -3;
+    launches += 3 + (hyper ? 1 : 0);
+    int it = 0;
+    const int rc = anelastic_project(*this, dts[s], Xo, &it);
+    an_last_iters = it;
+    if (rc) return rc;
+  }
+  if (forcing != 0) {
+    if (launch_k(k_surface_p<R>, g1, bs, 0, stream, G, U, ph, Xt, T) ||
+        launch_k(k_physics<R>, g2, bs, 0, stream, G, U, ph, Xt, XtL, T, forcing, dt, hj_dT, kc))
+      return -3;
+    launches += 2;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+template int Impl<double>::anelastic_step(double);
+template int Impl<float>::anelastic_step(double);
 
 template <>
 cudaError_t Impl<float>::launch_solve_tma(dim3 grid, int stage, const Xf<float>& Xo, const Xf<float>& XsL,

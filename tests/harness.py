@@ -19,9 +19,10 @@ def planet_struct(P):
     return thor.thor_planet(P.radius, P.omega, P.gravity, P.Rd, P.cp, P.p_ref, P.diff_D)
 
 
-def init_struct(wl, precision=thor.THOR_FP64, hyper=1, divdamp=1, shallow=0, hydrostatic=0, profile=0, vorder=1):
+def init_struct(wl, precision=thor.THOR_FP64, hyper=1, divdamp=1, shallow=0, hydrostatic=0, profile=0, vorder=1,
+                anelastic=0):
     return thor.thor_init(wl.T0, wl.p_surf, wl.noise_amp, wl.seed, FORCING[wl.forcing], wl.hj_dT,
-                          precision, hyper, divdamp, shallow, hydrostatic, profile, vorder)
+                          precision, hyper, divdamp, shallow, hydrostatic, profile, vorder, anelastic)
 
 
 class Pair:
@@ -29,14 +30,15 @@ class Pair:
     column c."""
 
     def __init__(self, wl, precision=thor.THOR_FP64, hyper=True, divdamp=True, stream=None, shallow=False,
-                 hydrostatic=False, profile=False, vorder=1):
+                 hydrostatic=False, profile=False, vorder=1, anelastic=False):
         self.wl = wl
         sp = thor.thor_spring(1.15, 1.0, 1.0, 0.01, wl.spring_tol, wl.spring_max_iter)
         self.grid = thor.thor_grid_create(wl.glevel, wl.nv, wl.planet.radius, wl.z_top, sp)
         self.state = thor.thor_state_init(self.grid, planet_struct(wl.planet),
                                           init_struct(wl, precision, int(hyper), int(divdamp), int(shallow),
                                                       int(hydrostatic),
-                                                      thor.THOR_PROFILE_HELD_SUAREZ if profile else 0, vorder),
+                                                      thor.THOR_PROFILE_HELD_SUAREZ if profile else 0, vorder,
+                                                      int(anelastic)),
                                           stream)
         self.ncol, self.nv = wl.ncol, wl.nv
         self.profile = "held_suarez" if profile else None
@@ -46,7 +48,7 @@ class Pair:
                    dc.diffusion_parameter(P.dt_paper, P.tau_d))
         self.model = dc.Model(G, op.VerticalGrid(wl.nv, wl.z_top, P.radius, shallow=shallow), pl, forcing=wl.forcing,
                               hj_dT=wl.hj_dT, hyperdiffusion=hyper, divergence_damping=divdamp,
-                              hydrostatic=hydrostatic, vorder=vorder)
+                              hydrostatic=hydrostatic, vorder=vorder, anelastic=anelastic)
         d, self.perm = cKDTree(G.points).query(thor.thor_grid_points(self.grid))
         assert d.max() < 1e-11 and len(np.unique(self.perm)) == self.ncol
 
