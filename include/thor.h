@@ -164,8 +164,9 @@ typedef struct {
  * pressure gradient and gravity give way to the buoyancy g rho0 theta' /
  * theta0 at the interfaces, and each RK3 stage (dt/3, dt/2, dt) is one
  * projection from X^t with the pressure p' of L p' = D(M^, W^) / dt_s,
- * L = div o grad, solved in float64 (BiCGStab with a column preconditioner,
- * relative residual 1e-12, at most 500 iterations, else THOR_ENOTCONV from
+ * L = div o grad, solved in float64 (BiCGStab with a column preconditioner
+ * to a true relative residual of 1e-13, restarted from the true residual at
+ * most twice, at most 500 iterations a pass, else THOR_ENOTCONV from
  * thor_step); no acoustic small steps, so n_small is ignored, and no CUDA
  * graph (the solver checks convergence on the host every iteration). Not
  * with hydrostatic (THOR_EINVAL), not in ensembles (THOR_EINVAL from

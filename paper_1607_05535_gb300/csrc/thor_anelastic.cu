@@ -268,6 +268,10 @@ __global__ void k_an_full(double* x, double* r, const double* z, const double* t
     r[q] -= om * t[q];
   }
 }
+// r = b - y
+__global__ void k_an_sub(double* r, const double* b, const double* y, long long n) {
+  AN_LOOP(n) r[q] = b[q] - y[q];
+}
 __global__ void k_an_keep_rho(double* sc) {
   if (threadIdx.x == 0 && blockIdx.x == 0) sc[SC_RHO_OLD] = sc[SC_RHO];
 }
@@ -377,9 +381,26 @@ int anelastic_project(Impl<R>& I, double dts, const Xf<R>& Xo, int* iters) {
   if (cudaMemcpyAsync(hb, sc, sizeof(hb), cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
     return THOR_ECUDA;
   const double bb = hb[SC_BB];
-  int it = 0;
+  int it = 0, total = 0;
   int rc = THOR_OK;
-  if (bb > 0.0) {
+  // BiCGStab passes: the recursively updated residual drifts from the true
+  // one on this ill-conditioned operator, so a converged pass is checked
+  // against the true residual b - L x and, if that is still above the
+  // tolerance, the iteration restarts from it (at most three passes)
+  for (int pass = 0; pass < 3 && bb > 0.0; ++pass) {
+    if (pass > 0) {
+      apply(x, y);
+      k_an_sub<<<nb, nt, 0, st>>>(r, rhs, y, n);
+      cudaMemcpyAsync(r0, r, C * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      dot(r, r, nullptr, nullptr, SC_RR, -1, 0);
+      I.launches += 5;
+      if (cudaMemcpyAsync(hb, sc, sizeof(hb), cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
+        return THOR_ECUDA;
+      if (hb[SC_RR] <= I.an_tol * I.an_tol * bb) {
+        rc = THOR_OK;
+        break;
+      }
+    }
     rc = THOR_ENOTCONV;
     for (it = 1; it <= I.an_max_iter; ++it) {
       dot(r0, r, nullptr, nullptr, SC_RHO, -1, 0);
@@ -398,13 +419,15 @@ int anelastic_project(Impl<R>& I, double dts, const Xf<R>& Xo, int* iters) {
       if (cudaMemcpyAsync(hb, sc, sizeof(hb), cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
         return THOR_ECUDA;
       if (!(hb[SC_RR] == hb[SC_RR])) break;                     // NaN: leave as not converged
-      if (hb[SC_RR] <= I.an_tol * I.an_tol * bb) {
+      if (hb[SC_RR] <= 0.01 * I.an_tol * I.an_tol * bb) {      // the recursive residual, a decade below
         rc = THOR_OK;
         break;
       }
     }
+    total += it;
+    if (rc != THOR_OK && !(hb[SC_RR] == hb[SC_RR])) break;
   }
-  *iters = it;
+  *iters = total;
   apply(x, y);                                                 // G_h p' into gx, gy, gz
   k_an_correct<R><<<nb, nt, 0, st>>>(I.G, I.V, mx, my, mz, wi, gx, gy, gz, x, dts, Xo);
   I.launches += 8;

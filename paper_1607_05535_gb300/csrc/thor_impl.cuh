@@ -189,7 +189,7 @@ struct Impl : ImplBase {
   void* an_buf = nullptr;
   double* an_dh = nullptr;
   int an_max_iter = 500;
-  double an_tol = 1e-12;
+  double an_tol = 1e-13;
   int an_last_iters = 0;
   int anelastic_step(double dt);
   int hyper = 1, divdamp = 1, forcing = 0;
