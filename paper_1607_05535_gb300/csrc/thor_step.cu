@@ -42,7 +42,7 @@ cudaError_t launch_k(void (*kern)(K...), dim3 grid, dim3 block, size_t smem, cud
 // 3-D velocity, v_h = M/rho (centres) and v_r = W/rho (interfaces).
 // HO: the order-k interpolation of the explicit terms (thor_init.vorder > 1)
 template <typename R, bool HO = false>
-__device__ __forceinline__ void d_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int shallow, int kchunk,
+__device__ __forceinline__ void d_derived(const Geo<R>& G, const VR<R>& U, const Phys& ph, const Xf<R>& X, const Work<R>& T, int shallow, int kchunk,
                                           int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
@@ -90,7 +90,7 @@ __device__ __forceinline__ void d_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, W
 // First Laplacians of the hyperdiffusion (Sec. 4), already multiplied by
 // K_d and, for the momentum and temperature terms, by rho.
 template <typename R, bool HO = false>
-__device__ __forceinline__ void d_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk, int bx, int by) {
+__device__ __forceinline__ void d_lap1(const Geo<R>& G, const VR<R>& U, const Xf<R>& X, const Work<R>& T, R Kd, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -133,7 +133,7 @@ __device__ __forceinline__ void d_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R 
 // momentum only, and the horizontal velocity and w advected without the
 // metric terms the approximation drops)
 template <typename R, bool SH = false, bool HO = false>
-__device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper,
+__device__ __forceinline__ void d_slow(const Geo<R>& G, const VR<R>& U, const Phys& ph, const Xf<R>& X, const Work<R>& T, const Slow<R>& SL, int hyper,
                                             R* d0, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
@@ -283,9 +283,9 @@ __device__ __forceinline__ void d_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work
 // is X^t itself or the state is not compensated); the stage state is stored
 // as floats
 template <typename R, bool HO = false>
-__device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Slow<R> SL,
-                                         Pert<R> P, int hyper, int init, int kchunk, int bx, int by,
-                                         Xf<R> XtL = Xf<R>{}) {
+__device__ __forceinline__ void d_slow_w(const Geo<R>& G, const VR<R>& U, const Phys& ph, const Xf<R>& Xt, const Xf<R>& X, const Work<R>& T, const Slow<R>& SL,
+                                         const Pert<R>& P, int hyper, int init, int kchunk, int bx, int by,
+                                         const Xf<R>& XtL = Xf<R>{}) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -352,8 +352,8 @@ __device__ __forceinline__ void d_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, X
 // state (null: stored as floats), so that Phi^t - Phi^(s) is taken from the
 // full values.
 template <typename R>
-__device__ __forceinline__ void d_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Pert<R> P,
-                                             Xf<R> XtL, Xf<R> XL, int zero, int kchunk, int bx, int by) {
+__device__ __forceinline__ void d_stage_init(const Geo<R>& G, const VR<R>& U, const Phys& ph, const Xf<R>& Xt, const Xf<R>& X, const Work<R>& T, const Pert<R>& P,
+                                             const Xf<R>& XtL, const Xf<R>& XL, int zero, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -397,7 +397,7 @@ template <typename R>
 // momentum, D = d0 in the first small step of a stage and later the D the
 // previous column step formed; stored packed with the cell's p* (the
 // momentum step gathers both)
-__device__ __forceinline__ void d_ss_lapd(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, const R* pstar, int kchunk,
+__device__ __forceinline__ void d_ss_lapd(const Geo<R>& G, const VR<R>& U, const Work<R>& T, const R* dsrc, const R* pstar, int kchunk,
                                           int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
@@ -417,8 +417,8 @@ __device__ __forceinline__ void d_ss_lapd(Geo<R> G, VR<R> U, Work<R> T, const R*
 // may be Xs itself: each cell reads its own Xs value before writing it), with
 // the low parts XsL -> XoL of a compensated state (null: none)
 template <typename R>
-__device__ __forceinline__ void d_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, R Kd,
-                                            int divdamp, Xf<R> Xs, Xf<R> Xo, Xf<R> XsL, Xf<R> XoL, int last,
+__device__ __forceinline__ void d_ss_mom(const Geo<R>& G, const VR<R>& U, const Slow<R>& SL, const Pert<R>& P, const Work<R>& T, R dtau, R Kd,
+                                            int divdamp, const Xf<R>& Xs, const Xf<R>& Xo, const Xf<R>& XsL, const Xf<R>& XoL, int last,
                                             int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
@@ -508,7 +508,7 @@ __device__ __forceinline__ FluxCell<R> flux_cell(const W7x3<R>& wd, const Nbr7& 
 }
 
 template <typename R>
-__device__ __forceinline__ void d_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, int kchunk, int bx, int by) {
+__device__ __forceinline__ void d_ss_flux(const Geo<R>& G, const VR<R>& U, const Slow<R>& SL, const Pert<R>& P, const Work<R>& T, R dtau, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -547,7 +547,7 @@ __device__ __forceinline__ void d_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R>
 // or up times the pivot reciprocal; per column: 1 / (1 - c'_p e'_p+1) for the
 // junction rows p, p+1.
 template <typename R>
-__device__ __forceinline__ void d_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> SL, Fac<R> F,
+__device__ __forceinline__ void d_ss_factor(const Geo<R>& G, const VR<R>& U, const Phys& ph, const Slow<R>& SL, const Fac<R>& F,
                                             double dtau, int bx, int by) {
   const int nv = G.nv, S = G.colp, N = nv - 1;
   const int tx = threadIdx.x & 31, half = threadIdx.x >> 5;
@@ -638,9 +638,9 @@ __device__ __forceinline__ void stage_end_cell(const Xf<R>& Xs, const Xf<R>& Xo,
 // and pt2 and p* from the nonlinear Eq. theta_to_p. One block = 32 columns
 // x 2 warps.
 template <typename R>
-__device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs, Slow<R> SL,
-                                            Pert<R> P, Work<R> T, Fac<R> F, double dtau,
-                                            int want_div, Xf<R> Xo, Xf<R> XsL, Xf<R> XoL, int last, int bx,
+__device__ __forceinline__ void d_ss_solve(const Geo<R>& G, const VR<R>& U, const Phys& ph, const Xf<R>& Xs, const Slow<R>& SL,
+                                            const Pert<R>& P, const Work<R>& T, const Fac<R>& F, double dtau,
+                                            int want_div, const Xf<R>& Xo, const Xf<R>& XsL, const Xf<R>& XoL, int last, int bx,
                                             int by) {
   extern __shared__ double sm[];
   const int nv = G.nv, S = G.colp, N = nv - 1;
@@ -752,7 +752,7 @@ __device__ __forceinline__ void d_ss_solve(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xs,
 // (one thread per column; the update kernel then works on chunks of levels
 // and changes the lowest layer's rho theta)
 template <typename R>
-__device__ __forceinline__ void d_surface_p(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int bx) {
+__device__ __forceinline__ void d_surface_p(const Geo<R>& G, const VR<R>& U, const Phys& ph, const Xf<R>& X, const Work<R>& T, int bx) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const R gamma = pc<R>(ph.gamma, ph.gamma_f), Rd = pc<R>(ph.Rd, ph.Rd_f);
@@ -766,7 +766,7 @@ __device__ __forceinline__ void d_surface_p(Geo<R> G, VR<R> U, Phys ph, Xf<R> X,
 // update written as M (1/(1 + K_v dt) - 1) and rho theta at fixed rho
 // scaled by (T_new / T)^(1/gamma).
 template <typename R>
-__device__ __forceinline__ void d_physics(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Xf<R> XL, Work<R> T, int forcing,
+__device__ __forceinline__ void d_physics(const Geo<R>& G, const VR<R>& U, const Phys& ph, const Xf<R>& X, const Xf<R>& XL, const Work<R>& T, int forcing,
                                           double dt, double hj_dT, int kchunk, int bx, int by) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
@@ -1184,10 +1184,24 @@ __global__ void __launch_bounds__(32 * kSolveWarps)
 // member table. Per-member switches (hyperdiffusion, divergence damping,
 // forcing) are uniform over a block. s is the RK stage, j the small step.
 
-#define THOR_MEMBER()                 \
-  const int2 e = map[blockIdx.x];     \
-  const Member<R>& a = M[e.x];        \
-  const Xf<R> Xs = s == 0 ? a.Xt : a.Xst
+// The block's member record is copied to shared memory once, and the device
+// functions read its fields from there as they need them (by reference), so
+// that the record's pointers do not all occupy registers.
+template <typename T>
+__device__ __forceinline__ const T& stage_record(const T* src, T* dst) {
+  static_assert(sizeof(T) % 4 == 0, "record of whole words");
+  const uint32_t* a = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* b = reinterpret_cast<uint32_t*>(dst);
+  for (int w = threadIdx.x; w < (int)(sizeof(T) / 4); w += blockDim.x) b[w] = a[w];
+  __syncthreads();
+  return *dst;
+}
+
+#define THOR_MEMBER()                                   \
+  __shared__ Member<R> a_sm;                            \
+  const int2 e = map[blockIdx.x];                       \
+  const Member<R>& a = stage_record(M + e.x, &a_sm);    \
+  const Xf<R>& Xs = s == 0 ? a.Xt : a.Xst
 
 template <typename R>
 __global__ void ke_derived(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
