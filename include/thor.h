@@ -475,8 +475,14 @@ int thor_mlp_info(const thor_mlp* mlp, size_t* nparam);
 int thor_mlp_get_params(thor_mlp* mlp, float* host, size_t n);
 /* GEMM path. THOR_MLP_TUNE_TCGEN05: 1 (default) runs the products as
  * tcgen05.mma (bfloat16 operands in shared memory, float32 accumulators in
- * tensor memory, 128-row tiles); 0 runs the warp-level mma.sync kernel.
- * Both accumulate in float32; results agree to summation order. */
+ * tensor memory, 128-row tiles) with the operands brought in by TMA in the
+ * 128-byte swizzled layout through a 4-stage ring, when every layer width
+ * is a multiple of 8 (the forward then also keeps transposed copies of the
+ * weights and layer inputs so that every product reads both operands along
+ * its contraction), else with threads staging the operands; 2 forces the
+ * thread-staged tcgen05 kernel; 0 runs the warp-level mma.sync kernel. All
+ * accumulate in float32; results agree to summation order. Other values:
+ * THOR_EINVAL. */
 enum { THOR_MLP_TUNE_TCGEN05 = 0 };
 int thor_mlp_tune(thor_mlp* mlp, int knob, int value);
 /* Sets the float32 master weights and resets the Adam moments. */

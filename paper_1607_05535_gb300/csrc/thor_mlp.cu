@@ -4,10 +4,13 @@
 // master weights, bfloat16 weights and layer inputs on the tensor cores and
 // float32 accumulation; trained with a mean-squared-error loss and Adam
 // (Kingma and Ba 2015). The GEMMs run on the fifth-generation tensor cores:
-// tcgen05.mma kind::f16 with bfloat16 operands staged in shared memory and
-// the float32 accumulator in tensor memory (k_gemm_tc); the warp-level
-// mma.sync m16n8k16 kernel (k_gemm_bf16) is kept as a switchable reference
-// path (thor_mlp_tune).
+// tcgen05.mma kind::f16 with bfloat16 operands in shared memory and the
+// float32 accumulator in tensor memory, the operands brought in by TMA in
+// the 128-byte swizzled layout (k_gemm_tma; transposed copies of the
+// weights, layer inputs and gradients make every product read both operands
+// along its contraction) or, for widths that are not multiples of 8, staged
+// by threads (k_gemm_tc); the warp-level mma.sync m16n8k16 kernel
+// (k_gemm_bf16) is kept as a switchable reference path (thor_mlp_tune).
 //
 // Closure: per column, the inputs are 5 fields (rho', M_x, M_y, M_z, Th') at
 // all levels and the neighbour means of the same (as anomalies); the
@@ -15,8 +18,10 @@
 // added as field += dt * tendency after every large step. Training data come
 // from high-resolution runs area-averaged onto the coarse grid
 // (thor_coarse_grain).
+#include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -129,25 +134,36 @@ __global__ void k_relu_back(float* g, const __nv_bfloat16* h, __nv_bfloat16* gb,
   }
 }
 
-// column sums of g [M][N] (deterministic: one thread per column, fixed order)
-// out[n] = sum over m of g[m][n]: a block sums 32 columns, its 32 x 32
-// threads each take every 32nd row, then the 32 partials of a column are
-// added in a fixed order
-__global__ void __launch_bounds__(1024) k_colsum(const float* g, int M, int N, float* out) {
-  __shared__ float part[32][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, n = blockIdx.x * 32 + tx;
-  float s = 0.0f;
+// column sums of g [M][N] in two deterministic passes: partial sums over
+// row blocks of 128 (k_colsum_part: 32 columns x 8 row lanes per block,
+// lanes added in a fixed order), then one warp per column adds the R
+// partials part[R][N] in a fixed order (k_colsum_final)
+__global__ void __launch_bounds__(256) k_colsum_part(const float* g, int M, int N, float* part) {
+  __shared__ float s[8][33];
+  const int tx = threadIdx.x, ty = threadIdx.y, n = blockIdx.x * 32 + tx, r0 = blockIdx.y * 128;
+  const int r1 = min(r0 + 128, M);
+  float a = 0.0f;
   if (n < N) {
 #pragma unroll 4
-    for (int m = ty; m < M; m += 32) s += g[(size_t)m * N + n];
+    for (int r = r0 + ty; r < r1; r += 8) a += g[(size_t)r * N + n];
   }
-  part[ty][tx] = s;
+  s[ty][tx] = a;
   __syncthreads();
   if (ty == 0 && n < N) {
     float t = 0.0f;
-    for (int j = 0; j < 32; ++j) t += part[j][tx];
-    out[n] = t;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t += s[j][tx];
+    part[(size_t)blockIdx.y * N + n] = t;
   }
+}
+__global__ void k_colsum_final(const float* part, int R, int N, float* out) {
+  const int col = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (col >= N) return;
+  float t = 0.0f;
+  for (int j = lane; j < R; j += 32) t += part[(size_t)j * N + col];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) out[col] = t;
 }
 
 // dY = 2 (Y - T) / (M N); per-block partial sums of (Y - T)^2
@@ -168,11 +184,19 @@ __global__ void k_mse(const float* y, const float* t, float* dy, size_t n, float
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-__global__ void k_sum_parts(const float* part, int n, float scale, float* out) {
-  if (threadIdx.x || blockIdx.x) return;
-  float s = 0.0f;
-  for (int i = 0; i < n; ++i) s += part[i];
-  *out = s * scale;
+// scale * (sum of part[0..n)), one block of 1024 threads, fixed-order tree
+__global__ void __launch_bounds__(1024) k_sum_parts(const float* part, int n, float scale, float* out) {
+  __shared__ float sh[1024];
+  const int t = threadIdx.x;
+  float a = 0.0f;
+  for (int i = t; i < n; i += 1024) a += part[i];
+  sh[t] = a;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if (t < w) sh[t] += sh[t + w];
+    __syncthreads();
+  }
+  if (t == 0) *out = sh[0] * scale;
 }
 
 // Adam on float32 master weights, refreshing the bfloat16 copy of weights
@@ -438,6 +462,268 @@ size_t tc_smem_bytes(int nt) {
   const size_t cap = (size_t)(228 * 1024) / ctas - 2048;
   return std::max(tiles, std::min(cap, (size_t)200 * 1024));
 }
+
+// ------------------------------------------------ TMA-fed tcgen05 GEMM
+//
+// C[M][N] = A B^T for operands that both run along k in global memory
+// (A [M][lda], B [N][ldb], ld a multiple of 8 elements, 16-byte aligned).
+// The copy engine brings 128 x 64 and NT x 64 bfloat16 boxes into shared
+// memory in the 128-byte swizzled K-major layout: one 128-byte row per
+// matrix row, its eight 16-byte chunks permuted by XOR with (row mod 8),
+// groups of 8 rows 1024 B apart (the stride byte offset); the four MMAs of
+// a 64-deep chunk start 32 B apart inside those rows. Rows and k outside
+// the operands arrive as zeros (tensor-map bounds). Stages form a ring of
+// S <= TMA_STAGES with a full barrier (copies landed, by transaction bytes) and
+// an empty barrier (the MMAs that read the stage are done, by
+// tcgen05.commit). One thread issues copies and MMAs; all four warps run
+// the epilogue, which can also store the bfloat16 result transposed (CbT,
+// [N][ldt]) for a later product that contracts over the rows.
+
+constexpr int TMA_STAGES = 4, TMA_KC = 64, kMaxSplit = 8;
+
+// shared-memory matrix descriptor of the 128-byte swizzled K-major layout:
+// stride byte offset 1024 (8-row atoms), leading byte offset unused within
+// one swizzle row (encoded 1), version bits 46-47 = 1, layout type 2
+// (SWIZZLE_128B) at bits 61-63
+__device__ __forceinline__ uint64_t tc_desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
+}
+
+__device__ __forceinline__ void tma_load_box(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__global__ void __launch_bounds__(128, 1) k_gemm_tma(const __grid_constant__ CUtensorMap ma,
+                                                     const __grid_constant__ CUtensorMap mb, int M, int N, int K,
+                                                     float* C, int ldc, const float* bias, int relu,
+                                                     __nv_bfloat16* Cb, int ldcb, __nv_bfloat16* CbT, int ldt,
+                                                     int NT, int S, int kc_per, size_t c_split, int* err) {
+  extern __shared__ unsigned char tma_raw[];
+  __shared__ uint64_t full[TMA_STAGES], empty[TMA_STAGES], done;   // the first S in use
+  __shared__ uint32_t tmem_base;
+  __shared__ int all_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * NT;
+  const uint32_t ncols = (uint32_t)tc_cols(NT);
+  const uint32_t raw = smem_u32(tma_raw), base = (raw + 1023u) & ~1023u;   // swizzle atoms need 1024 B alignment
+  const uint32_t a_bytes = TC_M * TMA_KC * 2, stage_bytes = (uint32_t)(TC_M + NT) * TMA_KC * 2;
+  if (warp == 0) tc_alloc(&tmem_base, ncols);
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    mbar_init_fence();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  // split-K: blockIdx.z takes chunks [c0, c0 + nchunks) and stores its
+  // partial product at C + blockIdx.z * c_split
+  const int c0 = blockIdx.z * kc_per;
+  const int nchunks = min(kc_per, (K + TMA_KC - 1) / TMA_KC - c0);
+  C += blockIdx.z * c_split;
+  if (tid == 0) {
+    const uint32_t idesc = tc_idesc(TC_M, NT);
+    auto load = [&](int c) {
+      const int s = c % S;
+      const uint32_t a = base + (uint32_t)s * stage_bytes;
+      mbar_arrive_expect_tx(&full[s], stage_bytes);
+      tma_load_box(a, &ma, (c0 + c) * TMA_KC, m0, &full[s]);
+      tma_load_box(a + a_bytes, &mb, (c0 + c) * TMA_KC, n0, &full[s]);
+    };
+    int issued = 0, c = 0;
+    bool ok = true;
+    for (; issued < nchunks && issued < S; ++issued) load(issued);
+    for (; c < nchunks; ++c) {
+      const int s = c % S;
+      if (!mbar_wait(&full[s], (uint32_t)(c / S) & 1u)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a = base + (uint32_t)s * stage_bytes, b = a + a_bytes;
+#pragma unroll
+      for (int kk = 0; kk < TMA_KC / 16; ++kk)
+        tc_mma(tmem, tc_desc_sw128(a + kk * 32), tc_desc_sw128(b + kk * 32), idesc, (c > 0 || kk > 0) ? 1u : 0u);
+      tc_commit(&empty[s]);
+      // refill the stage of the previous chunk (issued == c - 1 + S)
+      if (c >= 1 && issued < nchunks) {
+        const int p = c - 1;
+        if (!mbar_wait(&empty[p % S], (uint32_t)(p / S) & 1u)) {
+          ok = false;
+          ++c;
+          break;
+        }
+        load(issued++);
+      }
+    }
+    // on a timed-out wait, let the copies still in flight (chunks c .. issued - 1) land first (bounded)
+    for (int q = c; q < issued; ++q) mbar_wait(&full[q % S], (uint32_t)(q / S) & 1u);
+    tc_commit(&done);                                   // completes when every MMA issued above has
+    const bool fin = mbar_wait(&done, 0u);
+    all_ok = ok && fin;
+    if (!(ok && fin)) atomicExch(err, 1);
+  }
+  __syncthreads();
+  __syncwarp();
+  tc_fence_after();
+  if (all_ok) {
+    // straight from the accumulator: lane r of warp w holds row 32w + r, 16
+    // columns per tcgen05.ld; row-major stores move 16-byte vectors (N and
+    // the leading dimensions are multiples of 8), the transposed store is
+    // coalesced across the warp's 32 consecutive rows
+    const int row = m0 + warp * 32 + lane;
+    for (int c = 0; c < NT; c += 16) {
+      uint32_t v[16];
+      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+      const int n = n0 + c;
+      if (n >= N) break;                                 // warp-uniform
+      float x[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        x[j] = __uint_as_float(v[j]);
+        if (bias && n + j < N) x[j] += bias[n + j];
+        if (relu) x[j] = x[j] > 0.0f ? x[j] : 0.0f;
+      }
+      if (row < M) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (n + 8 * h >= N) break;
+          const float* y = x + 8 * h;
+          if (C) {
+            float4* o = reinterpret_cast<float4*>(C + (size_t)row * ldc + n + 8 * h);
+            o[0] = make_float4(y[0], y[1], y[2], y[3]);
+            o[1] = make_float4(y[4], y[5], y[6], y[7]);
+          }
+          if (Cb) {
+            uint4 q;
+            q.x = pack_bf16(__float2bfloat16(y[0]), __float2bfloat16(y[1]));
+            q.y = pack_bf16(__float2bfloat16(y[2]), __float2bfloat16(y[3]));
+            q.z = pack_bf16(__float2bfloat16(y[4]), __float2bfloat16(y[5]));
+            q.w = pack_bf16(__float2bfloat16(y[6]), __float2bfloat16(y[7]));
+            *reinterpret_cast<uint4*>(Cb + (size_t)row * ldcb + n + 8 * h) = q;
+          }
+        }
+        if (CbT) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (n + j < N) CbT[(size_t)(n + j) * ldt + row] = __float2bfloat16(x[j]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  __syncwarp();
+  if (warp == 0) tc_dealloc(tmem, ncols);
+}
+
+size_t tma_smem_bytes(int nt, int stages = TMA_STAGES) {
+  return 1024 + (size_t)stages * (TC_M + nt) * TMA_KC * 2;
+}
+
+// C[M][N] (ldc) = sum over z < splits of W[z][M][N] (row length N), in z
+// order; N a multiple of 4
+__global__ void k_split_sum(const float* W, int splits, int M, int N, float* C, int ldc) {
+  const size_t n4 = (size_t)M * (N / 4);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = i / (N / 4), c = (i % (N / 4)) * 4;
+    float4 a = *reinterpret_cast<const float4*>(W + r * N + c);
+    for (int z = 1; z < splits; ++z) {
+      const float4 b = *reinterpret_cast<const float4*>(W + (size_t)z * M * N + r * N + c);
+      a.x += b.x;
+      a.y += b.y;
+      a.z += b.z;
+      a.w += b.w;
+    }
+    *reinterpret_cast<float4*>(C + r * ldc + c) = a;
+  }
+}
+
+// x (float32 [m][K]) -> h (bfloat16 [m][K]) and its transpose hT ([K][ldt])
+// through a 32 x 32 shared-memory tile (both stores coalesced)
+__global__ void k_to_bf16_t(const float* x, __nv_bfloat16* h, __nv_bfloat16* hT, int m, int K, int ldt) {
+  __shared__ float t[32][33];
+  const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int r = r0 + j, k = k0 + tx;
+    float v = 0.0f;
+    if (r < m && k < K) {
+      v = x[(size_t)r * K + k];
+      h[(size_t)r * K + k] = __float2bfloat16(v);
+    }
+    t[j][tx] = v;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int k = k0 + j, r = r0 + tx;
+    if (k < K && r < m) hT[(size_t)k * ldt + r] = __float2bfloat16(t[tx][j]);
+  }
+}
+
+// k_relu_back with the bfloat16 gradient also stored transposed (gbT
+// [N][ldt]) and the column sums of the masked float32 gradient over each
+// 32-row tile in part[row tile][N] (fixed order; k_colsum_final adds them)
+__global__ void k_relu_back_t(float* g, const __nv_bfloat16* h, __nv_bfloat16* gb, __nv_bfloat16* gbT, int m, int N,
+                              int ldt, int mask, float* part) {
+  __shared__ float t[32][33];
+  const int n0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int r = r0 + j, n = n0 + tx;
+    float v = 0.0f;
+    if (r < m && n < N) {
+      const size_t i = (size_t)r * N + n;
+      v = g[i];
+      if (mask && !(__bfloat162float(h[i]) > 0.0f)) v = 0.0f;
+      g[i] = v;
+      gb[i] = __float2bfloat16(v);
+    }
+    t[j][tx] = v;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int n = n0 + j, r = r0 + tx;
+    if (n < N && r < m) gbT[(size_t)n * ldt + r] = __float2bfloat16(t[tx][j]);
+  }
+  if (threadIdx.y == 0 && n0 + tx < N) {
+    float a = 0.0f;
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) a += t[j][tx];
+    part[(size_t)blockIdx.y * N + n0 + tx] = a;
+  }
+}
+
+// bfloat16 weights W_l [K][N] -> their transposes [N][K] at wtoff[l], every
+// layer in one launch (blockIdx.z = layer)
+struct WTable {
+  int K[16], N[16];
+  unsigned long long woff[16], wtoff[16];
+};
+__global__ void k_weights_t(const __nv_bfloat16* pb, __nv_bfloat16* pbt, WTable T) {
+  __shared__ __nv_bfloat16 t[32][34];
+  const int l = blockIdx.z, K = T.K[l], N = T.N[l];
+  const int n0 = blockIdx.x * 32, k0 = blockIdx.y * 32, tx = threadIdx.x;
+  if (n0 >= N || k0 >= K) return;
+  const __nv_bfloat16* W = pb + T.woff[l];
+  __nv_bfloat16* Wt = pbt + T.wtoff[l];
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int k = k0 + j, n = n0 + tx;
+    if (k < K && n < N) t[j][tx] = W[(size_t)k * N + n];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int n = n0 + j, k = k0 + tx;
+    if (n < N && k < K) Wt[(size_t)n * K + k] = t[tx][j];
+  }
+}
 }  // namespace
 }  // namespace thor
 
@@ -445,8 +731,12 @@ size_t tc_smem_bytes(int nt) {
 
 struct thor_mlp {
   std::vector<int> sizes;              // layer widths, n_layers + 1 entries
-  int use_tc = 1;                      // tcgen05 GEMMs (1) or the mma.sync reference path (0)
-  int* err = nullptr;                  // device flag of the tcgen05 kernel
+  int use_tc = 1;                      // tcgen05 TMA-fed (1) or thread-staged (2), mma.sync reference path (0)
+  bool tma_ok = false;                 // every width a multiple of 8 and the tensor-map encoder found
+  bool fwd_tma = false;                // the last forward kept the transposed layer inputs
+  int sms = 148;                       // streaming multiprocessors of the device
+  int ldt = 0;                         // row length of the transposed buffers (max_batch rounded up to 64)
+  int* err = nullptr;                  // device flag of the tcgen05 kernels
   int max_batch = 0;
   cudaStream_t stream = nullptr;
   size_t nparam = 0;
@@ -454,12 +744,19 @@ struct thor_mlp {
   void* arena = nullptr;
   float *p = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;   // flat float32 [nparam]
   __nv_bfloat16* pb = nullptr;         // bf16 copy of all parameters (weights used)
+  __nv_bfloat16* pbt = nullptr;        // bf16 transposed weights, W_l^T [N][K] at wtoff[l]
+  std::vector<size_t> wtoff;
   std::vector<__nv_bfloat16*> h;       // layer inputs (bf16) [max_batch][sizes[l]]
+  std::vector<__nv_bfloat16*> hT;      // their transposes [sizes[l]][ldt] (TMA-fed backward)
+  __nv_bfloat16* gbT = nullptr;        // transposed bf16 gradient scratch [max width][ldt]
   std::vector<float*> z;               // hidden outputs / gradients (float32) [max_batch][sizes[l+1]]
   __nv_bfloat16* gb = nullptr;         // bf16 gradient scratch [max_batch][max width]
   float* y = nullptr;                  // network output [max_batch][n_out]
   float* dy = nullptr;                 // output gradient
   float* part = nullptr;               // reduction partials
+  float* cpart = nullptr;              // column-sum partials [row blocks][max width]
+  float* ws = nullptr;                 // split-K partial products [splits][M][N]
+  size_t ws_elems = 0;
   int last_m = 0;
   long long step_count = 0;
   int n_layers() const { return (int)sizes.size() - 1; }
@@ -493,16 +790,117 @@ void gemm(const thor_mlp* net, int M, int N, int K, const __nv_bfloat16* A, int 
   k_gemm_bf16<<<grid, 128, 0, st>>>(M, N, K, A, lda, transA, B, ldb, transB, C, ldc, bias, relu, Cb, ldcb);
 }
 
-// forward for m rows of x (float32 [m][n_in] on the device)
-int mlp_forward(thor_mlp* net, const float* x, int m) {
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_tiled() {
+  static void* fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+  }
+  return reinterpret_cast<EncodeTiled>(fn);
+}
+
+// tensor map of a bfloat16 operand X [rows][ld] read along k (k < kext):
+// boxes of 64 k x box_rows rows, 128-byte swizzle, zeros outside
+bool encode_operand(CUtensorMap* map, const __nv_bfloat16* X, int kext, int rows, int ld, int box_rows) {
+  EncodeTiled enc = encode_tiled();
+  if (!enc || (reinterpret_cast<uintptr_t>(X) & 15) || ld % 8) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)kext, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)TMA_KC, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(X), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// C = A B^T, A [M][lda] and B [N][ldb] both along k, on k_gemm_tma: the
+// widest tile (fewest re-reads of A) that still gives a CTA per SM, else
+// 16 columns
+int gemm_tma(const thor_mlp* net, int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B,
+             int ldb, float* C, int ldc, const float* bias, int relu, __nv_bfloat16* Cb, int ldcb,
+             __nv_bfloat16* CbT, int ldt) {
+  const int mtiles = (M + TC_M - 1) / TC_M;
+  int width = 16;
+  for (int w : {256, 128, 64, 32})
+    if (mtiles * ((N + w - 1) / w) >= net->sms) {
+      width = w;
+      break;
+    }
+  const int ntiles = (N + width - 1) / width;
+  const int nt = ((N + ntiles - 1) / ntiles + 15) / 16 * 16;
+  // a long contraction on too few tiles (the weight gradients: K = batch)
+  // is split along k over the idle SMs; the float32 partials are added in
+  // a fixed order afterwards
+  const int nchunks = (K + TMA_KC - 1) / TMA_KC, ctas = mtiles * ntiles;
+  int splits = 1;
+  if (C && !Cb && !CbT && !bias && !relu && 2 * ctas <= net->sms && nchunks >= 8) {
+    splits = std::min({(net->sms + ctas - 1) / ctas, nchunks / 4, kMaxSplit});
+    while (splits > 1 && (size_t)splits * M * N > net->ws_elems) --splits;
+  }
+  const int kc_per = (nchunks + splits - 1) / splits;
+  splits = (nchunks + kc_per - 1) / kc_per;
+  // the deepest ring that still lets every CTA of the grid be resident at
+  // once (a second, partial wave would double the time of a short product)
+  const int per_sm = (ctas * splits + net->sms - 1) / net->sms;
+  int stages = 2;
+  for (int st = TMA_STAGES; st > 2; --st)
+    if ((size_t)per_sm * (tma_smem_bytes(nt, st) + 2048) <= (size_t)227 * 1024 && per_sm * tc_cols(nt) <= 512) {
+      stages = st;
+      break;
+    }
+  CUtensorMap ma, mb;
+  if (!encode_operand(&ma, A, K, M, lda, TC_M) || !encode_operand(&mb, B, K, N, ldb, nt)) return THOR_ECUDA;
+  dim3 grid(ntiles, mtiles, splits);
+  const size_t smem = tma_smem_bytes(nt, stages);
+  if (splits == 1) {
+    k_gemm_tma<<<grid, 128, smem, net->stream>>>(ma, mb, M, N, K, C, ldc, bias, relu, Cb, ldcb, CbT, ldt, nt, stages,
+                                                  kc_per, 0, net->err);
+  } else {
+    k_gemm_tma<<<grid, 128, smem, net->stream>>>(ma, mb, M, N, K, net->ws, N, nullptr, 0, nullptr, 0, nullptr, 0, nt,
+                                                  stages, kc_per, (size_t)M * N, net->err);
+    const size_t n4 = (size_t)M * N / 4;
+    k_split_sum<<<(int)std::min<size_t>((n4 + 255) / 256, 2048), 256, 0, net->stream>>>(net->ws, splits, M, N, C,
+                                                                                          ldc);
+  }
+  return THOR_OK;
+}
+
+// forward for m rows of x (float32 [m][n_in] on the device); keep_t: also
+// store the transposed layer inputs the TMA-fed backward contracts over
+int mlp_forward(thor_mlp* net, const float* x, int m, bool keep_t = true) {
   cudaStream_t st = net->stream;
   const int L = net->n_layers();
-  k_to_bf16<<<blocks_for((size_t)m * net->sizes[0]), 256, 0, st>>>(x, net->h[0], (size_t)m * net->sizes[0]);
+  const bool tma = net->use_tc == 1 && net->tma_ok;
+  net->fwd_tma = tma && keep_t;
+  if (net->fwd_tma) {
+    dim3 g((net->sizes[0] + 31) / 32, (m + 31) / 32);
+    k_to_bf16_t<<<g, dim3(32, 8), 0, st>>>(x, net->h[0], net->hT[0], m, net->sizes[0], net->ldt);
+  } else {
+    k_to_bf16<<<blocks_for((size_t)m * net->sizes[0]), 256, 0, st>>>(x, net->h[0], (size_t)m * net->sizes[0]);
+  }
   for (int l = 0; l < L; ++l) {
     const int K = net->sizes[l], N = net->sizes[l + 1];
-    const __nv_bfloat16* W = net->pb + net->woff[l];
     const float* b = net->p + net->boff[l];
-    if (l + 1 < L)
+    const bool last = l + 1 == L;
+    if (tma) {
+      // op(B) = W_l read along k from its transposed copy [N][K]
+      int rc = gemm_tma(net, m, N, K, net->h[l], K, net->pbt + net->wtoff[l], K, last ? net->y : nullptr, N, b,
+                        !last, last ? nullptr : net->h[l + 1], N,
+                        last || !net->fwd_tma ? nullptr : net->hT[l + 1], net->ldt);
+      if (rc) return rc;
+      continue;
+    }
+    const __nv_bfloat16* W = net->pb + net->woff[l];
+    if (!last)
       gemm(net, m, N, K, net->h[l], K, 0, W, N, 0, nullptr, 0, b, 1, net->h[l + 1], N);
     else
       gemm(net, m, N, K, net->h[l], K, 0, W, N, 0, net->y, N, b, 0, nullptr, 0);
@@ -519,23 +917,62 @@ int mlp_backward(thor_mlp* net, const float* dy, int m) {
   float* g = net->z[L - 1];
   if (cudaMemcpyAsync(g, dy, (size_t)m * net->sizes[L] * sizeof(float), cudaMemcpyDeviceToDevice, st))
     return THOR_ECUDA;
+  // the TMA-fed products need the transposed inputs of a TMA-fed forward
+  const bool tma = net->fwd_tma && net->use_tc == 1;
   for (int l = L - 1; l >= 0; --l) {
     const int K = net->sizes[l], N = net->sizes[l + 1];
     float* gl = net->z[l];
     const size_t cnt = (size_t)m * N;
+    const __nv_bfloat16* W = net->pb + net->woff[l];
     // relu mask of this layer's output (hidden layers), then bf16 copy
-    k_relu_back<<<blocks_for(cnt), 256, 0, st>>>(gl, l + 1 < L ? net->h[l + 1] : nullptr, net->gb, cnt,
-                                                 l + 1 < L);
-    // dW_l = h_l^T gb  ([K][N]), db_l = column sums of g
-    gemm(net, K, N, m, net->h[l], K, 1, net->gb, N, 0, net->grad + net->woff[l], N, nullptr, 0, nullptr, 0);
-    k_colsum<<<(N + 31) / 32, 1024, 0, st>>>(gl, m, N, net->grad + net->boff[l]);
+    if (tma) {
+      dim3 g((N + 31) / 32, (m + 31) / 32);
+      k_relu_back_t<<<g, dim3(32, 8), 0, st>>>(gl, l + 1 < L ? net->h[l + 1] : nullptr, net->gb, net->gbT, m, N,
+                                               net->ldt, l + 1 < L, net->cpart);
+      // db_l = column sums of g
+      k_colsum_final<<<(N * 32 + 255) / 256, 256, 0, st>>>(net->cpart, (m + 31) / 32, N, net->grad + net->boff[l]);
+      // dW_l = h_l^T gb ([K][N]) from the transposes, both along the batch
+      int rc = gemm_tma(net, K, N, m, net->hT[l], net->ldt, net->gbT, net->ldt, net->grad + net->woff[l], N,
+                        nullptr, 0, nullptr, 0, nullptr, 0);
+      if (rc) return rc;
+    } else {
+      k_relu_back<<<blocks_for(cnt), 256, 0, st>>>(gl, l + 1 < L ? net->h[l + 1] : nullptr, net->gb, cnt,
+                                                   l + 1 < L);
+      // dW_l = h_l^T gb  ([K][N])
+      gemm(net, K, N, m, net->h[l], K, 1, net->gb, N, 0, net->grad + net->woff[l], N, nullptr, 0, nullptr, 0);
+      // db_l = column sums of g
+      k_colsum_part<<<dim3((N + 31) / 32, (m + 127) / 128), dim3(32, 8), 0, st>>>(gl, m, N, net->cpart);
+      k_colsum_final<<<(N * 32 + 255) / 256, 256, 0, st>>>(net->cpart, (m + 127) / 128, N, net->grad + net->boff[l]);
+    }
     if (l > 0) {
-      // g_{l-1} = gb W_l^T ([m][K]) into z[l-1]
-      const __nv_bfloat16* W = net->pb + net->woff[l];
-      gemm(net, m, K, N, net->gb, N, 0, W, N, 1, net->z[l - 1], K, nullptr, 0, nullptr, 0);
+      // g_{l-1} = gb W_l^T ([m][K]) into z[l-1]; W_l [K][N] runs along N, the contraction
+      if (tma) {
+        int rc = gemm_tma(net, m, K, N, net->gb, N, W, N, net->z[l - 1], K, nullptr, 0, nullptr, 0, nullptr, 0);
+        if (rc) return rc;
+      } else {
+        gemm(net, m, K, N, net->gb, N, 0, W, N, 1, net->z[l - 1], K, nullptr, 0, nullptr, 0);
+      }
     }
   }
   return cudaGetLastError() == cudaSuccess ? THOR_OK : THOR_ECUDA;
+}
+
+// refreshes the transposed bfloat16 weights from pb (TMA-fed forward)
+void weights_t(const thor_mlp* net) {
+  if (!net->tma_ok) return;
+  WTable T{};
+  int kmax = 0, nmax = 0;
+  const int L = net->n_layers();
+  for (int l = 0; l < L; ++l) {
+    T.K[l] = net->sizes[l];
+    T.N[l] = net->sizes[l + 1];
+    T.woff[l] = net->woff[l];
+    T.wtoff[l] = net->wtoff[l];
+    kmax = std::max(kmax, T.K[l]);
+    nmax = std::max(nmax, T.N[l]);
+  }
+  dim3 g((nmax + 31) / 32, (kmax + 31) / 32, L);
+  k_weights_t<<<g, dim3(32, 8), 0, net->stream>>>(net->pb, net->pbt, T);
 }
 
 }  // namespace
@@ -563,16 +1000,42 @@ int thor_mlp_create(const int* sizes, int n_sizes, int max_batch, unsigned long 
     net->nparam += sizes[l + 1];
   }
   for (int i = 0; i < n_sizes; ++i) wmax = std::max(wmax, sizes[i]);
+  // the TMA-fed products read rows of 16-byte multiples
+  net->tma_ok = encode_tiled() != nullptr;
+  for (int i = 0; i < n_sizes; ++i) net->tma_ok = net->tma_ok && sizes[i] % 8 == 0;
+  net->ldt = (max_batch + 63) / 64 * 64;
+  size_t nwt = 0;
+  for (int l = 0; l < L; ++l) {
+    net->wtoff.push_back(nwt);
+    nwt += ((size_t)sizes[l] * sizes[l + 1] + 63) / 64 * 64;
+  }
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+      net->sms = sms;
+  }
   // one arena: params, grads, Adam moments, bf16 params, activations
   size_t bytes = 0;
   auto take = [&](size_t b) { size_t o = bytes; bytes += (b + 255) / 256 * 256; return o; };
   size_t o_p = take(net->nparam * 4), o_g = take(net->nparam * 4), o_m = take(net->nparam * 4),
          o_v = take(net->nparam * 4), o_pb = take(net->nparam * 2);
-  std::vector<size_t> o_h, o_z;
+  std::vector<size_t> o_h, o_z, o_ht;
   for (int l = 0; l < L; ++l) o_h.push_back(take((size_t)max_batch * sizes[l] * 2));
   for (int l = 0; l < L; ++l) o_z.push_back(take((size_t)max_batch * sizes[l + 1] * 4));
   size_t o_gb = take((size_t)max_batch * wmax * 2), o_y = take((size_t)max_batch * sizes[L] * 4),
-         o_dy = take((size_t)max_batch * sizes[L] * 4), o_part = take(4096 * 4 + 64), o_err = take(64);
+         o_dy = take((size_t)max_batch * sizes[L] * 4), o_part = take(4096 * 4 + 64), o_err = take(64),
+         o_cpart = take((size_t)((max_batch + 31) / 32) * wmax * 4);
+  size_t o_pbt = 0, o_gbt = 0, o_ws = 0;
+  if (net->tma_ok) {
+    size_t wmn = 0;
+    for (int l = 0; l < L; ++l) wmn = std::max(wmn, (size_t)sizes[l] * sizes[l + 1]);
+    net->ws_elems = (size_t)kMaxSplit * wmn;
+    o_ws = take(net->ws_elems * 4);
+    o_pbt = take(nwt * 2);
+    for (int l = 0; l < L; ++l) o_ht.push_back(take((size_t)sizes[l] * net->ldt * 2));
+    o_gbt = take((size_t)wmax * net->ldt * 2);
+  }
   if (cudaMalloc(&net->arena, bytes) != cudaSuccess) {
     delete net;
     return THOR_ENOMEM;
@@ -590,14 +1053,22 @@ int thor_mlp_create(const int* sizes, int n_sizes, int max_batch, unsigned long 
   net->gb = (__nv_bfloat16*)(base + o_gb);
   net->y = (float*)(base + o_y);
   net->err = (int*)(base + o_err);
+  if (net->tma_ok) {
+    net->pbt = (__nv_bfloat16*)(base + o_pbt);
+    for (int l = 0; l < L; ++l) net->hT.push_back((__nv_bfloat16*)(base + o_ht[l]));
+    net->gbT = (__nv_bfloat16*)(base + o_gbt);
+    net->ws = (float*)(base + o_ws);
+  }
   if (cudaMemsetAsync(net->err, 0, 64, net->stream) ||
-      cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024)) {
+      cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024) ||
+      cudaFuncSetAttribute(k_gemm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes(256))) {
     cudaFree(net->arena);
     delete net;
     return THOR_ECUDA;
   }
   net->dy = (float*)(base + o_dy);
   net->part = (float*)(base + o_part);
+  net->cpart = (float*)(base + o_cpart);
   // He-uniform initial weights from SplitMix64, zero biases
   std::vector<float> host(net->nparam, 0.0f);
   for (int l = 0; l < L; ++l) {
@@ -617,6 +1088,7 @@ int thor_mlp_create(const int* sizes, int n_sizes, int max_batch, unsigned long 
     return THOR_ECUDA;
   }
   k_to_bf16<<<blocks_for(net->nparam), 256, 0, st>>>(net->p, net->pb, net->nparam);
+  weights_t(net);
   if (cudaStreamSynchronize(st)) {
     cudaFree(net->arena);
     delete net;
@@ -644,7 +1116,8 @@ int thor_mlp_get_params(thor_mlp* net, float* host, size_t n) {
 int thor_mlp_tune(thor_mlp* net, int knob, int value) {
   if (!net) return THOR_EINVAL;
   if (knob == THOR_MLP_TUNE_TCGEN05) {
-    net->use_tc = value != 0;
+    if (value < 0 || value > 2) return THOR_EINVAL;
+    net->use_tc = value;
     return THOR_OK;
   }
   return THOR_EINVAL;
@@ -655,6 +1128,7 @@ int thor_mlp_set_params(thor_mlp* net, const float* host, size_t n) {
   if (!net || !host || n != net->nparam) return THOR_EINVAL;
   if (cudaMemcpyAsync(net->p, host, n * 4, cudaMemcpyHostToDevice, net->stream)) return THOR_ECUDA;
   k_to_bf16<<<blocks_for(n), 256, 0, net->stream>>>(net->p, net->pb, n);
+  weights_t(net);
   if (cudaMemsetAsync(net->m, 0, n * 4, net->stream) || cudaMemsetAsync(net->v, 0, n * 4, net->stream))
     return THOR_ECUDA;
   net->step_count = 0;
@@ -688,7 +1162,7 @@ int thor_mlp_train_step(thor_mlp* net, const float* x, const float* target, int 
   const size_t cnt = (size_t)m * net->sizes.back();
   const int nb = std::min(blocks_for(cnt), 1024);
   k_mse<<<nb, 256, 0, st>>>(net->y, target, net->dy, cnt, 1.0f / (float)cnt, net->part);
-  if (loss) k_sum_parts<<<1, 32, 0, st>>>(net->part, nb, 1.0f / (float)cnt, loss);
+  if (loss) k_sum_parts<<<1, 1024, 0, st>>>(net->part, nb, 1.0f / (float)cnt, loss);
   rc = mlp_backward(net, net->dy, m);
   if (rc) return rc;
   net->step_count += 1;
@@ -696,6 +1170,7 @@ int thor_mlp_train_step(thor_mlp* net, const float* x, const float* target, int 
   const float c1 = 1.0f - powf(b1, (float)net->step_count), c2 = 1.0f - powf(b2, (float)net->step_count);
   k_adam<<<blocks_for(net->nparam), 256, 0, st>>>(net->p, net->grad, net->m, net->v, net->pb, net->nparam, lr,
                                                   b1, b2, c1, c2, 1e-8f);
+  weights_t(net);
   return cudaGetLastError() == cudaSuccess ? THOR_OK : THOR_ECUDA;
 }
 
@@ -787,7 +1262,7 @@ int closure_evaluate_t(thor_state* s) {
   const int Fin = 2 * kClosureFields * nv, Fout = kClosureFields * nv;
   for (int c0 = 0; c0 < ncol; c0 += net->max_batch) {
     const int m = std::min(net->max_batch, ncol - c0);
-    int rc = mlp_forward(net, cb.x + (size_t)c0 * Fin, m);
+    int rc = mlp_forward(net, cb.x + (size_t)c0 * Fin, m, false);
     if (rc) return rc;
     if (cudaMemcpyAsync(cb.y + (size_t)c0 * Fout, net->y, (size_t)m * Fout * 4, cudaMemcpyDeviceToDevice, st))
       return THOR_ECUDA;

@@ -6,7 +6,9 @@
     python -m paper_1607_05535_gb300.run --mlp --steps 3
 
 --mlp runs training steps of the closure-sized MLP (320-256-256-256-160,
-batch 1024) on seeded random data.
+batch --mlp-batch, default 1024) on seeded random data, on the GEMM path
+--mlp-path; --mlp-timed N adds the mean time of N further training steps
+and of N forwards.
 
 Workloads (seeded, synthetic; module ``workloads`` at the repository root):
 hs_g4 (Held-Suarez glevel 4 x 20), hs_g6 (glevel 6 x 32), hj_g6 (hot
@@ -72,19 +74,39 @@ def run_ensemble(thor, wls, steps, spring_iters):
             thor.thor_grid_destroy(g)
 
 
-def run_mlp(thor, torch, steps):
+def run_mlp(thor, torch, steps, path=1, batch=1024, timed=0):
+    """`steps` training steps of the closure-sized network on the default
+    stream; with timed > 0, then the mean time of `timed` further training
+    steps and of `timed` forwards (CUDA events on that stream)."""
     sizes = [320, 256, 256, 256, 160]
-    net = thor.thor_mlp_create(sizes, 1024, seed=1)
+    net = thor.thor_mlp_create(sizes, batch, seed=1)
     try:
+        thor.thor_mlp_tune(net, thor.THOR_MLP_TUNE_TCGEN05, path)
         g = torch.Generator(device="cuda")
         g.manual_seed(5)
-        x = torch.randn(1024, sizes[0], device="cuda", generator=g)
-        t = torch.randn(1024, sizes[-1], device="cuda", generator=g)
+        x = torch.randn(batch, sizes[0], device="cuda", generator=g)
+        t = torch.randn(batch, sizes[-1], device="cuda", generator=g)
+        y = torch.empty(batch, sizes[-1], device="cuda")
         loss = torch.zeros(1, device="cuda")
         for _ in range(steps):
             thor.thor_mlp_train_step(net, x, t, 1e-3, loss)
         thor.thor_mlp_get_params(net)
-        return {"mlp": sizes, "batch": 1024, "steps": steps, "loss": float(loss.item())}
+        out = {"mlp": sizes, "batch": batch, "path": path, "steps": steps, "loss": float(loss.item())}
+        if timed > 0:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            torch.cuda.synchronize()
+            ev[0].record()
+            for _ in range(timed):
+                thor.thor_mlp_train_step(net, x, t, 1e-3, loss)
+            ev[1].record()
+            for _ in range(timed):
+                thor.thor_mlp_forward(net, x, y)
+            ev[2].record()
+            torch.cuda.synchronize()
+            thor.thor_mlp_get_params(net)
+            out["ms_train_step"] = ev[0].elapsed_time(ev[1]) / timed
+            out["ms_forward"] = ev[1].elapsed_time(ev[2]) / timed
+        return out
     finally:
         thor.thor_mlp_destroy(net)
 
@@ -99,6 +121,10 @@ def main(argv=None):
     ap.add_argument("--solve-tma", type=int, default=1, choices=[0, 1])
     ap.add_argument("--ensemble", action="store_true")
     ap.add_argument("--mlp", action="store_true")
+    ap.add_argument("--mlp-path", type=int, default=1, choices=[0, 1, 2],
+                    help="GEMM path: 1 TMA-fed tcgen05, 2 thread-staged tcgen05, 0 mma.sync")
+    ap.add_argument("--mlp-batch", type=int, default=1024)
+    ap.add_argument("--mlp-timed", type=int, default=0)
     args = ap.parse_args(argv)
     import torch
     import paper_1607_05535_gb300 as thor
@@ -107,7 +133,7 @@ def main(argv=None):
     torch.cuda.set_device(0)
     wls, table = _workloads()
     if args.mlp:
-        out = run_mlp(thor, torch, args.steps)
+        out = run_mlp(thor, torch, args.steps, args.mlp_path, args.mlp_batch, args.mlp_timed)
     elif args.ensemble:
         out = run_ensemble(thor, wls, args.steps, args.spring_iters)
     else:
