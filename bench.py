@@ -656,7 +656,7 @@ def run_thor(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _config(wl),
         "precision": ("mixed: f32 stencils and tendencies, the state as compensated f32 pairs, f64 vertical "
-                      "solve and reductions"),
+                      "factorisation with a double-float elimination per small step, f64 reductions"),
         "model_days_per_hour": days_per_hour,
         "error": err,
         "plain_float_state": plain,

@@ -142,6 +142,12 @@ __global__ void k_convert_probe(long long n, unsigned long long seed, unsigned l
     const double d = __longlong_as_double((long long)b);
     const float fa = d2f_alu(d), fh = __double2float_rn(d);
     if (__float_as_uint(fa) != __float_as_uint(fh) && !(fa != fa && fh != fh)) ++local;
+    // double-float split: hi, and the float64-exact remainder rounded
+    const float2 sp = df_split(d);
+    const float lh = __double2float_rn(d - (double)fh);
+    if ((__float_as_uint(sp.x) != __float_as_uint(fh) && !(sp.x != sp.x && fh != fh)) ||
+        (__float_as_uint(sp.y) != __float_as_uint(lh) && !(sp.y != sp.y && lh != lh)))
+      ++local;
     // binary32 -> binary64
     const float f = __uint_as_float((uint32_t)(r2 >> 7));
     const double da = f2d_alu(f), dh = (double)f;

@@ -103,10 +103,12 @@ template <typename R> __device__ __forceinline__ R pc(double d, float f);
 template <> __device__ __forceinline__ double pc<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float pc<float>(double, float f) { return f; }
 
-// Float64 factors of the per-stage vertical matrix: planes [nv + 1][colp]
-// (rows 1..nv-1 used) and one plane for the junction of the two sweeps. Per
-// row: the pivot reciprocal, c' (downward sweep) or e' (upward sweep), and q,
-// the off-diagonal entry lo (down) or up (up) times the pivot reciprocal.
+// Factors of the per-stage vertical matrix, computed in float64: planes
+// [nv + 1][colp] (rows 1..nv-1 used) and one plane for the junction of the
+// two sweeps. Per row: the pivot reciprocal, c' (downward sweep) or e'
+// (upward sweep), and q, the off-diagonal entry lo (down) or up (up) times
+// the pivot reciprocal. 8 bytes per entry: float64 values for float64
+// states, double-float pairs (float2, df_split) for float-storage states.
 template <typename R>
 struct Fac {
   double *inv, *cf, *junction, *q;
@@ -225,6 +227,75 @@ __device__ __forceinline__ double rcp64_1(double x) {
   double r = f2d_alu(__frcp_rn(d2f_alu(x)));
   return fma(r, fma(-x, r, 1.0), r);
 }
+
+// Double-float numbers: an unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi) / 2, about 48 significant bits, on the float32 pipes
+// (double-double arithmetic of Hida, Li and Bailey 2001, with float words).
+// The column elimination of float-storage states runs in this form: its
+// row recurrences are chains of dependent operations, and on the GB300 a
+// dependent float64 FMA takes 64 cycles per step (a float32 one under 5),
+// so a double-float row step (about 18 float32 operations) finishes in
+// about a fifth of the time of the float64 one. The error-free parts use
+// explicitly rounded intrinsics, which the compiler never contracts into
+// FMAs.
+//
+// splits a float64 value into its double-float pair: hi = x rounded to
+// float (nearest, ties to even), lo = the remainder x - hi rounded to float.
+// With the 53-bit significand M and exponent E of x, hi = H 2^(E-23) for
+// H = M / 2^29 rounded, and the remainder is exactly (M - H 2^29) 2^(E-52),
+// so both come from integer operations and exact scalings by powers of two;
+// exponents outside [-70, 126] (zero, tiny, huge, non-finite values) take
+// the float64 route.
+__device__ __forceinline__ float2 df_split(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long a = u & 0x7fffffffffffffffull;
+  const int E = (int)(a >> 52) - 1023;
+  if (E < -70 || E > 126) {
+    const float h = d2f_alu(x);
+    return make_float2(h, d2f_alu(x - f2d_alu(h)));
+  }
+  const unsigned long long M = (a & ((1ull << 52) - 1)) | (1ull << 52);
+  unsigned long long H = M >> 29;
+  long long rem = (long long)(M & ((1ull << 29) - 1));
+  if (rem > (1ll << 28) || (rem == (1ll << 28) && (H & 1ull))) {
+    H += 1;
+    rem -= 1ll << 29;
+  }
+  float h = __fmul_rn(__int2float_rn((int)H), __int_as_float((E - 23 + 127) << 23));
+  float l = __fmul_rn(__int2float_rn((int)rem), __int_as_float((E - 52 + 127) << 23));
+  if (u >> 63) {
+    h = -h;
+    l = -l;
+  }
+  return make_float2(h, l);
+}
+// (ph + pl) - c x, renormalised: the product's error-free high part by FMA
+// (Dekker's TwoProduct), the difference of the high words by Knuth's
+// TwoSum, the low words added to the error, then one fast TwoSum
+__device__ __forceinline__ float2 df_fms(float ph, float pl, float2 c, float2 x) {
+  const float th = __fmul_rn(c.x, x.x);
+  const float tl = __fmaf_rn(c.x, x.y, __fmaf_rn(c.y, x.x, __fmaf_rn(c.x, x.x, -th)));
+  const float s = __fsub_rn(ph, th);
+  const float bb = __fsub_rn(s, ph);
+  const float e = __fadd_rn(__fsub_rn(__fsub_rn(ph, __fsub_rn(s, bb)), __fadd_rn(th, bb)), __fsub_rn(pl, tl));
+  const float h = __fadd_rn(s, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+// r inv - q d for a float r: the sweep step of the elimination
+__device__ __forceinline__ float2 df_sweep(float r, float2 inv, float2 q, float2 d) {
+  const float ph = __fmul_rn(r, inv.x);
+  const float pl = __fmaf_rn(r, inv.y, __fmaf_rn(r, inv.x, -ph));
+  return df_fms(ph, pl, q, d);
+}
+// a b, renormalised
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float h = __fmul_rn(a.x, b.x);
+  const float l = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, __fmaf_rn(a.x, b.x, -h)));
+  const float s = __fadd_rn(h, l);
+  return make_float2(s, __fsub_rn(l, __fsub_rn(s, h)));
+}
+// the float nearest to hi + lo (one rounding of the exact sum)
+__device__ __forceinline__ float df_to_float(float2 a) { return __fadd_rn(a.x, a.y); }
 
 // read-only load through the non-coherent path: the fields a kernel reads
 // are never written by another thread of the same kernel, so the compiler may

@@ -526,6 +526,21 @@ __device__ __forceinline__ void d_ss_flux(const Geo<R>& G, const VR<R>& U, const
   }
 }
 
+// one row's factors, as float64 values or, for float-storage states, as
+// double-float pairs
+template <typename R>
+__device__ __forceinline__ void fac_store(const Fac<R>& F, int i, double inv, double cf, double q) {
+  if (sizeof(R) == sizeof(double)) {
+    F.inv[i] = inv;
+    F.cf[i] = cf;
+    F.q[i] = q;
+  } else {
+    reinterpret_cast<float2*>(F.inv)[i] = df_split(inv);
+    reinterpret_cast<float2*>(F.cf)[i] = df_split(cf);
+    reinterpret_cast<float2*>(F.q)[i] = df_split(q);
+  }
+}
+
 // HE-VI column step, part 2 (matrix). Substituting Eqs. dens2 and pt2 into
 // Eq. momr2 gives at the interior interfaces m = 1..nv-1 (rigid lid: W* = 0
 // at m = 0 and nv)
@@ -579,11 +594,7 @@ __device__ __forceinline__ void d_ss_factor(const Geo<R>& G, const VR<R>& U, con
       coef(m, lo, di, up);
       const double inv = inv_of(di - lo * last);
       last = up * inv;
-      if (valid) {
-        F.inv[m * S + c] = inv;
-        F.cf[m * S + c] = last;
-        F.q[m * S + c] = lo * inv;
-      }
+      if (valid) fac_store(F, m * S + c, inv, last, lo * inv);
     }
   } else {
     for (int m = N; m > p; --m) {
@@ -591,16 +602,18 @@ __device__ __forceinline__ void d_ss_factor(const Geo<R>& G, const VR<R>& U, con
       coef(m, lo, di, up);
       const double inv = inv_of(di - up * last);
       last = lo * inv;
-      if (valid) {
-        F.inv[m * S + c] = inv;
-        F.cf[m * S + c] = last;
-        F.q[m * S + c] = up * inv;
-      }
+      if (valid) fac_store(F, m * S + c, inv, last, up * inv);
     }
   }
   sj[half][tx] = last;     // c'_p (warp 0) and e'_p+1 (warp 1)
   __syncthreads();
-  if (half == 0 && valid) F.junction[c] = p < N ? 1.0 / (1.0 - sj[0][tx] * sj[1][tx]) : 1.0;
+  if (half == 0 && valid) {
+    const double j = p < N ? 1.0 / (1.0 - sj[0][tx] * sj[1][tx]) : 1.0;
+    if (sizeof(R) == sizeof(double))
+      F.junction[c] = j;
+    else
+      reinterpret_cast<float2*>(F.junction)[c] = df_split(j);
+  }
 }
 
 // End of an RK stage for one cell of the column step: Phi^(s+1) = Phi^(s) +
@@ -628,15 +641,26 @@ __device__ __forceinline__ void stage_end_cell(const Xf<R>& Xs, const Xf<R>& Xo,
   if (k == nv - 1) Xo.w[i + S] = ld(Xs.w + (i + S)) + ld(P.w + (i + S));
 }
 
+// the solved W* of row o of the direct solve's shared array: a float64
+// value, or for float storage the float in the first word of the row
+template <typename R>
+__device__ __forceinline__ R solved_w(const double* sdp, int o) {
+  if constexpr (sizeof(R) == sizeof(double))
+    return sdp[o];
+  else
+    return reinterpret_cast<const float2*>(sdp)[o].x;
+}
+
 // HE-VI column step, part 3 (every small step). The right-hand side
 //   rh_m = W*_m + dtau S_W,m - dtau/dzc_m (c_m - c_m-1) - dtau g (w- a_m-1 + w+ a_m)
-// goes through the stored factors in float64 (d'_m = rh_m / piv_m - q_m d'_m-1
-// downwards, f'_m = rh_m / piv_m - q_m f'_m+1 upwards: one dependent FMA per
-// row, the product rh_m / piv_m off the chain; then the junction rows
-// x_p = (d'_p - c'_p f'_p+1) / (1 - c'_p e'_p+1), x_p+1 = f'_p+1 - e'_p+1 x_p,
-// then back substitution outwards); then rho* and Th* follow from Eqs. dens2
-// and pt2 and p* from the nonlinear Eq. theta_to_p. One block = 32 columns
-// x 2 warps.
+// goes through the stored factors (d'_m = rh_m / piv_m - q_m d'_m-1
+// downwards, f'_m = rh_m / piv_m - q_m f'_m+1 upwards: one dependent
+// multiply-add per row, the product rh_m / piv_m off the chain; then the
+// junction rows x_p = (d'_p - c'_p f'_p+1) / (1 - c'_p e'_p+1),
+// x_p+1 = f'_p+1 - e'_p+1 x_p, then back substitution outwards), in float64
+// for float64 states and in double-float for float-storage states; then
+// rho* and Th* follow from Eqs. dens2 and pt2 and p* from the nonlinear Eq.
+// theta_to_p. One block = 32 columns x 2 warps.
 template <typename R>
 __device__ __forceinline__ void d_ss_solve(const Geo<R>& G, const VR<R>& U, const Phys& ph, const Xf<R>& Xs, const Slow<R>& SL,
                                             const Pert<R>& P, const Work<R>& T, const Fac<R>& F, double dtau,
@@ -654,65 +678,129 @@ __device__ __forceinline__ void d_ss_solve(const Geo<R>& G, const VR<R>& U, cons
   const int p = N / 2 > 0 ? N / 2 : 1;
   const R rdt = (R)dtau, g = pc<R>(ph.g, ph.g_f), delta = pc<R>(ph.delta, ph.delta_f);
 
-  auto rhs = [&](int m) {
+  auto rhs_r = [&](int m) {
     const int i = m * S + cs;
     const R wlo = ld(U.wlo + m), whi = ld(U.whi + m);
-    return to_f64<R>(delta * ld(P.w + i) + rdt * ld(SL.sw + i)
-                    - rdt * ld(U.inv_dzc + m) * (ld(T.cc + i) - ld(T.cc + (i - S)))
-                    - rdt * g * (wlo * ld(T.ca + (i - S)) + whi * ld(T.ca + i)));
+    return delta * ld(P.w + i) + rdt * ld(SL.sw + i) - rdt * ld(U.inv_dzc + m) * (ld(T.cc + i) - ld(T.cc + (i - S)))
+           - rdt * g * (wlo * ld(T.ca + (i - S)) + whi * ld(T.ca + i));
   };
-  // forward recurrences through the stored factors
-  if (half == 0) {
-    double d1 = 0.0;
+  if constexpr (sizeof(R) == sizeof(float)) {
+    // float storage: the elimination in double-float, the same operations
+    // in the same order as the staged solve (solve_sweeps); W* (float) over
+    // the first word of each row of sdp
+    const float2* Fq = reinterpret_cast<const float2*>(F.q);
+    const float2* Finv = reinterpret_cast<const float2*>(F.inv);
+    const float2* Fcf = reinterpret_cast<const float2*>(F.cf);
+    float2* dp2 = reinterpret_cast<float2*>(sdp);
+    float2* sx2 = reinterpret_cast<float2*>(sx);
+    float2* cf2 = reinterpret_cast<float2*>(scf);
+    if (half == 0) {
+      float2 d1 = make_float2(0.f, 0.f);
 #pragma unroll 4
-    for (int m = 1; m <= p; ++m) {
-      const int i = m * S + cs;
-      scf[m * 32 + tx] = ld(F.cf + i);
-      d1 = fma(-ld(F.q + i), d1, rhs(m) * ld(F.inv + i));
-      sdp[m * 32 + tx] = d1;
-    }
-  } else {
-    double f1 = 0.0;
-#pragma unroll 4
-    for (int m = N; m > p; --m) {
-      const int i = m * S + cs;
-      scf[m * 32 + tx] = ld(F.cf + i);
-      f1 = fma(-ld(F.q + i), f1, rhs(m) * ld(F.inv + i));
-      sdp[m * 32 + tx] = f1;
-    }
-  }
-  __syncthreads();
-  if (half == 0) {
-    double xp, xq = 0.0;
-    if (p < N) {
-      const double cp_ = scf[p * 32 + tx], eq = scf[(p + 1) * 32 + tx];
-      const double dp_ = sdp[p * 32 + tx], fq = sdp[(p + 1) * 32 + tx];
-      xp = (dp_ - cp_ * fq) * ld(F.junction + cs);
-      xq = fq - eq * xp;
+      for (int m = 1; m <= p; ++m) {
+        const int i = m * S + cs;
+        cf2[m * 32 + tx] = Fcf[i];
+        d1 = df_sweep(rhs_r(m), Finv[i], Fq[i], d1);
+        dp2[m * 32 + tx] = d1;
+      }
     } else {
-      xp = sdp[p * 32 + tx];
+      float2 f1 = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int m = N; m > p; --m) {
+        const int i = m * S + cs;
+        cf2[m * 32 + tx] = Fcf[i];
+        f1 = df_sweep(rhs_r(m), Finv[i], Fq[i], f1);
+        dp2[m * 32 + tx] = f1;
+      }
     }
-    sx[tx] = xp;
-    sx[32 + tx] = xq;
-  }
-  __syncthreads();
-  // back substitution, each warp over its own rows
-  if (half == 0) {
-    double x = sx[tx];
-    sdp[p * 32 + tx] = x;
-    for (int m = p - 1; m >= 1; --m) {
-      x = sdp[m * 32 + tx] - scf[m * 32 + tx] * x;
-      sdp[m * 32 + tx] = x;
+    __syncthreads();
+    if (half == 0) {
+      float2 xp, xq = make_float2(0.f, 0.f);
+      if (p < N) {
+        const float2 dp_ = dp2[p * 32 + tx], fq = dp2[(p + 1) * 32 + tx];
+        xp = df_mul(df_fms(dp_.x, dp_.y, cf2[p * 32 + tx], fq), reinterpret_cast<const float2*>(F.junction)[cs]);
+        xq = df_fms(fq.x, fq.y, cf2[(p + 1) * 32 + tx], xp);
+      } else {
+        xp = dp2[p * 32 + tx];
+      }
+      sx2[tx] = xp;
+      sx2[32 + tx] = xq;
     }
-    sdp[tx] = 0.0;                 // bottom interface
+    __syncthreads();
+    if (half == 0) {
+      float2 x = sx2[tx];
+      dp2[p * 32 + tx] = make_float2(df_to_float(x), 0.f);
+      for (int m = p - 1; m >= 1; --m) {
+        const float2 d = dp2[m * 32 + tx];
+        x = df_fms(d.x, d.y, cf2[m * 32 + tx], x);
+        dp2[m * 32 + tx] = make_float2(df_to_float(x), 0.f);
+      }
+      dp2[tx] = make_float2(0.f, 0.f);             // bottom interface
+    } else {
+      float2 x = sx2[32 + tx];
+      if (p < N) dp2[(p + 1) * 32 + tx] = make_float2(df_to_float(x), 0.f);
+      for (int m = p + 2; m <= N; ++m) {
+        const float2 d = dp2[m * 32 + tx];
+        x = df_fms(d.x, d.y, cf2[m * 32 + tx], x);
+        dp2[m * 32 + tx] = make_float2(df_to_float(x), 0.f);
+      }
+      dp2[nv * 32 + tx] = make_float2(0.f, 0.f);    // top interface
+    }
   } else {
-    double x = sx[32 + tx];
-    if (p < N) sdp[(p + 1) * 32 + tx] = x;
-    for (int m = p + 2; m <= N; ++m) {
-      x = sdp[m * 32 + tx] - scf[m * 32 + tx] * x;
-      sdp[m * 32 + tx] = x;
+    // float64 storage: the elimination in float64
+    auto rhs = [&](int m) { return to_f64<R>(rhs_r(m)); };
+    if (half == 0) {
+      double d1 = 0.0;
+#pragma unroll 4
+      for (int m = 1; m <= p; ++m) {
+        const int i = m * S + cs;
+        scf[m * 32 + tx] = ld(F.cf + i);
+        d1 = fma(-ld(F.q + i), d1, rhs(m) * ld(F.inv + i));
+        sdp[m * 32 + tx] = d1;
+      }
+    } else {
+      double f1 = 0.0;
+#pragma unroll 4
+      for (int m = N; m > p; --m) {
+        const int i = m * S + cs;
+        scf[m * 32 + tx] = ld(F.cf + i);
+        f1 = fma(-ld(F.q + i), f1, rhs(m) * ld(F.inv + i));
+        sdp[m * 32 + tx] = f1;
+      }
     }
-    sdp[nv * 32 + tx] = 0.0;       // top interface
+    __syncthreads();
+    if (half == 0) {
+      double xp, xq = 0.0;
+      if (p < N) {
+        const double cp_ = scf[p * 32 + tx], eq = scf[(p + 1) * 32 + tx];
+        const double dp_ = sdp[p * 32 + tx], fq = sdp[(p + 1) * 32 + tx];
+        xp = (dp_ - cp_ * fq) * ld(F.junction + cs);
+        xq = fq - eq * xp;
+      } else {
+        xp = sdp[p * 32 + tx];
+      }
+      sx[tx] = xp;
+      sx[32 + tx] = xq;
+    }
+    __syncthreads();
+    // back substitution, each warp over its own rows
+    if (half == 0) {
+      double x = sx[tx];
+      sdp[p * 32 + tx] = x;
+      for (int m = p - 1; m >= 1; --m) {
+        x = sdp[m * 32 + tx] - scf[m * 32 + tx] * x;
+        sdp[m * 32 + tx] = x;
+      }
+      sdp[tx] = 0.0;                 // bottom interface
+    } else {
+      double x = sx[32 + tx];
+      if (p < N) sdp[(p + 1) * 32 + tx] = x;
+      for (int m = p + 2; m <= N; ++m) {
+        x = sdp[m * 32 + tx] - scf[m * 32 + tx] * x;
+        sdp[m * 32 + tx] = x;
+      }
+      sdp[nv * 32 + tx] = 0.0;       // top interface
+    }
   }
   __syncthreads();
   // Eqs. dens2, pt2, theta_to_p with the new W*; the two warps share the levels
@@ -721,7 +809,7 @@ __device__ __forceinline__ void d_ss_solve(const Geo<R>& G, const VR<R>& U, cons
 #pragma unroll 4
     for (int k = half; k < nv; k += 2) {
       const int i = k * S + c;
-      const R wl = from_f64<R>(sdp[k * 32 + tx]), wh = from_f64<R>(sdp[(k + 1) * 32 + tx]);
+      const R wl = solved_w<R>(sdp, k * 32 + tx), wh = solved_w<R>(sdp, (k + 1) * 32 + tx);
       const R thl = k > 0 ? ld(SL.thi + i) : R(0);
       const R thh = k + 1 < nv ? ld(SL.thi + (i + S)) : R(0);
       const R el = ld(U.sq_lo + k), eh = ld(U.sq_hi + k);
@@ -1022,47 +1110,49 @@ __device__ __forceinline__ void solve_issue(const SolveSm& s, const SolveMaps& M
   }
 }
 
-// the two float64 sweeps of one group, sweep 0 (rows 1..p, downwards) or 1
-// (rows nv-1..p+1, upwards) by one warp each, then the junction rows and the
-// back substitution; the solved W* over s.w. The two warps meet at named
-// barrier 1.
-__device__ __forceinline__ void solve_sweeps(const SolveSm& s, double* sx, const VR<float>& U, float rdt, float g,
+// the two sweeps of one group, sweep 0 (rows 1..p, downwards) or 1 (rows
+// nv-1..p+1, upwards) by one warp each, then the junction rows and the back
+// substitution; the solved W* over s.w. The elimination runs in
+// double-float on the float32 pipes (the factors arrive as double-float
+// pairs). The two warps meet at named barrier 1.
+__device__ __forceinline__ void solve_sweeps(const SolveSm& s, float2* sx, const VR<float>& U, float rdt, float g,
                                              float delta, int nv, int tx, int sweep) {
   const int N = nv - 1, p = N / 2 > 0 ? N / 2 : 1;
   auto rhs = [&](int m) {
     const int o = m * 32 + tx;
     const float wlo = ld(U.wlo + m), whi = ld(U.whi + m);
-    return f2d_alu(delta * s.w[o] + rdt * s.sw[o] - rdt * ld(U.inv_dzc + m) * (s.cc[o] - s.cc[o - 32])
-                   - rdt * g * (wlo * s.ca[o - 32] + whi * s.ca[o]));
+    return delta * s.w[o] + rdt * s.sw[o] - rdt * ld(U.inv_dzc + m) * (s.cc[o] - s.cc[o - 32])
+           - rdt * g * (wlo * s.ca[o - 32] + whi * s.ca[o]);
   };
-  double* sdp = s.inv;
+  const float2* q = reinterpret_cast<const float2*>(s.q);
+  const float2* cf = reinterpret_cast<const float2*>(s.cf);
+  float2* sdp = reinterpret_cast<float2*>(s.inv);      // d' / f' over the pivot reciprocals
   float* s_wf = s.w;
   if (sweep == 0) {
-    double d1 = 0.0;
+    float2 d1 = make_float2(0.f, 0.f);
 #pragma unroll 4
     for (int m = 1; m <= p; ++m) {
       const int o = m * 32 + tx;
-      d1 = fma(-s.q[o], d1, rhs(m) * s.inv[o]);
+      d1 = df_sweep(rhs(m), sdp[o], q[o], d1);
       sdp[o] = d1;
     }
   } else {
-    double f1 = 0.0;
+    float2 f1 = make_float2(0.f, 0.f);
 #pragma unroll 4
     for (int m = N; m > p; --m) {
       const int o = m * 32 + tx;
-      f1 = fma(-s.q[o], f1, rhs(m) * s.inv[o]);
+      f1 = df_sweep(rhs(m), sdp[o], q[o], f1);
       sdp[o] = f1;
     }
   }
   asm volatile("bar.sync 1, 64;" ::: "memory");        // the two sweeps only
   if (sweep == 0) {
     const int op = p * 32 + tx;
-    double xp, xq = 0.0;
+    float2 xp, xq = make_float2(0.f, 0.f);
     if (p < N) {
-      const double cp_ = s.cf[op], eq = s.cf[op + 32];
-      const double dp_ = sdp[op], fq = sdp[op + 32];
-      xp = (dp_ - cp_ * fq) * s.junc[tx];
-      xq = fq - eq * xp;
+      const float2 dp_ = sdp[op], fq = sdp[op + 32];
+      xp = df_mul(df_fms(dp_.x, dp_.y, cf[op], fq), reinterpret_cast<const float2*>(s.junc)[tx]);
+      xq = df_fms(fq.x, fq.y, cf[op + 32], xp);
     } else {
       xp = sdp[op];
     }
@@ -1071,19 +1161,21 @@ __device__ __forceinline__ void solve_sweeps(const SolveSm& s, double* sx, const
   }
   asm volatile("bar.sync 1, 64;" ::: "memory");
   if (sweep == 0) {
-    double x = sx[tx];
-    s_wf[p * 32 + tx] = d2f_alu(x);
+    float2 x = sx[tx];
+    s_wf[p * 32 + tx] = df_to_float(x);
     for (int m = p - 1; m >= 1; --m) {
-      x = sdp[m * 32 + tx] - s.cf[m * 32 + tx] * x;
-      s_wf[m * 32 + tx] = d2f_alu(x);
+      const float2 d = sdp[m * 32 + tx];
+      x = df_fms(d.x, d.y, cf[m * 32 + tx], x);
+      s_wf[m * 32 + tx] = df_to_float(x);
     }
     s_wf[tx] = 0.f;
   } else {
-    double x = sx[32 + tx];
-    if (p < N) s_wf[(p + 1) * 32 + tx] = d2f_alu(x);
+    float2 x = sx[32 + tx];
+    if (p < N) s_wf[(p + 1) * 32 + tx] = df_to_float(x);
     for (int m = p + 2; m <= N; ++m) {
-      x = sdp[m * 32 + tx] - s.cf[m * 32 + tx] * x;
-      s_wf[m * 32 + tx] = d2f_alu(x);
+      const float2 d = sdp[m * 32 + tx];
+      x = df_fms(d.x, d.y, cf[m * 32 + tx], x);
+      s_wf[m * 32 + tx] = df_to_float(x);
     }
     s_wf[nv * 32 + tx] = 0.f;
   }
@@ -1143,7 +1235,7 @@ __device__ __forceinline__ void d_ss_solve_tma(const Geo<float>& G, const VR<flo
   const int c0 = bx * 32, c = c0 + tx;
   unsigned char* base = smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u);
   const SolveSm s = solve_sm(base, nv);
-  double* sx = reinterpret_cast<double*>(base + solve_stage_bytes(nv));   // [2][32]
+  float2* sx = reinterpret_cast<float2*>(base + solve_stage_bytes(nv));   // [2][32]
   uint64_t* bar = reinterpret_cast<uint64_t*>(sx + 64);
 
   if (tid == 0) {
