@@ -188,10 +188,11 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   X(I.Xt);
   X(I.Xst);
   Work<R>& T = I.T;
-  R** cen[] = {&T.pp, &T.Tp, &T.theta, &T.vx, &T.vy, &T.vz, &T.vhx, &T.vhy, &T.vhz,
-               &T.qrho, &T.qvx, &T.qvy, &T.qvz, &T.qT, &T.dd, &T.dd0,
-               &T.ca, &T.cb, &T.cc, &T.dhm};
+  R** cen[] = {&T.pp, &T.theta, &T.qT, &T.dd, &T.dd0, &T.ca, &T.cb, &T.cc, &T.dhm};
   for (R** p : cen) *p = cv.take<R>(C);
+  T.v4 = cv.take<R>(4 * C);
+  T.vh4 = cv.take<R>(4 * C);
+  T.q4 = cv.take<R>(4 * C);
   T.vr = cv.take<R>(F);
   T.qvr = cv.take<R>(F);
   T.wc = cv.take<R>(C);

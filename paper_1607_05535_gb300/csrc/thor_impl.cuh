@@ -14,12 +14,14 @@ namespace thor {
 // Derived fields and intermediates
 template <typename R>
 struct Work {
-  R *pp, *Tp, *theta;              // p', T', theta at the centres
-  R *vx, *vy, *vz;                 // full 3-D velocity at the centres
-  R *vhx, *vhy, *vhz;              // horizontal velocity M / rho
+  // packed [nv][colp][4] planes (one 16-byte gather per neighbour, ld4):
+  // v4 = the full 3-D velocity and theta, vh4 = the horizontal velocity
+  // M / rho and T', q4 = K_d lap(v_h) rho (x, y, z) and K_d lap(rho)
+  R *v4, *vh4, *q4;
+  R *pp, *theta;                   // p', theta at the centres
   R *vr;                           // W / rho at the interfaces
   R *wc;                           // W / rho at the centres (shallow atmosphere)
-  R *qrho, *qvx, *qvy, *qvz, *qT;  // K_d lap(.) (times rho) for the hyperdiffusion
+  R *qT;                           // K_d lap(T') rho for the hyperdiffusion
   R *qvr;                          // interfaces
   R *dd;                           // 3-D divergence (small step)
   R *dd0;                          // 3-D divergence of X^t (first small step of every stage)

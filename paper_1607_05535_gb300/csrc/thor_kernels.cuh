@@ -3,7 +3,9 @@
 // Data layout in HBM: every field is a set of planes [level][colp] (colp =
 // column count padded to a multiple of 128), so a warp reads 32 consecutive
 // columns of one level in one coalesced transaction; interface fields have
-// nv+1 planes; Cartesian vectors are three separate scalar fields. Columns
+// nv+1 planes; the state's Cartesian vectors are three separate scalar
+// fields, while intermediates that stencils gather together sit in packed
+// [level][colp][4] (or [2]) planes. Columns
 // follow the rhombus numbering of the grid, so the six neighbours of an
 // interior column sit at offsets +-1, +-n, +-(n+1) in the same plane.
 //
@@ -420,6 +422,23 @@ __device__ __forceinline__ R vint_iface(const VR<R>& U, const R* f, const R* ref
   }
   return s;
 }
+// vint_iface of the four values of a packed plane (no reference column)
+template <typename R>
+__device__ __forceinline__ Q4<R> vint_iface4(const VR<R>& U, const R* f4, int m, int c, int S, int nv) {
+  const int j0 = ld(U.ij0 + m);
+  Q4<R> s = {0, 0, 0, 0};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int q = min(j0 + j, nv - 1);
+    const Q4<R> v = ld4(f4, (size_t)q * S + c);
+    const R wj = ld(U.iw + (j * (nv + 1) + m));
+    s.x += wj * v.x;
+    s.y += wj * v.y;
+    s.z += wj * v.z;
+    s.w += wj * v.w;
+  }
+  return s;
+}
 template <typename R>
 __device__ __forceinline__ R vint_centre(const VR<R>& U, const R* fi, int k, int c, int S, int nv) {
   const int j0 = ld(U.cj0 + k);
@@ -438,6 +457,21 @@ __device__ __forceinline__ R apply7(const W7<R>& w, const Nbr7& nb, const R* pla
   R s = 0;
 #pragma unroll
   for (int j = 0; j < 7; ++j) s += w.v[j] * ld(plane + nb.n[j]);
+  return s;
+}
+// the same for the four values of a packed plane at level offset o (each
+// sum in the order of apply7)
+template <typename R>
+__device__ __forceinline__ Q4<R> apply7x4(const W7<R>& w, const Nbr7& nb, const R* packed, int o) {
+  Q4<R> s = {0, 0, 0, 0};
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    const Q4<R> v = ld4(packed, (size_t)(o + nb.n[j]));
+    s.x += w.v[j] * v.x;
+    s.y += w.v[j] * v.y;
+    s.z += w.v[j] * v.z;
+    s.w += w.v[j] * v.w;
+  }
   return s;
 }
 // sum_j w_j . F(n_j) with F given by three planes

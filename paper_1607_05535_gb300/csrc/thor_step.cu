@@ -39,7 +39,9 @@ cudaError_t launch_k(void (*kern)(K...), dim3 grid, dim3 block, size_t smem, cud
 // ---------------------------------------------------------------- slow terms
 
 // Pointwise derived quantities at the stage state: p', T', theta, the full
-// 3-D velocity, v_h = M/rho (centres) and v_r = W/rho (interfaces).
+// 3-D velocity, v_h = M/rho (centres) and v_r = W/rho (interfaces); the
+// velocities go into packed planes with theta (v4) and T' (vh4) beside them,
+// the fields the next stencils gather together.
 // HO: the order-k interpolation of the explicit terms (thor_init.vorder > 1)
 template <typename R, bool HO = false>
 __device__ __forceinline__ void d_derived(const Geo<R>& G, const VR<R>& U, const Phys& ph, const Xf<R>& X, const Work<R>& T, int shallow, int kchunk,
@@ -63,15 +65,11 @@ __device__ __forceinline__ void d_derived(const Geo<R>& G, const VR<R>& U, const
       R wc = HO ? vint_centre(U, X.w, k, c, S, G.nv)
                            : ld(U.clo + (k)) * ld(X.w + (i)) + ld(U.chi + (k)) * ld(X.w + (i + S));
       R mx = ld(X.mx + (i)), my = ld(X.my + (i)), mz = ld(X.mz + (i));
+      const R theta = (ld(U.thb + (k)) + thp) * inv;
       T.pp[i] = pp;
-      T.Tp[i] = Temp - ld(U.Tb + (k));
-      T.theta[i] = (ld(U.thb + (k)) + thp) * inv;
-      T.vx[i] = (mx + wc * rx) * inv;
-      T.vy[i] = (my + wc * ry) * inv;
-      T.vz[i] = (mz + wc * rz) * inv;
-      T.vhx[i] = mx * inv;
-      T.vhy[i] = my * inv;
-      T.vhz[i] = mz * inv;
+      T.theta[i] = theta;
+      st4(T.v4, i, (mx + wc * rx) * inv, (my + wc * ry) * inv, (mz + wc * rz) * inv, theta);
+      st4(T.vh4, i, mx * inv, my * inv, mz * inv, Temp - ld(U.Tb + (k)));
       if (shallow) T.wc[i] = wc * inv;
     }
     if (k >= 1 && k < G.nv) {
@@ -103,12 +101,10 @@ __device__ __forceinline__ void d_lap1(const Geo<R>& G, const VR<R>& U, const Xf
       int o = k * S;
       R inv_r2 = ld(U.inv_rc2 + (k));
       R rho = ld(U.rhob + (k)) + ld(X.rho + (o + c));
-      T.qrho[o + c] = Kd * apply7(wl, nb, X.rho + o) * inv_r2;
       R rk = rho * Kd * inv_r2;
-      T.qvx[o + c] = rk * apply7(wl, nb, T.vhx + o);
-      T.qvy[o + c] = rk * apply7(wl, nb, T.vhy + o);
-      T.qvz[o + c] = rk * apply7(wl, nb, T.vhz + o);
-      T.qT[o + c] = rk * apply7(wl, nb, T.Tp + o);
+      const Q4<R> lv = apply7x4(wl, nb, T.vh4, o);       // lap of v_h (x, y, z) and of T'
+      st4(T.q4, o + c, rk * lv.x, rk * lv.y, rk * lv.z, Kd * apply7(wl, nb, X.rho + o) * inv_r2);
+      T.qT[o + c] = rk * lv.w;
     }
     if (k >= 1 && k < G.nv) {
       int o = k * S;
@@ -162,27 +158,30 @@ __device__ __forceinline__ void d_slow(const Geo<R>& G, const VR<R>& U, const Ph
     // second Laplacians of the hyperdiffusion
     R sa0 = 0, sa1 = 0, sa2 = 0, sa3 = 0, sdh = 0, sdt = 0, gx = 0, gy = 0, gz = 0;
     R hr = 0, hx = 0, hy = 0, hz = 0, hT = 0;
-    // advected velocity: the full 3-D one, or (SH) the horizontal one and w
-    const R *avx = SH ? T.vhx : T.vx, *avy = SH ? T.vhy : T.vy, *avz = SH ? T.vhz : T.vz;
+    // advected velocity (packed with theta or T'): the full 3-D one, or (SH)
+    // the horizontal one and w
+    const R* av4 = SH ? T.vh4 : T.v4;
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
       const int q = o + nb.n[j];
       const R f = wd.x[j] * ld(X.mx + q) + wd.y[j] * ld(X.my + q) + wd.z[j] * ld(X.mz + q);
-      sa0 += ld(avx + q) * f;
-      sa1 += ld(avy + q) * f;
-      sa2 += ld(avz + q) * f;
+      const Q4<R> av = ld4(av4, (size_t)q);
+      sa0 += av.x * f;
+      sa1 += av.y * f;
+      sa2 += av.z * f;
       if constexpr (SH) sa3 += ld(T.wc + q) * f;
       sdh += f;
-      sdt += ld(T.theta + q) * f;
+      sdt += (SH ? ld(T.theta + q) : av.w) * f;
       const R pq = ld(T.pp + q);
       gx += wg.x[j] * pq;
       gy += wg.y[j] * pq;
       gz += wg.z[j] * pq;
       if (hyper) {
-        hr += wl.v[j] * ld(T.qrho + q);
-        hx += wl.v[j] * ld(T.qvx + q);
-        hy += wl.v[j] * ld(T.qvy + q);
-        hz += wl.v[j] * ld(T.qvz + q);
+        const Q4<R> hq = ld4(T.q4, (size_t)q);
+        hr += wl.v[j] * hq.w;
+        hx += wl.v[j] * hq.x;
+        hy += wl.v[j] * hq.y;
+        hz += wl.v[j] * hq.z;
         hT += wl.v[j] * ld(T.qT + q);
       }
     }
@@ -200,22 +199,32 @@ __device__ __forceinline__ void d_slow(const Geo<R>& G, const VR<R>& U, const Ph
     }
 
     // advection div(rho v v_j) of the Cartesian components (Sec. 3)
-    const R* vs[3] = {avx, avy, avz};
     const R sa[3] = {sa0, sa1, sa2};
     R A[3];
     R wlo_w = ld(X.w + (i)), whi_w = ld(X.w + (i + S));
+    // the advected velocity at the cell's lower and upper interfaces
+    Q4<R> vl = {0, 0, 0, 0}, vh = {0, 0, 0, 0};
+    if constexpr (HO) {
+      if (k >= 1) vl = vint_iface4(U, av4, k, c, S, G.nv);
+      if (k + 1 < G.nv) vh = vint_iface4(U, av4, k + 1, c, S, G.nv);
+    } else {
+      const Q4<R> v0 = ld4(av4, (size_t)i);
+      if (k >= 1) {
+        const Q4<R> vm = ld4(av4, (size_t)(i - S));
+        const R a = ld(U.wlo + (k)), b = ld(U.whi + (k));
+        vl = {a * vm.x + b * v0.x, a * vm.y + b * v0.y, a * vm.z + b * v0.z, 0};
+      }
+      if (k + 1 < G.nv) {
+        const Q4<R> vp = ld4(av4, (size_t)(i + S));
+        const R a = ld(U.wlo + (k + 1)), b = ld(U.whi + (k + 1));
+        vh = {a * v0.x + b * vp.x, a * v0.y + b * vp.y, a * v0.z + b * vp.z, 0};
+      }
+    }
+    const R vlo3[3] = {vl.x, vl.y, vl.z}, vhi3[3] = {vh.x, vh.y, vh.z};
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       R ah = sa[j] * inv_r;
-      R vlo = 0, vhi = 0;
-      if constexpr (HO) {
-        if (k >= 1) vlo = vint_iface(U, vs[j], (const R*)nullptr, k, c, S, G.nv);
-        if (k + 1 < G.nv) vhi = vint_iface(U, vs[j], (const R*)nullptr, k + 1, c, S, G.nv);
-      } else {
-        if (k >= 1) vlo = ld(U.wlo + (k)) * vs[j][i - S] + ld(U.whi + (k)) * vs[j][i];
-        if (k + 1 < G.nv) vhi = ld(U.wlo + (k + 1)) * vs[j][i] + ld(U.whi + (k + 1)) * vs[j][i + S];
-      }
-      A[j] = ah + sqh * whi_w * vhi - sql * wlo_w * vlo;
+      A[j] = ah + sqh * whi_w * vhi3[j] - sql * wlo_w * vlo3[j];
     }
     R acr, ahx, ahy, ahz;
     if constexpr (SH) {
