@@ -351,6 +351,8 @@ Impl<R>::~Impl() {
   if (ev_fork) cudaEventDestroy(ev_fork);
   if (ev_join) cudaEventDestroy(ev_join);
   if (ev_join0) cudaEventDestroy(ev_join0);
+  for (cudaEvent_t e : ev_x)
+    if (e) cudaEventDestroy(e);
   if (arena) cudaFree(arena);
   if (lo_buf) cudaFree(lo_buf);
   if (an_buf) cudaFree(an_buf);
@@ -383,12 +385,22 @@ int Impl<R>::set(int field, const double* host, size_t n) {
   return cudaStreamSynchronize(stream) == cudaSuccess ? THOR_OK : THOR_ECUDA;
 }
 
+// All four fields: with the side stream, the copies run back to back on it
+// and each field's conversion on the state's stream waits for its own copy
+// (set) or the copy waits for its conversion (get), so conversions overlap
+// the other fields' copies; every field has its own region of the staging
+// buffer.
 template <typename R>
 int Impl<R>::set_all(const double* const host[4]) {
-  size_t off = 0;
-  for (int f = 0; f < 4; ++f) {
+  for (int f = 0; f < 4; ++f)
     if (!host[f]) return THOR_EINVAL;
-    const int rc = set_async(f, host[f], staging + off);
+  size_t off = 0;
+  if (side) {
+    // the side stream must not overwrite staging before the state's stream is done with it
+    if (cudaEventRecord(ev_x[0], stream) || cudaStreamWaitEvent(side, ev_x[0], 0)) return THOR_ECUDA;
+  }
+  for (int f = 0; f < 4; ++f) {
+    const int rc = set_async(f, host[f], staging + off, side);
     if (rc) return rc;
     off += field_count(f, G.ncol, G.nv);
   }
@@ -397,22 +409,30 @@ int Impl<R>::set_all(const double* const host[4]) {
 
 template <typename R>
 int Impl<R>::get_all(double* const host[4]) {
+  for (int f = 0; f < 4; ++f)
+    if (!host[f]) return THOR_EINVAL;
   size_t off = 0;
   for (int f = 0; f < 4; ++f) {
-    if (!host[f]) return THOR_EINVAL;
     const size_t n = field_count(f, G.ncol, G.nv);
     dim3 grid((G.ncol + 127) / 128, f == THOR_FIELD_W ? G.nv + 1 : G.nv);
     k_to_canonical<R><<<grid, 128, 0, stream>>>(staging + off, G, V, ph, Xt, XtL, f);
     ++launches;
-    if (cudaMemcpyAsync(host[f], staging + off, n * sizeof(double), cudaMemcpyDeviceToHost, stream))
-      return THOR_ECUDA;
+    cudaStream_t cs = stream;
+    if (side) {
+      if (cudaEventRecord(ev_x[f], stream) || cudaStreamWaitEvent(side, ev_x[f], 0)) return THOR_ECUDA;
+      cs = side;
+    }
+    if (cudaMemcpyAsync(host[f], staging + off, n * sizeof(double), cudaMemcpyDeviceToHost, cs)) return THOR_ECUDA;
     off += n;
   }
+  if (side && cudaStreamSynchronize(side)) return THOR_ECUDA;
   return cudaStreamSynchronize(stream) == cudaSuccess ? THOR_OK : THOR_ECUDA;
 }
 
+// copy (on cs, the state's stream by default) and convert (on the state's
+// stream, after the copy) one field
 template <typename R>
-int Impl<R>::set_async(int field, const double* host, double* buf) {
+int Impl<R>::set_async(int field, const double* host, double* buf, cudaStream_t cs) {
   const int nv = G.nv;
   int nlev = nv, ncomp = 1, zero_ends = 0;
   const double* ref = nullptr;
@@ -427,7 +447,11 @@ int Impl<R>::set_async(int field, const double* host, double* buf) {
     default: return THOR_EINVAL;
   }
   const size_t n = (size_t)G.ncol * nlev * ncomp;
-  if (cudaMemcpyAsync(buf, host, n * sizeof(double), cudaMemcpyHostToDevice, stream)) return THOR_ECUDA;
+  if (!cs) cs = stream;
+  if (cudaMemcpyAsync(buf, host, n * sizeof(double), cudaMemcpyHostToDevice, cs)) return THOR_ECUDA;
+  if (cs != stream) {
+    if (cudaEventRecord(ev_x[field], cs) || cudaStreamWaitEvent(stream, ev_x[field], 0)) return THOR_ECUDA;
+  }
   dim3 grid((G.ncol + 127) / 128, nlev);
   k_from_canonical<R><<<grid, 128, 0, stream>>>(buf, G.ncol, G.colp, nlev, ncomp, ref, d0, d1, d2, l0, l1, l2,
                                                 zero_ends);
@@ -704,7 +728,11 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
   if (cudaStreamCreateWithFlags(&I->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&I->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&I->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&I->ev_join0, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&I->ev_join0, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&I->ev_x[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&I->ev_x[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&I->ev_x[2], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&I->ev_x[3], cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     if (I->side) cudaStreamDestroy(I->side);
     I->side = nullptr;

@@ -224,6 +224,9 @@ struct Impl : ImplBase {
   // state's stream)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join0 = nullptr;
+  // whole-state transfers: one event per field between its conversion (on
+  // the state's stream) and its copy (on the side stream)
+  cudaEvent_t ev_x[4] = {nullptr, nullptr, nullptr, nullptr};
   int build_solve_maps();
   cudaError_t launch_solve_tma(dim3 grid, int stage, const Xf<R>& Xo, const Xf<R>& XsL, const Xf<R>& XoL,
                                double dtau, int want_div, int last);
@@ -290,7 +293,8 @@ struct Impl : ImplBase {
   int set(int field, const double* host, size_t n) override;
   int get_all(double* const host[4]) override;
   int set_all(const double* const host[4]) override;
-  int set_async(int field, const double* host, double* buf);   // queue one field, no synchronisation
+  // queue one field (copy on cs, default the state's stream), no synchronisation
+  int set_async(int field, const double* host, double* buf, cudaStream_t cs = nullptr);
   int set_compensated(int on) override;
   bool anelastic() const override { return ph.anelastic != 0; }
   // rho, M (3), rho theta: nv planes each; W: nv + 1 planes (and the same
