@@ -655,8 +655,8 @@ def run_thor(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _config(wl),
-        "precision": ("mixed: f32 stencils and tendencies, the state as compensated f32 pairs, f64 vertical "
-                      "factorisation with a double-float elimination per small step, f64 reductions"),
+        "precision": ("mixed: f32 stencils and tendencies, the state as compensated f32 pairs, double-float "
+                      "vertical factorisation and elimination, f64 reductions"),
         "model_days_per_hour": days_per_hour,
         "error": err,
         "plain_float_state": plain,

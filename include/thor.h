@@ -262,20 +262,6 @@ int thor_checkpoint_load(thor_state* state, const void* buf, size_t bytes);
  * and the context stays usable. Synchronous (default stream). */
 int thor_wait_selftest(int arrive, unsigned int limit_us, int* gave_up);
 
-/* Self-test of the integer-ALU binary32 <-> binary64 conversions that the
- * float kernels of the column factorisation and solve use in place of the
- * conversion instructions (which issue on the narrow float64 pipe), and of
- * the integer split of a binary64 value into a double-float pair (hi = the
- * value rounded to binary32, lo = the remainder rounded to binary32) that the
- * factorisation of float-storage states stores: n seeded bit patterns per
- * direction (1 <= n <= 2^32; seed any), converted and compared bit for bit
- * with the conversion instructions (IEEE 754 round to nearest, ties to even;
- * the split against the conversion of the value and of its exact float64
- * remainder). *mismatches = the number of differing results, 0 when all are
- * exact. Synchronous (default stream); allocates one counter. No
- * counterpart in the paper. */
-int thor_convert_selftest(long long n, unsigned long long seed, long long* mismatches);
-
 /* Kernel launches issued by this state so far (instrumentation; no passage
  * of the paper). THOR_EINVAL for NULL arguments. */
 int thor_launch_count(const thor_state* state, long long* count);

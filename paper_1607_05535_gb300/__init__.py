@@ -38,7 +38,7 @@ EXPORTED = [
     "thor_autotune", "thor_ensemble_create", "thor_ensemble_step", "thor_ensemble_info",
     "thor_ensemble_tune", "thor_ensemble_autotune", "thor_ensemble_destroy", "thor_mlp_tune",
     "thor_checkpoint_bytes", "thor_checkpoint_save", "thor_checkpoint_load", "thor_wait_selftest",
-    "thor_convert_selftest", "thor_budget_read", "thor_zonal_accumulate", "thor_zonal_read",
+    "thor_budget_read", "thor_zonal_accumulate", "thor_zonal_read",
     "thor_zonal_read_w",
 ]
 
@@ -139,7 +139,6 @@ def _load():
         "thor_checkpoint_save": (I, [P, P, Z]),
         "thor_checkpoint_load": (I, [P, P, Z]),
         "thor_wait_selftest": (I, [I, ctypes.c_uint, IP]),
-        "thor_convert_selftest": (I, [ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]),
         "thor_budget_read": (I, [P, ctypes.POINTER(D), I, IP]),
         "thor_zonal_accumulate": (I, [P, I]),
         "thor_zonal_read": (I, [P, I, ctypes.POINTER(D), Z, I, ctypes.POINTER(ctypes.c_longlong)]),
@@ -458,14 +457,6 @@ def thor_wait_selftest(arrive, limit_us):
     g = ctypes.c_int()
     _check(_lib.thor_wait_selftest(int(arrive), int(limit_us), ctypes.byref(g)), "thor_wait_selftest")
     return g.value
-
-
-def thor_convert_selftest(n, seed=1):
-    """Bit mismatches of the integer-ALU float conversions against the
-    conversion instructions over n seeded patterns per direction."""
-    m = ctypes.c_longlong()
-    _check(_lib.thor_convert_selftest(int(n), int(seed), ctypes.byref(m)), "thor_convert_selftest")
-    return m.value
 
 
 def thor_budget_read(state, max_rows=1 << 16):

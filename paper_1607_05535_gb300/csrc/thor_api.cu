@@ -110,51 +110,6 @@ __global__ void k_wait_probe(int arrive, unsigned long long limit_ns, int* out) 
   *out = mbar_wait(&bar, 0, limit_ns) ? 0 : 1;
 }
 
-// The integer-ALU float conversions (f2d_alu, d2f_alu) against the conversion
-// instructions on n seeded bit patterns per direction (SplitMix64 of
-// seed + index): binary64 patterns with exponents around the binary32 range
-// (subnormal results, the normal range, overflow), every eighth with a
-// remainder of exactly half a binary32 unit (ties), every sixteenth a special
-// value (zeros, binary64 subnormals, infinities, NaN); binary32 patterns
-// uniformly over all encodings. Counts results that differ in any bit (two
-// NaN count as equal).
-__device__ __forceinline__ unsigned long long probe_mix64(unsigned long long x) {   // SplitMix64
-  x += 0x9e3779b97f4a7c15ull;
-  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
-  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
-  return x ^ (x >> 31);
-}
-__global__ void k_convert_probe(long long n, unsigned long long seed, unsigned long long* bad) {
-  unsigned long long local = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const unsigned long long r1 = probe_mix64(seed + 2 * (unsigned long long)i);
-    const unsigned long long r2 = probe_mix64(seed + 2 * (unsigned long long)i + 1);
-    // binary64 -> binary32
-    unsigned long long b = (r1 & 0x800fffffffffffffull) |
-                           ((unsigned long long)(1023 - 160 + (int)(r2 % 320)) << 52);
-    if ((r2 >> 20) % 8 == 0) b = (b & ~((1ull << 29) - 1)) | (1ull << 28);
-    if ((r2 >> 24) % 16 == 0) {
-      const unsigned long long sp[8] = {0ull, 0x8000000000000000ull, 1ull, 0x000fffffffffffffull,
-                                        0x7ff0000000000000ull, 0xfff0000000000000ull, 0x7ff8000000000000ull,
-                                        0x47efffffefffffffull};
-      b = sp[(r2 >> 32) % 8];
-    }
-    const double d = __longlong_as_double((long long)b);
-    const float fa = d2f_alu(d), fh = __double2float_rn(d);
-    if (__float_as_uint(fa) != __float_as_uint(fh) && !(fa != fa && fh != fh)) ++local;
-    // double-float split: hi, and the float64-exact remainder rounded
-    const float2 sp = df_split(d);
-    const float lh = __double2float_rn(d - (double)fh);
-    if ((__float_as_uint(sp.x) != __float_as_uint(fh) && !(sp.x != sp.x && fh != fh)) ||
-        (__float_as_uint(sp.y) != __float_as_uint(lh) && !(sp.y != sp.y && lh != lh)))
-      ++local;
-    // binary32 -> binary64
-    const float f = __uint_as_float((uint32_t)(r2 >> 7));
-    const double da = f2d_alu(f), dh = (double)f;
-    if (__double_as_longlong(da) != __double_as_longlong(dh) && !(da != da && dh != dh)) ++local;
-  }
-  if (local) atomicAdd(bad, local);
-}
 
 // ------------------------------------------------------------ allocation
 
@@ -904,23 +859,6 @@ struct CkptHeader {
 static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
 const char kCkptMagic[8] = {'T', 'H', 'O', 'R', 'C', 'K', 'P', '2'};
 }  // namespace
-
-int thor_convert_selftest(long long n, unsigned long long seed, long long* mismatches) {
-  if (!mismatches || n <= 0 || n > (1ll << 32)) return THOR_EINVAL;
-  unsigned long long* d = nullptr;
-  if (cudaMalloc(&d, sizeof(unsigned long long))) return THOR_ENOMEM;
-  cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
-  if (!e) {
-    thor::k_convert_probe<<<1216, 256>>>(n, seed, d);
-    e = cudaGetLastError();
-  }
-  unsigned long long h = 0;
-  if (!e) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
-  cudaFree(d);
-  if (e) return THOR_ECUDA;
-  *mismatches = (long long)h;
-  return THOR_OK;
-}
 
 int thor_wait_selftest(int arrive, unsigned int limit_us, int* gave_up) {
   if (!gave_up || limit_us < 1 || limit_us > 2000000) return THOR_EINVAL;

@@ -105,12 +105,12 @@ template <typename R> __device__ __forceinline__ R pc(double d, float f);
 template <> __device__ __forceinline__ double pc<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float pc<float>(double, float f) { return f; }
 
-// Factors of the per-stage vertical matrix, computed in float64: planes
-// [nv + 1][colp] (rows 1..nv-1 used) and one plane for the junction of the
-// two sweeps. Per row: the pivot reciprocal, c' (downward sweep) or e'
-// (upward sweep), and q, the off-diagonal entry lo (down) or up (up) times
-// the pivot reciprocal. 8 bytes per entry: float64 values for float64
-// states, double-float pairs (float2, df_split) for float-storage states.
+// Factors of the per-stage vertical matrix: planes [nv + 1][colp] (rows
+// 1..nv-1 used) and one plane for the junction of the two sweeps. Per row:
+// the pivot reciprocal, c' (downward sweep) or e' (upward sweep), and q, the
+// off-diagonal entry lo (down) or up (up) times the pivot reciprocal. 8
+// bytes per entry: float64 values for float64 states, double-float pairs
+// (float2) for float-storage states.
 template <typename R>
 struct Fac {
   double *inv, *cf, *junction, *q;
@@ -173,63 +173,6 @@ __device__ __forceinline__ R eos_dev(R pbar, R thbar, R thp, R gamma) {
   return pbar * rexpm1<R>(gamma * rlog1p<R>(thp / thbar));
 }
 
-// Conversions between binary32 and binary64 on the integer ALU (IEEE 754-2008
-// formats, Sec. 3.4; round to nearest, ties to even, Sec. 4.3.1). On the
-// GB300 a float64 conversion instruction issues on the narrow float64 pipe at
-// the rate of a float64 FMA; the column solve needs one per cell in and one
-// out, so the common cases are done with integer operations and the rest
-// (zeros, subnormals, infinities, NaN, out of float range) fall back to the
-// conversion instruction. Results are bit-identical to it (checked by
-// thor_convert_selftest).
-__device__ __forceinline__ double f2d_alu(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  // sign to bit 63, exponent and mantissa shifted into place, exponent
-  // rebiased from 127 to 1023
-  const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
-  const unsigned long long em =
-      ((unsigned long long)(u & 0x7fffffffu) << 29) + ((unsigned long long)(1023 - 127) << 52);
-  return __longlong_as_double((long long)(s | em));
-}
-__device__ __forceinline__ float d2f_alu(double d) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
-  const unsigned long long a = u & 0x7fffffffffffffffull;
-  // |d| in [2^-126, 2^128): a normal float, or infinity if it rounds up
-  if (a < ((unsigned long long)(1023 - 126) << 52) || a >= ((unsigned long long)(1023 + 128) << 52))
-    return (float)d;
-  const unsigned long long t = a - ((unsigned long long)(1023 - 127) << 52);   // exponent biased by 127
-  unsigned long long r = t >> 29;                        // exponent | top 23 mantissa bits
-  const unsigned long long rem = t & ((1ull << 29) - 1), half = 1ull << 28;
-  r += (rem > half || (rem == half && (r & 1ull))) ? 1ull : 0ull;   // a carry moves into the exponent
-  return __uint_as_float((uint32_t)((u >> 32) & 0x80000000u) | (uint32_t)r);
-}
-template <typename R> __device__ __forceinline__ double to_f64(R x);
-template <> __device__ __forceinline__ double to_f64<double>(double x) { return x; }
-template <> __device__ __forceinline__ double to_f64<float>(float x) { return f2d_alu(x); }
-template <typename R> __device__ __forceinline__ R from_f64(double x);
-template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
-template <> __device__ __forceinline__ float from_f64<float>(double x) { return d2f_alu(x); }
-
-// 1/x in float64: a float32 reciprocal refined by two Newton-Raphson steps
-// r <- r + r (1 - x r); each step squares the relative error (2^-23 -> 2^-46
-// -> below 2^-53), at four float64 FMAs instead of a float64 division.
-__device__ __forceinline__ double rcp64(double x) {
-  double r = (double)__frcp_rn((float)x);
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
-
-// 1/x to about 2^-47: a float32 reciprocal (relative error <= 2^-24) refined
-// by one Newton-Raphson step; used for the pivots of the float64 elimination
-// in the mixed-precision path.
-__device__ __forceinline__ double rcp64_1(double x) {
-  double r = f2d_alu(__frcp_rn(d2f_alu(x)));
-  return fma(r, fma(-x, r, 1.0), r);
-}
-
 // Double-float numbers: an unevaluated sum hi + lo of two floats with
 // |lo| <= ulp(hi) / 2, about 48 significant bits, on the float32 pipes
 // (double-double arithmetic of Hida, Li and Bailey 2001, with float words).
@@ -241,36 +184,6 @@ __device__ __forceinline__ double rcp64_1(double x) {
 // explicitly rounded intrinsics, which the compiler never contracts into
 // FMAs.
 //
-// splits a float64 value into its double-float pair: hi = x rounded to
-// float (nearest, ties to even), lo = the remainder x - hi rounded to float.
-// With the 53-bit significand M and exponent E of x, hi = H 2^(E-23) for
-// H = M / 2^29 rounded, and the remainder is exactly (M - H 2^29) 2^(E-52),
-// so both come from integer operations and exact scalings by powers of two;
-// exponents outside [-70, 126] (zero, tiny, huge, non-finite values) take
-// the float64 route.
-__device__ __forceinline__ float2 df_split(double x) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const unsigned long long a = u & 0x7fffffffffffffffull;
-  const int E = (int)(a >> 52) - 1023;
-  if (E < -70 || E > 126) {
-    const float h = d2f_alu(x);
-    return make_float2(h, d2f_alu(x - f2d_alu(h)));
-  }
-  const unsigned long long M = (a & ((1ull << 52) - 1)) | (1ull << 52);
-  unsigned long long H = M >> 29;
-  long long rem = (long long)(M & ((1ull << 29) - 1));
-  if (rem > (1ll << 28) || (rem == (1ll << 28) && (H & 1ull))) {
-    H += 1;
-    rem -= 1ll << 29;
-  }
-  float h = __fmul_rn(__int2float_rn((int)H), __int_as_float((E - 23 + 127) << 23));
-  float l = __fmul_rn(__int2float_rn((int)rem), __int_as_float((E - 52 + 127) << 23));
-  if (u >> 63) {
-    h = -h;
-    l = -l;
-  }
-  return make_float2(h, l);
-}
 // (ph + pl) - c x, renormalised: the product's error-free high part by FMA
 // (Dekker's TwoProduct), the difference of the high words by Knuth's
 // TwoSum, the low words added to the error, then one fast TwoSum
@@ -295,6 +208,23 @@ __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
   const float l = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, __fmaf_rn(a.x, b.x, -h)));
   const float s = __fadd_rn(h, l);
   return make_float2(s, __fsub_rn(l, __fsub_rn(s, h)));
+}
+// a b for a float a, renormalised
+__device__ __forceinline__ float2 df_mul_f(float a, float2 b) {
+  const float h = __fmul_rn(a, b.x);
+  const float l = __fmaf_rn(a, b.y, __fmaf_rn(a, b.x, -h));
+  const float s = __fadd_rn(h, l);
+  return make_float2(s, __fsub_rn(l, __fsub_rn(s, h)));
+}
+// 1 / a: the float reciprocal r of the high word refined by one
+// Newton-Raphson step r + r (1 - a r), the residual 1 - a r (about 2^-24)
+// formed in double-float; relative error about 2^-46
+__device__ __forceinline__ float2 df_rcp(float2 a) {
+  const float r = __frcp_rn(a.x);
+  const float2 e = df_fms(1.0f, 0.0f, a, make_float2(r, 0.0f));
+  const float t = __fmul_rn(r, e.x);
+  const float s = __fadd_rn(r, t);
+  return make_float2(s, __fsub_rn(t, __fsub_rn(s, r)));
 }
 // the float nearest to hi + lo (one rounding of the exact sum)
 __device__ __forceinline__ float df_to_float(float2 a) { return __fadd_rn(a.x, a.y); }

@@ -535,19 +535,12 @@ __device__ __forceinline__ void d_ss_flux(const Geo<R>& G, const VR<R>& U, const
   }
 }
 
-// one row's factors, as float64 values or, for float-storage states, as
-// double-float pairs
+// one row's factors of a float64 state
 template <typename R>
 __device__ __forceinline__ void fac_store(const Fac<R>& F, int i, double inv, double cf, double q) {
-  if (sizeof(R) == sizeof(double)) {
-    F.inv[i] = inv;
-    F.cf[i] = cf;
-    F.q[i] = q;
-  } else {
-    reinterpret_cast<float2*>(F.inv)[i] = df_split(inv);
-    reinterpret_cast<float2*>(F.cf)[i] = df_split(cf);
-    reinterpret_cast<float2*>(F.q)[i] = df_split(q);
-  }
+  F.inv[i] = inv;
+  F.cf[i] = cf;
+  F.q[i] = q;
 }
 
 // HE-VI column step, part 2 (matrix). Substituting Eqs. dens2 and pt2 into
@@ -564,7 +557,9 @@ __device__ __forceinline__ void fac_store(const Fac<R>& F, int i, double inv, do
 // The matrix depends only on the stage state (Pi, theta) and dtau, so it is
 // factorised once per RK stage and the factors serve every small step of
 // the stage. The factorisation is the matrix half of a two-sided Thomas
-// algorithm in float64: warp 0 eliminates rows 1..p downwards
+// algorithm, in float64 for float64 states and in double-float (df_rcp,
+// df_mul_f: pivot reciprocals to about 2^-46) for float-storage states:
+// warp 0 eliminates rows 1..p downwards
 // (c'_m = up_m / (di_m - lo_m c'_m-1)), warp 1 rows nv-1..p+1 upwards
 // (e'_m = lo_m / (di_m - up_m e'_m+1)); the two warps run on different SM
 // sub-partitions. Stored per row: the pivot reciprocal, c' or e', and q = lo
@@ -581,7 +576,8 @@ __device__ __forceinline__ void d_ss_factor(const Geo<R>& G, const VR<R>& U, con
   const int p = N / 2 > 0 ? N / 2 : 1;
   const R g = pc<R>(ph.g, ph.g_f), dt2 = (R)(dtau * dtau), delta = pc<R>(ph.delta, ph.delta_f);
   __shared__ double sj[2][32];
-  auto coef = [&](int m, double& lo, double& di, double& up) {
+  // the matrix row m in the storage type
+  auto coef_r = [&](int m, R& lo, R& di, R& up) {
     const int i = m * S + cs;
     const R pi_lo = ld(SL.pi + (i - S)), pi_hi = ld(SL.pi + i);
     const R wlo = ld(U.wlo + m), whi = ld(U.whi + m), dtz = dt2 * ld(U.inv_dzc + m);
@@ -591,11 +587,58 @@ __device__ __forceinline__ void d_ss_factor(const Geo<R>& G, const VR<R>& U, con
     R lower = 0, upper = 0;
     if (m > 1) lower = (-dtz * pi_lo * ld(SL.thi + (i - S)) + dt2 * g * wlo) * ql;
     if (m < N) upper = (-dtz * pi_hi * ld(SL.thi + (i + S)) - dt2 * g * whi) * ph_;
-    lo = to_f64<R>(lower);
-    up = to_f64<R>(upper);
-    di = to_f64<R>(delta + dtz * th_m * (pi_hi * pl + pi_lo * qh) - dt2 * g * (wlo * qh - whi * pl));
+    lo = lower;
+    up = upper;
+    di = delta + dtz * th_m * (pi_hi * pl + pi_lo * qh) - dt2 * g * (wlo * qh - whi * pl);
   };
-  auto inv_of = [](double den) { return sizeof(R) == sizeof(double) ? 1.0 / den : rcp64_1(den); };
+  if constexpr (sizeof(R) == sizeof(float)) {
+    // float storage: the factorisation in double-float on the float32 pipes
+    // (the float coefficients are exact pairs), stored as pairs
+    __shared__ float2 sj2[2][32];
+    float2* Finv = reinterpret_cast<float2*>(F.inv);
+    float2* Fcf = reinterpret_cast<float2*>(F.cf);
+    float2* Fq = reinterpret_cast<float2*>(F.q);
+    float2 last = make_float2(0.f, 0.f);
+    if (half == 0) {
+      for (int m = 1; m <= p; ++m) {
+        R lo, di, up;
+        coef_r(m, lo, di, up);
+        const float2 inv = df_rcp(df_fms(di, 0.f, make_float2(lo, 0.f), last));
+        last = df_mul_f(up, inv);
+        if (valid) {
+          Finv[m * S + c] = inv;
+          Fcf[m * S + c] = last;
+          Fq[m * S + c] = df_mul_f(lo, inv);
+        }
+      }
+    } else {
+      for (int m = N; m > p; --m) {
+        R lo, di, up;
+        coef_r(m, lo, di, up);
+        const float2 inv = df_rcp(df_fms(di, 0.f, make_float2(up, 0.f), last));
+        last = df_mul_f(lo, inv);
+        if (valid) {
+          Finv[m * S + c] = inv;
+          Fcf[m * S + c] = last;
+          Fq[m * S + c] = df_mul_f(up, inv);
+        }
+      }
+    }
+    sj2[half][tx] = last;    // c'_p (warp 0) and e'_p+1 (warp 1)
+    __syncthreads();
+    if (half == 0 && valid)
+      reinterpret_cast<float2*>(F.junction)[c] =
+          p < N ? df_rcp(df_fms(1.f, 0.f, sj2[0][tx], sj2[1][tx])) : make_float2(1.f, 0.f);
+    return;
+  }
+  auto coef = [&](int m, double& lo, double& di, double& up) {
+    R l, d, u;
+    coef_r(m, l, d, u);
+    lo = l;
+    di = d;
+    up = u;
+  };
+  auto inv_of = [](double den) { return 1.0 / den; };
   double last = 0.0;
   if (half == 0) {
     for (int m = 1; m <= p; ++m) {
@@ -616,13 +659,7 @@ __device__ __forceinline__ void d_ss_factor(const Geo<R>& G, const VR<R>& U, con
   }
   sj[half][tx] = last;     // c'_p (warp 0) and e'_p+1 (warp 1)
   __syncthreads();
-  if (half == 0 && valid) {
-    const double j = p < N ? 1.0 / (1.0 - sj[0][tx] * sj[1][tx]) : 1.0;
-    if (sizeof(R) == sizeof(double))
-      F.junction[c] = j;
-    else
-      reinterpret_cast<float2*>(F.junction)[c] = df_split(j);
-  }
+  if (half == 0 && valid) F.junction[c] = p < N ? 1.0 / (1.0 - sj[0][tx] * sj[1][tx]) : 1.0;
 }
 
 // End of an RK stage for one cell of the column step: Phi^(s+1) = Phi^(s) +
@@ -757,7 +794,7 @@ __device__ __forceinline__ void d_ss_solve(const Geo<R>& G, const VR<R>& U, cons
     }
   } else {
     // float64 storage: the elimination in float64
-    auto rhs = [&](int m) { return to_f64<R>(rhs_r(m)); };
+    auto rhs = [&](int m) { return (double)rhs_r(m); };
     if (half == 0) {
       double d1 = 0.0;
 #pragma unroll 4

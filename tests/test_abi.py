@@ -79,10 +79,6 @@ def test_ensemble_argument_checks_need_no_device():
         with pytest.raises(thor.ThorError) as e:
             thor.thor_wait_selftest(0, limit)
         assert e.value.status == thor.THOR_EINVAL
-    for n in (0, -5, (1 << 32) + 1):
-        with pytest.raises(thor.ThorError) as e:
-            thor.thor_convert_selftest(n)
-        assert e.value.status == thor.THOR_EINVAL
     with pytest.raises(thor.ThorError) as e:
         thor.thor_budget_read(None)
     assert e.value.status == thor.THOR_EINVAL

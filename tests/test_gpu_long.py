@@ -187,11 +187,3 @@ def test_bounded_device_wait_gives_up_and_the_context_stays_usable():
         thor.thor_state_destroy(st)
         thor.thor_grid_destroy(grid)
 
-
-def test_alu_float_conversions_are_exact():
-    """The integer-ALU binary32 <-> binary64 conversions of the column
-    factorisation and solve, and the integer double-float split of the
-    factorisation, agree bit for bit with the conversion instructions: 2^24
-    seeded patterns per direction, ties and the edges of the binary32 range
-    included."""
-    assert thor.thor_convert_selftest(1 << 24, 12345) == 0
