@@ -280,7 +280,7 @@ int thor_launch_count(const thor_state* state, long long* count);
  * after the step (restore a checkpoint with thor_state_set). Default 0. */
 enum { THOR_TUNE_KCHUNK = 0, THOR_TUNE_GRAPH = 1, THOR_TUNE_CHECK_FINITE = 2, THOR_TUNE_BLOCK = 3,
        THOR_TUNE_SOLVE_TMA = 4, THOR_TUNE_ENERGY_FIXER = 5, THOR_TUNE_BUDGET = 6,
-       THOR_TUNE_RK_STAGES = 7, THOR_TUNE_COMPENSATED = 8 };
+       THOR_TUNE_RK_STAGES = 7, THOR_TUNE_COMPENSATED = 8, THOR_TUNE_L2_HINTS = 9 };
 int thor_tune(thor_state* state, int knob, int value);
 
 /* Energy and angular-momentum budget of the large steps recorded since
@@ -370,7 +370,15 @@ int thor_zonal_read_w(thor_state* state, int nlat, double* out, size_t n, long l
  * the low parts (6 planes), zeroed; 0 frees them and rounds the state to
  * its float parts. Synchronises the state's stream. Ensembles step
  * compensated members the same way. THOR_EINVAL for THOR_FP64 states.
- * Default 1 for THOR_MIXED states (thor_state_init allocates the low parts). */
+ * Default 1 for THOR_MIXED states (thor_state_init allocates the low parts).
+ * THOR_TUNE_L2_HINTS (0..3; no passage of the paper: a memory-placement
+ * knob): L2 eviction priorities of the acoustic small steps' loads and
+ * stores. Bit 0 loads the stage constants (slow tendencies, Pi, theta at
+ * the interfaces, the column matrix's factors) evict-first, bit 1 keeps
+ * the perturbations and the kernel split's intermediates evict-last.
+ * Results do not depend on it (tested bit for bit). Library-wide on the
+ * current device (every state and ensemble); default 1. THOR_EINVAL
+ * outside 0..3, THOR_ECUDA if the device rejects it. */
 
 /* Launch-shape autotuner (an extension; the paper fixes no launch shapes).
  * Times `steps` large steps of (n_small, dt) for every levels-per-thread

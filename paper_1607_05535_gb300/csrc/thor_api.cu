@@ -982,6 +982,10 @@ int thor_tune(thor_state* s, int knob, int value) {
     return THOR_OK;
   }
   if (knob == THOR_TUNE_COMPENSATED) return s->impl->set_compensated(value != 0);
+  if (knob == THOR_TUNE_L2_HINTS) {
+    if (value < 0 || value > 3) return THOR_EINVAL;
+    return thor::set_l2_mode(value) ? THOR_ECUDA : THOR_OK;
+  }
   if (knob == THOR_TUNE_RK_STAGES) {
     if (value < 1 || value > 3) return THOR_EINVAL;
     s->impl->rk_stages = value;

@@ -11,6 +11,10 @@
 
 namespace thor {
 
+// L2 eviction priorities of the small-step kernels (THOR_TUNE_L2_HINTS);
+// 0 on success
+int set_l2_mode(int mode);
+
 // Derived fields and intermediates
 template <typename R>
 struct Work {

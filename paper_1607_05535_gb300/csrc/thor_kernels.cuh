@@ -143,6 +143,13 @@ template <typename R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return sqrtf(x); }
 
+// a b + c with one rounding, written out where a sum of two products could
+// otherwise be contracted either way (kernels that must agree bit for bit
+// then contract alike)
+template <typename R> __device__ __forceinline__ R fmar(R a, R b, R c);
+template <> __device__ __forceinline__ double fmar<double>(double a, double b, double c) { return fma(a, b, c); }
+template <> __device__ __forceinline__ float fmar<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
 // Knuth's TwoSum: s = fl(a + b) and the rounding error e, so that s + e equals
 // a + b exactly (no multiplication, so no contraction into an FMA can touch
 // it). The compensated state keeps every prognostic field as such a pair.
@@ -235,6 +242,44 @@ __device__ __forceinline__ float df_to_float(float2 a) { return __fadd_rn(a.x, a
 template <typename T>
 __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
+// L2 eviction priority of single loads and stores (createpolicy with
+// .L2::cache_hint). The acoustic small steps of a stage read two kinds of
+// planes: stage constants (slow tendencies, Pi, theta, the factors of the
+// column matrix), read once per small step, and perturbations and the
+// split's intermediates, written by one kernel and read by the next. At
+// glevel 6 x 32 levels the two sets together exceed L2, so without hints
+// each small step streams both from HBM; loading the constants evict-first
+// and keeping the perturbations evict-last lets the second set stay in L2.
+// Hints change where a line lives, never a value.
+enum { kL2Normal = 0, kL2First = 1, kL2Last = 2 };
+__device__ __forceinline__ uint64_t l2_policy(int prio) {
+  uint64_t p;
+  if (prio == kL2First)
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  else if (prio == kL2Last)
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  else
+    asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// read-only loads (non-coherent path, like ld) with a policy
+__device__ __forceinline__ float ldh(const float* p, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double ldh(const double* p, uint64_t pol) {
+  double v;
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void sth(float* p, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void sth(double* p, double v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+
 // Four values of one cell stored together ([level][colp][4] planes), so that
 // a stencil gathers them with one 16-byte (float) or two 16-byte (double)
 // loads per neighbour instead of four.
@@ -258,6 +303,32 @@ __device__ __forceinline__ void st4(double* base, size_t cell, double x, double 
   reinterpret_cast<double2*>(base)[2 * cell] = make_double2(x, y);
   reinterpret_cast<double2*>(base)[2 * cell + 1] = make_double2(z, w);
 }
+// the same with an L2 policy (l2_policy)
+__device__ __forceinline__ Q4<float> ld4h(const float* base, size_t cell, uint64_t pol) {
+  Q4<float> v;
+  asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(base + 4 * cell), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ Q4<double> ld4h(const double* base, size_t cell, uint64_t pol) {
+  Q4<double> v;
+  asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(base + 4 * cell), "l"(pol));
+  asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.z), "=d"(v.w) : "l"(base + 4 * cell + 2), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st4h(float* base, size_t cell, float x, float y, float z, float w, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(base + 4 * cell), "f"(x), "f"(y),
+               "f"(z), "f"(w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void st4h(double* base, size_t cell, double x, double y, double z, double w, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(base + 4 * cell), "d"(x), "d"(y), "l"(pol)
+               : "memory");
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(base + 4 * cell + 2), "d"(z), "d"(w),
+               "l"(pol)
+               : "memory");
+}
 
 // two values of one cell stored together ([level][colp][2] planes)
 template <typename R>
@@ -277,6 +348,24 @@ __device__ __forceinline__ void st2(float* base, size_t cell, float x, float y) 
 }
 __device__ __forceinline__ void st2(double* base, size_t cell, double x, double y) {
   reinterpret_cast<double2*>(base)[cell] = make_double2(x, y);
+}
+__device__ __forceinline__ Q2<float> ld2h(const float* base, size_t cell, uint64_t pol) {
+  Q2<float> v;
+  asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(base + 2 * cell), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ Q2<double> ld2h(const double* base, size_t cell, uint64_t pol) {
+  Q2<double> v;
+  asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(base + 2 * cell), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st2h(float* base, size_t cell, float x, float y, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(base + 2 * cell), "f"(x), "f"(y), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void st2h(double* base, size_t cell, double x, double y, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(base + 2 * cell), "d"(x), "d"(y), "l"(pol)
+               : "memory");
 }
 
 struct Nbr7 {
@@ -510,6 +599,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// the same two with an L2 policy (thor::l2_policy)
+__device__ __forceinline__ void tma_prefetch_2d(const void* map, int x, int y, uint64_t pol) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.L2::cache_hint [%0, {%1, %2}], %3;" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, "
+      "%3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
 }
 // box of a 2-D tensor map (x = column, y = plane) into shared memory
 __device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y, uint64_t* bar) {

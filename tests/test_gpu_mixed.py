@@ -91,3 +91,31 @@ def test_staged_solve_matches_direct_solve(graph):
         thor.thor_state_destroy(a)
         thor.thor_state_destroy(b)
         thor.thor_grid_destroy(grid)
+
+
+def test_l2_hints_change_no_value():
+    """The L2 eviction priorities of the small steps (THOR_TUNE_L2_HINTS)
+    only place lines in the cache: every mode steps a mixed state to the
+    same bits; values outside 0..3 are refused."""
+    from harness import init_struct, planet_struct
+    wl = wls.HS_G4.with_(n_large=3)
+    grid = thor.thor_grid_create(wl.glevel, wl.nv, wl.planet.radius, wl.z_top,
+                                 thor.thor_spring(1.15, 1.0, 1.0, 0.01, 0.0, wl.spring_max_iter))
+    fields = (thor.THOR_FIELD_RHO, thor.THOR_FIELD_MOM, thor.THOR_FIELD_W, thor.THOR_FIELD_RHOTHETA)
+    out = []
+    try:
+        for mode in (0, 3, 2, 1):          # ends at the default, 1
+            s_ = thor.thor_state_init(grid, planet_struct(wl.planet), init_struct(wl, thor.THOR_MIXED), None)
+            try:
+                thor.thor_tune(s_, thor.THOR_TUNE_L2_HINTS, mode)
+                thor.thor_step(s_, wl.n_large, wl.n_small, wl.dt)
+                out.append([thor.thor_state_get(s_, f, wl.ncol, wl.nv) for f in fields])
+                with pytest.raises(thor.ThorError):
+                    thor.thor_tune(s_, thor.THOR_TUNE_L2_HINTS, 4)
+            finally:
+                thor.thor_state_destroy(s_)
+    finally:
+        thor.thor_grid_destroy(grid)
+    for o in out[1:]:
+        for x, y, f in zip(out[0], o, fields):
+            assert np.array_equal(x, y), f
