@@ -280,7 +280,8 @@ int thor_launch_count(const thor_state* state, long long* count);
  * after the step (restore a checkpoint with thor_state_set). Default 0. */
 enum { THOR_TUNE_KCHUNK = 0, THOR_TUNE_GRAPH = 1, THOR_TUNE_CHECK_FINITE = 2, THOR_TUNE_BLOCK = 3,
        THOR_TUNE_SOLVE_TMA = 4, THOR_TUNE_ENERGY_FIXER = 5, THOR_TUNE_BUDGET = 6,
-       THOR_TUNE_RK_STAGES = 7, THOR_TUNE_COMPENSATED = 8, THOR_TUNE_L2_HINTS = 9 };
+       THOR_TUNE_RK_STAGES = 7, THOR_TUNE_COMPENSATED = 8, THOR_TUNE_L2_HINTS = 9,
+       THOR_TUNE_LEVEL_SPLIT = 10 };
 int thor_tune(thor_state* state, int knob, int value);
 
 /* Energy and angular-momentum budget of the large steps recorded since
@@ -378,7 +379,15 @@ int thor_zonal_read_w(thor_state* state, int nlat, double* out, size_t n, long l
  * the perturbations and the kernel split's intermediates evict-last.
  * Results do not depend on it (tested bit for bit). Library-wide on the
  * current device (every state and ensemble); default 1. THOR_EINVAL
- * outside 0..3, THOR_ECUDA if the device rejects it. */
+ * outside 0..3, THOR_ECUDA if the device rejects it.
+ * THOR_TUNE_LEVEL_SPLIT (0 or 1; a launch-shape knob): 1 runs the small
+ * steps' three horizontal stencils (the Laplacian of D, the momentum step,
+ * the column fluxes) as two chains, the lower and the upper half of the
+ * levels, on two streams (graph branches), joined before the column solve:
+ * the levels of a horizontal stencil do not depend on each other, and one
+ * chain's kernels fill the SMs the other's leave idle while they start and
+ * drain. Default 1 (g6 x 32 large step 1.477 -> 1.426 ms at 4 levels per
+ * thread); the same numbers either way (tested bit for bit). */
 
 /* Launch-shape autotuner (an extension; the paper fixes no launch shapes).
  * Times `steps` large steps of (n_small, dt) for every levels-per-thread

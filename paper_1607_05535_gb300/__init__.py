@@ -23,7 +23,7 @@ THOR_FIELD_RHO, THOR_FIELD_MOM, THOR_FIELD_W, THOR_FIELD_RHOTHETA, THOR_FIELD_PR
     THOR_FIELD_TEMPERATURE = range(6)
 (THOR_TUNE_KCHUNK, THOR_TUNE_GRAPH, THOR_TUNE_CHECK_FINITE, THOR_TUNE_BLOCK, THOR_TUNE_SOLVE_TMA,
  THOR_TUNE_ENERGY_FIXER, THOR_TUNE_BUDGET, THOR_TUNE_RK_STAGES, THOR_TUNE_COMPENSATED,
- THOR_TUNE_L2_HINTS) = range(10)
+ THOR_TUNE_L2_HINTS, THOR_TUNE_LEVEL_SPLIT) = range(11)
 THOR_ENSEMBLE_MAX = 4096
 THOR_MLP_TUNE_TCGEN05 = 0
 

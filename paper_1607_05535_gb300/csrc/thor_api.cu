@@ -303,6 +303,12 @@ Impl<R>::~Impl() {
     cudaStreamSynchronize(side);
     cudaStreamDestroy(side);
   }
+  if (side2) {
+    cudaStreamSynchronize(side2);
+    cudaStreamDestroy(side2);
+  }
+  if (ev_s1) cudaEventDestroy(ev_s1);
+  if (ev_s2) cudaEventDestroy(ev_s2);
   if (ev_fork) cudaEventDestroy(ev_fork);
   if (ev_join) cudaEventDestroy(ev_join);
   if (ev_join0) cudaEventDestroy(ev_join0);
@@ -692,6 +698,15 @@ int make_impl(thor_grid* grid, const thor_planet& pl, const thor_init& in, cudaS
     if (I->side) cudaStreamDestroy(I->side);
     I->side = nullptr;
   }
+  // third stream for the upper levels of the small steps' stencils
+  // (THOR_TUNE_LEVEL_SPLIT; optional as well)
+  if (cudaStreamCreateWithFlags(&I->side2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&I->ev_s1, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&I->ev_s2, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (I->side2) cudaStreamDestroy(I->side2);
+    I->side2 = nullptr;
+  }
   HostSetup hs;
   int rc = host_setup(h, pl, in, hs);
   if (rc) return rc;
@@ -982,6 +997,11 @@ int thor_tune(thor_state* s, int knob, int value) {
     return THOR_OK;
   }
   if (knob == THOR_TUNE_COMPENSATED) return s->impl->set_compensated(value != 0);
+  if (knob == THOR_TUNE_LEVEL_SPLIT) {
+    s->impl->level_split = value != 0;
+    s->impl->reset_graph();
+    return THOR_OK;
+  }
   if (knob == THOR_TUNE_L2_HINTS) {
     if (value < 0 || value > 3) return THOR_EINVAL;
     return thor::set_l2_mode(value) ? THOR_ECUDA : THOR_OK;

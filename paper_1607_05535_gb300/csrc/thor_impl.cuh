@@ -110,6 +110,7 @@ struct ImplBase {
   int kchunk = 2;                      // levels per thread in the stencil kernels
   int block = kBlock;                  // threads (columns) per block of the stencil kernels
   int solve_tma = 1;                   // TMA-staged column solve where available
+  int level_split = 1;                 // small-step stencils in two level halves on two streams
   int rk_stages = 3;                   // RK3 stages a large step runs (THOR_TUNE_RK_STAGES; tests)
   int* dev_err = nullptr;              // device flag: 1 = a bounded device wait timed out
   // energy fixer and budget (thor_tune THOR_TUNE_ENERGY_FIXER / THOR_TUNE_BUDGET)
@@ -228,6 +229,10 @@ struct Impl : ImplBase {
   // state's stream)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join0 = nullptr;
+  // the small steps' stencils over the upper levels run on side2 beside the
+  // lower levels on the state's stream (THOR_TUNE_LEVEL_SPLIT)
+  cudaStream_t side2 = nullptr;
+  cudaEvent_t ev_s1 = nullptr, ev_s2 = nullptr;
   // whole-state transfers: one event per field between its conversion (on
   // the state's stream) and its copy (on the side stream)
   cudaEvent_t ev_x[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -88,13 +88,14 @@ __device__ __forceinline__ void d_derived(const Geo<R>& G, const VR<R>& U, const
 // First Laplacians of the hyperdiffusion (Sec. 4), already multiplied by
 // K_d and, for the momentum and temperature terms, by rho.
 template <typename R, bool HO = false>
-__device__ __forceinline__ void d_lap1(const Geo<R>& G, const VR<R>& U, const Xf<R>& X, const Work<R>& T, R Kd, int kchunk, int bx, int by) {
+__device__ __forceinline__ void d_lap1(const Geo<R>& G, const VR<R>& U, const Xf<R>& X, const Work<R>& T, R Kd, int kchunk, int bx, int by,
+                                       int kend) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
   W7<R> wl = load_w7(G.wlap, S, c);
-  int k0 = by * kchunk, k1 = min(G.nv + 1, k0 + kchunk);
+  int k0 = by * kchunk, k1 = min(kend, k0 + kchunk);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
     if (k < G.nv) {
@@ -130,7 +131,7 @@ __device__ __forceinline__ void d_lap1(const Geo<R>& G, const VR<R>& U, const Xf
 // metric terms the approximation drops)
 template <typename R, bool SH = false, bool HO = false>
 __device__ __forceinline__ void d_slow(const Geo<R>& G, const VR<R>& U, const Phys& ph, const Xf<R>& X, const Work<R>& T, const Slow<R>& SL, int hyper,
-                                            R* d0, int kchunk, int bx, int by) {
+                                            R* d0, int kchunk, int bx, int by, int kend) {
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
@@ -142,7 +143,7 @@ __device__ __forceinline__ void d_slow(const Geo<R>& G, const VR<R>& U, const Ph
   R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
   const R two_om = pc<R>(ph.two_omega, ph.two_omega_f), gamma = pc<R>(ph.gamma, ph.gamma_f),
           Rd = pc<R>(ph.Rd, ph.Rd_f);
-  int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
+  int k0 = by * kchunk, k1 = min(kend, k0 + kchunk);
   constexpr int kUnroll = sizeof(R) == sizeof(float) ? 2 : 1;   // float64: registers
 #pragma unroll kUnroll
   for (int k = k0; k < k1; ++k) {
@@ -1057,13 +1058,14 @@ __global__ void k_derived(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, int sh
   d_derived<R, HO>(G, U, ph, X, T, shallow, kchunk, blockIdx.x, blockIdx.y);
 }
 template <typename R, bool HO>
-__global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk) {
-  d_lap1<R, HO>(G, U, X, T, Kd, kchunk, blockIdx.x, blockIdx.y);
+__global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk, int klo, int kend) {
+  d_lap1<R, HO>(G, U, X, T, Kd, kchunk, blockIdx.x, blockIdx.y + klo, kend);
 }
 template <typename R, bool SH, bool HO>
 __global__ void __launch_bounds__(kMaxBlock, 2)
-    k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper, R* d0, int kchunk) {
-  d_slow<R, SH, HO>(G, U, ph, X, T, SL, hyper, d0, kchunk, blockIdx.x, blockIdx.y);
+    k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper, R* d0, int kchunk, int klo,
+           int kend) {
+  d_slow<R, SH, HO>(G, U, ph, X, T, SL, hyper, d0, kchunk, blockIdx.x, blockIdx.y + klo, kend);
 }
 template <typename R, bool HO>
 __global__ void k_slow_w(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work<R> T, Slow<R> SL, Pert<R> P, int hyper,
@@ -1075,20 +1077,28 @@ __global__ void k_stage_init(Geo<R> G, VR<R> U, Phys ph, Xf<R> Xt, Xf<R> X, Work
                              Xf<R> XL, int zero, int kchunk) {
   d_stage_init<R>(G, U, ph, Xt, X, T, P, XtL, XL, zero, kchunk, blockIdx.x, blockIdx.y);
 }
+// the small-step stencils take a level range [kchunk * klo, khi) (klo in
+// chunks), so that the lower and upper levels can run as separate launches
 template <typename R>
-__global__ void k_ss_lapd(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, const R* pstar, int kchunk) {
-  d_ss_lapd<R>(G, U, T, dsrc, pstar, kchunk, blockIdx.x, blockIdx.y);
+__global__ void k_ss_lapd(Geo<R> G, VR<R> U, Work<R> T, const R* dsrc, const R* pstar, int kchunk, int klo,
+                          int khi) {
+  G.nv = khi;
+  d_ss_lapd<R>(G, U, T, dsrc, pstar, kchunk, blockIdx.x, blockIdx.y + klo);
 }
 // LAST: the last small step of a stage (a separate instantiation, so the
 // other small steps carry no registers for the stage end)
 template <typename R, bool LAST>
 __global__ void k_ss_mom(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, R Kd, int divdamp,
-                         Xf<R> Xs, Xf<R> Xo, Xf<R> XsL, Xf<R> XoL, int kchunk) {
-  d_ss_mom<R>(G, U, SL, P, T, dtau, Kd, divdamp, Xs, Xo, XsL, XoL, LAST ? 1 : 0, kchunk, blockIdx.x, blockIdx.y);
+                         Xf<R> Xs, Xf<R> Xo, Xf<R> XsL, Xf<R> XoL, int kchunk, int klo, int khi) {
+  G.nv = khi;
+  d_ss_mom<R>(G, U, SL, P, T, dtau, Kd, divdamp, Xs, Xo, XsL, XoL, LAST ? 1 : 0, kchunk, blockIdx.x,
+              blockIdx.y + klo);
 }
 template <typename R>
-__global__ void k_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, int kchunk) {
-  d_ss_flux<R>(G, U, SL, P, T, dtau, kchunk, blockIdx.x, blockIdx.y);
+__global__ void k_ss_flux(Geo<R> G, VR<R> U, Slow<R> SL, Pert<R> P, Work<R> T, R dtau, int kchunk, int klo,
+                          int khi) {
+  G.nv = khi;
+  d_ss_flux<R>(G, U, SL, P, T, dtau, kchunk, blockIdx.x, blockIdx.y + klo);
 }
 template <typename R>
 __global__ void __launch_bounds__(64) k_ss_factor(Geo<R> G, VR<R> U, Phys ph, Slow<R> SL, Fac<R> F, double dtau) {
@@ -1372,9 +1382,9 @@ template <typename R>
 __global__ void ke_lap1(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
   THOR_MEMBER();
   if (a.hyper && a.ph.vorder > 1)
-    d_lap1<R, true>(a.G, a.U, Xs, a.T, a.Kd, kchunk, e.y, blockIdx.y);
+    d_lap1<R, true>(a.G, a.U, Xs, a.T, a.Kd, kchunk, e.y, blockIdx.y, a.G.nv + 1);
   else if (a.hyper)
-    d_lap1<R>(a.G, a.U, Xs, a.T, a.Kd, kchunk, e.y, blockIdx.y);
+    d_lap1<R>(a.G, a.U, Xs, a.T, a.Kd, kchunk, e.y, blockIdx.y, a.G.nv + 1);
 }
 template <typename R>
 __global__ void __launch_bounds__(kMaxBlock, 2)
@@ -1383,13 +1393,13 @@ __global__ void __launch_bounds__(kMaxBlock, 2)
   R* d0 = s == 0 && a.divdamp ? a.T.dd0 : nullptr;
   const bool ho = a.ph.vorder > 1;
   if (a.shallow && ho)
-    d_slow<R, true, true>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, d0, kchunk, e.y, blockIdx.y);
+    d_slow<R, true, true>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, d0, kchunk, e.y, blockIdx.y, a.G.nv);
   else if (a.shallow)
-    d_slow<R, true>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, d0, kchunk, e.y, blockIdx.y);
+    d_slow<R, true>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, d0, kchunk, e.y, blockIdx.y, a.G.nv);
   else if (ho)
-    d_slow<R, false, true>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, d0, kchunk, e.y, blockIdx.y);
+    d_slow<R, false, true>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, d0, kchunk, e.y, blockIdx.y, a.G.nv);
   else
-    d_slow<R, false>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, d0, kchunk, e.y, blockIdx.y);
+    d_slow<R, false>(a.G, a.U, a.ph, Xs, a.T, a.SL, a.hyper, d0, kchunk, e.y, blockIdx.y, a.G.nv);
 }
 template <typename R>
 __global__ void ke_slow_w(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
@@ -1493,8 +1503,13 @@ int Impl<R>::large_step(double dt, int n_small) {
   dim3 gsolve((G.ncol + 31) / 32);
   const size_t solve_smem = solve_smem_bytes(G.nv);
   const bool staged = solve_tma && smaps != nullptr;
-  auto lapd = [&](cudaStream_t st, const R* dsrc) -> cudaError_t {
-    return launch_k(k_ss_lapd<R>, g2, bs, 0, st, G, U, T, dsrc, (const R*)P.p, kc);
+  // level halves of the small-step stencils (THOR_TUNE_LEVEL_SPLIT): levels
+  // [0, kc * hc) on the state's stream, [kc * hc, nv) on side2
+  const bool lsplit = level_split && side != nullptr && !prof_on && side2 != nullptr && G.nv >= 2 * kc;
+  const int nch = (G.nv + kc - 1) / kc, hc = lsplit ? nch / 2 : nch;
+  dim3 glo(g2.x, hc), ghi(g2.x, nch - hc);
+  auto lapd = [&](cudaStream_t st, const R* dsrc, dim3 g, int klo, int khi) -> cudaError_t {
+    return launch_k(k_ss_lapd<R>, g, bs, 0, st, G, U, T, dsrc, (const R*)P.p, kc, klo, khi);
   };
   const R Kd = (R)(diff_D * dbar4 / dt);
   const double dts[3] = {dt / 3.0, dt / n_small, dt / n_small};
@@ -1548,14 +1563,14 @@ int Impl<R>::large_step(double dt, int n_small) {
     const bool early_grad = divdamp && s > 0;    // D of X^t is ready before the slow terms
     if (early_grad) {
       mark(THOR_K_SS_LAPD, true);
-      chk(lapd(aux, (const R*)T.dd0));
+      chk(lapd(aux, (const R*)T.dd0, g2, 0, G.nv));
       mark(THOR_K_SS_LAPD, false);
       ++launches;
     }
     if (fork) chk(cudaEventRecord(ev_join0, side));
     if (hyper) {
       mark(THOR_K_LAP1, true);
-      chk(launch_k(ho ? k_lap1<R, true> : k_lap1<R, false>, g2i, bs, 0, stream, G, U, Xs, T, Kd, kc));
+      chk(launch_k(ho ? k_lap1<R, true> : k_lap1<R, false>, g2i, bs, 0, stream, G, U, Xs, T, Kd, kc, 0, G.nv + 1));
       mark(THOR_K_LAP1, false);
       ++launches;
     }
@@ -1563,8 +1578,9 @@ int Impl<R>::large_step(double dt, int n_small) {
     auto slow = shallow ? (ho ? k_slow<R, true, true> : k_slow<R, true, false>)
                         : (ho ? k_slow<R, false, true> : k_slow<R, false, false>);
     chk(launch_k(slow, g2, bs, 0, stream, G, U, ph, Xs, T, SL, hyper,
-                 s == 0 && divdamp ? T.dd0 : (R*)nullptr, kc));
+                 s == 0 && divdamp ? T.dd0 : (R*)nullptr, kc, 0, G.nv));
     mark(THOR_K_SLOW, false);
+    ++launches;
     mark(THOR_K_SLOW_W, true);
     chk(launch_k(ho ? k_slow_w<R, true> : k_slow_w<R, false>, g2i, bs, 0, stream, G, U, ph, Xt, Xs, T, SL, P, hyper,
                  0, kc));
@@ -1580,25 +1596,39 @@ int Impl<R>::large_step(double dt, int n_small) {
       chk(cudaEventRecord(ev_join, side));
       chk(cudaStreamWaitEvent(stream, ev_join0, 0));
     }
-    launches += 3;
+    launches += 2;
     for (int j = 0; j < nsub[s]; ++j) {
-      // D: of X^t in the first small step, then from the previous column step
-      if (divdamp && !(j == 0 && early_grad)) {
-        mark(THOR_K_SS_LAPD, true);
-        chk(lapd(stream, (const R*)(j == 0 ? T.dd0 : T.dd)));
-        mark(THOR_K_SS_LAPD, false);
-        ++launches;
-      }
       // the last small step of a stage also ends the stage: X^(s+1) = X^(s) + X*
       const int last = j + 1 == nsub[s];
-      mark(THOR_K_SS_MOM, true);
-      chk(launch_k(last ? k_ss_mom<R, true> : k_ss_mom<R, false>, g2, bs, 0, stream, G, U, SL, P, T, (R)dts[s], Kd,
-                   divdamp, Xs, Xo, XsL, XoL, kc));
-      mark(THOR_K_SS_MOM, false);
+      // the three horizontal stencils over levels [kc * klo, khi) on st
+      auto stencils = [&](cudaStream_t st, dim3 g, int klo, int khi) {
+        // D: of X^t in the first small step, then from the previous column step
+        if (divdamp && !(j == 0 && early_grad)) {
+          mark(THOR_K_SS_LAPD, true);
+          chk(lapd(st, (const R*)(j == 0 ? T.dd0 : T.dd), g, klo, khi));
+          mark(THOR_K_SS_LAPD, false);
+          ++launches;
+        }
+        mark(THOR_K_SS_MOM, true);
+        chk(launch_k(last ? k_ss_mom<R, true> : k_ss_mom<R, false>, g, bs, 0, st, G, U, SL, P, T, (R)dts[s], Kd,
+                     divdamp, Xs, Xo, XsL, XoL, kc, klo, khi));
+        mark(THOR_K_SS_MOM, false);
+        mark(THOR_K_SS_FLUX, true);
+        chk(launch_k(k_ss_flux<R>, g, bs, 0, st, G, U, SL, P, T, (R)dts[s], kc, klo, khi));
+        mark(THOR_K_SS_FLUX, false);
+        launches += 2;
+      };
+      if (lsplit) {
+        chk(cudaEventRecord(ev_s1, stream));
+        chk(cudaStreamWaitEvent(side2, ev_s1, 0));
+        stencils(stream, glo, 0, kc * hc);
+        stencils(side2, ghi, hc, G.nv);
+        chk(cudaEventRecord(ev_s2, side2));
+        chk(cudaStreamWaitEvent(stream, ev_s2, 0));
+      } else {
+        stencils(stream, g2, 0, G.nv);
+      }
       const int want_div = divdamp && !last;
-      mark(THOR_K_SS_FLUX, true);
-      chk(launch_k(k_ss_flux<R>, g2, bs, 0, stream, G, U, SL, P, T, (R)dts[s], kc));
-      mark(THOR_K_SS_FLUX, false);
       if (fork && j == 0) chk(cudaStreamWaitEvent(stream, ev_join, 0));
       mark(THOR_K_SS_SOLVE, true);
       if (staged)
@@ -1607,7 +1637,7 @@ int Impl<R>::large_step(double dt, int n_small) {
         chk(launch_k(k_ss_solve<R>, gsolve, 64, solve_smem, stream, G, U, ph, Xs, SL, P, T, F, dts[s],
                      want_div, Xo, XsL, XoL, last));
       mark(THOR_K_SS_SOLVE, false);
-      launches += 3;
+      ++launches;
     }
   }
   if (energy) {
@@ -1652,11 +1682,12 @@ int Impl<R>::anelastic_step(double dt) {
     Xf<R> Xs = s == 0 ? Xt : Xst, Xo = s == 2 ? Xt : Xst;
     if (launch_k(ho ? k_derived<R, true> : k_derived<R, false>, g2i, bs, 0, stream, G, U, ph, Xs, T, shallow, kc))
       return -3;
-    if (hyper && launch_k(ho ? k_lap1<R, true> : k_lap1<R, false>, g2i, bs, 0, stream, G, U, Xs, T, Kd, kc))
+    if (hyper && launch_k(ho ? k_lap1<R, true> : k_lap1<R, false>, g2i, bs, 0, stream, G, U, Xs, T, Kd, kc, 0,
+                          G.nv + 1))
       return -3;
     auto slow = shallow ? (ho ? k_slow<R, true, true> : k_slow<R, true, false>)
                         : (ho ? k_slow<R, false, true> : k_slow<R, false, false>);
-    if (launch_k(slow, g2, bs, 0, stream, G, U, ph, Xs, T, SL, hyper, (R*)nullptr, kc) ||
+    if (launch_k(slow, g2, bs, 0, stream, G, U, ph, Xs, T, SL, hyper, (R*)nullptr, kc, 0, G.nv) ||
         launch_k(ho ? k_slow_w<R, true> : k_slow_w<R, false>, g2i, bs, 0, stream, G, U, ph, Xt, Xs, T, SL, P,
                  hyper, 0, kc))
       return -3;

@@ -119,3 +119,34 @@ def test_l2_hints_change_no_value():
     for o in out[1:]:
         for x, y, f in zip(out[0], o, fields):
             assert np.array_equal(x, y), f
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_level_split_matches_one_chain(prec):
+    """The small steps' stencils split into a lower and an upper level half
+    on two streams (THOR_TUNE_LEVEL_SPLIT, graph replay) compute the same
+    numbers as one chain over all levels."""
+    import torch
+    from harness import init_struct, planet_struct
+    wl = wls.HS_G4.with_(n_large=3)
+    p = thor.THOR_MIXED if prec == "mixed" else thor.THOR_FP64
+    st = torch.cuda.Stream()
+    grid = thor.thor_grid_create(wl.glevel, wl.nv, wl.planet.radius, wl.z_top,
+                                 thor.thor_spring(1.15, 1.0, 1.0, 0.01, 0.0, wl.spring_max_iter))
+    fields = (thor.THOR_FIELD_RHO, thor.THOR_FIELD_MOM, thor.THOR_FIELD_W, thor.THOR_FIELD_RHOTHETA)
+    out = []
+    try:
+        for split, kc in ((0, 2), (1, 2), (1, 3)):
+            s_ = thor.thor_state_init(grid, planet_struct(wl.planet), init_struct(wl, p), st.cuda_stream)
+            try:
+                thor.thor_tune(s_, thor.THOR_TUNE_KCHUNK, kc)
+                thor.thor_tune(s_, thor.THOR_TUNE_LEVEL_SPLIT, split)
+                thor.thor_step(s_, wl.n_large, wl.n_small, wl.dt)
+                out.append([thor.thor_state_get(s_, f, wl.ncol, wl.nv) for f in fields])
+            finally:
+                thor.thor_state_destroy(s_)
+    finally:
+        thor.thor_grid_destroy(grid)
+    for o in out[1:]:
+        for x, y, f in zip(out[0], o, fields):
+            assert np.array_equal(x, y), f
