@@ -1581,14 +1581,17 @@ int Impl<R>::large_step(double dt, int n_small) {
                  s == 0 && divdamp ? T.dd0 : (R*)nullptr, kc, 0, G.nv));
     mark(THOR_K_SLOW, false);
     ++launches;
-    mark(THOR_K_SLOW_W, true);
-    chk(launch_k(ho ? k_slow_w<R, true> : k_slow_w<R, false>, g2i, bs, 0, stream, G, U, ph, Xt, Xs, T, SL, P, hyper,
-                 0, kc));
-    mark(THOR_K_SLOW_W, false);
+    // the vertical momentum's slow term and the factorisation only gate the
+    // first column solve: they run on the side stream beside the first
+    // small step's stencils
     if (fork) {
       chk(cudaEventRecord(ev_fork, stream));
       chk(cudaStreamWaitEvent(side, ev_fork, 0));
     }
+    mark(THOR_K_SLOW_W, true);
+    chk(launch_k(ho ? k_slow_w<R, true> : k_slow_w<R, false>, g2i, bs, 0, aux, G, U, ph, Xt, Xs, T, SL, P, hyper, 0,
+                 kc));
+    mark(THOR_K_SLOW_W, false);
     mark(THOR_K_SS_FACTOR, true);
     chk(launch_k(k_ss_factor<R>, gsolve, 64, 0, aux, G, U, ph, SL, F, dts[s]));
     mark(THOR_K_SS_FACTOR, false);
