@@ -173,6 +173,7 @@ void carve(Carver& cv, Impl<R>& I, int ncol, int nv) {
   I.G.wgrad = cv.take<R>(28 * S);
   I.G.wlap = cv.take<R>(7 * S);
   I.G.rhat = cv.take<R>(3 * S);
+  I.G.gcor = cv.take<R>(3 * S);
   I.G.sinlat = cv.take<R>(S);
   I.G.coslat = cv.take<R>(S);
   I.G.xdir = cv.take<R>(S);
@@ -207,7 +208,7 @@ int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert
   const int ncol = h.ncol, S = colp_of(ncol), nv = h.nv;
   std::vector<int> nbr(6 * (size_t)S, 0);
   std::vector<R> wdiv(28 * (size_t)S, 0), wgrad(28 * (size_t)S, 0), wlap(7 * (size_t)S, 0),
-      rhat(3 * (size_t)S, 0), sl(S, 0), cl(S, 0), clon(S, 0);
+      rhat(3 * (size_t)S, 0), gcor(3 * (size_t)S, 0), sl(S, 0), cl(S, 0), clon(S, 0);
   std::vector<double> area(S, 0.0);
   for (int c = 0; c < ncol; ++c) {
     for (int j = 0; j < 6; ++j) {
@@ -221,8 +222,10 @@ int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert
         wgrad[q + d] = (R)h.w_grad[21 * c + 3 * j + d];
       }
       wgrad[q + 3] = (R)h.w_lap[7 * c + j];
+      wdiv[q + 3] = (R)h.w_lap[7 * c + j];
       wlap[(size_t)j * S + c] = (R)h.w_lap[7 * c + j];
     }
+    for (int d = 0; d < 3; ++d) gcor[(size_t)d * S + c] = (R)(h.w_grad[21 * c + d] - h.w_div[21 * c + d]);
     double x = h.P[3 * c], y = h.P[3 * c + 1], z = h.P[3 * c + 2];
     rhat[c] = (R)x;
     rhat[S + c] = (R)y;
@@ -242,6 +245,7 @@ int upload_tables(Impl<R>& I, const HostGrid& h, const std::vector<double>* vert
   e = e ? e : up(I.G.wgrad, wgrad.data(), wgrad.size() * sizeof(R));
   e = e ? e : up(I.G.wlap, wlap.data(), wlap.size() * sizeof(R));
   e = e ? e : up(I.G.rhat, rhat.data(), rhat.size() * sizeof(R));
+  e = e ? e : up(I.G.gcor, gcor.data(), gcor.size() * sizeof(R));
   e = e ? e : up(I.G.sinlat, sl.data(), sl.size() * sizeof(R));
   e = e ? e : up(I.G.coslat, cl.data(), cl.size() * sizeof(R));
   e = e ? e : up(I.G.xdir, clon.data(), clon.size() * sizeof(R));

@@ -72,8 +72,13 @@ template <typename R>
 struct Geo {
   int ncol, colp, nv;
   const int* nbr;       // [6][colp]; slot 5 of a pentagon repeats the column
-  const R* wdiv;        // [7][colp][4]: x, y, z, 0
+  const R* wdiv;        // [7][colp][4]: x, y, z and the Laplacian weight of the point
   const R* wgrad;       // [7][colp][4]: x, y, z and the Laplacian weight of the point
+  // [3][colp]: wgrad_0 - wdiv_0. The gradient weights are the divergence
+  // weights projected on the tangent plane, plus -sum_e l_e n_e / A at the
+  // centre point, so grad f = P_h(sum_j wdiv_j f_j + gcor f_0): a kernel
+  // that projects its result anyway needs only the divergence weights.
+  const R* gcor;
   const R* wlap;        // [7][colp]
   const R* rhat;        // [3][colp]
   const R* sinlat;      // [colp]

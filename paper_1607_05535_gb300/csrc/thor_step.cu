@@ -136,10 +136,13 @@ __device__ __forceinline__ void d_slow(const Geo<R>& G, const VR<R>& U, const Ph
   if (c >= G.ncol) return;
   const int S = G.colp;
   Nbr7 nb = load_nbr(G, c);
-  W7x3<R> wd = load_w7x3(G.wdiv, S, c);
-  W7x3<R> wg;
+  // the divergence and Laplacian weights; the gradient of p below is taken
+  // with the divergence weights plus the centre correction, unprojected
+  // (S_M is projected as a whole)
+  W7x3<R> wd;
   W7<R> wl;
-  load_w7x3_lap(G.wgrad, S, c, wg, wl);
+  load_w7x3_lap(G.wdiv, S, c, wd, wl);
+  const R gcx = ld(G.gcor + (c)), gcy = ld(G.gcor + (S + c)), gcz = ld(G.gcor + (2 * S + c));
   R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
   const R two_om = pc<R>(ph.two_omega, ph.two_omega_f), gamma = pc<R>(ph.gamma, ph.gamma_f),
           Rd = pc<R>(ph.Rd, ph.Rd_f);
@@ -174,9 +177,14 @@ __device__ __forceinline__ void d_slow(const Geo<R>& G, const VR<R>& U, const Ph
       sdh += f;
       sdt += (SH ? ld(T.theta + q) : av.w) * f;
       const R pq = ld(T.pp + q);
-      gx += wg.x[j] * pq;
-      gy += wg.y[j] * pq;
-      gz += wg.z[j] * pq;
+      gx += wd.x[j] * pq;
+      gy += wd.y[j] * pq;
+      gz += wd.z[j] * pq;
+      if (j == 0) {
+        gx += gcx * pq;
+        gy += gcy * pq;
+        gz += gcz * pq;
+      }
       if (hyper) {
         const Q4<R> hq = ld4(T.q4, (size_t)q);
         hr += wl.v[j] * hq.w;
@@ -1062,7 +1070,7 @@ __global__ void k_lap1(Geo<R> G, VR<R> U, Xf<R> X, Work<R> T, R Kd, int kchunk, 
   d_lap1<R, HO>(G, U, X, T, Kd, kchunk, blockIdx.x, blockIdx.y + klo, kend);
 }
 template <typename R, bool SH, bool HO>
-__global__ void __launch_bounds__(kMaxBlock, 2)
+__global__ void __launch_bounds__(kMaxBlock, sizeof(R) == sizeof(float) ? 3 : 2)
     k_slow(Geo<R> G, VR<R> U, Phys ph, Xf<R> X, Work<R> T, Slow<R> SL, int hyper, R* d0, int kchunk, int klo,
            int kend) {
   d_slow<R, SH, HO>(G, U, ph, X, T, SL, hyper, d0, kchunk, blockIdx.x, blockIdx.y + klo, kend);
