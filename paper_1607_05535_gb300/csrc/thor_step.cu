@@ -975,20 +975,26 @@ __device__ __forceinline__ void d_physics(const Geo<R>& G, const VR<R>& U, const
       KT = R(1) / R(1.5e5);
       Teq = Tv + bt * (R)hj_dT * clcl;
     }
+    // no friction (K_v = 0: above sigma_b, and everywhere on the hot Jupiter)
+    // leaves the momentum as it is, so it is neither read nor written there
     if (cmp) {
-      const R dfr = -Kv * rdt / (R(1) + Kv * rdt);      // 1 / (1 + K_v dt) - 1
-      comp_add<R>(X.mx, XL.mx, X.mx, XL.mx, i, (ld(X.mx + i) + ld(XL.mx + i)) * dfr);
-      comp_add<R>(X.my, XL.my, X.my, XL.my, i, (ld(X.my + i) + ld(XL.my + i)) * dfr);
-      comp_add<R>(X.mz, XL.mz, X.mz, XL.mz, i, (ld(X.mz + i) + ld(XL.mz + i)) * dfr);
+      if (Kv != R(0)) {
+        const R dfr = -Kv * rdt / (R(1) + Kv * rdt);      // 1 / (1 + K_v dt) - 1
+        comp_add<R>(X.mx, XL.mx, X.mx, XL.mx, i, (ld(X.mx + i) + ld(XL.mx + i)) * dfr);
+        comp_add<R>(X.my, XL.my, X.my, XL.my, i, (ld(X.my + i) + ld(XL.my + i)) * dfr);
+        comp_add<R>(X.mz, XL.mz, X.mz, XL.mz, i, (ld(X.mz + i) + ld(XL.mz + i)) * dfr);
+      }
       const R dT = KT * rdt * (Teq - Temp) / (R(1) + KT * rdt);
       const R th = ld(U.thb + (k)) + thp;
       comp_add<R>(X.th, XL.th, X.th, XL.th, i, th * rexpm1<R>(rlog1p<R>(dT / Temp) * inv_gamma));
       continue;
     }
-    R fr = R(1) / (R(1) + Kv * rdt);
-    X.mx[i] *= fr;
-    X.my[i] *= fr;
-    X.mz[i] *= fr;
+    if (Kv != R(0)) {
+      R fr = R(1) / (R(1) + Kv * rdt);
+      X.mx[i] *= fr;
+      X.my[i] *= fr;
+      X.mz[i] *= fr;
+    }
     R Tn = (Temp + KT * rdt * Teq) / (R(1) + KT * rdt);
     // rho theta at fixed rho: Th/Th_bar = ((rho/rho_bar)(T/T_bar))^(1/gamma)
     R lr = rlog1p<R>(rhop / ld(U.rhob + (k))) + rlog<R>(Tn / ld(U.Tb + (k)));
