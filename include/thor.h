@@ -96,6 +96,19 @@ int thor_grid_neighbours(const thor_grid* grid, int* nbr, size_t n);
  * area[ncol] (caller's buffer); n must be ncol, else THOR_EINVAL. */
 int thor_grid_areas(const thor_grid* grid, double* area, size_t n);
 
+/* Nearest coarse cell of every fine cell: fine_to_coarse[i] = the column of
+ * `coarse` whose centre is closest (largest dot product on the unit sphere)
+ * to fine column i, the map thor_coarse_grain takes. No passage of the
+ * paper (the learned closure's coarse graining, an extension): a greedy
+ * walk over the coarse grid's neighbour graph from the previous fine
+ * column's answer, which ends at the nearest centre because the coarse
+ * cells are the Voronoi-like control volumes of their centres; a walk that
+ * stops at a local optimum that is not the global one is caught by a check
+ * against every neighbour's neighbours, and such a column falls back to a
+ * search over all coarse columns. Host only; n must be the fine column
+ * count, else THOR_EINVAL. */
+int thor_grid_coarse_map(const thor_grid* fine, const thor_grid* coarse, int* fine_to_coarse, size_t n);
+
 void thor_grid_destroy(thor_grid* grid);
 
 /* ----------------------------------------------------------------- state */

@@ -29,7 +29,7 @@ THOR_MLP_TUNE_TCGEN05 = 0
 
 EXPORTED = [
     "thor_strerror", "thor_grid_create", "thor_grid_info", "thor_grid_points",
-    "thor_grid_neighbours", "thor_grid_areas", "thor_grid_destroy", "thor_state_init",
+    "thor_grid_neighbours", "thor_grid_areas", "thor_grid_coarse_map", "thor_grid_destroy", "thor_state_init",
     "thor_step", "thor_diag", "thor_state_get", "thor_state_set", "thor_state_get_all", "thor_state_set_all",
     "thor_launch_count",
     "thor_tune", "thor_profile", "thor_profile_read", "thor_state_destroy",
@@ -101,6 +101,7 @@ def _load():
         "thor_grid_points": (I, [P, P, Z]),
         "thor_grid_neighbours": (I, [P, P, Z]),
         "thor_grid_areas": (I, [P, P, Z]),
+        "thor_grid_coarse_map": (I, [P, P, P, Z]),
         "thor_grid_destroy": (None, [P]),
         "thor_state_init": (I, [P, ctypes.POINTER(thor_planet), ctypes.POINTER(thor_init), P,
                                 ctypes.POINTER(P)]),
@@ -203,6 +204,15 @@ def thor_grid_areas(grid):
     n = thor_grid_info(grid)["ncol"]
     out = np.empty(n, dtype=np.float64)
     _check(_lib.thor_grid_areas(grid, _ptr(out), out.size), "thor_grid_areas")
+    return out
+
+
+def thor_grid_coarse_map(fine, coarse):
+    """Nearest coarse column of every fine column (int32, the fine grid's
+    column count), the map thor_coarse_grain takes."""
+    n = thor_grid_info(fine)["ncol"]
+    out = np.empty(n, dtype=np.int32)
+    _check(_lib.thor_grid_coarse_map(fine, coarse, _ptr(out), out.size), "thor_grid_coarse_map")
     return out
 
 

@@ -30,20 +30,13 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import (THOR_FIELD_MOM, THOR_FIELD_RHO, THOR_FIELD_RHOTHETA, thor_closure_attach,
+from . import (THOR_FIELD_MOM, THOR_FIELD_RHO, THOR_FIELD_RHOTHETA, thor_closure_attach, thor_grid_coarse_map,
                thor_closure_features, thor_coarse_grain, thor_grid_create, thor_grid_info,
                thor_grid_points, thor_init, thor_mlp_forward, thor_mlp_train_step, thor_planet,
                thor_grid_destroy, thor_mlp_create, thor_mlp_destroy, thor_spring, thor_state_destroy,
                thor_state_get, thor_state_init, thor_state_set, thor_step)
 
 FIELDS = 5
-
-
-def fine_to_coarse_map(fine_points, coarse_points):
-    """Coarse column whose centre is nearest to each fine centre (the coarse
-    control volume containing it, up to the centroid offsets)."""
-    from scipy.spatial import cKDTree
-    return cKDTree(coarse_points).query(fine_points)[1].astype(np.int32)
 
 
 def column_fields(state, ncol, nv):
@@ -80,7 +73,9 @@ def make_setup(wl, fine_glevel, coarse_glevel, precision, stream, spring_iters=1
     coarse = thor_state_init(gc, planet, init, stream)
     scratch = thor_state_init(gc, planet, init, stream)
     extra = thor_state_init(gc, planet, init, stream)
-    fmap = fine_to_coarse_map(thor_grid_points(gf), thor_grid_points(gc))
+    # coarse column whose centre is nearest to each fine centre (the coarse
+    # control volume containing it, up to the centroid offsets)
+    fmap = thor_grid_coarse_map(gf, gc)
     return Setup(gf, gc, fine, coarse, scratch, extra, fmap, thor_grid_info(gf)["ncol"],
                  thor_grid_info(gc)["ncol"], wl.nv)
 

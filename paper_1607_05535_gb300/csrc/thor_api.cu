@@ -818,6 +818,60 @@ int thor_grid_areas(const thor_grid* g, double* area, size_t n) {
   return THOR_OK;
 }
 
+int thor_grid_coarse_map(const thor_grid* fine, const thor_grid* coarse, int* map, size_t n) {
+  if (!fine || !coarse || !map || n != (size_t)fine->h.ncol) return THOR_EINVAL;
+  const std::vector<double>& F = fine->h.P;
+  const std::vector<double>& C = coarse->h.P;
+  const std::vector<int>& nb = coarse->h.nbr;
+  const int nc = coarse->h.ncol;
+  auto dot = [&](int i, int c) { return F[3 * i] * C[3 * c] + F[3 * i + 1] * C[3 * c + 1] + F[3 * i + 2] * C[3 * c + 2]; };
+  // greedy ascent of the dot product over the neighbour graph
+  auto walk = [&](int i, int c) {
+    double best = dot(i, c);
+    for (int it = 0; it < nc; ++it) {
+      int next = -1;
+      for (int k = 0; k < 6; ++k) {
+        const int q = nb[6 * c + k];
+        if (q < 0) continue;
+        const double d = dot(i, q);
+        if (d > best) {
+          best = d;
+          next = q;
+        }
+      }
+      if (next < 0) break;
+      c = next;
+    }
+    return c;
+  };
+  // no point of the second ring beats c (the walk's end is the global
+  // nearest centre unless the grid is badly distorted)
+  auto local_ok = [&](int i, int c) {
+    const double d0 = dot(i, c);
+    for (int k = 0; k < 6; ++k) {
+      const int q = nb[6 * c + k];
+      if (q < 0) continue;
+      for (int l = 0; l < 6; ++l) {
+        const int r = nb[6 * q + l];
+        if (r >= 0 && dot(i, r) > d0) return false;
+      }
+    }
+    return true;
+  };
+  int c = 0;
+  for (int i = 0; i < (int)n; ++i) {
+    c = walk(i, c);
+    if (!local_ok(i, c)) {
+      int bc = 0;
+      for (int q = 1; q < nc; ++q)
+        if (dot(i, q) > dot(i, bc)) bc = q;
+      c = bc;
+    }
+    map[i] = c;
+  }
+  return THOR_OK;
+}
+
 void thor_grid_destroy(thor_grid* g) { delete g; }
 
 int thor_state_init(thor_grid* grid, const thor_planet* pl, const thor_init* in, void* stream,

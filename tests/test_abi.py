@@ -132,3 +132,26 @@ def test_canonical_numbering():
     assert np.allclose(P[0], [np.cos(lat), 0, np.sin(lat)])
     # south rhombus 0 owns L_0 (lat -atan(1/2), lon 36 deg)
     assert np.allclose(P[5 * n * n], [np.cos(lat) * np.cos(np.pi / 5), np.cos(lat) * np.sin(np.pi / 5), -np.sin(lat)])
+
+
+@pytest.mark.parametrize("gf,gc,iters", [(3, 2, 10), (4, 3, 10), (5, 4, 0), (4, 2, 10)])
+def test_coarse_map_is_the_nearest_centre(gf, gc, iters):
+    """thor_grid_coarse_map (the closure's coarse-graining map, built on the
+    host by a walk over the coarse neighbour graph) gives every fine column
+    the coarse column of largest dot product, as a brute-force search does;
+    every coarse column receives at least one fine column."""
+    sp = thor.thor_spring(1.15, 1.0, 1.0, 0.01, 0.0, iters)
+    F = thor.thor_grid_create(gf, 4, 6.371e6, 3.0e4, sp)
+    C = thor.thor_grid_create(gc, 4, 6.371e6, 3.0e4, sp)
+    try:
+        m = thor.thor_grid_coarse_map(F, C)
+        pf, pc = thor.thor_grid_points(F), thor.thor_grid_points(C)
+        d = pf @ pc.T
+        best = d.max(axis=1)
+        assert np.all(d[np.arange(len(m)), m] >= best - 1e-15)
+        assert len(np.unique(m)) == len(pc)
+        with pytest.raises(thor.ThorError):
+            thor._check(thor._lib.thor_grid_coarse_map(F, C, thor._ptr(m), len(m) - 1), "thor_grid_coarse_map")
+    finally:
+        thor.thor_grid_destroy(F)
+        thor.thor_grid_destroy(C)
