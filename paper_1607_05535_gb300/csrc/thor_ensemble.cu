@@ -33,6 +33,9 @@ struct EnsImpl : EnsBase {
   std::vector<cudaStream_t> streams;  // distinct member streams other than the ensemble's
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // the upper level halves of the small steps' stencils (a graph branch)
+  cudaStream_t side2 = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   EnsPlan<R> plan;
   Member<R>* dM = nullptr;
   SolveMaps* dmaps = nullptr;          // members' staged-solve descriptors, in plan order
@@ -55,6 +58,12 @@ struct EnsImpl : EnsBase {
     if (dmapc) cudaFree(dmapc);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
+    if (side2) {
+      cudaStreamSynchronize(side2);
+      cudaStreamDestroy(side2);
+    }
+    if (ev_a) cudaEventDestroy(ev_a);
+    if (ev_b) cudaEventDestroy(ev_b);
   }
   void drop_graph() override {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -73,6 +82,9 @@ struct EnsImpl : EnsBase {
     p.nv = mem[0]->G.nv;
     p.kchunk = kchunk;
     p.block = block;
+    p.side2 = side2;
+    p.ev_a = ev_a;
+    p.ev_b = ev_b;
     for (int q = 0; q < n; ++q) {
       const int i = order[q];
       const Impl<R>* I = mem[i];
@@ -266,6 +278,14 @@ int make_ens(thor_ensemble* E) {
   if (cudaEventCreateWithFlags(&impl->ev_in, cudaEventDisableTiming) ||
       cudaEventCreateWithFlags(&impl->ev_out, cudaEventDisableTiming))
     return THOR_ECUDA;
+  // optional: without it the stencils run as one chain
+  if (cudaStreamCreateWithFlags(&impl->side2, cudaStreamNonBlocking) ||
+      cudaEventCreateWithFlags(&impl->ev_a, cudaEventDisableTiming) ||
+      cudaEventCreateWithFlags(&impl->ev_b, cudaEventDisableTiming)) {
+    cudaGetLastError();
+    if (impl->side2) cudaStreamDestroy(impl->side2);
+    impl->side2 = nullptr;
+  }
   E->impl = std::move(impl);
   return THOR_OK;
 }

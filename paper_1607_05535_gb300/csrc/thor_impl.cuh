@@ -371,6 +371,10 @@ struct EnsPlan {
   std::vector<int> active[3], activec[3];  // blocks of the members still stepping at small step j
   int any_hyper = 0, any_divdamp = 0, any_forcing = 0;
   int staged = 0;                   // every member runs the TMA-staged column solve
+  // the small steps' stencils in two level halves, the upper on side2,
+  // forked and joined by ev_a / ev_b (null side2: one chain)
+  cudaStream_t side2 = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
 };
 
 template <typename R>

@@ -1431,22 +1431,31 @@ __global__ void __launch_bounds__(64)
   d_ss_factor<R>(a.G, a.U, a.ph, a.SL, a.F, a.dts[s], e.y, 0);
 }
 template <typename R>
+// the small-step stencils over levels [kchunk * klo, khi) (as k_ss_*)
 __global__ void ke_ss_lapd(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int j,
-                           int kchunk) {
+                           int kchunk, int klo, int khi) {
   THOR_MEMBER();
-  if (a.divdamp) d_ss_lapd<R>(a.G, a.U, a.T, j == 0 ? a.T.dd0 : a.T.dd, a.P.p, kchunk, e.y, blockIdx.y);
+  Geo<R> G = a.G;
+  G.nv = khi;
+  if (a.divdamp) d_ss_lapd<R>(G, a.U, a.T, j == 0 ? a.T.dd0 : a.T.dd, a.P.p, kchunk, e.y, blockIdx.y + klo);
 }
 template <typename R>
 __global__ void ke_ss_mom(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int j,
-                          int kchunk) {
+                          int kchunk, int klo, int khi) {
   THOR_MEMBER();
-  d_ss_mom<R>(a.G, a.U, a.SL, a.P, a.T, (R)a.dts[s], a.Kd, a.divdamp, Xs, s == 2 ? a.Xt : a.Xst,
-              s == 0 ? a.XtL : Xf<R>{}, s == 2 ? a.XtL : Xf<R>{}, j + 1 == a.nsub[s], kchunk, e.y, blockIdx.y);
+  Geo<R> G = a.G;
+  G.nv = khi;
+  d_ss_mom<R>(G, a.U, a.SL, a.P, a.T, (R)a.dts[s], a.Kd, a.divdamp, Xs, s == 2 ? a.Xt : a.Xst,
+              s == 0 ? a.XtL : Xf<R>{}, s == 2 ? a.XtL : Xf<R>{}, j + 1 == a.nsub[s], kchunk, e.y,
+              blockIdx.y + klo);
 }
 template <typename R>
-__global__ void ke_ss_flux(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk) {
+__global__ void ke_ss_flux(const Member<R>* __restrict__ M, const int2* __restrict__ map, int s, int kchunk,
+                           int klo, int khi) {
   THOR_MEMBER();
-  d_ss_flux<R>(a.G, a.U, a.SL, a.P, a.T, (R)a.dts[s], kchunk, e.y, blockIdx.y);
+  Geo<R> G = a.G;
+  G.nv = khi;
+  d_ss_flux<R>(G, a.U, a.SL, a.P, a.T, (R)a.dts[s], kchunk, e.y, blockIdx.y + klo);
 }
 template <typename R>
 __global__ void __launch_bounds__(64)
@@ -1824,13 +1833,28 @@ int ensemble_large_step(const EnsPlan<R>& E, cudaStream_t stream, long long* lau
     n += 4;
     for (int j = 0; j < E.maxsub[s]; ++j) {
       const int nb = E.active[s][j], nbc = E.activec[s][j];
-      const dim3 a2(nb, yc);
-      if (E.any_divdamp) {
-        ke_ss_lapd<R><<<a2, bs, 0, stream>>>(M, E.map, s, j, kc);
-        ++n;
+      // the stencils over level chunks [c0, c1) on st
+      auto stencils = [&](cudaStream_t st, int c0, int c1) {
+        const dim3 a2(nb, c1 - c0);
+        const int khi = min(E.nv, c1 * kc);
+        if (E.any_divdamp) {
+          ke_ss_lapd<R><<<a2, bs, 0, st>>>(M, E.map, s, j, kc, c0, khi);
+          ++n;
+        }
+        ke_ss_mom<R><<<a2, bs, 0, st>>>(M, E.map, s, j, kc, c0, khi);
+        ke_ss_flux<R><<<a2, bs, 0, st>>>(M, E.map, s, kc, c0, khi);
+        n += 2;
+      };
+      if (E.side2 && yc >= 2) {
+        cudaEventRecord(E.ev_a, stream);
+        cudaStreamWaitEvent(E.side2, E.ev_a, 0);
+        stencils(stream, 0, yc / 2);
+        stencils(E.side2, yc / 2, yc);
+        cudaEventRecord(E.ev_b, E.side2);
+        cudaStreamWaitEvent(stream, E.ev_b, 0);
+      } else {
+        stencils(stream, 0, yc);
       }
-      ke_ss_mom<R><<<a2, bs, 0, stream>>>(M, E.map, s, j, kc);
-      ke_ss_flux<R><<<a2, bs, 0, stream>>>(M, E.map, s, kc);
       if constexpr (sizeof(R) == sizeof(float)) {
         if (E.staged)
           ke_ss_solve_tma<<<nbc, 32 * kSolveWarps, solve_tma_smem_bytes(E.nv), stream>>>(M, E.mapc, s, j);
@@ -1839,7 +1863,7 @@ int ensemble_large_step(const EnsPlan<R>& E, cudaStream_t stream, long long* lau
       } else {
         ke_ss_solve<R><<<nbc, 64, solve_smem, stream>>>(M, E.mapc, s, j);
       }
-      n += 3;
+      ++n;
     }
   }
   if (E.any_forcing) {
