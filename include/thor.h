@@ -404,7 +404,7 @@ int thor_zonal_read_w(thor_state* state, int nlat, double* out, size_t n, long l
 
 /* Launch-shape autotuner (an extension; the paper fixes no launch shapes).
  * Times `steps` large steps of (n_small, dt) for every levels-per-thread
- * value in {1, 2, 4, 8} and block size in {64, 128, 256}, each after one
+ * value in {1, 2, 3, 4, 6, 8} and block size in {64, 96, 128, 192, 256}, each after one
  * untimed step, with CUDA events on the state's stream; restores the state's
  * prognostic fields before every candidate and at the end (the state is
  * unchanged), sets the fastest shape (as thor_tune would) and returns it with

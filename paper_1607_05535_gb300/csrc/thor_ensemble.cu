@@ -218,8 +218,10 @@ struct EnsImpl : EnsBase {
 template <typename Run, typename Set, typename Save>
 int autotune_loop(cudaStream_t st, int steps, Run run, Set set, Save save_restore, int* best_kc, int* best_bs,
                   double* best_ms) {
-  static const int kcs[] = {1, 2, 4, 8};
-  static const int bss[] = {64, 128, 256};
+  // levels per thread and block sizes that need not divide the level and
+  // column counts (3 levels and 128 columns win at glevel 6 x 32 levels)
+  static const int kcs[] = {1, 2, 3, 4, 6, 8};
+  static const int bss[] = {64, 96, 128, 192, 256};
   cudaEvent_t a = nullptr, b = nullptr;
   if (cudaEventCreate(&a) || cudaEventCreate(&b)) return THOR_ECUDA;
   int rc = save_restore(true);
