@@ -252,10 +252,10 @@ __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 // planes: stage constants (slow tendencies, Pi, theta, the factors of the
 // column matrix), read once per small step, and perturbations and the
 // split's intermediates, written by one kernel and read by the next. At
-// glevel 6 x 32 levels the two sets together exceed L2, so without hints
-// each small step streams both from HBM; loading the constants evict-first
-// and keeping the perturbations evict-last lets the second set stay in L2.
-// Hints change where a line lives, never a value.
+// glevel 6 x 32 levels the two sets together exceed L2; the constants can
+// be loaded evict-first and the perturbations kept evict-last, so that the
+// second set has the better chance of staying in L2 (the first alone is
+// what pays at that size). Hints change where a line lives, never a value.
 enum { kL2Normal = 0, kL2First = 1, kL2Last = 2 };
 __device__ __forceinline__ uint64_t l2_policy(int prio) {
   uint64_t p;
