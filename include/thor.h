@@ -391,7 +391,7 @@ int thor_zonal_read_w(thor_state* state, int nlat, double* out, size_t n, long l
  * the interfaces, the column matrix's factors) evict-first, bit 1 keeps
  * the perturbations and the kernel split's intermediates evict-last.
  * Results do not depend on it (tested bit for bit). Library-wide on the
- * current device (every state and ensemble); default 1. THOR_EINVAL
+ * current device (every state and ensemble); default 3. THOR_EINVAL
  * outside 0..3, THOR_ECUDA if the device rejects it.
  * THOR_TUNE_LEVEL_SPLIT (0 or 1; a launch-shape knob): 1 runs the small
  * steps' three horizontal stencils (the Laplacian of D, the momentum step,

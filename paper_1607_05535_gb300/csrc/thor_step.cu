@@ -412,12 +412,17 @@ __device__ __forceinline__ void d_stage_init(const Geo<R>& G, const VR<R>& U, co
 // L2 eviction priorities of the small step's planes (thor_tune
 // THOR_TUNE_L2_HINTS): bit 0 loads the stage constants evict-first, bit 1
 // keeps the perturbations and the split's intermediates evict-last. Default
-// 1: at glevel 6 x 32 levels the large step runs 2% faster than without
-// hints (1.486 against 1.521 ms); keeping the perturbations evict-last as
-// well gains nothing more.
-__constant__ int c_l2mode = 1;
+// 3 (both): at glevel 6 x 32 levels the large step takes 1.368 ms, against
+// 1.373 with the constants' hint alone and 1.402 without hints. Float64
+// states keep their perturbations at the normal priority whatever the mode:
+// their set is twice the size, and held evict-last it slowed the float64
+// large step from 9.85 to 11.1 ms.
+__constant__ int c_l2mode = 3;
 __device__ __forceinline__ uint64_t pol_stream() { return l2_policy((c_l2mode & 1) ? kL2First : kL2Normal); }
-__device__ __forceinline__ uint64_t pol_keep() { return l2_policy((c_l2mode & 2) ? kL2Last : kL2Normal); }
+template <typename R = float>
+__device__ __forceinline__ uint64_t pol_keep() {
+  return l2_policy(sizeof(R) == sizeof(float) && (c_l2mode & 2) ? kL2Last : kL2Normal);
+}
 int set_l2_mode(int mode) { return cudaMemcpyToSymbol(c_l2mode, &mode, sizeof mode) == cudaSuccess ? 0 : -1; }
 
 template <typename R>
@@ -431,7 +436,7 @@ __device__ __forceinline__ void d_ss_lapd(const Geo<R>& G, const VR<R>& U, const
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
-  const uint64_t pk = pol_keep();
+  const uint64_t pk = pol_keep<R>();
   Nbr7 nb = load_nbr(G, c);
   W7<R> wl = load_w7(G.wlap, S, c);
   int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);
@@ -456,7 +461,7 @@ __device__ __forceinline__ void d_ss_mom(const Geo<R>& G, const VR<R>& U, const 
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
-  const uint64_t ps = pol_stream(), pk = pol_keep();
+  const uint64_t ps = pol_stream(), pk = pol_keep<R>();
   Nbr7 nb = load_nbr(G, c);
   W7x3<R> wg = load_w7x3(G.wgrad, S, c);
   R rx = ld(G.rhat + (c)), ry = ld(G.rhat + (S + c)), rz = ld(G.rhat + (2 * S + c));
@@ -546,7 +551,7 @@ __device__ __forceinline__ void d_ss_flux(const Geo<R>& G, const VR<R>& U, const
   int c = bx * blockDim.x + threadIdx.x;
   if (c >= G.ncol) return;
   const int S = G.colp;
-  const uint64_t ps = pol_stream(), pk = pol_keep();
+  const uint64_t ps = pol_stream(), pk = pol_keep<R>();
   Nbr7 nb = load_nbr(G, c);
   W7x3<R> wd = load_w7x3(G.wdiv, S, c);
   int k0 = by * kchunk, k1 = min(G.nv, k0 + kchunk);

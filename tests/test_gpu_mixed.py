@@ -104,7 +104,7 @@ def test_l2_hints_change_no_value():
     fields = (thor.THOR_FIELD_RHO, thor.THOR_FIELD_MOM, thor.THOR_FIELD_W, thor.THOR_FIELD_RHOTHETA)
     out = []
     try:
-        for mode in (0, 3, 2, 1):          # ends at the default, 1
+        for mode in (0, 1, 2, 3):          # ends at the default, 3
             s_ = thor.thor_state_init(grid, planet_struct(wl.planet), init_struct(wl, thor.THOR_MIXED), None)
             try:
                 thor.thor_tune(s_, thor.THOR_TUNE_L2_HINTS, mode)
