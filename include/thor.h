@@ -389,7 +389,8 @@ int thor_zonal_read_w(thor_state* state, int nlat, double* out, size_t n, long l
  * knob): L2 eviction priorities of the acoustic small steps' loads and
  * stores. Bit 0 loads the stage constants (slow tendencies, Pi, theta at
  * the interfaces, the column matrix's factors) evict-first, bit 1 keeps
- * the perturbations and the kernel split's intermediates evict-last.
+ * the perturbations and the kernel split's intermediates evict-last (in
+ * THOR_MIXED states only; THOR_FP64 states keep them at normal priority).
  * Results do not depend on it (tested bit for bit). Library-wide on the
  * current device (every state and ensemble); default 3. THOR_EINVAL
  * outside 0..3, THOR_ECUDA if the device rejects it.
